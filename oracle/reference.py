@@ -1,0 +1,389 @@
+"""FP64 CPU oracle for the new ParaDiag method (Gander & Palitta, arXiv 2304.12597).
+
+TEST INFRASTRUCTURE ONLY.  Only tests/, the smoke check in __graft_entry__ and
+the CPU-baseline leg of bench.py may import this module.  It shares no code
+with the CUDA path; the two meet only in the seeded inputs of `workloads`.
+
+What each function follows (paper sections/equations):
+
+* ``be_solve``          eq. (2) by its plain definition: sequential backward Euler
+                        (C routines in be_oracle.c).  ParaDiag with alpha = 1 and
+                        exact inner solves reaches exactly this solution.
+* ``aao_apply``         left-hand side of eq. (2), (I + tau K) U - U Sigma_1^T.
+* ``sigma1``, ``c_alpha``  Sigma_1 and the (alpha-)circulant C_alpha, eqs. (3), (15).
+* ``dft_matrix``        F, F_{jk} = omega^{(j-1)(k-1)}, omega = exp(-2 pi i / l)
+                        (appendix, proof of Theorem 3.1).
+* ``circulant_eigs``    pi = F C_1 e_1 and gamma = F^{-T} e_l (Algorithm 1, first step).
+* ``dft_time``/``idft_time``  U F^T and U F^{-T} along time (eq. 5, Sec. 2 end).
+* ``paradiag``          Algorithm 1: parallel-in-time solves, b = L F^{-T} e_l (eq. 7),
+                        Algorithm 2 for eq. (8), correction W, U = (L - W) F^{-T}.
+* ``fom_like``          Algorithm 2 with the Arnoldi relation (10), the shifted
+                        relation (11), the projected system (12) and residual (13).
+* ``j_dense``           J_l of eq. (8), formed densely (tiny sizes only).
+* ``periodic_solve_dense``  P^{-1} of Sec. 2 mapped back to time: the circulant
+                        all-at-once system (I + tau K) U - U C_1^T = R.
+* ``kappa_bound``       eq. (14), Theorem 3.1.
+* ``j_extreme_eigs``    the extreme eigenvalues of J_l for SPD K (Sec. 6.1).
+
+Readings of points where the paper is silent or inconsistent (all listed in
+the design doc with their justification):
+
+1. eq. (11)-(13) and Algorithm 2 write t_{m+1,m} where the shifted Arnoldi
+   relation for (1 - pi_i) I + tau K carries tau * t_{m+1,m}; the factor tau is
+   kept here.  (Without it eq. (13) does not equal the explicit residual.)
+2. The residual-norm line of Algorithm 2 omits gamma_i; eq. (13) has it: kept.
+3. Algorithm 2 starts with ||r|| = 1; here ||r|| starts at beta = ||b||, the
+   residual of x_0 = 0, so that at least one iteration runs whenever b != 0.
+4. Breakdown t_{m+1,m} ~ 0 (silent in the paper): K_m(K, b) is invariant, the
+   t-term of eq. (12) vanishes, the residual is zero and the iteration stops.
+5. U = Re((L - W) F^{-T}); the imaginary part is roundoff for real data.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import native
+
+# ----------------------------------------------------------------------------
+# Operators (the problem definition; built independently of the CUDA path)
+# ----------------------------------------------------------------------------
+
+
+class TridiagOp:
+    """Tridiagonal real K given by (lo, diag, up); row i = lo[i], diag[i], up[i]."""
+
+    def __init__(self, lo, diag, up):
+        self.lo = np.asarray(lo, dtype=np.float64)
+        self.diag = np.asarray(diag, dtype=np.float64)
+        self.up = np.asarray(up, dtype=np.float64)
+        self.n = self.diag.size
+
+    def matvec(self, v):
+        w = self.diag * v
+        w[1:] += self.lo[1:] * v[:-1]
+        w[:-1] += self.up[:-1] * v[1:]
+        return w
+
+    def dense(self):
+        n = self.n
+        K = np.diag(self.diag)
+        if n > 1:
+            K += np.diag(self.lo[1:], -1) + np.diag(self.up[:-1], 1)
+        return K
+
+    def shifted_solve(self, s, tau, r):
+        """((s) I + tau K)^{-1} r, complex shift s."""
+        return native.shifted_tridiag_solve(s, tau, self.lo, self.diag, self.up,
+                                            np.asarray(r, dtype=np.complex128))
+
+
+class DenseOp:
+    """Any real K held densely (used for the 2D operator at tiny sizes)."""
+
+    def __init__(self, K):
+        self.K = np.asarray(K, dtype=np.float64)
+        self.n = self.K.shape[0]
+
+    def matvec(self, v):
+        return self.K @ v
+
+    def dense(self):
+        return self.K
+
+    def shifted_solve(self, s, tau, r):
+        return np.linalg.solve(s * np.eye(self.n) + tau * self.K, np.asarray(r, dtype=np.complex128))
+
+
+def k_dense(problem):
+    """K of the problem as a dense matrix.  2D: K = I (x) T_x + T_y (x) I (Sec. 6.1)."""
+    Tx = TridiagOp(problem.k_lo, problem.k_diag, problem.k_up).dense()
+    if problem.dim == 1:
+        return Tx
+    Ty = TridiagOp(problem.k_lo_y, problem.k_diag_y, problem.k_up_y).dense()
+    return np.kron(np.eye(problem.ny), Tx) + np.kron(Ty, np.eye(problem.nx))
+
+
+def k_band(problem):
+    """Row-major band storage of K (kl = ku = 1 in 1D, nx in 2D, x fastest)."""
+    nx, ny = problem.nx, problem.ny
+    if problem.dim == 1:
+        B = np.zeros((nx, 3))
+        B[:, 0] = problem.k_lo
+        B[:, 1] = problem.k_diag
+        B[:, 2] = problem.k_up
+        B[0, 0] = 0.0
+        B[-1, 2] = 0.0
+        return 1, 1, B
+    n = nx * ny
+    w = 2 * nx + 1
+    B = np.zeros((n, w))
+    for iy in range(ny):
+        for ix in range(nx):
+            i = iy * nx + ix
+            B[i, nx] = problem.k_diag[ix] + problem.k_diag_y[iy]
+            if ix > 0:
+                B[i, nx - 1] = problem.k_lo[ix]
+            if ix < nx - 1:
+                B[i, nx + 1] = problem.k_up[ix]
+            if iy > 0:
+                B[i, 0] = problem.k_lo_y[iy]
+            if iy < ny - 1:
+                B[i, 2 * nx] = problem.k_up_y[iy]
+    return nx, nx, B
+
+
+def operator(problem, dense_limit: int = 4096):
+    if problem.dim == 1:
+        return TridiagOp(problem.k_lo, problem.k_diag, problem.k_up)
+    if problem.nbar > dense_limit:
+        raise ValueError("2D oracle operator is dense; use a small grid")
+    return DenseOp(k_dense(problem))
+
+
+# ----------------------------------------------------------------------------
+# eq. (2): definition and sequential solution
+# ----------------------------------------------------------------------------
+
+
+def be_solve(problem, G=None, mdiag=None):
+    """Exact solution of eq. (2): sequential backward Euler, u_0 := 0, G_1 = u0 + tau f_1."""
+    G = problem.G if G is None else G
+    if problem.dim == 1:
+        return native.be_tridiag(problem.tau, problem.k_lo, problem.k_diag, problem.k_up, G, mdiag)
+    kl, ku, B = k_band(problem)
+    return native.be_banded(problem.tau, kl, ku, B, G, mdiag)
+
+
+def aao_apply(problem, U):
+    """(I + tau K) U - U Sigma_1^T of eq. (2) in the row layout (row j = u_{j+1}).
+
+    Column j of U Sigma_1^T is u_{j-1} (Sigma_1 has ones on the first
+    subdiagonal, eq. 3), and u_0 contributes nothing.
+    """
+    U = np.asarray(U, dtype=np.float64)
+    tau = problem.tau
+    if problem.dim == 1:
+        op = TridiagOp(problem.k_lo, problem.k_diag, problem.k_up)
+        KU = np.stack([op.matvec(u) for u in U])
+    else:
+        nx, ny = problem.nx, problem.ny
+        X = U.reshape(U.shape[0], ny, nx)
+        KU = problem.k_diag[None, None, :] * X + problem.k_diag_y[None, :, None] * X
+        KU[:, :, 1:] += problem.k_lo[None, None, 1:] * X[:, :, :-1]
+        KU[:, :, :-1] += problem.k_up[None, None, :-1] * X[:, :, 1:]
+        KU[:, 1:, :] += problem.k_lo_y[None, 1:, None] * X[:, :-1, :]
+        KU[:, :-1, :] += problem.k_up_y[None, :-1, None] * X[:, 1:, :]
+        KU = KU.reshape(U.shape)
+    R = U + tau * KU
+    R[1:] -= U[:-1]
+    return R
+
+
+def sigma1(ell):
+    """Sigma_1: zeros with ones on the first subdiagonal (eq. 3)."""
+    return np.eye(ell, k=-1)
+
+
+def c_alpha(ell, alpha=1.0):
+    """C_alpha = Sigma_1 + alpha e_1 e_l^T (eq. 15; alpha = 1 gives C_1 of eq. 3)."""
+    C = sigma1(ell)
+    C[0, ell - 1] = alpha
+    return C
+
+
+# ----------------------------------------------------------------------------
+# Fourier quantities (Sec. 2 and the appendix)
+# ----------------------------------------------------------------------------
+
+
+def dft_matrix(ell):
+    """F with F_{jk} = omega^{jk} (0-based), omega = exp(-2 pi i / l).  Exponents are
+    reduced mod l before the exponential so every entry is an exact root of unity."""
+    j = np.arange(ell)
+    e = np.outer(j, j) % ell
+    return np.exp(-2j * np.pi * e / ell)
+
+
+def circulant_eigs(ell):
+    """Algorithm 1, first step: pi = F C_1 e_1 and gamma = F^{-T} e_l."""
+    F = dft_matrix(ell)
+    pi = F @ c_alpha(ell, 1.0)[:, 0]
+    e_ell = np.zeros(ell)
+    e_ell[-1] = 1.0
+    gamma = np.linalg.solve(F.T, e_ell.astype(np.complex128))
+    return pi, gamma
+
+
+def dft_time(X):
+    """Row layout of U F^T: hat X[k] = sum_j omega^{jk} X[j] (forward DFT along time)."""
+    X = np.asarray(X)
+    return dft_matrix(X.shape[0]) @ X
+
+
+def idft_time(Xhat):
+    """Row layout of Y F^{-T}: F^{-1} Y (F is symmetric)."""
+    Xhat = np.asarray(Xhat)
+    return np.linalg.solve(dft_matrix(Xhat.shape[0]), Xhat)
+
+
+# ----------------------------------------------------------------------------
+# Algorithm 2 (FOM-like method for eq. 8)
+# ----------------------------------------------------------------------------
+
+
+def fom_like(op, tau, b, pi, gamma, eps=1e-8, maxit=50, q=1, breakdown_tol=1e-14,
+             keep_tau=True, keep_gamma_in_residual=True):
+    """Algorithm 2 for J_l x = b with J_l = I + sum_i gamma_i ((1-pi_i) I + tau K)^{-1}.
+
+    Krylov space K_m(K, b) (eq. 9), Arnoldi by modified Gram-Schmidt (eq. 10).
+    Every q iterations: h_i = ((1-pi_i) I + tau K)^{-1} v_{m+1},
+    S_i = ((1-pi_i) I_m + tau T_m)^{-1}, y_m from eq. (12), ||r_m|| from eq. (13).
+    Returns (x_m, info) with info = dict(m, y, resnorms, breakdown, T, V).
+    ``keep_tau``/``keep_gamma_in_residual`` exist only so tests can show that the
+    literal (tau-less / gamma-less) forms disagree with the explicit residual.
+    """
+    b = np.asarray(b, dtype=np.float64)
+    n = b.size
+    ell = pi.size
+    beta = float(np.linalg.norm(b))
+    info = {"m": 0, "y": np.zeros(0), "resnorms": [], "breakdown": False, "beta": beta}
+    if beta == 0.0:
+        return np.zeros(n), info
+    V = np.zeros((maxit + 1, n))
+    T = np.zeros((maxit + 1, maxit))
+    V[0] = b / beta
+    m = 0
+    r = beta
+    y = None
+    tfac = tau if keep_tau else 1.0
+    while r > eps * beta and m < maxit:
+        m += 1
+        w = op.matvec(V[m - 1])
+        wnorm0 = float(np.linalg.norm(w))
+        for k in range(m):
+            T[k, m - 1] = V[k] @ w
+            w = w - T[k, m - 1] * V[k]
+        t = float(np.linalg.norm(w))
+        T[m, m - 1] = t
+        breakdown = t <= breakdown_tol * max(wnorm0, 1e-300)
+        if not breakdown:
+            V[m] = w / t
+        if m % q == 0 or breakdown or m == maxit:
+            Tm = T[:m, :m]
+            Vm = V[:m]
+            Msys = np.eye(m, dtype=np.complex128)
+            S = []
+            H = []
+            for i in range(ell):
+                Si = np.linalg.inv((1.0 - pi[i]) * np.eye(m) + tau * Tm)
+                S.append(Si)
+                if breakdown:
+                    Msys += gamma[i] * Si
+                else:
+                    hi = op.shifted_solve(1.0 - pi[i], tau, V[m])
+                    H.append(hi)
+                    gi = Vm @ hi  # V_m^T h_i
+                    # (I - tau t V_m^T h_i e_m^T) S_i = S_i - tau t g_i (e_m^T S_i)
+                    Msys += gamma[i] * (Si - tfac * t * np.outer(gi, Si[m - 1, :]))
+            rhs = np.zeros(m, dtype=np.complex128)
+            rhs[0] = beta
+            y = np.linalg.solve(Msys, rhs)
+            if breakdown:
+                r = 0.0
+            else:
+                z = np.zeros(n, dtype=np.complex128)
+                for i in range(ell):
+                    c = S[i][m - 1, :] @ y
+                    g = gamma[i] if keep_gamma_in_residual else 1.0
+                    z += g * H[i] * c
+                proj = z - Vm.T @ (Vm @ z)
+                r = abs(tfac * t) * float(np.linalg.norm(proj))
+            info["resnorms"].append(r)
+        if breakdown:
+            info["breakdown"] = True
+            break
+    x = V[:m].T @ y
+    info.update(m=m, y=y, T=T[: m + 1, :m], V=V[: m + 1], x_imag=float(np.linalg.norm(x.imag)))
+    return x.real, info
+
+
+# ----------------------------------------------------------------------------
+# Algorithm 1 (new ParaDiag with backward Euler)
+# ----------------------------------------------------------------------------
+
+
+def paradiag(problem, G=None, eps=1e-8, maxit=50, q=1, op=None, **kw):
+    """Algorithm 1 end to end on the row layout.  Returns (U, info).
+
+    info holds pi, gamma, Ghat (= rows of G F^T), L, b, x, the Algorithm-2 info
+    and the imaginary part discarded from U.
+    """
+    G = problem.G if G is None else np.asarray(G, dtype=np.float64)
+    op = operator(problem) if op is None else op
+    ell = G.shape[0]
+    tau = problem.tau
+    pi, gamma = circulant_eigs(ell)
+    Ghat = dft_time(G)  # rows: [u0 + tau f_1, ..., tau f_l] F^T e_i
+    L = np.stack([op.shifted_solve(1.0 - pi[i], tau, Ghat[i]) for i in range(ell)])
+    b_c = gamma @ L  # L F^{-T} e_l  (sum_i gamma_i L e_i)
+    b = b_c.real
+    x, kinfo = fom_like(op, tau, b, pi, gamma, eps=eps, maxit=maxit, q=q, **kw)
+    W = np.stack([op.shifted_solve(1.0 - pi[i], tau, x) for i in range(ell)])
+    Uc = idft_time(L - W)
+    info = {"pi": pi, "gamma": gamma, "Ghat": Ghat, "L": L, "b": b,
+            "b_imag": float(np.linalg.norm(b_c.imag)), "x": x, "krylov": kinfo,
+            "U_imag": float(np.linalg.norm(Uc.imag))}
+    return Uc.real, info
+
+
+# ----------------------------------------------------------------------------
+# Dense objects for pins (tiny sizes)
+# ----------------------------------------------------------------------------
+
+
+def j_dense(K, tau, ell):
+    """J_l = I + sum_i gamma_i ((1 - pi_i) I + tau K)^{-1} (eq. 8), formed densely."""
+    K = np.asarray(K, dtype=np.float64)
+    n = K.shape[0]
+    pi, gamma = circulant_eigs(ell)
+    J = np.eye(n, dtype=np.complex128)
+    for i in range(ell):
+        J += gamma[i] * np.linalg.inv((1.0 - pi[i]) * np.eye(n) + tau * K)
+    return J
+
+
+def aao_matrix(K, tau, ell, circulant=False):
+    """I_l (x) (I + tau K) - Sigma_1 (x) I on vec(U) (C_1 instead of Sigma_1 if circulant)."""
+    n = K.shape[0]
+    S = c_alpha(ell, 1.0) if circulant else sigma1(ell)
+    return np.kron(np.eye(ell), np.eye(n) + tau * K) - np.kron(S, np.eye(n))
+
+
+def periodic_solve_dense(K, tau, R):
+    """Solve the circulant system (I + tau K) U - U C_1^T = R (row layout) densely."""
+    R = np.asarray(R)
+    ell, n = R.shape
+    A = aao_matrix(np.asarray(K), tau, ell, circulant=True)
+    return np.linalg.solve(A, R.reshape(-1)).reshape(ell, n)
+
+
+def kappa_bound(tau, lam_min):
+    """eq. (14): kappa(J_l) <= 1 + 1 / (tau lambda_min(K))."""
+    return 1.0 + 1.0 / (tau * lam_min)
+
+
+def j_extreme_eigs(tau, ell, lam_min, lam_max):
+    """Sec. 6.1: lambda_min(J) = 1 + sum_i gamma_i / (1 - pi_i + tau lambda_max(K)),
+    lambda_max(J) = 1 + sum_i gamma_i / (1 - pi_i + tau lambda_min(K))."""
+    pi, gamma = circulant_eigs(ell)
+    lo = 1.0 + np.sum(gamma / (1.0 - pi + tau * lam_max))
+    hi = 1.0 + np.sum(gamma / (1.0 - pi + tau * lam_min))
+    return lo, hi
+
+
+def rel_err(A, B):
+    """||A - B||_F / ||B||_F."""
+    A = np.asarray(A)
+    B = np.asarray(B)
+    nb = np.linalg.norm(B)
+    return float(np.linalg.norm(A - B) / (nb if nb > 0 else 1.0))

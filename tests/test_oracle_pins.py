@@ -1,0 +1,316 @@
+"""Pins of the CPU oracle against facts fixed by the paper and the mathematics.
+
+Each test checks the oracle against something other than itself: a closed
+form, a dense direct solve, an algebraic identity, a library routine, or a
+value printed in the paper (tests/golden/, with citations).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import reference as R
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _sine_eig(k, h):
+    """Eigenvalue of tridiag(-1,2,-1)/h^2 for sin(k pi x): (4/h^2) sin^2(k pi h / 2)."""
+    return 4.0 / h ** 2 * np.sin(k * np.pi * h / 2.0) ** 2
+
+
+# ----------------------------------------------------------------------------
+# Sequential backward Euler (the definition of eq. 2) against closed forms
+# ----------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("n,nt", [(127, 64), (31, 16), (255, 8)])
+def test_be_sine_mode_decay(n, nt):
+    """u0 in sine eigenmodes, f = 0: u_j = sum_k a_k (1 + tau mu_k)^{-j} sin(k pi x)."""
+    P = W.heat1d_sine_modes(n, nt, 1.0, seed=5)
+    U = R.be_solve(P)
+    h = 1.0 / (n + 1)
+    x = h * np.arange(1, n + 1)
+    j = np.arange(1, nt + 1)[:, None]
+    Uc = np.zeros((nt, n))
+    for k, a in zip(P.extra["modes"], P.extra["amps"]):
+        Uc += a * (1.0 + P.tau * _sine_eig(k, h)) ** (-j) * np.sin(k * np.pi * x)[None, :]
+    assert R.rel_err(U, Uc) < 1e-12
+
+
+def test_be_forced_sine_modes_recurrence():
+    """Forcing in sine modes: each mode obeys c_j = (c_{j-1} + g_j) / (1 + tau mu_k)."""
+    n, nt = 63, 64
+    P = W.heat1d_forced(n, nt, 1.0, seed=11)
+    U = R.be_solve(P)
+    h = 1.0 / (n + 1)
+    x = h * np.arange(1, n + 1)
+    t = P.tau * np.arange(1, nt + 1)
+    Uc = np.zeros((nt, n))
+    for k in sorted(set(P.extra["k"])):
+        g = np.zeros(nt)
+        for a, kq, pq in zip(P.extra["amps"], P.extra["k"], P.extra["p"]):
+            if kq == k:
+                g += P.tau * a * np.sin(pq * np.pi * t)
+        c, coef = 0.0, np.zeros(nt)
+        for jj in range(nt):
+            c = (c + g[jj]) / (1.0 + P.tau * _sine_eig(k, h))
+            coef[jj] = c
+        Uc += np.outer(coef, np.sin(k * np.pi * x))
+    assert R.rel_err(U, Uc) < 1e-12
+
+
+def _tiny_problems():
+    return [
+        W.random_tridiag_problem(6, 5, seed=1),
+        W.random_tridiag_problem(1, 4, seed=2),
+        W.random_tridiag_problem(9, 8, seed=3, symmetric=True),
+        W.advdiff1d_pulse(9, 8, 1.0, seed=4),
+        W.heat2d_smooth(3, 4, 0.1, seed=5),
+        W.heat2d_smooth(4, 6, 0.1, seed=6),
+    ]
+
+
+@pytest.mark.parametrize("P", _tiny_problems(), ids=lambda p: p.name)
+def test_be_equals_dense_all_at_once_solve(P):
+    """Dense LU (numpy.linalg.solve) of I_l (x) (I + tau K) - Sigma_1 (x) I equals the oracle."""
+    K = R.k_dense(P)
+    A = R.aao_matrix(K, P.tau, P.nt)
+    Ud = np.linalg.solve(A, P.G.reshape(-1)).reshape(P.nt, P.nbar)
+    assert R.rel_err(R.be_solve(P), Ud) < 1e-13
+
+
+@pytest.mark.parametrize("name", ["config1", "config2", "config4"])
+def test_be_solution_satisfies_eq2(name):
+    """The oracle's U makes the left side of eq. (2) equal G (full-size 1D configs)."""
+    P = W.by_name(name)
+    U = R.be_solve(P)
+    res = R.aao_apply(P, U) - P.G
+    scale = np.linalg.norm(U) * (1.0 + P.tau * np.abs(P.k_diag).max() * 2) + np.linalg.norm(P.G)
+    assert np.linalg.norm(res) / scale < 1e-15
+
+
+def test_be_2d_satisfies_eq2():
+    P = W.heat2d_smooth(31, 16, 0.1, seed=2)
+    U = R.be_solve(P)
+    res = R.aao_apply(P, U) - P.G
+    assert np.linalg.norm(res) / np.linalg.norm(P.G) < 1e-13
+
+
+# ----------------------------------------------------------------------------
+# Sigma_1 = C_1 - e_1 e_l^T (eq. 3) and the B = (I - Sigma_1)/tau form
+# ----------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("ell", [2, 3, 8, 17])
+def test_sigma1_circulant_plus_rank_one(ell):
+    S = R.sigma1(ell)
+    C1 = R.c_alpha(ell, 1.0)
+    e1 = np.eye(ell)[:, [0]]
+    el = np.eye(ell)[:, [ell - 1]]
+    assert np.array_equal(S, C1 - e1 @ el.T)
+    # C_1 is circulant: every column is a cyclic shift of the first.
+    for j in range(ell):
+        assert np.array_equal(C1[:, j], np.roll(C1[:, 0], j))
+    tau = 0.37
+    B = (np.eye(ell) - S) / tau
+    C = (np.eye(ell) - C1) / tau
+    assert np.allclose(B, C + (e1 @ el.T) / tau, atol=0, rtol=0)
+    # The "B = C - (1/tau) e_1 e_l^T" form holds for the skew-circulant C_{-1} (alpha = -1, eq. 15).
+    Cm = (np.eye(ell) - R.c_alpha(ell, -1.0)) / tau
+    assert np.allclose(B, Cm - (e1 @ el.T) / tau, atol=1e-15)
+    if ell > 1:
+        assert not np.allclose(B, C - (e1 @ el.T) / tau)
+
+
+@pytest.mark.parametrize("P", _tiny_problems()[:4], ids=lambda p: p.name)
+def test_oracle_solves_kron_form(P):
+    """(B (x) I + I (x) K) u = G / tau with B = C + (1/tau) e_1 e_l^T, C = (I - C_1)/tau."""
+    K = R.k_dense(P)
+    ell, n = P.nt, P.nbar
+    C = (np.eye(ell) - R.c_alpha(ell, 1.0)) / P.tau
+    E = np.zeros((ell, ell))
+    E[0, ell - 1] = 1.0
+    B = C + E / P.tau
+    A = np.kron(B, np.eye(n)) + np.kron(np.eye(ell), K)
+    U = R.be_solve(P)
+    assert np.linalg.norm(A @ U.reshape(-1) - P.G.reshape(-1) / P.tau) <= 1e-12 * np.linalg.norm(P.G / P.tau)
+
+
+# ----------------------------------------------------------------------------
+# Fourier objects (Sec. 2, appendix)
+# ----------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("ell", [1, 2, 4, 6, 16, 64])
+def test_dft_matches_numpy_fft(ell):
+    rng = np.random.default_rng(ell)
+    X = rng.standard_normal((ell, 5)) + 1j * rng.standard_normal((ell, 5))
+    assert np.allclose(R.dft_time(X), np.fft.fft(X, axis=0), rtol=0, atol=1e-12 * ell)
+    assert np.allclose(R.idft_time(X), np.fft.ifft(X, axis=0), rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("ell", [2, 3, 8, 32])
+def test_circulant_eigs(ell):
+    """F C_1 F^{-1} = diag(pi), pi_i = omega^i, gamma = F^{-T} e_l = pi / l (appendix)."""
+    F = R.dft_matrix(ell)
+    pi, gamma = R.circulant_eigs(ell)
+    D = F @ R.c_alpha(ell, 1.0) @ np.linalg.inv(F)
+    assert np.allclose(D, np.diag(pi), atol=1e-12)
+    assert np.allclose(pi, np.exp(-2j * np.pi * np.arange(ell) / ell), atol=1e-13)
+    assert np.allclose(gamma, pi / ell, atol=1e-13)
+
+
+# ----------------------------------------------------------------------------
+# Table 1 and the Sec. 6.1 heat claims
+# ----------------------------------------------------------------------------
+
+
+def _read_table1():
+    rows = []
+    with open(os.path.join(GOLDEN, "table1.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                nbar, ell, val = line.split()
+                rows.append((int(nbar), int(ell), float(val)))
+    return rows
+
+
+@pytest.mark.parametrize("nbar,ell,val", _read_table1())
+def test_table1_bound(nbar, ell, val):
+    """eq. (14) evaluated with lambda_min(K) of the generator's 2D operator matches Table 1."""
+    n = int(round(np.sqrt(nbar)))
+    if n <= 512:
+        lo, diag, up = W.heat2d_axis_operator(n)
+        T = np.diag(diag) + np.diag(lo[1:], -1) + np.diag(up[:-1], 1)
+        lam_T = np.linalg.eigvalsh(T)[0]
+    else:  # the same eigenvalue in closed form (Sec. 6.1) for the largest grid
+        h = 1.0 / (n + 1)
+        lam_T = 4.0 / h ** 2 * np.sin(np.pi * h / 2) ** 2
+    lam = 2.0 * lam_T  # K = I (x) T + T (x) I
+    h = 1.0 / (n + 1)
+    assert abs(lam - 8.0 / h ** 2 * np.sin(np.pi / (2 * (n + 1))) ** 2) < 1e-9 * lam
+    assert abs(R.kappa_bound(1.0 / ell, lam) - val) <= 1.0e-3
+
+
+def _read_claims():
+    d = {}
+    with open(os.path.join(GOLDEN, "heat_claims.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()
+                d[k] = float(v)
+    return d
+
+
+@pytest.mark.parametrize("nbar,ell", [(r[0], r[1]) for r in _read_table1()])
+def test_heat_spectrum_of_J(nbar, ell):
+    """[lambda_min(J), lambda_max(J)] in [1, 1.004] (Sec. 6.1), and equal to the closed
+    form z^l / (z^l - 1), z = 1 + tau lambda (geometric sum over the l-th roots of unity)."""
+    c = _read_claims()
+    n = int(round(np.sqrt(nbar)))
+    h = 1.0 / (n + 1)
+    tau = 1.0 / ell
+    lam_min = 8.0 / h ** 2 * np.sin(np.pi * h / 2) ** 2
+    lam_max = 8.0 / h ** 2 * np.cos(np.pi * h / 2) ** 2
+    lo, hi = R.j_extreme_eigs(tau, ell, lam_min, lam_max)
+    for val, lam in ((lo, lam_max), (hi, lam_min)):
+        w = np.exp(-ell * np.log1p(tau * lam))  # z^{-l}, z = 1 + tau lambda
+        assert abs(val.imag) < 1e-12
+        assert abs(val.real - (1.0 + w / (1.0 - w))) < 1e-12
+    assert c["spec_lo"] <= lo.real <= hi.real <= c["spec_hi"]
+
+
+def test_mcdonald_example_one_iteration():
+    """Algorithm 1 on f = 0, u0 = x y (x-1)(1-y): one Algorithm-2 iteration reaches
+    relative residual < 1e-8 (Sec. 6.1), here on a 15 x 15 grid with l = 16, 32."""
+    c = _read_claims()
+    for ell in (16, 32):
+        P = W.heat2d_smooth(15, ell, 1.0, seed=0)
+        h = 1.0 / 16
+        x = h * np.arange(1, 16)
+        X, Y = np.meshgrid(x, x)  # (iy, ix)
+        G = np.zeros_like(P.G)
+        G[0] = (X * Y * (X - 1) * (1 - Y)).reshape(-1)
+        U, info = R.paradiag(P, G=G, eps=c["eps"], maxit=20)
+        k = info["krylov"]
+        assert k["m"] == int(c["iterations"])
+        assert k["resnorms"][0] < c["eps"] * k["beta"]
+        assert R.rel_err(U, R.be_solve(P, G=G)) < 1e-7
+
+
+# ----------------------------------------------------------------------------
+# Theorem 3.1 and the capacitance operator J_l (eq. 8)
+# ----------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("n,ell", [(8, 8), (8, 16), (5, 7)])
+def test_theorem31_hpd_and_bound(n, ell):
+    P = W.random_tridiag_problem(n, ell, seed=n + ell, symmetric=True)
+    K = R.k_dense(P)
+    J = R.j_dense(K, P.tau, ell)
+    assert np.allclose(J, J.conj().T, atol=1e-13)
+    ev = np.linalg.eigvalsh(J)
+    assert ev.min() > 0
+    lam = np.linalg.eigvalsh(K)
+    assert ev.max() / ev.min() <= R.kappa_bound(P.tau, lam.min()) + 1e-12
+    z = 1.0 + P.tau * lam
+    assert np.allclose(np.sort(ev), np.sort(z ** ell / (z ** ell - 1.0)), rtol=1e-12)
+
+
+# ----------------------------------------------------------------------------
+# Algorithm 2: eq. (13) against the explicit residual, x = u_l, b = periodic u_l
+# ----------------------------------------------------------------------------
+
+
+def _slow_problems():
+    return [W.heat2d_smooth(5, 8, 0.05, seed=3), W.advdiff1d_pulse(31, 16, 0.2, seed=1),
+            W.random_tridiag_problem(12, 8, 0.1, seed=9)]
+
+
+@pytest.mark.parametrize("P", _slow_problems(), ids=lambda p: p.name)
+def test_eq13_equals_explicit_residual(P):
+    """||r_m|| of eq. (13), with tau * t_{m+1,m}, equals ||J_l x_m - b|| at every m;
+    the literal tau-less form does not."""
+    op = R.operator(P)
+    K = R.k_dense(P)
+    J = R.j_dense(K, P.tau, P.nt)
+    pi, gamma = R.circulant_eigs(P.nt)
+    b = np.random.default_rng(0).standard_normal(P.nbar)
+    mismatch_without_tau = 0.0
+    for m in range(1, 6):
+        x, info = R.fom_like(op, P.tau, b, pi, gamma, eps=0.0, maxit=m)
+        if info["breakdown"]:
+            break
+        explicit = np.linalg.norm(J @ x - b)
+        assert abs(info["resnorms"][-1] - explicit) <= 1e-9 * np.linalg.norm(b) + 1e-6 * explicit
+        # Galerkin condition V_m^T r_m = 0
+        assert np.linalg.norm(info["V"][:m] @ (J @ x - b).real) <= 1e-10 * np.linalg.norm(b)
+        _, info2 = R.fom_like(op, P.tau, b, pi, gamma, eps=0.0, maxit=m, keep_tau=False)
+        x2 = info2["V"][:m].T @ info2["y"]
+        mismatch_without_tau = max(mismatch_without_tau,
+                                   abs(info2["resnorms"][-1] - np.linalg.norm(J @ x2 - b)) / np.linalg.norm(b))
+    assert mismatch_without_tau > 1e-6
+
+
+@pytest.mark.parametrize("P", _tiny_problems()[:5] + _slow_problems(), ids=lambda p: p.name)
+def test_b_is_periodic_final_state_and_x_is_u_ell(P):
+    """b = L F^{-T} e_l (eq. 7) is the last time slice of the circulant (periodic) solution,
+    and the exact solution x of eq. (8) is the true final state u_l."""
+    K = R.k_dense(P)
+    U_per = R.periodic_solve_dense(K, P.tau, P.G)
+    U, info = R.paradiag(P, eps=1e-14, maxit=60)
+    assert np.linalg.norm(info["b"] - U_per[-1].real) <= 1e-12 * max(1.0, np.linalg.norm(U_per[-1]))
+    assert info["b_imag"] <= 1e-12 * max(1.0, np.linalg.norm(info["b"]))
+    Ube = R.be_solve(P)
+    assert np.linalg.norm(info["x"] - Ube[-1]) <= 1e-11 * max(1.0, np.linalg.norm(Ube[-1]))
+
+
+@pytest.mark.parametrize("name,size", [("heat1d_sine_modes", (63, 32)), ("heat1d_forced", (127, 64)),
+                                       ("advdiff1d_pulse", (255, 64)), ("heat2d_smooth", (7, 16))])
+def test_algorithm1_equals_sequential(name, size):
+    P = getattr(W, name)(*size)
+    U, info = R.paradiag(P, eps=1e-13, maxit=60)
+    assert R.rel_err(U, R.be_solve(P)) < 1e-12
+    assert info["U_imag"] < 1e-12 * np.linalg.norm(U)
