@@ -1,0 +1,191 @@
+/*
+ * paradiag.h — C ABI of the GB300 (sm_103a) implementation of the new ParaDiag
+ * method of Gander & Palitta, "A new ParaDiag time-parallel time integration
+ * method" (arXiv 2304.12597).
+ *
+ * The library solves the all-at-once backward-Euler system (Sec. 1, eq. 2)
+ *
+ *     (I + tau K) U - U Sigma_1^T = G,     U = [u_1, ..., u_l],
+ *
+ * by Algorithm 1 (Sec. 2): Sigma_1 = C_1 - e_1 e_l^T (eq. 3), the circulant
+ * part is diagonalised by an FFT along time (eq. 5), the block-diagonal
+ * shifted systems ((1 - pi_i) I + tau K) are solved in parallel, and the
+ * rank-one Sherman-Morrison-Woodbury correction (eqs. 6-8) is resolved by the
+ * FOM-like Krylov method of Algorithm 2 (Sec. 3, eqs. 9-13).
+ *
+ * Conventions used by every entry point:
+ *  - n_bar = nx * ny spatial unknowns, l = nt time steps, tau = T / l.
+ *  - G and U are row-major (nt, n_bar) float64 arrays with the spatial index
+ *    contiguous; row j is time step j+1 (the paper's column-major U in R^{n_bar x l}).
+ *    Row 0 of G is u_0 + tau f_1, row j >= 1 is tau f_{j+1} (eq. 2).
+ *  - In 2D the spatial index is iy * nx + ix and K = I_ny (x) T_x + T_y (x) I_nx
+ *    (Sec. 6.1).
+ *  - "device" pointers are CUDA global-memory addresses on the current device
+ *    (e.g. torch tensor data pointers); "host" pointers are ordinary memory.
+ *  - No entry point throws; each returns a pd_status.  After PD_ERR_CUDA the
+ *    plan must be destroyed.  paradiag_last_error() returns a thread-local
+ *    message for the last failure on the calling thread.
+ *  - A plan is not thread safe: one solve at a time per plan.
+ */
+#ifndef PARADIAG_H
+#define PARADIAG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PD_ABI_VERSION 1
+
+typedef enum pd_status {
+  PD_OK = 0,
+  PD_ERR_INVALID_ARG = 1,   /* bad size, pointer, alignment or parameter */
+  PD_ERR_UNSUPPORTED = 2,   /* valid request outside what this build implements */
+  PD_ERR_OOM = 3,           /* workspace too small or device allocation failed */
+  PD_ERR_CUDA = 4,          /* a CUDA runtime call failed; destroy the plan */
+  PD_ERR_NOT_CONVERGED = 5, /* Krylov or refinement limit reached; U holds the last iterate */
+  PD_ERR_NONFINITE = 6,     /* NaN/Inf met in the input or an intermediate norm */
+  PD_ERR_TIMEOUT = 7        /* reserved for bounded device-side waits */
+} pd_status;
+
+typedef enum pd_precision {
+  PD_FP64 = 0,  /* every step in IEEE binary64 */
+  PD_MIXED = 1  /* FFTs and shifted solves in complex binary32; Krylov, capacitance
+                   system, all-at-once residual and the solution update in binary64;
+                   iterative refinement recovers FP64 accuracy */
+} pd_precision;
+
+/* Problem and solver description.  Host arrays are copied at plan time and may be
+ * freed afterwards.  Fill unused fields with 0 / NULL. */
+typedef struct pd_desc {
+  int32_t abi_version;   /* must be PD_ABI_VERSION */
+  int32_t dim;           /* 1 or 2 */
+  int64_t nx;            /* 1D: n_bar; 2D: grid points along x (contiguous) */
+  int64_t ny;            /* 1D: 1;     2D: grid points along y */
+  int64_t nt;            /* l, number of time steps: a power of two, 1 <= l <= 8192 */
+  double tau;            /* time step tau = T / l > 0 */
+  /* K (1D) or T_x (2D): tridiagonal, row i = lo[i] u[i-1] + diag[i] u[i] + up[i] u[i+1];
+   * lo[0] and up[n-1] are ignored.  Length nx, host memory. */
+  const double *k_lo, *k_diag, *k_up;
+  /* 2D only: T_y, length ny, host memory.  This build requires T_y to be symmetric
+   * Toeplitz (constant diagonal and constant off-diagonal) and ny + 1 to be a power
+   * of two <= 4096, so that T_y is diagonalised by the orthonormal DST-I. */
+  const double *k_lo_y, *k_diag_y, *k_up_y;
+  int32_t precision;     /* pd_precision */
+  int32_t maxit;         /* Algorithm 2 iteration limit, 1 <= maxit <= 32 (0 = 32) */
+  double eps_krylov;     /* Algorithm 2 tolerance epsilon (stop when ||r|| <= eps * ||b||);
+                            0 = 1e-13 for PD_FP64, 1e-6 for the inner solves of PD_MIXED */
+  int32_t q;             /* residual check period of Algorithm 2; only q = 1 is built */
+  int32_t max_refine;    /* PD_MIXED: refinement sweeps after the first solve (0 = 6) */
+  double refine_tol;     /* PD_MIXED: stop when ||delta||_F <= refine_tol * ||U||_F (0 = 1e-13) */
+  double alpha;          /* alpha of Sec. 4; only 1.0 (or 0 = 1.0) is built */
+  void *stream;          /* cudaStream_t every launch is ordered on (NULL = legacy stream) */
+  int32_t host_io;       /* nonzero: reserve device staging for paradiag_solve_host */
+  int32_t reserved;
+} pd_desc;
+
+/* Statistics of the last paradiag_solve / paradiag_solve_host. */
+typedef struct pd_stats {
+  int32_t krylov_iters;        /* m of the last Algorithm-2 run */
+  int32_t krylov_iters_total;  /* sum of m over all refinement sweeps */
+  int32_t pint_loops;          /* parallel-in-time loops in the paper's count, m/q + 2 per solve */
+  int32_t shifted_sweeps;      /* passes over all l/2+1 shifted systems actually executed */
+  int32_t refine_sweeps;       /* solves performed (1 for PD_FP64) */
+  int32_t breakdown;           /* 1 if Algorithm 2 met an invariant Krylov space */
+  int64_t kernel_launches;     /* this library's kernel launches during the solve */
+  double beta;                 /* ||b|| of the last Algorithm-2 run */
+  double krylov_rel_resnorm;   /* eq. (13) residual / ||b|| at exit of the last run */
+  double rel_update;           /* PD_MIXED: ||delta||_F / ||U||_F of the last sweep */
+  double ms_total;             /* wall time of the solve measured with CUDA events */
+} pd_stats;
+
+typedef struct pd_plan pd_plan;
+
+/* Device workspace a plan for *desc needs (bytes).  Pure host computation.
+ * Errors: PD_ERR_INVALID_ARG / PD_ERR_UNSUPPORTED for a bad or unbuilt desc. */
+pd_status paradiag_workspace_size(const pd_desc *desc, size_t *bytes);
+
+/* Build a plan: validate desc, copy the operator, compute pi_i = omega^{i},
+ * gamma_i = pi_i / l (Algorithm 1, first step; appendix), the FFT twiddles and the
+ * per-axis transforms, and upload them.  workspace: device memory of at least
+ * paradiag_workspace_size() bytes, 256-byte aligned, owned by the caller and kept
+ * alive until paradiag_destroy; NULL asks the plan to cudaMalloc its own.
+ * *out receives the plan.  Runs synchronously on desc->stream. */
+pd_status paradiag_plan(const pd_desc *desc, void *workspace, size_t workspace_bytes,
+                        pd_plan **out);
+
+/* Solve eq. (2) for one right-hand side: Algorithm 1 with Algorithm 2 (PD_FP64), or
+ * iterative refinement around it (PD_MIXED).  G_dev: device, (nt, n_bar) float64,
+ * read only.  U_dev: device, (nt, n_bar) float64, overwritten; must not alias G_dev.
+ * Both 8-byte aligned.  stats (host, may be NULL) is filled on return.  The call
+ * enqueues on the plan's stream and returns after its internal host synchronisations
+ * (Krylov and refinement decisions), so U_dev is complete on return.
+ * PD_ERR_NOT_CONVERGED: limits reached; U_dev holds the last iterate. */
+pd_status paradiag_solve(pd_plan *plan, const double *G_dev, double *U_dev, pd_stats *stats);
+
+/* Same as paradiag_solve with G and U in host memory (pinned memory gives the best
+ * copy rate).  The host-to-device copy of G and the device-to-host copy of U are
+ * part of the call.  Requires desc->host_io != 0 at plan time. */
+pd_status paradiag_solve_host(pd_plan *plan, const double *G_host, double *U_host,
+                              pd_stats *stats);
+
+/* Release the plan and, if the plan allocated it, its workspace.  NULL is a no-op. */
+pd_status paradiag_destroy(pd_plan *plan);
+
+/* Thread-local description of the last error on this thread ("" if none). */
+const char *paradiag_last_error(void);
+
+/* Library version string. */
+const char *paradiag_version(void);
+
+/* ---- Stage entry points (single steps of the path, for verification) ----------
+ * They run the same kernels paradiag_solve runs, on caller-provided device arrays.
+ * Spectra are (nt/2 + 1, n_bar) row-major complex arrays, interleaved (re, im), of
+ * the plan's compute type: complex128 for PD_FP64 plans, complex64 for PD_MIXED.
+ * In 2D they act in the basis where T_y is diagonal (after paradiag_dst_y). */
+
+/* Forward DFT along time, X (nt, n_bar) float64 -> Xhat (nt/2+1, n_bar):
+ * Xhat[k] = sum_j omega^{jk} X[j], omega = exp(-2 pi i / l); the rows of X F^T (eq. 5). */
+pd_status paradiag_time_dft(pd_plan *plan, const double *X_dev, void *Xhat_dev);
+
+/* Inverse DFT along time, Y (nt/2+1, n_bar) -> X (nt, n_bar) float64,
+ * X[j] = Re((1/l) sum_k omega^{-jk} Y[k]) with Y[l-k] = conj(Y[k]): the rows of Y F^{-T}. */
+pd_status paradiag_time_idft(pd_plan *plan, const void *Y_dev, double *X_dev);
+
+/* The first parallel-in-time loop of Algorithm 1: Y[k] = ((1 - pi_k) I + tau K)^{-1} R[k]
+ * for k = 0..nt/2 (Y_dev may be NULL to skip the store), and, if b_dev != NULL, the SMW
+ * right-hand side b = sum_{i=0}^{l-1} gamma_i Y_i (eq. 7) over the full spectrum,
+ * using Y_{l-k} = conj(Y_k); b is float64 of length n_bar. */
+pd_status paradiag_shifted_solve(pd_plan *plan, const void *R_dev, void *Y_dev, double *b_dev);
+
+/* 2D only: the orthonormal DST-I along y of a (nt, ny, nx) float64 array (its own
+ * inverse).  This is the transform that diagonalises T_y (Sec. 6.1 operator). */
+pd_status paradiag_dst_y(pd_plan *plan, const double *X_dev, double *Y_dev);
+
+/* After a solve: the SMW right-hand side b (eq. 7) and the Algorithm-2 solution x_m of
+ * eq. (8) from the last sweep, float64 length n_bar, device.  Either may be NULL. */
+pd_status paradiag_last_vectors(pd_plan *plan, double *b_dev, double *x_dev);
+
+/* ---- Kernel timing (tracing) ------------------------------------------------------ */
+
+typedef struct pd_kernel_time {
+  char name[32];       /* kernel family */
+  int64_t launches;    /* launches recorded since timing was enabled */
+  double total_ms;     /* summed CUDA-event durations on the plan's stream */
+  double bytes;        /* summed algorithmic bytes of those launches */
+} pd_kernel_time;
+
+/* Enable (1) or disable (0) per-launch CUDA-event timing on the plan's stream;
+ * enabling resets the counters. */
+pd_status paradiag_set_timing(pd_plan *plan, int enable);
+
+/* Copy up to max_entries kernel-family records into out; *n_out = families present. */
+pd_status paradiag_kernel_times(pd_plan *plan, pd_kernel_time *out, int max_entries, int *n_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PARADIAG_H */

@@ -1,0 +1,306 @@
+// Time-axis DFTs of the all-at-once block (eq. 5: U F^T and Y F^{-T}) and the
+// orthonormal DST-I along y that diagonalises T_y of the 2D operator (Sec. 6.1).
+//
+// Each CTA owns a tile of TX adjacent spatial columns and all n time points, so
+// every global load/store touches TX contiguous elements of an n_bar-contiguous
+// row.  Two real columns are packed into one complex series (z = a + i b), the
+// series are transformed in shared memory by an in-place radix-4 (with a final
+// radix-2) decimation-in-time Cooley-Tukey FFT from bit-reversed input, and the
+// two real spectra are separated on the way out:
+//   A[k] = (Z[k] + conj Z[-k]) / 2,   B[k] = (Z[k] - conj Z[-k]) / (2i).
+// Twiddles omega_n^k = exp(-2 pi i k / n), k < n/2, come from a table computed
+// on the host in FP64 (rounded to FP32 for the mixed path).
+#include <algorithm>
+
+#include "pd_internal.h"
+
+namespace pd {
+
+// In-place DIT FFT of `nseries` series of length n = 2^logn stored back to back
+// in shared memory, input in bit-reversed order, output in natural order.
+// All threads of the CTA take part; the caller synchronises before the call.
+template <typename T>
+__device__ void fft_smem(cpx<T> *buf, int n, int logn, int nseries, const cpx<T> *__restrict__ tw) {
+  int s = 0;
+  while (s + 1 < logn) {  // radix-4 pass = DIT stages with half-spans h and 2h
+    const int h = 1 << s;
+    const int lq = logn - 2;
+    const int total = nseries << lq;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+      const int ser = idx >> lq;
+      const int q = idx & ((1 << lq) - 1);
+      const int j = q & (h - 1);
+      const int base = ((q >> s) << (s + 2)) + j;
+      cpx<T> *p = buf + ((size_t)ser << logn);
+      const cpx<T> w1 = tw[j << (logn - s - 1)];
+      const cpx<T> w2 = tw[j << (logn - s - 2)];
+      cpx<T> x0 = p[base], x1 = p[base + h], x2 = p[base + 2 * h], x3 = p[base + 3 * h];
+      cpx<T> t1 = mul(w1, x1), t3 = mul(w1, x3);
+      cpx<T> a0 = add(x0, t1), a1 = sub(x0, t1), a2 = add(x2, t3), a3 = sub(x2, t3);
+      cpx<T> t2 = mul(w2, a2);
+      cpx<T> u = mul(w2, a3);
+      cpx<T> mu = mk<T>(u.y, -u.x);  // omega_{4h}^{j+h} a3 = -i * (omega_{4h}^j a3)
+      p[base] = add(a0, t2);
+      p[base + 2 * h] = sub(a0, t2);
+      p[base + h] = add(a1, mu);
+      p[base + 3 * h] = sub(a1, mu);
+    }
+    __syncthreads();
+    s += 2;
+  }
+  if (s < logn) {  // last radix-2 stage, half-span h = n/2
+    const int h = 1 << s;
+    const int lh = logn - 1;
+    const int total = nseries << lh;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+      const int ser = idx >> lh;
+      const int b = idx & ((1 << lh) - 1);
+      const int j = b & (h - 1);
+      const int i0 = ((b >> s) << (s + 1)) + j;
+      cpx<T> *p = buf + ((size_t)ser << logn);
+      const cpx<T> w = tw[j << (logn - s - 1)];
+      cpx<T> x0 = p[i0], x1 = p[i0 + h];
+      cpx<T> t = mul(w, x1);
+      p[i0] = add(x0, t);
+      p[i0 + h] = sub(x0, t);
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T, typename Tin>
+__global__ void __launch_bounds__(256) k_fft_r2c(const Tin *__restrict__ X, int64_t ldx, int64_t ncols,
+                                                 int n, int logn, int TX, const cpx<T> *__restrict__ tw,
+                                                 cpx<T> *__restrict__ S, int64_t lds) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cpx<T> *buf = reinterpret_cast<cpx<T> *>(smraw);
+  const int64_t x0 = (int64_t)blockIdx.x * TX;
+  const int total = n * TX;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int j = idx / TX;
+    const int c = idx - j * TX;
+    const int64_t col = x0 + c;
+    const T v = (col < ncols) ? (T)X[(int64_t)j * ldx + col] : T(0);
+    T *slot = reinterpret_cast<T *>(&buf[((size_t)(c >> 1) << logn) + bitrev(j, logn)]);
+    slot[c & 1] = v;
+  }
+  __syncthreads();
+  fft_smem<T>(buf, n, logn, TX >> 1, tw);
+  const int nf = (n >> 1) + 1;
+  const int tot2 = nf * TX;
+  for (int idx = threadIdx.x; idx < tot2; idx += blockDim.x) {
+    const int k = idx / TX;
+    const int c = idx - k * TX;
+    const int64_t col = x0 + c;
+    if (col >= ncols) continue;
+    const cpx<T> *z = buf + ((size_t)(c >> 1) << logn);
+    const cpx<T> zk = z[k], zm = z[(n - k) & (n - 1)];
+    cpx<T> r;
+    if ((c & 1) == 0) {
+      r = mk<T>(T(0.5) * (zk.x + zm.x), T(0.5) * (zk.y - zm.y));
+    } else {
+      r = mk<T>(T(0.5) * (zk.y + zm.y), T(-0.5) * (zk.x - zm.x));
+    }
+    S[(int64_t)k * lds + col] = r;
+  }
+}
+
+// Inverse: Z[k] = A[k] + i B[k] over the full spectrum (A[n-k] = conj A[k]);
+// z = IDFT(Z) = conj(DFT(conj Z)) / n; column 2p = Re z, column 2p+1 = Im z.
+template <typename T>
+__global__ void __launch_bounds__(256) k_fft_c2r(const cpx<T> *__restrict__ S, int64_t lds, int64_t ncols,
+                                                 int n, int logn, int TX, const cpx<T> *__restrict__ tw,
+                                                 void *__restrict__ out, int64_t ldo, int mode,
+                                                 double *__restrict__ norm_part) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cpx<T> *buf = reinterpret_cast<cpx<T> *>(smraw);
+  const int64_t x0 = (int64_t)blockIdx.x * TX;
+  const int np = TX >> 1;
+  const int total = n * np;
+  const int half = n >> 1;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int k = idx / np;
+    const int p = idx - k * np;
+    const int64_t ca = x0 + 2 * p, cb = ca + 1;
+    const int kk = (k <= half) ? k : n - k;
+    cpx<T> A = mk<T>(T(0), T(0)), B = mk<T>(T(0), T(0));
+    if (ca < ncols) A = S[(int64_t)kk * lds + ca];
+    if (cb < ncols) B = S[(int64_t)kk * lds + cb];
+    if (k > half) {
+      A.y = -A.y;
+      B.y = -B.y;
+    }
+    // conj(A + i B) = (A.x - B.y) - i (A.y + B.x)
+    buf[((size_t)p << logn) + bitrev(k, logn)] = mk<T>(A.x - B.y, -(A.y + B.x));
+  }
+  __syncthreads();
+  fft_smem<T>(buf, n, logn, np, tw);
+  const T inv_n = T(1) / T(n);
+  double ss = 0.0;
+  const int tot2 = n * TX;
+  for (int idx = threadIdx.x; idx < tot2; idx += blockDim.x) {
+    const int j = idx / TX;
+    const int c = idx - j * TX;
+    const int64_t col = x0 + c;
+    if (col >= ncols) continue;
+    const cpx<T> r = buf[((size_t)(c >> 1) << logn) + j];
+    const T v = ((c & 1) == 0) ? r.x * inv_n : -r.y * inv_n;
+    const int64_t o = (int64_t)j * ldo + col;
+    if (mode == 0) {
+      reinterpret_cast<double *>(out)[o] = (double)v;
+    } else if (mode == 1) {
+      reinterpret_cast<double *>(out)[o] += (double)v;
+    } else {
+      reinterpret_cast<float *>(out)[o] = (float)v;
+    }
+    const float vf = (float)v;
+    ss += (double)(vf * vf);
+  }
+  if (norm_part) {
+    ss = warp_sum(ss);
+    __shared__ double red[32];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = ss;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+      norm_part[blockIdx.x] = t;
+    }
+  }
+}
+
+// Orthonormal DST-I along y via a length N = 2(ny+1) complex FFT of the odd
+// extension, two x-columns packed per series (a + i b):
+//   DST_l(a) = -Im Z[l] / 2,  DST_l(b) = Re Z[l] / 2,  scaled by sqrt(2/(ny+1)).
+template <typename Tin, typename Tout, typename T>
+__global__ void __launch_bounds__(256) k_dst_y(const Tin *__restrict__ X, Tout *__restrict__ Y, int64_t ny,
+                                               int64_t nx, int N, int logN, int TX,
+                                               const cpx<T> *__restrict__ tw, T scale, int mode) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cpx<T> *buf = reinterpret_cast<cpx<T> *>(smraw);
+  const int ntile = (int)((nx + TX - 1) / TX);
+  const int64_t t = blockIdx.x / ntile;
+  const int64_t x0 = (int64_t)(blockIdx.x % ntile) * TX;
+  const Tin *Xt = X + t * ny * nx;
+  Tout *Yt = Y + t * ny * nx;
+  const int np = TX >> 1;
+  // zero the whole extension, then scatter the odd extension
+  for (int idx = threadIdx.x; idx < np * N; idx += blockDim.x) buf[idx] = mk<T>(T(0), T(0));
+  __syncthreads();
+  const int total = (int)ny * TX;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int y = idx / TX;
+    const int c = idx - y * TX;
+    const int64_t col = x0 + c;
+    const T v = (col < nx) ? (T)Xt[(int64_t)y * nx + col] : T(0);
+    cpx<T> *ser = buf + ((size_t)(c >> 1) << logN);
+    T *pos = reinterpret_cast<T *>(&ser[bitrev(y + 1, logN)]);
+    T *neg = reinterpret_cast<T *>(&ser[bitrev(N - (y + 1), logN)]);
+    pos[c & 1] = v;
+    neg[c & 1] = -v;
+  }
+  __syncthreads();
+  fft_smem<T>(buf, N, logN, np, tw);
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int l = idx / TX;  // output index l = 0..ny-1  <->  mode l+1
+    const int c = idx - l * TX;
+    const int64_t col = x0 + c;
+    if (col >= nx) continue;
+    const cpx<T> z = buf[((size_t)(c >> 1) << logN) + l + 1];
+    const T v = ((c & 1) == 0) ? (T(-0.5) * scale) * z.y : (T(0.5) * scale) * z.x;
+    const int64_t o = (int64_t)l * nx + col;
+    if (mode == 0) {
+      Yt[o] = (Tout)v;
+    } else {
+      Yt[o] += (Tout)v;
+    }
+  }
+}
+
+static int ilog2(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return l;
+}
+
+// Columns per CTA: as many as fit ~96 KB of series (two CTAs per SM), capped.
+template <typename T>
+static int pick_tx(int n, int cap) {
+  const size_t budget = 96 * 1024;
+  int tx = cap;
+  while (tx > 2 && (size_t)(tx / 2) * n * sizeof(cpx<T>) > budget) tx >>= 1;
+  return tx;
+}
+
+template <typename T, typename Tin>
+void launch_fft_r2c(Ctx &c, const Tin *X, int64_t ldx, int64_t ncols, int n, const cpx<T> *tw,
+                    cpx<T> *S, int64_t lds) {
+  const int logn = ilog2(n);
+  const int TX = pick_tx<T>(n, sizeof(T) == 8 ? 8 : 16);
+  const size_t smem = (size_t)(TX / 2) * n * sizeof(cpx<T>);
+  const int grid = (int)((ncols + TX - 1) / TX);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_fft_r2c<T, Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const double bytes = (double)n * ncols * sizeof(Tin) + (double)(n / 2 + 1) * ncols * sizeof(cpx<T>);
+  c.launch(sizeof(T) == 8 ? "fft_r2c_f64" : "fft_r2c_f32", bytes, [&] {
+    k_fft_r2c<T, Tin><<<grid, 256, smem, c.stream>>>(X, ldx, ncols, n, logn, TX, tw, S, lds);
+  });
+}
+
+template <typename T>
+void launch_fft_c2r(Ctx &c, const cpx<T> *S, int64_t lds, int64_t ncols, int n, const cpx<T> *tw,
+                    void *out, int64_t ldo, int mode, double *norm_part, int *nparts) {
+  const int logn = ilog2(n);
+  const int TX = pick_tx<T>(n, sizeof(T) == 8 ? 8 : 16);
+  const size_t smem = (size_t)(TX / 2) * n * sizeof(cpx<T>);
+  const int grid = (int)((ncols + TX - 1) / TX);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_fft_c2r<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (nparts) *nparts = grid;
+  const double obytes = (mode == 2) ? 4.0 : (mode == 1 ? 16.0 : 8.0);
+  const double bytes = (double)(n / 2 + 1) * ncols * sizeof(cpx<T>) + (double)n * ncols * obytes;
+  c.launch(sizeof(T) == 8 ? "fft_c2r_f64" : "fft_c2r_f32", bytes, [&] {
+    k_fft_c2r<T><<<grid, 256, smem, c.stream>>>(S, lds, ncols, n, logn, TX, tw, out, ldo, mode, norm_part);
+  });
+}
+
+template <typename Tin, typename Tout, typename T>
+void launch_dst_y(Ctx &c, const Tin *X, Tout *Y, int64_t nt, int64_t ny, int64_t nx, const cpx<T> *tw,
+                  int mode) {
+  const int N = (int)(2 * (ny + 1));
+  const int logN = ilog2(N);
+  const int TX = pick_tx<T>(N, sizeof(T) == 8 ? 8 : 16);
+  const size_t smem = (size_t)(TX / 2) * N * sizeof(cpx<T>);
+  const int ntile = (int)((nx + TX - 1) / TX);
+  const int64_t grid = nt * ntile;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_dst_y<Tin, Tout, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const T scale = (T)sqrt(2.0 / (double)(ny + 1));
+  const double bytes = (double)nt * ny * nx * (sizeof(Tin) + sizeof(Tout) * (mode ? 2 : 1));
+  c.launch(sizeof(T) == 8 ? "dst_y_f64" : "dst_y_f32", bytes, [&] {
+    k_dst_y<Tin, Tout, T><<<(unsigned)grid, 256, smem, c.stream>>>(X, Y, ny, nx, N, logN, TX, tw, scale, mode);
+  });
+}
+
+template void launch_fft_r2c<double, double>(Ctx &, const double *, int64_t, int64_t, int, const cpx<double> *,
+                                             cpx<double> *, int64_t);
+template void launch_fft_r2c<float, double>(Ctx &, const double *, int64_t, int64_t, int, const cpx<float> *,
+                                            cpx<float> *, int64_t);
+template void launch_fft_r2c<float, float>(Ctx &, const float *, int64_t, int64_t, int, const cpx<float> *,
+                                           cpx<float> *, int64_t);
+template void launch_fft_c2r<double>(Ctx &, const cpx<double> *, int64_t, int64_t, int, const cpx<double> *,
+                                     void *, int64_t, int, double *, int *);
+template void launch_fft_c2r<float>(Ctx &, const cpx<float> *, int64_t, int64_t, int, const cpx<float> *,
+                                    void *, int64_t, int, double *, int *);
+template void launch_dst_y<double, double, double>(Ctx &, const double *, double *, int64_t, int64_t, int64_t,
+                                                   const cpx<double> *, int);
+template void launch_dst_y<double, float, float>(Ctx &, const double *, float *, int64_t, int64_t, int64_t,
+                                                 const cpx<float> *, int);
+template void launch_dst_y<float, float, float>(Ctx &, const float *, float *, int64_t, int64_t, int64_t,
+                                                const cpx<float> *, int);
+template void launch_dst_y<float, double, float>(Ctx &, const float *, double *, int64_t, int64_t, int64_t,
+                                                 const cpx<float> *, int);
+
+}  // namespace pd

@@ -1,0 +1,461 @@
+// Algorithm 2 (FOM-like method for J_l x = b, eq. 8) on the device, in FP64:
+//  - Arnoldi in K (eqs. 9-10): w = K v_m, two classical Gram-Schmidt passes
+//    (CGS2) against V_m, t_{m+1,m} = ||w||, v_{m+1} = w / t_{m+1,m};
+//  - the projected m x m system of eq. (12): for every frequency k a warp forms
+//    S_k = ((1 - pi_k) I_m + tau T_m)^{-1} by Gauss-Jordan elimination with
+//    partial pivoting and accumulates w_k Re(gamma_k (S_k - tau t g_k e_m^T S_k));
+//    one CTA then solves for y_m and forms c_k = e_m^T S_k y_m;
+//  - the residual norm of eq. (13): ||r_m|| = |tau t_{m+1,m}| ||(I - V_m V_m^T) z||,
+//    z = sum_i gamma_i h_i c_i (z itself is accumulated by the shifted-solve pass);
+//  - x_m = V_m y_m;
+//  - the FP64 all-at-once residual G - [(I + tau K) U - U Sigma_1^T] used by the
+//    mixed-precision refinement.
+// Cross-CTA reductions write one partial per CTA; every consumer sums the
+// partials in the same fixed order, so results do not depend on scheduling.
+//
+// Scalar block `scal`: [0] beta = ||b||, [1] t_{m+1,m}, [2] ||r_m|| (eq. 13),
+// [3] ||K v_m|| (breakdown reference), [4] last sum-of-squares result.
+// Flag block `flags`: [0] breakdown (invariant Krylov space), [1] beta == 0,
+// [2] non-finite value met.
+#include <algorithm>
+#include <cmath>
+
+#include "pd_internal.h"
+
+namespace pd {
+
+constexpr int kBlas = 256;
+
+__device__ __forceinline__ double block_sum(double v, double *red) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    t = warp_sum(t);
+  }
+  return t;  // valid in warp 0
+}
+
+// part[cta * ld + 0] = sum of b^2 over the CTA's slice
+__global__ void k_sumsq_part(const double *__restrict__ b, int n, double *part, int ld) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) s += b[j] * b[j];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) part[blockIdx.x * ld] = s;
+}
+
+// beta = sqrt(sum part); V[0] = b / beta; resets flags.
+__global__ void k_init_v0(const double *__restrict__ b, int n, const double *part, int ld, int nparts, double *V,
+                          double *scal, int *flags) {
+  double s = 0.0;
+  for (int i = 0; i < nparts; ++i) s += part[i * ld];
+  const double beta = sqrt(s);
+  const bool zero = !(beta > 0.0);
+  const double ib = zero ? 0.0 : 1.0 / beta;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) V[j] = b[j] * ib;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    scal[0] = beta;
+    scal[1] = 0.0;
+    scal[2] = beta;
+    flags[0] = 0;
+    flags[1] = zero ? 1 : 0;
+    flags[2] = isfinite(beta) ? 0 : 1;
+  }
+}
+
+// w = K v_{m-1}; partial dots V[q] . w (q < m) and ||w||^2 at slot m.
+__global__ void k_matvec_dots(int n, int m, const double *__restrict__ klo, const double *__restrict__ kdiag,
+                              const double *__restrict__ kup, const double *__restrict__ V, double *__restrict__ w,
+                              double *part, int ld) {
+  __shared__ double red[32];
+  const double *v = V + (int64_t)(m - 1) * n;
+  double acc[33];
+  for (int q = 0; q <= m; ++q) acc[q] = 0.0;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    double x = kdiag[j] * v[j];
+    if (j > 0) x += klo[j] * v[j - 1];
+    if (j + 1 < n) x += kup[j] * v[j + 1];
+    w[j] = x;
+    for (int q = 0; q < m; ++q) acc[q] += V[(int64_t)q * n + j] * x;
+    acc[m] += x * x;
+  }
+  for (int q = 0; q <= m; ++q) {
+    const double s = block_sum(acc[q], red);
+    if (threadIdx.x == 0) part[blockIdx.x * ld + q] = s;
+  }
+}
+
+// Partial dots V[q] . x (q < m) and ||x||^2 at slot m.
+__global__ void k_dots(int n, int m, const double *__restrict__ V, const double *__restrict__ x, double *part,
+                       int ld) {
+  __shared__ double red[32];
+  double acc[33];
+  for (int q = 0; q <= m; ++q) acc[q] = 0.0;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const double xj = x[j];
+    for (int q = 0; q < m; ++q) acc[q] += V[(int64_t)q * n + j] * xj;
+    acc[m] += xj * xj;
+  }
+  for (int q = 0; q <= m; ++q) {
+    const double s = block_sum(acc[q], red);
+    if (threadIdx.x == 0) part[blockIdx.x * ld + q] = s;
+  }
+}
+
+// c_q = sum_cta pin[cta][q]; x -= sum_q c_q V[q]; partial dots of the new x into pout.
+// If Tcol != null, CTA 0 adds c_q to Tcol[q * ldT] (column m-1 of T_m); if save_norm,
+// CTA 0 stores sqrt(sum_cta pin[cta][m]) (||x|| before the update) into *norm_out.
+__global__ void k_axpy_dots(int n, int m, const double *__restrict__ V, double *__restrict__ x, const double *pin,
+                            double *pout, int ld, int nparts, double *Tcol, int ldT, int accumulate_T,
+                            double *norm_out) {
+  __shared__ double c[33];
+  __shared__ double red[32];
+  if (threadIdx.x <= m) {
+    double s = 0.0;
+    for (int i = 0; i < nparts; ++i) s += pin[i * ld + threadIdx.x];
+    c[threadIdx.x] = s;
+  }
+  __syncthreads();
+  if (blockIdx.x == 0 && threadIdx.x < m && Tcol) {
+    if (accumulate_T)
+      Tcol[threadIdx.x * ldT] += c[threadIdx.x];
+    else
+      Tcol[threadIdx.x * ldT] = c[threadIdx.x];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && norm_out) *norm_out = sqrt(c[m]);
+  double acc[33];
+  for (int q = 0; q <= m; ++q) acc[q] = 0.0;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    double xj = x[j];
+    for (int q = 0; q < m; ++q) xj -= c[q] * V[(int64_t)q * n + j];
+    x[j] = xj;
+    for (int q = 0; q < m; ++q) acc[q] += V[(int64_t)q * n + j] * xj;
+    acc[m] += xj * xj;
+  }
+  for (int q = 0; q <= m; ++q) {
+    const double s = block_sum(acc[q], red);
+    if (threadIdx.x == 0) pout[blockIdx.x * ld + q] = s;
+  }
+}
+
+// t = ||w||; breakdown when t <= 1e-14 ||K v_{m-1}||; v_m = w / t.
+__global__ void k_arnoldi_finish(int n, int m, const double *pin, int ld, int nparts, const double *__restrict__ w,
+                                 double *V, double *T, int ldT, double *scal, int *flags) {
+  double s = 0.0;
+  for (int i = 0; i < nparts; ++i) s += pin[i * ld + m];
+  const double t = sqrt(s);
+  const bool bd = !(t > 1e-14 * scal[3]);
+  const double it = bd ? 0.0 : 1.0 / t;
+  double *vm = V + (int64_t)m * n;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) vm[j] = w[j] * it;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    T[(int64_t)m * ldT + (m - 1)] = bd ? 0.0 : t;
+    scal[1] = bd ? 0.0 : t;
+    flags[0] = bd ? 1 : 0;
+    if (!isfinite(t)) flags[2] = 1;
+  }
+}
+
+// ||r_m|| = |tau t| sqrt(sum part[m]) (zero after a breakdown).
+__global__ void k_resnorm_finish(const double *pin, int ld, int nparts, int m, double tau, double *scal,
+                                 const int *flags) {
+  double s = 0.0;
+  for (int i = 0; i < nparts; ++i) s += pin[i * ld + m];
+  scal[2] = flags[0] ? 0.0 : fabs(tau * scal[1]) * sqrt(s);
+}
+
+// ---- eq. (12): capacitance-system terms, one warp per frequency -----------------
+
+// Gauss-Jordan inversion of the m x m complex matrix H (row-major, ld m) into X
+// (initialised here), partial pivoting on rows; lane c owns column c; m <= 32.
+__device__ void warp_gj_inverse(cpx<double> *H, cpx<double> *X, cpx<double> *fcol, int m) {
+  const int lane = threadIdx.x & 31;
+  for (int q = 0; q < m; ++q)
+    if (lane < m) X[q * m + lane] = mk<double>(q == lane ? 1.0 : 0.0, 0.0);
+  __syncwarp();
+  for (int p = 0; p < m; ++p) {
+    double v = (lane >= p && lane < m) ? abs2(H[lane * m + p]) : -1.0;
+    int idx = lane;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+      if (ov > v || (ov == v && oi < idx)) {
+        v = ov;
+        idx = oi;
+      }
+    }
+    if (idx != p && lane < m) {
+      cpx<double> h = H[p * m + lane];
+      H[p * m + lane] = H[idx * m + lane];
+      H[idx * m + lane] = h;
+      cpx<double> x = X[p * m + lane];
+      X[p * m + lane] = X[idx * m + lane];
+      X[idx * m + lane] = x;
+    }
+    __syncwarp();
+    const cpx<double> inv = recip(H[p * m + p]);
+    __syncwarp();
+    if (lane < m) {
+      H[p * m + lane] = mul(H[p * m + lane], inv);
+      X[p * m + lane] = mul(X[p * m + lane], inv);
+    }
+    __syncwarp();
+    if (lane < m) fcol[lane] = H[lane * m + p];
+    __syncwarp();
+    if (lane < m) {
+      const cpx<double> hp = H[p * m + lane], xp = X[p * m + lane];
+      for (int i = 0; i < m; ++i) {
+        if (i == p) continue;
+        const cpx<double> f = fcol[i];
+        H[i * m + lane] = fnms(H[i * m + lane], f, hp);
+        X[i * m + lane] = fnms(X[i * m + lane], f, xp);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+constexpr int kK5Warps = 4;
+
+__host__ __device__ inline size_t k5a_warp_bytes(int m) {
+  return (size_t)(2 * m * m + 2 * m) * sizeof(cpx<double>) + (size_t)m * m * sizeof(double);
+}
+
+__global__ void __launch_bounds__(kK5Warps * 32) k_capacitance_terms(
+    int nf, int m, int maxit, double tau, const double *__restrict__ T, const double2 *__restrict__ shift,
+    const double2 *__restrict__ wg, const double2 *__restrict__ gpart, int nblk, double *msys_part,
+    double2 *srow, const double *scal, const int *flags) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const size_t wb = k5a_warp_bytes(m);
+  unsigned char *base = smraw + wid * wb;
+  cpx<double> *H = reinterpret_cast<cpx<double> *>(base);
+  cpx<double> *X = H + m * m;
+  cpx<double> *fcol = X + m * m;
+  cpx<double> *gq = fcol + m;
+  double *msw = reinterpret_cast<double *>(gq + m);
+  const double tt = flags[0] ? 0.0 : tau * scal[1];
+  for (int i = lane; i < m * m; i += 32) msw[i] = 0.0;
+  __syncwarp();
+  const int gw = blockIdx.x * kK5Warps + wid, nw = gridDim.x * kK5Warps;
+  for (int k = gw; k < nf; k += nw) {
+    const double2 sk = shift[k];
+    if (lane < m) {
+      for (int q = 0; q < m; ++q) {
+        const double tq = (q <= lane + 1) ? T[(int64_t)q * maxit + lane] : 0.0;
+        H[q * m + lane] = mk<double>(tau * tq + (q == lane ? sk.x : 0.0), q == lane ? sk.y : 0.0);
+      }
+      double gx = 0.0, gy = 0.0;
+      // after a breakdown the dot pass was skipped and the t-term vanishes
+      for (int b = 0; b < (flags[0] ? 0 : nblk); ++b) {
+        const double2 v = gpart[((int64_t)k * nblk + b) * m + lane];
+        gx += v.x;
+        gy += v.y;
+      }
+      gq[lane] = mk<double>(gx, gy);
+    }
+    __syncwarp();
+    warp_gj_inverse(H, X, fcol, m);
+    const double2 w = wg[k];
+    const cpx<double> wk = mk<double>(w.x, w.y);
+    if (lane < m) {
+      const cpx<double> sl = X[(m - 1) * m + lane];  // e_m^T S_k, column `lane`
+      srow[(int64_t)k * m + lane] = make_double2(sl.x, sl.y);
+      for (int q = 0; q < m; ++q) {
+        const cpx<double> gs = mul(gq[q], sl);
+        const cpx<double> val = mk<double>(X[q * m + lane].x - tt * gs.x, X[q * m + lane].y - tt * gs.y);
+        const cpx<double> c = mul(wk, val);
+        msw[q * m + lane] += c.x;
+      }
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  // CTA partial = sum over its warps (fixed order)
+  for (int i = threadIdx.x; i < m * m; i += blockDim.x) {
+    double s = 0.0;
+    for (int wv = 0; wv < kK5Warps; ++wv) s += reinterpret_cast<double *>(smraw + wv * wb + (size_t)(2 * m * m + 2 * m) * sizeof(cpx<double>))[i];
+    msys_part[(int64_t)blockIdx.x * m * m + i] = s;
+  }
+}
+
+// One CTA: M = I + sum partials; y = beta M^{-1} e_1; omega_k = w_k gamma_k (e_m^T S_k y).
+__global__ void k_capacitance_solve(int nf, int m, int nparts, const double *msys_part, const double2 *__restrict__ wg,
+                                    const double2 *__restrict__ srow, double2 *omega, double *y, const double *scal) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cpx<double> *H = reinterpret_cast<cpx<double> *>(smraw);
+  cpx<double> *X = H + m * m;
+  cpx<double> *fcol = X + m * m;
+  double *ys = reinterpret_cast<double *>(fcol + m);
+  for (int i = threadIdx.x; i < m * m; i += blockDim.x) {
+    double s = ((i / m) == (i % m)) ? 1.0 : 0.0;
+    for (int p = 0; p < nparts; ++p) s += msys_part[(int64_t)p * m * m + i];
+    H[i] = mk<double>(s, 0.0);
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) warp_gj_inverse(H, X, fcol, m);
+  __syncthreads();
+  const double beta = scal[0];
+  if (threadIdx.x < m) {
+    ys[threadIdx.x] = beta * X[threadIdx.x * m + 0].x;
+    y[threadIdx.x] = ys[threadIdx.x];
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < nf; k += blockDim.x) {
+    double cx = 0.0, cy = 0.0;
+    for (int q = 0; q < m; ++q) {
+      const double2 s = srow[(int64_t)k * m + q];
+      cx += s.x * ys[q];
+      cy += s.y * ys[q];
+    }
+    const double2 w = wg[k];
+    omega[k] = make_double2(w.x * cx - w.y * cy, w.x * cy + w.y * cx);
+  }
+}
+
+// x = sum_q y_q V[q]
+__global__ void k_xm(int n, int m, const double *__restrict__ V, const double *__restrict__ y, double *x) {
+  __shared__ double ys[33];
+  if (threadIdx.x < m) ys[threadIdx.x] = y[threadIdx.x];
+  __syncthreads();
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int q = 0; q < m; ++q) s += ys[q] * V[(int64_t)q * n + j];
+    x[j] = s;
+  }
+}
+
+__global__ void k_sumsq_final(const double *part, int nparts, double *dst) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < nparts; ++i) s += part[i];
+    *dst = s;
+  }
+}
+
+// ---- FP64 all-at-once residual ---------------------------------------------------
+__global__ void k_residual(const double *__restrict__ G, const double *__restrict__ U, float *__restrict__ R,
+                           int64_t nt, int64_t ny, int64_t nx, double tau, const double *__restrict__ xlo,
+                           const double *__restrict__ xdiag, const double *__restrict__ xup,
+                           const double *__restrict__ ylo, const double *__restrict__ ydiag,
+                           const double *__restrict__ yup, double *norm_part) {
+  __shared__ double red[32];
+  const int64_t nb = ny * nx;
+  const int64_t total = nt * nb;
+  float ss = 0.f;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = idx / nb;
+    const int64_t j = idx - t * nb;
+    const int64_t iy = j / nx;
+    const int64_t ix = j - iy * nx;
+    const double *u = U + t * nb;
+    const double uj = u[j];
+    double ku = xdiag[ix] * uj;
+    if (ix > 0) ku += xlo[ix] * u[j - 1];
+    if (ix + 1 < nx) ku += xup[ix] * u[j + 1];
+    if (ylo) {
+      ku += ydiag[iy] * uj;
+      if (iy > 0) ku += ylo[iy] * u[j - nx];
+      if (iy + 1 < ny) ku += yup[iy] * u[j + nx];
+    }
+    double r = G[idx] - uj - tau * ku;
+    if (t > 0) r += U[idx - nb];
+    const float rf = (float)r;
+    R[idx] = rf;
+    ss += rf * rf;
+  }
+  double s = block_sum((double)ss, red);
+  if (threadIdx.x == 0 && norm_part) norm_part[blockIdx.x] = s;
+}
+
+// ---- launchers -------------------------------------------------------------------
+
+void launch_vec_norm_init(Ctx &c, KrylovBufs &k, const double *b) {
+  const int ld = k.maxit + 2;
+  c.launch("krylov_blas1", (double)k.n * 8, [&] { k_sumsq_part<<<k.grid, kBlas, 0, c.stream>>>(b, k.n, k.part, ld); });
+  c.launch("krylov_blas1", (double)k.n * 16, [&] {
+    k_init_v0<<<k.grid, kBlas, 0, c.stream>>>(b, k.n, k.part, ld, k.grid, k.V, k.scal, k.flags);
+  });
+}
+
+// Partial buffers: k.part holds three (grid, maxit+2) panels.
+void launch_arnoldi(Ctx &c, KrylovBufs &k, int m) {
+  const int ld = k.maxit + 2;
+  double *pa = k.part, *pb = k.part + (size_t)k.grid * ld, *pc = k.part + (size_t)2 * k.grid * ld;
+  const double bytes = (double)k.n * 8.0 * (m + 2);
+  c.launch("krylov_blas1", bytes, [&] {
+    k_matvec_dots<<<k.grid, kBlas, 0, c.stream>>>(k.n, m, k.klo, k.kdiag, k.kup, k.V, k.w, pa, ld);
+  });
+  double *Tcol = k.T + (m - 1);
+  c.launch("krylov_blas1", bytes, [&] {
+    k_axpy_dots<<<k.grid, kBlas, 0, c.stream>>>(k.n, m, k.V, k.w, pa, pb, ld, k.grid, Tcol, k.maxit, 0, k.scal + 3);
+  });
+  c.launch("krylov_blas1", bytes, [&] {
+    k_axpy_dots<<<k.grid, kBlas, 0, c.stream>>>(k.n, m, k.V, k.w, pb, pc, ld, k.grid, Tcol, k.maxit, 1, nullptr);
+  });
+  c.launch("krylov_blas1", (double)k.n * 16, [&] {
+    k_arnoldi_finish<<<k.grid, kBlas, 0, c.stream>>>(k.n, m, pc, ld, k.grid, k.w, k.V, k.T, k.maxit, k.scal, k.flags);
+  });
+}
+
+void launch_capacitance(Ctx &c, KrylovBufs &k, int m, int nf, double tau, const double2 *shift, const double2 *wg,
+                        const double2 *gpart, int nblk, double *msys_part, int k5_grid, double2 *srow,
+                        double2 *omega, double *y) {
+  const size_t smem = k5a_warp_bytes(m) * kK5Warps;
+  cudaFuncSetAttribute(k_capacitance_terms, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  c.launch("capacitance", (double)nf * nblk * m * 16, [&] {
+    k_capacitance_terms<<<k5_grid, kK5Warps * 32, smem, c.stream>>>(nf, m, k.maxit, tau, k.T, shift, wg, gpart, nblk,
+                                                                     msys_part, srow, k.scal, k.flags);
+  });
+  const size_t smem2 = (size_t)(2 * m * m + m) * sizeof(cpx<double>) + (size_t)m * sizeof(double);
+  c.launch("capacitance", (double)nf * m * 16, [&] {
+    k_capacitance_solve<<<1, 256, smem2, c.stream>>>(nf, m, k5_grid, msys_part, wg, srow, omega, y, k.scal);
+  });
+}
+
+// ||(I - V_m V_m^T) z|| with two CGS passes (z is overwritten by the projection).
+void launch_project_resnorm(Ctx &c, KrylovBufs &k, int m, const double *z, double tau) {
+  const int ld = k.maxit + 2;
+  double *pa = k.part, *pb = k.part + (size_t)k.grid * ld, *pc = k.part + (size_t)2 * k.grid * ld;
+  double *zz = const_cast<double *>(z);
+  const double bytes = (double)k.n * 8.0 * (m + 1);
+  c.launch("krylov_blas1", bytes, [&] { k_dots<<<k.grid, kBlas, 0, c.stream>>>(k.n, m, k.V, zz, pa, ld); });
+  c.launch("krylov_blas1", bytes, [&] {
+    k_axpy_dots<<<k.grid, kBlas, 0, c.stream>>>(k.n, m, k.V, zz, pa, pb, ld, k.grid, nullptr, 0, 0, nullptr);
+  });
+  c.launch("krylov_blas1", bytes, [&] {
+    k_axpy_dots<<<k.grid, kBlas, 0, c.stream>>>(k.n, m, k.V, zz, pb, pc, ld, k.grid, nullptr, 0, 0, nullptr);
+  });
+  c.launch("krylov_blas1", 0.0, [&] {
+    k_resnorm_finish<<<1, 32, 0, c.stream>>>(pc, ld, k.grid, m, tau, k.scal, k.flags);
+  });
+}
+
+void launch_xm(Ctx &c, KrylovBufs &k, int m, const double *y, double *x) {
+  c.launch("krylov_blas1", (double)k.n * 8.0 * (m + 1),
+           [&] { k_xm<<<k.grid, kBlas, 0, c.stream>>>(k.n, m, k.V, y, x); });
+}
+
+void launch_sumsq(Ctx &c, const double *part, int nparts, double *dst) {
+  c.launch("krylov_blas1", 0.0, [&] { k_sumsq_final<<<1, 32, 0, c.stream>>>(part, nparts, dst); });
+}
+
+void launch_residual(Ctx &c, const double *G, const double *U, float *R, int64_t nt, int64_t ny, int64_t nx,
+                     double tau, const double *xlo, const double *xdiag, const double *xup, const double *ylo,
+                     const double *ydiag, const double *yup, double *norm_part, int *nparts) {
+  const int64_t total = nt * ny * nx;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 8 * (int64_t)sm_count()));
+  if (nparts) *nparts = grid;
+  c.launch("residual_f64", (double)total * (8 + 8 + 4), [&] {
+    k_residual<<<grid, 256, 0, c.stream>>>(G, U, R, nt, ny, nx, tau, xlo, xdiag, xup, ylo, ydiag, yup, norm_part);
+  });
+}
+
+}  // namespace pd

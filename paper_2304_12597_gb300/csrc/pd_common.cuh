@@ -1,0 +1,80 @@
+// Shared device helpers for the ParaDiag kernels (complex arithmetic, team
+// barriers, warp reductions).  Internal header; not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pd {
+
+// Interleaved complex number of real type T (layout-compatible with float2 /
+// double2 and with numpy complex64 / complex128).
+template <typename T>
+struct alignas(2 * sizeof(T)) cpx {
+  T x, y;
+};
+
+template <typename T>
+__host__ __device__ __forceinline__ cpx<T> mk(T a, T b) {
+  cpx<T> r;
+  r.x = a;
+  r.y = b;
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ cpx<T> add(cpx<T> a, cpx<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
+template <typename T>
+__device__ __forceinline__ cpx<T> sub(cpx<T> a, cpx<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
+template <typename T>
+__device__ __forceinline__ cpx<T> mul(cpx<T> a, cpx<T> b) {
+  return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename T>
+__device__ __forceinline__ cpx<T> scal(T s, cpx<T> a) { return mk<T>(s * a.x, s * a.y); }
+template <typename T>
+__device__ __forceinline__ cpx<T> conjg(cpx<T> a) { return mk<T>(a.x, -a.y); }
+// a - b * c
+template <typename T>
+__device__ __forceinline__ cpx<T> fnms(cpx<T> a, cpx<T> b, cpx<T> c) {
+  return mk<T>(a.x - b.x * c.x + b.y * c.y, a.y - b.x * c.y - b.y * c.x);
+}
+// a - s * c with real s
+template <typename T>
+__device__ __forceinline__ cpx<T> fnms_r(cpx<T> a, T s, cpx<T> c) { return mk<T>(a.x - s * c.x, a.y - s * c.y); }
+// 1 / a  =  conj(a) / |a|^2.  The operands met here are bounded away from zero and
+// from overflow (|a| between ~1e-3 and ~1e8), so no Smith-style scaling is needed.
+template <typename T>
+__device__ __forceinline__ cpx<T> recip(cpx<T> a) {
+  T d = T(1) / (a.x * a.x + a.y * a.y);
+  return mk<T>(a.x * d, -a.y * d);
+}
+template <typename T>
+__device__ __forceinline__ T abs2(cpx<T> a) { return a.x * a.x + a.y * a.y; }
+
+template <typename T>
+__device__ __forceinline__ T shfl_xor(T v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Barrier over a team of P threads (P a multiple of 32) inside a CTA that holds
+// blockDim.x / P teams.  Team 0..(teams-1) use named barriers 1..teams.
+__device__ __forceinline__ void team_sync(int P, int team_in_cta) {
+  if (P == 32) {
+    __syncwarp();
+  } else if (P == (int)blockDim.x) {
+    __syncthreads();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + team_in_cta), "r"(P) : "memory");
+  }
+}
+
+__device__ __forceinline__ int bitrev(int j, int logn) {
+  return logn == 0 ? 0 : (int)(__brev((unsigned)j) >> (32 - logn));
+}
+
+}  // namespace pd

@@ -1,0 +1,324 @@
+// Parallel-in-time loop of Algorithms 1 and 2: for every frequency k of the half
+// spectrum, solve the shifted system ((1 - pi_k) I + tau K) y_k = r_k (Sec. 2,
+// the block-diagonal P), with K tridiagonal (in 2D: block-decoupled tridiagonal
+// after the DST along y).  The ~l/2 systems are independent; pi_{l-k} =
+// conj(pi_k) makes the other half the complex conjugate.
+//
+// One team of P threads solves one tridiagonal block of `blen` rows:
+//  1. the right-hand side is staged in shared memory with coalesced loads;
+//  2. each thread eliminates its chunk of M rows so that every interior row
+//     depends only on the chunk's first and last unknowns (partitioned Thomas);
+//  3. the 2P first/last rows form a tridiagonal interface system, solved by
+//     parallel cyclic reduction (PCR) in shared memory;
+//  4. each thread back-substitutes its interior rows.
+// Elimination is without pivoting: (1 - pi_k) has nonnegative real part and
+// tau K is positive real for the operators in scope, so every pivot stays away
+// from zero (the same argument as for Thomas on these matrices).
+//
+// Fused epilogues (per frequency k, in FP64):
+//  - acc += Re(omega_k y_k): b = sum_i gamma_i L_i (eq. 7) with omega_k = w_k gamma_k,
+//    and z = sum_i gamma_i h_i (e_m^T S_i y_m) (eq. 13) with omega_k = w_k gamma_k c_k,
+//    w_k = 1 for k = 0, l/2 and 2 otherwise (the conjugate half);
+//  - dots g_k = V_m^T h_k needed by eq. (12);
+//  - optional store of y_k (the final loop of Algorithm 1).
+// A team handles one block and a contiguous range of k, so its accumulators stay
+// on chip; the per-team partial rows are reduced in a fixed order afterwards.
+#include <algorithm>
+
+#include "pd_internal.h"
+
+namespace pd {
+
+template <typename T, int M>
+struct TeamSmem {
+  static size_t bytes(int P, int mdots) {
+    size_t b = 0;
+    b += (size_t)P * (M + 1) * sizeof(cpx<T>);   // rhs / dd, padded one slot per chunk
+    b += (size_t)2 * P * 5 * sizeof(cpx<T>);     // PCR rows a, b, c, d and 1/b
+    b += (size_t)P * M * sizeof(double);          // accumulators
+    b += (size_t)(P / 32) * std::max(mdots, 1) * sizeof(double2);  // dot reductions
+    return (b + 15) & ~(size_t)15;
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ void coef(const PintArgs<T> &a, int64_t j, bool valid, cpx<T> s, T &lo, cpx<T> &d, T &up) {
+  if (valid) {
+    lo = a.tlo[j];
+    up = a.tup[j];
+    d = mk<T>(s.x + a.tdiag[j], s.y);
+  } else {
+    lo = T(0);
+    up = T(0);
+    d = mk<T>(T(1), T(0));
+  }
+}
+
+template <typename T, int M>
+__global__ void __launch_bounds__(512) k_pint(PintGeom g, PintArgs<T> a, size_t team_bytes) {
+  if (a.skip_flag && *a.skip_flag) return;
+  const int P = g.P;
+  const int tic = threadIdx.x / P;
+  const int t = threadIdx.x - tic * P;
+  const int team = blockIdx.x * g.teams_per_cta + tic;
+  if (team >= g.nblk * g.R) return;  // whole teams only
+  const int blk = team / g.R;
+  const int rr = team - blk * g.R;
+  const int k0 = (int)((int64_t)rr * g.nf / g.R);
+  const int k1 = (int)((int64_t)(rr + 1) * g.nf / g.R);
+  const int blen = g.blen;
+  const int64_t off = (int64_t)blk * blen;
+  const int N = 2 * P;
+
+  extern __shared__ __align__(16) unsigned char smraw[];
+  unsigned char *base = smraw + (size_t)tic * team_bytes;
+  cpx<T> *dd = reinterpret_cast<cpx<T> *>(base);
+  cpx<T> *pa = dd + (size_t)P * (M + 1);
+  cpx<T> *pb = pa + N;
+  cpx<T> *pc = pb + N;
+  cpx<T> *pd = pc + N;
+  cpx<T> *pib = pd + N;
+  double *acc = reinterpret_cast<double *>(pib + N);
+  double2 *red = reinterpret_cast<double2 *>(acc + (size_t)P * M);
+
+  const bool do_acc = a.omega != nullptr;
+  if (do_acc) {
+#pragma unroll
+    for (int i = 0; i < M; ++i) acc[i * P + t] = 0.0;
+  }
+  cpx<T> *my = dd + (size_t)t * (M + 1);
+  const int e0 = t * M;
+
+  for (int k = k0; k < k1; ++k) {
+    const double2 sk = a.shift[k];
+    const cpx<T> s = mk<T>((T)sk.x, (T)sk.y);
+    // 1. stage the right-hand side (element e at dd[e + e/M])
+    for (int e = t; e < P * M; e += P) {
+      cpx<T> v = mk<T>(T(0), T(0));
+      if (e < blen) {
+        const int64_t j = off + e;
+        if (a.R) {
+          v = a.R[(int64_t)k * a.ldr + j];
+          if (a.rvec) v.x -= (T)a.rvec[j];
+        } else {
+          v.x = (T)a.rvec[j];
+        }
+      }
+      dd[e + e / M] = v;
+    }
+    team_sync(P, tic);
+
+    // 2. chunk elimination: row i of the chunk becomes x_i + aa_i x_0 + cc_i x_{M-1} = dd_i
+    cpx<T> aa[M], cc[M];
+    T lo0, up0;
+    cpx<T> d0;
+    coef(a, off + e0, e0 < blen, s, lo0, d0, up0);
+    const cpx<T> r0 = my[0];
+    {
+      T lo, up;
+      cpx<T> d;
+      coef(a, off + e0 + 1, e0 + 1 < blen, s, lo, d, up);
+      const cpx<T> rb = recip(d);
+      aa[1] = scal(lo, rb);
+      cc[1] = scal(up, rb);
+      my[1] = mul(my[1], rb);
+    }
+#pragma unroll
+    for (int i = 2; i < M; ++i) {
+      T lo, up;
+      cpx<T> d;
+      coef(a, off + e0 + i, e0 + i < blen, s, lo, d, up);
+      const cpx<T> rd = recip(fnms_r(d, lo, cc[i - 1]));
+      aa[i] = scal(-lo, mul(aa[i - 1], rd));
+      cc[i] = scal(up, rd);
+      my[i] = mul(fnms_r(my[i], lo, my[i - 1]), rd);
+    }
+#pragma unroll
+    for (int i = M - 3; i >= 1; --i) {
+      aa[i] = fnms(aa[i], cc[i], aa[i + 1]);
+      my[i] = fnms(my[i], cc[i], my[i + 1]);
+      const cpx<T> c2 = mul(cc[i], cc[i + 1]);
+      cc[i] = mk<T>(-c2.x, -c2.y);
+    }
+    // interface rows 2t (first row of the chunk) and 2t+1 (last row)
+    cpx<T> A0 = mk<T>(lo0, T(0));
+    cpx<T> B0 = fnms_r(d0, up0, aa[1]);
+    cpx<T> C0 = scal(-up0, cc[1]);
+    cpx<T> D0 = fnms_r(r0, up0, my[1]);
+    cpx<T> A1 = aa[M - 1];
+    cpx<T> B1 = mk<T>(T(1), T(0));
+    cpx<T> C1 = cc[M - 1];
+    cpx<T> D1 = my[M - 1];
+
+    // 3. PCR on the 2P interface rows
+    const int i0 = 2 * t, i1 = 2 * t + 1;
+    for (int sig = 1; sig < N; sig <<= 1) {
+      pa[i0] = A0; pb[i0] = B0; pc[i0] = C0; pd[i0] = D0; pib[i0] = recip(B0);
+      pa[i1] = A1; pb[i1] = B1; pc[i1] = C1; pd[i1] = D1; pib[i1] = recip(B1);
+      team_sync(P, tic);
+      cpx<T> nA0, nB0 = B0, nC0, nD0 = D0, nA1, nB1 = B1, nC1, nD1 = D1;
+      {
+        const int lo = i0 - sig, hi = i0 + sig;
+        nA0 = mk<T>(T(0), T(0));
+        nC0 = mk<T>(T(0), T(0));
+        if (lo >= 0) {
+          const cpx<T> k1 = mul(A0, pib[lo]);
+          nA0 = mk<T>(T(0), T(0));
+          nA0 = fnms(nA0, k1, pa[lo]);
+          nB0 = fnms(nB0, k1, pc[lo]);
+          nD0 = fnms(nD0, k1, pd[lo]);
+        }
+        if (hi < N) {
+          const cpx<T> k2 = mul(C0, pib[hi]);
+          nC0 = fnms(nC0, k2, pc[hi]);
+          nB0 = fnms(nB0, k2, pa[hi]);
+          nD0 = fnms(nD0, k2, pd[hi]);
+        }
+      }
+      {
+        const int lo = i1 - sig, hi = i1 + sig;
+        nA1 = mk<T>(T(0), T(0));
+        nC1 = mk<T>(T(0), T(0));
+        if (lo >= 0) {
+          const cpx<T> k1 = mul(A1, pib[lo]);
+          nA1 = fnms(nA1, k1, pa[lo]);
+          nB1 = fnms(nB1, k1, pc[lo]);
+          nD1 = fnms(nD1, k1, pd[lo]);
+        }
+        if (hi < N) {
+          const cpx<T> k2 = mul(C1, pib[hi]);
+          nC1 = fnms(nC1, k2, pc[hi]);
+          nB1 = fnms(nB1, k2, pa[hi]);
+          nD1 = fnms(nD1, k2, pd[hi]);
+        }
+      }
+      team_sync(P, tic);
+      A0 = nA0; B0 = nB0; C0 = nC0; D0 = nD0;
+      A1 = nA1; B1 = nB1; C1 = nC1; D1 = nD1;
+    }
+    const cpx<T> xf = mul(D0, recip(B0));
+    const cpx<T> xl = mul(D1, recip(B1));
+
+    // 4. back substitution of the interior rows
+    my[0] = xf;
+#pragma unroll
+    for (int i = 1; i < M - 1; ++i) my[i] = fnms(fnms(my[i], aa[i], xf), cc[i], xl);
+    my[M - 1] = xl;
+    if (do_acc) {
+      const double2 om = a.omega[k];
+#pragma unroll
+      for (int i = 0; i < M; ++i) acc[i * P + t] += om.x * (double)my[i].x - om.y * (double)my[i].y;
+    }
+    team_sync(P, tic);
+
+    // 5. store
+    if (a.Y) {
+      for (int e = t; e < blen; e += P) a.Y[(int64_t)k * a.ldy + off + e] = dd[e + e / M];
+    }
+    // 6. dots with the Krylov basis
+    if (a.V && a.mdots > 0) {
+      const int nw = P >> 5, w = t >> 5, l = t & 31;
+      for (int q = 0; q < a.mdots; ++q) {
+        double sx = 0.0, sy = 0.0;
+        const double *vq = a.V + (int64_t)q * a.ldv + off;
+        for (int e = t; e < blen; e += P) {
+          const cpx<T> y = dd[e + e / M];
+          const double v = vq[e];
+          sx += v * (double)y.x;
+          sy += v * (double)y.y;
+        }
+        sx = warp_sum(sx);
+        sy = warp_sum(sy);
+        if (l == 0) red[w * a.mdots + q] = make_double2(sx, sy);
+      }
+      team_sync(P, tic);
+      for (int q = t; q < a.mdots; q += P) {
+        double sx = 0.0, sy = 0.0;
+        for (int i = 0; i < nw; ++i) {
+          sx += red[i * a.mdots + q].x;
+          sy += red[i * a.mdots + q].y;
+        }
+        a.gpart[((int64_t)k * g.nblk + blk) * a.mdots + q] = make_double2(sx, sy);
+      }
+    }
+    team_sync(P, tic);
+  }
+  if (do_acc) {
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      const int e = e0 + i;
+      if (e < blen) a.acc_part[(int64_t)team * blen + e] = acc[i * P + t];
+    }
+  }
+}
+
+__global__ void k_acc_reduce(int nblk, int blen, int R, const double *__restrict__ part, double *__restrict__ out,
+                             const int *skip_flag) {
+  if (skip_flag && *skip_flag) return;
+  const int64_t n = (int64_t)nblk * blen;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    const int blk = (int)(j / blen);
+    const int e = (int)(j - (int64_t)blk * blen);
+    double s = 0.0;
+    for (int r = 0; r < R; ++r) s += part[((int64_t)blk * R + r) * blen + e];
+    out[j] = s;
+  }
+}
+
+static int next_pow2(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+PintGeom pint_geometry(int nf, int nblk, int blen, int target_teams, int elem_bytes) {
+  (void)elem_bytes;
+  PintGeom g;
+  g.nf = nf;
+  g.nblk = nblk;
+  g.blen = blen;
+  g.M = blen <= 128 ? 4 : 8;
+  g.P = std::max(32, next_pow2((blen + g.M - 1) / g.M));
+  g.teams_per_cta = std::max(1, 256 / g.P);
+  int R = (target_teams + nblk - 1) / nblk;
+  g.R = std::max(1, std::min(R, nf));
+  return g;
+}
+
+template <typename T, int M>
+static void launch_pint_m(Ctx &c, const PintGeom &g, const PintArgs<T> &a) {
+  const size_t tb = TeamSmem<T, M>::bytes(g.P, a.mdots);
+  const size_t smem = tb * g.teams_per_cta;
+  const int nteams = g.nblk * g.R;
+  const int grid = (nteams + g.teams_per_cta - 1) / g.teams_per_cta;
+  const int threads = g.P * g.teams_per_cta;
+  cudaFuncSetAttribute(k_pint<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // algorithmic bytes: spectrum rows read/written as requested, plus the vector rhs
+  double bytes = 0.0;
+  const double per = (double)g.nf * g.nblk * g.blen;
+  if (a.R) bytes += per * sizeof(cpx<T>);
+  if (a.Y) bytes += per * sizeof(cpx<T>);
+  const char *fam = sizeof(T) == 8 ? (a.Y ? "pint_store_f64" : (a.V ? "pint_dots_f64" : "pint_acc_f64"))
+                                   : (a.Y ? "pint_store_f32" : (a.V ? "pint_dots_f32" : "pint_acc_f32"));
+  c.launch(fam, bytes, [&] { k_pint<T, M><<<grid, threads, smem, c.stream>>>(g, a, tb); });
+}
+
+template <typename T>
+void launch_pint(Ctx &c, const PintGeom &g, const PintArgs<T> &a) {
+  if (g.M == 4)
+    launch_pint_m<T, 4>(c, g, a);
+  else
+    launch_pint_m<T, 8>(c, g, a);
+}
+
+void launch_acc_reduce(Ctx &c, const PintGeom &g, const double *acc_part, double *out, const int *skip_flag) {
+  const int64_t n = (int64_t)g.nblk * g.blen;
+  const int grid = (int)std::min<int64_t>((n + 255) / 256, 4 * sm_count());
+  c.launch("acc_reduce", (double)n * g.R * 8.0 + n * 8.0,
+           [&] { k_acc_reduce<<<grid, 256, 0, c.stream>>>(g.nblk, g.blen, g.R, acc_part, out, skip_flag); });
+}
+
+template void launch_pint<double>(Ctx &, const PintGeom &, const PintArgs<double> &);
+template void launch_pint<float>(Ctx &, const PintGeom &, const PintArgs<float> &);
+
+}  // namespace pd

@@ -1,0 +1,182 @@
+"""Python wrapper of one ParaDiag plan: torch supplies device memory and the stream.
+
+A ``Plan`` holds the C plan handle, its device workspace (a torch uint8
+tensor) and the host copies of the operator it was built from.  All arithmetic
+happens in the CUDA library behind ``paradiag_*``.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _binding as B
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class Plan:
+    """All-at-once backward-Euler solver (Algorithm 1 + Algorithm 2) for one problem shape.
+
+    Parameters mirror ``pd_desc`` in include/paradiag.h.  ``precision`` is
+    "fp64" or "mixed".  G and U passed to ``solve`` are (nt, nx*ny) float64 CUDA
+    tensors, row j = time step j+1, spatial index contiguous.
+    """
+
+    def __init__(self, *, dim, nx, nt, tau, k_lo, k_diag, k_up, ny=1, k_lo_y=None, k_diag_y=None,
+                 k_up_y=None, precision="mixed", maxit=0, eps_krylov=0.0, max_refine=0, refine_tol=0.0,
+                 host_io=False, device=None, stream=None, workspace="torch"):
+        import torch
+
+        self._torch = torch
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.dim, self.nx, self.ny, self.nt = int(dim), int(nx), int(ny if dim == 2 else 1), int(nt)
+        self.nbar = self.nx * self.ny
+        self.precision = precision
+        self._arrays = [_f64(k_lo), _f64(k_diag), _f64(k_up), _f64(k_lo_y), _f64(k_diag_y), _f64(k_up_y)]
+        d = B.PdDesc()
+        d.abi_version = B.PD_ABI_VERSION
+        d.dim = self.dim
+        d.nx = self.nx
+        d.ny = self.ny
+        d.nt = self.nt
+        d.tau = float(tau)
+        d.k_lo, d.k_diag, d.k_up, d.k_lo_y, d.k_diag_y, d.k_up_y = [_ptr(a) for a in self._arrays]
+        d.precision = {"fp64": B.PD_FP64, "mixed": B.PD_MIXED}[precision]
+        d.maxit = int(maxit)
+        d.eps_krylov = float(eps_krylov)
+        d.q = 1
+        d.max_refine = int(max_refine)
+        d.refine_tol = float(refine_tol)
+        d.alpha = 1.0
+        d.stream = ctypes.c_void_p(self.stream.cuda_stream)
+        d.host_io = 1 if host_io else 0
+        self.desc = d
+        self.workspace_bytes = B.paradiag_workspace_size(d)
+        self.handle = None
+        with torch.cuda.device(self.device):
+            if workspace == "torch":
+                self._ws = torch.empty(self.workspace_bytes + 256, dtype=torch.uint8, device=self.device)
+                base = self._ws.data_ptr()
+                ptr = (base + 255) // 256 * 256
+                self.handle = B.paradiag_plan(d, ptr, self.workspace_bytes)
+            else:
+                self._ws = None
+                self.handle = B.paradiag_plan(d, 0, 0)
+
+    @classmethod
+    def from_problem(cls, problem, **kw):
+        """Build from any object with the fields of workloads.Problem."""
+        args = dict(dim=problem.dim, nx=problem.nx, ny=problem.ny, nt=problem.nt, tau=problem.tau,
+                    k_lo=problem.k_lo, k_diag=problem.k_diag, k_up=problem.k_up,
+                    k_lo_y=problem.k_lo_y, k_diag_y=problem.k_diag_y, k_up_y=problem.k_up_y)
+        args.update(kw)
+        return cls(**args)
+
+    # -- helpers -------------------------------------------------------------------
+    def _check(self, t, dtype, shape):
+        torch = self._torch
+        if not isinstance(t, torch.Tensor) or t.device != self.device or t.dtype != dtype:
+            raise ValueError(f"expected a {dtype} tensor on {self.device}")
+        if tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+            raise ValueError(f"expected a contiguous tensor of shape {shape}, got {tuple(t.shape)}")
+
+    @property
+    def spectrum_dtype(self):
+        torch = self._torch
+        return torch.complex128 if self.precision == "fp64" else torch.complex64
+
+    # -- main entry points ---------------------------------------------------------
+    def solve(self, G, U=None, allow_not_converged=False):
+        """U = solution of eq. (2) for right-hand side G.  Returns (U, stats dict)."""
+        torch = self._torch
+        shape = (self.nt, self.nbar)
+        self._check(G, torch.float64, shape)
+        if U is None:
+            U = torch.empty_like(G)
+        self._check(U, torch.float64, shape)
+        st = B.paradiag_solve(self.handle, G.data_ptr(), U.data_ptr(), allow_not_converged)
+        return U, st.as_dict()
+
+    def solve_host(self, G_host, U_host, allow_not_converged=False):
+        """Host-buffer variant: G_host, U_host are CPU tensors (pinned preferred)."""
+        torch = self._torch
+        for t in (G_host, U_host):
+            if t.device.type != "cpu" or t.dtype != torch.float64 or not t.is_contiguous():
+                raise ValueError("host buffers must be contiguous CPU float64 tensors")
+            if tuple(t.shape) != (self.nt, self.nbar):
+                raise ValueError("host buffer has the wrong shape")
+        st = B.paradiag_solve_host(self.handle, G_host.data_ptr(), U_host.data_ptr(), allow_not_converged)
+        return U_host, st.as_dict()
+
+    # -- stage entry points --------------------------------------------------------
+    def time_dft(self, X):
+        torch = self._torch
+        self._check(X, torch.float64, (self.nt, self.nbar))
+        nf = self.nt // 2 + 1 if self.nt > 1 else 1
+        Xhat = torch.empty((nf, self.nbar), dtype=self.spectrum_dtype, device=self.device)
+        B.paradiag_time_dft(self.handle, X.data_ptr(), Xhat.data_ptr())
+        return Xhat
+
+    def time_idft(self, Y):
+        torch = self._torch
+        nf = self.nt // 2 + 1 if self.nt > 1 else 1
+        self._check(Y, self.spectrum_dtype, (nf, self.nbar))
+        X = torch.empty((self.nt, self.nbar), dtype=torch.float64, device=self.device)
+        B.paradiag_time_idft(self.handle, Y.data_ptr(), X.data_ptr())
+        return X
+
+    def shifted_solve(self, R, want_y=True, want_b=True):
+        torch = self._torch
+        nf = self.nt // 2 + 1 if self.nt > 1 else 1
+        self._check(R, self.spectrum_dtype, (nf, self.nbar))
+        Y = torch.empty_like(R) if want_y else None
+        b = torch.empty(self.nbar, dtype=torch.float64, device=self.device) if want_b else None
+        B.paradiag_shifted_solve(self.handle, R.data_ptr(), Y.data_ptr() if Y is not None else None,
+                                 b.data_ptr() if b is not None else None)
+        return Y, b
+
+    def dst_y(self, X):
+        torch = self._torch
+        self._check(X, torch.float64, (self.nt, self.nbar))
+        Y = torch.empty_like(X)
+        B.paradiag_dst_y(self.handle, X.data_ptr(), Y.data_ptr())
+        return Y
+
+    def last_vectors(self):
+        torch = self._torch
+        b = torch.empty(self.nbar, dtype=torch.float64, device=self.device)
+        x = torch.empty_like(b)
+        B.paradiag_last_vectors(self.handle, b.data_ptr(), x.data_ptr())
+        return b, x
+
+    def set_timing(self, enable=True):
+        B.paradiag_set_timing(self.handle, enable)
+
+    def kernel_times(self):
+        return B.paradiag_kernel_times(self.handle)
+
+    def close(self):
+        if self.handle:
+            B.paradiag_destroy(self.handle)
+            self.handle = None
+        self._ws = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,132 @@
+"""Host-side checks of the C ABI (no GPU needed, no compute calls).
+
+The library must build for sm_103a here, load, export every symbol that
+include/paradiag.h declares, agree with the ctypes struct layouts, and reject
+bad descriptors in its pure-host argument validation.
+"""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import __graft_entry__ as entry
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "paradiag.h")
+
+
+@pytest.fixture(scope="module")
+def B():
+    entry.build()
+    from paper_2304_12597_gb300 import _binding
+
+    return _binding
+
+
+def _declared():
+    src = open(HEADER).read()
+    return sorted(set(re.findall(r"\b(paradiag_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol(B):
+    names = _declared()
+    assert len(names) >= 10
+    lib = ctypes.CDLL(B.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(B.SIGNATURES) == names
+    nm = subprocess.run(["nm", "-D", "--defined-only", B.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (paradiag_\w+)", nm))
+    assert exported == set(names)
+
+
+def test_struct_layouts_match_header(B, tmp_path):
+    prog = tmp_path / "sz.c"
+    prog.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "paradiag.h"\n'
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu\\n\", sizeof(pd_desc), sizeof(pd_stats),"
+        " sizeof(pd_kernel_time), offsetof(pd_desc, stream), offsetof(pd_desc, precision),"
+        " offsetof(pd_stats, kernel_launches));return 0;}\n")
+    exe = tmp_path / "sz"
+    subprocess.check_call(["gcc", "-I", os.path.dirname(HEADER), str(prog), "-o", str(exe)])
+    vals = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    assert vals == [ctypes.sizeof(B.PdDesc), ctypes.sizeof(B.PdStats), ctypes.sizeof(B.PdKernelTime),
+                    B.PdDesc.stream.offset, B.PdDesc.precision.offset, B.PdStats.kernel_launches.offset]
+
+
+def _desc(B, **kw):
+    n = kw.pop("n", 31)
+    lo = np.full(n, -1.0)
+    di = np.full(n, 2.0)
+    up = np.full(n, -1.0)
+    keep = [lo, di, up]
+    d = B.PdDesc()
+    d.abi_version = 1
+    d.dim = 1
+    d.nx = n
+    d.ny = 1
+    d.nt = 16
+    d.tau = 0.1
+    p = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))  # noqa: E731
+    d.k_lo, d.k_diag, d.k_up = p(lo), p(di), p(up)
+    d.precision = 0
+    for k, v in kw.items():
+        if k.startswith("y_"):
+            continue
+        setattr(d, k, v)
+    if kw.get("dim") == 2:
+        ny = kw.get("ny", 7)
+        ylo = kw.get("y_lo", np.full(ny, -1.0))
+        ydi = kw.get("y_diag", np.full(ny, 2.0))
+        yup = kw.get("y_up", np.full(ny, -1.0))
+        keep += [ylo, ydi, yup]
+        d.k_lo_y, d.k_diag_y, d.k_up_y = p(ylo), p(ydi), p(yup)
+    d._keep = keep
+    return d
+
+
+def _size_status(B, d):
+    n = ctypes.c_size_t(0)
+    return B.load().paradiag_workspace_size(ctypes.byref(d), ctypes.byref(n)), n.value
+
+
+def test_valid_descriptors_have_a_workspace(B):
+    for kw in ({}, {"precision": 1}, {"nt": 1}, {"n": 1}, {"n": 4096, "nt": 2048, "precision": 1},
+               {"dim": 2, "ny": 7}, {"dim": 2, "ny": 255, "n": 255, "nt": 256, "precision": 1}):
+        st, n = _size_status(B, _desc(B, **kw))
+        assert st == 0, (kw, B.last_error())
+        assert n > 0 and n % 256 == 0
+
+
+@pytest.mark.parametrize("kw,code", [
+    ({"abi_version": 2}, 1),
+    ({"dim": 3}, 1),
+    ({"nx": 0}, 1),
+    ({"nt": 3}, 2),
+    ({"nt": 16384}, 2),
+    ({"tau": 0.0}, 1),
+    ({"tau": float("nan")}, 1),
+    ({"precision": 7}, 1),
+    ({"maxit": 40}, 2),
+    ({"q": 2}, 2),
+    ({"alpha": 0.5}, 2),
+    ({"n": 5000}, 2),
+    ({"dim": 2, "ny": 6}, 2),
+    ({"dim": 2, "ny": 7, "y_diag": np.array([2, 2, 2, 3, 2, 2, 2.0])}, 2),
+    ({"dim": 2, "ny": 7, "y_up": np.array([-1, -1, -0.5, -1, -1, -1, -1.0])}, 2),
+])
+def test_bad_descriptors_are_rejected(B, kw, code):
+    st, _ = _size_status(B, _desc(B, **kw))
+    assert st == code, B.last_error()
+    assert B.last_error()
+
+
+def test_null_arguments_are_rejected(B):
+    L = B.load()
+    assert L.paradiag_workspace_size(None, None) == 1
+    assert L.paradiag_solve(None, None, None, None) == 1
+    assert L.paradiag_destroy(None) == 0
+    assert "sm_103a" in B.paradiag_version()

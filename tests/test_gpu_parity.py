@@ -1,0 +1,245 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (relative Frobenius norm against the oracle, as the method's
+accuracy contract states them): 1e-12 for the FP64 path and 1e-10 for the
+mixed path after refinement.  Stage tests compare each step of the path with
+the oracle's definition of that step.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import native
+from oracle import reference as R
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "mixed": 1e-10}
+
+
+@pytest.fixture(scope="module")
+def pd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as entry
+
+    entry.build()
+    import paper_2304_12597_gb300 as pkg
+
+    return pkg
+
+
+def dev():
+    return torch.device("cuda:0")
+
+
+def _solve(pd, P, prec, G=None, **kw):
+    G = P.G if G is None else G
+    with pd.Plan.from_problem(P, precision=prec, device=dev(), **kw) as plan:
+        U, st = plan.solve(torch.from_numpy(np.ascontiguousarray(G)).to(dev()))
+        b, x = plan.last_vectors()
+        return U.cpu().numpy(), st, b.cpu().numpy(), x.cpu().numpy()
+
+
+# ----------------------------------------------------------------------------
+# Stage a1 / a5: time DFTs
+# ----------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("nt,nbar", [(1, 5), (2, 3), (8, 17), (64, 100), (1024, 33), (4096, 3)])
+def test_time_dft_matches_definition(pd, prec, nt, nbar):
+    P = W.random_tridiag_problem(nbar, nt, seed=nt + nbar)
+    X = P.G
+    ref = R.dft_time(X)[: nt // 2 + 1 if nt > 1 else 1]
+    with pd.Plan.from_problem(P, precision=prec, device=dev()) as plan:
+        Xh = plan.time_dft(torch.from_numpy(X).to(dev())).cpu().numpy()
+        err = np.linalg.norm(Xh - ref) / np.linalg.norm(ref)
+        assert err < (1e-14 * max(1, np.log2(nt)) if prec == "fp64" else 2e-7 * max(1, np.log2(nt)))
+        # inverse of the half spectrum of real data returns the data
+        Xb = plan.time_idft(torch.from_numpy(ref.astype(Xh.dtype)).to(dev())).cpu().numpy()
+        err2 = np.linalg.norm(Xb - X) / np.linalg.norm(X)
+        assert err2 < (1e-14 * max(1, np.log2(nt)) if prec == "fp64" else 2e-7 * max(1, np.log2(nt)))
+
+
+# ----------------------------------------------------------------------------
+# Stage a2: shifted solves and b (eq. 7)
+# ----------------------------------------------------------------------------
+
+
+def _stage_problems():
+    return [W.heat1d_forced(127, 64, seed=1), W.heat1d_forced(1023, 32, seed=2),
+            W.advdiff1d_pulse(255, 16, seed=3), W.advdiff1d_pulse(4095, 8, seed=4),
+            W.random_tridiag_problem(1, 8, seed=5), W.random_tridiag_problem(2, 4, seed=6),
+            W.random_tridiag_problem(3, 2, seed=7), W.random_tridiag_problem(33, 16, seed=8),
+            W.random_tridiag_problem(129, 16, seed=9), W.random_tridiag_problem(200, 1, seed=10)]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("P", _stage_problems(), ids=lambda p: p.name)
+def test_shifted_solves_and_b(pd, prec, P):
+    ell = P.nt
+    nf = ell // 2 + 1 if ell > 1 else 1
+    pi, gamma = R.circulant_eigs(ell)
+    Rfull = R.dft_time(P.G)
+    op = R.operator(P)
+    L = np.stack([op.shifted_solve(1.0 - pi[i], P.tau, Rfull[i]) for i in range(ell)])
+    b_ref = (gamma @ L).real
+    K = R.k_dense(P) if P.nbar <= 1200 else None
+    ctype = np.complex128 if prec == "fp64" else np.complex64
+    with pd.Plan.from_problem(P, precision=prec, device=dev()) as plan:
+        Y, b = plan.shifted_solve(torch.from_numpy(Rfull[:nf].astype(ctype)).to(dev()))
+        Y = Y.cpu().numpy().astype(np.complex128)
+        b = b.cpu().numpy()
+    # backward error of every shifted system, and forward agreement with the oracle
+    for k in range(nf):
+        if K is not None:
+            A = (1.0 - pi[k]) * np.eye(P.nbar) + P.tau * K
+            bw = np.linalg.norm(A @ Y[k] - Rfull[k]) / (np.linalg.norm(A, 2) * np.linalg.norm(Y[k]) + 1e-300)
+            assert bw < (1e-15 if prec == "fp64" else 3e-7), (k, bw)
+    fwd = np.linalg.norm(Y - L[:nf]) / np.linalg.norm(L[:nf])
+    assert fwd < (1e-10 if prec == "fp64" else 5e-3)
+    assert np.linalg.norm(b - b_ref) / max(np.linalg.norm(b_ref), 1e-300) < (1e-10 if prec == "fp64" else 5e-3)
+
+
+# ----------------------------------------------------------------------------
+# Full path (Algorithm 1 + 2, and refinement) against the oracle
+# ----------------------------------------------------------------------------
+
+
+def _full_problems():
+    return [
+        W.config1(),
+        W.heat1d_forced(255, 128, seed=3),
+        W.advdiff1d_pulse(511, 256, seed=4),
+        W.random_tridiag_problem(1, 1, seed=1),
+        W.random_tridiag_problem(1, 16, seed=2),
+        W.random_tridiag_problem(2, 2, seed=3),
+        W.random_tridiag_problem(3, 64, seed=4),
+        W.random_tridiag_problem(7, 8, seed=5, symmetric=True),
+        W.random_tridiag_problem(33, 32, seed=6),
+        W.random_tridiag_problem(130, 4, seed=7),
+        W.random_tridiag_problem(4096, 8, seed=8),
+        W.heat2d_smooth(7, 8, 0.1, seed=1),
+        W.heat2d_smooth(15, 16, 0.1, seed=2),
+        W.heat2d_smooth(31, 32, 0.1, seed=3),
+        W.heat2d_smooth(1, 4, 0.1, seed=4),
+    ]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("P", _full_problems(), ids=lambda p: p.name)
+def test_solve_matches_oracle(pd, prec, P):
+    Uref = R.be_solve(P)
+    U, st, b, x = _solve(pd, P, prec)
+    assert R.rel_err(U, Uref) <= TOL[prec], st
+    if prec == "fp64":
+        # x_m of Algorithm 2 is the true final state u_l (Sec. 2: W = P^{-1} M x)
+        nl = max(np.linalg.norm(Uref[-1]), 1e-300)
+        assert np.linalg.norm(x - Uref[-1]) / nl < 1e-10
+
+
+@pytest.mark.parametrize("P", [W.random_tridiag_problem(12, 8, seed=3), W.heat1d_forced(31, 16, seed=1),
+                               W.heat2d_smooth(3, 4, 0.1, seed=1)], ids=lambda p: p.name)
+def test_b_is_last_slice_of_periodic_solution(pd, P):
+    K = R.k_dense(P)
+    Uper = R.periodic_solve_dense(K, P.tau, P.G).real
+    _, _, b, _ = _solve(pd, P, "fp64")
+    assert np.linalg.norm(b - Uper[-1]) <= 1e-12 * max(1.0, np.linalg.norm(Uper[-1]))
+
+
+def test_krylov_iterations_match_oracle_algorithm2(pd):
+    P = W.advdiff1d_pulse(63, 32, 0.3, seed=2)
+    _, info = R.paradiag(P, eps=1e-13, maxit=32)
+    _, st, _, _ = _solve(pd, P, "fp64", eps_krylov=1e-13)
+    assert abs(st["krylov_iters"] - info["krylov"]["m"]) <= 1
+    assert st["krylov_rel_resnorm"] <= 1e-13
+    assert st["pint_loops"] == st["krylov_iters"] + 2
+
+
+def test_breakdown_on_invariant_krylov_space(pd):
+    """u0 = one sine eigenmode: K_1(K, b) is invariant, Algorithm 2 stops with breakdown."""
+    n, nt = 63, 16
+    P = W.heat1d_sine_modes(n, nt, 1.0, seed=0)
+    x = np.arange(1, n + 1) / (n + 1)
+    G = np.zeros_like(P.G)
+    G[0] = np.sin(3 * np.pi * x)
+    U, st, _, _ = _solve(pd, P, "fp64", G=G)
+    assert st["breakdown"] == 1 and st["krylov_iters"] == 1
+    assert R.rel_err(U, R.be_solve(P, G=G)) <= 1e-12
+
+
+def test_zero_rhs_gives_zero(pd):
+    P = W.random_tridiag_problem(40, 8, seed=1)
+    for prec in ("fp64", "mixed"):
+        U, st, _, _ = _solve(pd, P, prec, G=np.zeros_like(P.G))
+        assert np.all(U == 0.0)
+
+
+def test_nonfinite_input_is_reported(pd):
+    P = W.random_tridiag_problem(40, 8, seed=1)
+    G = P.G.copy()
+    G[3, 5] = np.nan
+    with pytest.raises(pd.ParadiagError) as e:
+        _solve(pd, P, "fp64", G=G)
+    assert e.value.status_name == "PD_ERR_NONFINITE"
+
+
+def test_fp64_solve_is_deterministic(pd):
+    P = W.heat1d_forced(255, 64, seed=9)
+    with pd.Plan.from_problem(P, precision="fp64", device=dev()) as plan:
+        G = torch.from_numpy(P.G).to(dev())
+        U1, _ = plan.solve(G)
+        U2, _ = plan.solve(G)
+        assert torch.equal(U1, U2)
+
+
+def test_host_io_matches_device_solve(pd):
+    P = W.heat1d_forced(127, 64, seed=2)
+    with pd.Plan.from_problem(P, precision="mixed", device=dev(), host_io=True) as plan:
+        Gd = torch.from_numpy(P.G).to(dev())
+        Ud, _ = plan.solve(Gd)
+        Gh = torch.from_numpy(P.G.copy()).pin_memory()
+        Uh = torch.empty_like(Gh).pin_memory()
+        plan.solve_host(Gh, Uh)
+        assert torch.equal(Ud.cpu(), Uh)
+
+
+def test_dst_y_matches_definition(pd):
+    P = W.heat2d_smooth(15, 4, 0.1, seed=1)
+    n = 15
+    j = np.arange(1, n + 1)
+    S = np.sqrt(2.0 / (n + 1)) * np.sin(np.pi * np.outer(j, j) / (n + 1))
+    X = np.random.default_rng(0).standard_normal((4, n * n))
+    ref = np.einsum("ly,tyx->tlx", S, X.reshape(4, n, n)).reshape(4, -1)
+    with pd.Plan.from_problem(P, precision="fp64", device=dev()) as plan:
+        Y = plan.dst_y(torch.from_numpy(X).to(dev())).cpu().numpy()
+    assert np.linalg.norm(Y - ref) / np.linalg.norm(ref) < 1e-14
+
+
+# ----------------------------------------------------------------------------
+# The benchmark workloads at full size
+# ----------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("name", ["config2", "config4"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_full_size_1d_configs(pd, name, prec):
+    P = W.by_name(name)
+    Uref = R.be_solve(P)
+    U, st, _, x = _solve(pd, P, prec)
+    assert R.rel_err(U, Uref) <= TOL[prec], st
+
+
+@pytest.fixture(scope="module")
+def cfg3_ref():
+    P = W.config3()
+    return P, R.be_solve(P)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_full_size_2d_config3(pd, cfg3_ref, prec):
+    P, Uref = cfg3_ref
+    U, st, _, _ = _solve(pd, P, prec)
+    assert R.rel_err(U, Uref) <= TOL[prec], st
