@@ -1,0 +1,385 @@
+"""Benchmark of the all-at-once backward-Euler solve (ParaDiag, Algorithms 1-2).
+
+One step = one paradiag_solve of the whole path (time DFT, parallel-in-time
+shifted solves, Algorithm 2, final solves, inverse DFT; in mixed precision the
+FP64 residual and refinement sweeps as well) on one right-hand side of the
+workload, inputs resident in HBM.  Default workload: 1D heat, n_x = 1023,
+n_t = 1024, T = 1, 16 seeded space-time sine-mode forcing terms.
+
+Prints ONE JSON line (rank 0).  `value` = unknowns (n_x * n_t) solved per
+second summed over ranks, mixed path; the FP64 GPU path, the host-buffer end-to-
+end number, the dominant kernel's roofline and the CPU oracle are reported
+beside it.  `--impl reference` times the CPU oracle instead.
+
+Multi-GPU: every rank solves its own copy of the workload (independent
+problems, weak scaling, no collective on the data path); rank 0 reports
+max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "n_x·n_t unknowns/s at rel err ≤1e-10, mixed vs FP64 GPU; p50/p99 serve latency"
+UNIT = "unknowns/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="config2")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name):
+    import workloads as W
+
+    P = W.by_name(name)
+    desc = {
+        "config1": "1D heat n_x=127 n_t=64 T=1 sine-mode u0",
+        "config2": "1D heat n_x=1023 n_t=1024 T=1, 16 seeded space-time sine-mode forcing terms",
+        "config3": "2D heat 255x255 n_t=256 T=0.1 smooth random u0",
+        "config4": "1D advection-diffusion a=1 nu=1e-3 n_x=4095 n_t=2048 T=1 Gaussian pulse",
+    }[name]
+    return P, desc
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def max_over_ranks(value, world, device=None):
+    """Max of a float over ranks (identity for one rank)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_index(local):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    ids = [v for v in vis.split(",") if v.strip()]
+    if ids and local < len(ids):
+        return ids[local].strip()
+    return local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def csrc_hash():
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2304_12597_gb300", "csrc", "*"))):
+        with open(p, "rb") as f:
+            h.update(os.path.basename(p).encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(family, workload_name):
+    """DRAM bytes per launch from a committed ncu summary, if taken on the current kernels."""
+    path = os.path.join(ROOT, "profiles", f"traffic_{family}_{workload_name}.txt")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+    if kv.get("csrc_sha256_16") != csrc_hash():
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def flush_l2(buf):
+    buf.add_(1.0)  # writes 256 MiB, more than the 129 MB L2
+
+
+def time_steps(plan, G, U, steps, stream, flush, torch):
+    """Per-step CUDA-event times (ms) with an L2 flush before each step (not timed)."""
+    ts, launches = [], 0
+    for _ in range(steps):
+        flush()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, st = plan.solve(G, U)
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+        launches += st["kernel_launches"]
+    return ts, launches, st
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as entry
+
+    entry.build()
+    from paper_2304_12597_gb300 import Plan
+
+    rank, world, local = dist_env()
+    if args.gpus > 1 and world == 1:
+        print(json.dumps({"error": "--gpus > 1 needs torchrun (one process per GPU)"}))
+        return 2
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=device)
+    P, wdesc = workload(args.workload)
+    stream = torch.cuda.current_stream(device)
+    G = torch.from_numpy(P.G).to(device)
+    U = torch.empty_like(G)
+    flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
+    flush = lambda: flush_l2(flush_buf)  # noqa: E731
+    unknowns = P.unknowns
+
+    # ---- mixed path: the headline --------------------------------------------------
+    mixed = Plan.from_problem(P, precision="mixed", device=device, host_io=True)
+    for _ in range(max(args.warmup, 3)):
+        mixed.solve(G, U)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(gpu_index(local)) if rank == 0 else None
+    ts, launches, st_mixed = time_steps(mixed, G, U, args.steps, stream, flush, torch)
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    barrier(world)
+    total_ms = max_over_ranks(sum(ts), world, device)
+    U_mixed = U.cpu().numpy()
+    value = unknowns * args.steps * world / (total_ms / 1e3)
+
+    # ---- per-kernel timing pass (same workload, CUDA events on the plan's stream) ----
+    mixed.set_timing(True)
+    nk = max(3, min(args.steps, 20))
+    for _ in range(nk):
+        flush()
+        mixed.solve(G, U)
+    kt = mixed.kernel_times()
+    mixed.set_timing(False)
+    dom = max(kt, key=lambda r: r["total_ms"])
+    peak, peak_kind = peaks()
+    achieved = (dom["bytes"] / dom["launches"]) / (dom["total_ms"] / dom["launches"] / 1e3) / 1e9
+    traffic = ncu_traffic(dom["name"], args.workload)
+    roofline = {"bound": "hbm", "kernel": dom["name"], "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+                "traffic": traffic, "bytes_per_launch": dom["bytes"] / dom["launches"],
+                "ms_per_launch": dom["total_ms"] / dom["launches"],
+                "share_of_kernel_time": round(dom["total_ms"] / sum(r["total_ms"] for r in kt), 3)}
+    kernel_table = {r["name"]: {"launches_per_step": r["launches"] / nk,
+                                "ms_per_step": r["total_ms"] / nk} for r in kt}
+
+    # ---- end to end through the host-buffer C ABI call ------------------------------
+    Gh = torch.from_numpy(P.G.copy()).pin_memory()
+    Uh = torch.empty_like(Gh).pin_memory()
+    mixed.solve_host(Gh, Uh)
+    e2e_ts = []
+    for _ in range(max(3, min(args.steps, 50))):
+        flush()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mixed.solve_host(Gh, Uh)
+        e2e_ts.append(time.perf_counter() - t0)
+    e2e_s = max_over_ranks(sum(e2e_ts), world, device)
+    e2e_value = unknowns * len(e2e_ts) * world / e2e_s
+    mixed.close()
+
+    # ---- plain FP64 GPU path ----------------------------------------------------------
+    fp = Plan.from_problem(P, precision="fp64", device=device)
+    for _ in range(3):
+        fp.solve(G, U)
+    nfp = max(3, min(args.steps, 50))
+    ts64, _, st64 = time_steps(fp, G, U, nfp, stream, flush, torch)
+    fp64_ms = max_over_ranks(sum(ts64), world, device)
+    U_fp64 = U.cpu().numpy()
+    fp.close()
+    fp64_value = unknowns * nfp * world / (fp64_ms / 1e3)
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64 shifted solves/FFTs + f64 Krylov, residual, update",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {wdesc}", "n_x": P.nbar, "n_t": P.nt, "precision": "mixed",
+                   "l2": "flushed before every timed step (256 MiB write, not timed)",
+                   "parallelism": f"replicas x{world} (independent solves per GPU)"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(P.G.nbytes),
+                "d2h_bytes_per_step": int(P.G.nbytes)},
+        "gpu_launches": int(launches),
+        "fp64_gpu": {"value": fp64_value, "unit": UNIT, "ms_per_step": fp64_ms / nfp,
+                     "krylov_iters": st64["krylov_iters"]},
+        "mixed_over_fp64": value / fp64_value,
+        "solver": {"refine_sweeps": st_mixed["refine_sweeps"], "krylov_iters_total": st_mixed["krylov_iters_total"],
+                   "pint_loops": st_mixed["pint_loops"], "launches_per_step": launches / args.steps},
+        "roofline": roofline,
+        "kernels": kernel_table,
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"], out["parity"] = cpu_baseline(P, args.workload, {"mixed": U_mixed, "fp64": U_fp64})
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def cpu_baseline(P, name, gpu_results):
+    """The CPU oracle (sequential backward Euler, FP64, one host core), timed on a
+    bounded sample, plus the parity of the GPU results against its output."""
+    import numpy as np
+
+    from oracle import reference as R
+
+    t0 = time.perf_counter()
+    Uref = R.be_solve(P)
+    dt = time.perf_counter() - t0
+    reps = 1
+    budget = 3.0
+    while time.perf_counter() - t0 < budget and reps < 1000:
+        R.be_solve(P)
+        reps += 1
+    total = time.perf_counter() - t0
+    parity = {k: R.rel_err(v, Uref) for k, v in gpu_results.items()}
+    parity["tolerance"] = {"mixed": 1e-10, "fp64": 1e-12}
+    parity["pass"] = bool(parity["mixed"] <= 1e-10 and parity["fp64"] <= 1e-12)
+    base = {"value": P.unknowns * reps / total, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{reps} full solves of {name} ({P.unknowns} unknowns each, ~{budget:.0f} s budget, "
+                      f"first solve {dt * 1e3:.1f} ms)"}
+    return base, parity
+
+
+def run_reference(args):
+    """The oracle as the reference arm: sequential FP64 backward Euler on host cores."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import native
+    from oracle import reference as R
+
+    native.build()
+    P, wdesc = workload(args.workload)
+    for _ in range(max(args.warmup, 1)):
+        R.be_solve(P)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        R.be_solve(P)
+        ts.append(time.perf_counter() - t0)
+    total = sum(ts)
+    value = P.unknowns * args.steps / total
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": max(args.warmup, 1), "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {wdesc}", "n_x": P.nbar, "n_t": P.nt, "precision": "fp64",
+                   "l2": "host run", "parallelism": "one host core (sequential time stepping)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} full solves of {args.workload}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -76,10 +76,17 @@ typedef struct pd_desc {
   int32_t precision;     /* pd_precision */
   int32_t maxit;         /* Algorithm 2 iteration limit, 1 <= maxit <= 32 (0 = 32) */
   double eps_krylov;     /* Algorithm 2 tolerance epsilon (stop when ||r|| <= eps * ||b||);
-                            0 = 1e-13 for PD_FP64, 1e-6 for the inner solves of PD_MIXED */
+                            0 = 1e-13 for PD_FP64, 1e-6 for the inner solves of PD_MIXED.
+                            Both also stop when ||r|| stalls (no halving over 1 iteration in
+                            PD_MIXED, over 3 in PD_FP64) */
   int32_t q;             /* residual check period of Algorithm 2; only q = 1 is built */
-  int32_t max_refine;    /* PD_MIXED: refinement sweeps after the first solve (0 = 6) */
-  double refine_tol;     /* PD_MIXED: stop when ||delta||_F <= refine_tol * ||U||_F (0 = 1e-13) */
+  int32_t max_refine;    /* refinement sweeps after the first solve (0 = 8).  PD_MIXED always
+                            refines; PD_FP64 refines only when Algorithm 2 stopped short of
+                            eps_krylov (stall or maxit), since the residual of eq. (2) left by
+                            an inexact x_m is exactly -r_m in the first time step */
+  double refine_tol;     /* refinement stops when the predicted remaining relative error,
+                            (||delta_s|| / ||delta_{s-1}||) * ||delta_s|| / ||U||, is <= refine_tol
+                            (0 = 1e-14 for PD_FP64, 1e-12 for PD_MIXED) */
   double alpha;          /* alpha of Sec. 4; only 1.0 (or 0 = 1.0) is built */
   void *stream;          /* cudaStream_t every launch is ordered on (NULL = legacy stream) */
   int32_t host_io;       /* nonzero: reserve device staging for paradiag_solve_host */
@@ -92,12 +99,12 @@ typedef struct pd_stats {
   int32_t krylov_iters_total;  /* sum of m over all refinement sweeps */
   int32_t pint_loops;          /* parallel-in-time loops in the paper's count, m/q + 2 per solve */
   int32_t shifted_sweeps;      /* passes over all l/2+1 shifted systems actually executed */
-  int32_t refine_sweeps;       /* solves performed (1 for PD_FP64) */
+  int32_t refine_sweeps;       /* solves performed (first solve + refinement sweeps) */
   int32_t breakdown;           /* 1 if Algorithm 2 met an invariant Krylov space */
   int64_t kernel_launches;     /* this library's kernel launches during the solve */
   double beta;                 /* ||b|| of the last Algorithm-2 run */
   double krylov_rel_resnorm;   /* eq. (13) residual / ||b|| at exit of the last run */
-  double rel_update;           /* PD_MIXED: ||delta||_F / ||U||_F of the last sweep */
+  double rel_update;           /* ||delta||_F / ||U||_F of the last refinement sweep (0 if none) */
   double ms_total;             /* wall time of the solve measured with CUDA events */
 } pd_stats;
 
@@ -164,8 +171,9 @@ pd_status paradiag_shifted_solve(pd_plan *plan, const void *R_dev, void *Y_dev, 
  * inverse).  This is the transform that diagonalises T_y (Sec. 6.1 operator). */
 pd_status paradiag_dst_y(pd_plan *plan, const double *X_dev, double *Y_dev);
 
-/* After a solve: the SMW right-hand side b (eq. 7) and the Algorithm-2 solution x_m of
- * eq. (8) from the last sweep, float64 length n_bar, device.  Either may be NULL. */
+/* After a solve: the SMW right-hand side b (eq. 7) for G and the Algorithm-2 solution
+ * x_m of eq. (8) from the first solve (before any refinement sweep), float64 length
+ * n_bar, device.  Either may be NULL. */
 pd_status paradiag_last_vectors(pd_plan *plan, double *b_dev, double *x_dev);
 
 /* ---- Kernel timing (tracing) ------------------------------------------------------ */

@@ -225,12 +225,15 @@ static int ilog2(int n) {
   return l;
 }
 
-// Columns per CTA: as many as fit ~96 KB of series (two CTAs per SM), capped.
+// Columns per CTA: as many as fit ~96 KB of series (two CTAs per SM), capped,
+// then narrowed (down to 4 columns = one 32-byte sector of doubles per row) until
+// the grid covers every SM twice.
 template <typename T>
-static int pick_tx(int n, int cap) {
+static int pick_tx(int n, int cap, int64_t ncols) {
   const size_t budget = 96 * 1024;
   int tx = cap;
   while (tx > 2 && (size_t)(tx / 2) * n * sizeof(cpx<T>) > budget) tx >>= 1;
+  while (tx > 4 && (ncols + tx - 1) / tx < 2 * (int64_t)sm_count()) tx >>= 1;
   return tx;
 }
 
@@ -238,7 +241,7 @@ template <typename T, typename Tin>
 void launch_fft_r2c(Ctx &c, const Tin *X, int64_t ldx, int64_t ncols, int n, const cpx<T> *tw,
                     cpx<T> *S, int64_t lds) {
   const int logn = ilog2(n);
-  const int TX = pick_tx<T>(n, sizeof(T) == 8 ? 8 : 16);
+  const int TX = pick_tx<T>(n, sizeof(T) == 8 ? 8 : 16, ncols);
   const size_t smem = (size_t)(TX / 2) * n * sizeof(cpx<T>);
   const int grid = (int)((ncols + TX - 1) / TX);
   if (smem > 48 * 1024)
@@ -253,7 +256,7 @@ template <typename T>
 void launch_fft_c2r(Ctx &c, const cpx<T> *S, int64_t lds, int64_t ncols, int n, const cpx<T> *tw,
                     void *out, int64_t ldo, int mode, double *norm_part, int *nparts) {
   const int logn = ilog2(n);
-  const int TX = pick_tx<T>(n, sizeof(T) == 8 ? 8 : 16);
+  const int TX = pick_tx<T>(n, sizeof(T) == 8 ? 8 : 16, ncols);
   const size_t smem = (size_t)(TX / 2) * n * sizeof(cpx<T>);
   const int grid = (int)((ncols + TX - 1) / TX);
   if (smem > 48 * 1024)
@@ -271,7 +274,7 @@ void launch_dst_y(Ctx &c, const Tin *X, Tout *Y, int64_t nt, int64_t ny, int64_t
                   int mode) {
   const int N = (int)(2 * (ny + 1));
   const int logN = ilog2(N);
-  const int TX = pick_tx<T>(N, sizeof(T) == 8 ? 8 : 16);
+  const int TX = pick_tx<T>(N, sizeof(T) == 8 ? 8 : 16, nt * nx);
   const size_t smem = (size_t)(TX / 2) * N * sizeof(cpx<T>);
   const int ntile = (int)((nx + TX - 1) / TX);
   const int64_t grid = nt * ntile;

@@ -20,7 +20,11 @@
 #include <algorithm>
 #include <cmath>
 
+#include <cooperative_groups.h>
+
 #include "pd_internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace pd {
 
@@ -40,21 +44,57 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
   return t;  // valid in warp 0
 }
 
-// part[cta * ld + 0] = sum of b^2 over the CTA's slice
-__global__ void k_sumsq_part(const double *__restrict__ b, int n, double *part, int ld) {
+// Cooperative kernels: one CTA per SM at most (co-residency is checked by the
+// cooperative launch), phases separated by grid-wide barriers.  `part` holds
+// three (grid, ld) panels of per-CTA partial sums; every CTA re-reduces a panel
+// in the same order, so all CTAs see identical coefficients.
+
+// part_row[q] = sum over this CTA's slice of V[q][j] x[j] (q < m); part_row[m] = ||x||^2.
+__device__ void cta_dots(int n, int m, const double *__restrict__ V, const double *__restrict__ x,
+                         double *part_row, double *red) {
+  for (int q = 0; q <= m; ++q) {
+    double s = 0.0;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+      const double xj = x[j];
+      s += (q < m ? V[(int64_t)q * n + j] : xj) * xj;
+    }
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) part_row[q] = s;
+  }
+}
+
+// c[q] = sum_cta panel[cta][q], q <= m (threads 0..m), then a CTA barrier.
+__device__ void cta_gather(const double *panel, int ld, int nparts, int m, double *c) {
+  if ((int)threadIdx.x <= m) {
+    double s = 0.0;
+    for (int i = 0; i < nparts; ++i) s += panel[i * ld + threadIdx.x];
+    c[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+// x -= sum_{q<m} c[q] V[q] over this CTA's slice.
+__device__ void cta_axpy(int n, int m, const double *__restrict__ V, double *x, const double *c) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    double xj = x[j];
+    for (int q = 0; q < m; ++q) xj -= c[q] * V[(int64_t)q * n + j];
+    x[j] = xj;
+  }
+}
+
+// beta = ||b||, V[0] = b / beta; resets scal/flags.
+__global__ void __launch_bounds__(kBlas) k_init_v0_coop(const double *__restrict__ b, int n, double *part, int ld,
+                                                        double *V, double *scal, int *flags) {
+  cg::grid_group grid = cg::this_grid();
   __shared__ double red[32];
+  __shared__ double c[34];
   double s = 0.0;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) s += b[j] * b[j];
   s = block_sum(s, red);
   if (threadIdx.x == 0) part[blockIdx.x * ld] = s;
-}
-
-// beta = sqrt(sum part); V[0] = b / beta; resets flags.
-__global__ void k_init_v0(const double *__restrict__ b, int n, const double *part, int ld, int nparts, double *V,
-                          double *scal, int *flags) {
-  double s = 0.0;
-  for (int i = 0; i < nparts; ++i) s += part[i * ld];
-  const double beta = sqrt(s);
+  grid.sync();
+  cta_gather(part, ld, gridDim.x, 0, c);
+  const double beta = sqrt(c[0]);
   const bool zero = !(beta > 0.0);
   const double ib = zero ? 0.0 : 1.0 / beta;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) V[j] = b[j] * ib;
@@ -68,105 +108,86 @@ __global__ void k_init_v0(const double *__restrict__ b, int n, const double *par
   }
 }
 
-// w = K v_{m-1}; partial dots V[q] . w (q < m) and ||w||^2 at slot m.
-__global__ void k_matvec_dots(int n, int m, const double *__restrict__ klo, const double *__restrict__ kdiag,
-                              const double *__restrict__ kup, const double *__restrict__ V, double *__restrict__ w,
-                              double *part, int ld) {
+// One Arnoldi step (eq. 10): w = K v_{m-1}; two classical Gram-Schmidt passes
+// against v_0..v_{m-1} (their coefficients summed into column m-1 of T_m);
+// t = ||w||; v_m = w / t, or breakdown when t <= 1e-14 ||K v_{m-1}||.
+__global__ void __launch_bounds__(kBlas) k_arnoldi_coop(int n, int m, const double *__restrict__ klo,
+                                                        const double *__restrict__ kdiag,
+                                                        const double *__restrict__ kup, double *V, double *w,
+                                                        double *T, int ldT, double *part, int ld, double *scal,
+                                                        int *flags) {
+  cg::grid_group grid = cg::this_grid();
   __shared__ double red[32];
+  __shared__ double c[34];
+  const int G = gridDim.x;
+  double *pa = part, *pb = part + (size_t)G * ld, *pc = part + (size_t)2 * G * ld;
   const double *v = V + (int64_t)(m - 1) * n;
-  double acc[33];
-  for (int q = 0; q <= m; ++q) acc[q] = 0.0;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
     double x = kdiag[j] * v[j];
     if (j > 0) x += klo[j] * v[j - 1];
     if (j + 1 < n) x += kup[j] * v[j + 1];
     w[j] = x;
-    for (int q = 0; q < m; ++q) acc[q] += V[(int64_t)q * n + j] * x;
-    acc[m] += x * x;
   }
-  for (int q = 0; q <= m; ++q) {
-    const double s = block_sum(acc[q], red);
-    if (threadIdx.x == 0) part[blockIdx.x * ld + q] = s;
-  }
-}
-
-// Partial dots V[q] . x (q < m) and ||x||^2 at slot m.
-__global__ void k_dots(int n, int m, const double *__restrict__ V, const double *__restrict__ x, double *part,
-                       int ld) {
-  __shared__ double red[32];
-  double acc[33];
-  for (int q = 0; q <= m; ++q) acc[q] = 0.0;
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-    const double xj = x[j];
-    for (int q = 0; q < m; ++q) acc[q] += V[(int64_t)q * n + j] * xj;
-    acc[m] += xj * xj;
-  }
-  for (int q = 0; q <= m; ++q) {
-    const double s = block_sum(acc[q], red);
-    if (threadIdx.x == 0) part[blockIdx.x * ld + q] = s;
-  }
-}
-
-// c_q = sum_cta pin[cta][q]; x -= sum_q c_q V[q]; partial dots of the new x into pout.
-// If Tcol != null, CTA 0 adds c_q to Tcol[q * ldT] (column m-1 of T_m); if save_norm,
-// CTA 0 stores sqrt(sum_cta pin[cta][m]) (||x|| before the update) into *norm_out.
-__global__ void k_axpy_dots(int n, int m, const double *__restrict__ V, double *__restrict__ x, const double *pin,
-                            double *pout, int ld, int nparts, double *Tcol, int ldT, int accumulate_T,
-                            double *norm_out) {
-  __shared__ double c[33];
-  __shared__ double red[32];
-  if (threadIdx.x <= m) {
-    double s = 0.0;
-    for (int i = 0; i < nparts; ++i) s += pin[i * ld + threadIdx.x];
-    c[threadIdx.x] = s;
-  }
-  __syncthreads();
-  if (blockIdx.x == 0 && threadIdx.x < m && Tcol) {
-    if (accumulate_T)
-      Tcol[threadIdx.x * ldT] += c[threadIdx.x];
-    else
-      Tcol[threadIdx.x * ldT] = c[threadIdx.x];
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0 && norm_out) *norm_out = sqrt(c[m]);
-  double acc[33];
-  for (int q = 0; q <= m; ++q) acc[q] = 0.0;
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-    double xj = x[j];
-    for (int q = 0; q < m; ++q) xj -= c[q] * V[(int64_t)q * n + j];
-    x[j] = xj;
-    for (int q = 0; q < m; ++q) acc[q] += V[(int64_t)q * n + j] * xj;
-    acc[m] += xj * xj;
-  }
-  for (int q = 0; q <= m; ++q) {
-    const double s = block_sum(acc[q], red);
-    if (threadIdx.x == 0) pout[blockIdx.x * ld + q] = s;
-  }
-}
-
-// t = ||w||; breakdown when t <= 1e-14 ||K v_{m-1}||; v_m = w / t.
-__global__ void k_arnoldi_finish(int n, int m, const double *pin, int ld, int nparts, const double *__restrict__ w,
-                                 double *V, double *T, int ldT, double *scal, int *flags) {
+  cta_dots(n, m, V, w, pa + (size_t)blockIdx.x * ld, red);
+  grid.sync();
+  cta_gather(pa, ld, G, m, c);
+  const double knorm = sqrt(c[m]);
+  if (blockIdx.x == 0 && (int)threadIdx.x < m) T[(int64_t)threadIdx.x * ldT + (m - 1)] = c[threadIdx.x];
+  cta_axpy(n, m, V, w, c);
+  cta_dots(n, m, V, w, pb + (size_t)blockIdx.x * ld, red);
+  grid.sync();
+  cta_gather(pb, ld, G, m, c);
+  if (blockIdx.x == 0 && (int)threadIdx.x < m) T[(int64_t)threadIdx.x * ldT + (m - 1)] += c[threadIdx.x];
+  cta_axpy(n, m, V, w, c);
   double s = 0.0;
-  for (int i = 0; i < nparts; ++i) s += pin[i * ld + m];
-  const double t = sqrt(s);
-  const bool bd = !(t > 1e-14 * scal[3]);
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) s += w[j] * w[j];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) pc[(size_t)blockIdx.x * ld] = s;
+  grid.sync();
+  __syncthreads();
+  cta_gather(pc, ld, G, 0, c);
+  const double t = sqrt(c[0]);
+  const bool bd = !(t > 1e-14 * knorm);
   const double it = bd ? 0.0 : 1.0 / t;
   double *vm = V + (int64_t)m * n;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) vm[j] = w[j] * it;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     T[(int64_t)m * ldT + (m - 1)] = bd ? 0.0 : t;
     scal[1] = bd ? 0.0 : t;
+    scal[3] = knorm;
     flags[0] = bd ? 1 : 0;
     if (!isfinite(t)) flags[2] = 1;
   }
 }
 
-// ||r_m|| = |tau t| sqrt(sum part[m]) (zero after a breakdown).
-__global__ void k_resnorm_finish(const double *pin, int ld, int nparts, int m, double tau, double *scal,
-                                 const int *flags) {
+// eq. (13): ||r_m|| = |tau t_{m+1,m}| ||(I - V_m V_m^T) z|| with two CGS passes
+// (z is overwritten by its projection); zero after a breakdown.
+__global__ void __launch_bounds__(kBlas) k_project_coop(int n, int m, const double *__restrict__ V, double *z,
+                                                        double tau, double *part, int ld, double *scal,
+                                                        const int *flags) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ double red[32];
+  __shared__ double c[34];
+  const int G = gridDim.x;
+  double *pa = part, *pb = part + (size_t)G * ld, *pc = part + (size_t)2 * G * ld;
+  cta_dots(n, m, V, z, pa + (size_t)blockIdx.x * ld, red);
+  grid.sync();
+  cta_gather(pa, ld, G, m, c);
+  cta_axpy(n, m, V, z, c);
+  cta_dots(n, m, V, z, pb + (size_t)blockIdx.x * ld, red);
+  grid.sync();
+  cta_gather(pb, ld, G, m, c);
+  cta_axpy(n, m, V, z, c);
   double s = 0.0;
-  for (int i = 0; i < nparts; ++i) s += pin[i * ld + m];
-  scal[2] = flags[0] ? 0.0 : fabs(tau * scal[1]) * sqrt(s);
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) s += z[j] * z[j];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) pc[(size_t)blockIdx.x * ld] = s;
+  grid.sync();
+  if (blockIdx.x == 0) {
+    __syncthreads();
+    cta_gather(pc, ld, G, 0, c);
+    if (threadIdx.x == 0) scal[2] = flags[0] ? 0.0 : fabs(tau * scal[1]) * sqrt(c[0]);
+  }
 }
 
 // ---- eq. (12): capacitance-system terms, one warp per frequency -----------------
@@ -223,8 +244,11 @@ __device__ void warp_gj_inverse(cpx<double> *H, cpx<double> *X, cpx<double> *fco
 
 constexpr int kK5Warps = 4;
 
+// Per-warp shared-memory slice, rounded up to 16 bytes so that every warp's
+// complex (16-byte) arrays stay aligned for any m.
 __host__ __device__ inline size_t k5a_warp_bytes(int m) {
-  return (size_t)(2 * m * m + 2 * m) * sizeof(cpx<double>) + (size_t)m * m * sizeof(double);
+  const size_t b = (size_t)(2 * m * m + 2 * m) * sizeof(cpx<double>) + (size_t)m * m * sizeof(double);
+  return (b + 15) & ~(size_t)15;
 }
 
 __global__ void __launch_bounds__(kK5Warps * 32) k_capacitance_terms(
@@ -340,7 +364,8 @@ __global__ void k_sumsq_final(const double *part, int nparts, double *dst) {
 }
 
 // ---- FP64 all-at-once residual ---------------------------------------------------
-__global__ void k_residual(const double *__restrict__ G, const double *__restrict__ U, float *__restrict__ R,
+template <typename Tout>
+__global__ void k_residual(const double *__restrict__ G, const double *__restrict__ U, Tout *__restrict__ R,
                            int64_t nt, int64_t ny, int64_t nx, double tau, const double *__restrict__ xlo,
                            const double *__restrict__ xdiag, const double *__restrict__ xup,
                            const double *__restrict__ ylo, const double *__restrict__ ydiag,
@@ -348,7 +373,7 @@ __global__ void k_residual(const double *__restrict__ G, const double *__restric
   __shared__ double red[32];
   const int64_t nb = ny * nx;
   const int64_t total = nt * nb;
-  float ss = 0.f;
+  double ss = 0.0;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int64_t t = idx / nb;
@@ -367,42 +392,40 @@ __global__ void k_residual(const double *__restrict__ G, const double *__restric
     }
     double r = G[idx] - uj - tau * ku;
     if (t > 0) r += U[idx - nb];
-    const float rf = (float)r;
-    R[idx] = rf;
-    ss += rf * rf;
+    const Tout ro = (Tout)r;
+    R[idx] = ro;
+    const float rf = (float)ro;
+    ss += (double)(rf * rf);
   }
-  double s = block_sum((double)ss, red);
+  double s = block_sum(ss, red);
   if (threadIdx.x == 0 && norm_part) norm_part[blockIdx.x] = s;
 }
 
 // ---- launchers -------------------------------------------------------------------
 
+static void coop_launch(Ctx &c, const char *fam, double bytes, const void *fn, int grid, void **args) {
+  c.launch(fam, bytes, [&] { cudaLaunchCooperativeKernel(fn, grid, kBlas, args, 0, c.stream); });
+}
+
 void launch_vec_norm_init(Ctx &c, KrylovBufs &k, const double *b) {
   const int ld = k.maxit + 2;
-  c.launch("krylov_blas1", (double)k.n * 8, [&] { k_sumsq_part<<<k.grid, kBlas, 0, c.stream>>>(b, k.n, k.part, ld); });
-  c.launch("krylov_blas1", (double)k.n * 16, [&] {
-    k_init_v0<<<k.grid, kBlas, 0, c.stream>>>(b, k.n, k.part, ld, k.grid, k.V, k.scal, k.flags);
-  });
+  int n = k.n;
+  double *part = k.part, *V = k.V, *scal = k.scal;
+  int *flags = k.flags;
+  void *args[] = {(void *)&b, &n, &part, (void *)&ld, &V, &scal, &flags};
+  coop_launch(c, "krylov_blas1", (double)k.n * 16, (const void *)k_init_v0_coop, k.grid, args);
 }
 
 // Partial buffers: k.part holds three (grid, maxit+2) panels.
 void launch_arnoldi(Ctx &c, KrylovBufs &k, int m) {
   const int ld = k.maxit + 2;
-  double *pa = k.part, *pb = k.part + (size_t)k.grid * ld, *pc = k.part + (size_t)2 * k.grid * ld;
-  const double bytes = (double)k.n * 8.0 * (m + 2);
-  c.launch("krylov_blas1", bytes, [&] {
-    k_matvec_dots<<<k.grid, kBlas, 0, c.stream>>>(k.n, m, k.klo, k.kdiag, k.kup, k.V, k.w, pa, ld);
-  });
-  double *Tcol = k.T + (m - 1);
-  c.launch("krylov_blas1", bytes, [&] {
-    k_axpy_dots<<<k.grid, kBlas, 0, c.stream>>>(k.n, m, k.V, k.w, pa, pb, ld, k.grid, Tcol, k.maxit, 0, k.scal + 3);
-  });
-  c.launch("krylov_blas1", bytes, [&] {
-    k_axpy_dots<<<k.grid, kBlas, 0, c.stream>>>(k.n, m, k.V, k.w, pb, pc, ld, k.grid, Tcol, k.maxit, 1, nullptr);
-  });
-  c.launch("krylov_blas1", (double)k.n * 16, [&] {
-    k_arnoldi_finish<<<k.grid, kBlas, 0, c.stream>>>(k.n, m, pc, ld, k.grid, k.w, k.V, k.T, k.maxit, k.scal, k.flags);
-  });
+  int n = k.n, ldT = k.maxit;
+  const double *klo = k.klo, *kdiag = k.kdiag, *kup = k.kup;
+  double *V = k.V, *w = k.w, *T = k.T, *part = k.part, *scal = k.scal;
+  int *flags = k.flags;
+  void *args[] = {&n, &m, (void *)&klo, (void *)&kdiag, (void *)&kup, &V, &w, &T, &ldT, &part, (void *)&ld, &scal,
+                  &flags};
+  coop_launch(c, "krylov_blas1", (double)k.n * 8.0 * (3 * m + 4), (const void *)k_arnoldi_coop, k.grid, args);
 }
 
 void launch_capacitance(Ctx &c, KrylovBufs &k, int m, int nf, double tau, const double2 *shift, const double2 *wg,
@@ -423,19 +446,13 @@ void launch_capacitance(Ctx &c, KrylovBufs &k, int m, int nf, double tau, const 
 // ||(I - V_m V_m^T) z|| with two CGS passes (z is overwritten by the projection).
 void launch_project_resnorm(Ctx &c, KrylovBufs &k, int m, const double *z, double tau) {
   const int ld = k.maxit + 2;
-  double *pa = k.part, *pb = k.part + (size_t)k.grid * ld, *pc = k.part + (size_t)2 * k.grid * ld;
+  int n = k.n;
+  const double *V = k.V;
   double *zz = const_cast<double *>(z);
-  const double bytes = (double)k.n * 8.0 * (m + 1);
-  c.launch("krylov_blas1", bytes, [&] { k_dots<<<k.grid, kBlas, 0, c.stream>>>(k.n, m, k.V, zz, pa, ld); });
-  c.launch("krylov_blas1", bytes, [&] {
-    k_axpy_dots<<<k.grid, kBlas, 0, c.stream>>>(k.n, m, k.V, zz, pa, pb, ld, k.grid, nullptr, 0, 0, nullptr);
-  });
-  c.launch("krylov_blas1", bytes, [&] {
-    k_axpy_dots<<<k.grid, kBlas, 0, c.stream>>>(k.n, m, k.V, zz, pb, pc, ld, k.grid, nullptr, 0, 0, nullptr);
-  });
-  c.launch("krylov_blas1", 0.0, [&] {
-    k_resnorm_finish<<<1, 32, 0, c.stream>>>(pc, ld, k.grid, m, tau, k.scal, k.flags);
-  });
+  double *part = k.part, *scal = k.scal;
+  const int *flags = k.flags;
+  void *args[] = {&n, &m, (void *)&V, &zz, &tau, &part, (void *)&ld, &scal, (void *)&flags};
+  coop_launch(c, "krylov_blas1", (double)k.n * 8.0 * (3 * m + 3), (const void *)k_project_coop, k.grid, args);
 }
 
 void launch_xm(Ctx &c, KrylovBufs &k, int m, const double *y, double *x) {
@@ -447,15 +464,25 @@ void launch_sumsq(Ctx &c, const double *part, int nparts, double *dst) {
   c.launch("krylov_blas1", 0.0, [&] { k_sumsq_final<<<1, 32, 0, c.stream>>>(part, nparts, dst); });
 }
 
-void launch_residual(Ctx &c, const double *G, const double *U, float *R, int64_t nt, int64_t ny, int64_t nx,
+template <typename Tout>
+void launch_residual(Ctx &c, const double *G, const double *U, Tout *R, int64_t nt, int64_t ny, int64_t nx,
                      double tau, const double *xlo, const double *xdiag, const double *xup, const double *ylo,
                      const double *ydiag, const double *yup, double *norm_part, int *nparts) {
   const int64_t total = nt * ny * nx;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 8 * (int64_t)sm_count()));
   if (nparts) *nparts = grid;
-  c.launch("residual_f64", (double)total * (8 + 8 + 4), [&] {
-    k_residual<<<grid, 256, 0, c.stream>>>(G, U, R, nt, ny, nx, tau, xlo, xdiag, xup, ylo, ydiag, yup, norm_part);
-  });
+  c.launch(sizeof(Tout) == 8 ? "residual_f64_to_f64" : "residual_f64_to_f32", (double)total * (8 + 8 + sizeof(Tout)),
+           [&] {
+             k_residual<Tout><<<grid, 256, 0, c.stream>>>(G, U, R, nt, ny, nx, tau, xlo, xdiag, xup, ylo, ydiag, yup,
+                                                          norm_part);
+           });
 }
+
+template void launch_residual<float>(Ctx &, const double *, const double *, float *, int64_t, int64_t, int64_t, double,
+                                     const double *, const double *, const double *, const double *, const double *,
+                                     const double *, double *, int *);
+template void launch_residual<double>(Ctx &, const double *, const double *, double *, int64_t, int64_t, int64_t,
+                                      double, const double *, const double *, const double *, const double *,
+                                      const double *, const double *, double *, int *);
 
 }  // namespace pd

@@ -123,11 +123,12 @@ void launch_capacitance(Ctx &c, KrylovBufs &k, int m, int nf, double tau, const 
 void launch_project_resnorm(Ctx &c, KrylovBufs &k, int m, const double *z, double tau);
 void launch_xm(Ctx &c, KrylovBufs &k, int m, const double *y, double *x);
 void launch_sumsq(Ctx &c, const double *part, int nparts, double *dst);
-// FP64 all-at-once residual R = G - [(I + tau K) U - U Sigma_1^T], stored as float.
-// 1D: K tridiagonal (lo, diag, up) of length nx; 2D adds T_y along the middle axis.
-void launch_residual(Ctx &c, const double *G, const double *U, float *R, int64_t nt, int64_t ny,
-                     int64_t nx, double tau, const double *xlo, const double *xdiag,
-                     const double *xup, const double *ylo, const double *ydiag,
-                     const double *yup, double *norm_part, int *nparts);
+// FP64 all-at-once residual R = G - [(I + tau K) U - U Sigma_1^T], stored as Tout
+// (float for the mixed path, double for the FP64 path).  1D: K tridiagonal
+// (lo, diag, up) of length nx; 2D adds T_y along the middle axis.
+template <typename Tout>
+void launch_residual(Ctx &c, const double *G, const double *U, Tout *R, int64_t nt, int64_t ny, int64_t nx,
+                     double tau, const double *xlo, const double *xdiag, const double *xup, const double *ylo,
+                     const double *ydiag, const double *yup, double *norm_part, int *nparts);
 
 }  // namespace pd

@@ -252,16 +252,36 @@ __global__ void __launch_bounds__(512) k_pint(PintGeom g, PintArgs<T> a, size_t 
   }
 }
 
-__global__ void k_acc_reduce(int nblk, int blen, int R, const double *__restrict__ part, double *__restrict__ out,
-                             const int *skip_flag) {
+// out[j] = sum_r part[(blk*R + r)*blen + e], j = blk*blen + e.  A CTA of 32 x 32
+// threads owns 32 consecutive outputs; its 32 row groups each sum every 32nd
+// partial row (four independent accumulators), then one fixed-order pass over
+// the groups finishes the sum, so the result does not depend on scheduling.
+__global__ void __launch_bounds__(1024) k_acc_reduce(int nblk, int blen, int R, const double *__restrict__ part,
+                                                     double *__restrict__ out, const int *skip_flag) {
   if (skip_flag && *skip_flag) return;
+  __shared__ double sm[32][33];
   const int64_t n = (int64_t)nblk * blen;
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t j = (int64_t)blockIdx.x * 32 + threadIdx.x;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  if (j < n) {
     const int blk = (int)(j / blen);
     const int e = (int)(j - (int64_t)blk * blen);
-    double s = 0.0;
-    for (int r = 0; r < R; ++r) s += part[((int64_t)blk * R + r) * blen + e];
-    out[j] = s;
+    const double *base = part + (int64_t)blk * R * blen + e;
+    int r = threadIdx.y;
+    for (; r + 96 < R; r += 128) {
+      s0 += base[(int64_t)r * blen];
+      s1 += base[(int64_t)(r + 32) * blen];
+      s2 += base[(int64_t)(r + 64) * blen];
+      s3 += base[(int64_t)(r + 96) * blen];
+    }
+    for (; r < R; r += 32) s0 += base[(int64_t)r * blen];
+  }
+  sm[threadIdx.y][threadIdx.x] = (s0 + s1) + (s2 + s3);
+  __syncthreads();
+  if (threadIdx.y == 0 && j < n) {
+    double t = 0.0;
+    for (int i = 0; i < 32; ++i) t += sm[i][threadIdx.x];
+    out[j] = t;
   }
 }
 
@@ -313,9 +333,9 @@ void launch_pint(Ctx &c, const PintGeom &g, const PintArgs<T> &a) {
 
 void launch_acc_reduce(Ctx &c, const PintGeom &g, const double *acc_part, double *out, const int *skip_flag) {
   const int64_t n = (int64_t)g.nblk * g.blen;
-  const int grid = (int)std::min<int64_t>((n + 255) / 256, 4 * sm_count());
+  const int grid = (int)((n + 31) / 32);
   c.launch("acc_reduce", (double)n * g.R * 8.0 + n * 8.0,
-           [&] { k_acc_reduce<<<grid, 256, 0, c.stream>>>(g.nblk, g.blen, g.R, acc_part, out, skip_flag); });
+           [&] { k_acc_reduce<<<grid, dim3(32, 32), 0, c.stream>>>(g.nblk, g.blen, g.R, acc_part, out, skip_flag); });
 }
 
 template void launch_pint<double>(Ctx &, const PintGeom &, const PintArgs<double> &);

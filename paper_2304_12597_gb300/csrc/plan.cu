@@ -173,12 +173,13 @@ struct pd_plan {
   double *V = nullptr, *T = nullptr, *w = nullptr, *part = nullptr, *scal = nullptr;
   int *flags = nullptr;
   double *b = nullptr, *z = nullptr, *x = nullptr, *y = nullptr;
+  double *b0 = nullptr, *x0 = nullptr;  // b and x_m of the first solve (for paradiag_last_vectors)
   double *acc_part = nullptr;
   double2 *gpart = nullptr, *srow = nullptr, *omega = nullptr;
   double *msys_part = nullptr;
   double *norm_part = nullptr;
   float *res_f = nullptr, *tmp_f = nullptr;
-  double *tmp_d = nullptr;
+  double *res_d = nullptr, *tmp_d = nullptr;
   double *G_stage = nullptr, *U_stage = nullptr;
   // pinned host mirrors of the scalar and flag blocks
   double *h_scal = nullptr;
@@ -246,8 +247,8 @@ void fill_geometry(pd_plan *p, const pd_desc *d) {
   p->precision = d->precision;
   p->maxit = d->maxit ? d->maxit : 32;
   p->eps = d->eps_krylov > 0 ? d->eps_krylov : (d->precision == PD_FP64 ? 1e-13 : 1e-6);
-  p->max_refine = d->max_refine ? d->max_refine : 6;
-  p->refine_tol = d->refine_tol > 0 ? d->refine_tol : 1e-13;
+  p->max_refine = d->max_refine ? d->max_refine : 8;
+  p->refine_tol = d->refine_tol > 0 ? d->refine_tol : (d->precision == PD_FP64 ? 1e-14 : 1e-12);
   p->host_io = d->host_io;
   p->nblk = (int)p->ny;
   p->blen = (int)p->nx;
@@ -264,7 +265,8 @@ void fill_geometry(pd_plan *p, const pd_desc *d) {
   const int ctas_per_sm = std::max(1, std::min(by_smem, by_threads));
   const int target = sms * ctas_per_sm * g0.teams_per_cta;
   p->geom = pd::pint_geometry(p->nf, p->nblk, p->blen, target, esz);
-  p->blas_grid = (int)std::max<int64_t>(1, std::min<int64_t>((p->nbar + 255) / 256, 2 * (int64_t)sms));
+  // cooperative Krylov kernels: at most one 256-thread CTA per SM (always co-resident)
+  p->blas_grid = (int)std::max<int64_t>(1, std::min<int64_t>((p->nbar + 255) / 256, (int64_t)sms));
   p->k5_grid = std::max(1, std::min((p->nf + 3) / 4, 2 * sms));
 }
 
@@ -313,6 +315,8 @@ size_t layout(pd_plan *p, unsigned char *base) {
   p->b = A.take<double>(nbar);
   p->z = A.take<double>(nbar);
   p->x = A.take<double>(nbar);
+  p->b0 = A.take<double>(nbar);
+  p->x0 = A.take<double>(nbar);
   p->y = A.take<double>(mx + 1);
   p->acc_part = A.take<double>((size_t)p->geom.nblk * p->geom.R * p->geom.blen);
   p->gpart = A.take<double2>((size_t)nf * p->nblk * mx);
@@ -322,6 +326,7 @@ size_t layout(pd_plan *p, unsigned char *base) {
   p->norm_part = A.take<double>((size_t)std::max<int64_t>(nbar / 2 + 2, 8 * (int64_t)pd::sm_count()));
   if (mixed) p->res_f = A.take<float>((size_t)nt * nbar);
   if (mixed && p->dim == 2) p->tmp_f = A.take<float>((size_t)nt * nbar);
+  if (!mixed) p->res_d = A.take<double>((size_t)nt * nbar);
   if (!mixed && p->dim == 2) p->tmp_d = A.take<double>((size_t)nt * nbar);
   if (p->host_io) {
     p->G_stage = A.take<double>((size_t)nt * nbar);
@@ -462,8 +467,18 @@ pd_status run_paradiag(pd_plan *p, const Tin *X, void *out, int out_mode, SolveI
   if (!std::isfinite(beta) || p->h_flags[2]) return fail(PD_ERR_NONFINITE, "non-finite ||b|| (input contains NaN/Inf?)");
   int m = 0;
   double res = beta;
+  double hist[40];
+  hist[0] = beta;
+  // Algorithm 2 stops at eps * beta or maxit (Sec. 3), and here also once the eq. (13)
+  // residual stops halving: in binary32 it levels off at the rounding-noise floor of
+  // the shifted solves, and in FP64 the polynomial space K_m(K, b) can stall for
+  // many steps when J_l is far from I.  The refinement sweeps recover the rest.
+  // Window: 1 iteration in binary32 (the floor is flat), 3 in FP64 (FOM residuals
+  // are not monotone, so a single non-halving step is not yet a stall).
+  const int win = p->precision == PD_MIXED ? 1 : 3;
   if (beta > 0.0) {
     while (res > p->eps * beta && m < p->maxit) {
+      if (m >= win + 1 && res > 0.5 * hist[m - win]) break;
       ++m;
       pd::launch_arnoldi(c, kb, m);
       // h_k = ((1 - pi_k) I + tau K)^{-1} v_{m+1} and g_k = V_m^T h_k
@@ -495,6 +510,7 @@ pd_status run_paradiag(pd_plan *p, const Tin *X, void *out, int out_mode, SolveI
       st = sync_read(p);
       if (st != PD_OK) return st;
       res = p->h_scal[2];
+      hist[m] = res;
       if (p->h_flags[2] || !std::isfinite(res)) return fail(PD_ERR_NONFINITE, "non-finite value in Algorithm 2");
       if (p->h_flags[0]) {
         info.breakdown = true;
@@ -527,61 +543,71 @@ pd_status run_paradiag(pd_plan *p, const Tin *X, void *out, int out_mode, SolveI
   return ctx_status(p);
 }
 
-pd_status solve_fp64(pd_plan *p, const double *G, double *U, pd_stats &s) {
-  SolveInfo info;
-  pd_status st;
-  if (p->dim == 1) {
-    st = run_paradiag<double, double>(p, G, U, 0, info);
-  } else {
-    pd::launch_dst_y<double, double, double>(p->ctx, G, p->tmp_d, p->nt, p->ny, p->nx, p->twy_d, 0);
-    st = run_paradiag<double, double>(p, p->tmp_d, p->tmp_d, 0, info);
-    if (st == PD_OK) pd::launch_dst_y<double, double, double>(p->ctx, p->tmp_d, U, p->nt, p->ny, p->nx, p->twy_d, 0);
-  }
-  if (st != PD_OK) return st;
-  s.krylov_iters = info.m;
-  s.krylov_iters_total = info.m;
-  s.pint_loops = info.pint_loops;
-  s.shifted_sweeps = info.sweeps_exec;
-  s.refine_sweeps = 1;
-  s.breakdown = info.breakdown;
-  s.beta = info.beta;
-  s.krylov_rel_resnorm = info.rel_res;
-  s.rel_update = 0.0;
-  st = ctx_status(p);
-  if (st != PD_OK) return st;
-  return info.converged ? PD_OK : fail(PD_ERR_NOT_CONVERGED, "Algorithm 2 reached maxit = %d", p->maxit);
-}
+template <typename T>
+T *res_buf(pd_plan *p);
+template <>
+double *res_buf<double>(pd_plan *p) { return p->res_d; }
+template <>
+float *res_buf<float>(pd_plan *p) { return p->res_f; }
+template <typename T>
+T *tmp_buf(pd_plan *p);
+template <>
+double *tmp_buf<double>(pd_plan *p) { return p->tmp_d; }
+template <>
+float *tmp_buf<float>(pd_plan *p) { return p->tmp_f; }
+template <typename T>
+const cpx<T> *dst_tw(pd_plan *p);
+template <>
+const cpx<double> *dst_tw<double>(pd_plan *p) { return p->twy_d; }
+template <>
+const cpx<float> *dst_tw<float>(pd_plan *p) { return p->twy_f; }
 
-pd_status solve_mixed(pd_plan *p, const double *G, double *U, pd_stats &s) {
-  double ref2 = 0.0;
+// Iterative refinement around Algorithm 1 on the all-at-once residual.
+// Sweep 0 solves eq. (2) for G; sweep s >= 1 solves it for the FP64 residual
+// G - [(I + tau K) U - U Sigma_1^T] and adds the correction to U (FP64).
+// If Algorithm 2 stops with ||r_m|| > 0, the U it produces satisfies eq. (2)
+// up to exactly -r_m in the first time step (its last slice is x_m - r_m while
+// the correction used x_m), so a sweep on that residual corrects precisely the
+// Krylov error.  T = compute type of the FFTs and shifted solves (double for
+// PD_FP64, float for PD_MIXED); residuals are stored in T.
+template <typename T>
+pd_status solve_refined(pd_plan *p, const double *G, double *U, pd_stats &s) {
+  const bool fp64 = sizeof(T) == 8;
+  const int out_mode_2d = fp64 ? 0 : 2;  // inverse DFT into the 2D temporary buffer
+  T *res = res_buf<T>(p);
+  T *tmp = tmp_buf<T>(p);
+  double ref2 = 0.0, rel_update = 1.0;
   int total_m = 0, loops = 0, execs = 0, sweeps = 0;
   SolveInfo info;
-  double rel_update = 1.0;
   bool conv = false;
   for (int sweep = 0; sweep <= p->max_refine; ++sweep) {
     SolveInfo si;
     pd_status st;
     if (sweep == 0) {
       if (p->dim == 1) {
-        st = run_paradiag<float, double>(p, G, U, 0, si);
+        st = run_paradiag<T, double>(p, G, U, 0, si);
       } else {
-        pd::launch_dst_y<double, float, float>(p->ctx, G, p->tmp_f, p->nt, p->ny, p->nx, p->twy_f, 0);
-        st = run_paradiag<float, float>(p, p->tmp_f, p->tmp_f, 2, si);
-        if (st == PD_OK) pd::launch_dst_y<float, double, float>(p->ctx, p->tmp_f, U, p->nt, p->ny, p->nx, p->twy_f, 0);
+        pd::launch_dst_y<double, T, T>(p->ctx, G, tmp, p->nt, p->ny, p->nx, dst_tw<T>(p), 0);
+        st = run_paradiag<T, T>(p, tmp, tmp, out_mode_2d, si);
+        if (st == PD_OK) pd::launch_dst_y<T, double, T>(p->ctx, tmp, U, p->nt, p->ny, p->nx, dst_tw<T>(p), 0);
       }
     } else {
       int np = 0;
-      pd::launch_residual(p->ctx, G, U, p->res_f, p->nt, p->ny, p->nx, p->tau, p->xlo, p->xdiag, p->xup, p->ylo,
-                          p->ydiag, p->yup, nullptr, &np);
+      pd::launch_residual<T>(p->ctx, G, U, res, p->nt, p->ny, p->nx, p->tau, p->xlo, p->xdiag, p->xup, p->ylo,
+                             p->ydiag, p->yup, nullptr, &np);
       if (p->dim == 1) {
-        st = run_paradiag<float, float>(p, p->res_f, U, 1, si);
+        st = run_paradiag<T, T>(p, res, U, 1, si);
       } else {
-        pd::launch_dst_y<float, float, float>(p->ctx, p->res_f, p->tmp_f, p->nt, p->ny, p->nx, p->twy_f, 0);
-        st = run_paradiag<float, float>(p, p->tmp_f, p->tmp_f, 2, si);
-        if (st == PD_OK) pd::launch_dst_y<float, double, float>(p->ctx, p->tmp_f, U, p->nt, p->ny, p->nx, p->twy_f, 1);
+        pd::launch_dst_y<T, T, T>(p->ctx, res, tmp, p->nt, p->ny, p->nx, dst_tw<T>(p), 0);
+        st = run_paradiag<T, T>(p, tmp, tmp, out_mode_2d, si);
+        if (st == PD_OK) pd::launch_dst_y<T, double, T>(p->ctx, tmp, U, p->nt, p->ny, p->nx, dst_tw<T>(p), 1);
       }
     }
     if (st != PD_OK) return st;
+    if (sweep == 0) {
+      CK(cudaMemcpyAsync(p->b0, p->b, sizeof(double) * p->nbar, cudaMemcpyDeviceToDevice, p->ctx.stream));
+      CK(cudaMemcpyAsync(p->x0, p->x, sizeof(double) * p->nbar, cudaMemcpyDeviceToDevice, p->ctx.stream));
+    }
     st = sync_read(p);
     if (st != PD_OK) return st;
     const double d2 = p->h_scal[4];
@@ -592,14 +618,32 @@ pd_status solve_mixed(pd_plan *p, const double *G, double *U, pd_stats &s) {
     execs += si.sweeps_exec;
     info = si;
     if (sweep == 0) ref2 = d2;
+    const double prev_update = rel_update;
     rel_update = ref2 > 0 ? std::sqrt(d2 / ref2) : 0.0;
-    if (sweep > 0 && rel_update <= p->refine_tol) {
-      conv = true;
-      break;
-    }
     if (ref2 == 0.0) {
       conv = true;
       break;
+    }
+    // FP64: Algorithm 2 met its tolerance, so this sweep's correction is exact to
+    // working accuracy (sweep 0: the paper's Algorithm 1 itself).
+    if (fp64 && si.converged) {
+      conv = true;
+      break;
+    }
+    // Each sweep contracts the error by rho ~ ||delta_s|| / ||delta_{s-1}||, so the
+    // error left after sweep s is about rho * ||delta_s||: stop once that predicted
+    // remainder (relative to ||U|| ~ ||delta_0||) is below refine_tol.
+    if (sweep > 0) {
+      const double rho = prev_update > 0 ? rel_update / prev_update : 0.0;
+      if (rho * rel_update <= p->refine_tol || rel_update <= 1e-15) {
+        conv = true;
+        break;
+      }
+      // No longer contracting: the rounding floor of the residual is reached.
+      if (sweep > 1 && rho > 0.5) {
+        conv = rel_update <= 1e-10;
+        break;
+      }
     }
   }
   s.krylov_iters = info.m;
@@ -610,7 +654,7 @@ pd_status solve_mixed(pd_plan *p, const double *G, double *U, pd_stats &s) {
   s.breakdown = info.breakdown;
   s.beta = info.beta;
   s.krylov_rel_resnorm = info.rel_res;
-  s.rel_update = rel_update;
+  s.rel_update = sweeps > 1 ? rel_update : 0.0;
   return conv ? PD_OK : fail(PD_ERR_NOT_CONVERGED, "refinement did not reach refine_tol in %d sweeps", sweeps);
 }
 
@@ -760,7 +804,7 @@ pd_status paradiag_solve(pd_plan *p, const double *G, double *U, pd_stats *stats
   const int64_t l0 = p->ctx.launches;
   CK(cudaEventRecord(p->ev0, p->ctx.stream));
   pd_stats s{};
-  st = p->precision == PD_FP64 ? solve_fp64(p, G, U, s) : solve_mixed(p, G, U, s);
+  st = p->precision == PD_FP64 ? solve_refined<double>(p, G, U, s) : solve_refined<float>(p, G, U, s);
   if (st == PD_ERR_CUDA) return st;
   CK(cudaEventRecord(p->ev1, p->ctx.stream));
   CK(cudaEventSynchronize(p->ev1));
@@ -863,7 +907,7 @@ pd_status paradiag_dst_y(pd_plan *p, const double *X, double *Y) {
 pd_status paradiag_last_vectors(pd_plan *p, double *b, double *x) {
   pd_status st = check_plan(p);
   if (st != PD_OK) return st;
-  const double *src[2] = {p->b, p->x};
+  const double *src[2] = {p->b0, p->x0};
   double *dst[2] = {b, x};
   for (int i = 0; i < 2; ++i) {
     if (!dst[i]) continue;
