@@ -332,7 +332,11 @@ def cpu_baseline(P, name, gpu_results):
         R.be_solve(P)
         reps += 1
     total = time.perf_counter() - t0
-    parity = {k: R.rel_err(v, Uref) for k, v in gpu_results.items()}
+    # parity against the oracle with one extended-precision correction (the plain
+    # FP64 oracle is itself ~4e-13 off on this workload)
+    Uref2 = R.be_solve_refined(P)
+    parity = {k: R.rel_err(v, Uref2) for k, v in gpu_results.items()}
+    parity["plain_oracle"] = {k: R.rel_err(v, Uref) for k, v in gpu_results.items()}
     parity["tolerance"] = {"mixed": 1e-10, "fp64": 1e-12}
     parity["pass"] = bool(parity["mixed"] <= 1e-10 and parity["fp64"] <= 1e-12)
     base = {"value": P.unknowns * reps / total, "unit": UNIT, "cores": 1, "kind": "oracle",

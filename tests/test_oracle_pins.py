@@ -314,3 +314,41 @@ def test_algorithm1_equals_sequential(name, size):
     U, info = R.paradiag(P, eps=1e-13, maxit=60)
     assert R.rel_err(U, R.be_solve(P)) < 1e-12
     assert info["U_imag"] < 1e-12 * np.linalg.norm(U)
+
+
+# ----------------------------------------------------------------------------
+# The refined reference (one correction on an extended-precision residual)
+# ----------------------------------------------------------------------------
+
+
+def test_refined_oracle_closed_form():
+    """With the extended residual the sine-mode closed form is met to ~1e-15."""
+    n, nt = 255, 64
+    P = W.heat1d_sine_modes(n, nt, 1.0, seed=5)
+    h = 1.0 / (n + 1)
+    x = h * np.arange(1, n + 1)
+    j = np.arange(1, nt + 1)[:, None]
+    Uc = np.zeros((nt, n))
+    for k, a in zip(P.extra["modes"], P.extra["amps"]):
+        Uc += a * (1.0 + P.tau * _sine_eig(k, h)) ** (-j) * np.sin(k * np.pi * x)[None, :]
+    assert R.rel_err(R.be_solve_refined(P), Uc) < 2e-15
+
+
+@pytest.mark.parametrize("P", [W.heat2d_smooth(63, 64, 0.1, seed=1), W.config2(), W.advdiff1d_pulse(511, 256, seed=2)],
+                         ids=lambda p: p.name)
+def test_refined_oracle_converges(P):
+    """A second correction on the extended residual is negligible next to the first
+    (the refinement has converged to working precision)."""
+    U = R.be_solve(P)
+    d1 = R.be_solve(P, G=R.residual_extended(P, U))
+    d2 = R.be_solve(P, G=R.residual_extended(P, U + d1))
+    n = np.linalg.norm(U)
+    assert np.linalg.norm(d1) / n < 1e-10
+    assert np.linalg.norm(d2) / n < 1e-15
+    assert np.linalg.norm(d2) <= 0.05 * np.linalg.norm(d1) + 1e-16 * n
+
+
+def test_extended_residual_matches_float64_residual():
+    P = W.heat2d_smooth(7, 8, 0.1, seed=2)
+    U = np.random.default_rng(1).standard_normal(P.G.shape)
+    assert np.allclose(R.residual_extended(P, U), P.G - R.aao_apply(P, U), rtol=1e-13, atol=1e-13)
