@@ -176,6 +176,32 @@ pd_status paradiag_dst_y(pd_plan *plan, const double *X_dev, double *Y_dev);
  * n_bar, device.  Either may be NULL. */
 pd_status paradiag_last_vectors(pd_plan *plan, double *b_dev, double *x_dev);
 
+/* ---- Allocation-free variant ---------------------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers that cannot
+ * call cudaMalloc when they need this step (an arena or pool that owns all device
+ * memory, a real-time loop where an allocation would stall, a host application that
+ * forbids allocation after start-up).  It computes what paradiag_shifted_solve computes
+ * with b requested (the first parallel-in-time loop of Algorithm 1 and b of eq. 7), in
+ * FP64, without a plan and without allocating anything: its scratch is a file-scope
+ * __device__ array of PD_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds
+ * until the process exits.
+ *   nt      time steps l (power of two, 1 <= nt <= 8192), n rows of K (1 <= n <= 4096);
+ *           larger sizes return PD_ERR_UNSUPPORTED with a message in paradiag_last_error().
+ *   tau     time step; k_lo, k_diag, k_up: device, length n, the tridiagonal K
+ *           (k_lo[0], k_up[n-1] ignored).
+ *   R       device, (nt/2+1, n) complex128 right-hand sides (half spectrum of real data).
+ *   Y       device, (nt/2+1, n) complex128 solutions, or NULL to skip the store.
+ *   b       device, length n float64: b = sum_{i=0}^{l-1} gamma_i Y_i.
+ *   stream  cudaStream_t the work is enqueued on; the call returns without waiting.
+ * The first call on each device looks up the device address of the scratch array
+ * (cudaGetSymbolAddress, with that device current); make that first call before any
+ * stream capture.  All calls share the one array and each rewrites every word it reads,
+ * so calls that overlap on the GPU race: serialise them. */
+#define PD_NOALLOC_SCRATCH_BYTES (4u * 1024u * 1024u)
+pd_status paradiag_smw_rhs_noalloc(int64_t nt, int64_t n, double tau, const double *k_lo,
+                                   const double *k_diag, const double *k_up, const void *R, void *Y,
+                                   double *b, void *stream);
+
 /* ---- Kernel timing (tracing) ------------------------------------------------------ */
 
 typedef struct pd_kernel_time {

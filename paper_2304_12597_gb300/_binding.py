@@ -109,6 +109,9 @@ SIGNATURES = {
     "paradiag_shifted_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "paradiag_dst_y": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "paradiag_last_vectors": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "paradiag_smw_rhs_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p,
+                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_void_p, ctypes.c_void_p]),
     "paradiag_set_timing": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "paradiag_kernel_times": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(PdKernelTime), ctypes.c_int,
                                              ctypes.POINTER(ctypes.c_int)]),
@@ -195,6 +198,14 @@ def paradiag_dst_y(plan: int, X_ptr: int, Y_ptr: int) -> None:
 
 def paradiag_last_vectors(plan: int, b_ptr, x_ptr) -> None:
     check("paradiag_last_vectors", load().paradiag_last_vectors(plan, b_ptr, x_ptr))
+
+
+def paradiag_smw_rhs_noalloc(nt: int, n: int, tau: float, k_lo_ptr: int, k_diag_ptr: int, k_up_ptr: int,
+                             R_ptr: int, Y_ptr, b_ptr: int, stream_ptr) -> None:
+    """Allocation-free first parallel-in-time loop and b (eq. 7); see include/paradiag.h.
+    For callers that cannot allocate device memory: scratch is a static device array."""
+    check("paradiag_smw_rhs_noalloc", load().paradiag_smw_rhs_noalloc(nt, n, tau, k_lo_ptr, k_diag_ptr, k_up_ptr,
+                                                                      R_ptr, Y_ptr, b_ptr, stream_ptr))
 
 
 def paradiag_set_timing(plan: int, enable: bool) -> None:

@@ -48,6 +48,8 @@ struct Ctx {
 
 int sm_count();
 size_t smem_optin();
+// Sets the thread-local message returned by paradiag_last_error().
+void set_last_error(const char *msg);
 
 // ---- time FFT / DST (fft.cu) ----------------------------------------------------
 // Forward DFT along time of real (n, ncols) rows -> half spectrum (n/2+1, ncols).

@@ -56,6 +56,8 @@ struct Arena {
 
 namespace pd {
 
+void set_last_error(const char *msg) { g_err = msg ? msg : ""; }
+
 int sm_count() {
   static int n = 0;
   if (n == 0) {
