@@ -231,8 +231,10 @@ def run_ours(args):
     barrier(world)
     torch.cuda.synchronize()
     sampler = ClockSampler(gpu_index(local)) if rank == 0 else None
+    torch.cuda.nvtx.range_push("timed_mixed")
     ts, launches, st_mixed = time_steps(mixed, G, U, args.steps, stream, flush, torch)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     clocks = sampler.stop() if sampler else None
     barrier(world)
     total_ms = max_over_ranks(sum(ts), world, device)
@@ -279,7 +281,10 @@ def run_ours(args):
     for _ in range(3):
         fp.solve(G, U)
     nfp = max(3, min(args.steps, 50))
+    torch.cuda.nvtx.range_push("timed_fp64")
     ts64, _, st64 = time_steps(fp, G, U, nfp, stream, flush, torch)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     fp64_ms = max_over_ranks(sum(ts64), world, device)
     U_fp64 = U.cpu().numpy()
     fp.close()
@@ -300,7 +305,10 @@ def run_ours(args):
                      "krylov_iters": st64["krylov_iters"]},
         "mixed_over_fp64": value / fp64_value,
         "solver": {"refine_sweeps": st_mixed["refine_sweeps"], "krylov_iters_total": st_mixed["krylov_iters_total"],
-                   "pint_loops": st_mixed["pint_loops"], "launches_per_step": launches / args.steps},
+                   "pint_loops": st_mixed["pint_loops"], "launches_per_step": launches / args.steps,
+                   "sweep_krylov_iters": st_mixed["sweep_krylov_iters"],
+                   "sweep_rel_update": [float(f"{v:.3e}") for v in st_mixed["sweep_rel_update"]],
+                   "sweep_krylov_rel_resnorm": [float(f"{v:.3e}") for v in st_mixed["sweep_krylov_rel_resnorm"]]},
         "roofline": roofline,
         "kernels": kernel_table,
         "clocks": clocks,

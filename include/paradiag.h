@@ -76,9 +76,12 @@ typedef struct pd_desc {
   int32_t precision;     /* pd_precision */
   int32_t maxit;         /* Algorithm 2 iteration limit, 1 <= maxit <= 32 (0 = 32) */
   double eps_krylov;     /* Algorithm 2 tolerance epsilon (stop when ||r|| <= eps * ||b||);
-                            0 = 1e-13 for PD_FP64, 1e-6 for the inner solves of PD_MIXED.
-                            Both also stop when ||r|| stalls (no halving over 1 iteration in
-                            PD_MIXED, over 3 in PD_FP64) */
+                            0 = 1e-13 for PD_FP64, 1e-5 for the first solve of PD_MIXED
+                            (its refinement sweeps use max(eps_krylov, 1e-3)).
+                            Both also stop when ||r|| stalls near the precision floor (no
+                            halving over 1 iteration in PD_MIXED once ||r|| <= 1e-3 ||b||, and
+                            at any level in its refinement sweeps; over 3 iterations in PD_FP64
+                            once ||r|| <= 1e-6 ||b||) */
   int32_t q;             /* residual check period of Algorithm 2; only q = 1 is built */
   int32_t max_refine;    /* refinement sweeps after the first solve (0 = 8).  PD_MIXED always
                             refines; PD_FP64 refines only when Algorithm 2 stopped short of
@@ -86,7 +89,7 @@ typedef struct pd_desc {
                             an inexact x_m is exactly -r_m in the first time step */
   double refine_tol;     /* refinement stops when the predicted remaining relative error,
                             (||delta_s|| / ||delta_{s-1}||) * ||delta_s|| / ||U||, is <= refine_tol
-                            (0 = 1e-14 for PD_FP64, 1e-12 for PD_MIXED) */
+                            (0 = 1e-14 for PD_FP64, 1e-11 for PD_MIXED) */
   double alpha;          /* alpha of Sec. 4; only 1.0 (or 0 = 1.0) is built */
   void *stream;          /* cudaStream_t every launch is ordered on (NULL = legacy stream) */
   int32_t host_io;       /* nonzero: reserve device staging for paradiag_solve_host */
@@ -106,6 +109,10 @@ typedef struct pd_stats {
   double krylov_rel_resnorm;   /* eq. (13) residual / ||b|| at exit of the last run */
   double rel_update;           /* ||delta||_F / ||U||_F of the last refinement sweep (0 if none) */
   double ms_total;             /* wall time of the solve measured with CUDA events */
+  /* per solve (first solve, then each refinement sweep; first 16): */
+  int32_t sweep_krylov_iters[16];        /* m of Algorithm 2 */
+  double sweep_krylov_rel_resnorm[16];   /* eq. (13) residual / ||b|| at exit */
+  double sweep_rel_update[16];           /* ||delta_s||_F / ||delta_0||_F */
 } pd_stats;
 
 typedef struct pd_plan pd_plan;

@@ -70,10 +70,18 @@ class PdStats(ctypes.Structure):
         ("krylov_rel_resnorm", ctypes.c_double),
         ("rel_update", ctypes.c_double),
         ("ms_total", ctypes.c_double),
+        ("sweep_krylov_iters", ctypes.c_int32 * 16),
+        ("sweep_krylov_rel_resnorm", ctypes.c_double * 16),
+        ("sweep_rel_update", ctypes.c_double * 16),
     ]
 
     def as_dict(self):
-        return {name: getattr(self, name) for name, _ in self._fields_}
+        d = {}
+        n = self.refine_sweeps
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            d[name] = list(v)[: min(n, 16)] if name.startswith("sweep_") else v
+        return d
 
 
 class PdKernelTime(ctypes.Structure):

@@ -84,7 +84,7 @@ __device__ void cta_axpy(int n, int m, const double *__restrict__ V, double *x, 
 
 // beta = ||b||, V[0] = b / beta; resets scal/flags.
 __global__ void __launch_bounds__(kBlas) k_init_v0_coop(const double *__restrict__ b, int n, double *part, int ld,
-                                                        double *V, double *scal, int *flags) {
+                                                        double *V, float *Vf, double *scal, int *flags) {
   cg::grid_group grid = cg::this_grid();
   __shared__ double red[32];
   __shared__ double c[34];
@@ -97,7 +97,10 @@ __global__ void __launch_bounds__(kBlas) k_init_v0_coop(const double *__restrict
   const double beta = sqrt(c[0]);
   const bool zero = !(beta > 0.0);
   const double ib = zero ? 0.0 : 1.0 / beta;
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) V[j] = b[j] * ib;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    V[j] = b[j] * ib;
+    if (Vf) Vf[j] = (float)V[j];
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     scal[0] = beta;
     scal[1] = 0.0;
@@ -113,9 +116,9 @@ __global__ void __launch_bounds__(kBlas) k_init_v0_coop(const double *__restrict
 // t = ||w||; v_m = w / t, or breakdown when t <= 1e-14 ||K v_{m-1}||.
 __global__ void __launch_bounds__(kBlas) k_arnoldi_coop(int n, int m, const double *__restrict__ klo,
                                                         const double *__restrict__ kdiag,
-                                                        const double *__restrict__ kup, double *V, double *w,
-                                                        double *T, int ldT, double *part, int ld, double *scal,
-                                                        int *flags) {
+                                                        const double *__restrict__ kup, double *V, float *Vf,
+                                                        double *w, double *T, int ldT, double *part, int ld,
+                                                        double *scal, int *flags) {
   cg::grid_group grid = cg::this_grid();
   __shared__ double red[32];
   __shared__ double c[34];
@@ -150,7 +153,11 @@ __global__ void __launch_bounds__(kBlas) k_arnoldi_coop(int n, int m, const doub
   const bool bd = !(t > 1e-14 * knorm);
   const double it = bd ? 0.0 : 1.0 / t;
   double *vm = V + (int64_t)m * n;
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) vm[j] = w[j] * it;
+  float *vmf = Vf ? Vf + (int64_t)m * n : nullptr;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    vm[j] = w[j] * it;
+    if (vmf) vmf[j] = (float)vm[j];
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     T[(int64_t)m * ldT + (m - 1)] = bd ? 0.0 : t;
     scal[1] = bd ? 0.0 : t;
@@ -317,10 +324,15 @@ __global__ void k_capacitance_solve(int nf, int m, int nparts, const double *msy
   cpx<double> *X = H + m * m;
   cpx<double> *fcol = X + m * m;
   double *ys = reinterpret_cast<double *>(fcol + m);
-  for (int i = threadIdx.x; i < m * m; i += blockDim.x) {
-    double s = ((i / m) == (i % m)) ? 1.0 : 0.0;
-    for (int p = 0; p < nparts; ++p) s += msys_part[(int64_t)p * m * m + i];
-    H[i] = mk<double>(s, 0.0);
+  // M = I + sum of the per-CTA partials: one warp per entry, lanes stride over CTAs
+  {
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int i = wid; i < m * m; i += nw) {
+      double s = 0.0;
+      for (int p = lane; p < nparts; p += 32) s += msys_part[(int64_t)p * m * m + i];
+      s = warp_sum(s);
+      if (lane == 0) H[i] = mk<double>(s + (((i / m) == (i % m)) ? 1.0 : 0.0), 0.0);
+    }
   }
   __syncthreads();
   if (threadIdx.x < 32) warp_gj_inverse(H, X, fcol, m);
@@ -343,8 +355,8 @@ __global__ void k_capacitance_solve(int nf, int m, int nparts, const double *msy
   }
 }
 
-// x = sum_q y_q V[q]
-__global__ void k_xm(int n, int m, const double *__restrict__ V, const double *__restrict__ y, double *x) {
+// x = sum_q y_q V[q] (and its binary32 copy xf when requested)
+__global__ void k_xm(int n, int m, const double *__restrict__ V, const double *__restrict__ y, double *x, float *xf) {
   __shared__ double ys[33];
   if (threadIdx.x < m) ys[threadIdx.x] = y[threadIdx.x];
   __syncthreads();
@@ -352,53 +364,44 @@ __global__ void k_xm(int n, int m, const double *__restrict__ V, const double *_
     double s = 0.0;
     for (int q = 0; q < m; ++q) s += ys[q] * V[(int64_t)q * n + j];
     x[j] = s;
+    if (xf) xf[j] = (float)s;
   }
 }
 
+// *dst = sum of part[0..nparts) (one warp, fixed order)
 __global__ void k_sumsq_final(const double *part, int nparts, double *dst) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double s = 0.0;
-    for (int i = 0; i < nparts; ++i) s += part[i];
-    *dst = s;
-  }
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += 32) s += part[i];
+  s = warp_sum(s);
+  if (threadIdx.x == 0) *dst = s;
 }
 
 // ---- FP64 all-at-once residual ---------------------------------------------------
-template <typename Tout>
+template <typename Tout, bool TWO_D>
 __global__ void k_residual(const double *__restrict__ G, const double *__restrict__ U, Tout *__restrict__ R,
-                           int64_t nt, int64_t ny, int64_t nx, double tau, const double *__restrict__ xlo,
+                           int nb, int nx, double tau, const double *__restrict__ xlo,
                            const double *__restrict__ xdiag, const double *__restrict__ xup,
                            const double *__restrict__ ylo, const double *__restrict__ ydiag,
-                           const double *__restrict__ yup, double *norm_part) {
-  __shared__ double red[32];
-  const int64_t nb = ny * nx;
-  const int64_t total = nt * nb;
-  double ss = 0.0;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t t = idx / nb;
-    const int64_t j = idx - t * nb;
-    const int64_t iy = j / nx;
-    const int64_t ix = j - iy * nx;
-    const double *u = U + t * nb;
-    const double uj = u[j];
-    double ku = xdiag[ix] * uj;
-    if (ix > 0) ku += xlo[ix] * u[j - 1];
-    if (ix + 1 < nx) ku += xup[ix] * u[j + 1];
-    if (ylo) {
-      ku += ydiag[iy] * uj;
-      if (iy > 0) ku += ylo[iy] * u[j - nx];
-      if (iy + 1 < ny) ku += yup[iy] * u[j + nx];
-    }
-    double r = G[idx] - uj - tau * ku;
-    if (t > 0) r += U[idx - nb];
-    const Tout ro = (Tout)r;
-    R[idx] = ro;
-    const float rf = (float)ro;
-    ss += (double)(rf * rf);
+                           const double *__restrict__ yup, int ny) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;  // spatial index
+  const int64_t t = blockIdx.y;                         // time step
+  if (j >= nb) return;
+  const double *u = U + t * nb;
+  const int iy = TWO_D ? j / nx : 0;
+  const int ix = TWO_D ? j - iy * nx : j;
+  const double uj = u[j];
+  double ku = xdiag[ix] * uj;
+  if (ix > 0) ku += xlo[ix] * u[j - 1];
+  if (ix + 1 < nx) ku += xup[ix] * u[j + 1];
+  if (TWO_D) {
+    ku += ydiag[iy] * uj;
+    if (iy > 0) ku += ylo[iy] * u[j - nx];
+    if (iy + 1 < ny) ku += yup[iy] * u[j + nx];
   }
-  double s = block_sum(ss, red);
-  if (threadIdx.x == 0 && norm_part) norm_part[blockIdx.x] = s;
+  const int64_t idx = t * nb + j;
+  double r = G[idx] - uj - tau * ku;
+  if (t > 0) r += U[idx - nb];
+  R[idx] = (Tout)r;
 }
 
 // ---- launchers -------------------------------------------------------------------
@@ -411,8 +414,9 @@ void launch_vec_norm_init(Ctx &c, KrylovBufs &k, const double *b) {
   const int ld = k.maxit + 2;
   int n = k.n;
   double *part = k.part, *V = k.V, *scal = k.scal;
+  float *Vf = k.Vf;
   int *flags = k.flags;
-  void *args[] = {(void *)&b, &n, &part, (void *)&ld, &V, &scal, &flags};
+  void *args[] = {(void *)&b, &n, &part, (void *)&ld, &V, &Vf, &scal, &flags};
   coop_launch(c, "krylov_blas1", (double)k.n * 16, (const void *)k_init_v0_coop, k.grid, args);
 }
 
@@ -422,9 +426,10 @@ void launch_arnoldi(Ctx &c, KrylovBufs &k, int m) {
   int n = k.n, ldT = k.maxit;
   const double *klo = k.klo, *kdiag = k.kdiag, *kup = k.kup;
   double *V = k.V, *w = k.w, *T = k.T, *part = k.part, *scal = k.scal;
+  float *Vf = k.Vf;
   int *flags = k.flags;
-  void *args[] = {&n, &m, (void *)&klo, (void *)&kdiag, (void *)&kup, &V, &w, &T, &ldT, &part, (void *)&ld, &scal,
-                  &flags};
+  void *args[] = {&n, &m, (void *)&klo, (void *)&kdiag, (void *)&kup, &V, &Vf, &w, &T, &ldT, &part, (void *)&ld,
+                  &scal, &flags};
   coop_launch(c, "krylov_blas1", (double)k.n * 8.0 * (3 * m + 4), (const void *)k_arnoldi_coop, k.grid, args);
 }
 
@@ -455,9 +460,9 @@ void launch_project_resnorm(Ctx &c, KrylovBufs &k, int m, const double *z, doubl
   coop_launch(c, "krylov_blas1", (double)k.n * 8.0 * (3 * m + 3), (const void *)k_project_coop, k.grid, args);
 }
 
-void launch_xm(Ctx &c, KrylovBufs &k, int m, const double *y, double *x) {
+void launch_xm(Ctx &c, KrylovBufs &k, int m, const double *y, double *x, float *xf) {
   c.launch("krylov_blas1", (double)k.n * 8.0 * (m + 1),
-           [&] { k_xm<<<k.grid, kBlas, 0, c.stream>>>(k.n, m, k.V, y, x); });
+           [&] { k_xm<<<k.grid, kBlas, 0, c.stream>>>(k.n, m, k.V, y, x, xf); });
 }
 
 void launch_sumsq(Ctx &c, const double *part, int nparts, double *dst) {
@@ -468,13 +473,18 @@ template <typename Tout>
 void launch_residual(Ctx &c, const double *G, const double *U, Tout *R, int64_t nt, int64_t ny, int64_t nx,
                      double tau, const double *xlo, const double *xdiag, const double *xup, const double *ylo,
                      const double *ydiag, const double *yup, double *norm_part, int *nparts) {
-  const int64_t total = nt * ny * nx;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 8 * (int64_t)sm_count()));
-  if (nparts) *nparts = grid;
-  c.launch(sizeof(Tout) == 8 ? "residual_f64_to_f64" : "residual_f64_to_f32", (double)total * (8 + 8 + sizeof(Tout)),
-           [&] {
-             k_residual<Tout><<<grid, 256, 0, c.stream>>>(G, U, R, nt, ny, nx, tau, xlo, xdiag, xup, ylo, ydiag, yup,
-                                                          norm_part);
+  (void)norm_part;
+  const int nb = (int)(ny * nx);
+  const dim3 grid((unsigned)((nb + 255) / 256), (unsigned)nt);
+  if (nparts) *nparts = 0;
+  c.launch(sizeof(Tout) == 8 ? "residual_f64_to_f64" : "residual_f64_to_f32",
+           (double)nt * nb * (8 + 8 + sizeof(Tout)), [&] {
+             if (ylo)
+               k_residual<Tout, true><<<grid, 256, 0, c.stream>>>(G, U, R, nb, (int)nx, tau, xlo, xdiag, xup, ylo,
+                                                                  ydiag, yup, (int)ny);
+             else
+               k_residual<Tout, false><<<grid, 256, 0, c.stream>>>(G, U, R, nb, (int)nx, tau, xlo, xdiag, xup, ylo,
+                                                                   ydiag, yup, (int)ny);
            });
 }
 

@@ -86,13 +86,14 @@ struct PintArgs {
   const T *tlo, *tdiag, *tup;  // tau * K (block-decoupled), length nblk*blen
   const cpx<T> *R;         // spectrum right-hand sides (nf, ldr) or null
   int64_t ldr;
-  const double *rvec;      // real vector: the right-hand side when R is null,
+  const T *rvec;           // real vector: the right-hand side when R is null,
                            // subtracted from every R[k] otherwise (may be null)
   cpx<T> *Y;               // solution store (nf, ldy) or null
   int64_t ldy;
-  const double2 *omega;    // accumulation weights: acc += Re(omega_k y_k), or null
+  const double2 *omega;    // accumulation weights: acc += Re(omega_k y_k) (summed in T per
+                           // team, over that team's few frequencies), or null
   double *acc_part;        // (teams, blen) partial sums when omega != null
-  const double *V;         // Krylov basis rows (ldv stride) for dots, or null
+  const T *V;              // Krylov basis rows in the compute type (ldv stride) for dots, or null
   int64_t ldv;
   int mdots;               // number of basis vectors dotted with y_k
   double2 *gpart;          // (nf, nblk, mdots) dot products y_k . V[q]
@@ -110,6 +111,7 @@ struct KrylovBufs {
   int maxit;
   const double *klo, *kdiag, *kup;  // K (block-decoupled tridiagonal), unscaled
   double *V;          // (maxit+1, n)
+  float *Vf;          // binary32 copy of V for the mixed-precision shifted solves, or null
   double *T;          // (maxit+1, maxit) upper Hessenberg, row-major T[q*maxit + c]
   double *w;          // work vector (n)
   double *part;       // per-CTA partials (grid, maxit+2)
@@ -123,7 +125,7 @@ void launch_capacitance(Ctx &c, KrylovBufs &k, int m, int nf, double tau, const 
                         const double2 *wg, const double2 *gpart, int nblk, double *msys_part,
                         int k5_grid, double2 *srow, double2 *omega, double *y);
 void launch_project_resnorm(Ctx &c, KrylovBufs &k, int m, const double *z, double tau);
-void launch_xm(Ctx &c, KrylovBufs &k, int m, const double *y, double *x);
+void launch_xm(Ctx &c, KrylovBufs &k, int m, const double *y, double *x, float *xf);
 void launch_sumsq(Ctx &c, const double *part, int nparts, double *dst);
 // FP64 all-at-once residual R = G - [(I + tau K) U - U Sigma_1^T], stored as Tout
 // (float for the mixed path, double for the FP64 path).  1D: K tridiagonal

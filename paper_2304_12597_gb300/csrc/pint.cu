@@ -35,7 +35,7 @@ struct TeamSmem {
     size_t b = 0;
     b += (size_t)P * (M + 1) * sizeof(cpx<T>);   // rhs / dd, padded one slot per chunk
     b += (size_t)2 * P * 5 * sizeof(cpx<T>);     // PCR rows a, b, c, d and 1/b
-    b += (size_t)P * M * sizeof(double);          // accumulators
+    b += ((size_t)P * M * sizeof(T) + 15) & ~(size_t)15;  // per-team accumulators (compute type)
     b += (size_t)(P / 32) * std::max(mdots, 1) * sizeof(double2);  // dot reductions
     return (b + 15) & ~(size_t)15;
   }
@@ -78,13 +78,14 @@ __global__ void __launch_bounds__(512) k_pint(PintGeom g, PintArgs<T> a, size_t 
   cpx<T> *pc = pb + N;
   cpx<T> *pd = pc + N;
   cpx<T> *pib = pd + N;
-  double *acc = reinterpret_cast<double *>(pib + N);
-  double2 *red = reinterpret_cast<double2 *>(acc + (size_t)P * M);
+  T *acc = reinterpret_cast<T *>(pib + N);
+  double2 *red = reinterpret_cast<double2 *>(reinterpret_cast<unsigned char *>(acc) +
+                                             (((size_t)P * M * sizeof(T) + 15) & ~(size_t)15));
 
   const bool do_acc = a.omega != nullptr;
   if (do_acc) {
 #pragma unroll
-    for (int i = 0; i < M; ++i) acc[i * P + t] = 0.0;
+    for (int i = 0; i < M; ++i) acc[i * P + t] = T(0);
   }
   cpx<T> *my = dd + (size_t)t * (M + 1);
   const int e0 = t * M;
@@ -99,9 +100,9 @@ __global__ void __launch_bounds__(512) k_pint(PintGeom g, PintArgs<T> a, size_t 
         const int64_t j = off + e;
         if (a.R) {
           v = a.R[(int64_t)k * a.ldr + j];
-          if (a.rvec) v.x -= (T)a.rvec[j];
+          if (a.rvec) v.x -= a.rvec[j];
         } else {
-          v.x = (T)a.rvec[j];
+          v.x = a.rvec[j];
         }
       }
       dd[e + e / M] = v;
@@ -205,9 +206,10 @@ __global__ void __launch_bounds__(512) k_pint(PintGeom g, PintArgs<T> a, size_t 
     for (int i = 1; i < M - 1; ++i) my[i] = fnms(fnms(my[i], aa[i], xf), cc[i], xl);
     my[M - 1] = xl;
     if (do_acc) {
-      const double2 om = a.omega[k];
+      const double2 omd = a.omega[k];
+      const T ox = (T)omd.x, oy = (T)omd.y;
 #pragma unroll
-      for (int i = 0; i < M; ++i) acc[i * P + t] += om.x * (double)my[i].x - om.y * (double)my[i].y;
+      for (int i = 0; i < M; ++i) acc[i * P + t] += ox * my[i].x - oy * my[i].y;
     }
     team_sync(P, tic);
 
@@ -219,16 +221,16 @@ __global__ void __launch_bounds__(512) k_pint(PintGeom g, PintArgs<T> a, size_t 
     if (a.V && a.mdots > 0) {
       const int nw = P >> 5, w = t >> 5, l = t & 31;
       for (int q = 0; q < a.mdots; ++q) {
-        double sx = 0.0, sy = 0.0;
-        const double *vq = a.V + (int64_t)q * a.ldv + off;
+        T px = T(0), py = T(0);
+        const T *vq = a.V + (int64_t)q * a.ldv + off;
         for (int e = t; e < blen; e += P) {
           const cpx<T> y = dd[e + e / M];
-          const double v = vq[e];
-          sx += v * (double)y.x;
-          sy += v * (double)y.y;
+          const T v = vq[e];
+          px += v * y.x;
+          py += v * y.y;
         }
-        sx = warp_sum(sx);
-        sy = warp_sum(sy);
+        double sx = warp_sum((double)px);
+        double sy = warp_sum((double)py);
         if (l == 0) red[w * a.mdots + q] = make_double2(sx, sy);
       }
       team_sync(P, tic);
@@ -247,7 +249,7 @@ __global__ void __launch_bounds__(512) k_pint(PintGeom g, PintArgs<T> a, size_t 
 #pragma unroll
     for (int i = 0; i < M; ++i) {
       const int e = e0 + i;
-      if (e < blen) a.acc_part[(int64_t)team * blen + e] = acc[i * P + t];
+      if (e < blen) a.acc_part[(int64_t)team * blen + e] = (double)acc[i * P + t];
     }
   }
 }

@@ -47,14 +47,15 @@ def test_struct_layouts_match_header(B, tmp_path):
     prog = tmp_path / "sz.c"
     prog.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "paradiag.h"\n'
-        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu\\n\", sizeof(pd_desc), sizeof(pd_stats),"
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(pd_desc), sizeof(pd_stats),"
         " sizeof(pd_kernel_time), offsetof(pd_desc, stream), offsetof(pd_desc, precision),"
-        " offsetof(pd_stats, kernel_launches));return 0;}\n")
+        " offsetof(pd_stats, kernel_launches), offsetof(pd_stats, sweep_rel_update));return 0;}\n")
     exe = tmp_path / "sz"
     subprocess.check_call(["gcc", "-I", os.path.dirname(HEADER), str(prog), "-o", str(exe)])
     vals = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     assert vals == [ctypes.sizeof(B.PdDesc), ctypes.sizeof(B.PdStats), ctypes.sizeof(B.PdKernelTime),
-                    B.PdDesc.stream.offset, B.PdDesc.precision.offset, B.PdStats.kernel_launches.offset]
+                    B.PdDesc.stream.offset, B.PdDesc.precision.offset, B.PdStats.kernel_launches.offset,
+                    B.PdStats.sweep_rel_update.offset]
 
 
 def _desc(B, **kw):
