@@ -93,7 +93,9 @@ typedef struct pd_desc {
   double alpha;          /* alpha of Sec. 4; only 1.0 (or 0 = 1.0) is built */
   void *stream;          /* cudaStream_t every launch is ordered on (NULL = legacy stream) */
   int32_t host_io;       /* nonzero: reserve device staging for paradiag_solve_host */
-  int32_t reserved;
+  int32_t no_graph;      /* nonzero: drive the Algorithm-2 and refinement loops from the host
+                            instead of running each solve as one CUDA graph with device-side
+                            conditionals (also the behaviour while kernel timing is enabled) */
 } pd_desc;
 
 /* Statistics of the last paradiag_solve / paradiag_solve_host. */
@@ -104,6 +106,7 @@ typedef struct pd_stats {
   int32_t shifted_sweeps;      /* passes over all l/2+1 shifted systems actually executed */
   int32_t refine_sweeps;       /* solves performed (first solve + refinement sweeps) */
   int32_t breakdown;           /* 1 if Algorithm 2 met an invariant Krylov space */
+  int32_t graph;               /* 1 if the solve ran as one CUDA-graph launch */
   int64_t kernel_launches;     /* this library's kernel launches during the solve */
   double beta;                 /* ||b|| of the last Algorithm-2 run */
   double krylov_rel_resnorm;   /* eq. (13) residual / ||b|| at exit of the last run */
@@ -134,8 +137,10 @@ pd_status paradiag_plan(const pd_desc *desc, void *workspace, size_t workspace_b
  * iterative refinement around it (PD_MIXED).  G_dev: device, (nt, n_bar) float64,
  * read only.  U_dev: device, (nt, n_bar) float64, overwritten; must not alias G_dev.
  * Both 8-byte aligned.  stats (host, may be NULL) is filled on return.  The call
- * enqueues on the plan's stream and returns after its internal host synchronisations
- * (Krylov and refinement decisions), so U_dev is complete on return.
+ * enqueues on the plan's stream and returns after it has synchronised with it, so U_dev
+ * is complete on return.  By default the whole solve is one CUDA-graph launch whose
+ * loops are decided on the device (the graph is built on the first solve for a given
+ * (G_dev, U_dev) pair and reused while both pointers stay the same).
  * PD_ERR_NOT_CONVERGED: limits reached; U_dev holds the last iterate. */
 pd_status paradiag_solve(pd_plan *plan, const double *G_dev, double *U_dev, pd_stats *stats);
 

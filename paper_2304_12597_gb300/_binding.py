@@ -53,7 +53,7 @@ class PdDesc(ctypes.Structure):
         ("alpha", ctypes.c_double),
         ("stream", ctypes.c_void_p),
         ("host_io", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("no_graph", ctypes.c_int32),
     ]
 
 
@@ -65,6 +65,7 @@ class PdStats(ctypes.Structure):
         ("shifted_sweeps", ctypes.c_int32),
         ("refine_sweeps", ctypes.c_int32),
         ("breakdown", ctypes.c_int32),
+        ("graph", ctypes.c_int32),
         ("kernel_launches", ctypes.c_int64),
         ("beta", ctypes.c_double),
         ("krylov_rel_resnorm", ctypes.c_double),

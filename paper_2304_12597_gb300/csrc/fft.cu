@@ -68,9 +68,9 @@ __device__ void fft_smem(cpx<T> *buf, int n, int logn, int nseries, const cpx<T>
   }
 }
 
-template <typename T, typename Tin>
+template <typename T, typename Tin, int TX>
 __global__ void __launch_bounds__(256) k_fft_r2c(const Tin *__restrict__ X, int64_t ldx, int64_t ncols,
-                                                 int n, int logn, int TX, const cpx<T> *__restrict__ tw,
+                                                 int n, int logn, const cpx<T> *__restrict__ tw,
                                                  cpx<T> *__restrict__ S, int64_t lds) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cpx<T> *buf = reinterpret_cast<cpx<T> *>(smraw);
@@ -107,9 +107,9 @@ __global__ void __launch_bounds__(256) k_fft_r2c(const Tin *__restrict__ X, int6
 
 // Inverse: Z[k] = A[k] + i B[k] over the full spectrum (A[n-k] = conj A[k]);
 // z = IDFT(Z) = conj(DFT(conj Z)) / n; column 2p = Re z, column 2p+1 = Im z.
-template <typename T>
+template <typename T, int TX>
 __global__ void __launch_bounds__(256) k_fft_c2r(const cpx<T> *__restrict__ S, int64_t lds, int64_t ncols,
-                                                 int n, int logn, int TX, const cpx<T> *__restrict__ tw,
+                                                 int n, int logn, const cpx<T> *__restrict__ tw,
                                                  void *__restrict__ out, int64_t ldo, int mode,
                                                  double *__restrict__ norm_part) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -174,9 +174,9 @@ __global__ void __launch_bounds__(256) k_fft_c2r(const cpx<T> *__restrict__ S, i
 // Orthonormal DST-I along y via a length N = 2(ny+1) complex FFT of the odd
 // extension, two x-columns packed per series (a + i b):
 //   DST_l(a) = -Im Z[l] / 2,  DST_l(b) = Re Z[l] / 2,  scaled by sqrt(2/(ny+1)).
-template <typename Tin, typename Tout, typename T>
+template <typename Tin, typename Tout, typename T, int TX>
 __global__ void __launch_bounds__(256) k_dst_y(const Tin *__restrict__ X, Tout *__restrict__ Y, int64_t ny,
-                                               int64_t nx, int N, int logN, int TX,
+                                               int64_t nx, int N, int logN,
                                                const cpx<T> *__restrict__ tw, T scale, int mode) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cpx<T> *buf = reinterpret_cast<cpx<T> *>(smraw);
@@ -237,6 +237,15 @@ static int pick_tx(int n, int cap, int64_t ncols) {
   return tx;
 }
 
+// Instantiate the body for the tile width chosen at run time (kTX is a constant).
+#define PD_TX_DISPATCH(TX, ...)                        \
+  switch (TX) {                                        \
+    case 2: { constexpr int kTX = 2; __VA_ARGS__; } break;  \
+    case 4: { constexpr int kTX = 4; __VA_ARGS__; } break;  \
+    case 8: { constexpr int kTX = 8; __VA_ARGS__; } break;  \
+    default: { constexpr int kTX = 16; __VA_ARGS__; } break; \
+  }
+
 template <typename T, typename Tin>
 void launch_fft_r2c(Ctx &c, const Tin *X, int64_t ldx, int64_t ncols, int n, const cpx<T> *tw,
                     cpx<T> *S, int64_t lds) {
@@ -244,11 +253,13 @@ void launch_fft_r2c(Ctx &c, const Tin *X, int64_t ldx, int64_t ncols, int n, con
   const int TX = pick_tx<T>(n, sizeof(T) == 8 ? 8 : 16, ncols);
   const size_t smem = (size_t)(TX / 2) * n * sizeof(cpx<T>);
   const int grid = (int)((ncols + TX - 1) / TX);
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_fft_r2c<T, Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const double bytes = (double)n * ncols * sizeof(Tin) + (double)(n / 2 + 1) * ncols * sizeof(cpx<T>);
   c.launch(sizeof(T) == 8 ? "fft_r2c_f64" : "fft_r2c_f32", bytes, [&] {
-    k_fft_r2c<T, Tin><<<grid, 256, smem, c.stream>>>(X, ldx, ncols, n, logn, TX, tw, S, lds);
+    PD_TX_DISPATCH(TX, {
+      if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_fft_r2c<T, Tin, kTX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_fft_r2c<T, Tin, kTX><<<grid, 256, smem, c.stream>>>(X, ldx, ncols, n, logn, tw, S, lds);
+    })
   });
 }
 
@@ -259,13 +270,15 @@ void launch_fft_c2r(Ctx &c, const cpx<T> *S, int64_t lds, int64_t ncols, int n, 
   const int TX = pick_tx<T>(n, sizeof(T) == 8 ? 8 : 16, ncols);
   const size_t smem = (size_t)(TX / 2) * n * sizeof(cpx<T>);
   const int grid = (int)((ncols + TX - 1) / TX);
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_fft_c2r<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (nparts) *nparts = grid;
   const double obytes = (mode == 2) ? 4.0 : (mode == 1 ? 16.0 : 8.0);
   const double bytes = (double)(n / 2 + 1) * ncols * sizeof(cpx<T>) + (double)n * ncols * obytes;
   c.launch(sizeof(T) == 8 ? "fft_c2r_f64" : "fft_c2r_f32", bytes, [&] {
-    k_fft_c2r<T><<<grid, 256, smem, c.stream>>>(S, lds, ncols, n, logn, TX, tw, out, ldo, mode, norm_part);
+    PD_TX_DISPATCH(TX, {
+      if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_fft_c2r<T, kTX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_fft_c2r<T, kTX><<<grid, 256, smem, c.stream>>>(S, lds, ncols, n, logn, tw, out, ldo, mode, norm_part);
+    })
   });
 }
 
@@ -278,12 +291,14 @@ void launch_dst_y(Ctx &c, const Tin *X, Tout *Y, int64_t nt, int64_t ny, int64_t
   const size_t smem = (size_t)(TX / 2) * N * sizeof(cpx<T>);
   const int ntile = (int)((nx + TX - 1) / TX);
   const int64_t grid = nt * ntile;
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_dst_y<Tin, Tout, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const T scale = (T)sqrt(2.0 / (double)(ny + 1));
   const double bytes = (double)nt * ny * nx * (sizeof(Tin) + sizeof(Tout) * (mode ? 2 : 1));
   c.launch(sizeof(T) == 8 ? "dst_y_f64" : "dst_y_f32", bytes, [&] {
-    k_dst_y<Tin, Tout, T><<<(unsigned)grid, 256, smem, c.stream>>>(X, Y, ny, nx, N, logN, TX, tw, scale, mode);
+    PD_TX_DISPATCH(TX, {
+      if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_dst_y<Tin, Tout, T, kTX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_dst_y<Tin, Tout, T, kTX><<<(unsigned)grid, 256, smem, c.stream>>>(X, Y, ny, nx, N, logN, tw, scale, mode);
+    })
   });
 }
 

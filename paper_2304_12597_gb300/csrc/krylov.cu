@@ -16,7 +16,7 @@
 // Scalar block `scal`: [0] beta = ||b||, [1] t_{m+1,m}, [2] ||r_m|| (eq. 13),
 // [3] ||K v_m|| (breakdown reference), [4] last sum-of-squares result.
 // Flag block `flags`: [0] breakdown (invariant Krylov space), [1] beta == 0,
-// [2] non-finite value met.
+// [2] non-finite value met, [3] completion counter of k_capacitance_terms.
 #include <algorithm>
 #include <cmath>
 
@@ -28,7 +28,7 @@ namespace cg = cooperative_groups;
 
 namespace pd {
 
-constexpr int kBlas = 256;
+constexpr int kBlas = 64;  // small CTAs: FP64 reduction trees are short per SM
 
 __device__ __forceinline__ double block_sum(double v, double *red) {
   v = warp_sum(v);
@@ -84,7 +84,8 @@ __device__ void cta_axpy(int n, int m, const double *__restrict__ V, double *x, 
 
 // beta = ||b||, V[0] = b / beta; resets scal/flags.
 __global__ void __launch_bounds__(kBlas) k_init_v0_coop(const double *__restrict__ b, int n, double *part, int ld,
-                                                        double *V, float *Vf, double *scal, int *flags) {
+                                                        double *V, float *Vf, double *scal, int *flags,
+                                                        int use_handle, cudaGraphConditionalHandle h) {
   cg::grid_group grid = cg::this_grid();
   __shared__ double red[32];
   __shared__ double c[34];
@@ -102,19 +103,27 @@ __global__ void __launch_bounds__(kBlas) k_init_v0_coop(const double *__restrict
     if (Vf) Vf[j] = (float)V[j];
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    scal[0] = beta;
-    scal[1] = 0.0;
-    scal[2] = beta;
-    flags[0] = 0;
-    flags[1] = zero ? 1 : 0;
-    flags[2] = isfinite(beta) ? 0 : 1;
+    const bool finite = isfinite(beta);
+    scal[S_BETA] = beta;
+    scal[S_T] = 0.0;
+    scal[S_RES] = beta;
+    scal[S_HIST] = beta;
+    flags[F_BREAK] = 0;
+    flags[F_BZERO] = zero ? 1 : 0;
+    if (!finite) flags[F_NONFIN] = 1;
+    flags[F_CAPCNT] = 0;
+    flags[F_M] = 0;
+    const bool run = finite && !zero;
+    flags[F_KSTOP] = run ? 0 : 1;
+    flags[F_KCONV] = zero ? 1 : 0;
+    if (use_handle) cudaGraphSetConditional(h, run ? 1u : 0u);
   }
 }
 
 // One Arnoldi step (eq. 10): w = K v_{m-1}; two classical Gram-Schmidt passes
 // against v_0..v_{m-1} (their coefficients summed into column m-1 of T_m);
 // t = ||w||; v_m = w / t, or breakdown when t <= 1e-14 ||K v_{m-1}||.
-__global__ void __launch_bounds__(kBlas) k_arnoldi_coop(int n, int m, const double *__restrict__ klo,
+__global__ void __launch_bounds__(kBlas) k_arnoldi_coop(int n, const double *__restrict__ klo,
                                                         const double *__restrict__ kdiag,
                                                         const double *__restrict__ kup, double *V, float *Vf,
                                                         double *w, double *T, int ldT, double *part, int ld,
@@ -122,6 +131,7 @@ __global__ void __launch_bounds__(kBlas) k_arnoldi_coop(int n, int m, const doub
   cg::grid_group grid = cg::this_grid();
   __shared__ double red[32];
   __shared__ double c[34];
+  const int m = flags[F_M] + 1;  // the step computed here produces v_m
   const int G = gridDim.x;
   double *pa = part, *pb = part + (size_t)G * ld, *pc = part + (size_t)2 * G * ld;
   const double *v = V + (int64_t)(m - 1) * n;
@@ -160,21 +170,22 @@ __global__ void __launch_bounds__(kBlas) k_arnoldi_coop(int n, int m, const doub
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     T[(int64_t)m * ldT + (m - 1)] = bd ? 0.0 : t;
-    scal[1] = bd ? 0.0 : t;
-    scal[3] = knorm;
-    flags[0] = bd ? 1 : 0;
-    if (!isfinite(t)) flags[2] = 1;
+    scal[S_T] = bd ? 0.0 : t;
+    scal[S_KNORM] = knorm;
+    flags[F_BREAK] = bd ? 1 : 0;
+    if (!isfinite(t)) flags[F_NONFIN] = 1;
   }
 }
 
 // eq. (13): ||r_m|| = |tau t_{m+1,m}| ||(I - V_m V_m^T) z|| with two CGS passes
 // (z is overwritten by its projection); zero after a breakdown.
-__global__ void __launch_bounds__(kBlas) k_project_coop(int n, int m, const double *__restrict__ V, double *z,
+__global__ void __launch_bounds__(kBlas) k_project_coop(int n, const double *__restrict__ V, double *z,
                                                         double tau, double *part, int ld, double *scal,
                                                         const int *flags) {
   cg::grid_group grid = cg::this_grid();
   __shared__ double red[32];
   __shared__ double c[34];
+  const int m = flags[F_M] + 1;
   const int G = gridDim.x;
   double *pa = part, *pb = part + (size_t)G * ld, *pc = part + (size_t)2 * G * ld;
   cta_dots(n, m, V, z, pa + (size_t)blockIdx.x * ld, red);
@@ -193,7 +204,7 @@ __global__ void __launch_bounds__(kBlas) k_project_coop(int n, int m, const doub
   if (blockIdx.x == 0) {
     __syncthreads();
     cta_gather(pc, ld, G, 0, c);
-    if (threadIdx.x == 0) scal[2] = flags[0] ? 0.0 : fabs(tau * scal[1]) * sqrt(c[0]);
+    if (threadIdx.x == 0) scal[S_RES] = flags[F_BREAK] ? 0.0 : fabs(tau * scal[S_T]) * sqrt(c[0]);
   }
 }
 
@@ -251,6 +262,10 @@ __device__ void warp_gj_inverse(cpx<double> *H, cpx<double> *X, cpx<double> *fco
 
 constexpr int kK5Warps = 4;
 
+__device__ void capacitance_solve_cta(int nf, int m, int nparts, const double *msys_part,
+                                      const double2 *__restrict__ wg, const double2 *__restrict__ srow,
+                                      double2 *omega, double *y, const double *scal, unsigned char *smem);
+
 // Per-warp shared-memory slice, rounded up to 16 bytes so that every warp's
 // complex (16-byte) arrays stay aligned for any m.
 __host__ __device__ inline size_t k5a_warp_bytes(int m) {
@@ -259,10 +274,11 @@ __host__ __device__ inline size_t k5a_warp_bytes(int m) {
 }
 
 __global__ void __launch_bounds__(kK5Warps * 32) k_capacitance_terms(
-    int nf, int m, int maxit, double tau, const double *__restrict__ T, const double2 *__restrict__ shift,
+    int nf, int maxit, double tau, const double *__restrict__ T, const double2 *__restrict__ shift,
     const double2 *__restrict__ wg, const double2 *__restrict__ gpart, int nblk, double *msys_part,
-    double2 *srow, const double *scal, const int *flags) {
+    double2 *srow, const double *scal, int *flags, double2 *omega, double *y) {
   extern __shared__ __align__(16) unsigned char smraw[];
+  const int m = flags[F_M] + 1;
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const size_t wb = k5a_warp_bytes(m);
   unsigned char *base = smraw + wid * wb;
@@ -271,7 +287,7 @@ __global__ void __launch_bounds__(kK5Warps * 32) k_capacitance_terms(
   cpx<double> *fcol = X + m * m;
   cpx<double> *gq = fcol + m;
   double *msw = reinterpret_cast<double *>(gq + m);
-  const double tt = flags[0] ? 0.0 : tau * scal[1];
+  const double tt = flags[F_BREAK] ? 0.0 : tau * scal[S_T];
   for (int i = lane; i < m * m; i += 32) msw[i] = 0.0;
   __syncwarp();
   const int gw = blockIdx.x * kK5Warps + wid, nw = gridDim.x * kK5Warps;
@@ -284,7 +300,7 @@ __global__ void __launch_bounds__(kK5Warps * 32) k_capacitance_terms(
       }
       double gx = 0.0, gy = 0.0;
       // after a breakdown the dot pass was skipped and the t-term vanishes
-      for (int b = 0; b < (flags[0] ? 0 : nblk); ++b) {
+      for (int b = 0; b < (flags[F_BREAK] ? 0 : nblk); ++b) {
         const double2 v = gpart[((int64_t)k * nblk + b) * m + lane];
         gx += v.x;
         gy += v.y;
@@ -314,13 +330,26 @@ __global__ void __launch_bounds__(kK5Warps * 32) k_capacitance_terms(
     for (int wv = 0; wv < kK5Warps; ++wv) s += reinterpret_cast<double *>(smraw + wv * wb + (size_t)(2 * m * m + 2 * m) * sizeof(cpx<double>))[i];
     msys_part[(int64_t)blockIdx.x * m * m + i] = s;
   }
+  // The last CTA to finish (counted in flags[3]; no CTA waits for another) sums the
+  // partials and solves the m x m system, then resets the counter.
+  __shared__ int last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&flags[F_CAPCNT], 1) == (int)gridDim.x - 1;
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    capacitance_solve_cta(nf, m, gridDim.x, msys_part, wg, srow, omega, y, scal, smraw);
+    if (threadIdx.x == 0) flags[F_CAPCNT] = 0;
+  }
 }
 
-// One CTA: M = I + sum partials; y = beta M^{-1} e_1; omega_k = w_k gamma_k (e_m^T S_k y).
-__global__ void k_capacitance_solve(int nf, int m, int nparts, const double *msys_part, const double2 *__restrict__ wg,
-                                    const double2 *__restrict__ srow, double2 *omega, double *y, const double *scal) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  cpx<double> *H = reinterpret_cast<cpx<double> *>(smraw);
+// M = I + sum of the per-CTA partials; y = beta M^{-1} e_1; omega_k = w_k gamma_k
+// (e_m^T S_k y).  Run by one CTA; smem holds H, X (m x m complex), fcol and y.
+__device__ void capacitance_solve_cta(int nf, int m, int nparts, const double *msys_part,
+                                      const double2 *__restrict__ wg, const double2 *__restrict__ srow,
+                                      double2 *omega, double *y, const double *scal, unsigned char *smem) {
+  cpx<double> *H = reinterpret_cast<cpx<double> *>(smem);
   cpx<double> *X = H + m * m;
   cpx<double> *fcol = X + m * m;
   double *ys = reinterpret_cast<double *>(fcol + m);
@@ -337,8 +366,8 @@ __global__ void k_capacitance_solve(int nf, int m, int nparts, const double *msy
   __syncthreads();
   if (threadIdx.x < 32) warp_gj_inverse(H, X, fcol, m);
   __syncthreads();
-  const double beta = scal[0];
-  if (threadIdx.x < m) {
+  const double beta = scal[S_BETA];
+  if ((int)threadIdx.x < m) {
     ys[threadIdx.x] = beta * X[threadIdx.x * m + 0].x;
     y[threadIdx.x] = ys[threadIdx.x];
   }
@@ -346,9 +375,9 @@ __global__ void k_capacitance_solve(int nf, int m, int nparts, const double *msy
   for (int k = threadIdx.x; k < nf; k += blockDim.x) {
     double cx = 0.0, cy = 0.0;
     for (int q = 0; q < m; ++q) {
-      const double2 s = srow[(int64_t)k * m + q];
-      cx += s.x * ys[q];
-      cy += s.y * ys[q];
+      const double2 sv = srow[(int64_t)k * m + q];
+      cx += sv.x * ys[q];
+      cy += sv.y * ys[q];
     }
     const double2 w = wg[k];
     omega[k] = make_double2(w.x * cx - w.y * cy, w.x * cy + w.y * cx);
@@ -356,8 +385,10 @@ __global__ void k_capacitance_solve(int nf, int m, int nparts, const double *msy
 }
 
 // x = sum_q y_q V[q] (and its binary32 copy xf when requested)
-__global__ void k_xm(int n, int m, const double *__restrict__ V, const double *__restrict__ y, double *x, float *xf) {
+__global__ void k_xm(int n, const int *flags, const double *__restrict__ V, const double *__restrict__ y, double *x,
+                     float *xf) {
   __shared__ double ys[33];
+  const int m = flags[F_M];  // 0 when b == 0: x = 0
   if (threadIdx.x < m) ys[threadIdx.x] = y[threadIdx.x];
   __syncthreads();
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
@@ -377,12 +408,14 @@ __global__ void k_sumsq_final(const double *part, int nparts, double *dst) {
 }
 
 // ---- FP64 all-at-once residual ---------------------------------------------------
+// r = G_t + u_{t-1} - [ (I + tau T_x) u_t  (+ tau T_y u_t in 2D) ] with the coefficient
+// arrays pre-scaled on the host: rx = (tau lo_x, 1 + tau diag_x, tau up_x),
+// ry = (tau lo_y, tau diag_y, tau up_y): five FP64 operations per point in 1D.
 template <typename Tout, bool TWO_D>
 __global__ void k_residual(const double *__restrict__ G, const double *__restrict__ U, Tout *__restrict__ R,
-                           int nb, int nx, double tau, const double *__restrict__ xlo,
-                           const double *__restrict__ xdiag, const double *__restrict__ xup,
-                           const double *__restrict__ ylo, const double *__restrict__ ydiag,
-                           const double *__restrict__ yup, int ny) {
+                           int nb, int nx, const double *__restrict__ rxl, const double *__restrict__ rxd,
+                           const double *__restrict__ rxu, const double *__restrict__ ryl,
+                           const double *__restrict__ ryd, const double *__restrict__ ryu, int ny) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;  // spatial index
   const int64_t t = blockIdx.y;                         // time step
   if (j >= nb) return;
@@ -390,79 +423,88 @@ __global__ void k_residual(const double *__restrict__ G, const double *__restric
   const int iy = TWO_D ? j / nx : 0;
   const int ix = TWO_D ? j - iy * nx : j;
   const double uj = u[j];
-  double ku = xdiag[ix] * uj;
-  if (ix > 0) ku += xlo[ix] * u[j - 1];
-  if (ix + 1 < nx) ku += xup[ix] * u[j + 1];
+  double au = rxd[ix] * uj;
+  if (ix > 0) au = fma(rxl[ix], u[j - 1], au);
+  if (ix + 1 < nx) au = fma(rxu[ix], u[j + 1], au);
   if (TWO_D) {
-    ku += ydiag[iy] * uj;
-    if (iy > 0) ku += ylo[iy] * u[j - nx];
-    if (iy + 1 < ny) ku += yup[iy] * u[j + nx];
+    au = fma(ryd[iy], uj, au);
+    if (iy > 0) au = fma(ryl[iy], u[j - nx], au);
+    if (iy + 1 < ny) au = fma(ryu[iy], u[j + nx], au);
   }
   const int64_t idx = t * nb + j;
-  double r = G[idx] - uj - tau * ku;
-  if (t > 0) r += U[idx - nb];
-  R[idx] = (Tout)r;
+  double g = G[idx];
+  if (t > 0) g += U[idx - nb];
+  R[idx] = (Tout)(g - au);
 }
 
 // ---- launchers -------------------------------------------------------------------
 
+// Cooperative launch through cudaLaunchKernelEx (capturable into a CUDA graph).
 static void coop_launch(Ctx &c, const char *fam, double bytes, const void *fn, int grid, void **args) {
-  c.launch(fam, bytes, [&] { cudaLaunchCooperativeKernel(fn, grid, kBlas, args, 0, c.stream); });
+  c.launch(fam, bytes, [&] {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kBlas);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = c.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelExC(&cfg, fn, args);
+  });
 }
 
-void launch_vec_norm_init(Ctx &c, KrylovBufs &k, const double *b) {
+void launch_vec_norm_init(Ctx &c, KrylovBufs &k, const double *b, int use_handle, cudaGraphConditionalHandle h) {
   const int ld = k.maxit + 2;
   int n = k.n;
   double *part = k.part, *V = k.V, *scal = k.scal;
   float *Vf = k.Vf;
   int *flags = k.flags;
-  void *args[] = {(void *)&b, &n, &part, (void *)&ld, &V, &Vf, &scal, &flags};
+  void *args[] = {(void *)&b, &n, &part, (void *)&ld, &V, &Vf, &scal, &flags, &use_handle, &h};
   coop_launch(c, "krylov_blas1", (double)k.n * 16, (const void *)k_init_v0_coop, k.grid, args);
 }
 
 // Partial buffers: k.part holds three (grid, maxit+2) panels.
-void launch_arnoldi(Ctx &c, KrylovBufs &k, int m) {
+void launch_arnoldi(Ctx &c, KrylovBufs &k) {
   const int ld = k.maxit + 2;
   int n = k.n, ldT = k.maxit;
   const double *klo = k.klo, *kdiag = k.kdiag, *kup = k.kup;
   double *V = k.V, *w = k.w, *T = k.T, *part = k.part, *scal = k.scal;
   float *Vf = k.Vf;
   int *flags = k.flags;
-  void *args[] = {&n, &m, (void *)&klo, (void *)&kdiag, (void *)&kup, &V, &Vf, &w, &T, &ldT, &part, (void *)&ld,
+  void *args[] = {&n, (void *)&klo, (void *)&kdiag, (void *)&kup, &V, &Vf, &w, &T, &ldT, &part, (void *)&ld,
                   &scal, &flags};
-  coop_launch(c, "krylov_blas1", (double)k.n * 8.0 * (3 * m + 4), (const void *)k_arnoldi_coop, k.grid, args);
+  coop_launch(c, "krylov_blas1", (double)k.n * 8.0 * 8, (const void *)k_arnoldi_coop, k.grid, args);
 }
 
-void launch_capacitance(Ctx &c, KrylovBufs &k, int m, int nf, double tau, const double2 *shift, const double2 *wg,
+void launch_capacitance(Ctx &c, KrylovBufs &k, int nf, double tau, const double2 *shift, const double2 *wg,
                         const double2 *gpart, int nblk, double *msys_part, int k5_grid, double2 *srow,
                         double2 *omega, double *y) {
-  const size_t smem = k5a_warp_bytes(m) * kK5Warps;
+  const size_t smem = k5a_warp_bytes(k.maxit) * kK5Warps;  // sized for the largest m
   cudaFuncSetAttribute(k_capacitance_terms, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  c.launch("capacitance", (double)nf * nblk * m * 16, [&] {
-    k_capacitance_terms<<<k5_grid, kK5Warps * 32, smem, c.stream>>>(nf, m, k.maxit, tau, k.T, shift, wg, gpart, nblk,
-                                                                     msys_part, srow, k.scal, k.flags);
-  });
-  const size_t smem2 = (size_t)(2 * m * m + m) * sizeof(cpx<double>) + (size_t)m * sizeof(double);
-  c.launch("capacitance", (double)nf * m * 16, [&] {
-    k_capacitance_solve<<<1, 256, smem2, c.stream>>>(nf, m, k5_grid, msys_part, wg, srow, omega, y, k.scal);
+  c.launch("capacitance", (double)nf * nblk * 16, [&] {
+    k_capacitance_terms<<<k5_grid, kK5Warps * 32, smem, c.stream>>>(nf, k.maxit, tau, k.T, shift, wg, gpart, nblk,
+                                                                     msys_part, srow, k.scal, k.flags, omega, y);
   });
 }
 
 // ||(I - V_m V_m^T) z|| with two CGS passes (z is overwritten by the projection).
-void launch_project_resnorm(Ctx &c, KrylovBufs &k, int m, const double *z, double tau) {
+void launch_project_resnorm(Ctx &c, KrylovBufs &k, const double *z, double tau) {
   const int ld = k.maxit + 2;
   int n = k.n;
   const double *V = k.V;
   double *zz = const_cast<double *>(z);
   double *part = k.part, *scal = k.scal;
   const int *flags = k.flags;
-  void *args[] = {&n, &m, (void *)&V, &zz, &tau, &part, (void *)&ld, &scal, (void *)&flags};
-  coop_launch(c, "krylov_blas1", (double)k.n * 8.0 * (3 * m + 3), (const void *)k_project_coop, k.grid, args);
+  void *args[] = {&n, (void *)&V, &zz, &tau, &part, (void *)&ld, &scal, (void *)&flags};
+  coop_launch(c, "krylov_blas1", (double)k.n * 8.0 * 6, (const void *)k_project_coop, k.grid, args);
 }
 
-void launch_xm(Ctx &c, KrylovBufs &k, int m, const double *y, double *x, float *xf) {
-  c.launch("krylov_blas1", (double)k.n * 8.0 * (m + 1),
-           [&] { k_xm<<<k.grid, kBlas, 0, c.stream>>>(k.n, m, k.V, y, x, xf); });
+void launch_xm(Ctx &c, KrylovBufs &k, const double *y, double *x, float *xf) {
+  c.launch("krylov_blas1", (double)k.n * 8.0 * 2,
+           [&] { k_xm<<<k.grid, kBlas, 0, c.stream>>>(k.n, k.flags, k.V, y, x, xf); });
 }
 
 void launch_sumsq(Ctx &c, const double *part, int nparts, double *dst) {
@@ -471,28 +513,26 @@ void launch_sumsq(Ctx &c, const double *part, int nparts, double *dst) {
 
 template <typename Tout>
 void launch_residual(Ctx &c, const double *G, const double *U, Tout *R, int64_t nt, int64_t ny, int64_t nx,
-                     double tau, const double *xlo, const double *xdiag, const double *xup, const double *ylo,
-                     const double *ydiag, const double *yup, double *norm_part, int *nparts) {
-  (void)norm_part;
+                     const double *rxl, const double *rxd, const double *rxu, const double *ryl, const double *ryd,
+                     const double *ryu) {
   const int nb = (int)(ny * nx);
   const dim3 grid((unsigned)((nb + 255) / 256), (unsigned)nt);
-  if (nparts) *nparts = 0;
   c.launch(sizeof(Tout) == 8 ? "residual_f64_to_f64" : "residual_f64_to_f32",
            (double)nt * nb * (8 + 8 + sizeof(Tout)), [&] {
-             if (ylo)
-               k_residual<Tout, true><<<grid, 256, 0, c.stream>>>(G, U, R, nb, (int)nx, tau, xlo, xdiag, xup, ylo,
-                                                                  ydiag, yup, (int)ny);
+             if (ryl)
+               k_residual<Tout, true><<<grid, 256, 0, c.stream>>>(G, U, R, nb, (int)nx, rxl, rxd, rxu, ryl, ryd, ryu,
+                                                                  (int)ny);
              else
-               k_residual<Tout, false><<<grid, 256, 0, c.stream>>>(G, U, R, nb, (int)nx, tau, xlo, xdiag, xup, ylo,
-                                                                   ydiag, yup, (int)ny);
+               k_residual<Tout, false><<<grid, 256, 0, c.stream>>>(G, U, R, nb, (int)nx, rxl, rxd, rxu, ryl, ryd,
+                                                                   ryu, (int)ny);
            });
 }
 
-template void launch_residual<float>(Ctx &, const double *, const double *, float *, int64_t, int64_t, int64_t, double,
+template void launch_residual<float>(Ctx &, const double *, const double *, float *, int64_t, int64_t, int64_t,
                                      const double *, const double *, const double *, const double *, const double *,
-                                     const double *, double *, int *);
+                                     const double *);
 template void launch_residual<double>(Ctx &, const double *, const double *, double *, int64_t, int64_t, int64_t,
-                                      double, const double *, const double *, const double *, const double *,
-                                      const double *, const double *, double *, int *);
+                                      const double *, const double *, const double *, const double *, const double *,
+                                      const double *);
 
 }  // namespace pd

@@ -121,6 +121,7 @@ extern "C" pd_status paradiag_smw_rhs_noalloc(int64_t nt, int64_t n, double tau,
   pd::PintGeom g = pd::pint_geometry(nf, 1, (int)n, 4 * pd::sm_count(), 16);
   const int rmax = (int)(kAccDoubles / (size_t)n);
   if (g.R > rmax) g.R = rmax;
+  pd::set_acc_rows(g);
   pd::PintArgs<double> a{};
   a.shift = shift;
   a.tlo = tlo;

@@ -43,9 +43,11 @@ template <typename T>
 __device__ __forceinline__ cpx<T> fnms_r(cpx<T> a, T s, cpx<T> c) { return mk<T>(a.x - s * c.x, a.y - s * c.y); }
 // 1 / a  =  conj(a) / |a|^2.  The operands met here are bounded away from zero and
 // from overflow (|a| between ~1e-3 and ~1e8), so no Smith-style scaling is needed.
+__device__ __forceinline__ float rcp_rn(float v) { return __frcp_rn(v); }
+__device__ __forceinline__ double rcp_rn(double v) { return __drcp_rn(v); }
 template <typename T>
 __device__ __forceinline__ cpx<T> recip(cpx<T> a) {
-  T d = T(1) / (a.x * a.x + a.y * a.y);
+  const T d = rcp_rn(a.x * a.x + a.y * a.y);  // correctly rounded reciprocal
   return mk<T>(a.x * d, -a.y * d);
 }
 template <typename T>

@@ -13,6 +13,38 @@
 
 namespace pd {
 
+// Device control block layout (the plan's `flags` int array and `scal` double array).
+enum FlagIndex {
+  F_BREAK = 0,    // Algorithm 2 met an invariant Krylov space
+  F_BZERO = 1,    // ||b|| == 0
+  F_NONFIN = 2,   // a non-finite value was met
+  F_CAPCNT = 3,   // completion counter of the capacitance kernel
+  F_KSTOP = 4,    // Algorithm 2 loop finished
+  F_M = 5,        // completed Algorithm-2 iterations m of the current solve
+  F_SWEEP = 6,    // completed solves (first solve + refinement sweeps)
+  F_RCONV = 7,    // refinement reached its tolerance
+  F_KCONV = 8,    // Algorithm 2 reached eps (or b == 0, or breakdown)
+  F_RSTOP = 9,    // refinement loop finished
+  F_MTOT = 10,    // sum of m over the solves
+  F_SWM = 16,     // [16, 32): m of each solve
+  kFlagWords = 64
+};
+enum ScalIndex {
+  S_BETA = 0,     // ||b|| of the current solve
+  S_T = 1,        // t_{m+1,m}
+  S_RES = 2,      // ||r_m|| of eq. (13)
+  S_KNORM = 3,    // ||K v_m|| (breakdown reference)
+  S_D2 = 4,       // ||delta||_F^2 of the last solve's output
+  S_REF2 = 5,     // ||delta_0||_F^2
+  S_PREV = 6,     // previous relative update
+  S_UPD = 7,      // last relative update
+  S_HIST = 16,    // [16, 49): ||r_m|| history of the current solve
+  S_SWRES = 64,   // [64, 80): eq. (13) residual / ||b|| at exit of each solve
+  S_SWUPD = 80,   // [80, 96): ||delta_s|| / ||delta_0|| of each solve
+  S_SWBETA = 96,  // [96, 112): ||b|| of each solve
+  kScalWords = 128
+};
+
 // Launch context: the stream every kernel is ordered on, a launch counter, and
 // optional per-launch timing with CUDA events recorded on that same stream.
 struct Ctx {
@@ -77,11 +109,18 @@ struct PintGeom {
   int R;         // k-range splits: teams = nblk * R
   int teams_per_cta;
   int M;         // rows per thread (template value)
+  int cta_sum;   // 1: the teams of a CTA add their partial rows (nblk == 1)
+  int acc_rows;  // partial rows per block in acc_part (R, or CTAs when cta_sum)
 };
 PintGeom pint_geometry(int nf, int nblk, int blen, int target_teams, int elem_bytes);
+void set_acc_rows(PintGeom &g);  // recompute cta_sum / acc_rows after changing R
 
 template <typename T>
 struct PintArgs {
+  const int *mcount;       // device m (completed Algorithm-2 steps), or null: when set the
+                           // right-hand side is V[m+1] and the dots use V[0..m]
+  int want_dots;           // with mcount: compute g_k = V^T y_k
+  int mdots_max;           // with mcount: largest possible number of dots (smem sizing)
   const double2 *shift;    // s_k = 1 - pi_k, length nf
   const T *tlo, *tdiag, *tup;  // tau * K (block-decoupled), length nblk*blen
   const cpx<T> *R;         // spectrum right-hand sides (nf, ldr) or null
@@ -119,20 +158,43 @@ struct KrylovBufs {
   double *scal;       // scalar block (see krylov.cu)
   int *flags;         // flag block (see krylov.cu)
 };
-void launch_vec_norm_init(Ctx &c, KrylovBufs &k, const double *b);
-void launch_arnoldi(Ctx &c, KrylovBufs &k, int m);
-void launch_capacitance(Ctx &c, KrylovBufs &k, int m, int nf, double tau, const double2 *shift,
+// All Algorithm-2 kernels read m from flags[F_M] (completed steps), so one captured
+// iteration serves every m.  `use_handle` / `h`: set a CUDA-graph conditional.
+void launch_vec_norm_init(Ctx &c, KrylovBufs &k, const double *b, int use_handle,
+                          cudaGraphConditionalHandle h);
+void launch_arnoldi(Ctx &c, KrylovBufs &k);
+void launch_capacitance(Ctx &c, KrylovBufs &k, int nf, double tau, const double2 *shift,
                         const double2 *wg, const double2 *gpart, int nblk, double *msys_part,
                         int k5_grid, double2 *srow, double2 *omega, double *y);
-void launch_project_resnorm(Ctx &c, KrylovBufs &k, int m, const double *z, double tau);
-void launch_xm(Ctx &c, KrylovBufs &k, int m, const double *y, double *x, float *xf);
+void launch_project_resnorm(Ctx &c, KrylovBufs &k, const double *z, double tau);
+void launch_xm(Ctx &c, KrylovBufs &k, const double *y, double *x, float *xf);
+
+// Device-side control of Algorithm 2 and of the refinement loop (control.cu).
+struct KrylovCtl {
+  double eps;          // stop when ||r_m|| <= eps * beta
+  double stall_floor;  // stall exit only once ||r_m|| <= stall_floor * beta
+  int win;             // stall: no halving over `win` steps
+  int maxit;
+};
+struct RefineCtl {
+  int fp64;
+  double eps_first, eps_refine;  // Algorithm-2 tolerances of the first solve / sweeps
+  double refine_tol;
+  int max_refine;
+};
+void launch_solve_reset(Ctx &c, double *scal, int *flags);
+void launch_krylov_decide(Ctx &c, double *scal, int *flags, const KrylovCtl &k, int use_handle,
+                          cudaGraphConditionalHandle h);
+void launch_refine_decide(Ctx &c, double *scal, int *flags, const RefineCtl &r, int use_handle,
+                          cudaGraphConditionalHandle h);
 void launch_sumsq(Ctx &c, const double *part, int nparts, double *dst);
 // FP64 all-at-once residual R = G - [(I + tau K) U - U Sigma_1^T], stored as Tout
-// (float for the mixed path, double for the FP64 path).  1D: K tridiagonal
-// (lo, diag, up) of length nx; 2D adds T_y along the middle axis.
+// (float for the mixed path, double for the FP64 path).  rx = (tau lo_x, 1 + tau diag_x,
+// tau up_x) of length nx; 2D adds ry = (tau lo_y, tau diag_y, tau up_y) along the middle
+// axis (ryl == null in 1D).
 template <typename Tout>
 void launch_residual(Ctx &c, const double *G, const double *U, Tout *R, int64_t nt, int64_t ny, int64_t nx,
-                     double tau, const double *xlo, const double *xdiag, const double *xup, const double *ylo,
-                     const double *ydiag, const double *yup, double *norm_part, int *nparts);
+                     const double *rxl, const double *rxd, const double *rxu, const double *ryl, const double *ryd,
+                     const double *ryu);
 
 }  // namespace pd

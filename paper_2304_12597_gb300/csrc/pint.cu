@@ -34,7 +34,7 @@ struct TeamSmem {
   static size_t bytes(int P, int mdots) {
     size_t b = 0;
     b += (size_t)P * (M + 1) * sizeof(cpx<T>);   // rhs / dd, padded one slot per chunk
-    b += (size_t)2 * P * 5 * sizeof(cpx<T>);     // PCR rows a, b, c, d and 1/b
+    b += (size_t)P * 5 * sizeof(cpx<T>);         // condensed rows a, b, c, d and 1/b
     b += ((size_t)P * M * sizeof(T) + 15) & ~(size_t)15;  // per-team accumulators (compute type)
     b += (size_t)(P / 32) * std::max(mdots, 1) * sizeof(double2);  // dot reductions
     return (b + 15) & ~(size_t)15;
@@ -55,20 +55,20 @@ __device__ __forceinline__ void coef(const PintArgs<T> &a, int64_t j, bool valid
 }
 
 template <typename T, int M>
-__global__ void __launch_bounds__(512) k_pint(PintGeom g, PintArgs<T> a, size_t team_bytes) {
+__global__ void __launch_bounds__(M >= 16 ? 256 : 512) k_pint(PintGeom g, PintArgs<T> a, size_t team_bytes) {
   if (a.skip_flag && *a.skip_flag) return;
   const int P = g.P;
   const int tic = threadIdx.x / P;
   const int t = threadIdx.x - tic * P;
   const int team = blockIdx.x * g.teams_per_cta + tic;
-  if (team >= g.nblk * g.R) return;  // whole teams only
-  const int blk = team / g.R;
+  const bool active = team < g.nblk * g.R;  // idle teams stay for the CTA-level sum
+  const int blk = active ? team / g.R : 0;
   const int rr = team - blk * g.R;
-  const int k0 = (int)((int64_t)rr * g.nf / g.R);
-  const int k1 = (int)((int64_t)(rr + 1) * g.nf / g.R);
+  const int k0 = active ? (int)((int64_t)rr * g.nf / g.R) : 0;
+  const int k1 = active ? (int)((int64_t)(rr + 1) * g.nf / g.R) : 0;
   const int blen = g.blen;
   const int64_t off = (int64_t)blk * blen;
-  const int N = 2 * P;
+  const int N = P;  // condensed interface rows
 
   extern __shared__ __align__(16) unsigned char smraw[];
   unsigned char *base = smraw + (size_t)tic * team_bytes;
@@ -82,6 +82,14 @@ __global__ void __launch_bounds__(512) k_pint(PintGeom g, PintArgs<T> a, size_t 
   double2 *red = reinterpret_cast<double2 *>(reinterpret_cast<unsigned char *>(acc) +
                                              (((size_t)P * M * sizeof(T) + 15) & ~(size_t)15));
 
+  // right-hand-side vector and number of dots: fixed, or from the device step count
+  const T *rvec = a.rvec;
+  int mdots = a.V ? a.mdots : 0;
+  if (a.mcount) {
+    const int m = *a.mcount + 1;  // v_m of the step in progress
+    rvec = a.V + (int64_t)m * a.ldv;
+    mdots = a.want_dots ? m : 0;
+  }
   const bool do_acc = a.omega != nullptr;
   if (do_acc) {
 #pragma unroll
@@ -100,9 +108,9 @@ __global__ void __launch_bounds__(512) k_pint(PintGeom g, PintArgs<T> a, size_t 
         const int64_t j = off + e;
         if (a.R) {
           v = a.R[(int64_t)k * a.ldr + j];
-          if (a.rvec) v.x -= a.rvec[j];
+          if (rvec) v.x -= rvec[j];
         } else {
-          v.x = a.rvec[j];
+          v.x = rvec[j];
         }
       }
       dd[e + e / M] = v;
@@ -141,64 +149,62 @@ __global__ void __launch_bounds__(512) k_pint(PintGeom g, PintArgs<T> a, size_t 
       const cpx<T> c2 = mul(cc[i], cc[i + 1]);
       cc[i] = mk<T>(-c2.x, -c2.y);
     }
-    // interface rows 2t (first row of the chunk) and 2t+1 (last row)
-    cpx<T> A0 = mk<T>(lo0, T(0));
-    cpx<T> B0 = fnms_r(d0, up0, aa[1]);
-    cpx<T> C0 = scal(-up0, cc[1]);
-    cpx<T> D0 = fnms_r(r0, up0, my[1]);
-    cpx<T> A1 = aa[M - 1];
-    cpx<T> B1 = mk<T>(T(1), T(0));
-    cpx<T> C1 = cc[M - 1];
-    cpx<T> D1 = my[M - 1];
+    // interface rows: first row of the chunk (unknown xs_t) couples xe_{t-1}, xs_t, xe_t;
+    // last row (unknown xe_t, unit diagonal) couples xs_t, xe_t, xs_{t+1}
+    const cpx<T> A0 = mk<T>(lo0, T(0));
+    const cpx<T> B0 = fnms_r(d0, up0, aa[1]);
+    const cpx<T> C0 = scal(-up0, cc[1]);
+    const cpx<T> D0 = fnms_r(r0, up0, my[1]);
+    const cpx<T> A1 = aa[M - 1];
+    const cpx<T> C1 = cc[M - 1];
+    const cpx<T> D1 = my[M - 1];
 
-    // 3. PCR on the 2P interface rows
-    const int i0 = 2 * t, i1 = 2 * t + 1;
-    for (int sig = 1; sig < N; sig <<= 1) {
-      pa[i0] = A0; pb[i0] = B0; pc[i0] = C0; pd[i0] = D0; pib[i0] = recip(B0);
-      pa[i1] = A1; pb[i1] = B1; pc[i1] = C1; pd[i1] = D1; pib[i1] = recip(B1);
-      team_sync(P, tic);
-      cpx<T> nA0, nB0 = B0, nC0, nD0 = D0, nA1, nB1 = B1, nC1, nD1 = D1;
-      {
-        const int lo = i0 - sig, hi = i0 + sig;
-        nA0 = mk<T>(T(0), T(0));
-        nC0 = mk<T>(T(0), T(0));
-        if (lo >= 0) {
-          const cpx<T> k1 = mul(A0, pib[lo]);
-          nA0 = mk<T>(T(0), T(0));
-          nA0 = fnms(nA0, k1, pa[lo]);
-          nB0 = fnms(nB0, k1, pc[lo]);
-          nD0 = fnms(nD0, k1, pd[lo]);
-        }
-        if (hi < N) {
-          const cpx<T> k2 = mul(C0, pib[hi]);
-          nC0 = fnms(nC0, k2, pc[hi]);
-          nB0 = fnms(nB0, k2, pa[hi]);
-          nD0 = fnms(nD0, k2, pd[hi]);
-        }
-      }
-      {
-        const int lo = i1 - sig, hi = i1 + sig;
-        nA1 = mk<T>(T(0), T(0));
-        nC1 = mk<T>(T(0), T(0));
-        if (lo >= 0) {
-          const cpx<T> k1 = mul(A1, pib[lo]);
-          nA1 = fnms(nA1, k1, pa[lo]);
-          nB1 = fnms(nB1, k1, pc[lo]);
-          nD1 = fnms(nD1, k1, pd[lo]);
-        }
-        if (hi < N) {
-          const cpx<T> k2 = mul(C1, pib[hi]);
-          nC1 = fnms(nC1, k2, pc[hi]);
-          nB1 = fnms(nB1, k2, pa[hi]);
-          nD1 = fnms(nD1, k2, pd[hi]);
-        }
-      }
-      team_sync(P, tic);
-      A0 = nA0; B0 = nB0; C0 = nC0; D0 = nD0;
-      A1 = nA1; B1 = nB1; C1 = nC1; D1 = nD1;
+    // 3a. eliminate every xe with the last rows: P rows in the xs alone, one per thread
+    pa[t] = A1;
+    pc[t] = C1;
+    pd[t] = D1;
+    team_sync(P, tic);
+    cpx<T> A, B, C, D;
+    {
+      const cpx<T> z = mk<T>(T(0), T(0));
+      const cpx<T> pA1 = t > 0 ? pa[t - 1] : z, pC1 = t > 0 ? pc[t - 1] : z, pD1 = t > 0 ? pd[t - 1] : z;
+      // xe_{t-1} = pD1 - pA1 xs_{t-1} - pC1 xs_t ;  xe_t = D1 - A1 xs_t - C1 xs_{t+1}
+      A = mul(A0, pA1);
+      A = mk<T>(-A.x, -A.y);
+      B = fnms(fnms(B0, A0, pC1), C0, A1);
+      C = mul(C0, C1);
+      C = mk<T>(-C.x, -C.y);
+      D = fnms(fnms(D0, A0, pD1), C0, D1);
     }
-    const cpx<T> xf = mul(D0, recip(B0));
-    const cpx<T> xl = mul(D1, recip(B1));
+    team_sync(P, tic);
+
+    // 3b. PCR on the P condensed rows
+    for (int sig = 1; sig < P; sig <<= 1) {
+      pa[t] = A; pb[t] = B; pc[t] = C; pd[t] = D; pib[t] = recip(B);
+      team_sync(P, tic);
+      cpx<T> nA = mk<T>(T(0), T(0)), nB = B, nC = mk<T>(T(0), T(0)), nD = D;
+      const int lo = t - sig, hi = t + sig;
+      if (lo >= 0) {
+        const cpx<T> k1 = mul(A, pib[lo]);
+        nA = fnms(nA, k1, pa[lo]);
+        nB = fnms(nB, k1, pc[lo]);
+        nD = fnms(nD, k1, pd[lo]);
+      }
+      if (hi < P) {
+        const cpx<T> k2 = mul(C, pib[hi]);
+        nC = fnms(nC, k2, pc[hi]);
+        nB = fnms(nB, k2, pa[hi]);
+        nD = fnms(nD, k2, pd[hi]);
+      }
+      team_sync(P, tic);
+      A = nA; B = nB; C = nC; D = nD;
+    }
+    const cpx<T> xf = mul(D, recip(B));
+    // 3c. recover xe_t from the last row and xs_{t+1}
+    pd[t] = xf;
+    team_sync(P, tic);
+    const cpx<T> xnext = t + 1 < P ? pd[t + 1] : mk<T>(T(0), T(0));
+    const cpx<T> xl = fnms(fnms(D1, A1, xf), C1, xnext);
 
     // 4. back substitution of the interior rows
     my[0] = xf;
@@ -218,9 +224,9 @@ __global__ void __launch_bounds__(512) k_pint(PintGeom g, PintArgs<T> a, size_t 
       for (int e = t; e < blen; e += P) a.Y[(int64_t)k * a.ldy + off + e] = dd[e + e / M];
     }
     // 6. dots with the Krylov basis
-    if (a.V && a.mdots > 0) {
+    if (mdots > 0) {
       const int nw = P >> 5, w = t >> 5, l = t & 31;
-      for (int q = 0; q < a.mdots; ++q) {
+      for (int q = 0; q < mdots; ++q) {
         T px = T(0), py = T(0);
         const T *vq = a.V + (int64_t)q * a.ldv + off;
         for (int e = t; e < blen; e += P) {
@@ -231,25 +237,42 @@ __global__ void __launch_bounds__(512) k_pint(PintGeom g, PintArgs<T> a, size_t 
         }
         double sx = warp_sum((double)px);
         double sy = warp_sum((double)py);
-        if (l == 0) red[w * a.mdots + q] = make_double2(sx, sy);
+        if (l == 0) red[w * mdots + q] = make_double2(sx, sy);
       }
       team_sync(P, tic);
-      for (int q = t; q < a.mdots; q += P) {
+      for (int q = t; q < mdots; q += P) {
         double sx = 0.0, sy = 0.0;
         for (int i = 0; i < nw; ++i) {
-          sx += red[i * a.mdots + q].x;
-          sy += red[i * a.mdots + q].y;
+          sx += red[i * mdots + q].x;
+          sy += red[i * mdots + q].y;
         }
-        a.gpart[((int64_t)k * g.nblk + blk) * a.mdots + q] = make_double2(sx, sy);
+        a.gpart[((int64_t)k * g.nblk + blk) * mdots + q] = make_double2(sx, sy);
       }
     }
     team_sync(P, tic);
   }
   if (do_acc) {
+    if (g.cta_sum) {
+      // nblk == 1: every team of the CTA owns the same rows, so the CTA adds its
+      // teams' accumulators (fixed order) and writes one partial row
+      __syncthreads();
+      if (tic == 0) {
 #pragma unroll
-    for (int i = 0; i < M; ++i) {
-      const int e = e0 + i;
-      if (e < blen) a.acc_part[(int64_t)team * blen + e] = (double)acc[i * P + t];
+        for (int i = 0; i < M; ++i) {
+          const int e = e0 + i;
+          double sum = 0.0;
+          for (int j = 0; j < g.teams_per_cta; ++j)
+            sum += (double)reinterpret_cast<const T *>(reinterpret_cast<const unsigned char *>(acc) +
+                                                       (size_t)j * team_bytes)[i * P + t];
+          if (e < blen) a.acc_part[(int64_t)blockIdx.x * blen + e] = sum;
+        }
+      }
+    } else if (active) {
+#pragma unroll
+      for (int i = 0; i < M; ++i) {
+        const int e = e0 + i;
+        if (e < blen) a.acc_part[(int64_t)team * blen + e] = (double)acc[i * P + t];
+      }
     }
   }
 }
@@ -268,7 +291,7 @@ __global__ void __launch_bounds__(1024) k_acc_reduce(int nblk, int blen, int R, 
   if (j < n) {
     const int blk = (int)(j / blen);
     const int e = (int)(j - (int64_t)blk * blen);
-    const double *base = part + (int64_t)blk * R * blen + e;
+    const double *base = part + (int64_t)blk * R * blen + e;  // R = partial rows per block
     int r = threadIdx.y;
     for (; r + 96 < R; r += 128) {
       s0 += base[(int64_t)r * blen];
@@ -293,23 +316,30 @@ static int next_pow2(int v) {
   return p;
 }
 
+void set_acc_rows(PintGeom &g) {
+  g.cta_sum = (g.nblk == 1 && g.teams_per_cta > 1) ? 1 : 0;
+  g.acc_rows = g.cta_sum ? (g.R + g.teams_per_cta - 1) / g.teams_per_cta : g.R;
+}
+
 PintGeom pint_geometry(int nf, int nblk, int blen, int target_teams, int elem_bytes) {
-  (void)elem_bytes;
   PintGeom g;
   g.nf = nf;
   g.nblk = nblk;
   g.blen = blen;
-  g.M = blen <= 128 ? 4 : 8;
+  // rows per thread: longer chunks in binary32 (registers allow it) halve the
+  // threads per block and the interface system
+  g.M = blen <= 128 ? 4 : (elem_bytes == 8 && blen > 512 ? 16 : 8);
   g.P = std::max(32, next_pow2((blen + g.M - 1) / g.M));
   g.teams_per_cta = std::max(1, 256 / g.P);
   int R = (target_teams + nblk - 1) / nblk;
   g.R = std::max(1, std::min(R, nf));
+  set_acc_rows(g);
   return g;
 }
 
 template <typename T, int M>
 static void launch_pint_m(Ctx &c, const PintGeom &g, const PintArgs<T> &a) {
-  const size_t tb = TeamSmem<T, M>::bytes(g.P, a.mdots);
+  const size_t tb = TeamSmem<T, M>::bytes(g.P, a.mcount ? (a.want_dots ? a.mdots_max : 0) : a.mdots);
   const size_t smem = tb * g.teams_per_cta;
   const int nteams = g.nblk * g.R;
   const int grid = (nteams + g.teams_per_cta - 1) / g.teams_per_cta;
@@ -320,24 +350,29 @@ static void launch_pint_m(Ctx &c, const PintGeom &g, const PintArgs<T> &a) {
   const double per = (double)g.nf * g.nblk * g.blen;
   if (a.R) bytes += per * sizeof(cpx<T>);
   if (a.Y) bytes += per * sizeof(cpx<T>);
-  const char *fam = sizeof(T) == 8 ? (a.Y ? "pint_store_f64" : (a.V ? "pint_dots_f64" : "pint_acc_f64"))
-                                   : (a.Y ? "pint_store_f32" : (a.V ? "pint_dots_f32" : "pint_acc_f32"));
+  const bool dots = a.mcount ? a.want_dots != 0 : a.mdots > 0;
+  const char *fam = sizeof(T) == 8 ? (a.Y ? "pint_store_f64" : (dots ? "pint_dots_f64" : "pint_acc_f64"))
+                                   : (a.Y ? "pint_store_f32" : (dots ? "pint_dots_f32" : "pint_acc_f32"));
   c.launch(fam, bytes, [&] { k_pint<T, M><<<grid, threads, smem, c.stream>>>(g, a, tb); });
 }
 
 template <typename T>
 void launch_pint(Ctx &c, const PintGeom &g, const PintArgs<T> &a) {
-  if (g.M == 4)
+  if (g.M == 4) {
     launch_pint_m<T, 4>(c, g, a);
-  else
+  } else if (g.M == 16) {
+    if constexpr (sizeof(T) == 4) launch_pint_m<T, 16>(c, g, a);
+  } else {
     launch_pint_m<T, 8>(c, g, a);
+  }
 }
 
 void launch_acc_reduce(Ctx &c, const PintGeom &g, const double *acc_part, double *out, const int *skip_flag) {
   const int64_t n = (int64_t)g.nblk * g.blen;
   const int grid = (int)((n + 31) / 32);
-  c.launch("acc_reduce", (double)n * g.R * 8.0 + n * 8.0,
-           [&] { k_acc_reduce<<<grid, dim3(32, 32), 0, c.stream>>>(g.nblk, g.blen, g.R, acc_part, out, skip_flag); });
+  c.launch("acc_reduce", (double)n * g.acc_rows * 8.0 + n * 8.0, [&] {
+    k_acc_reduce<<<grid, dim3(32, 32), 0, c.stream>>>(g.nblk, g.blen, g.acc_rows, acc_part, out, skip_flag);
+  });
 }
 
 template void launch_pint<double>(Ctx &, const PintGeom &, const PintArgs<double> &);

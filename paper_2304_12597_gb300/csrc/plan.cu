@@ -169,6 +169,8 @@ struct pd_plan {
   double *tlo_d = nullptr, *tdiag_d = nullptr, *tup_d = nullptr;
   float *tlo_f = nullptr, *tdiag_f = nullptr, *tup_f = nullptr;
   double *xlo = nullptr, *xdiag = nullptr, *xup = nullptr, *ylo = nullptr, *ydiag = nullptr, *yup = nullptr;
+  // residual coefficients: (tau lo_x, 1 + tau diag_x, tau up_x) and (tau lo_y, tau diag_y, tau up_y)
+  double *rxl = nullptr, *rxd = nullptr, *rxu = nullptr, *ryl = nullptr, *ryd = nullptr, *ryu = nullptr;
   cpx<double> *tw_d = nullptr, *twy_d = nullptr;
   cpx<float> *tw_f = nullptr, *twy_f = nullptr;
   void *spec = nullptr;
@@ -189,6 +191,16 @@ struct pd_plan {
   int *h_flags = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   pd_stats last{};
+  // CUDA graph of the whole solve, built for one (G, U) pair
+  int use_graphs = 1;
+  bool graph_failed = false;
+  cudaStream_t cap[3] = {nullptr, nullptr, nullptr};  // capture streams (top level, bodies)
+  cudaGraphExec_t gexec = nullptr;
+  const double *g_G = nullptr;
+  double *g_U = nullptr;
+  struct {
+    int64_t pre0 = 0, iter0 = 0, post0 = 0, pre1 = 0, iter1 = 0, post1 = 0;
+  } seg;  // kernel launches per segment (for the launch count of graph solves)
 };
 
 namespace {
@@ -268,8 +280,8 @@ void fill_geometry(pd_plan *p, const pd_desc *d) {
   const int ctas_per_sm = std::max(1, std::min(by_smem, by_threads));
   const int target = sms * ctas_per_sm * g0.teams_per_cta;
   p->geom = pd::pint_geometry(p->nf, p->nblk, p->blen, target, esz);
-  // cooperative Krylov kernels: at most one 256-thread CTA per SM (always co-resident)
-  p->blas_grid = (int)std::max<int64_t>(1, std::min<int64_t>((p->nbar + 255) / 256, (int64_t)sms));
+  // cooperative Krylov kernels: 64-thread CTAs, at most one per SM (always co-resident)
+  p->blas_grid = (int)std::max<int64_t>(1, std::min<int64_t>((p->nbar + 63) / 64, (int64_t)sms));
   // capacitance terms: a few frequencies per warp keeps the partial reduction short
   p->k5_grid = std::max(1, std::min((p->nf + 15) / 16, 64));
 }
@@ -297,10 +309,16 @@ size_t layout(pd_plan *p, unsigned char *base) {
   p->xlo = A.take<double>(p->nx);
   p->xdiag = A.take<double>(p->nx);
   p->xup = A.take<double>(p->nx);
+  p->rxl = A.take<double>(p->nx);
+  p->rxd = A.take<double>(p->nx);
+  p->rxu = A.take<double>(p->nx);
   if (p->dim == 2) {
     p->ylo = A.take<double>(p->ny);
     p->ydiag = A.take<double>(p->ny);
     p->yup = A.take<double>(p->ny);
+    p->ryl = A.take<double>(p->ny);
+    p->ryd = A.take<double>(p->ny);
+    p->ryu = A.take<double>(p->ny);
   }
   const int ntw = std::max<int>(1, (int)(nt / 2));
   p->tw_d = A.take<cpx<double>>(ntw);
@@ -318,8 +336,8 @@ size_t layout(pd_plan *p, unsigned char *base) {
   p->T = A.take<double>((size_t)(mx + 1) * mx);
   p->w = A.take<double>(nbar);
   p->part = A.take<double>((size_t)3 * p->blas_grid * (mx + 2));
-  p->scal = A.take<double>(16);
-  p->flags = A.take<int>(16);
+  p->scal = A.take<double>(pd::kScalWords);
+  p->flags = A.take<int>(pd::kFlagWords);
   p->b = A.take<double>(nbar);
   p->z = A.take<double>(nbar);
   p->x = A.take<double>(nbar);
@@ -395,8 +413,8 @@ pd_status ctx_status(pd_plan *p) {
 }
 
 pd_status sync_read(pd_plan *p) {
-  CK(cudaMemcpyAsync(p->h_scal, p->scal, 16 * sizeof(double), cudaMemcpyDeviceToHost, p->ctx.stream));
-  CK(cudaMemcpyAsync(p->h_flags, p->flags, 16 * sizeof(int), cudaMemcpyDeviceToHost, p->ctx.stream));
+  CK(cudaMemcpyAsync(p->h_scal, p->scal, pd::kScalWords * sizeof(double), cudaMemcpyDeviceToHost, p->ctx.stream));
+  CK(cudaMemcpyAsync(p->h_flags, p->flags, pd::kFlagWords * sizeof(int), cudaMemcpyDeviceToHost, p->ctx.stream));
   CK(cudaStreamSynchronize(p->ctx.stream));
   return ctx_status(p);
 }
@@ -442,132 +460,6 @@ pd::PintArgs<float> base_args<float>(pd_plan *p) {
   return a;
 }
 
-struct SolveInfo {
-  int m = 0;
-  int pint_loops = 0;
-  int sweeps_exec = 0;
-  bool breakdown = false;
-  bool converged = true;
-  double beta = 0.0;
-  double rel_res = 0.0;
-};
-
-// Algorithm 1 in the solve basis on real input X (nt, nbar); the result is
-// written by the inverse DFT in `out_mode` (0 store double, 1 add double,
-// 2 store float) and ||result||_F^2 is left in scal[4].
-template <typename T, typename Tin>
-pd_status run_paradiag(pd_plan *p, const Tin *X, void *out, int out_mode, SolveInfo &info, double eps,
-                       double stall_floor) {
-  pd::Ctx &c = p->ctx;
-  cpx<T> *S = reinterpret_cast<cpx<T> *>(p->spec);
-  const int nt = (int)p->nt;
-  // forward DFT along time: rows of G F^T (eq. 5)
-  pd::launch_fft_r2c<T, Tin>(c, X, p->nbar, p->nbar, nt, time_tw<T>(p), S, p->lds);
-  // first parallel-in-time loop and b = L F^{-T} e_l (eq. 7)
-  {
-    pd::PintArgs<T> a = base_args<T>(p);
-    a.R = S;
-    a.ldr = p->lds;
-    a.omega = p->wg;
-    a.acc_part = p->acc_part;
-    pd::launch_pint<T>(c, p->geom, a);
-    pd::launch_acc_reduce(c, p->geom, p->acc_part, p->b, nullptr);
-  }
-  info.pint_loops += 1;
-  info.sweeps_exec += 1;
-  // Algorithm 2 on J_l x = b (eq. 8)
-  pd::KrylovBufs kb{(int)p->nbar, p->maxit, p->klo, p->kdiag, p->kup, p->V, sizeof(T) == 4 ? p->Vf : nullptr,
-                    p->T, p->w, p->part, p->blas_grid, p->scal, p->flags};
-  CK(cudaMemsetAsync(p->T, 0, sizeof(double) * (p->maxit + 1) * p->maxit, c.stream));
-  pd::launch_vec_norm_init(c, kb, p->b);
-  pd_status st = sync_read(p);
-  if (st != PD_OK) return st;
-  const double beta = p->h_scal[0];
-  info.beta = beta;
-  info.m = 0;
-  info.breakdown = false;
-  if (!std::isfinite(beta) || p->h_flags[2]) return fail(PD_ERR_NONFINITE, "non-finite ||b|| (input contains NaN/Inf?)");
-  int m = 0;
-  double res = beta;
-  double hist[40];
-  hist[0] = beta;
-  // Algorithm 2 stops at eps * beta or maxit (Sec. 3), and here also once the eq. (13)
-  // residual stops halving: in binary32 it levels off at the rounding-noise floor of
-  // the shifted solves, and in FP64 the polynomial space K_m(K, b) can stall for
-  // many steps when J_l is far from I.  The refinement sweeps recover the rest.
-  // Window: 1 iteration in binary32 (the floor is flat), 3 in FP64 (FOM residuals
-  // are not monotone, so a single non-halving step is not yet a stall).  The stall
-  // exit only applies once ||r|| <= stall_floor * beta: above it a slow phase is
-  // convergence, not noise.
-  const int win = p->precision == PD_MIXED ? 1 : 3;
-  if (beta > 0.0) {
-    while (res > eps * beta && m < p->maxit) {
-      if (m >= win + 1 && res <= stall_floor * beta && res > 0.5 * hist[m - win]) break;
-      ++m;
-      pd::launch_arnoldi(c, kb, m);
-      // h_k = ((1 - pi_k) I + tau K)^{-1} v_{m+1} and g_k = V_m^T h_k
-      {
-        pd::PintArgs<T> a = base_args<T>(p);
-        a.rvec = vbasis<T>(p) + (size_t)m * p->nbar;
-        a.V = vbasis<T>(p);
-        a.ldv = p->nbar;
-        a.mdots = m;
-        a.gpart = p->gpart;
-        a.skip_flag = p->flags;
-        pd::launch_pint<T>(c, p->geom, a);
-      }
-      pd::launch_capacitance(c, kb, m, p->nf, p->tau, p->shift, p->wg, p->gpart, p->nblk, p->msys_part, p->k5_grid,
-                             p->srow, p->omega, p->y);
-      // z = sum_i gamma_i h_i (e_m^T S_i y_m), then eq. (13)
-      {
-        pd::PintArgs<T> a = base_args<T>(p);
-        a.rvec = vbasis<T>(p) + (size_t)m * p->nbar;
-        a.omega = p->omega;
-        a.acc_part = p->acc_part;
-        a.skip_flag = p->flags;
-        pd::launch_pint<T>(c, p->geom, a);
-        pd::launch_acc_reduce(c, p->geom, p->acc_part, p->z, p->flags);
-      }
-      info.sweeps_exec += 2;
-      info.pint_loops += 1;
-      pd::launch_project_resnorm(c, kb, m, p->z, p->tau);
-      st = sync_read(p);
-      if (st != PD_OK) return st;
-      res = p->h_scal[2];
-      hist[m] = res;
-      if (p->h_flags[2] || !std::isfinite(res)) return fail(PD_ERR_NONFINITE, "non-finite value in Algorithm 2");
-      if (p->h_flags[0]) {
-        info.breakdown = true;
-        break;
-      }
-    }
-    pd::launch_xm(c, kb, m, p->y, p->x, sizeof(T) == 4 ? p->xf : nullptr);
-  } else {
-    CK(cudaMemsetAsync(p->x, 0, sizeof(double) * p->nbar, c.stream));
-    if (p->xf) CK(cudaMemsetAsync(p->xf, 0, sizeof(float) * p->nbar, c.stream));
-  }
-  info.m = m;
-  info.rel_res = beta > 0 ? res / beta : 0.0;
-  info.converged = (beta == 0.0) || info.breakdown || res <= eps * beta;
-  // final parallel-in-time loop: Y_k = A_k^{-1} (G^_k - x_m), i.e. L - W fused
-  {
-    pd::PintArgs<T> a = base_args<T>(p);
-    a.R = S;
-    a.ldr = p->lds;
-    a.rvec = xvec<T>(p);
-    a.Y = S;
-    a.ldy = p->lds;
-    pd::launch_pint<T>(c, p->geom, a);
-  }
-  info.pint_loops += 1;
-  info.sweeps_exec += 1;
-  // U = (L - W) F^{-T}
-  int nparts = 0;
-  pd::launch_fft_c2r<T>(c, S, p->lds, p->nbar, nt, time_tw<T>(p), out, p->nbar, out_mode, p->norm_part, &nparts);
-  pd::launch_sumsq(c, p->norm_part, nparts, p->scal + 4);
-  return ctx_status(p);
-}
-
 template <typename T>
 T *res_buf(pd_plan *p);
 template <>
@@ -587,118 +479,368 @@ const cpx<double> *dst_tw<double>(pd_plan *p) { return p->twy_d; }
 template <>
 const cpx<float> *dst_tw<float>(pd_plan *p) { return p->twy_f; }
 
-// Iterative refinement around Algorithm 1 on the all-at-once residual.
-// Sweep 0 solves eq. (2) for G; sweep s >= 1 solves it for the FP64 residual
-// G - [(I + tau K) U - U Sigma_1^T] and adds the correction to U (FP64).
-// If Algorithm 2 stops with ||r_m|| > 0, the U it produces satisfies eq. (2)
-// up to exactly -r_m in the first time step (its last slice is x_m - r_m while
-// the correction used x_m), so a sweep on that residual corrects precisely the
-// Krylov error.  T = compute type of the FFTs and shifted solves (double for
-// PD_FP64, float for PD_MIXED); residuals are stored in T.
 template <typename T>
-pd_status solve_refined(pd_plan *p, const double *G, double *U, pd_stats &s) {
-  const bool fp64 = sizeof(T) == 8;
-  const int out_mode_2d = fp64 ? 0 : 2;  // inverse DFT into the 2D temporary buffer
+pd::KrylovBufs kbufs(pd_plan *p) {
+  return pd::KrylovBufs{(int)p->nbar, p->maxit, p->klo, p->kdiag, p->kup, p->V, sizeof(T) == 4 ? p->Vf : nullptr,
+                        p->T, p->w, p->part, p->blas_grid, p->scal, p->flags};
+}
+
+// Algorithm-2 stopping parameters of the first solve (kind 0) and of refinement
+// sweeps (kind 1).  Algorithm 2 stops at eps * beta or maxit (Sec. 3), and also once
+// the eq. (13) residual stops halving near the precision floor: in binary32 it
+// levels off at the rounding noise of the shifted solves, and in FP64 the polynomial
+// space K_m(K, b) can stall for many steps when J_l is far from I.  A binary32
+// refinement sweep contracts the error by ~1e-3 at best (rounding noise of the
+// residual, amplified by the solution operator), so its Algorithm 2 asks for 1e-3 and
+// stops at its first stall; FP64 refinement sweeps (only after a stall) ask for 1e-8.
+pd::KrylovCtl krylov_ctl(pd_plan *p, int kind) {
+  const bool fp64 = p->precision == PD_FP64;
+  pd::KrylovCtl k;
+  k.eps = kind == 0 ? p->eps : std::max(p->eps, fp64 ? 1e-8 : 1e-3);
+  k.stall_floor = fp64 ? 1e-6 : (kind == 0 ? 1e-3 : 1.0);
+  k.win = fp64 ? 3 : 1;
+  k.maxit = p->maxit;
+  return k;
+}
+
+pd::RefineCtl refine_ctl(pd_plan *p) {
+  const bool fp64 = p->precision == PD_FP64;
+  pd::RefineCtl r;
+  r.fp64 = fp64 ? 1 : 0;
+  r.eps_first = p->eps;
+  r.eps_refine = std::max(p->eps, fp64 ? 1e-8 : 1e-3);
+  r.refine_tol = p->refine_tol;
+  r.max_refine = p->max_refine;
+  return r;
+}
+
+// ---- the three segments of one solve -------------------------------------------
+// kind 0: the first solve, for G (Algorithm 1).  kind 1: a refinement sweep, for the
+// FP64 all-at-once residual G - [(I + tau K) U - U Sigma_1^T], added into U.  If
+// Algorithm 2 stops with ||r_m|| > 0, the U it produces satisfies eq. (2) up to
+// exactly -r_m in the first time step (its last slice is x_m - r_m while the
+// correction used x_m), so a sweep on that residual corrects precisely the Krylov
+// error.  In 2D every solve runs between one DST along y of its input and one of
+// its output.
+
+// forward DFT (eq. 5), first parallel-in-time loop with b = L F^{-T} e_l (eq. 7),
+// beta = ||b|| and v_1 (Algorithm 2, first step)
+template <typename T>
+pd_status emit_pre(pd_plan *p, int kind, const double *G, double *U, int use_handle,
+                   cudaGraphConditionalHandle hk) {
+  pd::Ctx &c = p->ctx;
+  cpx<T> *S = reinterpret_cast<cpx<T> *>(p->spec);
+  const int nt = (int)p->nt;
   T *res = res_buf<T>(p);
   T *tmp = tmp_buf<T>(p);
-  double ref2 = 0.0, rel_update = 1.0;
-  int total_m = 0, loops = 0, execs = 0, sweeps = 0;
-  SolveInfo info;
-  bool conv = false;
-  for (int sweep = 0; sweep <= p->max_refine; ++sweep) {
-    SolveInfo si;
-    pd_status st;
-    // A binary32 refinement sweep contracts the error by ~1e-3 at best (rounding
-    // noise of the residual, amplified by the solution operator), so its inner
-    // Algorithm 2 needs no more than that; the first solve uses eps_krylov.
-    // FP64 refinement sweeps (only after Algorithm 2 stalled) ask for 1e-8: the error
-    // they leave is about that times their (already small) update.
-    const double eps = sweep == 0 ? p->eps : std::max(p->eps, fp64 ? 1e-8 : 1e-3);
-    // Stall exit: FP64 near its floor (1e-6 beta); binary32 first solve once below
-    // 1e-3 beta; binary32 refinement sweeps at any level (their residuals are
-    // rounding noise and the eq. (13) estimate levels off at 1e-3..1e-2).
-    const double stall_floor = fp64 ? 1e-6 : (sweep == 0 ? 1e-3 : 1.0);
-    if (sweep == 0) {
-      if (p->dim == 1) {
-        st = run_paradiag<T, double>(p, G, U, 0, si, eps, stall_floor);
-      } else {
-        pd::launch_dst_y<double, T, T>(p->ctx, G, tmp, p->nt, p->ny, p->nx, dst_tw<T>(p), 0);
-        st = run_paradiag<T, T>(p, tmp, tmp, out_mode_2d, si, eps, stall_floor);
-        if (st == PD_OK) pd::launch_dst_y<T, double, T>(p->ctx, tmp, U, p->nt, p->ny, p->nx, dst_tw<T>(p), 0);
-      }
+  if (kind == 0) {
+    if (p->dim == 1) {
+      pd::launch_fft_r2c<T, double>(c, G, p->nbar, p->nbar, nt, time_tw<T>(p), S, p->lds);
     } else {
-      int np = 0;
-      pd::launch_residual<T>(p->ctx, G, U, res, p->nt, p->ny, p->nx, p->tau, p->xlo, p->xdiag, p->xup, p->ylo,
-                             p->ydiag, p->yup, nullptr, &np);
-      if (p->dim == 1) {
-        st = run_paradiag<T, T>(p, res, U, 1, si, eps, stall_floor);
-      } else {
-        pd::launch_dst_y<T, T, T>(p->ctx, res, tmp, p->nt, p->ny, p->nx, dst_tw<T>(p), 0);
-        st = run_paradiag<T, T>(p, tmp, tmp, out_mode_2d, si, eps, stall_floor);
-        if (st == PD_OK) pd::launch_dst_y<T, double, T>(p->ctx, tmp, U, p->nt, p->ny, p->nx, dst_tw<T>(p), 1);
-      }
+      pd::launch_dst_y<double, T, T>(c, G, tmp, p->nt, p->ny, p->nx, dst_tw<T>(p), 0);
+      pd::launch_fft_r2c<T, T>(c, tmp, p->nbar, p->nbar, nt, time_tw<T>(p), S, p->lds);
     }
-    if (st != PD_OK) return st;
-    if (sweep == 0) {
-      CK(cudaMemcpyAsync(p->b0, p->b, sizeof(double) * p->nbar, cudaMemcpyDeviceToDevice, p->ctx.stream));
-      CK(cudaMemcpyAsync(p->x0, p->x, sizeof(double) * p->nbar, cudaMemcpyDeviceToDevice, p->ctx.stream));
-    }
-    st = sync_read(p);
-    if (st != PD_OK) return st;
-    const double d2 = p->h_scal[4];
-    if (!std::isfinite(d2)) return fail(PD_ERR_NONFINITE, "non-finite update in refinement sweep %d", sweep);
-    if (sweeps < 16) {
-      s.sweep_krylov_iters[sweeps] = si.m;
-      s.sweep_rel_update[sweeps] = ref2 > 0 || sweep == 0 ? (sweep == 0 ? 1.0 : std::sqrt(d2 / ref2)) : 0.0;
-      s.sweep_krylov_rel_resnorm[sweeps] = si.rel_res;
-    }
-    ++sweeps;
-    total_m += si.m;
-    loops += si.pint_loops;
-    execs += si.sweeps_exec;
-    info = si;
-    if (sweep == 0) ref2 = d2;
-    const double prev_update = rel_update;
-    rel_update = ref2 > 0 ? std::sqrt(d2 / ref2) : 0.0;
-    if (ref2 == 0.0) {
-      conv = true;
-      break;
-    }
-    // FP64: Algorithm 2 met its tolerance, so this sweep's correction is exact to
-    // working accuracy (sweep 0: the paper's Algorithm 1 itself); a refinement sweep
-    // leaves about eps * ||delta_s||.
-    if (fp64 && si.converged && (sweep == 0 || eps * rel_update <= p->refine_tol)) {
-      conv = true;
-      break;
-    }
-    // Each refinement sweep contracts the error by rho ~ ||delta_s|| / ||delta_{s-1}||
-    // (s >= 2: delta_1 / delta_0 is the first solve's error, not a contraction), so
-    // the error left after sweep s is about rho * ||delta_s||: stop once that
-    // predicted remainder (relative to ||U|| ~ ||delta_0||) is below refine_tol and
-    // the last update itself is small.
-    if (sweep > 0) {
-      const double rho = prev_update > 0 ? rel_update / prev_update : 0.0;
-      if ((sweep >= 2 && rho * rel_update <= p->refine_tol && rel_update <= 1e-7) || rel_update <= 1e-15) {
-        conv = true;
-        break;
-      }
-      // No longer contracting: the rounding floor of the residual is reached.
-      if (sweep > 1 && rho > 0.5) {
-        conv = rel_update <= 1e-10;
-        break;
-      }
+  } else {
+    pd::launch_residual<T>(c, G, U, res, p->nt, p->ny, p->nx, p->rxl, p->rxd, p->rxu, p->ryl, p->ryd, p->ryu);
+    if (p->dim == 1) {
+      pd::launch_fft_r2c<T, T>(c, res, p->nbar, p->nbar, nt, time_tw<T>(p), S, p->lds);
+    } else {
+      pd::launch_dst_y<T, T, T>(c, res, tmp, p->nt, p->ny, p->nx, dst_tw<T>(p), 0);
+      pd::launch_fft_r2c<T, T>(c, tmp, p->nbar, p->nbar, nt, time_tw<T>(p), S, p->lds);
     }
   }
-  s.krylov_iters = info.m;
-  s.krylov_iters_total = total_m;
-  s.pint_loops = loops;
-  s.shifted_sweeps = execs;
+  pd::PintArgs<T> a = base_args<T>(p);
+  a.R = S;
+  a.ldr = p->lds;
+  a.omega = p->wg;
+  a.acc_part = p->acc_part;
+  pd::launch_pint<T>(c, p->geom, a);
+  pd::launch_acc_reduce(c, p->geom, p->acc_part, p->b, nullptr);
+  CK(cudaMemsetAsync(p->T, 0, sizeof(double) * (p->maxit + 1) * p->maxit, c.stream));
+  pd::KrylovBufs kb = kbufs<T>(p);
+  pd::launch_vec_norm_init(c, kb, p->b, use_handle, hk);
+  return PD_OK;
+}
+
+// one step of Algorithm 2 (m read on the device)
+template <typename T>
+pd_status emit_iter(pd_plan *p, int kind, int use_handle, cudaGraphConditionalHandle hk) {
+  pd::Ctx &c = p->ctx;
+  pd::KrylovBufs kb = kbufs<T>(p);
+  pd::launch_arnoldi(c, kb);
+  {  // h_k = ((1 - pi_k) I + tau K)^{-1} v_{m+1} and g_k = V_m^T h_k
+    pd::PintArgs<T> a = base_args<T>(p);
+    a.mcount = p->flags + pd::F_M;
+    a.want_dots = 1;
+    a.mdots_max = p->maxit;
+    a.V = vbasis<T>(p);
+    a.ldv = p->nbar;
+    a.gpart = p->gpart;
+    a.skip_flag = p->flags + pd::F_BREAK;
+    pd::launch_pint<T>(c, p->geom, a);
+  }
+  pd::launch_capacitance(c, kb, p->nf, p->tau, p->shift, p->wg, p->gpart, p->nblk, p->msys_part, p->k5_grid,
+                         p->srow, p->omega, p->y);
+  {  // z = sum_i gamma_i h_i (e_m^T S_i y_m), then eq. (13)
+    pd::PintArgs<T> a = base_args<T>(p);
+    a.mcount = p->flags + pd::F_M;
+    a.want_dots = 0;
+    a.V = vbasis<T>(p);
+    a.ldv = p->nbar;
+    a.omega = p->omega;
+    a.acc_part = p->acc_part;
+    a.skip_flag = p->flags + pd::F_BREAK;
+    pd::launch_pint<T>(c, p->geom, a);
+    pd::launch_acc_reduce(c, p->geom, p->acc_part, p->z, p->flags + pd::F_BREAK);
+  }
+  pd::launch_project_resnorm(c, kb, p->z, p->tau);
+  pd::launch_krylov_decide(c, p->scal, p->flags, krylov_ctl(p, kind), use_handle, hk);
+  return PD_OK;
+}
+
+// x_m = V_m y_m; final parallel-in-time loop Y_k = A_k^{-1} (G^_k - x_m) (L - W fused);
+// U = (L - W) F^{-T}; ||delta||^2; refinement decision
+template <typename T>
+pd_status emit_post(pd_plan *p, int kind, double *U, int use_handle, cudaGraphConditionalHandle hr) {
+  pd::Ctx &c = p->ctx;
+  cpx<T> *S = reinterpret_cast<cpx<T> *>(p->spec);
+  const int nt = (int)p->nt;
+  const bool fp64 = sizeof(T) == 8;
+  pd::KrylovBufs kb = kbufs<T>(p);
+  pd::launch_xm(c, kb, p->y, p->x, sizeof(T) == 4 ? p->xf : nullptr);
+  pd::PintArgs<T> a = base_args<T>(p);
+  a.R = S;
+  a.ldr = p->lds;
+  a.rvec = xvec<T>(p);
+  a.Y = S;
+  a.ldy = p->lds;
+  pd::launch_pint<T>(c, p->geom, a);
+  int nparts = 0;
+  if (p->dim == 1) {
+    pd::launch_fft_c2r<T>(c, S, p->lds, p->nbar, nt, time_tw<T>(p), U, p->nbar, kind == 0 ? 0 : 1, p->norm_part,
+                          &nparts);
+  } else {
+    T *tmp = tmp_buf<T>(p);
+    pd::launch_fft_c2r<T>(c, S, p->lds, p->nbar, nt, time_tw<T>(p), tmp, p->nbar, fp64 ? 0 : 2, p->norm_part,
+                          &nparts);
+    pd::launch_dst_y<T, double, T>(c, tmp, U, p->nt, p->ny, p->nx, dst_tw<T>(p), kind == 0 ? 0 : 1);
+  }
+  pd::launch_sumsq(c, p->norm_part, nparts, p->scal + pd::S_D2);
+  if (kind == 0) {
+    CK(cudaMemcpyAsync(p->b0, p->b, sizeof(double) * p->nbar, cudaMemcpyDeviceToDevice, c.stream));
+    CK(cudaMemcpyAsync(p->x0, p->x, sizeof(double) * p->nbar, cudaMemcpyDeviceToDevice, c.stream));
+  }
+  pd::launch_refine_decide(c, p->scal, p->flags, refine_ctl(p), use_handle, hr);
+  return PD_OK;
+}
+
+// Host-driven loops (timing mode, or when graphs are unavailable): the same kernels,
+// with the host reading the control block after each step.
+template <typename T>
+pd_status solve_hostloop(pd_plan *p, const double *G, double *U) {
+  pd::Ctx &c = p->ctx;
+  pd_status st;
+  pd::launch_solve_reset(c, p->scal, p->flags);
+  for (int kind = 0;; kind = 1) {
+    if ((st = emit_pre<T>(p, kind, G, U, 0, 0)) != PD_OK) return st;
+    if ((st = sync_read(p)) != PD_OK) return st;
+    while (!p->h_flags[pd::F_KSTOP]) {
+      if ((st = emit_iter<T>(p, kind, 0, 0)) != PD_OK) return st;
+      if ((st = sync_read(p)) != PD_OK) return st;
+    }
+    if ((st = emit_post<T>(p, kind, U, 0, 0)) != PD_OK) return st;
+    if ((st = sync_read(p)) != PD_OK) return st;
+    if (p->h_flags[pd::F_RSTOP]) break;
+  }
+  return ctx_status(p);
+}
+
+// ---- CUDA graph of the whole solve -------------------------------------------------
+// top:   reset, pre(0), WHILE_k0 { iter(0) }, post(0),
+//        WHILE_R { pre(1), WHILE_k1 { iter(1) }, post(1) }
+// The conditionals are set on the device by the init / decide kernels, so one graph
+// launch runs the solve with a single host synchronisation at the end.
+
+#define GK(call)                   \
+  do {                             \
+    cudaError_t e_ = (call);       \
+    if (e_ != cudaSuccess) return e_; \
+  } while (0)
+
+// Append a WHILE node after the capture frontier of `s`; return its body graph.
+cudaError_t splice_while(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraph_t *body) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t *deps = nullptr;
+  size_t nd = 0;
+  GK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
+  if (cs != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  GK(cudaGraphAddNode(&node, g, deps, nullptr, nd, &np));
+  *body = np.conditional.phGraph_out[0];
+  GK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t capture_iter_body(pd_plan *p, cudaGraph_t body, cudaStream_t s, int kind, cudaGraphConditionalHandle hk) {
+  GK(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  cudaStream_t keep = p->ctx.stream;
+  p->ctx.stream = s;
+  const pd_status st = emit_iter<T>(p, kind, 1, hk);
+  p->ctx.stream = keep;
+  cudaGraph_t out = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(s, &out);
+  if (st != PD_OK || p->ctx.err != cudaSuccess) return cudaErrorUnknown;
+  return e;
+}
+
+template <typename T>
+cudaError_t build_graph(pd_plan *p, const double *G, double *U, cudaGraph_t *gout) {
+  cudaStream_t s0 = p->cap[0], s1 = p->cap[1], s2 = p->cap[2];
+  cudaStream_t keep = p->ctx.stream;
+  cudaGraph_t g = nullptr;
+  GK(cudaStreamBeginCapture(s0, cudaStreamCaptureModeRelaxed));
+  cudaError_t err = cudaSuccess;
+  do {
+    cudaStreamCaptureStatus cs;
+    if ((err = cudaStreamGetCaptureInfo(s0, &cs, nullptr, &g, nullptr, nullptr, nullptr)) != cudaSuccess) break;
+    cudaGraphConditionalHandle hk0, hR, hk1;
+    if ((err = cudaGraphConditionalHandleCreate(&hk0, g, 1, cudaGraphCondAssignDefault)) != cudaSuccess) break;
+    if ((err = cudaGraphConditionalHandleCreate(&hR, g, 0, cudaGraphCondAssignDefault)) != cudaSuccess) break;
+    p->ctx.stream = s0;
+    int64_t l0 = p->ctx.launches;
+    pd::launch_solve_reset(p->ctx, p->scal, p->flags);
+    if (emit_pre<T>(p, 0, G, U, 1, hk0) != PD_OK) { err = cudaErrorUnknown; break; }
+    p->seg.pre0 = p->ctx.launches - l0;
+    cudaGraph_t body;
+    if ((err = splice_while(s0, hk0, &body)) != cudaSuccess) break;
+    l0 = p->ctx.launches;
+    if ((err = capture_iter_body<T>(p, body, s1, 0, hk0)) != cudaSuccess) break;
+    p->seg.iter0 = p->ctx.launches - l0;
+    p->ctx.stream = s0;
+    l0 = p->ctx.launches;
+    if (emit_post<T>(p, 0, U, 1, hR) != PD_OK) { err = cudaErrorUnknown; break; }
+    p->seg.post0 = p->ctx.launches - l0;
+    cudaGraph_t bodyR;
+    if ((err = splice_while(s0, hR, &bodyR)) != cudaSuccess) break;
+    if ((err = cudaGraphConditionalHandleCreate(&hk1, bodyR, 1, cudaGraphCondAssignDefault)) != cudaSuccess) break;
+    // refinement body: pre(1), WHILE_k1 { iter(1) }, post(1), captured on s1
+    if ((err = cudaStreamBeginCaptureToGraph(s1, bodyR, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed)) !=
+        cudaSuccess)
+      break;
+    p->ctx.stream = s1;
+    l0 = p->ctx.launches;
+    bool ok = emit_pre<T>(p, 1, G, U, 1, hk1) == PD_OK;
+    p->seg.pre1 = p->ctx.launches - l0;
+    cudaGraph_t body1;
+    if (ok) ok = splice_while(s1, hk1, &body1) == cudaSuccess;
+    l0 = p->ctx.launches;
+    if (ok) ok = capture_iter_body<T>(p, body1, s2, 1, hk1) == cudaSuccess;
+    p->seg.iter1 = p->ctx.launches - l0;
+    p->ctx.stream = s1;
+    l0 = p->ctx.launches;
+    if (ok) ok = emit_post<T>(p, 1, U, 1, hR) == PD_OK;
+    p->seg.post1 = p->ctx.launches - l0;
+    cudaGraph_t outR = nullptr;
+    const cudaError_t e1 = cudaStreamEndCapture(s1, &outR);
+    if (!ok || e1 != cudaSuccess || p->ctx.err != cudaSuccess) {
+      err = cudaErrorUnknown;
+      break;
+    }
+  } while (false);
+  p->ctx.stream = keep;
+  cudaGraph_t out = nullptr;
+  const cudaError_t e0 = cudaStreamEndCapture(s0, &out);
+  if (err == cudaSuccess) err = e0;
+  if (err != cudaSuccess) {
+    if (out) cudaGraphDestroy(out);
+    return err;
+  }
+  *gout = out;
+  return cudaSuccess;
+}
+
+void drop_graph(pd_plan *p) {
+  if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  p->gexec = nullptr;
+  p->g_G = nullptr;
+  p->g_U = nullptr;
+}
+
+template <typename T>
+pd_status solve_graph(pd_plan *p, const double *G, double *U, bool *used) {
+  *used = false;
+  if (p->graph_failed || p->ctx.timing) return PD_OK;
+  if (!p->gexec || p->g_G != G || p->g_U != U) {
+    drop_graph(p);
+    const int64_t l0 = p->ctx.launches;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = build_graph<T>(p, G, U, &g);
+    p->ctx.launches = l0;  // capture launches nothing
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&p->gexec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess || p->ctx.err != cudaSuccess) {
+      // graphs unavailable here: use the host-driven loops from now on
+      cudaGetLastError();
+      p->ctx.err = cudaSuccess;
+      p->gexec = nullptr;
+      p->graph_failed = true;
+      return PD_OK;
+    }
+    p->g_G = G;
+    p->g_U = U;
+  }
+  CK(cudaGraphLaunch(p->gexec, p->ctx.stream));
+  pd_status st = sync_read(p);
+  if (st != PD_OK) return st;
+  // kernels run = fixed segments + m steps of Algorithm 2 per solve
+  const int sweeps = p->h_flags[pd::F_SWEEP];
+  int64_t n = p->seg.pre0 + p->seg.post0 + (int64_t)p->seg.iter0 * p->h_flags[pd::F_SWM];
+  for (int s = 1; s < sweeps && s < 16; ++s)
+    n += p->seg.pre1 + p->seg.post1 + (int64_t)p->seg.iter1 * p->h_flags[pd::F_SWM + s];
+  p->ctx.launches += n;
+  *used = true;
+  return PD_OK;
+}
+
+template <typename T>
+pd_status solve_refined(pd_plan *p, const double *G, double *U, pd_stats &s) {
+  bool used = false;
+  pd_status st = p->use_graphs ? solve_graph<T>(p, G, U, &used) : PD_OK;
+  if (st != PD_OK) return st;
+  if (!used) {
+    if ((st = solve_hostloop<T>(p, G, U)) != PD_OK) return st;
+  }
+  const int *f = p->h_flags;
+  const double *sc = p->h_scal;
+  const int sweeps = f[pd::F_SWEEP];
+  const int last = std::min(std::max(sweeps - 1, 0), 15);
   s.refine_sweeps = sweeps;
-  s.breakdown = info.breakdown;
-  s.beta = info.beta;
-  s.krylov_rel_resnorm = info.rel_res;
-  s.rel_update = sweeps > 1 ? rel_update : 0.0;
-  return conv ? PD_OK : fail(PD_ERR_NOT_CONVERGED, "refinement did not reach refine_tol in %d sweeps", sweeps);
+  s.krylov_iters = f[pd::F_SWM + last];
+  s.krylov_iters_total = f[pd::F_MTOT];
+  s.pint_loops = 0;
+  s.shifted_sweeps = 0;
+  for (int i = 0; i < sweeps && i < 16; ++i) {
+    s.sweep_krylov_iters[i] = f[pd::F_SWM + i];
+    s.sweep_krylov_rel_resnorm[i] = sc[pd::S_SWRES + i];
+    s.sweep_rel_update[i] = sc[pd::S_SWUPD + i];
+    s.pint_loops += f[pd::F_SWM + i] + 2;
+    s.shifted_sweeps += 2 * f[pd::F_SWM + i] + 2;
+  }
+  s.breakdown = f[pd::F_BREAK];
+  s.beta = sc[pd::S_SWBETA + last];
+  s.krylov_rel_resnorm = sc[pd::S_SWRES + last];
+  s.rel_update = sweeps > 1 ? sc[pd::S_UPD] : 0.0;
+  s.graph = used ? 1 : 0;
+  if (f[pd::F_NONFIN]) return fail(PD_ERR_NONFINITE, "non-finite value met (input contains NaN/Inf?)");
+  return f[pd::F_RCONV] ? PD_OK
+                        : fail(PD_ERR_NOT_CONVERGED, "refinement did not reach refine_tol in %d solves", sweeps);
 }
 
 pd_status check_plan(pd_plan *p) {
@@ -756,9 +898,15 @@ pd_status paradiag_plan(const pd_desc *desc, void *workspace, size_t workspace_b
     paradiag_destroy(p);
     return s;
   };
-  if (cudaMallocHost(&p->h_scal, 16 * sizeof(double)) != cudaSuccess ||
-      cudaMallocHost(&p->h_flags, 16 * sizeof(int)) != cudaSuccess)
+  if (cudaMallocHost(&p->h_scal, pd::kScalWords * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost(&p->h_flags, pd::kFlagWords * sizeof(int)) != cudaSuccess)
     return cleanup(fail(PD_ERR_OOM, "cudaMallocHost failed"));
+  std::memset(p->h_scal, 0, pd::kScalWords * sizeof(double));
+  std::memset(p->h_flags, 0, pd::kFlagWords * sizeof(int));
+  for (int i = 0; i < 3; ++i)
+    if (cudaStreamCreateWithFlags(&p->cap[i], cudaStreamNonBlocking) != cudaSuccess)
+      return cleanup(fail(PD_ERR_CUDA, "cudaStreamCreateWithFlags failed"));
+  p->use_graphs = desc->no_graph ? 0 : 1;
   if (cudaEventCreate(&p->ev0) != cudaSuccess || cudaEventCreate(&p->ev1) != cudaSuccess)
     return cleanup(fail(PD_ERR_CUDA, "cudaEventCreate failed"));
 
@@ -794,6 +942,18 @@ pd_status paradiag_plan(const pd_desc *desc, void *workspace, size_t workspace_b
     fdiag[j] = (float)tdiag[j];
     fup[j] = (float)tup[j];
   }
+  std::vector<double> rxl(p->nx), rxd(p->nx), rxu(p->nx), ryl(p->ny), ryd(p->ny), ryu(p->ny);
+  for (int64_t i = 0; i < p->nx; ++i) {
+    rxl[i] = p->tau * h.xlo[i];
+    rxd[i] = 1.0 + p->tau * h.xdiag[i];
+    rxu[i] = p->tau * h.xup[i];
+  }
+  if (p->dim == 2)
+    for (int64_t i = 0; i < p->ny; ++i) {
+      ryl[i] = p->tau * h.ylo[i];
+      ryd[i] = p->tau * h.ydiag[i];
+      ryu[i] = p->tau * h.yup[i];
+    }
   cudaStream_t s = p->ctx.stream;
   if ((st = upload(p->shift, shift.data(), nf, s)) || (st = upload(p->wg, wg.data(), nf, s)) ||
       (st = upload(p->klo, h.lo.data(), nbar, s)) || (st = upload(p->kdiag, h.diag.data(), nbar, s)) ||
@@ -803,6 +963,12 @@ pd_status paradiag_plan(const pd_desc *desc, void *workspace, size_t workspace_b
       (st = upload(p->tup_f, fup.data(), nbar, s)) || (st = upload(p->xlo, h.xlo.data(), p->nx, s)) ||
       (st = upload(p->xdiag, h.xdiag.data(), p->nx, s)) || (st = upload(p->xup, h.xup.data(), p->nx, s)) ||
       (st = upload(p->tw_d, tw.data(), ntw, s)) || (st = upload(p->tw_f, twf.data(), ntw, s)))
+    return cleanup(st);
+  if ((st = upload(p->rxl, rxl.data(), p->nx, s)) || (st = upload(p->rxd, rxd.data(), p->nx, s)) ||
+      (st = upload(p->rxu, rxu.data(), p->nx, s)))
+    return cleanup(st);
+  if (p->dim == 2 && ((st = upload(p->ryl, ryl.data(), p->ny, s)) || (st = upload(p->ryd, ryd.data(), p->ny, s)) ||
+                      (st = upload(p->ryu, ryu.data(), p->ny, s))))
     return cleanup(st);
   if (p->dim == 2) {
     const int N = (int)(2 * (p->ny + 1));
@@ -818,6 +984,8 @@ pd_status paradiag_plan(const pd_desc *desc, void *workspace, size_t workspace_b
         (st = upload(p->twy_f, tyf.data(), N / 2, s)))
       return cleanup(st);
   }
+  if (cudaMemsetAsync(p->flags, 0, pd::kFlagWords * sizeof(int), s) != cudaSuccess)
+    return cleanup(fail(PD_ERR_CUDA, "plan upload failed"));
   if (cudaStreamSynchronize(s) != cudaSuccess) return cleanup(fail(PD_ERR_CUDA, "plan upload failed"));
   *out = p;
   return PD_OK;
@@ -826,6 +994,9 @@ pd_status paradiag_plan(const pd_desc *desc, void *workspace, size_t workspace_b
 pd_status paradiag_destroy(pd_plan *p) {
   if (!p) return PD_OK;
   if (p->ctx.stream) cudaStreamSynchronize(p->ctx.stream);
+  drop_graph(p);
+  for (int i = 0; i < 3; ++i)
+    if (p->cap[i]) cudaStreamDestroy(p->cap[i]);
   p->ctx.release();
   if (p->own_ws && p->ws) cudaFree(p->ws);
   if (p->h_scal) cudaFreeHost(p->h_scal);

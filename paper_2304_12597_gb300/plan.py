@@ -31,7 +31,7 @@ class Plan:
 
     def __init__(self, *, dim, nx, nt, tau, k_lo, k_diag, k_up, ny=1, k_lo_y=None, k_diag_y=None,
                  k_up_y=None, precision="mixed", maxit=0, eps_krylov=0.0, max_refine=0, refine_tol=0.0,
-                 host_io=False, device=None, stream=None, workspace="torch"):
+                 host_io=False, no_graph=False, device=None, stream=None, workspace="torch"):
         import torch
 
         self._torch = torch
@@ -58,6 +58,7 @@ class Plan:
         d.alpha = 1.0
         d.stream = ctypes.c_void_p(self.stream.cuda_stream)
         d.host_io = 1 if host_io else 0
+        d.no_graph = 1 if no_graph else 0
         self.desc = d
         self.workspace_bytes = B.paradiag_workspace_size(d)
         self.handle = None

@@ -256,3 +256,22 @@ def test_full_size_2d_config3(pd, cfg3_ref, prec):
     P, Uref = cfg3_ref
     U, st, _, _ = _solve(pd, P, prec)
     assert R.rel_err(U, Uref) <= TOL[prec], st
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("P", [W.heat1d_forced(255, 64, seed=4), W.heat2d_smooth(15, 16, 0.1, seed=2),
+                               W.advdiff1d_pulse(127, 32, 0.3, seed=5)], ids=lambda p: p.name)
+def test_graph_solve_equals_host_driven_solve(pd, prec, P):
+    """One CUDA-graph launch with device-side loop control runs exactly the kernels the
+    host-driven loops run: identical U and statistics."""
+    G = torch.from_numpy(P.G).to(dev())
+    with pd.Plan.from_problem(P, precision=prec, device=dev()) as pg, \
+            pd.Plan.from_problem(P, precision=prec, device=dev(), no_graph=True) as ph:
+        Ug, sg = pg.solve(G)
+        Ug2, sg2 = pg.solve(G)  # graph reused
+        Uh, sh = ph.solve(G)
+    assert sg["graph"] == 1 and sg2["graph"] == 1 and sh["graph"] == 0
+    assert torch.equal(Ug, Uh) and torch.equal(Ug2, Uh)
+    for key in ("refine_sweeps", "krylov_iters_total", "sweep_krylov_iters", "kernel_launches"):
+        assert sg[key] == sh[key], key
+    assert R.rel_err(Ug.cpu().numpy(), R.be_solve_refined(P)) <= TOL[prec]
