@@ -12,7 +12,7 @@
 // on the host in FP64 (rounded to FP32 for the mixed path).
 #include <algorithm>
 
-#include "pd_internal.h"
+#include "pd_control.cuh"
 
 namespace pd {
 
@@ -68,24 +68,10 @@ __device__ void fft_smem(cpx<T> *buf, int n, int logn, int nseries, const cpx<T>
   }
 }
 
-template <typename T, typename Tin, int TX>
-__global__ void __launch_bounds__(256) k_fft_r2c(const Tin *__restrict__ X, int64_t ldx, int64_t ncols,
-                                                 int n, int logn, const cpx<T> *__restrict__ tw,
-                                                 cpx<T> *__restrict__ S, int64_t lds) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  cpx<T> *buf = reinterpret_cast<cpx<T> *>(smraw);
-  const int64_t x0 = (int64_t)blockIdx.x * TX;
-  const int total = n * TX;
-  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int j = idx / TX;
-    const int c = idx - j * TX;
-    const int64_t col = x0 + c;
-    const T v = (col < ncols) ? (T)X[(int64_t)j * ldx + col] : T(0);
-    T *slot = reinterpret_cast<T *>(&buf[((size_t)(c >> 1) << logn) + bitrev(j, logn)]);
-    slot[c & 1] = v;
-  }
-  __syncthreads();
-  fft_smem<T>(buf, n, logn, TX >> 1, tw);
+// Separate the packed spectra and store the half spectrum of the tile's columns.
+template <typename T, int TX>
+__device__ void r2c_store(const cpx<T> *buf, int n, int logn, int64_t x0, int64_t ncols, cpx<T> *__restrict__ S,
+                          int64_t lds) {
   const int nf = (n >> 1) + 1;
   const int tot2 = nf * TX;
   for (int idx = threadIdx.x; idx < tot2; idx += blockDim.x) {
@@ -105,13 +91,70 @@ __global__ void __launch_bounds__(256) k_fft_r2c(const Tin *__restrict__ X, int6
   }
 }
 
+template <typename T, typename Tin, int TX>
+__global__ void __launch_bounds__(256) k_fft_r2c(const Tin *__restrict__ X, int64_t ldx, int64_t ncols,
+                                                 int n, int logn, const cpx<T> *__restrict__ tw,
+                                                 cpx<T> *__restrict__ S, int64_t lds) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cpx<T> *buf = reinterpret_cast<cpx<T> *>(smraw);
+  const int64_t x0 = (int64_t)blockIdx.x * TX;
+  const int total = n * TX;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int j = idx / TX;
+    const int c = idx - j * TX;
+    const int64_t col = x0 + c;
+    const T v = (col < ncols) ? (T)X[(int64_t)j * ldx + col] : T(0);
+    T *slot = reinterpret_cast<T *>(&buf[((size_t)(c >> 1) << logn) + bitrev(j, logn)]);
+    slot[c & 1] = v;
+  }
+  __syncthreads();
+  fft_smem<T>(buf, n, logn, TX >> 1, tw);
+  r2c_store<T, TX>(buf, n, logn, x0, ncols, S, lds);
+}
+
+// Same transform of the 1D FP64 residual r = G_t + u_{t-1} - (I + tau K) u_t, formed
+// while the tile is loaded (rx = (tau lo, 1 + tau diag, tau up)); neighbour columns
+// outside the tile come from L1/L2.
+template <typename T, int TX>
+__global__ void __launch_bounds__(256) k_fft_r2c_res(const double *__restrict__ G, const double *__restrict__ U,
+                                                     int64_t ncols, int n, int logn, const double *__restrict__ rxl,
+                                                     const double *__restrict__ rxd,
+                                                     const double *__restrict__ rxu,
+                                                     const cpx<T> *__restrict__ tw, cpx<T> *__restrict__ S,
+                                                     int64_t lds) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cpx<T> *buf = reinterpret_cast<cpx<T> *>(smraw);
+  const int64_t x0 = (int64_t)blockIdx.x * TX;
+  const int total = n * TX;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int j = idx / TX;
+    const int c = idx - j * TX;
+    const int64_t col = x0 + c;
+    T v = T(0);
+    if (col < ncols) {
+      const double *u = U + (int64_t)j * ncols;
+      double au = rxd[col] * u[col];
+      if (col > 0) au = fma(rxl[col], u[col - 1], au);
+      if (col + 1 < ncols) au = fma(rxu[col], u[col + 1], au);
+      double g = G[(int64_t)j * ncols + col];
+      if (j > 0) g += u[col - ncols];
+      v = (T)(g - au);
+    }
+    T *slot = reinterpret_cast<T *>(&buf[((size_t)(c >> 1) << logn) + bitrev(j, logn)]);
+    slot[c & 1] = v;
+  }
+  __syncthreads();
+  fft_smem<T>(buf, n, logn, TX >> 1, tw);
+  r2c_store<T, TX>(buf, n, logn, x0, ncols, S, lds);
+}
+
 // Inverse: Z[k] = A[k] + i B[k] over the full spectrum (A[n-k] = conj A[k]);
 // z = IDFT(Z) = conj(DFT(conj Z)) / n; column 2p = Re z, column 2p+1 = Im z.
 template <typename T, int TX>
 __global__ void __launch_bounds__(256) k_fft_c2r(const cpx<T> *__restrict__ S, int64_t lds, int64_t ncols,
                                                  int n, int logn, const cpx<T> *__restrict__ tw,
                                                  void *__restrict__ out, int64_t ldo, int mode,
-                                                 double *__restrict__ norm_part) {
+                                                 double *__restrict__ norm_part, StepFinish fin) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cpx<T> *buf = reinterpret_cast<cpx<T> *>(smraw);
   const int64_t x0 = (int64_t)blockIdx.x * TX;
@@ -167,6 +210,25 @@ __global__ void __launch_bounds__(256) k_fft_c2r(const cpx<T> *__restrict__ S, i
       double t = 0.0;
       for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
       norm_part[blockIdx.x] = t;
+    }
+    if (fin.enabled) {
+      // the last CTA to finish (no CTA waits) sums the squares and decides
+      __shared__ int last;
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) last = atomicAdd(fin.counter, 1) == (int)gridDim.x - 1;
+      __syncthreads();
+      if (last && threadIdx.x < 32) {
+        __threadfence();
+        double t = 0.0;
+        for (int i = threadIdx.x; i < (int)gridDim.x; i += 32) t += norm_part[i];
+        t = warp_sum(t);
+        if (threadIdx.x == 0) {
+          fin.scal[S_D2] = t;
+          *fin.counter = 0;
+          refine_decide(fin.scal, fin.flags, fin.rc, fin.use_handle, fin.h);
+        }
+      }
     }
   }
 }
@@ -264,8 +326,27 @@ void launch_fft_r2c(Ctx &c, const Tin *X, int64_t ldx, int64_t ncols, int n, con
 }
 
 template <typename T>
+void launch_fft_r2c_residual(Ctx &c, const double *G, const double *U, int64_t ncols, int n, const double *rxl,
+                             const double *rxd, const double *rxu, const cpx<T> *tw, cpx<T> *S, int64_t lds) {
+  const int logn = ilog2(n);
+  const int TX = pick_tx<T>(n, sizeof(T) == 8 ? 8 : 16, ncols);
+  const size_t smem = (size_t)(TX / 2) * n * sizeof(cpx<T>);
+  const int grid = (int)((ncols + TX - 1) / TX);
+  const double bytes = (double)n * ncols * 16.0 + (double)(n / 2 + 1) * ncols * sizeof(cpx<T>);
+  c.launch(sizeof(T) == 8 ? "fft_r2c_res_f64" : "fft_r2c_res_f32", bytes, [&] {
+    PD_TX_DISPATCH(TX, {
+      if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_fft_r2c_res<T, kTX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k_fft_r2c_res<T, kTX><<<grid, 256, smem, c.stream>>>(G, U, ncols, n, logn, rxl, rxd, rxu, tw, S, lds);
+    })
+  });
+}
+
+template <typename T>
 void launch_fft_c2r(Ctx &c, const cpx<T> *S, int64_t lds, int64_t ncols, int n, const cpx<T> *tw,
-                    void *out, int64_t ldo, int mode, double *norm_part, int *nparts) {
+                    void *out, int64_t ldo, int mode, double *norm_part, int *nparts, const StepFinish *finp) {
+  StepFinish fin{};
+  if (finp && norm_part) fin = *finp;
   const int logn = ilog2(n);
   const int TX = pick_tx<T>(n, sizeof(T) == 8 ? 8 : 16, ncols);
   const size_t smem = (size_t)(TX / 2) * n * sizeof(cpx<T>);
@@ -277,7 +358,8 @@ void launch_fft_c2r(Ctx &c, const cpx<T> *S, int64_t lds, int64_t ncols, int n, 
     PD_TX_DISPATCH(TX, {
       if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_fft_c2r<T, kTX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      k_fft_c2r<T, kTX><<<grid, 256, smem, c.stream>>>(S, lds, ncols, n, logn, tw, out, ldo, mode, norm_part);
+      k_fft_c2r<T, kTX><<<grid, 256, smem, c.stream>>>(S, lds, ncols, n, logn, tw, out, ldo, mode, norm_part,
+                                                         fin);
     })
   });
 }
@@ -309,9 +391,15 @@ template void launch_fft_r2c<float, double>(Ctx &, const double *, int64_t, int6
 template void launch_fft_r2c<float, float>(Ctx &, const float *, int64_t, int64_t, int, const cpx<float> *,
                                            cpx<float> *, int64_t);
 template void launch_fft_c2r<double>(Ctx &, const cpx<double> *, int64_t, int64_t, int, const cpx<double> *,
-                                     void *, int64_t, int, double *, int *);
+                                     void *, int64_t, int, double *, int *, const StepFinish *);
 template void launch_fft_c2r<float>(Ctx &, const cpx<float> *, int64_t, int64_t, int, const cpx<float> *,
-                                    void *, int64_t, int, double *, int *);
+                                    void *, int64_t, int, double *, int *, const StepFinish *);
+template void launch_fft_r2c_residual<double>(Ctx &, const double *, const double *, int64_t, int, const double *,
+                                              const double *, const double *, const cpx<double> *, cpx<double> *,
+                                              int64_t);
+template void launch_fft_r2c_residual<float>(Ctx &, const double *, const double *, int64_t, int, const double *,
+                                             const double *, const double *, const cpx<float> *, cpx<float> *,
+                                             int64_t);
 template void launch_dst_y<double, double, double>(Ctx &, const double *, double *, int64_t, int64_t, int64_t,
                                                    const cpx<double> *, int);
 template void launch_dst_y<double, float, float>(Ctx &, const double *, float *, int64_t, int64_t, int64_t,

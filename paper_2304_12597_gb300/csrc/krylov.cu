@@ -22,7 +22,7 @@
 
 #include <cooperative_groups.h>
 
-#include "pd_internal.h"
+#include "pd_control.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -48,6 +48,18 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
 // cooperative launch), phases separated by grid-wide barriers.  `part` holds
 // three (grid, ld) panels of per-CTA partial sums; every CTA re-reduces a panel
 // in the same order, so all CTAs see identical coefficients.
+
+constexpr int kBlasSingle = 512;  // threads of the one-CTA variants (short vectors)
+
+// Barrier between phases: grid-wide for the cooperative variant; with a single CTA
+// (short vectors) a CTA barrier is the same thing and needs no cooperative launch.
+template <bool COOP>
+__device__ __forceinline__ void phase_sync() {
+  if constexpr (COOP)
+    cg::this_grid().sync();
+  else
+    __syncthreads();
+}
 
 // part_row[q] = sum over this CTA's slice of V[q][j] x[j] (q < m); part_row[m] = ||x||^2.
 __device__ void cta_dots(int n, int m, const double *__restrict__ V, const double *__restrict__ x,
@@ -83,17 +95,19 @@ __device__ void cta_axpy(int n, int m, const double *__restrict__ V, double *x, 
 }
 
 // beta = ||b||, V[0] = b / beta; resets scal/flags.
-__global__ void __launch_bounds__(kBlas) k_init_v0_coop(const double *__restrict__ b, int n, double *part, int ld,
+template <bool COOP>
+__global__ void __launch_bounds__(COOP ? kBlas : kBlasSingle) k_init_v0_coop(const double *__restrict__ b, int n, double *part, int ld,
                                                         double *V, float *Vf, double *scal, int *flags,
-                                                        int use_handle, cudaGraphConditionalHandle h) {
-  cg::grid_group grid = cg::this_grid();
+                                                        int use_handle, cudaGraphConditionalHandle h, double *T,
+                                                        int nT) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nT; i += gridDim.x * blockDim.x) T[i] = 0.0;
   __shared__ double red[32];
   __shared__ double c[34];
   double s = 0.0;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) s += b[j] * b[j];
   s = block_sum(s, red);
   if (threadIdx.x == 0) part[blockIdx.x * ld] = s;
-  grid.sync();
+  phase_sync<COOP>();
   cta_gather(part, ld, gridDim.x, 0, c);
   const double beta = sqrt(c[0]);
   const bool zero = !(beta > 0.0);
@@ -123,12 +137,12 @@ __global__ void __launch_bounds__(kBlas) k_init_v0_coop(const double *__restrict
 // One Arnoldi step (eq. 10): w = K v_{m-1}; two classical Gram-Schmidt passes
 // against v_0..v_{m-1} (their coefficients summed into column m-1 of T_m);
 // t = ||w||; v_m = w / t, or breakdown when t <= 1e-14 ||K v_{m-1}||.
-__global__ void __launch_bounds__(kBlas) k_arnoldi_coop(int n, const double *__restrict__ klo,
+template <bool COOP>
+__global__ void __launch_bounds__(COOP ? kBlas : kBlasSingle) k_arnoldi_coop(int n, const double *__restrict__ klo,
                                                         const double *__restrict__ kdiag,
                                                         const double *__restrict__ kup, double *V, float *Vf,
                                                         double *w, double *T, int ldT, double *part, int ld,
                                                         double *scal, int *flags) {
-  cg::grid_group grid = cg::this_grid();
   __shared__ double red[32];
   __shared__ double c[34];
   const int m = flags[F_M] + 1;  // the step computed here produces v_m
@@ -142,13 +156,13 @@ __global__ void __launch_bounds__(kBlas) k_arnoldi_coop(int n, const double *__r
     w[j] = x;
   }
   cta_dots(n, m, V, w, pa + (size_t)blockIdx.x * ld, red);
-  grid.sync();
+  phase_sync<COOP>();
   cta_gather(pa, ld, G, m, c);
   const double knorm = sqrt(c[m]);
   if (blockIdx.x == 0 && (int)threadIdx.x < m) T[(int64_t)threadIdx.x * ldT + (m - 1)] = c[threadIdx.x];
   cta_axpy(n, m, V, w, c);
   cta_dots(n, m, V, w, pb + (size_t)blockIdx.x * ld, red);
-  grid.sync();
+  phase_sync<COOP>();
   cta_gather(pb, ld, G, m, c);
   if (blockIdx.x == 0 && (int)threadIdx.x < m) T[(int64_t)threadIdx.x * ldT + (m - 1)] += c[threadIdx.x];
   cta_axpy(n, m, V, w, c);
@@ -156,7 +170,7 @@ __global__ void __launch_bounds__(kBlas) k_arnoldi_coop(int n, const double *__r
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) s += w[j] * w[j];
   s = block_sum(s, red);
   if (threadIdx.x == 0) pc[(size_t)blockIdx.x * ld] = s;
-  grid.sync();
+  phase_sync<COOP>();
   __syncthreads();
   cta_gather(pc, ld, G, 0, c);
   const double t = sqrt(c[0]);
@@ -179,32 +193,36 @@ __global__ void __launch_bounds__(kBlas) k_arnoldi_coop(int n, const double *__r
 
 // eq. (13): ||r_m|| = |tau t_{m+1,m}| ||(I - V_m V_m^T) z|| with two CGS passes
 // (z is overwritten by its projection); zero after a breakdown.
-__global__ void __launch_bounds__(kBlas) k_project_coop(int n, const double *__restrict__ V, double *z,
+template <bool COOP>
+__global__ void __launch_bounds__(COOP ? kBlas : kBlasSingle) k_project_coop(int n, const double *__restrict__ V, double *z,
                                                         double tau, double *part, int ld, double *scal,
-                                                        const int *flags) {
-  cg::grid_group grid = cg::this_grid();
+                                                        int *flags, KrylovCtl kc, int use_handle,
+                                                        cudaGraphConditionalHandle h) {
   __shared__ double red[32];
   __shared__ double c[34];
   const int m = flags[F_M] + 1;
   const int G = gridDim.x;
   double *pa = part, *pb = part + (size_t)G * ld, *pc = part + (size_t)2 * G * ld;
   cta_dots(n, m, V, z, pa + (size_t)blockIdx.x * ld, red);
-  grid.sync();
+  phase_sync<COOP>();
   cta_gather(pa, ld, G, m, c);
   cta_axpy(n, m, V, z, c);
   cta_dots(n, m, V, z, pb + (size_t)blockIdx.x * ld, red);
-  grid.sync();
+  phase_sync<COOP>();
   cta_gather(pb, ld, G, m, c);
   cta_axpy(n, m, V, z, c);
   double s = 0.0;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) s += z[j] * z[j];
   s = block_sum(s, red);
   if (threadIdx.x == 0) pc[(size_t)blockIdx.x * ld] = s;
-  grid.sync();
+  phase_sync<COOP>();
   if (blockIdx.x == 0) {
     __syncthreads();
     cta_gather(pc, ld, G, 0, c);
-    if (threadIdx.x == 0) scal[S_RES] = flags[F_BREAK] ? 0.0 : fabs(tau * scal[S_T]) * sqrt(c[0]);
+    if (threadIdx.x == 0) {
+      scal[S_RES] = flags[F_BREAK] ? 0.0 : fabs(tau * scal[S_T]) * sqrt(c[0]);
+      krylov_decide(scal, flags, kc, use_handle, h);
+    }
   }
 }
 
@@ -439,8 +457,15 @@ __global__ void k_residual(const double *__restrict__ G, const double *__restric
 
 // ---- launchers -------------------------------------------------------------------
 
-// Cooperative launch through cudaLaunchKernelEx (capturable into a CUDA graph).
-static void coop_launch(Ctx &c, const char *fam, double bytes, const void *fn, int grid, void **args) {
+// One CTA (plain launch) when the vector is short, else a cooperative launch through
+// cudaLaunchKernelEx (capturable into a CUDA graph).
+static void coop_launch(Ctx &c, const char *fam, double bytes, const void *fn_single, const void *fn_coop, int grid,
+                        void **args) {
+  if (grid <= 1) {
+    c.launch(fam, bytes, [&] { cudaLaunchKernel(fn_single, dim3(1), dim3(kBlasSingle), args, 0, c.stream); });
+    return;
+  }
+  const void *fn = fn_coop;
   c.launch(fam, bytes, [&] {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
@@ -462,8 +487,11 @@ void launch_vec_norm_init(Ctx &c, KrylovBufs &k, const double *b, int use_handle
   double *part = k.part, *V = k.V, *scal = k.scal;
   float *Vf = k.Vf;
   int *flags = k.flags;
-  void *args[] = {(void *)&b, &n, &part, (void *)&ld, &V, &Vf, &scal, &flags, &use_handle, &h};
-  coop_launch(c, "krylov_blas1", (double)k.n * 16, (const void *)k_init_v0_coop, k.grid, args);
+  double *T = k.T;
+  int nT = (k.maxit + 1) * k.maxit;
+  void *args[] = {(void *)&b, &n, &part, (void *)&ld, &V, &Vf, &scal, &flags, &use_handle, &h, &T, &nT};
+  coop_launch(c, "krylov_blas1", (double)k.n * 16, (const void *)k_init_v0_coop<false>,
+              (const void *)k_init_v0_coop<true>, k.grid, args);
 }
 
 // Partial buffers: k.part holds three (grid, maxit+2) panels.
@@ -476,7 +504,8 @@ void launch_arnoldi(Ctx &c, KrylovBufs &k) {
   int *flags = k.flags;
   void *args[] = {&n, (void *)&klo, (void *)&kdiag, (void *)&kup, &V, &Vf, &w, &T, &ldT, &part, (void *)&ld,
                   &scal, &flags};
-  coop_launch(c, "krylov_blas1", (double)k.n * 8.0 * 8, (const void *)k_arnoldi_coop, k.grid, args);
+  coop_launch(c, "krylov_blas1", (double)k.n * 8.0 * 8, (const void *)k_arnoldi_coop<false>,
+              (const void *)k_arnoldi_coop<true>, k.grid, args);
 }
 
 void launch_capacitance(Ctx &c, KrylovBufs &k, int nf, double tau, const double2 *shift, const double2 *wg,
@@ -491,15 +520,18 @@ void launch_capacitance(Ctx &c, KrylovBufs &k, int nf, double tau, const double2
 }
 
 // ||(I - V_m V_m^T) z|| with two CGS passes (z is overwritten by the projection).
-void launch_project_resnorm(Ctx &c, KrylovBufs &k, const double *z, double tau) {
+void launch_project_resnorm(Ctx &c, KrylovBufs &k, const double *z, double tau, const KrylovCtl &kc0, int use_handle,
+                            cudaGraphConditionalHandle h) {
   const int ld = k.maxit + 2;
   int n = k.n;
   const double *V = k.V;
   double *zz = const_cast<double *>(z);
   double *part = k.part, *scal = k.scal;
-  const int *flags = k.flags;
-  void *args[] = {&n, (void *)&V, &zz, &tau, &part, (void *)&ld, &scal, (void *)&flags};
-  coop_launch(c, "krylov_blas1", (double)k.n * 8.0 * 6, (const void *)k_project_coop, k.grid, args);
+  int *flags = k.flags;
+  KrylovCtl kc = kc0;
+  void *args[] = {&n, (void *)&V, &zz, &tau, &part, (void *)&ld, &scal, &flags, &kc, &use_handle, &h};
+  coop_launch(c, "krylov_blas1", (double)k.n * 8.0 * 6, (const void *)k_project_coop<false>,
+              (const void *)k_project_coop<true>, k.grid, args);
 }
 
 void launch_xm(Ctx &c, KrylovBufs &k, const double *y, double *x, float *xf) {

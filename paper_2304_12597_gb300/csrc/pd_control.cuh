@@ -1,0 +1,83 @@
+// Device-side stopping logic of Algorithm 2 and of the refinement loop, shared
+// by the kernels that finish a step (the eq. (13) projection, the inverse DFT).
+// Internal header; single-thread functions, called by one thread of one CTA.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "pd_internal.h"
+
+namespace pd {
+
+// After an Algorithm-2 step (Sec. 3): record ||r_m||, decide whether to continue:
+// stop at ||r_m|| <= eps beta, at maxit, at a breakdown, or at a stall near the
+// precision floor (no halving over `win` steps once ||r_m|| <= stall_floor beta).
+__device__ __forceinline__ void krylov_decide(double *scal, int *flags, const KrylovCtl &k, int use_handle,
+                                              cudaGraphConditionalHandle h) {
+  const int m = flags[F_M] + 1;
+  const double res = scal[S_RES], beta = scal[S_BETA];
+  if (m < 33) scal[S_HIST + m] = res;
+  const bool nonfinite = flags[F_NONFIN] || !isfinite(res);
+  if (nonfinite) flags[F_NONFIN] = 1;
+  const bool conv = flags[F_BREAK] || res <= k.eps * beta;
+  const bool stall = m >= k.win + 1 && res <= k.stall_floor * beta && res > 0.5 * scal[S_HIST + m - k.win];
+  const bool stop = nonfinite || conv || stall || m >= k.maxit;
+  flags[F_M] = m;
+  flags[F_KCONV] = conv ? 1 : 0;
+  flags[F_KSTOP] = stop ? 1 : 0;
+  if (use_handle) cudaGraphSetConditional(h, stop ? 0u : 1u);
+}
+
+// After a solve (first or refinement sweep) has produced ||delta_s||^2 in
+// scal[S_D2]: record the sweep and decide whether another refinement sweep runs.
+__device__ __forceinline__ void refine_decide(double *scal, int *flags, const RefineCtl &r, int use_handle,
+                                              cudaGraphConditionalHandle h) {
+  const int s = flags[F_SWEEP];
+  const double d2 = scal[S_D2];
+  if (s == 0) scal[S_REF2] = d2;
+  const double ref2 = scal[S_REF2];
+  const double prev = scal[S_PREV];
+  const double rel = ref2 > 0.0 ? sqrt(d2 / ref2) : 0.0;
+  const double beta = scal[S_BETA];
+  if (s < 16) {
+    flags[F_SWM + s] = flags[F_M];
+    scal[S_SWRES + s] = beta > 0.0 ? scal[S_RES] / beta : 0.0;
+    scal[S_SWUPD + s] = rel;
+    scal[S_SWBETA + s] = beta;
+  }
+  flags[F_MTOT] += flags[F_M];
+  bool conv = false, stop = false;
+  if (!isfinite(d2) || flags[F_NONFIN]) {
+    flags[F_NONFIN] = 1;
+    stop = true;
+  } else if (ref2 == 0.0) {
+    conv = stop = true;
+  } else {
+    const double eps = s == 0 ? r.eps_first : r.eps_refine;
+    // FP64: Algorithm 2 met its tolerance, so this sweep's correction is exact to
+    // working accuracy (s = 0: the paper's Algorithm 1 itself); a refinement sweep
+    // leaves about eps * ||delta_s||.
+    if (r.fp64 && flags[F_KCONV] && (s == 0 || eps * rel <= r.refine_tol)) conv = stop = true;
+    // Refinement contracts the error by rho ~ ||delta_s|| / ||delta_{s-1}|| (s >= 2:
+    // delta_1 / delta_0 is the first solve's error, not a contraction), so about
+    // rho * ||delta_s|| remains after sweep s.
+    if (!stop && s > 0) {
+      const double rho = prev > 0.0 ? rel / prev : 0.0;
+      if ((s >= 2 && rho * rel <= r.refine_tol && rel <= 1e-7) || rel <= 1e-15) {
+        conv = stop = true;
+      } else if (s > 1 && rho > 0.5) {  // no longer contracting: rounding floor reached
+        conv = rel <= 1e-10;
+        stop = true;
+      }
+    }
+    if (!stop && s + 1 > r.max_refine) stop = true;
+  }
+  scal[S_PREV] = rel;
+  scal[S_UPD] = rel;
+  flags[F_SWEEP] = s + 1;
+  flags[F_RCONV] = conv ? 1 : 0;
+  flags[F_RSTOP] = stop ? 1 : 0;
+  if (use_handle) cudaGraphSetConditional(h, stop ? 0u : 1u);
+}
+
+}  // namespace pd

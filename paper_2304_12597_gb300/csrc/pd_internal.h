@@ -26,6 +26,7 @@ enum FlagIndex {
   F_KCONV = 8,    // Algorithm 2 reached eps (or b == 0, or breakdown)
   F_RSTOP = 9,    // refinement loop finished
   F_MTOT = 10,    // sum of m over the solves
+  F_C2RCNT = 11,  // completion counter of the inverse DFT's finishing epilogue
   F_SWM = 16,     // [16, 32): m of each solve
   kFlagWords = 64
 };
@@ -83,17 +84,48 @@ size_t smem_optin();
 // Sets the thread-local message returned by paradiag_last_error().
 void set_last_error(const char *msg);
 
+// Device-side control of Algorithm 2 and of the refinement loop (control.cu).
+struct KrylovCtl {
+  double eps;          // stop when ||r_m|| <= eps * beta
+  double stall_floor;  // stall exit only once ||r_m|| <= stall_floor * beta
+  int win;             // stall: no halving over `win` steps
+  int maxit;
+};
+struct RefineCtl {
+  int fp64;
+  double eps_first, eps_refine;  // Algorithm-2 tolerances of the first solve / sweeps
+  double refine_tol;
+  int max_refine;
+};
 // ---- time FFT / DST (fft.cu) ----------------------------------------------------
 // Forward DFT along time of real (n, ncols) rows -> half spectrum (n/2+1, ncols).
 template <typename T, typename Tin>
 void launch_fft_r2c(Ctx &c, const Tin *X, int64_t ldx, int64_t ncols, int n, const cpx<T> *tw,
                     cpx<T> *S, int64_t lds);
+// Forward DFT along time of the FP64 all-at-once residual
+// R = G - [(I + tau K) U - U Sigma_1^T] (1D), computed on load: R is never stored.
+template <typename T>
+void launch_fft_r2c_residual(Ctx &c, const double *G, const double *U, int64_t ncols, int n,
+                             const double *rxl, const double *rxd, const double *rxu, const cpx<T> *tw,
+                             cpx<T> *S, int64_t lds);
+// Optional epilogue of the inverse DFT: the last CTA to finish sums the per-CTA
+// squares into scal[S_D2] and runs the refinement decision.
+struct StepFinish {
+  int enabled;
+  int *counter;  // zero on entry; reset by the last CTA
+  double *scal;
+  int *flags;
+  RefineCtl rc;
+  int use_handle;
+  cudaGraphConditionalHandle h;
+};
 // Inverse DFT along time of a half spectrum; mode 0: store double, 1: add into
 // double, 2: store float.  norm_part (may be null) receives per-CTA sums of the
 // squared output values; *nparts = number of CTAs.
 template <typename T>
 void launch_fft_c2r(Ctx &c, const cpx<T> *S, int64_t lds, int64_t ncols, int n, const cpx<T> *tw,
-                    void *out, int64_t ldo, int mode, double *norm_part, int *nparts);
+                    void *out, int64_t ldo, int mode, double *norm_part, int *nparts,
+                    const StepFinish *fin = nullptr);
 // Orthonormal DST-I along the middle axis of (nt, ny, nx); ny + 1 a power of two.
 // mode 0: store, 1: add into (double output only).
 template <typename Tin, typename Tout, typename T>
@@ -111,6 +143,7 @@ struct PintGeom {
   int M;         // rows per thread (template value)
   int cta_sum;   // 1: the teams of a CTA add their partial rows (nblk == 1)
   int acc_rows;  // partial rows per block in acc_part (R, or CTAs when cta_sum)
+  int stage;     // 1: tau K staged in shared memory once per launch
 };
 PintGeom pint_geometry(int nf, int nblk, int blen, int target_teams, int elem_bytes);
 void set_acc_rows(PintGeom &g);  // recompute cta_sum / acc_rows after changing R
@@ -121,6 +154,10 @@ struct PintArgs {
                            // right-hand side is V[m+1] and the dots use V[0..m]
   int want_dots;           // with mcount: compute g_k = V^T y_k
   int mdots_max;           // with mcount: largest possible number of dots (smem sizing)
+  const int *xm_count;     // if set: subtract x_m = sum_{q < m} y_q V[q] (m = *xm_count), formed
+  const double *xm_y;      // per team from y (xm_y) and V (a.V, ldv) instead of rvec; the teams
+  const double *xm_Vd;     // starting at k = 0 also store x_m in FP64 (from xm_Vd) into xm_out
+  double *xm_out;
   const double2 *shift;    // s_k = 1 - pi_k, length nf
   const T *tlo, *tdiag, *tup;  // tau * K (block-decoupled), length nblk*blen
   const cpx<T> *R;         // spectrum right-hand sides (nf, ldr) or null
@@ -140,6 +177,10 @@ struct PintArgs {
 };
 template <typename T>
 void launch_pint(Ctx &c, const PintGeom &g, const PintArgs<T> &a);
+// z[j] = sum_k Re(omega_k H[k][j]) over stored h_k (nf rows, leading dimension ldh)
+template <typename T>
+void launch_zsum(Ctx &c, int nf, int64_t n, const cpx<T> *H, int64_t ldh, const double2 *omega, double *z,
+                 const int *skip_flag);
 // out[j] = sum_r acc_part[(blk*R + r)*blen + e], j = blk*blen + e
 void launch_acc_reduce(Ctx &c, const PintGeom &g, const double *acc_part, double *out,
                        const int *skip_flag);
@@ -161,27 +202,16 @@ struct KrylovBufs {
 // All Algorithm-2 kernels read m from flags[F_M] (completed steps), so one captured
 // iteration serves every m.  `use_handle` / `h`: set a CUDA-graph conditional.
 void launch_vec_norm_init(Ctx &c, KrylovBufs &k, const double *b, int use_handle,
-                          cudaGraphConditionalHandle h);
+                          cudaGraphConditionalHandle h);  // also zeroes T
 void launch_arnoldi(Ctx &c, KrylovBufs &k);
 void launch_capacitance(Ctx &c, KrylovBufs &k, int nf, double tau, const double2 *shift,
                         const double2 *wg, const double2 *gpart, int nblk, double *msys_part,
                         int k5_grid, double2 *srow, double2 *omega, double *y);
-void launch_project_resnorm(Ctx &c, KrylovBufs &k, const double *z, double tau);
+// eq. (13) and the Algorithm-2 stopping decision (krylov_decide) in one kernel
+void launch_project_resnorm(Ctx &c, KrylovBufs &k, const double *z, double tau, const KrylovCtl &kc,
+                            int use_handle, cudaGraphConditionalHandle h);
 void launch_xm(Ctx &c, KrylovBufs &k, const double *y, double *x, float *xf);
 
-// Device-side control of Algorithm 2 and of the refinement loop (control.cu).
-struct KrylovCtl {
-  double eps;          // stop when ||r_m|| <= eps * beta
-  double stall_floor;  // stall exit only once ||r_m|| <= stall_floor * beta
-  int win;             // stall: no halving over `win` steps
-  int maxit;
-};
-struct RefineCtl {
-  int fp64;
-  double eps_first, eps_refine;  // Algorithm-2 tolerances of the first solve / sweeps
-  double refine_tol;
-  int max_refine;
-};
 void launch_solve_reset(Ctx &c, double *scal, int *flags);
 void launch_krylov_decide(Ctx &c, double *scal, int *flags, const KrylovCtl &k, int use_handle,
                           cudaGraphConditionalHandle h);

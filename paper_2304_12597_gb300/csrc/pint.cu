@@ -31,8 +31,12 @@ namespace pd {
 
 template <typename T, int M>
 struct TeamSmem {
-  static size_t bytes(int P, int mdots) {
-    size_t b = 0;
+  // staged coefficients tau*K (lo, diag, up), padded like the right-hand side
+  __host__ __device__ static size_t stage_bytes(int P, int stage) {
+    return stage ? (((size_t)3 * P * (M + 1) * sizeof(T) + 15) & ~(size_t)15) : 0;
+  }
+  static size_t bytes(int P, int mdots, int stage) {
+    size_t b = stage_bytes(P, stage);
     b += (size_t)P * (M + 1) * sizeof(cpx<T>);   // rhs / dd, padded one slot per chunk
     b += (size_t)P * 5 * sizeof(cpx<T>);         // condensed rows a, b, c, d and 1/b
     b += ((size_t)P * M * sizeof(T) + 15) & ~(size_t)15;  // per-team accumulators (compute type)
@@ -42,11 +46,18 @@ struct TeamSmem {
 };
 
 template <typename T>
-__device__ __forceinline__ void coef(const PintArgs<T> &a, int64_t j, bool valid, cpx<T> s, T &lo, cpx<T> &d, T &up) {
+__device__ __forceinline__ void coef(const PintArgs<T> &a, const T *cs, int cs_stride, int64_t j, int ps, bool valid,
+                                     cpx<T> s, T &lo, cpx<T> &d, T &up) {
   if (valid) {
-    lo = a.tlo[j];
-    up = a.tup[j];
-    d = mk<T>(s.x + a.tdiag[j], s.y);
+    if (cs) {  // staged in shared memory at padded index ps
+      lo = cs[ps];
+      d = mk<T>(s.x + cs[cs_stride + ps], s.y);
+      up = cs[2 * cs_stride + ps];
+    } else {
+      lo = a.tlo[j];
+      up = a.tup[j];
+      d = mk<T>(s.x + a.tdiag[j], s.y);
+    }
   } else {
     lo = T(0);
     up = T(0);
@@ -72,7 +83,9 @@ __global__ void __launch_bounds__(M >= 16 ? 256 : 512) k_pint(PintGeom g, PintAr
 
   extern __shared__ __align__(16) unsigned char smraw[];
   unsigned char *base = smraw + (size_t)tic * team_bytes;
-  cpx<T> *dd = reinterpret_cast<cpx<T> *>(base);
+  T *cs = g.stage ? reinterpret_cast<T *>(base) : nullptr;
+  const int cs_stride = P * (M + 1);
+  cpx<T> *dd = reinterpret_cast<cpx<T> *>(base + TeamSmem<T, M>::stage_bytes(P, g.stage));
   cpx<T> *pa = dd + (size_t)P * (M + 1);
   cpx<T> *pb = pa + N;
   cpx<T> *pc = pb + N;
@@ -97,6 +110,44 @@ __global__ void __launch_bounds__(M >= 16 ? 256 : 512) k_pint(PintGeom g, PintAr
   }
   cpx<T> *my = dd + (size_t)t * (M + 1);
   const int e0 = t * M;
+  const int ps0 = t * (M + 1);  // padded index of this thread's first row
+  if (cs && k0 < k1) {
+    // tau K does not depend on k: stage the team's block once (read after the first
+    // team barrier of the k loop)
+    for (int e = t; e < P * M; e += P) {
+      const int pe = e + e / M;
+      T lo = T(0), di = T(0), up = T(0);
+      if (e < blen) {
+        lo = a.tlo[off + e];
+        di = a.tdiag[off + e];
+        up = a.tup[off + e];
+      }
+      cs[pe] = lo;
+      cs[cs_stride + pe] = di;
+      cs[2 * cs_stride + pe] = up;
+    }
+  }
+
+  // x_m = V_m y_m for the team's rows (final loop of Algorithm 1), kept in the
+  // accumulator region, which this pass does not otherwise use
+  T *xs = nullptr;
+  if (a.xm_count && active) {
+    xs = acc;
+    const int m = *a.xm_count;
+    for (int e = t; e < P * M; e += P) {
+      T v = T(0);
+      if (e < blen)
+        for (int q = 0; q < m; ++q) v += (T)a.xm_y[q] * a.V[(int64_t)q * a.ldv + off + e];
+      xs[e] = v;
+    }
+    if (rr == 0 && a.xm_out) {
+      for (int e = t; e < blen; e += P) {
+        double v = 0.0;
+        for (int q = 0; q < m; ++q) v += a.xm_y[q] * a.xm_Vd[(int64_t)q * a.ldv + off + e];
+        a.xm_out[off + e] = v;
+      }
+    }
+  }
 
   for (int k = k0; k < k1; ++k) {
     const double2 sk = a.shift[k];
@@ -108,7 +159,10 @@ __global__ void __launch_bounds__(M >= 16 ? 256 : 512) k_pint(PintGeom g, PintAr
         const int64_t j = off + e;
         if (a.R) {
           v = a.R[(int64_t)k * a.ldr + j];
-          if (rvec) v.x -= rvec[j];
+          if (xs)
+            v.x -= xs[e];
+          else if (rvec)
+            v.x -= rvec[j];
         } else {
           v.x = rvec[j];
         }
@@ -121,12 +175,12 @@ __global__ void __launch_bounds__(M >= 16 ? 256 : 512) k_pint(PintGeom g, PintAr
     cpx<T> aa[M], cc[M];
     T lo0, up0;
     cpx<T> d0;
-    coef(a, off + e0, e0 < blen, s, lo0, d0, up0);
+    coef(a, cs, cs_stride, off + e0, ps0, e0 < blen, s, lo0, d0, up0);
     const cpx<T> r0 = my[0];
     {
       T lo, up;
       cpx<T> d;
-      coef(a, off + e0 + 1, e0 + 1 < blen, s, lo, d, up);
+      coef(a, cs, cs_stride, off + e0 + 1, ps0 + 1, e0 + 1 < blen, s, lo, d, up);
       const cpx<T> rb = recip(d);
       aa[1] = scal(lo, rb);
       cc[1] = scal(up, rb);
@@ -136,7 +190,7 @@ __global__ void __launch_bounds__(M >= 16 ? 256 : 512) k_pint(PintGeom g, PintAr
     for (int i = 2; i < M; ++i) {
       T lo, up;
       cpx<T> d;
-      coef(a, off + e0 + i, e0 + i < blen, s, lo, d, up);
+      coef(a, cs, cs_stride, off + e0 + i, ps0 + i, e0 + i < blen, s, lo, d, up);
       const cpx<T> rd = recip(fnms_r(d, lo, cc[i - 1]));
       aa[i] = scal(-lo, mul(aa[i - 1], rd));
       cc[i] = scal(up, rd);
@@ -310,6 +364,52 @@ __global__ void __launch_bounds__(1024) k_acc_reduce(int nblk, int blen, int R, 
   }
 }
 
+// z[j] = sum_k Re(omega_k H[k][j]) over the stored h_k (eq. 13's z), j < n; the same
+// fixed-order tiled reduction as k_acc_reduce (32 outputs x 32 row groups per CTA).
+template <typename T>
+__global__ void __launch_bounds__(1024) k_zsum(int nf, int64_t n, const cpx<T> *__restrict__ H, int64_t ldh,
+                                               const double2 *__restrict__ omega, double *__restrict__ z,
+                                               const int *skip_flag) {
+  if (skip_flag && *skip_flag) return;
+  __shared__ double sm[32][33];
+  const int64_t j = (int64_t)blockIdx.x * 32 + threadIdx.x;
+  T s0 = T(0), s1 = T(0);
+  if (j < n) {
+    int k = threadIdx.y;
+    for (; k + 32 < nf; k += 64) {
+      const double2 o0 = omega[k], o1 = omega[k + 32];
+      const cpx<T> h0 = H[(int64_t)k * ldh + j], h1 = H[(int64_t)(k + 32) * ldh + j];
+      s0 += (T)o0.x * h0.x - (T)o0.y * h0.y;
+      s1 += (T)o1.x * h1.x - (T)o1.y * h1.y;
+    }
+    for (; k < nf; k += 32) {
+      const double2 o0 = omega[k];
+      const cpx<T> h0 = H[(int64_t)k * ldh + j];
+      s0 += (T)o0.x * h0.x - (T)o0.y * h0.y;
+    }
+  }
+  sm[threadIdx.y][threadIdx.x] = (double)s0 + (double)s1;
+  __syncthreads();
+  if (threadIdx.y == 0 && j < n) {
+    double t = 0.0;
+    for (int i = 0; i < 32; ++i) t += sm[i][threadIdx.x];
+    z[j] = t;
+  }
+}
+
+template <typename T>
+void launch_zsum(Ctx &c, int nf, int64_t n, const cpx<T> *H, int64_t ldh, const double2 *omega, double *z,
+                 const int *skip_flag) {
+  const int grid = (int)((n + 31) / 32);
+  c.launch("zsum", (double)nf * n * sizeof(cpx<T>) + n * 8.0, [&] {
+    k_zsum<T><<<grid, dim3(32, 32), 0, c.stream>>>(nf, n, H, ldh, omega, z, skip_flag);
+  });
+}
+template void launch_zsum<double>(Ctx &, int, int64_t, const cpx<double> *, int64_t, const double2 *, double *,
+                                  const int *);
+template void launch_zsum<float>(Ctx &, int, int64_t, const cpx<float> *, int64_t, const double2 *, double *,
+                                 const int *);
+
 static int next_pow2(int v) {
   int p = 1;
   while (p < v) p <<= 1;
@@ -333,13 +433,22 @@ PintGeom pint_geometry(int nf, int nblk, int blen, int target_teams, int elem_by
   g.teams_per_cta = std::max(1, 256 / g.P);
   int R = (target_teams + nblk - 1) / nblk;
   g.R = std::max(1, std::min(R, nf));
+  // fewer teams per CTA while the grid would not cover every SM
+  const int nteams = nblk * g.R;
+  while (g.teams_per_cta > 1 && (nteams + g.teams_per_cta - 1) / g.teams_per_cta < sm_count()) g.teams_per_cta >>= 1;
+  // stage tau K in shared memory when the CTA stays within ~160 KB
+  const size_t esz = elem_bytes == 16 ? 8 : 4;  // real type of the compute precision
+  const size_t rest = (size_t)g.P * (g.M + 1) * 2 * esz + (size_t)g.P * 5 * 2 * esz + (size_t)g.P * g.M * esz +
+                      (size_t)(g.P / 32) * 33 * 16;
+  const size_t stage = (size_t)3 * g.P * (g.M + 1) * esz;
+  g.stage = (rest + stage) * g.teams_per_cta <= 160 * 1024 ? 1 : 0;
   set_acc_rows(g);
   return g;
 }
 
 template <typename T, int M>
 static void launch_pint_m(Ctx &c, const PintGeom &g, const PintArgs<T> &a) {
-  const size_t tb = TeamSmem<T, M>::bytes(g.P, a.mcount ? (a.want_dots ? a.mdots_max : 0) : a.mdots);
+  const size_t tb = TeamSmem<T, M>::bytes(g.P, a.mcount ? (a.want_dots ? a.mdots_max : 0) : a.mdots, g.stage);
   const size_t smem = tb * g.teams_per_cta;
   const int nteams = g.nblk * g.R;
   const int grid = (nteams + g.teams_per_cta - 1) / g.teams_per_cta;

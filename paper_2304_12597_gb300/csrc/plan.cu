@@ -174,6 +174,7 @@ struct pd_plan {
   cpx<double> *tw_d = nullptr, *twy_d = nullptr;
   cpx<float> *tw_f = nullptr, *twy_f = nullptr;
   void *spec = nullptr;
+  void *hbuf = nullptr;  // h_k of the current Algorithm-2 step (same shape as the spectrum)
   double *V = nullptr, *T = nullptr, *w = nullptr, *part = nullptr, *scal = nullptr;
   float *Vf = nullptr, *xf = nullptr;  // binary32 copies of V and x_m (mixed precision)
   int *flags = nullptr;
@@ -280,8 +281,9 @@ void fill_geometry(pd_plan *p, const pd_desc *d) {
   const int ctas_per_sm = std::max(1, std::min(by_smem, by_threads));
   const int target = sms * ctas_per_sm * g0.teams_per_cta;
   p->geom = pd::pint_geometry(p->nf, p->nblk, p->blen, target, esz);
-  // cooperative Krylov kernels: 64-thread CTAs, at most one per SM (always co-resident)
-  p->blas_grid = (int)std::max<int64_t>(1, std::min<int64_t>((p->nbar + 63) / 64, (int64_t)sms));
+  // Krylov vector kernels: one 512-thread CTA (plain launch) for vectors up to 8192
+  // entries; beyond, cooperative 64-thread CTAs, at most one per SM (co-resident)
+  p->blas_grid = p->nbar <= 8192 ? 1 : (int)std::max<int64_t>(1, std::min<int64_t>((p->nbar + 63) / 64, (int64_t)sms));
   // capacitance terms: a few frequencies per warp keeps the partial reduction short
   p->k5_grid = std::max(1, std::min((p->nf + 15) / 16, 64));
 }
@@ -328,6 +330,7 @@ size_t layout(pd_plan *p, unsigned char *base) {
     if (mixed) p->twy_f = A.take<cpx<float>>(p->ny + 1);
   }
   p->spec = mixed ? (void *)A.take<cpx<float>>((size_t)nf * p->lds) : (void *)A.take<cpx<double>>((size_t)nf * p->lds);
+  p->hbuf = mixed ? (void *)A.take<cpx<float>>((size_t)nf * p->lds) : (void *)A.take<cpx<double>>((size_t)nf * p->lds);
   p->V = A.take<double>((size_t)(mx + 1) * nbar);
   if (mixed) {
     p->Vf = A.take<float>((size_t)(mx + 1) * nbar);
@@ -541,10 +544,10 @@ pd_status emit_pre(pd_plan *p, int kind, const double *G, double *U, int use_han
       pd::launch_fft_r2c<T, T>(c, tmp, p->nbar, p->nbar, nt, time_tw<T>(p), S, p->lds);
     }
   } else {
-    pd::launch_residual<T>(c, G, U, res, p->nt, p->ny, p->nx, p->rxl, p->rxd, p->rxu, p->ryl, p->ryd, p->ryu);
-    if (p->dim == 1) {
-      pd::launch_fft_r2c<T, T>(c, res, p->nbar, p->nbar, nt, time_tw<T>(p), S, p->lds);
+    if (p->dim == 1) {  // the FP64 residual is formed while the DFT loads its tiles
+      pd::launch_fft_r2c_residual<T>(c, G, U, p->nbar, nt, p->rxl, p->rxd, p->rxu, time_tw<T>(p), S, p->lds);
     } else {
+      pd::launch_residual<T>(c, G, U, res, p->nt, p->ny, p->nx, p->rxl, p->rxd, p->rxu, p->ryl, p->ryd, p->ryu);
       pd::launch_dst_y<T, T, T>(c, res, tmp, p->nt, p->ny, p->nx, dst_tw<T>(p), 0);
       pd::launch_fft_r2c<T, T>(c, tmp, p->nbar, p->nbar, nt, time_tw<T>(p), S, p->lds);
     }
@@ -556,7 +559,6 @@ pd_status emit_pre(pd_plan *p, int kind, const double *G, double *U, int use_han
   a.acc_part = p->acc_part;
   pd::launch_pint<T>(c, p->geom, a);
   pd::launch_acc_reduce(c, p->geom, p->acc_part, p->b, nullptr);
-  CK(cudaMemsetAsync(p->T, 0, sizeof(double) * (p->maxit + 1) * p->maxit, c.stream));
   pd::KrylovBufs kb = kbufs<T>(p);
   pd::launch_vec_norm_init(c, kb, p->b, use_handle, hk);
   return PD_OK;
@@ -568,7 +570,8 @@ pd_status emit_iter(pd_plan *p, int kind, int use_handle, cudaGraphConditionalHa
   pd::Ctx &c = p->ctx;
   pd::KrylovBufs kb = kbufs<T>(p);
   pd::launch_arnoldi(c, kb);
-  {  // h_k = ((1 - pi_k) I + tau K)^{-1} v_{m+1} and g_k = V_m^T h_k
+  cpx<T> *H = reinterpret_cast<cpx<T> *>(p->hbuf);
+  {  // h_k = ((1 - pi_k) I + tau K)^{-1} v_{m+1} (stored) and g_k = V_m^T h_k
     pd::PintArgs<T> a = base_args<T>(p);
     a.mcount = p->flags + pd::F_M;
     a.want_dots = 1;
@@ -576,25 +579,16 @@ pd_status emit_iter(pd_plan *p, int kind, int use_handle, cudaGraphConditionalHa
     a.V = vbasis<T>(p);
     a.ldv = p->nbar;
     a.gpart = p->gpart;
+    a.Y = H;
+    a.ldy = p->lds;
     a.skip_flag = p->flags + pd::F_BREAK;
     pd::launch_pint<T>(c, p->geom, a);
   }
   pd::launch_capacitance(c, kb, p->nf, p->tau, p->shift, p->wg, p->gpart, p->nblk, p->msys_part, p->k5_grid,
                          p->srow, p->omega, p->y);
-  {  // z = sum_i gamma_i h_i (e_m^T S_i y_m), then eq. (13)
-    pd::PintArgs<T> a = base_args<T>(p);
-    a.mcount = p->flags + pd::F_M;
-    a.want_dots = 0;
-    a.V = vbasis<T>(p);
-    a.ldv = p->nbar;
-    a.omega = p->omega;
-    a.acc_part = p->acc_part;
-    a.skip_flag = p->flags + pd::F_BREAK;
-    pd::launch_pint<T>(c, p->geom, a);
-    pd::launch_acc_reduce(c, p->geom, p->acc_part, p->z, p->flags + pd::F_BREAK);
-  }
-  pd::launch_project_resnorm(c, kb, p->z, p->tau);
-  pd::launch_krylov_decide(c, p->scal, p->flags, krylov_ctl(p, kind), use_handle, hk);
+  // z = sum_i gamma_i h_i (e_m^T S_i y_m) from the stored h_i, then eq. (13)
+  pd::launch_zsum<T>(c, p->nf, p->nbar, H, p->lds, p->omega, p->z, p->flags + pd::F_BREAK);
+  pd::launch_project_resnorm(c, kb, p->z, p->tau, krylov_ctl(p, kind), use_handle, hk);
   return PD_OK;
 }
 
@@ -606,31 +600,41 @@ pd_status emit_post(pd_plan *p, int kind, double *U, int use_handle, cudaGraphCo
   cpx<T> *S = reinterpret_cast<cpx<T> *>(p->spec);
   const int nt = (int)p->nt;
   const bool fp64 = sizeof(T) == 8;
-  pd::KrylovBufs kb = kbufs<T>(p);
-  pd::launch_xm(c, kb, p->y, p->x, sizeof(T) == 4 ? p->xf : nullptr);
   pd::PintArgs<T> a = base_args<T>(p);
   a.R = S;
   a.ldr = p->lds;
-  a.rvec = xvec<T>(p);
+  a.xm_count = p->flags + pd::F_M;  // x_m = V_m y_m formed by each team
+  a.xm_y = p->y;
+  a.V = vbasis<T>(p);
+  a.ldv = p->nbar;
+  a.xm_Vd = p->V;
+  a.xm_out = p->x;
   a.Y = S;
   a.ldy = p->lds;
   pd::launch_pint<T>(c, p->geom, a);
-  int nparts = 0;
-  if (p->dim == 1) {
-    pd::launch_fft_c2r<T>(c, S, p->lds, p->nbar, nt, time_tw<T>(p), U, p->nbar, kind == 0 ? 0 : 1, p->norm_part,
-                          &nparts);
-  } else {
-    T *tmp = tmp_buf<T>(p);
-    pd::launch_fft_c2r<T>(c, S, p->lds, p->nbar, nt, time_tw<T>(p), tmp, p->nbar, fp64 ? 0 : 2, p->norm_part,
-                          &nparts);
-    pd::launch_dst_y<T, double, T>(c, tmp, U, p->nt, p->ny, p->nx, dst_tw<T>(p), kind == 0 ? 0 : 1);
-  }
-  pd::launch_sumsq(c, p->norm_part, nparts, p->scal + pd::S_D2);
   if (kind == 0) {
     CK(cudaMemcpyAsync(p->b0, p->b, sizeof(double) * p->nbar, cudaMemcpyDeviceToDevice, c.stream));
     CK(cudaMemcpyAsync(p->x0, p->x, sizeof(double) * p->nbar, cudaMemcpyDeviceToDevice, c.stream));
   }
-  pd::launch_refine_decide(c, p->scal, p->flags, refine_ctl(p), use_handle, hr);
+  // inverse DFT; its last CTA sums ||delta||^2 and takes the refinement decision
+  pd::StepFinish fin{};
+  fin.enabled = 1;
+  fin.counter = p->flags + pd::F_C2RCNT;
+  fin.scal = p->scal;
+  fin.flags = p->flags;
+  fin.rc = refine_ctl(p);
+  fin.use_handle = use_handle;
+  fin.h = hr;
+  int nparts = 0;
+  if (p->dim == 1) {
+    pd::launch_fft_c2r<T>(c, S, p->lds, p->nbar, nt, time_tw<T>(p), U, p->nbar, kind == 0 ? 0 : 1, p->norm_part,
+                          &nparts, &fin);
+  } else {
+    T *tmp = tmp_buf<T>(p);
+    pd::launch_fft_c2r<T>(c, S, p->lds, p->nbar, nt, time_tw<T>(p), tmp, p->nbar, fp64 ? 0 : 2, p->norm_part,
+                          &nparts, &fin);
+    pd::launch_dst_y<T, double, T>(c, tmp, U, p->nt, p->ny, p->nx, dst_tw<T>(p), kind == 0 ? 0 : 1);
+  }
   return PD_OK;
 }
 
