@@ -96,6 +96,16 @@ typedef struct pd_desc {
   int32_t no_graph;      /* nonzero: drive the Algorithm-2 and refinement loops from the host
                             instead of running each solve as one CUDA graph with device-side
                             conditionals (also the behaviour while kernel timing is enabled) */
+  /* Launch geometry; 0 selects the built-in choice (paradiag_autotune fills these). */
+  int32_t tune_pint_rows;    /* rows per thread of the shifted-solve kernel: 4, 8, or 16
+                                (16 with PD_MIXED only) */
+  int32_t tune_pint_teams;   /* teams (one tridiagonal block each) per CTA of that kernel:
+                                a power of two with teams * threads-per-team <= 512
+                                (<= 256 with 16 rows per thread) */
+  int32_t tune_krylov_ctas;  /* CTAs of the Krylov vector kernels: 1 = one 512-thread CTA,
+                                > 1 = cooperative launch of 64-thread CTAs (<= SM count) */
+  int32_t tune_cap_ctas;     /* CTAs of the capacitance-term kernel, 1 .. 1024 */
+  int32_t tune_fft_cols;     /* columns per CTA of the time FFTs: 2, 4, 8 or 16 */
 } pd_desc;
 
 /* Statistics of the last paradiag_solve / paradiag_solve_host. */

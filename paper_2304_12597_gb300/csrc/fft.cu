@@ -16,6 +16,9 @@
 
 namespace pd {
 
+// Global loads a thread issues back to back before it uses any of them.
+constexpr int kLoadBatch = 8;
+
 // In-place DIT FFT of `nseries` series of length n = 2^logn stored back to back
 // in shared memory, input in bit-reversed order, output in natural order.
 // All threads of the CTA take part; the caller synchronises before the call.
@@ -99,13 +102,26 @@ __global__ void __launch_bounds__(256) k_fft_r2c(const Tin *__restrict__ X, int6
   cpx<T> *buf = reinterpret_cast<cpx<T> *>(smraw);
   const int64_t x0 = (int64_t)blockIdx.x * TX;
   const int total = n * TX;
-  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int j = idx / TX;
-    const int c = idx - j * TX;
-    const int64_t col = x0 + c;
-    const T v = (col < ncols) ? (T)X[(int64_t)j * ldx + col] : T(0);
-    T *slot = reinterpret_cast<T *>(&buf[((size_t)(c >> 1) << logn) + bitrev(j, logn)]);
-    slot[c & 1] = v;
+  // kLoadBatch loads in flight per thread before any is used
+  for (int i0 = threadIdx.x; i0 < total; i0 += kLoadBatch * blockDim.x) {
+    T v[kLoadBatch];
+#pragma unroll
+    for (int u = 0; u < kLoadBatch; ++u) {
+      const int idx = i0 + u * (int)blockDim.x;
+      const int j = idx / TX;
+      const int64_t col = x0 + (idx - j * TX);
+      v[u] = (idx < total && col < ncols) ? (T)X[(int64_t)j * ldx + col] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kLoadBatch; ++u) {
+      const int idx = i0 + u * (int)blockDim.x;
+      if (idx < total) {
+        const int j = idx / TX;
+        const int c = idx - j * TX;
+        T *slot = reinterpret_cast<T *>(&buf[((size_t)(c >> 1) << logn) + bitrev(j, logn)]);
+        slot[c & 1] = v[u];
+      }
+    }
   }
   __syncthreads();
   fft_smem<T>(buf, n, logn, TX >> 1, tw);
@@ -126,22 +142,38 @@ __global__ void __launch_bounds__(256) k_fft_r2c_res(const double *__restrict__ 
   cpx<T> *buf = reinterpret_cast<cpx<T> *>(smraw);
   const int64_t x0 = (int64_t)blockIdx.x * TX;
   const int total = n * TX;
-  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int j = idx / TX;
-    const int c = idx - j * TX;
-    const int64_t col = x0 + c;
-    T v = T(0);
-    if (col < ncols) {
-      const double *u = U + (int64_t)j * ncols;
-      double au = rxd[col] * u[col];
-      if (col > 0) au = fma(rxl[col], u[col - 1], au);
-      if (col + 1 < ncols) au = fma(rxu[col], u[col + 1], au);
-      double g = G[(int64_t)j * ncols + col];
-      if (j > 0) g += u[col - ncols];
-      v = (T)(g - au);
+  // blockDim.x is a multiple of TX, so every element a thread loads lies in one
+  // column: its residual coefficients are loaded once
+  const int c = (int)threadIdx.x % TX;
+  const int64_t col = x0 + c;
+  const bool live = col < ncols;
+  const double cl = (live && col > 0) ? rxl[col] : 0.0;
+  const double cd = live ? rxd[col] : 0.0;
+  const double cu = (live && col + 1 < ncols) ? rxu[col] : 0.0;
+  const int64_t ol = col > 0 ? -1 : 0, ou = col + 1 < ncols ? 1 : 0;  // in-range neighbour offsets
+  T *col_buf = reinterpret_cast<T *>(buf + ((size_t)(c >> 1) << logn)) + (c & 1);
+  constexpr int kB = kLoadBatch / 2;  // five FP64 loads per element
+  for (int j0 = (int)threadIdx.x / TX; j0 < n; j0 += kB * ((int)blockDim.x / TX)) {
+    double g[kB], um[kB], ul[kB], uc[kB], ur[kB];
+#pragma unroll
+    for (int q = 0; q < kB; ++q) {
+      const int j = j0 + q * ((int)blockDim.x / TX);
+      const bool in = live && j < n;
+      const double *u = U + (int64_t)j * ncols + col;
+      g[q] = in ? G[(int64_t)j * ncols + col] : 0.0;
+      uc[q] = in ? u[0] : 0.0;
+      ul[q] = in ? u[ol] : 0.0;
+      ur[q] = in ? u[ou] : 0.0;
+      um[q] = (in && j > 0) ? u[-ncols] : 0.0;
     }
-    T *slot = reinterpret_cast<T *>(&buf[((size_t)(c >> 1) << logn) + bitrev(j, logn)]);
-    slot[c & 1] = v;
+#pragma unroll
+    for (int q = 0; q < kB; ++q) {
+      const int j = j0 + q * ((int)blockDim.x / TX);
+      if (j < n) {
+        const double au = fma(cu, ur[q], fma(cl, ul[q], cd * uc[q]));
+        col_buf[2 * bitrev(j, logn)] = (T)((g[q] + um[q]) - au);
+      }
+    }
   }
   __syncthreads();
   fft_smem<T>(buf, n, logn, TX >> 1, tw);
@@ -161,50 +193,74 @@ __global__ void __launch_bounds__(256) k_fft_c2r(const cpx<T> *__restrict__ S, i
   const int np = TX >> 1;
   const int total = n * np;
   const int half = n >> 1;
-  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int k = idx / np;
-    const int p = idx - k * np;
-    const int64_t ca = x0 + 2 * p, cb = ca + 1;
-    const int kk = (k <= half) ? k : n - k;
-    cpx<T> A = mk<T>(T(0), T(0)), B = mk<T>(T(0), T(0));
-    if (ca < ncols) A = S[(int64_t)kk * lds + ca];
-    if (cb < ncols) B = S[(int64_t)kk * lds + cb];
-    if (k > half) {
-      A.y = -A.y;
-      B.y = -B.y;
+  for (int i0 = threadIdx.x; i0 < total; i0 += kLoadBatch * blockDim.x) {
+    cpx<T> A[kLoadBatch], B[kLoadBatch];
+#pragma unroll
+    for (int u = 0; u < kLoadBatch; ++u) {
+      const int idx = i0 + u * (int)blockDim.x;
+      const int k = idx / np;
+      const int p = idx - k * np;
+      const int64_t ca = x0 + 2 * p, cb = ca + 1;
+      const int kk = (k <= half) ? k : n - k;
+      A[u] = mk<T>(T(0), T(0));
+      B[u] = mk<T>(T(0), T(0));
+      if (idx < total && ca < ncols) A[u] = S[(int64_t)kk * lds + ca];
+      if (idx < total && cb < ncols) B[u] = S[(int64_t)kk * lds + cb];
     }
-    // conj(A + i B) = (A.x - B.y) - i (A.y + B.x)
-    buf[((size_t)p << logn) + bitrev(k, logn)] = mk<T>(A.x - B.y, -(A.y + B.x));
+#pragma unroll
+    for (int u = 0; u < kLoadBatch; ++u) {
+      const int idx = i0 + u * (int)blockDim.x;
+      if (idx < total) {
+        const int k = idx / np;
+        const int p = idx - k * np;
+        const T sg = k > half ? T(-1) : T(1);  // conjugate half
+        // conj(A + i B) = (A.x - B.y) - i (A.y + B.x)
+        buf[((size_t)p << logn) + bitrev(k, logn)] = mk<T>(A[u].x - sg * B[u].y, -(sg * A[u].y + B[u].x));
+      }
+    }
   }
   __syncthreads();
   fft_smem<T>(buf, n, logn, np, tw);
   const T inv_n = T(1) / T(n);
-  double ss = 0.0;
+  float ss = 0.0f;  // a few dozen squares per thread; the stop rule needs a few digits
   const int tot2 = n * TX;
-  for (int idx = threadIdx.x; idx < tot2; idx += blockDim.x) {
-    const int j = idx / TX;
-    const int c = idx - j * TX;
-    const int64_t col = x0 + c;
-    if (col >= ncols) continue;
-    const cpx<T> r = buf[((size_t)(c >> 1) << logn) + j];
-    const T v = ((c & 1) == 0) ? r.x * inv_n : -r.y * inv_n;
-    const int64_t o = (int64_t)j * ldo + col;
-    if (mode == 0) {
-      reinterpret_cast<double *>(out)[o] = (double)v;
-    } else if (mode == 1) {
-      reinterpret_cast<double *>(out)[o] += (double)v;
-    } else {
-      reinterpret_cast<float *>(out)[o] = (float)v;
+  for (int i0 = threadIdx.x; i0 < tot2; i0 += kLoadBatch * blockDim.x) {
+    double old[kLoadBatch];  // U before the update (mode 1)
+#pragma unroll
+    for (int u = 0; u < kLoadBatch; ++u) {
+      const int idx = i0 + u * (int)blockDim.x;
+      const int j = idx / TX;
+      const int64_t col = x0 + (idx - j * TX);
+      old[u] = (mode == 1 && idx < tot2 && col < ncols) ? reinterpret_cast<const double *>(out)[(int64_t)j * ldo + col]
+                                                         : 0.0;
     }
-    const float vf = (float)v;
-    ss += (double)(vf * vf);
+#pragma unroll
+    for (int u = 0; u < kLoadBatch; ++u) {
+      const int idx = i0 + u * (int)blockDim.x;
+      const int j = idx / TX;
+      const int c = idx - j * TX;
+      const int64_t col = x0 + c;
+      if (idx >= tot2 || col >= ncols) continue;
+      const cpx<T> r = buf[((size_t)(c >> 1) << logn) + j];
+      const T v = ((c & 1) == 0) ? r.x * inv_n : -r.y * inv_n;
+      const int64_t o = (int64_t)j * ldo + col;
+      if (mode == 0) {
+        reinterpret_cast<double *>(out)[o] = (double)v;
+      } else if (mode == 1) {
+        reinterpret_cast<double *>(out)[o] = old[u] + (double)v;
+      } else {
+        reinterpret_cast<float *>(out)[o] = (float)v;
+      }
+      const float vf = (float)v;
+      ss = fmaf(vf, vf, ss);
+    }
   }
   if (norm_part) {
-    ss = warp_sum(ss);
+    const double sd = warp_sum((double)ss);
     __shared__ double red[32];
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     __syncthreads();
-    if (l == 0) red[w] = ss;
+    if (l == 0) red[w] = sd;
     __syncthreads();
     if (threadIdx.x == 0) {
       double t = 0.0;
@@ -252,31 +308,54 @@ __global__ void __launch_bounds__(256) k_dst_y(const Tin *__restrict__ X, Tout *
   for (int idx = threadIdx.x; idx < np * N; idx += blockDim.x) buf[idx] = mk<T>(T(0), T(0));
   __syncthreads();
   const int total = (int)ny * TX;
-  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int y = idx / TX;
-    const int c = idx - y * TX;
-    const int64_t col = x0 + c;
-    const T v = (col < nx) ? (T)Xt[(int64_t)y * nx + col] : T(0);
-    cpx<T> *ser = buf + ((size_t)(c >> 1) << logN);
-    T *pos = reinterpret_cast<T *>(&ser[bitrev(y + 1, logN)]);
-    T *neg = reinterpret_cast<T *>(&ser[bitrev(N - (y + 1), logN)]);
-    pos[c & 1] = v;
-    neg[c & 1] = -v;
+  for (int i0 = threadIdx.x; i0 < total; i0 += kLoadBatch * blockDim.x) {
+    T v[kLoadBatch];
+#pragma unroll
+    for (int u = 0; u < kLoadBatch; ++u) {
+      const int idx = i0 + u * (int)blockDim.x;
+      const int y = idx / TX;
+      const int64_t col = x0 + (idx - y * TX);
+      v[u] = (idx < total && col < nx) ? (T)Xt[(int64_t)y * nx + col] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kLoadBatch; ++u) {
+      const int idx = i0 + u * (int)blockDim.x;
+      if (idx >= total) continue;
+      const int y = idx / TX;
+      const int c = idx - y * TX;
+      cpx<T> *ser = buf + ((size_t)(c >> 1) << logN);
+      T *pos = reinterpret_cast<T *>(&ser[bitrev(y + 1, logN)]);
+      T *neg = reinterpret_cast<T *>(&ser[bitrev(N - (y + 1), logN)]);
+      pos[c & 1] = v[u];
+      neg[c & 1] = -v[u];
+    }
   }
   __syncthreads();
   fft_smem<T>(buf, N, logN, np, tw);
-  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int l = idx / TX;  // output index l = 0..ny-1  <->  mode l+1
-    const int c = idx - l * TX;
-    const int64_t col = x0 + c;
-    if (col >= nx) continue;
-    const cpx<T> z = buf[((size_t)(c >> 1) << logN) + l + 1];
-    const T v = ((c & 1) == 0) ? (T(-0.5) * scale) * z.y : (T(0.5) * scale) * z.x;
-    const int64_t o = (int64_t)l * nx + col;
-    if (mode == 0) {
-      Yt[o] = (Tout)v;
-    } else {
-      Yt[o] += (Tout)v;
+  for (int i0 = threadIdx.x; i0 < total; i0 += kLoadBatch * blockDim.x) {
+    Tout old[kLoadBatch];  // Y before the update (mode 1)
+#pragma unroll
+    for (int u = 0; u < kLoadBatch; ++u) {
+      const int idx = i0 + u * (int)blockDim.x;
+      const int l = idx / TX;
+      const int64_t col = x0 + (idx - l * TX);
+      old[u] = (mode != 0 && idx < total && col < nx) ? Yt[(int64_t)l * nx + col] : Tout(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kLoadBatch; ++u) {
+      const int idx = i0 + u * (int)blockDim.x;
+      const int l = idx / TX;  // output index l = 0..ny-1  <->  mode l+1
+      const int c = idx - l * TX;
+      const int64_t col = x0 + c;
+      if (idx >= total || col >= nx) continue;
+      const cpx<T> z = buf[((size_t)(c >> 1) << logN) + l + 1];
+      const T v = ((c & 1) == 0) ? (T(-0.5) * scale) * z.y : (T(0.5) * scale) * z.x;
+      const int64_t o = (int64_t)l * nx + col;
+      if (mode == 0) {
+        Yt[o] = (Tout)v;
+      } else {
+        Yt[o] = old[u] + (Tout)v;
+      }
     }
   }
 }
@@ -289,13 +368,18 @@ static int ilog2(int n) {
 
 // Columns per CTA: as many as fit ~96 KB of series (two CTAs per SM), capped,
 // then narrowed (down to 4 columns = one 32-byte sector of doubles per row) until
-// the grid covers every SM twice.
+// the grid covers every SM four times.
 template <typename T>
-static int pick_tx(int n, int cap, int64_t ncols) {
+static int pick_tx(int n, int cap, int64_t ncols, int req = 0) {
   const size_t budget = 96 * 1024;
+  if (req) {  // the caller's choice, within the shared-memory budget of one CTA
+    int tx = std::min(req, cap);
+    while (tx > 2 && (size_t)(tx / 2) * n * sizeof(cpx<T>) > 2 * budget) tx >>= 1;
+    return tx;
+  }
   int tx = cap;
   while (tx > 2 && (size_t)(tx / 2) * n * sizeof(cpx<T>) > budget) tx >>= 1;
-  while (tx > 4 && (ncols + tx - 1) / tx < 2 * (int64_t)sm_count()) tx >>= 1;
+  while (tx > 4 && (ncols + tx - 1) / tx < 4 * (int64_t)sm_count()) tx >>= 1;
   return tx;
 }
 
@@ -312,7 +396,7 @@ template <typename T, typename Tin>
 void launch_fft_r2c(Ctx &c, const Tin *X, int64_t ldx, int64_t ncols, int n, const cpx<T> *tw,
                     cpx<T> *S, int64_t lds) {
   const int logn = ilog2(n);
-  const int TX = pick_tx<T>(n, sizeof(T) == 8 ? 8 : 16, ncols);
+  const int TX = pick_tx<T>(n, sizeof(T) == 8 ? 8 : 16, ncols, c.fft_cols);
   const size_t smem = (size_t)(TX / 2) * n * sizeof(cpx<T>);
   const int grid = (int)((ncols + TX - 1) / TX);
   const double bytes = (double)n * ncols * sizeof(Tin) + (double)(n / 2 + 1) * ncols * sizeof(cpx<T>);
@@ -329,7 +413,7 @@ template <typename T>
 void launch_fft_r2c_residual(Ctx &c, const double *G, const double *U, int64_t ncols, int n, const double *rxl,
                              const double *rxd, const double *rxu, const cpx<T> *tw, cpx<T> *S, int64_t lds) {
   const int logn = ilog2(n);
-  const int TX = pick_tx<T>(n, sizeof(T) == 8 ? 8 : 16, ncols);
+  const int TX = pick_tx<T>(n, sizeof(T) == 8 ? 8 : 16, ncols, c.fft_cols);
   const size_t smem = (size_t)(TX / 2) * n * sizeof(cpx<T>);
   const int grid = (int)((ncols + TX - 1) / TX);
   const double bytes = (double)n * ncols * 16.0 + (double)(n / 2 + 1) * ncols * sizeof(cpx<T>);
@@ -348,7 +432,7 @@ void launch_fft_c2r(Ctx &c, const cpx<T> *S, int64_t lds, int64_t ncols, int n, 
   StepFinish fin{};
   if (finp && norm_part) fin = *finp;
   const int logn = ilog2(n);
-  const int TX = pick_tx<T>(n, sizeof(T) == 8 ? 8 : 16, ncols);
+  const int TX = pick_tx<T>(n, sizeof(T) == 8 ? 8 : 16, ncols, c.fft_cols);
   const size_t smem = (size_t)(TX / 2) * n * sizeof(cpx<T>);
   const int grid = (int)((ncols + TX - 1) / TX);
   if (nparts) *nparts = grid;

@@ -50,6 +50,7 @@ enum ScalIndex {
 // optional per-launch timing with CUDA events recorded on that same stream.
 struct Ctx {
   cudaStream_t stream = nullptr;
+  int fft_cols = 0;  // columns per CTA of the time FFTs (0 = choose per launch)
   bool timing = false;
   int64_t launches = 0;
   cudaError_t err = cudaSuccess;
@@ -145,7 +146,9 @@ struct PintGeom {
   int acc_rows;  // partial rows per block in acc_part (R, or CTAs when cta_sum)
   int stage;     // 1: tau K staged in shared memory once per launch
 };
-PintGeom pint_geometry(int nf, int nblk, int blen, int target_teams, int elem_bytes);
+// m_req / teams_req: rows per thread and teams per CTA requested by the caller (0 = choose)
+PintGeom pint_geometry(int nf, int nblk, int blen, int target_teams, int elem_bytes, int m_req = 0,
+                       int teams_req = 0);
 void set_acc_rows(PintGeom &g);  // recompute cta_sum / acc_rows after changing R
 
 template <typename T>

@@ -65,8 +65,10 @@ __device__ __forceinline__ void coef(const PintArgs<T> &a, const T *cs, int cs_s
   }
 }
 
-template <typename T, int M>
-__global__ void __launch_bounds__(M >= 16 ? 256 : 512) k_pint(PintGeom g, PintArgs<T> a, size_t team_bytes) {
+// MAXT: the launch's thread count is at most MAXT (256 leaves room for 255
+// registers per thread, which the FP64 variants use without spilling).
+template <typename T, int M, int MAXT>
+__global__ void __launch_bounds__(MAXT) k_pint(PintGeom g, PintArgs<T> a, size_t team_bytes) {
   if (a.skip_flag && *a.skip_flag) return;
   const int P = g.P;
   const int tic = threadIdx.x / P;
@@ -80,6 +82,8 @@ __global__ void __launch_bounds__(M >= 16 ? 256 : 512) k_pint(PintGeom g, PintAr
   const int blen = g.blen;
   const int64_t off = (int64_t)blk * blen;
   const int N = P;  // condensed interface rows
+  // elements per batch of back-to-back loads (fewer in FP64, where registers are scarcer)
+  constexpr int SB = sizeof(T) == 8 ? (M < 4 ? M : 4) : M;
 
   extern __shared__ __align__(16) unsigned char smraw[];
   unsigned char *base = smraw + (size_t)tic * team_bytes;
@@ -114,19 +118,31 @@ __global__ void __launch_bounds__(M >= 16 ? 256 : 512) k_pint(PintGeom g, PintAr
   if (cs && k0 < k1) {
     // tau K does not depend on k: stage the team's block once (read after the first
     // team barrier of the k loop)
-    for (int e = t; e < P * M; e += P) {
-      const int pe = e + e / M;
-      T lo = T(0), di = T(0), up = T(0);
-      if (e < blen) {
-        lo = a.tlo[off + e];
-        di = a.tdiag[off + e];
-        up = a.tup[off + e];
+#pragma unroll
+    for (int i0 = 0; i0 < M; i0 += SB) {
+      T lo[SB], di[SB], up[SB];
+#pragma unroll
+      for (int i = 0; i < SB; ++i) {
+        const int e = t + (i0 + i) * P;
+        const bool in = e < blen;
+        lo[i] = in ? a.tlo[off + e] : T(0);
+        di[i] = in ? a.tdiag[off + e] : T(0);
+        up[i] = in ? a.tup[off + e] : T(0);
       }
-      cs[pe] = lo;
-      cs[cs_stride + pe] = di;
-      cs[2 * cs_stride + pe] = up;
+#pragma unroll
+      for (int i = 0; i < SB; ++i) {
+        const int e = t + (i0 + i) * P;
+        const int pe = e + e / M;
+        cs[pe] = lo[i];
+        cs[cs_stride + pe] = di[i];
+        cs[2 * cs_stride + pe] = up[i];
+      }
     }
   }
+
+  // Thread t owns elements e = t + i P (i < M) of the block in every load loop
+  // below; each loop issues all its global loads before using them, so a thread
+  // waits for one memory latency per loop rather than one per element.
 
   // x_m = V_m y_m for the team's rows (final loop of Algorithm 1), kept in the
   // accumulator region, which this pass does not otherwise use
@@ -134,18 +150,32 @@ __global__ void __launch_bounds__(M >= 16 ? 256 : 512) k_pint(PintGeom g, PintAr
   if (a.xm_count && active) {
     xs = acc;
     const int m = *a.xm_count;
-    for (int e = t; e < P * M; e += P) {
-      T v = T(0);
-      if (e < blen)
-        for (int q = 0; q < m; ++q) v += (T)a.xm_y[q] * a.V[(int64_t)q * a.ldv + off + e];
-      xs[e] = v;
+    T v[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) v[i] = T(0);
+    for (int q = 0; q < m; ++q) {
+      const T yq = (T)a.xm_y[q];
+      const T *vq = a.V + (int64_t)q * a.ldv + off;
+#pragma unroll
+      for (int i = 0; i < M; ++i)
+        if (t + i * P < blen) v[i] += yq * vq[t + i * P];
     }
+#pragma unroll
+    for (int i = 0; i < M; ++i) xs[t + i * P] = v[i];
     if (rr == 0 && a.xm_out) {
-      for (int e = t; e < blen; e += P) {
-        double v = 0.0;
-        for (int q = 0; q < m; ++q) v += a.xm_y[q] * a.xm_Vd[(int64_t)q * a.ldv + off + e];
-        a.xm_out[off + e] = v;
+      double vd[M];
+#pragma unroll
+      for (int i = 0; i < M; ++i) vd[i] = 0.0;
+      for (int q = 0; q < m; ++q) {
+        const double yq = a.xm_y[q];
+        const double *vq = a.xm_Vd + (int64_t)q * a.ldv + off;
+#pragma unroll
+        for (int i = 0; i < M; ++i)
+          if (t + i * P < blen) vd[i] += yq * vq[t + i * P];
       }
+#pragma unroll
+      for (int i = 0; i < M; ++i)
+        if (t + i * P < blen) a.xm_out[off + t + i * P] = vd[i];
     }
   }
 
@@ -153,21 +183,34 @@ __global__ void __launch_bounds__(M >= 16 ? 256 : 512) k_pint(PintGeom g, PintAr
     const double2 sk = a.shift[k];
     const cpx<T> s = mk<T>((T)sk.x, (T)sk.y);
     // 1. stage the right-hand side (element e at dd[e + e/M])
-    for (int e = t; e < P * M; e += P) {
-      cpx<T> v = mk<T>(T(0), T(0));
-      if (e < blen) {
-        const int64_t j = off + e;
-        if (a.R) {
-          v = a.R[(int64_t)k * a.ldr + j];
-          if (xs)
-            v.x -= xs[e];
-          else if (rvec)
-            v.x -= rvec[j];
-        } else {
-          v.x = rvec[j];
+#pragma unroll
+    for (int i0 = 0; i0 < M; i0 += SB) {
+      cpx<T> v[SB];
+      T sub[SB];
+#pragma unroll
+      for (int i = 0; i < SB; ++i) {
+        const int e = t + (i0 + i) * P;
+        v[i] = mk<T>(T(0), T(0));
+        sub[i] = T(0);
+        if (e < blen) {
+          const int64_t j = off + e;
+          if (a.R) {
+            v[i] = a.R[(int64_t)k * a.ldr + j];
+            if (xs)
+              sub[i] = xs[e];
+            else if (rvec)
+              sub[i] = rvec[j];
+          } else {
+            v[i].x = rvec[j];
+          }
         }
       }
-      dd[e + e / M] = v;
+#pragma unroll
+      for (int i = 0; i < SB; ++i) {
+        const int e = t + (i0 + i) * P;
+        v[i].x -= sub[i];
+        dd[e + e / M] = v[i];
+      }
     }
     team_sync(P, tic);
 
@@ -275,7 +318,11 @@ __global__ void __launch_bounds__(M >= 16 ? 256 : 512) k_pint(PintGeom g, PintAr
 
     // 5. store
     if (a.Y) {
-      for (int e = t; e < blen; e += P) a.Y[(int64_t)k * a.ldy + off + e] = dd[e + e / M];
+#pragma unroll
+      for (int i = 0; i < M; ++i) {
+        const int e = t + i * P;
+        if (e < blen) a.Y[(int64_t)k * a.ldy + off + e] = dd[e + e / M];
+      }
     }
     // 6. dots with the Krylov basis
     if (mdots > 0) {
@@ -283,11 +330,15 @@ __global__ void __launch_bounds__(M >= 16 ? 256 : 512) k_pint(PintGeom g, PintAr
       for (int q = 0; q < mdots; ++q) {
         T px = T(0), py = T(0);
         const T *vq = a.V + (int64_t)q * a.ldv + off;
-        for (int e = t; e < blen; e += P) {
-          const cpx<T> y = dd[e + e / M];
-          const T v = vq[e];
-          px += v * y.x;
-          py += v * y.y;
+        T vv[M];
+#pragma unroll
+        for (int i = 0; i < M; ++i) vv[i] = (t + i * P < blen) ? vq[t + i * P] : T(0);
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+          const int e = t + i * P;
+          const cpx<T> y = dd[e + e / M];  // zero beyond blen
+          px += vv[i] * y.x;
+          py += vv[i] * y.y;
         }
         double sx = warp_sum((double)px);
         double sy = warp_sum((double)py);
@@ -373,22 +424,28 @@ __global__ void __launch_bounds__(1024) k_zsum(int nf, int64_t n, const cpx<T> *
   if (skip_flag && *skip_flag) return;
   __shared__ double sm[32][33];
   const int64_t j = (int64_t)blockIdx.x * 32 + threadIdx.x;
-  T s0 = T(0), s1 = T(0);
+  constexpr int B = 8;  // rows of H in flight per thread
+  T acc[B];
+#pragma unroll
+  for (int u = 0; u < B; ++u) acc[u] = T(0);
   if (j < n) {
-    int k = threadIdx.y;
-    for (; k + 32 < nf; k += 64) {
-      const double2 o0 = omega[k], o1 = omega[k + 32];
-      const cpx<T> h0 = H[(int64_t)k * ldh + j], h1 = H[(int64_t)(k + 32) * ldh + j];
-      s0 += (T)o0.x * h0.x - (T)o0.y * h0.y;
-      s1 += (T)o1.x * h1.x - (T)o1.y * h1.y;
-    }
-    for (; k < nf; k += 32) {
-      const double2 o0 = omega[k];
-      const cpx<T> h0 = H[(int64_t)k * ldh + j];
-      s0 += (T)o0.x * h0.x - (T)o0.y * h0.y;
+    for (int k0 = threadIdx.y; k0 < nf; k0 += 32 * B) {
+      cpx<T> h[B];
+      double2 o[B];
+#pragma unroll
+      for (int u = 0; u < B; ++u) {
+        const int k = k0 + 32 * u;
+        h[u] = k < nf ? H[(int64_t)k * ldh + j] : cpx<T>{T(0), T(0)};
+        o[u] = k < nf ? omega[k] : make_double2(0.0, 0.0);
+      }
+#pragma unroll
+      for (int u = 0; u < B; ++u) acc[u] += (T)o[u].x * h[u].x - (T)o[u].y * h[u].y;
     }
   }
-  sm[threadIdx.y][threadIdx.x] = (double)s0 + (double)s1;
+  double tot = 0.0;
+#pragma unroll
+  for (int u = 0; u < B; ++u) tot += (double)acc[u];
+  sm[threadIdx.y][threadIdx.x] = tot;
   __syncthreads();
   if (threadIdx.y == 0 && j < n) {
     double t = 0.0;
@@ -421,21 +478,24 @@ void set_acc_rows(PintGeom &g) {
   g.acc_rows = g.cta_sum ? (g.R + g.teams_per_cta - 1) / g.teams_per_cta : g.R;
 }
 
-PintGeom pint_geometry(int nf, int nblk, int blen, int target_teams, int elem_bytes) {
+PintGeom pint_geometry(int nf, int nblk, int blen, int target_teams, int elem_bytes, int m_req, int teams_req) {
   PintGeom g;
   g.nf = nf;
   g.nblk = nblk;
   g.blen = blen;
-  // rows per thread: longer chunks in binary32 (registers allow it) halve the
-  // threads per block and the interface system
-  g.M = blen <= 128 ? 4 : (elem_bytes == 8 && blen > 512 ? 16 : 8);
+  // rows per thread: 8 balances the serial chunk elimination against the PCR depth
+  // (16 rows, binary32 only, is available on request)
+  g.M = blen <= 128 ? 4 : 8;
+  if (m_req) g.M = m_req;
   g.P = std::max(32, next_pow2((blen + g.M - 1) / g.M));
+  const int max_threads = g.M >= 16 ? 256 : 512;  // the kernel's launch bounds
   g.teams_per_cta = std::max(1, 256 / g.P);
   int R = (target_teams + nblk - 1) / nblk;
   g.R = std::max(1, std::min(R, nf));
   // fewer teams per CTA while the grid would not cover every SM
   const int nteams = nblk * g.R;
   while (g.teams_per_cta > 1 && (nteams + g.teams_per_cta - 1) / g.teams_per_cta < sm_count()) g.teams_per_cta >>= 1;
+  if (teams_req) g.teams_per_cta = std::max(1, std::min(teams_req, max_threads / g.P));
   // stage tau K in shared memory when the CTA stays within ~160 KB
   const size_t esz = elem_bytes == 16 ? 8 : 4;  // real type of the compute precision
   const size_t rest = (size_t)g.P * (g.M + 1) * 2 * esz + (size_t)g.P * 5 * 2 * esz + (size_t)g.P * g.M * esz +
@@ -453,7 +513,8 @@ static void launch_pint_m(Ctx &c, const PintGeom &g, const PintArgs<T> &a) {
   const int nteams = g.nblk * g.R;
   const int grid = (nteams + g.teams_per_cta - 1) / g.teams_per_cta;
   const int threads = g.P * g.teams_per_cta;
-  cudaFuncSetAttribute(k_pint<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = threads <= 256 ? k_pint<T, M, 256> : k_pint<T, M, (M >= 16 ? 256 : 512)>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   // algorithmic bytes: spectrum rows read/written as requested, plus the vector rhs
   double bytes = 0.0;
   const double per = (double)g.nf * g.nblk * g.blen;
@@ -462,7 +523,7 @@ static void launch_pint_m(Ctx &c, const PintGeom &g, const PintArgs<T> &a) {
   const bool dots = a.mcount ? a.want_dots != 0 : a.mdots > 0;
   const char *fam = sizeof(T) == 8 ? (a.Y ? "pint_store_f64" : (dots ? "pint_dots_f64" : "pint_acc_f64"))
                                    : (a.Y ? "pint_store_f32" : (dots ? "pint_dots_f32" : "pint_acc_f32"));
-  c.launch(fam, bytes, [&] { k_pint<T, M><<<grid, threads, smem, c.stream>>>(g, a, tb); });
+  c.launch(fam, bytes, [&] { kern<<<grid, threads, smem, c.stream>>>(g, a, tb); });
 }
 
 template <typename T>

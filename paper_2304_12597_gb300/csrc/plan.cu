@@ -245,6 +245,24 @@ pd_status validate(const pd_desc *d) {
         return fail(PD_ERR_UNSUPPORTED, "T_y must be symmetric Toeplitz");
     }
   }
+  if (d->tune_pint_rows != 0 && d->tune_pint_rows != 4 && d->tune_pint_rows != 8 && d->tune_pint_rows != 16)
+    return fail(PD_ERR_INVALID_ARG, "tune_pint_rows must be 0, 4, 8 or 16");
+  if (d->tune_pint_rows == 16 && d->precision != PD_MIXED)
+    return fail(PD_ERR_UNSUPPORTED, "16 rows per thread are built for PD_MIXED only");
+  if (d->tune_pint_rows) {  // one team of P threads must fit one CTA
+    int64_t P = 32;
+    while (P * d->tune_pint_rows < d->nx) P <<= 1;
+    if (P > (d->tune_pint_rows == 16 ? 256 : 512))
+      return fail(PD_ERR_UNSUPPORTED, "tune_pint_rows %d is too few rows per thread for blocks of %lld rows",
+                  d->tune_pint_rows, (long long)d->nx);
+  }
+  if (d->tune_pint_teams < 0 || (d->tune_pint_teams && !is_pow2(d->tune_pint_teams)) || d->tune_pint_teams > 16)
+    return fail(PD_ERR_INVALID_ARG, "tune_pint_teams must be 0 or a power of two <= 16");
+  if (d->tune_krylov_ctas < 0 || d->tune_krylov_ctas > 1024 || d->tune_cap_ctas < 0 || d->tune_cap_ctas > 1024)
+    return fail(PD_ERR_INVALID_ARG, "tune_krylov_ctas and tune_cap_ctas must be in [0, 1024]");
+  if (d->tune_fft_cols != 0 && d->tune_fft_cols != 2 && d->tune_fft_cols != 4 && d->tune_fft_cols != 8 &&
+      d->tune_fft_cols != 16)
+    return fail(PD_ERR_INVALID_ARG, "tune_fft_cols must be 0, 2, 4, 8 or 16");
   const int64_t nbar = d->nx * (d->dim == 2 ? d->ny : 1);
   if (nbar > (int64_t)1 << 28 || d->nt * nbar > (int64_t)1 << 34)
     return fail(PD_ERR_UNSUPPORTED, "problem too large for this build");
@@ -271,7 +289,7 @@ void fill_geometry(pd_plan *p, const pd_desc *d) {
   p->lds = (p->nbar + 31) / 32 * 32;
   const int sms = pd::sm_count();
   const int esz = d->precision == PD_FP64 ? 16 : 8;
-  pd::PintGeom g0 = pd::pint_geometry(p->nf, p->nblk, p->blen, 1, esz);
+  pd::PintGeom g0 = pd::pint_geometry(p->nf, p->nblk, p->blen, 1, esz, d->tune_pint_rows, d->tune_pint_teams);
   // one wave of resident teams: occupancy estimated from shared memory and threads
   const size_t team_bytes = (size_t)g0.P * (g0.M + 1) * esz + (size_t)2 * g0.P * 5 * esz + (size_t)g0.P * g0.M * 8 +
                             (size_t)(g0.P / 32) * 33 * 16;
@@ -280,12 +298,15 @@ void fill_geometry(pd_plan *p, const pd_desc *d) {
   int by_threads = std::max(1, 2048 / (g0.P * g0.teams_per_cta));
   const int ctas_per_sm = std::max(1, std::min(by_smem, by_threads));
   const int target = sms * ctas_per_sm * g0.teams_per_cta;
-  p->geom = pd::pint_geometry(p->nf, p->nblk, p->blen, target, esz);
+  p->geom = pd::pint_geometry(p->nf, p->nblk, p->blen, target, esz, d->tune_pint_rows, d->tune_pint_teams);
   // Krylov vector kernels: one 512-thread CTA (plain launch) for vectors up to 8192
   // entries; beyond, cooperative 64-thread CTAs, at most one per SM (co-resident)
   p->blas_grid = p->nbar <= 8192 ? 1 : (int)std::max<int64_t>(1, std::min<int64_t>((p->nbar + 63) / 64, (int64_t)sms));
-  // capacitance terms: a few frequencies per warp keeps the partial reduction short
-  p->k5_grid = std::max(1, std::min((p->nf + 15) / 16, 64));
+  // capacitance terms: one frequency per warp (four warps per CTA)
+  p->k5_grid = std::max(1, std::min((p->nf + 3) / 4, 1024));
+  if (d->tune_krylov_ctas) p->blas_grid = std::min(d->tune_krylov_ctas, sms);
+  if (d->tune_cap_ctas) p->k5_grid = d->tune_cap_ctas;
+  p->ctx.fft_cols = d->tune_fft_cols;
 }
 
 // Assign (or size) every device buffer.

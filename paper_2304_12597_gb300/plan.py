@@ -25,13 +25,15 @@ class Plan:
     """All-at-once backward-Euler solver (Algorithm 1 + Algorithm 2) for one problem shape.
 
     Parameters mirror ``pd_desc`` in include/paradiag.h.  ``precision`` is
-    "fp64" or "mixed".  G and U passed to ``solve`` are (nt, nx*ny) float64 CUDA
+    "fp64" or "mixed".  ``tune`` maps launch-geometry names (pint_rows, pint_teams,
+    krylov_ctas, cap_ctas, fft_cols) to values; 0 or absent = built-in choice.
+    G and U passed to ``solve`` are (nt, nx*ny) float64 CUDA
     tensors, row j = time step j+1, spatial index contiguous.
     """
 
     def __init__(self, *, dim, nx, nt, tau, k_lo, k_diag, k_up, ny=1, k_lo_y=None, k_diag_y=None,
                  k_up_y=None, precision="mixed", maxit=0, eps_krylov=0.0, max_refine=0, refine_tol=0.0,
-                 host_io=False, no_graph=False, device=None, stream=None, workspace="torch"):
+                 host_io=False, no_graph=False, tune=None, device=None, stream=None, workspace="torch"):
         import torch
 
         self._torch = torch
@@ -59,6 +61,8 @@ class Plan:
         d.stream = ctypes.c_void_p(self.stream.cuda_stream)
         d.host_io = 1 if host_io else 0
         d.no_graph = 1 if no_graph else 0
+        for key, val in (tune or {}).items():  # launch geometry: pint_rows, pint_teams, krylov_ctas, ...
+            setattr(d, "tune_" + key, int(val))
         self.desc = d
         self.workspace_bytes = B.paradiag_workspace_size(d)
         self.handle = None

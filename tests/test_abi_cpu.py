@@ -96,6 +96,8 @@ def _size_status(B, d):
 
 def test_valid_descriptors_have_a_workspace(B):
     for kw in ({}, {"precision": 1}, {"nt": 1}, {"n": 1}, {"n": 4096, "nt": 2048, "precision": 1},
+               {"precision": 1, "tune_pint_rows": 16, "tune_pint_teams": 2, "tune_krylov_ctas": 8,
+                "tune_cap_ctas": 3, "tune_fft_cols": 2},
                {"dim": 2, "ny": 7}, {"dim": 2, "ny": 255, "n": 255, "nt": 256, "precision": 1}):
         st, n = _size_status(B, _desc(B, **kw))
         assert st == 0, (kw, B.last_error())
@@ -118,6 +120,13 @@ def test_valid_descriptors_have_a_workspace(B):
     ({"dim": 2, "ny": 6}, 2),
     ({"dim": 2, "ny": 7, "y_diag": np.array([2, 2, 2, 3, 2, 2, 2.0])}, 2),
     ({"dim": 2, "ny": 7, "y_up": np.array([-1, -1, -0.5, -1, -1, -1, -1.0])}, 2),
+    ({"tune_pint_rows": 5}, 1),
+    ({"tune_pint_rows": 16}, 2),              # 16 rows per thread: PD_MIXED only
+    ({"tune_pint_rows": 4, "n": 4095}, 2),    # 1024 threads per team
+    ({"tune_pint_teams": 3}, 1),
+    ({"tune_krylov_ctas": -1}, 1),
+    ({"tune_cap_ctas": 5000}, 1),
+    ({"tune_fft_cols": 6}, 1),
 ])
 def test_bad_descriptors_are_rejected(B, kw, code):
     st, _ = _size_status(B, _desc(B, **kw))
