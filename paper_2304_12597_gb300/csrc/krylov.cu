@@ -30,26 +30,40 @@ namespace pd {
 
 constexpr int kBlas = 64;  // small CTAs: FP64 reduction trees are short per SM
 
-__device__ __forceinline__ double block_sum(double v, double *red) {
-  v = warp_sum(v);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+constexpr int kBlasSingle = 512;  // threads of the one-CTA variants (short vectors)
+constexpr int kRedQ = 4;          // sums reduced side by side
+constexpr int kRedWords = kRedQ * kBlasSingle;
+
+// out[i] = sum over the CTA of s[i], i < nq <= kRedQ (shared `out`, valid for every
+// thread on return).  The partials go through shared memory and warp i adds column
+// i (also i + warps, ... when the CTA has fewer warps than sums), so each sum costs
+// blockDim/32 + 5 dependent FP64 adds on one warp instead of a shuffle tree on every
+// warp (GB300's FP64 rate makes the instruction count matter).
+// red: kRedWords doubles of shared memory.
+__device__ void block_sums(const double *s, int nq, double *red, double *out) {
+  const int nt = blockDim.x, tid = threadIdx.x;
+  for (int i = 0; i < nq; ++i) red[i * nt + tid] = s[i];
   __syncthreads();
-  if (l == 0) red[w] = v;
-  __syncthreads();
-  double t = 0.0;
-  if (threadIdx.x < 32) {
-    t = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+  const int l = tid & 31, nw = nt >> 5;
+  for (int w = tid >> 5; w < nq; w += nw) {  // fewer warps than sums: warps take several
+    double t = 0.0;
+    for (int i = l; i < nt; i += 32) t += red[w * nt + i];
     t = warp_sum(t);
+    if (l == 0) out[w] = t;
   }
-  return t;  // valid in warp 0
+  __syncthreads();
+}
+
+__device__ __forceinline__ double block_sum(double v, double *red) {
+  __shared__ double out1[1];
+  block_sums(&v, 1, red, out1);
+  return out1[0];  // valid in every thread
 }
 
 // Cooperative kernels: one CTA per SM at most (co-residency is checked by the
 // cooperative launch), phases separated by grid-wide barriers.  `part` holds
 // three (grid, ld) panels of per-CTA partial sums; every CTA re-reduces a panel
 // in the same order, so all CTAs see identical coefficients.
-
-constexpr int kBlasSingle = 512;  // threads of the one-CTA variants (short vectors)
 
 // Barrier between phases: grid-wide for the cooperative variant; with a single CTA
 // (short vectors) a CTA barrier is the same thing and needs no cooperative launch.
@@ -62,16 +76,25 @@ __device__ __forceinline__ void phase_sync() {
 }
 
 // part_row[q] = sum over this CTA's slice of V[q][j] x[j] (q < m); part_row[m] = ||x||^2.
+// kRedQ sums per pass over x.
 __device__ void cta_dots(int n, int m, const double *__restrict__ V, const double *__restrict__ x,
                          double *part_row, double *red) {
-  for (int q = 0; q <= m; ++q) {
-    double s = 0.0;
+  __shared__ double out[kRedQ];
+  for (int q0 = 0; q0 <= m; q0 += kRedQ) {
+    const int nq = min(kRedQ, m + 1 - q0);
+    double s[kRedQ];
+#pragma unroll
+    for (int i = 0; i < kRedQ; ++i) s[i] = 0.0;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
       const double xj = x[j];
-      s += (q < m ? V[(int64_t)q * n + j] : xj) * xj;
+#pragma unroll
+      for (int i = 0; i < kRedQ; ++i) {
+        const int q = q0 + i;
+        if (i < nq) s[i] += (q < m ? V[(int64_t)q * n + j] : xj) * xj;
+      }
     }
-    s = block_sum(s, red);
-    if (threadIdx.x == 0) part_row[q] = s;
+    block_sums(s, nq, red, out);
+    if ((int)threadIdx.x < nq) part_row[q0 + threadIdx.x] = out[threadIdx.x];
   }
 }
 
@@ -101,7 +124,7 @@ __global__ void __launch_bounds__(COOP ? kBlas : kBlasSingle) k_init_v0_coop(con
                                                         int use_handle, cudaGraphConditionalHandle h, double *T,
                                                         int nT) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nT; i += gridDim.x * blockDim.x) T[i] = 0.0;
-  __shared__ double red[32];
+  __shared__ double red[kRedWords];
   __shared__ double c[34];
   double s = 0.0;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) s += b[j] * b[j];
@@ -143,7 +166,7 @@ __global__ void __launch_bounds__(COOP ? kBlas : kBlasSingle) k_arnoldi_coop(int
                                                         const double *__restrict__ kup, double *V, float *Vf,
                                                         double *w, double *T, int ldT, double *part, int ld,
                                                         double *scal, int *flags) {
-  __shared__ double red[32];
+  __shared__ double red[kRedWords];
   __shared__ double c[34];
   const int m = flags[F_M] + 1;  // the step computed here produces v_m
   const int G = gridDim.x;
@@ -198,7 +221,7 @@ __global__ void __launch_bounds__(COOP ? kBlas : kBlasSingle) k_project_coop(int
                                                         double tau, double *part, int ld, double *scal,
                                                         int *flags, KrylovCtl kc, int use_handle,
                                                         cudaGraphConditionalHandle h) {
-  __shared__ double red[32];
+  __shared__ double red[kRedWords];
   __shared__ double c[34];
   const int m = flags[F_M] + 1;
   const int G = gridDim.x;
@@ -376,6 +399,7 @@ __device__ void capacitance_solve_cta(int nf, int m, int nparts, const double *m
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int i = wid; i < m * m; i += nw) {
       double s = 0.0;
+#pragma unroll 4
       for (int p = lane; p < nparts; p += 32) s += msys_part[(int64_t)p * m * m + i];
       s = warp_sum(s);
       if (lane == 0) H[i] = mk<double>(s + (((i / m) == (i % m)) ? 1.0 : 0.0), 0.0);
@@ -390,6 +414,7 @@ __device__ void capacitance_solve_cta(int nf, int m, int nparts, const double *m
     y[threadIdx.x] = ys[threadIdx.x];
   }
   __syncthreads();
+#pragma unroll 4
   for (int k = threadIdx.x; k < nf; k += blockDim.x) {
     double cx = 0.0, cy = 0.0;
     for (int q = 0; q < m; ++q) {

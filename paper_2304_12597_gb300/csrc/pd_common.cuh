@@ -43,7 +43,15 @@ template <typename T>
 __device__ __forceinline__ cpx<T> fnms_r(cpx<T> a, T s, cpx<T> c) { return mk<T>(a.x - s * c.x, a.y - s * c.y); }
 // 1 / a  =  conj(a) / |a|^2.  The operands met here are bounded away from zero and
 // from overflow (|a| between ~1e-3 and ~1e8), so no Smith-style scaling is needed.
-__device__ __forceinline__ float rcp_rn(float v) { return __frcp_rn(v); }
+// binary32: the hardware approximation refined by one Newton-Raphson step,
+// r + r (1 - v r), which brings it to within rounding of 1/v for the normal-range
+// operands met here without the range checks of a correctly rounded reciprocal;
+// binary64: correctly rounded.
+__device__ __forceinline__ float rcp_rn(float v) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+  return fmaf(r, fmaf(-v, r, 1.0f), r);
+}
 __device__ __forceinline__ double rcp_rn(double v) { return __drcp_rn(v); }
 template <typename T>
 __device__ __forceinline__ cpx<T> recip(cpx<T> a) {

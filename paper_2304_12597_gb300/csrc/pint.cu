@@ -182,6 +182,8 @@ __global__ void __launch_bounds__(MAXT) k_pint(PintGeom g, PintArgs<T> a, size_t
   for (int k = k0; k < k1; ++k) {
     const double2 sk = a.shift[k];
     const cpx<T> s = mk<T>((T)sk.x, (T)sk.y);
+    const cpx<T> *Rk = a.R ? a.R + (int64_t)k * a.ldr + off : nullptr;  // this block's row of R
+    const T *rv = rvec ? rvec + off : nullptr;
     // 1. stage the right-hand side (element e at dd[e + e/M])
 #pragma unroll
     for (int i0 = 0; i0 < M; i0 += SB) {
@@ -193,15 +195,14 @@ __global__ void __launch_bounds__(MAXT) k_pint(PintGeom g, PintArgs<T> a, size_t
         v[i] = mk<T>(T(0), T(0));
         sub[i] = T(0);
         if (e < blen) {
-          const int64_t j = off + e;
-          if (a.R) {
-            v[i] = a.R[(int64_t)k * a.ldr + j];
+          if (Rk) {
+            v[i] = Rk[e];
             if (xs)
               sub[i] = xs[e];
-            else if (rvec)
-              sub[i] = rvec[j];
+            else if (rv)
+              sub[i] = rv[e];
           } else {
-            v[i].x = rvec[j];
+            v[i].x = rv[e];
           }
         }
       }
@@ -318,10 +319,11 @@ __global__ void __launch_bounds__(MAXT) k_pint(PintGeom g, PintArgs<T> a, size_t
 
     // 5. store
     if (a.Y) {
+      cpx<T> *Yk = a.Y + (int64_t)k * a.ldy + off;
 #pragma unroll
       for (int i = 0; i < M; ++i) {
         const int e = t + i * P;
-        if (e < blen) a.Y[(int64_t)k * a.ldy + off + e] = dd[e + e / M];
+        if (e < blen) Yk[e] = dd[e + e / M];
       }
     }
     // 6. dots with the Krylov basis
@@ -382,84 +384,112 @@ __global__ void __launch_bounds__(MAXT) k_pint(PintGeom g, PintArgs<T> a, size_t
   }
 }
 
-// out[j] = sum_r part[(blk*R + r)*blen + e], j = blk*blen + e.  A CTA of 32 x 32
-// threads owns 32 consecutive outputs; its 32 row groups each sum every 32nd
-// partial row (four independent accumulators), then one fixed-order pass over
-// the groups finishes the sum, so the result does not depend on scheduling.
-__global__ void __launch_bounds__(1024) k_acc_reduce(int nblk, int blen, int R, const double *__restrict__ part,
-                                                     double *__restrict__ out, const int *skip_flag) {
+// Column sums out[j] = sum_r X[r][j] in a fixed order.  A CTA owns kColW adjacent
+// columns (one 64-byte row segment) and kRowG row groups; group y sums rows
+// y, y + kRowG, ... with kColB loads in flight, then the groups' partials are added
+// in a fixed two-level order, so the result does not depend on scheduling.
+constexpr int kColW = 8, kRowG = 64, kColB = 8;
+
+__device__ __forceinline__ double colsum_finish(double v, double (*sm)[kColW + 1]) {
+  sm[threadIdx.y][threadIdx.x] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.y < 8) {
+#pragma unroll
+    for (int i = 0; i < kRowG / 8; ++i) t += sm[threadIdx.y * (kRowG / 8) + i][threadIdx.x];
+  }
+  __syncthreads();
+  if (threadIdx.y < 8) sm[threadIdx.y][threadIdx.x] = t;
+  __syncthreads();
+  t = 0.0;
+  if (threadIdx.y == 0) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) t += sm[i][threadIdx.x];
+  }
+  return t;  // valid for threadIdx.y == 0
+}
+
+// out[j] = sum_r part[(blk*R + r)*blen + e], j = blk*blen + e (the per-team partial
+// rows of b or z).
+__global__ void __launch_bounds__(kColW * kRowG) k_acc_reduce(int nblk, int blen, int R,
+                                                              const double *__restrict__ part,
+                                                              double *__restrict__ out, const int *skip_flag) {
   if (skip_flag && *skip_flag) return;
-  __shared__ double sm[32][33];
+  __shared__ double sm[kRowG][kColW + 1];
   const int64_t n = (int64_t)nblk * blen;
-  const int64_t j = (int64_t)blockIdx.x * 32 + threadIdx.x;
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  const int64_t j = (int64_t)blockIdx.x * kColW + threadIdx.x;
+  double acc[kColB];
+#pragma unroll
+  for (int u = 0; u < kColB; ++u) acc[u] = 0.0;
   if (j < n) {
     const int blk = (int)(j / blen);
     const int e = (int)(j - (int64_t)blk * blen);
     const double *base = part + (int64_t)blk * R * blen + e;  // R = partial rows per block
-    int r = threadIdx.y;
-    for (; r + 96 < R; r += 128) {
-      s0 += base[(int64_t)r * blen];
-      s1 += base[(int64_t)(r + 32) * blen];
-      s2 += base[(int64_t)(r + 64) * blen];
-      s3 += base[(int64_t)(r + 96) * blen];
-    }
-    for (; r < R; r += 32) s0 += base[(int64_t)r * blen];
-  }
-  sm[threadIdx.y][threadIdx.x] = (s0 + s1) + (s2 + s3);
-  __syncthreads();
-  if (threadIdx.y == 0 && j < n) {
-    double t = 0.0;
-    for (int i = 0; i < 32; ++i) t += sm[i][threadIdx.x];
-    out[j] = t;
-  }
-}
-
-// z[j] = sum_k Re(omega_k H[k][j]) over the stored h_k (eq. 13's z), j < n; the same
-// fixed-order tiled reduction as k_acc_reduce (32 outputs x 32 row groups per CTA).
-template <typename T>
-__global__ void __launch_bounds__(1024) k_zsum(int nf, int64_t n, const cpx<T> *__restrict__ H, int64_t ldh,
-                                               const double2 *__restrict__ omega, double *__restrict__ z,
-                                               const int *skip_flag) {
-  if (skip_flag && *skip_flag) return;
-  __shared__ double sm[32][33];
-  const int64_t j = (int64_t)blockIdx.x * 32 + threadIdx.x;
-  constexpr int B = 8;  // rows of H in flight per thread
-  T acc[B];
+    for (int r0 = threadIdx.y; r0 < R; r0 += kRowG * kColB) {
+      double v[kColB];
 #pragma unroll
-  for (int u = 0; u < B; ++u) acc[u] = T(0);
-  if (j < n) {
-    for (int k0 = threadIdx.y; k0 < nf; k0 += 32 * B) {
-      cpx<T> h[B];
-      double2 o[B];
-#pragma unroll
-      for (int u = 0; u < B; ++u) {
-        const int k = k0 + 32 * u;
-        h[u] = k < nf ? H[(int64_t)k * ldh + j] : cpx<T>{T(0), T(0)};
-        o[u] = k < nf ? omega[k] : make_double2(0.0, 0.0);
+      for (int u = 0; u < kColB; ++u) {
+        const int r = r0 + u * kRowG;
+        v[u] = r < R ? base[(int64_t)r * blen] : 0.0;
       }
 #pragma unroll
-      for (int u = 0; u < B; ++u) acc[u] += (T)o[u].x * h[u].x - (T)o[u].y * h[u].y;
+      for (int u = 0; u < kColB; ++u) acc[u] += v[u];
     }
   }
   double tot = 0.0;
 #pragma unroll
-  for (int u = 0; u < B; ++u) tot += (double)acc[u];
-  sm[threadIdx.y][threadIdx.x] = tot;
+  for (int u = 0; u < kColB; ++u) tot += acc[u];
+  tot = colsum_finish(tot, sm);
+  if (threadIdx.y == 0 && j < n) out[j] = tot;
+}
+
+// z[j] = sum_k Re(omega_k H[k][j]) over the stored h_k (eq. 13's z), j < n.  In
+// binary32 the weights are rounded once into shared memory (nf * 8 bytes).
+template <typename T>
+__global__ void __launch_bounds__(kColW * kRowG) k_zsum(int nf, int64_t n, const cpx<T> *__restrict__ H, int64_t ldh,
+                                                        const double2 *__restrict__ omega, double *__restrict__ z,
+                                                        const int *skip_flag) {
+  if (skip_flag && *skip_flag) return;
+  __shared__ double sm[kRowG][kColW + 1];
+  extern __shared__ __align__(16) unsigned char om_raw[];
+  cpx<T> *om = reinterpret_cast<cpx<T> *>(om_raw);
+  const int tid = threadIdx.y * kColW + threadIdx.x;
+  for (int k = tid; k < nf; k += kColW * kRowG) om[k] = mk<T>((T)omega[k].x, (T)omega[k].y);
   __syncthreads();
-  if (threadIdx.y == 0 && j < n) {
-    double t = 0.0;
-    for (int i = 0; i < 32; ++i) t += sm[i][threadIdx.x];
-    z[j] = t;
+  const int64_t j = (int64_t)blockIdx.x * kColW + threadIdx.x;
+  T acc[kColB];
+#pragma unroll
+  for (int u = 0; u < kColB; ++u) acc[u] = T(0);
+  if (j < n) {
+    for (int k0 = threadIdx.y; k0 < nf; k0 += kRowG * kColB) {
+      cpx<T> h[kColB];
+#pragma unroll
+      for (int u = 0; u < kColB; ++u) {
+        const int k = k0 + u * kRowG;
+        h[u] = k < nf ? H[(int64_t)k * ldh + j] : mk<T>(T(0), T(0));
+      }
+#pragma unroll
+      for (int u = 0; u < kColB; ++u) {
+        const int k = k0 + u * kRowG;
+        if (k < nf) acc[u] += om[k].x * h[u].x - om[k].y * h[u].y;
+      }
+    }
   }
+  double tot = 0.0;
+#pragma unroll
+  for (int u = 0; u < kColB; ++u) tot += (double)acc[u];
+  tot = colsum_finish(tot, sm);
+  if (threadIdx.y == 0 && j < n) z[j] = tot;
 }
 
 template <typename T>
 void launch_zsum(Ctx &c, int nf, int64_t n, const cpx<T> *H, int64_t ldh, const double2 *omega, double *z,
                  const int *skip_flag) {
-  const int grid = (int)((n + 31) / 32);
+  const int grid = (int)((n + kColW - 1) / kColW);
+  const size_t smem = (size_t)nf * sizeof(cpx<T>);
   c.launch("zsum", (double)nf * n * sizeof(cpx<T>) + n * 8.0, [&] {
-    k_zsum<T><<<grid, dim3(32, 32), 0, c.stream>>>(nf, n, H, ldh, omega, z, skip_flag);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k_zsum<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_zsum<T><<<grid, dim3(kColW, kRowG), smem, c.stream>>>(nf, n, H, ldh, omega, z, skip_flag);
   });
 }
 template void launch_zsum<double>(Ctx &, int, int64_t, const cpx<double> *, int64_t, const double2 *, double *,
@@ -539,9 +569,9 @@ void launch_pint(Ctx &c, const PintGeom &g, const PintArgs<T> &a) {
 
 void launch_acc_reduce(Ctx &c, const PintGeom &g, const double *acc_part, double *out, const int *skip_flag) {
   const int64_t n = (int64_t)g.nblk * g.blen;
-  const int grid = (int)((n + 31) / 32);
+  const int grid = (int)((n + kColW - 1) / kColW);
   c.launch("acc_reduce", (double)n * g.acc_rows * 8.0 + n * 8.0, [&] {
-    k_acc_reduce<<<grid, dim3(32, 32), 0, c.stream>>>(g.nblk, g.blen, g.acc_rows, acc_part, out, skip_flag);
+    k_acc_reduce<<<grid, dim3(kColW, kRowG), 0, c.stream>>>(g.nblk, g.blen, g.acc_rows, acc_part, out, skip_flag);
   });
 }
 
