@@ -515,7 +515,7 @@ void launch_vec_norm_init(Ctx &c, KrylovBufs &k, const double *b, int use_handle
   double *T = k.T;
   int nT = (k.maxit + 1) * k.maxit;
   void *args[] = {(void *)&b, &n, &part, (void *)&ld, &V, &Vf, &scal, &flags, &use_handle, &h, &T, &nT};
-  coop_launch(c, "krylov_blas1", (double)k.n * 16, (const void *)k_init_v0_coop<false>,
+  coop_launch(c, "krylov_init", (double)k.n * 16, (const void *)k_init_v0_coop<false>,
               (const void *)k_init_v0_coop<true>, k.grid, args);
 }
 
@@ -529,7 +529,7 @@ void launch_arnoldi(Ctx &c, KrylovBufs &k) {
   int *flags = k.flags;
   void *args[] = {&n, (void *)&klo, (void *)&kdiag, (void *)&kup, &V, &Vf, &w, &T, &ldT, &part, (void *)&ld,
                   &scal, &flags};
-  coop_launch(c, "krylov_blas1", (double)k.n * 8.0 * 8, (const void *)k_arnoldi_coop<false>,
+  coop_launch(c, "krylov_arnoldi", (double)k.n * 8.0 * 8, (const void *)k_arnoldi_coop<false>,
               (const void *)k_arnoldi_coop<true>, k.grid, args);
 }
 
@@ -555,17 +555,17 @@ void launch_project_resnorm(Ctx &c, KrylovBufs &k, const double *z, double tau, 
   int *flags = k.flags;
   KrylovCtl kc = kc0;
   void *args[] = {&n, (void *)&V, &zz, &tau, &part, (void *)&ld, &scal, &flags, &kc, &use_handle, &h};
-  coop_launch(c, "krylov_blas1", (double)k.n * 8.0 * 6, (const void *)k_project_coop<false>,
+  coop_launch(c, "krylov_project", (double)k.n * 8.0 * 6, (const void *)k_project_coop<false>,
               (const void *)k_project_coop<true>, k.grid, args);
 }
 
 void launch_xm(Ctx &c, KrylovBufs &k, const double *y, double *x, float *xf) {
-  c.launch("krylov_blas1", (double)k.n * 8.0 * 2,
+  c.launch("krylov_xm", (double)k.n * 8.0 * 2,
            [&] { k_xm<<<k.grid, kBlas, 0, c.stream>>>(k.n, k.flags, k.V, y, x, xf); });
 }
 
 void launch_sumsq(Ctx &c, const double *part, int nparts, double *dst) {
-  c.launch("krylov_blas1", 0.0, [&] { k_sumsq_final<<<1, 32, 0, c.stream>>>(part, nparts, dst); });
+  c.launch("krylov_sumsq", 0.0, [&] { k_sumsq_final<<<1, 32, 0, c.stream>>>(part, nparts, dst); });
 }
 
 template <typename Tout>

@@ -551,8 +551,8 @@ static void launch_pint_m(Ctx &c, const PintGeom &g, const PintArgs<T> &a) {
   if (a.R) bytes += per * sizeof(cpx<T>);
   if (a.Y) bytes += per * sizeof(cpx<T>);
   const bool dots = a.mcount ? a.want_dots != 0 : a.mdots > 0;
-  const char *fam = sizeof(T) == 8 ? (a.Y ? "pint_store_f64" : (dots ? "pint_dots_f64" : "pint_acc_f64"))
-                                   : (a.Y ? "pint_store_f32" : (dots ? "pint_dots_f32" : "pint_acc_f32"));
+  const char *fam = sizeof(T) == 8 ? (dots ? "pint_dots_f64" : (a.Y ? "pint_store_f64" : "pint_acc_f64"))
+                                   : (dots ? "pint_dots_f32" : (a.Y ? "pint_store_f32" : "pint_acc_f32"));
   c.launch(fam, bytes, [&] { kern<<<grid, threads, smem, c.stream>>>(g, a, tb); });
 }
 
