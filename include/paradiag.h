@@ -76,7 +76,9 @@ typedef struct pd_desc {
   int32_t precision;     /* pd_precision */
   int32_t maxit;         /* Algorithm 2 iteration limit, 1 <= maxit <= 32 (0 = 32) */
   double eps_krylov;     /* Algorithm 2 tolerance epsilon (stop when ||r|| <= eps * ||b||);
-                            0 = 1e-13 for PD_FP64, 1e-5 for the first solve of PD_MIXED
+                            0 = 1e-13 for PD_FP64 (1e-4 for PD_FP64 batches, which then
+                            refine and leave a stalled step at any level), 1e-5 for the
+                            first solve of PD_MIXED
                             (its refinement sweeps use max(eps_krylov, 1e-3)).
                             Both also stop when ||r|| stalls near the precision floor (no
                             halving over 1 iteration in PD_MIXED once ||r|| <= 1e-3 ||b||, and
@@ -84,9 +86,10 @@ typedef struct pd_desc {
                             once ||r|| <= 1e-6 ||b||) */
   int32_t q;             /* residual check period of Algorithm 2; only q = 1 is built */
   int32_t max_refine;    /* refinement sweeps after the first solve (0 = 8).  PD_MIXED always
-                            refines; PD_FP64 refines only when Algorithm 2 stopped short of
-                            eps_krylov (stall or maxit), since the residual of eq. (2) left by
-                            an inexact x_m is exactly -r_m in the first time step */
+                            refines; PD_FP64 refines when Algorithm 2 stopped short of
+                            eps_krylov (stall or maxit) or when eps_krylov > 1e-10, since the
+                            residual of eq. (2) left by an inexact x_m is exactly -r_m in the
+                            first time step */
   double refine_tol;     /* refinement stops when the predicted remaining relative error,
                             (||delta_s|| / ||delta_{s-1}||) * ||delta_s|| / ||U||, is <= refine_tol
                             (0 = 1e-14 for PD_FP64, 1e-11 for PD_MIXED) */
@@ -106,6 +109,18 @@ typedef struct pd_desc {
                                 > 1 = cooperative launch of 64-thread CTAs (<= SM count) */
   int32_t tune_cap_ctas;     /* CTAs of the capacitance-term kernel, 1 .. 1024 */
   int32_t tune_fft_cols;     /* columns per CTA of the time FFTs: 2, 4, 8 or 16 */
+  /* Batching (1D only): `batch` independent problems with the same nt are solved
+   * together as one block-diagonal problem (their DFTs, shifted solves, Krylov space
+   * and refinement are shared; the blocks never couple).  Problem b occupies slot b:
+   * columns [b*nx, b*nx + nx_b) of G and U, rows [b*nx, b*nx + nx_b) of k_lo/k_diag/
+   * k_up (so those arrays have length batch*nx); columns nx_b..nx-1 of a slot must be
+   * zero in G and are returned as zero.  Each problem is scaled to unit Frobenius norm
+   * on the device before the solve and scaled back after it, so the stopping rules
+   * hold for every problem, not just for the stack.  0 or 1 = a single problem. */
+  int32_t batch;
+  const int64_t *batch_nx;   /* host, length batch: rows of problem b, 1 <= nx_b <= nx
+                                (NULL = nx for all) */
+  const double *batch_tau;   /* host, length batch: time step of problem b (NULL = tau) */
 } pd_desc;
 
 /* Statistics of the last paradiag_solve / paradiag_solve_host. */

@@ -1,0 +1,92 @@
+// Per-problem scaling for batched plans: `batch` independent 1D problems share one
+// plan as a block-diagonal problem (slot b = columns [b*nxm, (b+1)*nxm) of every
+// time row).  The Krylov and refinement stopping rules measure the whole stack, so
+// every problem is first scaled to unit Frobenius norm (up to a factor of two) and
+// scaled back after the solve.  The scale factors are powers of two: the scaling is
+// exact and costs integer work on the exponent field, not FP64 multiplies.
+#include <algorithm>
+
+#include "pd_internal.h"
+
+namespace pd {
+
+// part[b * nc + c] = sum over time rows t = c, c + nc, ... of slot b's squares.
+__global__ void __launch_bounds__(256) k_batch_sumsq(const double *__restrict__ X, int64_t nt, int64_t ld, int nxm,
+                                                     int nc, double *__restrict__ part) {
+  const int c = blockIdx.x, b = blockIdx.y;
+  double s = 0.0;
+  for (int64_t t = c; t < nt; t += nc) {
+    const double *row = X + t * ld + (int64_t)b * nxm;
+    for (int i = threadIdx.x; i < nxm; i += blockDim.x) s = fma(row[i], row[i], s);
+  }
+  __shared__ double red[8];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+    part[(int64_t)b * nc + c] = t;
+  }
+}
+
+// ex[b] = -round(log2 ||slot b||_F): slot b is multiplied by 2^ex[b] before the solve
+// and its solution by 2^-ex[b] after it (0 for an all-zero or non-finite slot).
+__global__ void k_batch_exponents(int batch, int nc, const double *__restrict__ part, int *__restrict__ ex) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= batch) return;
+  double s = 0.0;
+  for (int c = 0; c < nc; ++c) s += part[(int64_t)b * nc + c];
+  int e = 0;
+  if (s > 0.0 && isfinite(s)) {
+    int e2;
+    frexp(s, &e2);  // s = f 2^e2, f in [0.5, 1): ||x|| ~ 2^(e2/2)
+    e = -(e2 / 2);
+  }
+  ex[b] = e;
+}
+
+// x * 2^k exactly: an exponent-field add for normal x whose result stays normal
+// (zero stays zero); other cases (subnormal, overflow, Inf/NaN) take ldexp.
+__device__ __forceinline__ double pow2_scale(double x, int k) {
+  const long long bits = __double_as_longlong(x);
+  if ((bits & 0x7fffffffffffffffLL) == 0) return x;
+  const int e = (int)((bits >> 52) & 0x7ff);
+  if (e > 0 && e < 0x7ff && e + k > 0 && e + k < 0x7ff) return __longlong_as_double(bits + ((long long)k << 52));
+  return ldexp(x, k);
+}
+
+// Y = X * 2^(sign * ex[slot]) over the (nt, ld) array, one time row per blockIdx.y;
+// Y may alias X.  With nxb != NULL, columns past problem b's n_x are set to zero
+// (they are decoupled from the problem, but the paired real-to-complex DFT leaves
+// rounding-level values there).
+__global__ void __launch_bounds__(256) k_batch_scale(const double *X, double *Y, int ld, int nxm,
+                                                     const int *__restrict__ ex, int sign,
+                                                     const int *__restrict__ nxb) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= ld) return;
+  const int b = j / nxm;
+  const int64_t i = (int64_t)blockIdx.y * ld + j;
+  Y[i] = (nxb && j - b * nxm >= nxb[b]) ? 0.0 : pow2_scale(X[i], sign * ex[b]);
+}
+
+void launch_batch_normalize(Ctx &c, const double *G, double *Gs, int64_t nt, int batch, int nxm, int nc,
+                            double *part, int *ex) {
+  const int64_t ld = (int64_t)batch * nxm;
+  c.launch("batch_scale", (double)nt * ld * 8.0, [&] {
+    k_batch_sumsq<<<dim3(nc, batch), 256, 0, c.stream>>>(G, nt, ld, nxm, nc, part);
+  });
+  c.launch("batch_scale", 0.0, [&] { k_batch_exponents<<<(batch + 127) / 128, 128, 0, c.stream>>>(batch, nc, part, ex); });
+  const dim3 grid((unsigned)((ld + 255) / 256), (unsigned)nt);
+  c.launch("batch_scale", (double)nt * ld * 16.0,
+           [&] { k_batch_scale<<<grid, 256, 0, c.stream>>>(G, Gs, (int)ld, nxm, ex, 1, nullptr); });
+}
+
+void launch_batch_unscale(Ctx &c, double *U, int64_t nt, int batch, int nxm, const int *ex, const int *nxb) {
+  const int64_t ld = (int64_t)batch * nxm;
+  const dim3 grid((unsigned)((ld + 255) / 256), (unsigned)nt);
+  c.launch("batch_scale", (double)nt * ld * 16.0,
+           [&] { k_batch_scale<<<grid, 256, 0, c.stream>>>(U, U, (int)ld, nxm, ex, -1, nxb); });
+}
+
+}  // namespace pd

@@ -54,10 +54,10 @@ __device__ __forceinline__ void refine_decide(double *scal, int *flags, const Re
     conv = stop = true;
   } else {
     const double eps = s == 0 ? r.eps_first : r.eps_refine;
-    // FP64: Algorithm 2 met its tolerance, so this sweep's correction is exact to
-    // working accuracy (s = 0: the paper's Algorithm 1 itself); a refinement sweep
-    // leaves about eps * ||delta_s||.
-    if (r.fp64 && flags[F_KCONV] && (s == 0 || eps * rel <= r.refine_tol)) conv = stop = true;
+    // FP64: Algorithm 2 met its tolerance.  With a tight tolerance the first solve is
+    // exact to working accuracy (the paper's Algorithm 1 itself); otherwise each sweep
+    // leaves about eps * ||delta_s|| (relative) behind.
+    if (r.fp64 && flags[F_KCONV] && (s == 0 ? eps <= 1e-10 : eps * rel <= r.refine_tol)) conv = stop = true;
     // Refinement contracts the error by rho ~ ||delta_s|| / ||delta_{s-1}|| (s >= 2:
     // delta_1 / delta_0 is the first solve's error, not a contraction), so about
     // rho * ||delta_s|| remains after sweep s.

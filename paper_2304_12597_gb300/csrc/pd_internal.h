@@ -185,6 +185,13 @@ template <typename T>
 void launch_zsum(Ctx &c, int nf, int64_t n, const cpx<T> *H, int64_t ldh, const double2 *omega, double *z,
                  const int *skip_flag);
 // out[j] = sum_r acc_part[(blk*R + r)*blen + e], j = blk*blen + e
+// Batched plans (batch.cu): Gs = G with slot b scaled by 2^ex[b] ~ 1/||slot b||_F
+// (part: batch * nc doubles of scratch), and the inverse scaling of U in place with
+// the columns past problem b's nxb[b] rows set to zero.
+void launch_batch_normalize(Ctx &c, const double *G, double *Gs, int64_t nt, int batch, int nxm, int nc,
+                            double *part, int *ex);
+void launch_batch_unscale(Ctx &c, double *U, int64_t nt, int batch, int nxm, const int *ex, const int *nxb);
+
 void launch_acc_reduce(Ctx &c, const PintGeom &g, const double *acc_part, double *out,
                        const int *skip_flag);
 

@@ -159,6 +159,14 @@ struct pd_plan {
   size_t ws_bytes = 0;
 
   int nblk = 1, blen = 0;
+  // batched plans: `batch` problems of up to nxm rows (slot b = columns [b nxm, (b+1) nxm))
+  int batch = 1;
+  int64_t nxm = 0;
+  int bnc = 0;                  // time-row groups of the per-problem norm pass
+  double *Gs = nullptr;         // G with every problem scaled to unit norm
+  double *bpart = nullptr;      // norm partials (batch * bnc)
+  int *bex = nullptr;           // per-problem power-of-two scale exponents
+  int *bnx = nullptr;           // rows of each problem
   pd::PintGeom geom{};
   int blas_grid = 1, k5_grid = 1;
   int64_t lds = 0;
@@ -263,7 +271,18 @@ pd_status validate(const pd_desc *d) {
   if (d->tune_fft_cols != 0 && d->tune_fft_cols != 2 && d->tune_fft_cols != 4 && d->tune_fft_cols != 8 &&
       d->tune_fft_cols != 16)
     return fail(PD_ERR_INVALID_ARG, "tune_fft_cols must be 0, 2, 4, 8 or 16");
-  const int64_t nbar = d->nx * (d->dim == 2 ? d->ny : 1);
+  if (d->batch < 0) return fail(PD_ERR_INVALID_ARG, "batch must be >= 0");
+  if (d->batch > 1) {
+    if (d->dim != 1) return fail(PD_ERR_UNSUPPORTED, "batching is built for 1D problems only");
+    if (d->batch > 65535) return fail(PD_ERR_UNSUPPORTED, "at most 65535 problems per batch");
+    for (int b = 0; b < d->batch; ++b) {
+      if (d->batch_nx && (d->batch_nx[b] < 1 || d->batch_nx[b] > d->nx))
+        return fail(PD_ERR_INVALID_ARG, "batch_nx[%d] = %lld is outside [1, nx]", b, (long long)d->batch_nx[b]);
+      if (d->batch_tau && !(d->batch_tau[b] > 0.0 && std::isfinite(d->batch_tau[b])))
+        return fail(PD_ERR_INVALID_ARG, "batch_tau[%d] must be finite and > 0", b);
+    }
+  }
+  const int64_t nbar = d->nx * (d->dim == 2 ? d->ny : 1) * (d->batch > 1 ? d->batch : 1);
   if (nbar > (int64_t)1 << 28 || d->nt * nbar > (int64_t)1 << 34)
     return fail(PD_ERR_UNSUPPORTED, "problem too large for this build");
   return PD_OK;
@@ -271,21 +290,29 @@ pd_status validate(const pd_desc *d) {
 
 void fill_geometry(pd_plan *p, const pd_desc *d) {
   p->dim = d->dim;
-  p->nx = d->nx;
+  p->batch = d->batch > 1 ? d->batch : 1;
+  p->nxm = d->nx;
+  p->nx = d->nx * p->batch;  // 1D: the stacked spatial length
   p->ny = d->dim == 2 ? d->ny : 1;
   p->nbar = p->nx * p->ny;
   p->nt = d->nt;
   p->nf = (int)(d->nt / 2 + 1);
   if (d->nt == 1) p->nf = 1;
-  p->tau = d->tau;
+  // a batch folds each problem's time step into its block of K (tau = 1 below)
+  p->tau = p->batch > 1 ? 1.0 : d->tau;
   p->precision = d->precision;
   p->maxit = d->maxit ? d->maxit : 32;
   p->eps = d->eps_krylov > 0 ? d->eps_krylov : (d->precision == PD_FP64 ? 1e-13 : 1e-5);
+  // FP64 batches: one Krylov space serves every problem and must resolve the union of
+  // their spectral content, so a loose tolerance per solve plus FP64 refinement
+  // sweeps costs far fewer iterations than one tight solve
+  if (d->batch > 1 && d->precision == PD_FP64 && !(d->eps_krylov > 0)) p->eps = 1e-4;
   p->max_refine = d->max_refine ? d->max_refine : 8;
   p->refine_tol = d->refine_tol > 0 ? d->refine_tol : (d->precision == PD_FP64 ? 1e-14 : 1e-11);
   p->host_io = d->host_io;
-  p->nblk = (int)p->ny;
-  p->blen = (int)p->nx;
+  p->nblk = p->batch > 1 ? p->batch : (int)p->ny;
+  p->blen = (int)p->nxm;
+  p->bnc = (int)std::min<int64_t>(p->nt, 64);
   p->lds = (p->nbar + 31) / 32 * 32;
   const int sms = pd::sm_count();
   const int esz = d->precision == PD_FP64 ? 16 : 8;
@@ -378,6 +405,12 @@ size_t layout(pd_plan *p, unsigned char *base) {
   if (mixed && p->dim == 2) p->tmp_f = A.take<float>((size_t)nt * nbar);
   if (!mixed) p->res_d = A.take<double>((size_t)nt * nbar);
   if (!mixed && p->dim == 2) p->tmp_d = A.take<double>((size_t)nt * nbar);
+  if (p->batch > 1) {
+    p->Gs = A.take<double>((size_t)nt * nbar);
+    p->bpart = A.take<double>((size_t)p->batch * p->bnc);
+    p->bex = A.take<int>(p->batch);
+    p->bnx = A.take<int>(p->batch);
+  }
   if (p->host_io) {
     p->G_stage = A.take<double>((size_t)nt * nbar);
     p->U_stage = A.take<double>((size_t)nt * nbar);
@@ -385,7 +418,32 @@ size_t layout(pd_plan *p, unsigned char *base) {
   return (A.off + 255) & ~(size_t)255;
 }
 
+// Batched plans: K~ = diag(tau_b K_b), each block padded to nx rows with decoupled
+// identity rows (their unknowns are zero); blocks never couple.
+HostOp build_batched_operator(const pd_desc *d) {
+  HostOp h;
+  const int64_t nx = d->nx, B = d->batch, n = nx * B;
+  h.xlo.assign(n, 0.0);
+  h.xdiag.assign(n, 1.0);
+  h.xup.assign(n, 0.0);
+  for (int64_t b = 0; b < B; ++b) {
+    const int64_t nb = d->batch_nx ? d->batch_nx[b] : nx;
+    const double tb = d->batch_tau ? d->batch_tau[b] : d->tau;
+    for (int64_t i = 0; i < nb; ++i) {
+      const int64_t j = b * nx + i;
+      h.xlo[j] = i > 0 ? tb * d->k_lo[j] : 0.0;
+      h.xdiag[j] = tb * d->k_diag[j];
+      h.xup[j] = i + 1 < nb ? tb * d->k_up[j] : 0.0;
+    }
+  }
+  h.lo = h.xlo;
+  h.diag = h.xdiag;
+  h.up = h.xup;
+  return h;
+}
+
 HostOp build_operator(const pd_desc *d) {
+  if (d->batch > 1) return build_batched_operator(d);
   HostOp h;
   const int64_t nx = d->nx, ny = d->dim == 2 ? d->ny : 1;
   h.xlo.assign(d->k_lo, d->k_lo + nx);
@@ -523,6 +581,10 @@ pd::KrylovCtl krylov_ctl(pd_plan *p, int kind) {
   k.eps = kind == 0 ? p->eps : std::max(p->eps, fp64 ? 1e-8 : 1e-3);
   k.stall_floor = fp64 ? 1e-6 : (kind == 0 ? 1e-3 : 1.0);
   k.win = fp64 ? 3 : 1;
+  if (fp64 && p->batch > 1) {  // refined FP64 batches: leave a stalled step at any level
+    k.stall_floor = 1.0;
+    k.win = 2;
+  }
   k.maxit = p->maxit;
   return k;
 }
@@ -1009,6 +1071,11 @@ pd_status paradiag_plan(const pd_desc *desc, void *workspace, size_t workspace_b
         (st = upload(p->twy_f, tyf.data(), N / 2, s)))
       return cleanup(st);
   }
+  if (p->batch > 1) {
+    std::vector<int> bnx(p->batch);
+    for (int b = 0; b < p->batch; ++b) bnx[b] = (int)(desc->batch_nx ? desc->batch_nx[b] : desc->nx);
+    if ((st = upload(p->bnx, bnx.data(), p->batch, s))) return cleanup(st);
+  }
   if (cudaMemsetAsync(p->flags, 0, pd::kFlagWords * sizeof(int), s) != cudaSuccess)
     return cleanup(fail(PD_ERR_CUDA, "plan upload failed"));
   if (cudaStreamSynchronize(s) != cudaSuccess) return cleanup(fail(PD_ERR_CUDA, "plan upload failed"));
@@ -1043,8 +1110,14 @@ pd_status paradiag_solve(pd_plan *p, const double *G, double *U, pd_stats *stats
   const int64_t l0 = p->ctx.launches;
   CK(cudaEventRecord(p->ev0, p->ctx.stream));
   pd_stats s{};
-  st = p->precision == PD_FP64 ? solve_refined<double>(p, G, U, s) : solve_refined<float>(p, G, U, s);
+  const double *Gin = G;
+  if (p->batch > 1) {  // every problem of the batch scaled to unit norm (exactly, by 2^k)
+    pd::launch_batch_normalize(p->ctx, G, p->Gs, p->nt, p->batch, (int)p->nxm, p->bnc, p->bpart, p->bex);
+    Gin = p->Gs;
+  }
+  st = p->precision == PD_FP64 ? solve_refined<double>(p, Gin, U, s) : solve_refined<float>(p, Gin, U, s);
   if (st == PD_ERR_CUDA) return st;
+  if (p->batch > 1) pd::launch_batch_unscale(p->ctx, U, p->nt, p->batch, (int)p->nxm, p->bex, p->bnx);
   CK(cudaEventRecord(p->ev1, p->ctx.stream));
   CK(cudaEventSynchronize(p->ev1));
   float ms = 0.f;

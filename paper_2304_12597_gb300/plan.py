@@ -33,16 +33,20 @@ class Plan:
 
     def __init__(self, *, dim, nx, nt, tau, k_lo, k_diag, k_up, ny=1, k_lo_y=None, k_diag_y=None,
                  k_up_y=None, precision="mixed", maxit=0, eps_krylov=0.0, max_refine=0, refine_tol=0.0,
-                 host_io=False, no_graph=False, tune=None, device=None, stream=None, workspace="torch"):
+                 host_io=False, no_graph=False, tune=None, batch=1, batch_nx=None, batch_tau=None,
+                 device=None, stream=None, workspace="torch"):
         import torch
 
         self._torch = torch
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.dim, self.nx, self.ny, self.nt = int(dim), int(nx), int(ny if dim == 2 else 1), int(nt)
-        self.nbar = self.nx * self.ny
+        self.batch = max(int(batch), 1)
+        self.nbar = self.nx * self.ny * self.batch
         self.precision = precision
         self._arrays = [_f64(k_lo), _f64(k_diag), _f64(k_up), _f64(k_lo_y), _f64(k_diag_y), _f64(k_up_y)]
+        self._batch_nx = None if batch_nx is None else np.ascontiguousarray(batch_nx, dtype=np.int64)
+        self._batch_tau = _f64(batch_tau)
         d = B.PdDesc()
         d.abi_version = B.PD_ABI_VERSION
         d.dim = self.dim
@@ -63,6 +67,11 @@ class Plan:
         d.no_graph = 1 if no_graph else 0
         for key, val in (tune or {}).items():  # launch geometry: pint_rows, pint_teams, krylov_ctas, ...
             setattr(d, "tune_" + key, int(val))
+        d.batch = self.batch if self.batch > 1 else 0
+        if self._batch_nx is not None:
+            d.batch_nx = self._batch_nx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        if self._batch_tau is not None:
+            d.batch_tau = _ptr(self._batch_tau)
         self.desc = d
         self.workspace_bytes = B.paradiag_workspace_size(d)
         self.handle = None
@@ -75,6 +84,35 @@ class Plan:
             else:
                 self._ws = None
                 self.handle = B.paradiag_plan(d, 0, 0)
+
+    @classmethod
+    def from_problems(cls, problems, **kw):
+        """One batched plan for a list of 1D problems with the same nt (fields of
+        workloads.Problem).  Slot b holds problem b, padded to the largest n_x."""
+        nt = problems[0].nt
+        if any(P.dim != 1 or P.nt != nt for P in problems):
+            raise ValueError("a batch needs 1D problems with one common nt")
+        nx = max(P.nx for P in problems)
+        B = len(problems)
+        lo, di, up = np.zeros((B, nx)), np.ones((B, nx)), np.zeros((B, nx))
+        for b, P in enumerate(problems):
+            lo[b, :P.nx], di[b, :P.nx], up[b, :P.nx] = P.k_lo, P.k_diag, P.k_up
+        args = dict(dim=1, nx=nx, nt=nt, tau=problems[0].tau, k_lo=lo.ravel(), k_diag=di.ravel(), k_up=up.ravel(),
+                    batch=B, batch_nx=[P.nx for P in problems], batch_tau=[P.tau for P in problems])
+        args.update(kw)
+        return cls(**args)
+
+    def stack(self, arrays):
+        """(nt, batch * nx) float64 array with array b (nt, n_x,b) in slot b, zero-padded."""
+        out = np.zeros((self.nt, self.batch, self.nx))
+        for b, a in enumerate(arrays):
+            out[:, b, :a.shape[1]] = a
+        return out.reshape(self.nt, self.batch * self.nx)
+
+    def unstack(self, U, nxs):
+        """Slot b of a (nt, batch * nx) array, cut to n_x,b columns."""
+        V = U.reshape(self.nt, self.batch, self.nx)
+        return [V[:, b, :n] for b, n in enumerate(nxs)]
 
     @classmethod
     def from_problem(cls, problem, **kw):

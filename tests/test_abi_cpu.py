@@ -75,9 +75,22 @@ def _desc(B, **kw):
     d.k_lo, d.k_diag, d.k_up = p(lo), p(di), p(up)
     d.precision = 0
     for k, v in kw.items():
-        if k.startswith("y_"):
+        if k.startswith("y_") or k in ("batch_nx", "batch_tau", "batch_k"):
             continue
         setattr(d, k, v)
+    if kw.get("batch", 0) > 1:  # K arrays hold batch * nx rows
+        B = kw["batch"]
+        lo, di, up = np.tile(lo, B), np.tile(di, B), np.tile(up, B)
+        keep += [lo, di, up]
+        d.k_lo, d.k_diag, d.k_up = p(lo), p(di), p(up)
+        if "batch_nx" in kw:
+            bn = np.asarray(kw["batch_nx"], dtype=np.int64)
+            keep.append(bn)
+            d.batch_nx = bn.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        if "batch_tau" in kw:
+            bt = np.asarray(kw["batch_tau"], dtype=np.float64)
+            keep.append(bt)
+            d.batch_tau = p(bt)
     if kw.get("dim") == 2:
         ny = kw.get("ny", 7)
         ylo = kw.get("y_lo", np.full(ny, -1.0))
@@ -98,6 +111,7 @@ def test_valid_descriptors_have_a_workspace(B):
     for kw in ({}, {"precision": 1}, {"nt": 1}, {"n": 1}, {"n": 4096, "nt": 2048, "precision": 1},
                {"precision": 1, "tune_pint_rows": 16, "tune_pint_teams": 2, "tune_krylov_ctas": 8,
                 "tune_cap_ctas": 3, "tune_fft_cols": 2},
+               {"batch": 3, "batch_nx": [31, 5, 1], "batch_tau": [0.1, 0.2, 1e-3]}, {"batch": 4},
                {"dim": 2, "ny": 7}, {"dim": 2, "ny": 255, "n": 255, "nt": 256, "precision": 1}):
         st, n = _size_status(B, _desc(B, **kw))
         assert st == 0, (kw, B.last_error())
@@ -127,6 +141,12 @@ def test_valid_descriptors_have_a_workspace(B):
     ({"tune_krylov_ctas": -1}, 1),
     ({"tune_cap_ctas": 5000}, 1),
     ({"tune_fft_cols": 6}, 1),
+    ({"batch": -1}, 1),
+    ({"batch": 2, "dim": 2, "ny": 7}, 2),
+    ({"batch": 3, "batch_nx": [31, 32, 1]}, 1),
+    ({"batch": 3, "batch_nx": [31, 0, 1]}, 1),
+    ({"batch": 2, "batch_tau": [0.1, 0.0]}, 1),
+    ({"batch": 2, "batch_tau": [0.1, float("inf")]}, 1),
 ])
 def test_bad_descriptors_are_rejected(B, kw, code):
     st, _ = _size_status(B, _desc(B, **kw))

@@ -1,0 +1,102 @@
+"""Batched plans (GPU, through the C ABI): many 1D problems with one n_t solved as one
+block-diagonal problem must give, for every problem, the oracle's solution of that
+problem alone, within the same tolerances as single solves (1e-12 FP64, 1e-10 mixed),
+whatever the mix of sizes, time steps and magnitudes in the batch.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import reference as R
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "mixed": 1e-10}
+
+
+@pytest.fixture(scope="module")
+def pd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as entry
+
+    entry.build()
+    import paper_2304_12597_gb300 as pkg
+
+    return pkg
+
+
+def dev():
+    return torch.device("cuda:0")
+
+
+def _scaled(P, s):
+    P.G = P.G * s
+    return P
+
+
+def _mix(nt):
+    """Uneven n_x, different T (so different tau), operators and magnitudes 1e-6..1e4."""
+    return [
+        _scaled(W.heat1d_forced(255, nt, seed=1), 1.0),
+        _scaled(W.heat1d_forced(127, nt, T=0.5, seed=2), 1e-6),
+        _scaled(W.advdiff1d_pulse(300, nt, seed=3), 1e4),
+        W.random_tridiag_problem(33, nt, seed=4),
+        _scaled(W.heat1d_sine_modes(63, nt, seed=5), 3e-3),
+        W.random_tridiag_problem(1, nt, seed=6),
+    ]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_matches_oracle_per_problem(pd, prec):
+    probs = _mix(64)
+    with pd.Plan.from_problems(probs, precision=prec, device=dev()) as plan:
+        G = torch.from_numpy(plan.stack([P.G for P in probs])).to(dev())
+        U, st = plan.solve(G)
+        parts = plan.unstack(U.cpu().numpy(), [P.nx for P in probs])
+    for P, Ub in zip(probs, parts):
+        err = R.rel_err(Ub, R.be_solve_refined(P))
+        assert err <= TOL[prec], (P.name, err, st)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_member_equals_its_single_solve(pd, prec):
+    probs = _mix(128)
+    with pd.Plan.from_problems(probs, precision=prec, device=dev()) as plan:
+        G = torch.from_numpy(plan.stack([P.G for P in probs])).to(dev())
+        U, _ = plan.solve(G)
+        parts = plan.unstack(U.cpu().numpy(), [P.nx for P in probs])
+    for P, Ub in zip(probs, parts):
+        with pd.Plan.from_problem(P, precision=prec, device=dev()) as single:
+            Us, _ = single.solve(torch.from_numpy(P.G).to(dev()))
+        Us = Us.cpu().numpy()
+        assert R.rel_err(Ub, Us) <= 2 * TOL[prec], P.name
+
+
+def test_batch_zero_problem_and_padding_stay_zero(pd):
+    probs = _mix(32)
+    probs[3].G = np.zeros_like(probs[3].G)
+    with pd.Plan.from_problems(probs, precision="mixed", device=dev()) as plan:
+        G = torch.from_numpy(plan.stack([P.G for P in probs])).to(dev())
+        U, _ = plan.solve(G)
+        V = U.cpu().numpy().reshape(plan.nt, plan.batch, plan.nx)
+    assert not np.any(V[:, 3, :])
+    for b, P in enumerate(probs):
+        assert not np.any(V[:, b, P.nx:])  # padding rows
+
+
+def test_batch_of_identical_problems_is_deterministic(pd):
+    P = W.heat1d_forced(1023, 256, seed=7)
+    probs = [P] * 8
+    with pd.Plan.from_problems(probs, precision="mixed", device=dev()) as plan:
+        G = torch.from_numpy(plan.stack([Q.G for Q in probs])).to(dev())
+        U1, _ = plan.solve(G)
+        U1 = U1.cpu().numpy()
+        U2, _ = plan.solve(G)
+        U2 = U2.cpu().numpy()
+    assert np.array_equal(U1, U2)
+    parts = plan.unstack(U1, [P.nx] * 8)
+    ref = R.be_solve_refined(P)
+    for Ub in parts:
+        assert R.rel_err(Ub, ref) <= TOL["mixed"]
