@@ -175,6 +175,15 @@ pd_status paradiag_solve(pd_plan *plan, const double *G_dev, double *U_dev, pd_s
 pd_status paradiag_solve_host(pd_plan *plan, const double *G_host, double *U_host,
                               pd_stats *stats);
 
+/* Replace the operator of an existing plan: desc must describe the plan's shape (dim,
+ * nx, ny, nt, batch, precision); its K arrays, tau, batch_nx and batch_tau are
+ * uploaded in place (host-synchronous; it first waits for the plan's stream), so the
+ * plan's workspace and, unless a single problem's tau changes, its captured CUDA
+ * graph are reused.  Errors: PD_ERR_INVALID_ARG for a different shape, and the
+ * validation errors of paradiag_plan.  Not part of the paper: it lets a solver
+ * service reuse plans across requests of one shape. */
+pd_status paradiag_set_operator(pd_plan *plan, const pd_desc *desc);
+
 /* Release the plan and, if the plan allocated it, its workspace.  NULL is a no-op. */
 pd_status paradiag_destroy(pd_plan *plan);
 

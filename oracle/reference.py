@@ -25,6 +25,8 @@ What each function follows (paper sections/equations):
 * ``periodic_solve_dense``  P^{-1} of Sec. 2 mapped back to time: the circulant
                         all-at-once system (I + tau K) U - U C_1^T = R.
 * ``kappa_bound``       eq. (14), Theorem 3.1.
+* ``alpha_quantities``, ``paradiag_alpha``, ``j_alpha_dense``  Algorithm 3 and
+                        eqs. (15)-(17) (alpha-circulant C_alpha, scaled DFT).
 * ``j_extreme_eigs``    the extreme eigenvalues of J_l for SPD K (Sec. 6.1).
 
 Readings of points where the paper is silent or inconsistent (all listed in
@@ -272,8 +274,12 @@ def idft_time(Xhat):
 
 
 def fom_like(op, tau, b, pi, gamma, eps=1e-8, maxit=50, q=1, breakdown_tol=1e-14,
-             keep_tau=True, keep_gamma_in_residual=True):
+             keep_tau=True, keep_gamma_in_residual=True, weight=1.0):
     """Algorithm 2 for J_l x = b with J_l = I + sum_i gamma_i ((1-pi_i) I + tau K)^{-1}.
+
+    ``weight`` = alpha^{1/l} gives the variant Algorithm 3 applies to
+    I + alpha^{1/l} sum_i gamma_i ((1-pi_i) I + tau K)^{-1} (eq. 17): the weight
+    multiplies the sum in the projected system (12) and in the residual (13).
 
     Krylov space K_m(K, b) (eq. 9), Arnoldi by modified Gram-Schmidt (eq. 10).
     Every q iterations: h_i = ((1-pi_i) I + tau K)^{-1} v_{m+1},
@@ -318,13 +324,13 @@ def fom_like(op, tau, b, pi, gamma, eps=1e-8, maxit=50, q=1, breakdown_tol=1e-14
                 Si = np.linalg.inv((1.0 - pi[i]) * np.eye(m) + tau * Tm)
                 S.append(Si)
                 if breakdown:
-                    Msys += gamma[i] * Si
+                    Msys += weight * gamma[i] * Si
                 else:
                     hi = op.shifted_solve(1.0 - pi[i], tau, V[m])
                     H.append(hi)
                     gi = Vm @ hi  # V_m^T h_i
                     # (I - tau t V_m^T h_i e_m^T) S_i = S_i - tau t g_i (e_m^T S_i)
-                    Msys += gamma[i] * (Si - tfac * t * np.outer(gi, Si[m - 1, :]))
+                    Msys += weight * gamma[i] * (Si - tfac * t * np.outer(gi, Si[m - 1, :]))
             rhs = np.zeros(m, dtype=np.complex128)
             rhs[0] = beta
             y = np.linalg.solve(Msys, rhs)
@@ -335,7 +341,7 @@ def fom_like(op, tau, b, pi, gamma, eps=1e-8, maxit=50, q=1, breakdown_tol=1e-14
                 for i in range(ell):
                     c = S[i][m - 1, :] @ y
                     g = gamma[i] if keep_gamma_in_residual else 1.0
-                    z += g * H[i] * c
+                    z += weight * g * H[i] * c
                 proj = z - Vm.T @ (Vm @ z)
                 r = abs(tfac * t) * float(np.linalg.norm(proj))
             info["resnorms"].append(r)
@@ -374,6 +380,60 @@ def paradiag(problem, G=None, eps=1e-8, maxit=50, q=1, op=None, **kw):
             "b_imag": float(np.linalg.norm(b_c.imag)), "x": x, "krylov": kinfo,
             "U_imag": float(np.linalg.norm(Uc.imag))}
     return Uc.real, info
+
+
+# ----------------------------------------------------------------------------
+# Algorithm 3 (alpha-acceleration, Sec. 4)
+# ----------------------------------------------------------------------------
+
+
+def alpha_quantities(ell, alpha):
+    """Algorithm 3, first step: pi = alpha^{1/l} F C_1 e_1, gamma = F^{-T} e_l and
+    the diagonal of D_alpha = diag(1, alpha^{1/l}, ..., alpha^{(l-1)/l})."""
+    pi1, gamma = circulant_eigs(ell)
+    a = alpha ** (1.0 / ell)
+    d = alpha ** (np.arange(ell) / ell)
+    return a * pi1, gamma, d
+
+
+def paradiag_alpha(problem, alpha, G=None, eps=1e-8, maxit=50, q=1, op=None, early_exit_eps=None, **kw):
+    """Algorithm 3 on the row layout (row j of G = column j of [u0 + tau f_1, ...]).
+    Returns (U, info).  early_exit_eps: the optional residual test on U_1 of the
+    algorithm (None = always run the correction)."""
+    G = problem.G if G is None else np.asarray(G, dtype=np.float64)
+    op = operator(problem) if op is None else op
+    ell = G.shape[0]
+    tau = problem.tau
+    pi, gamma, d = alpha_quantities(ell, alpha)
+    a = alpha ** (1.0 / ell)
+    Ghat = dft_time(d[:, None] * G)  # rows of [u0 + tau f_1, ...] D_alpha F^T
+    L = np.stack([op.shifted_solve(1.0 - pi[i], tau, Ghat[i]) for i in range(ell)])
+    U1 = (idft_time(L) / d[:, None])  # L F^{-T} D_alpha^{-1}
+    info = {"pi": pi, "gamma": gamma, "d": d, "L": L, "exited_early": False}
+    if early_exit_eps is not None:
+        res = np.linalg.norm(aao_apply(problem, U1.real) - G)
+        if res <= early_exit_eps * np.linalg.norm(U1.real):
+            info["exited_early"] = True
+            return U1.real, info
+    b_c = gamma @ L  # L F^{-T} e_l
+    b = b_c.real
+    x, kinfo = fom_like(op, tau, b, pi, gamma, eps=eps, maxit=maxit, q=q, weight=a, **kw)
+    W = np.stack([op.shifted_solve(1.0 - pi[i], tau, x) for i in range(ell)])
+    Uc = U1 - a * idft_time(W) / d[:, None]
+    info.update(b=b, x=x, krylov=kinfo, U_imag=float(np.linalg.norm(Uc.imag)))
+    return Uc.real, info
+
+
+def j_alpha_dense(K, tau, ell, alpha):
+    """I + alpha^{1/l} sum_i gamma_i ((1 - pi_i) I + tau K)^{-1} (eq. 17), densely."""
+    K = np.asarray(K, dtype=np.float64)
+    n = K.shape[0]
+    pi, gamma, _ = alpha_quantities(ell, alpha)
+    a = alpha ** (1.0 / ell)
+    J = np.eye(n, dtype=np.complex128)
+    for i in range(ell):
+        J += a * gamma[i] * np.linalg.inv((1.0 - pi[i]) * np.eye(n) + tau * K)
+    return J
 
 
 # ----------------------------------------------------------------------------

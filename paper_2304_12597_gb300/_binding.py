@@ -119,6 +119,7 @@ SIGNATURES = {
     "paradiag_solve_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.POINTER(PdStats)]),
     "paradiag_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "paradiag_set_operator": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(PdDesc)]),
     "paradiag_last_error": (ctypes.c_char_p, []),
     "paradiag_version": (ctypes.c_char_p, []),
     "paradiag_time_dft": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -195,6 +196,10 @@ def paradiag_solve_host(plan: int, G_host_ptr: int, U_host_ptr: int, allow_not_c
 
 def paradiag_destroy(plan: int) -> None:
     check("paradiag_destroy", load().paradiag_destroy(plan))
+
+
+def paradiag_set_operator(plan: int, desc: PdDesc) -> None:
+    check("paradiag_set_operator", load().paradiag_set_operator(plan, ctypes.byref(desc)))
 
 
 def paradiag_time_dft(plan: int, X_ptr: int, Xhat_ptr: int) -> None:

@@ -488,6 +488,59 @@ pd_status upload(X *dst, const X *src, size_t n, cudaStream_t s) {
   return PD_OK;
 }
 
+// K in the solve basis and every array derived from it (tau K in both precisions,
+// the residual coefficients, the per-problem row counts of a batch), uploaded on the
+// plan's stream.  Shared by paradiag_plan and paradiag_set_operator.
+pd_status upload_operator(pd_plan *p, const pd_desc *desc) {
+  pd_status st = PD_OK;
+  HostOp h = build_operator(desc);
+  const int64_t nbar = p->nbar;
+  std::vector<double> tlo(nbar), tdiag(nbar), tup(nbar);
+  std::vector<float> flo(nbar), fdiag(nbar), fup(nbar);
+  for (int64_t j = 0; j < nbar; ++j) {
+    tlo[j] = p->tau * h.lo[j];
+    tdiag[j] = p->tau * h.diag[j];
+    tup[j] = p->tau * h.up[j];
+    flo[j] = (float)tlo[j];
+    fdiag[j] = (float)tdiag[j];
+    fup[j] = (float)tup[j];
+  }
+  std::vector<double> rxl(p->nx), rxd(p->nx), rxu(p->nx), ryl(p->ny), ryd(p->ny), ryu(p->ny);
+  for (int64_t i = 0; i < p->nx; ++i) {
+    rxl[i] = p->tau * h.xlo[i];
+    rxd[i] = 1.0 + p->tau * h.xdiag[i];
+    rxu[i] = p->tau * h.xup[i];
+  }
+  if (p->dim == 2)
+    for (int64_t i = 0; i < p->ny; ++i) {
+      ryl[i] = p->tau * h.ylo[i];
+      ryd[i] = p->tau * h.ydiag[i];
+      ryu[i] = p->tau * h.yup[i];
+    }
+  cudaStream_t s = p->ctx.stream;
+  if ((st = upload(p->klo, h.lo.data(), nbar, s)) || (st = upload(p->kdiag, h.diag.data(), nbar, s)) ||
+      (st = upload(p->kup, h.up.data(), nbar, s)) || (st = upload(p->tlo_d, tlo.data(), nbar, s)) ||
+      (st = upload(p->tdiag_d, tdiag.data(), nbar, s)) || (st = upload(p->tup_d, tup.data(), nbar, s)) ||
+      (st = upload(p->tlo_f, flo.data(), nbar, s)) || (st = upload(p->tdiag_f, fdiag.data(), nbar, s)) ||
+      (st = upload(p->tup_f, fup.data(), nbar, s)) || (st = upload(p->xlo, h.xlo.data(), p->nx, s)) ||
+      (st = upload(p->xdiag, h.xdiag.data(), p->nx, s)) || (st = upload(p->xup, h.xup.data(), p->nx, s)) ||
+      (st = upload(p->rxl, rxl.data(), p->nx, s)) || (st = upload(p->rxd, rxd.data(), p->nx, s)) ||
+      (st = upload(p->rxu, rxu.data(), p->nx, s)))
+    return st;
+  if (p->dim == 2 && ((st = upload(p->ryl, ryl.data(), p->ny, s)) || (st = upload(p->ryd, ryd.data(), p->ny, s)) ||
+                      (st = upload(p->ryu, ryu.data(), p->ny, s)) || (st = upload(p->ylo, h.ylo.data(), p->ny, s)) ||
+                      (st = upload(p->ydiag, h.ydiag.data(), p->ny, s)) || (st = upload(p->yup, h.yup.data(), p->ny, s))))
+    return st;
+  if (p->batch > 1) {
+    std::vector<int> bnx(p->batch);
+    for (int b = 0; b < p->batch; ++b) bnx[b] = (int)(desc->batch_nx ? desc->batch_nx[b] : desc->nx);
+    if ((st = upload(p->bnx, bnx.data(), p->batch, s))) return st;
+  }
+  // the host vectors die on return: wait for the copies
+  if (cudaStreamSynchronize(s) != cudaSuccess) return fail(PD_ERR_CUDA, "operator upload failed");
+  return PD_OK;
+}
+
 pd_status ctx_status(pd_plan *p) {
   if (p->ctx.err != cudaSuccess)
     return fail(PD_ERR_CUDA, "kernel launch failed in %s: %s", p->ctx.err_where, cudaGetErrorString(p->ctx.err));
@@ -1017,45 +1070,9 @@ pd_status paradiag_plan(const pd_desc *desc, void *workspace, size_t workspace_b
     tw[k] = pd::mk<double>(std::cos(ang), std::sin(ang));
     twf[k] = pd::mk<float>((float)tw[k].x, (float)tw[k].y);
   }
-  HostOp h = build_operator(desc);
-  const int64_t nbar = p->nbar;
-  std::vector<double> tlo(nbar), tdiag(nbar), tup(nbar);
-  std::vector<float> flo(nbar), fdiag(nbar), fup(nbar);
-  for (int64_t j = 0; j < nbar; ++j) {
-    tlo[j] = p->tau * h.lo[j];
-    tdiag[j] = p->tau * h.diag[j];
-    tup[j] = p->tau * h.up[j];
-    flo[j] = (float)tlo[j];
-    fdiag[j] = (float)tdiag[j];
-    fup[j] = (float)tup[j];
-  }
-  std::vector<double> rxl(p->nx), rxd(p->nx), rxu(p->nx), ryl(p->ny), ryd(p->ny), ryu(p->ny);
-  for (int64_t i = 0; i < p->nx; ++i) {
-    rxl[i] = p->tau * h.xlo[i];
-    rxd[i] = 1.0 + p->tau * h.xdiag[i];
-    rxu[i] = p->tau * h.xup[i];
-  }
-  if (p->dim == 2)
-    for (int64_t i = 0; i < p->ny; ++i) {
-      ryl[i] = p->tau * h.ylo[i];
-      ryd[i] = p->tau * h.ydiag[i];
-      ryu[i] = p->tau * h.yup[i];
-    }
   cudaStream_t s = p->ctx.stream;
   if ((st = upload(p->shift, shift.data(), nf, s)) || (st = upload(p->wg, wg.data(), nf, s)) ||
-      (st = upload(p->klo, h.lo.data(), nbar, s)) || (st = upload(p->kdiag, h.diag.data(), nbar, s)) ||
-      (st = upload(p->kup, h.up.data(), nbar, s)) || (st = upload(p->tlo_d, tlo.data(), nbar, s)) ||
-      (st = upload(p->tdiag_d, tdiag.data(), nbar, s)) || (st = upload(p->tup_d, tup.data(), nbar, s)) ||
-      (st = upload(p->tlo_f, flo.data(), nbar, s)) || (st = upload(p->tdiag_f, fdiag.data(), nbar, s)) ||
-      (st = upload(p->tup_f, fup.data(), nbar, s)) || (st = upload(p->xlo, h.xlo.data(), p->nx, s)) ||
-      (st = upload(p->xdiag, h.xdiag.data(), p->nx, s)) || (st = upload(p->xup, h.xup.data(), p->nx, s)) ||
       (st = upload(p->tw_d, tw.data(), ntw, s)) || (st = upload(p->tw_f, twf.data(), ntw, s)))
-    return cleanup(st);
-  if ((st = upload(p->rxl, rxl.data(), p->nx, s)) || (st = upload(p->rxd, rxd.data(), p->nx, s)) ||
-      (st = upload(p->rxu, rxu.data(), p->nx, s)))
-    return cleanup(st);
-  if (p->dim == 2 && ((st = upload(p->ryl, ryl.data(), p->ny, s)) || (st = upload(p->ryd, ryd.data(), p->ny, s)) ||
-                      (st = upload(p->ryu, ryu.data(), p->ny, s))))
     return cleanup(st);
   if (p->dim == 2) {
     const int N = (int)(2 * (p->ny + 1));
@@ -1066,21 +1083,33 @@ pd_status paradiag_plan(const pd_desc *desc, void *workspace, size_t workspace_b
       ty[k] = pd::mk<double>(std::cos(ang), std::sin(ang));
       tyf[k] = pd::mk<float>((float)ty[k].x, (float)ty[k].y);
     }
-    if ((st = upload(p->ylo, h.ylo.data(), p->ny, s)) || (st = upload(p->ydiag, h.ydiag.data(), p->ny, s)) ||
-        (st = upload(p->yup, h.yup.data(), p->ny, s)) || (st = upload(p->twy_d, ty.data(), N / 2, s)) ||
-        (st = upload(p->twy_f, tyf.data(), N / 2, s)))
+    if ((st = upload(p->twy_d, ty.data(), N / 2, s)) || (st = upload(p->twy_f, tyf.data(), N / 2, s)))
       return cleanup(st);
   }
-  if (p->batch > 1) {
-    std::vector<int> bnx(p->batch);
-    for (int b = 0; b < p->batch; ++b) bnx[b] = (int)(desc->batch_nx ? desc->batch_nx[b] : desc->nx);
-    if ((st = upload(p->bnx, bnx.data(), p->batch, s))) return cleanup(st);
-  }
+  if ((st = upload_operator(p, desc)) != PD_OK) return cleanup(st);
   if (cudaMemsetAsync(p->flags, 0, pd::kFlagWords * sizeof(int), s) != cudaSuccess)
     return cleanup(fail(PD_ERR_CUDA, "plan upload failed"));
   if (cudaStreamSynchronize(s) != cudaSuccess) return cleanup(fail(PD_ERR_CUDA, "plan upload failed"));
   *out = p;
   return PD_OK;
+}
+
+pd_status paradiag_set_operator(pd_plan *p, const pd_desc *desc) {
+  pd_status st = check_plan(p);
+  if (st != PD_OK) return st;
+  if ((st = validate(desc)) != PD_OK) return st;
+  const int batch = desc->batch > 1 ? desc->batch : 1;
+  const int64_t ny = desc->dim == 2 ? desc->ny : 1;
+  if (desc->dim != p->dim || desc->nx != p->nxm || ny != p->ny || desc->nt != p->nt || batch != p->batch ||
+      desc->precision != p->precision)
+    return fail(PD_ERR_INVALID_ARG, "paradiag_set_operator: desc has a different shape or precision than the plan");
+  if (batch == 1 && desc->tau != p->tau) {  // tau reaches some kernels by value: re-capture
+    if (p->ctx.stream) cudaStreamSynchronize(p->ctx.stream);
+    drop_graph(p);
+    p->tau = desc->tau;
+  }
+  if (p->ctx.stream) cudaStreamSynchronize(p->ctx.stream);  // no solve may still read the old operator
+  return upload_operator(p, desc);
 }
 
 pd_status paradiag_destroy(pd_plan *p) {

@@ -88,11 +88,12 @@ class Plan:
     @classmethod
     def from_problems(cls, problems, **kw):
         """One batched plan for a list of 1D problems with the same nt (fields of
-        workloads.Problem).  Slot b holds problem b, padded to the largest n_x."""
+        workloads.Problem).  Slot b holds problem b, padded to the largest n_x (or to
+        the keyword nx, if larger)."""
         nt = problems[0].nt
         if any(P.dim != 1 or P.nt != nt for P in problems):
             raise ValueError("a batch needs 1D problems with one common nt")
-        nx = max(P.nx for P in problems)
+        nx = max(max(P.nx for P in problems), int(kw.pop("nx", 0) or 0))  # slot length
         B = len(problems)
         lo, di, up = np.zeros((B, nx)), np.ones((B, nx)), np.zeros((B, nx))
         for b, P in enumerate(problems):
@@ -122,6 +123,34 @@ class Plan:
                     k_lo_y=problem.k_lo_y, k_diag_y=problem.k_diag_y, k_up_y=problem.k_up_y)
         args.update(kw)
         return cls(**args)
+
+    def set_operator(self, *, tau, k_lo, k_diag, k_up, k_lo_y=None, k_diag_y=None, k_up_y=None, batch_nx=None,
+                     batch_tau=None):
+        """Swap in a new operator of the same shape (paradiag_set_operator)."""
+        arrays = [_f64(k_lo), _f64(k_diag), _f64(k_up), _f64(k_lo_y), _f64(k_diag_y), _f64(k_up_y)]
+        bnx = None if batch_nx is None else np.ascontiguousarray(batch_nx, dtype=np.int64)
+        btau = _f64(batch_tau)
+        d = B.PdDesc()
+        ctypes.pointer(d)[0] = self.desc  # copy of the plan's descriptor
+        d.tau = float(tau)
+        d.k_lo, d.k_diag, d.k_up, d.k_lo_y, d.k_diag_y, d.k_up_y = [_ptr(a) for a in arrays]
+        d.batch_nx = bnx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)) if bnx is not None else None
+        d.batch_tau = _ptr(btau) if btau is not None else None
+        B.paradiag_set_operator(self.handle, d)
+        self._arrays, self._batch_nx, self._batch_tau = arrays, bnx, btau
+        self.desc = d
+
+    def set_problems(self, problems):
+        """Swap in the operators of a list of 1D problems (same batch size, n_t and
+        n_x <= the plan's slot length); see from_problems."""
+        if len(problems) != self.batch or any(P.dim != 1 or P.nt != self.nt or P.nx > self.nx for P in problems):
+            raise ValueError("problems do not fit this plan's slots")
+        nx = self.nx
+        lo, di, up = np.zeros((self.batch, nx)), np.ones((self.batch, nx)), np.zeros((self.batch, nx))
+        for b, P in enumerate(problems):
+            lo[b, :P.nx], di[b, :P.nx], up[b, :P.nx] = P.k_lo, P.k_diag, P.k_up
+        self.set_operator(tau=problems[0].tau, k_lo=lo.ravel(), k_diag=di.ravel(), k_up=up.ravel(),
+                          batch_nx=[P.nx for P in problems], batch_tau=[P.tau for P in problems])
 
     # -- helpers -------------------------------------------------------------------
     def _check(self, t, dtype, shape):

@@ -1,0 +1,316 @@
+"""A continuous-batching solver service on top of the C ABI.
+
+Requests (workloads.serving.Request: kind, n_x, n_y, n_t, nu, forcing seed) arrive
+over time.  The scheduler groups the waiting ones into batches, and worker threads
+(one CUDA stream each) run them, so several batches are on the device at once:
+- 1D requests with one n_t and n_x in one size class share a batched plan (problem b in
+  slot b, zero-padded to the class's n_x);
+- 2D requests run one per plan.
+Requests that arrive while batches are running join the next batch as soon as a
+worker and enough device memory are free.  Admission is by an HBM budget that counts
+the workspace, G and U of every batch in flight plus the cached plans.
+
+Plans are cached per (shape, capacity) and worker; a new batch swaps its operators in
+with paradiag_set_operator, so the workspace and the captured CUDA graph are reused.
+All arithmetic of a solve runs in the library's kernels; this module only schedules.
+"""
+from __future__ import annotations
+
+import threading
+import time
+from collections import OrderedDict
+from dataclasses import dataclass, field
+from typing import Callable, Optional
+
+import numpy as np
+
+NX_CLASSES = (128, 256, 512, 1024, 2048, 4096)
+
+
+def size_class(nx: int) -> int:
+    for c in NX_CLASSES:
+        if nx <= c:
+            return c
+    raise ValueError(f"n_x = {nx} is above the largest size class")
+
+
+def next_pow2(v: int) -> int:
+    p = 1
+    while p < v:
+        p <<= 1
+    return p
+
+
+@dataclass(frozen=True)
+class BatchKey:
+    dim: int
+    nt: int
+    nx: int  # slot length (1D: size class; 2D: grid side)
+    ny: int
+
+
+def key_of(req) -> BatchKey:
+    if req.dim == 2:
+        return BatchKey(2, req.nt, req.nx, req.ny)
+    return BatchKey(1, req.nt, size_class(req.nx), 1)
+
+
+def capacity_for(count: int, max_batch: int) -> int:
+    """Slots of the plan that serves `count` 1D requests (a power of two >= 2, so that
+    one plan shape serves a range of batch sizes)."""
+    return max(2, min(next_pow2(count), max_batch))
+
+
+def batch_bytes(key: BatchKey, cap: int, workspace_bytes: Callable[[BatchKey, int], int]) -> int:
+    """Device bytes of one batch in flight: workspace plus G and U."""
+    return workspace_bytes(key, cap) + 2 * 8 * key.nt * key.nx * key.ny * cap
+
+
+@dataclass
+class Batch:
+    key: BatchKey
+    cap: int
+    requests: list
+    bytes: int
+
+
+class Scheduler:
+    """Waiting requests and the admission rule (host logic only; no GPU).
+
+    next_batch() takes the oldest waiting request, collects up to `max_batch` waiting
+    requests of its key in arrival order (2D: one), and admits the batch if the bytes
+    in flight stay within `budget`; otherwise nothing is admitted (the oldest request
+    keeps its place at the head of the queue).
+    """
+
+    def __init__(self, budget: int, workspace_bytes: Callable[[BatchKey, int], int], max_batch: int = 32):
+        self.budget = budget
+        self.workspace_bytes = workspace_bytes
+        self.max_batch = max_batch
+        self.waiting: list = []
+        self.in_flight = 0
+
+    def add(self, req) -> None:
+        self.waiting.append(req)
+
+    def next_batch(self) -> Optional[Batch]:
+        if not self.waiting:
+            return None
+        head = self.waiting[0]
+        key = key_of(head)
+        if key.dim == 2:
+            group = [head]
+            cap = 1
+        else:
+            group = [r for r in self.waiting if key_of(r) == key][: self.max_batch]
+            cap = capacity_for(len(group), self.max_batch)
+        need = batch_bytes(key, cap, self.workspace_bytes)
+        if self.in_flight > 0 and self.in_flight + need > self.budget:
+            return None  # wait for memory (a batch that fits nowhere still runs alone)
+        ids = {id(r) for r in group}
+        self.waiting = [r for r in self.waiting if id(r) not in ids]
+        self.in_flight += need
+        return Batch(key, cap, group, need)
+
+    def release(self, batch: Batch) -> None:
+        self.in_flight -= batch.bytes
+
+
+@dataclass
+class _Slot:
+    plan: object
+    G: object
+    U: object
+    bytes: int
+
+
+@dataclass
+class ServeStats:
+    requests: int = 0
+    failed: int = 0
+    batches: int = 0
+    elapsed_s: float = 0.0
+    unknowns: int = 0
+    latencies_ms: list = field(default_factory=list)
+
+    def summary(self) -> dict:
+        lat = np.array(self.latencies_ms) if self.latencies_ms else np.zeros(1)
+        return {"requests": self.requests, "failed": self.failed, "batches": self.batches,
+                "mean_batch": self.requests / max(self.batches, 1), "elapsed_s": self.elapsed_s,
+                "solves_per_s": self.requests / max(self.elapsed_s, 1e-9),
+                "unknowns_per_s": self.unknowns / max(self.elapsed_s, 1e-9),
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "max_ms": float(lat.max())}
+
+
+class Server:
+    """Runs a request stream in real time on one GPU with `workers` CUDA streams."""
+
+    def __init__(self, device=None, precision="mixed", workers=2, budget_bytes=40 << 30, max_batch=32,
+                 keep_results=False, plan_cache_bytes=None):
+        import torch
+
+        from . import _binding as B
+        from .plan import Plan
+
+        self.torch, self.B, self.Plan = torch, B, Plan
+        self.device = torch.device(device) if device is not None else torch.device("cuda", 0)
+        self.precision = precision
+        self.workers = workers
+        self.keep_results = keep_results
+        self.plan_cache_bytes = plan_cache_bytes if plan_cache_bytes is not None else budget_bytes // 2
+        self._ws_cache: dict = {}
+        self.sched = Scheduler(budget_bytes, self._workspace_bytes, max_batch)
+        self.cv = threading.Condition()
+
+    # -- sizes ------------------------------------------------------------------------
+    def _desc_for(self, key: BatchKey, cap: int):
+        B = self.B
+        d = B.PdDesc()
+        d.abi_version = B.PD_ABI_VERSION
+        d.dim, d.nx, d.ny, d.nt, d.tau = key.dim, key.nx, key.ny, key.nt, 1.0 / key.nt
+        d.precision = B.PD_MIXED if self.precision == "mixed" else B.PD_FP64
+        d.q, d.alpha = 1, 1.0
+        d.batch = cap if key.dim == 1 else 0
+        return d
+
+    def _workspace_bytes(self, key: BatchKey, cap: int) -> int:
+        k = (key, cap)
+        if k not in self._ws_cache:
+            n = key.nx * (cap if key.dim == 1 else key.ny)
+            one = np.ones(n)
+            d = self._desc_for(key, cap)
+            p = lambda a: a.ctypes.data_as(self.B.ctypes.POINTER(self.B.ctypes.c_double))  # noqa: E731
+            d.k_lo = d.k_diag = d.k_up = p(one)
+            if key.dim == 2:
+                y = np.ones(key.ny)
+                d.k_lo_y = d.k_diag_y = d.k_up_y = p(y)
+            self._ws_cache[k] = self.B.paradiag_workspace_size(d)
+        return self._ws_cache[k]
+
+    # -- one batch ----------------------------------------------------------------------
+    def _slot(self, cache: OrderedDict, batch: Batch, stream):
+        import workloads.serving as S
+
+        torch = self.torch
+        k = (batch.key, batch.cap)
+        if k in cache:
+            cache.move_to_end(k)
+            return cache[k], False
+        # evict least recently used plans beyond this worker's share of the cache budget
+        share = self.plan_cache_bytes // max(self.workers, 1)
+        while cache and sum(s.bytes for s in cache.values()) + batch.bytes > share:
+            _, old = cache.popitem(last=False)
+            old.plan.close()
+        r0 = batch.requests[0]
+        if batch.key.dim == 1:
+            probs = [S.request_problem_operator_only(r, batch.key.nx) for r in batch.requests]
+            probs += [S.empty_slot(batch.key.nt) for _ in range(batch.cap - len(probs))]
+            plan = self.Plan.from_problems(probs, nx=batch.key.nx, precision=self.precision, device=self.device,
+                                           stream=stream)
+            nb = batch.cap * batch.key.nx
+        else:
+            kx, ky = S.operator(r0)
+            plan = self.Plan(dim=2, nx=r0.nx, ny=r0.ny, nt=r0.nt, tau=r0.tau, k_lo=kx[0], k_diag=kx[1],
+                             k_up=kx[2], k_lo_y=ky[0], k_diag_y=ky[1], k_up_y=ky[2], precision=self.precision,
+                             device=self.device, stream=stream)
+            nb = r0.nx * r0.ny
+        with torch.cuda.stream(stream):
+            G = torch.zeros((batch.key.nt, nb), dtype=torch.float64, device=self.device)
+            U = torch.empty_like(G)
+        slot = _Slot(plan, G, U, batch.bytes)
+        cache[k] = slot
+        return slot, True
+
+    def _run(self, batch: Batch, cache: OrderedDict, stream) -> None:
+        import workloads.serving as S
+
+        torch = self.torch
+        slot, fresh = self._slot(cache, batch, stream)
+        reqs = batch.requests
+        with torch.cuda.stream(stream):
+            if batch.key.dim == 1:
+                if not fresh:
+                    probs = [S.request_problem_operator_only(r, batch.key.nx) for r in reqs]
+                    probs += [S.empty_slot(batch.key.nt) for _ in range(batch.cap - len(probs))]
+                    slot.plan.set_problems(probs)
+                slot.G.zero_()
+                Gv = slot.G.view(batch.key.nt, batch.cap, batch.key.nx)
+                for b, r in enumerate(reqs):
+                    S.rhs_device(r, torch, self.device, out=Gv[:, b, :])
+            else:
+                r0 = reqs[0]
+                if not fresh:
+                    kx, ky = S.operator(r0)
+                    slot.plan.set_operator(tau=r0.tau, k_lo=kx[0], k_diag=kx[1], k_up=kx[2], k_lo_y=ky[0],
+                                           k_diag_y=ky[1], k_up_y=ky[2])
+                S.rhs_device(r0, torch, self.device, out=slot.G)
+            try:
+                slot.plan.solve(slot.G, slot.U)
+                err = None
+            except Exception as e:  # a failed solve fails its requests, not the service
+                err = str(e)
+            last = slot.U[-1]
+            final = last.view(batch.cap, batch.key.nx) if batch.key.dim == 1 else last.view(1, -1)
+            host = final.cpu().numpy() if self.keep_results else None
+        now = time.perf_counter() - self.t0
+        for b, r in enumerate(reqs):
+            r.done, r.batch, r.error = now, len(reqs), err
+            if host is not None:
+                r.result = host[b, : r.nx].copy() if batch.key.dim == 1 else host[0].copy()
+
+    # -- the run ------------------------------------------------------------------------
+    def run(self, requests: list) -> ServeStats:
+        torch = self.torch
+        reqs = sorted(requests, key=lambda r: r.arrival)
+        stats = ServeStats()
+        pending = list(reqs)
+        lock = self.cv
+        done_count = [0]
+        self.t0 = time.perf_counter()
+
+        def feeder():
+            for r in pending:
+                delay = r.arrival - (time.perf_counter() - self.t0)
+                if delay > 0:
+                    time.sleep(delay)
+                with lock:
+                    self.sched.add(r)
+                    lock.notify_all()
+
+        def worker():
+            stream = torch.cuda.Stream(device=self.device)
+            cache: OrderedDict = OrderedDict()
+            while True:
+                with lock:
+                    while True:
+                        if done_count[0] >= len(reqs):
+                            for s in cache.values():
+                                s.plan.close()
+                            return
+                        batch = self.sched.next_batch()
+                        if batch is not None:
+                            break
+                        lock.wait(timeout=0.05)
+                t_start = time.perf_counter() - self.t0
+                for r in batch.requests:
+                    r.start = t_start
+                self._run(batch, cache, stream)
+                with lock:
+                    self.sched.release(batch)
+                    done_count[0] += len(batch.requests)
+                    stats.batches += 1
+                    lock.notify_all()
+
+        threads = [threading.Thread(target=feeder)] + [threading.Thread(target=worker) for _ in range(self.workers)]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        stats.elapsed_s = max(r.done for r in reqs) - min(r.arrival for r in reqs) if reqs else 0.0
+        for r in reqs:
+            stats.requests += 1
+            stats.failed += 1 if r.error else 0
+            stats.unknowns += r.unknowns
+            stats.latencies_ms.append((r.done - r.arrival) * 1e3)
+        return stats

@@ -1,0 +1,53 @@
+"""The solver service on the GPU: requests of mixed kind and size, arriving together,
+are batched and run on two streams; every request's result (its final state u_l)
+must equal the result of the same request solved alone, and the oracle's, within
+the mixed-precision tolerance 1e-10."""
+import numpy as np
+import pytest
+
+import workloads.serving as S
+from oracle import reference as R
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def pd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as entry
+
+    entry.build()
+    import paper_2304_12597_gb300 as pkg
+
+    return pkg
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def test_served_results_equal_alone_and_oracle(pd):
+    from paper_2304_12597_gb300.serve import Server
+
+    reqs = S.request_stream(24, 1e5, seed=11, nx_range=(127, 700), nt_choices=(32, 64))
+    server = Server(device="cuda:0", workers=2, max_batch=8, keep_results=True, budget_bytes=8 << 30)
+    stats = server.run(reqs)
+    summ = stats.summary()
+    assert summ["failed"] == 0, [r.error for r in reqs if r.error]
+    assert max(r.batch for r in reqs) > 1  # some requests shared a batch
+    dev = torch.device("cuda:0")
+    for r in reqs:
+        P = S.request_problem(r)
+        with pd.Plan.from_problem(P, precision="mixed", device=dev) as plan:
+            U, _ = plan.solve(S.rhs_device(r, torch, dev).contiguous())
+            alone = U[-1].cpu().numpy()
+        assert _rel(r.result, alone) <= 2 * TOL, (r.rid, r.kind, r.batch)
+    for r in reqs[:6]:
+        P = S.request_problem(r)
+        ref = R.be_solve_refined(P)[-1]
+        assert _rel(r.result, ref) <= TOL, (r.rid, r.kind)
+    assert summ["p99_ms"] >= summ["p50_ms"] > 0

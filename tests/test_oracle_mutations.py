@@ -145,3 +145,17 @@ def test_py_mutation_transposed_krylov_operator(monkeypatch):
     explicit = np.linalg.norm(J @ info["x"] - info["b"])
     reported = info["krylov"]["resnorms"][-1]
     assert abs(explicit - reported) > 1e-6 * np.linalg.norm(info["b"]) or R.rel_err(U, R.be_solve(P)) > 1e-6
+
+
+def test_py_mutation_alpha_weight_dropped(monkeypatch):
+    """Algorithm 3 without the weight alpha^{1/l} on the inner sum (eq. 17) misses eq. (2)."""
+    P = W.heat1d_forced(15, 16, seed=1)
+    good = R.fom_like
+
+    def unweighted(*a, **k):
+        k["weight"] = 1.0
+        return good(*a, **k)
+
+    monkeypatch.setattr(R, "fom_like", unweighted)
+    U, _ = R.paradiag_alpha(P, 1e-2, eps=1e-14, maxit=40)
+    assert R.rel_err(U, R.be_solve(P)) > 1e-6

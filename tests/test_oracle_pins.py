@@ -352,3 +352,83 @@ def test_extended_residual_matches_float64_residual():
     P = W.heat2d_smooth(7, 8, 0.1, seed=2)
     U = np.random.default_rng(1).standard_normal(P.G.shape)
     assert np.allclose(R.residual_extended(P, U), P.G - R.aao_apply(P, U), rtol=1e-13, atol=1e-13)
+
+
+# ----------------------------------------------------------------------------
+# Algorithm 3 (alpha-acceleration, Sec. 4)
+# ----------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("ell,alpha", [(8, 0.3), (16, 1e-3), (5, 1.0)])
+def test_c_alpha_is_diagonalised_by_the_scaled_dft(ell, alpha):
+    """eq. (15)-(16): C_alpha = D_alpha^{-1} F^{-1} diag(pi) F D_alpha with pi of Algorithm 3."""
+    pi, _, d = R.alpha_quantities(ell, alpha)
+    F = R.dft_matrix(ell)
+    C = np.diag(1.0 / d) @ np.linalg.solve(F, np.diag(pi) @ F @ np.diag(d))
+    assert np.allclose(C, R.c_alpha(ell, alpha), atol=1e-13 / alpha)
+    # and Sigma_1 = C_alpha - alpha e_1 e_l^T (eq. 15)
+    E = np.zeros((ell, ell))
+    E[0, -1] = alpha
+    assert np.array_equal(R.c_alpha(ell, alpha) - E, R.sigma1(ell))
+
+
+@pytest.mark.parametrize("alpha", [1.0, 0.2, 1e-4])
+def test_alpha_inner_matrix_eigenvalues(alpha):
+    """eq. (17) for SPD K: I + alpha^{1/l} sum_i gamma_i (1 - pi_i + tau lambda)^{-1} has
+    the eigenvalue z^l / (z^l - alpha), z = 1 + tau lambda (the identity
+    sum_i omega^i / (z - a omega^i) = l a^{l-1} / (z^l - a^l) summed over the roots of
+    unity); alpha = 1 is Theorem 3.1's z^l / (z^l - 1)."""
+    n, ell, tau = 12, 16, 0.05
+    K = (np.diag(np.full(n, 2.0)) - np.diag(np.ones(n - 1), 1) - np.diag(np.ones(n - 1), -1)) * (n + 1) ** 2 / 50.0
+    lam = np.linalg.eigvalsh(K)
+    z = 1.0 + tau * lam
+    expect = np.sort(z ** ell / (z ** ell - alpha))
+    got = np.sort(np.linalg.eigvals(R.j_alpha_dense(K, tau, ell, alpha)).real)
+    assert np.allclose(got, expect, rtol=1e-10)
+
+
+@pytest.mark.parametrize("alpha", [1.0, 0.1, 1e-3, 1e-6])
+def test_algorithm3_equals_sequential_stepping(alpha):
+    """Algorithm 3 with an exact inner solve reaches eq. (2)'s solution; the error grows
+    like kappa(F D_alpha) = alpha^{-(l-1)/l} times the rounding unit (Sec. 4)."""
+    P = W.heat1d_forced(15, 16, seed=1)
+    U, info = R.paradiag_alpha(P, alpha, eps=1e-14, maxit=40)
+    kappa = alpha ** (-(P.nt - 1) / P.nt)
+    assert R.rel_err(U, R.be_solve(P)) <= 50 * kappa * 2.2e-16
+    assert info["U_imag"] <= 1e-10 * np.linalg.norm(U)
+
+
+def test_algorithm3_with_alpha_one_is_algorithm1():
+    P = W.advdiff1d_pulse(31, 16, 0.2, seed=1)
+    U3, i3 = R.paradiag_alpha(P, 1.0, eps=1e-13, maxit=40)
+    U1, i1 = R.paradiag(P, eps=1e-13, maxit=40)
+    assert R.rel_err(U3, U1) <= 1e-13
+    assert i3["krylov"]["m"] == i1["krylov"]["m"]
+
+
+def test_small_alpha_accelerates_the_inner_solve():
+    """Sec. 4: the inner matrix is a small perturbation of I for alpha << 1, so FOM needs
+    fewer iterations; here slow diffusion (nu = 1e-3) makes J_l far from I at alpha = 1."""
+    lo, di, up = W.heat1d_operator(63)
+    P = W.heat1d_forced(63, 32, seed=3)
+    P.k_lo, P.k_diag, P.k_up = 1e-3 * lo, 1e-3 * di, 1e-3 * up
+    ref = R.be_solve(P)
+    U1, i1 = R.paradiag_alpha(P, 1.0, eps=1e-6, maxit=60)
+    U4, i4 = R.paradiag_alpha(P, 1e-4, eps=1e-6, maxit=60)
+    U6, i6 = R.paradiag_alpha(P, 1e-6, eps=1e-6, maxit=60)
+    assert i6["krylov"]["m"] < i4["krylov"]["m"] < i1["krylov"]["m"]
+    assert i6["krylov"]["m"] <= 2
+    # the correction is weighted by alpha^{1/l}: the same inner tolerance leaves a
+    # far smaller error in U
+    assert R.rel_err(U4, ref) <= 1e-2 * R.rel_err(U1, ref)
+
+
+def test_algorithm3_early_exit_on_u1():
+    """For small alpha the first term U_1 alone passes the residual test of Algorithm 3
+    (the correction is O(alpha)); far smaller alpha loses that to kappa(F D_alpha)."""
+    P = W.heat1d_forced(31, 16, seed=4)
+    U, info = R.paradiag_alpha(P, 1e-6, early_exit_eps=1e-6)
+    assert info["exited_early"]
+    assert R.rel_err(U, R.be_solve(P)) <= 1e-6
+    _, info = R.paradiag_alpha(P, 1e-12, early_exit_eps=1e-6)
+    assert not info["exited_early"]

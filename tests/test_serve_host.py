@@ -1,0 +1,73 @@
+"""Host logic of the solver service (no GPU): request streams and the scheduler's
+grouping and admission rules."""
+import workloads.serving as S
+from paper_2304_12597_gb300.serve import NX_CLASSES, BatchKey, Scheduler, capacity_for, key_of, size_class
+
+
+def test_request_stream_is_seeded_and_in_range():
+    a = S.request_stream(200, 500.0, seed=3)
+    b = S.request_stream(200, 500.0, seed=3)
+    assert [(r.kind, r.nx, r.nt, r.nu, r.seed, r.arrival) for r in a] == \
+           [(r.kind, r.nx, r.nt, r.nu, r.seed, r.arrival) for r in b]
+    assert all(a[i].arrival < a[i + 1].arrival for i in range(len(a) - 1))
+    for r in a:
+        assert r.nt in (32, 64, 128, 256, 512, 1024, 2048)
+        assert 1e-4 <= r.nu <= 1.0
+        if r.kind == "heat2d":
+            assert r.nx == r.ny and r.nx in S.SIDES_2D
+        else:
+            assert 127 <= r.nx <= 4095 and r.ny == 1
+    # mean inter-arrival ~ 1/rate
+    assert abs(a[-1].arrival / len(a) - 1 / 500.0) < 0.5 / 500.0
+
+
+def test_size_classes_and_capacity():
+    assert size_class(127) == 128 and size_class(128) == 128 and size_class(129) == 256
+    assert size_class(4095) == NX_CLASSES[-1]
+    assert [capacity_for(c, 32) for c in (1, 2, 3, 5, 16, 17, 40)] == [2, 2, 4, 8, 16, 32, 32]
+
+
+def _req(rid, kind, nx, nt, t):
+    ny = nx if kind == "heat2d" else 1
+    return S.Request(rid=rid, arrival=t, kind=kind, nx=nx, ny=ny, nt=nt, nu=0.1, seed=rid)
+
+
+def test_scheduler_groups_by_key_in_arrival_order():
+    sch = Scheduler(budget=1 << 40, workspace_bytes=lambda k, c: 1000, max_batch=4)
+    reqs = [_req(0, "heat1d", 300, 64, 0.0), _req(1, "heat1d", 500, 64, 0.1), _req(2, "advdiff1d", 260, 64, 0.2),
+            _req(3, "heat2d", 63, 64, 0.3), _req(4, "heat1d", 400, 128, 0.4), _req(5, "heat1d", 511, 64, 0.5),
+            _req(6, "heat1d", 270, 64, 0.6), _req(7, "heat1d", 290, 64, 0.7), _req(8, "heat1d", 280, 64, 0.8)]
+    for r in reqs:
+        sch.add(r)
+    b1 = sch.next_batch()
+    # key of request 0: 1D, nt 64, class 512 -> 0, 1, 2, 5 (first four of that key)
+    assert b1.key == BatchKey(1, 64, 512, 1) and [r.rid for r in b1.requests] == [0, 1, 2, 5] and b1.cap == 4
+    b2 = sch.next_batch()
+    assert b2.key.dim == 2 and [r.rid for r in b2.requests] == [3] and b2.cap == 1
+    b3 = sch.next_batch()
+    assert [r.rid for r in b3.requests] == [4] and b3.cap == 2
+    b4 = sch.next_batch()
+    assert [r.rid for r in b4.requests] == [6, 7, 8] and b4.cap == 4
+    assert sch.next_batch() is None
+    for b in (b1, b2, b3, b4):
+        sch.release(b)
+    assert sch.in_flight == 0
+
+
+def test_scheduler_admission_waits_for_memory():
+    per = lambda k, c: 10_000  # noqa: E731
+    sch = Scheduler(budget=1, workspace_bytes=per, max_batch=8)  # nothing fits beside another batch
+    for i in range(3):
+        sch.add(_req(i, "heat1d", 200, 32, 0.01 * i))
+    b1 = sch.next_batch()  # an idle device always takes the head batch
+    assert b1 is not None and len(b1.requests) == 3
+    sch.add(_req(9, "heat1d", 200, 32, 1.0))
+    assert sch.next_batch() is None  # budget exhausted while b1 is in flight
+    sch.release(b1)
+    b2 = sch.next_batch()
+    assert [r.rid for r in b2.requests] == [9]
+
+
+def test_key_of():
+    assert key_of(_req(0, "heat2d", 127, 256, 0)) == BatchKey(2, 256, 127, 127)
+    assert key_of(_req(0, "advdiff1d", 1025, 256, 0)) == BatchKey(1, 256, 2048, 1)
