@@ -157,5 +157,8 @@ def test_py_mutation_alpha_weight_dropped(monkeypatch):
         return good(*a, **k)
 
     monkeypatch.setattr(R, "fom_like", unweighted)
-    U, _ = R.paradiag_alpha(P, 1e-2, eps=1e-14, maxit=40)
-    assert R.rel_err(U, R.be_solve(P)) > 1e-6
+    alpha = 1e-2
+    U, _ = R.paradiag_alpha(P, alpha, eps=1e-14, maxit=40)
+    kappa = alpha ** (-(P.nt - 1) / P.nt)
+    # the bound test_algorithm3_equals_sequential_stepping holds the unmutated oracle to
+    assert R.rel_err(U, R.be_solve(P)) > 1e3 * 50 * kappa * 2.2e-16
