@@ -76,9 +76,9 @@ typedef struct pd_desc {
   int32_t precision;     /* pd_precision */
   int32_t maxit;         /* Algorithm 2 iteration limit, 1 <= maxit <= 32 (0 = 32) */
   double eps_krylov;     /* Algorithm 2 tolerance epsilon (stop when ||r|| <= eps * ||b||);
-                            0 = 1e-13 for PD_FP64 (1e-4 for PD_FP64 batches, which then
-                            refine and leave a stalled step at any level), 1e-5 for the
-                            first solve of PD_MIXED
+                            0 = 1e-13 for PD_FP64 (1e-5 for PD_FP64 batches and alpha < 1,
+                            which always refine and leave a stalled step at any level),
+                            1e-5 for the first solve of PD_MIXED
                             (its refinement sweeps use max(eps_krylov, 1e-3)).
                             Both also stop when ||r|| stalls near the precision floor (no
                             halving over 1 iteration in PD_MIXED once ||r|| <= 1e-3 ||b||, and
@@ -93,7 +93,14 @@ typedef struct pd_desc {
   double refine_tol;     /* refinement stops when the predicted remaining relative error,
                             (||delta_s|| / ||delta_{s-1}||) * ||delta_s|| / ||U||, is <= refine_tol
                             (0 = 1e-14 for PD_FP64, 1e-11 for PD_MIXED) */
-  double alpha;          /* alpha of Sec. 4; only 1.0 (or 0 = 1.0) is built */
+  double alpha;          /* alpha of Sec. 4 in (0, 1] (0 = 1): 1 runs Algorithm 1, alpha < 1
+                            Algorithm 3 (alpha-circulant C_alpha, eq. 15: pi_k = alpha^{1/l}
+                            omega^k, time rows scaled by D_alpha before the DFT and by
+                            D_alpha^{-1} after the inverse, the inner system of eq. 17 and
+                            the correction weighted by alpha^{1/l}).  Every solve then loses up
+                            to kappa(F D_alpha) = alpha^{-(l-1)/l}, so alpha < 1 always
+                            refines (PD_FP64 too).  The stage entry points keep the plain
+                            DFT; paradiag_shifted_solve uses the plan's shifts. */
   void *stream;          /* cudaStream_t every launch is ordered on (NULL = legacy stream) */
   int32_t host_io;       /* nonzero: reserve device staging for paradiag_solve_host */
   int32_t no_graph;      /* nonzero: drive the Algorithm-2 and refinement loops from the host

@@ -97,7 +97,7 @@ __device__ void r2c_store(const cpx<T> *buf, int n, int logn, int64_t x0, int64_
 template <typename T, typename Tin, int TX>
 __global__ void __launch_bounds__(256) k_fft_r2c(const Tin *__restrict__ X, int64_t ldx, int64_t ncols,
                                                  int n, int logn, const cpx<T> *__restrict__ tw,
-                                                 cpx<T> *__restrict__ S, int64_t lds) {
+                                                 cpx<T> *__restrict__ S, int64_t lds, const T *__restrict__ rs) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cpx<T> *buf = reinterpret_cast<cpx<T> *>(smraw);
   const int64_t x0 = (int64_t)blockIdx.x * TX;
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(256) k_fft_r2c(const Tin *__restrict__ X, int6
         const int j = idx / TX;
         const int c = idx - j * TX;
         T *slot = reinterpret_cast<T *>(&buf[((size_t)(c >> 1) << logn) + bitrev(j, logn)]);
-        slot[c & 1] = v[u];
+        slot[c & 1] = rs ? v[u] * rs[j] : v[u];
       }
     }
   }
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(256) k_fft_r2c_res(const double *__restrict__ 
                                                      const double *__restrict__ rxd,
                                                      const double *__restrict__ rxu,
                                                      const cpx<T> *__restrict__ tw, cpx<T> *__restrict__ S,
-                                                     int64_t lds) {
+                                                     int64_t lds, const T *__restrict__ rs) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cpx<T> *buf = reinterpret_cast<cpx<T> *>(smraw);
   const int64_t x0 = (int64_t)blockIdx.x * TX;
@@ -171,7 +171,8 @@ __global__ void __launch_bounds__(256) k_fft_r2c_res(const double *__restrict__ 
       const int j = j0 + q * ((int)blockDim.x / TX);
       if (j < n) {
         const double au = fma(cu, ur[q], fma(cl, ul[q], cd * uc[q]));
-        col_buf[2 * bitrev(j, logn)] = (T)((g[q] + um[q]) - au);
+        const T r = (T)((g[q] + um[q]) - au);
+        col_buf[2 * bitrev(j, logn)] = rs ? r * rs[j] : r;
       }
     }
   }
@@ -186,7 +187,8 @@ template <typename T, int TX>
 __global__ void __launch_bounds__(256) k_fft_c2r(const cpx<T> *__restrict__ S, int64_t lds, int64_t ncols,
                                                  int n, int logn, const cpx<T> *__restrict__ tw,
                                                  void *__restrict__ out, int64_t ldo, int mode,
-                                                 double *__restrict__ norm_part, StepFinish fin) {
+                                                 double *__restrict__ norm_part, StepFinish fin,
+                                                 const T *__restrict__ rsi) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cpx<T> *buf = reinterpret_cast<cpx<T> *>(smraw);
   const int64_t x0 = (int64_t)blockIdx.x * TX;
@@ -242,7 +244,8 @@ __global__ void __launch_bounds__(256) k_fft_c2r(const cpx<T> *__restrict__ S, i
       const int64_t col = x0 + c;
       if (idx >= tot2 || col >= ncols) continue;
       const cpx<T> r = buf[((size_t)(c >> 1) << logn) + j];
-      const T v = ((c & 1) == 0) ? r.x * inv_n : -r.y * inv_n;
+      const T sc = rsi ? inv_n * rsi[j] : inv_n;
+      const T v = ((c & 1) == 0) ? r.x * sc : -r.y * sc;
       const int64_t o = (int64_t)j * ldo + col;
       if (mode == 0) {
         reinterpret_cast<double *>(out)[o] = (double)v;
@@ -394,7 +397,7 @@ static int pick_tx(int n, int cap, int64_t ncols, int req = 0) {
 
 template <typename T, typename Tin>
 void launch_fft_r2c(Ctx &c, const Tin *X, int64_t ldx, int64_t ncols, int n, const cpx<T> *tw,
-                    cpx<T> *S, int64_t lds) {
+                    cpx<T> *S, int64_t lds, const T *rs) {
   const int logn = ilog2(n);
   const int TX = pick_tx<T>(n, sizeof(T) == 8 ? 8 : 16, ncols, c.fft_cols);
   const size_t smem = (size_t)(TX / 2) * n * sizeof(cpx<T>);
@@ -404,14 +407,15 @@ void launch_fft_r2c(Ctx &c, const Tin *X, int64_t ldx, int64_t ncols, int n, con
     PD_TX_DISPATCH(TX, {
       if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_fft_r2c<T, Tin, kTX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      k_fft_r2c<T, Tin, kTX><<<grid, 256, smem, c.stream>>>(X, ldx, ncols, n, logn, tw, S, lds);
+      k_fft_r2c<T, Tin, kTX><<<grid, 256, smem, c.stream>>>(X, ldx, ncols, n, logn, tw, S, lds, rs);
     })
   });
 }
 
 template <typename T>
 void launch_fft_r2c_residual(Ctx &c, const double *G, const double *U, int64_t ncols, int n, const double *rxl,
-                             const double *rxd, const double *rxu, const cpx<T> *tw, cpx<T> *S, int64_t lds) {
+                             const double *rxd, const double *rxu, const cpx<T> *tw, cpx<T> *S, int64_t lds,
+                             const T *rs) {
   const int logn = ilog2(n);
   const int TX = pick_tx<T>(n, sizeof(T) == 8 ? 8 : 16, ncols, c.fft_cols);
   const size_t smem = (size_t)(TX / 2) * n * sizeof(cpx<T>);
@@ -421,14 +425,15 @@ void launch_fft_r2c_residual(Ctx &c, const double *G, const double *U, int64_t n
     PD_TX_DISPATCH(TX, {
       if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_fft_r2c_res<T, kTX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      k_fft_r2c_res<T, kTX><<<grid, 256, smem, c.stream>>>(G, U, ncols, n, logn, rxl, rxd, rxu, tw, S, lds);
+      k_fft_r2c_res<T, kTX><<<grid, 256, smem, c.stream>>>(G, U, ncols, n, logn, rxl, rxd, rxu, tw, S, lds, rs);
     })
   });
 }
 
 template <typename T>
 void launch_fft_c2r(Ctx &c, const cpx<T> *S, int64_t lds, int64_t ncols, int n, const cpx<T> *tw,
-                    void *out, int64_t ldo, int mode, double *norm_part, int *nparts, const StepFinish *finp) {
+                    void *out, int64_t ldo, int mode, double *norm_part, int *nparts, const StepFinish *finp,
+                    const T *rsi) {
   StepFinish fin{};
   if (finp && norm_part) fin = *finp;
   const int logn = ilog2(n);
@@ -443,7 +448,7 @@ void launch_fft_c2r(Ctx &c, const cpx<T> *S, int64_t lds, int64_t ncols, int n, 
       if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_fft_c2r<T, kTX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       k_fft_c2r<T, kTX><<<grid, 256, smem, c.stream>>>(S, lds, ncols, n, logn, tw, out, ldo, mode, norm_part,
-                                                         fin);
+                                                         fin, rsi);
     })
   });
 }
@@ -469,21 +474,21 @@ void launch_dst_y(Ctx &c, const Tin *X, Tout *Y, int64_t nt, int64_t ny, int64_t
 }
 
 template void launch_fft_r2c<double, double>(Ctx &, const double *, int64_t, int64_t, int, const cpx<double> *,
-                                             cpx<double> *, int64_t);
+                                             cpx<double> *, int64_t, const double *);
 template void launch_fft_r2c<float, double>(Ctx &, const double *, int64_t, int64_t, int, const cpx<float> *,
-                                            cpx<float> *, int64_t);
+                                            cpx<float> *, int64_t, const float *);
 template void launch_fft_r2c<float, float>(Ctx &, const float *, int64_t, int64_t, int, const cpx<float> *,
-                                           cpx<float> *, int64_t);
+                                           cpx<float> *, int64_t, const float *);
 template void launch_fft_c2r<double>(Ctx &, const cpx<double> *, int64_t, int64_t, int, const cpx<double> *,
-                                     void *, int64_t, int, double *, int *, const StepFinish *);
+                                     void *, int64_t, int, double *, int *, const StepFinish *, const double *);
 template void launch_fft_c2r<float>(Ctx &, const cpx<float> *, int64_t, int64_t, int, const cpx<float> *,
-                                    void *, int64_t, int, double *, int *, const StepFinish *);
+                                    void *, int64_t, int, double *, int *, const StepFinish *, const float *);
 template void launch_fft_r2c_residual<double>(Ctx &, const double *, const double *, int64_t, int, const double *,
                                               const double *, const double *, const cpx<double> *, cpx<double> *,
-                                              int64_t);
+                                              int64_t, const double *);
 template void launch_fft_r2c_residual<float>(Ctx &, const double *, const double *, int64_t, int, const double *,
                                              const double *, const double *, const cpx<float> *, cpx<float> *,
-                                             int64_t);
+                                             int64_t, const float *);
 template void launch_dst_y<double, double, double>(Ctx &, const double *, double *, int64_t, int64_t, int64_t,
                                                    const cpx<double> *, int);
 template void launch_dst_y<double, float, float>(Ctx &, const double *, float *, int64_t, int64_t, int64_t,

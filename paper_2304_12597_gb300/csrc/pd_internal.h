@@ -100,15 +100,17 @@ struct RefineCtl {
 };
 // ---- time FFT / DST (fft.cu) ----------------------------------------------------
 // Forward DFT along time of real (n, ncols) rows -> half spectrum (n/2+1, ncols).
+// rs (may be null): row j of X is multiplied by rs[j] on load (the D_alpha of
+// Algorithm 3); rsi in the inverse: output row j multiplied by rsi[j].
 template <typename T, typename Tin>
 void launch_fft_r2c(Ctx &c, const Tin *X, int64_t ldx, int64_t ncols, int n, const cpx<T> *tw,
-                    cpx<T> *S, int64_t lds);
+                    cpx<T> *S, int64_t lds, const T *rs = nullptr);
 // Forward DFT along time of the FP64 all-at-once residual
 // R = G - [(I + tau K) U - U Sigma_1^T] (1D), computed on load: R is never stored.
 template <typename T>
 void launch_fft_r2c_residual(Ctx &c, const double *G, const double *U, int64_t ncols, int n,
                              const double *rxl, const double *rxd, const double *rxu, const cpx<T> *tw,
-                             cpx<T> *S, int64_t lds);
+                             cpx<T> *S, int64_t lds, const T *rs = nullptr);
 // Optional epilogue of the inverse DFT: the last CTA to finish sums the per-CTA
 // squares into scal[S_D2] and runs the refinement decision.
 struct StepFinish {
@@ -126,7 +128,7 @@ struct StepFinish {
 template <typename T>
 void launch_fft_c2r(Ctx &c, const cpx<T> *S, int64_t lds, int64_t ncols, int n, const cpx<T> *tw,
                     void *out, int64_t ldo, int mode, double *norm_part, int *nparts,
-                    const StepFinish *fin = nullptr);
+                    const StepFinish *fin = nullptr, const T *rsi = nullptr);
 // Orthonormal DST-I along the middle axis of (nt, ny, nx); ny + 1 a power of two.
 // mode 0: store, 1: add into (double output only).
 template <typename Tin, typename Tout, typename T>
@@ -177,6 +179,7 @@ struct PintArgs {
   int mdots;               // number of basis vectors dotted with y_k
   double2 *gpart;          // (nf, nblk, mdots) dot products y_k . V[q]
   const int *skip_flag;    // if non-null and *skip_flag != 0 the kernel does nothing
+  double xm_scale;         // with xm_count: subtract xm_scale * x_m (alpha^{1/l} in Algorithm 3)
 };
 template <typename T>
 void launch_pint(Ctx &c, const PintGeom &g, const PintArgs<T> &a);

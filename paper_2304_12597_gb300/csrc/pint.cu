@@ -144,8 +144,9 @@ __global__ void __launch_bounds__(MAXT) k_pint(PintGeom g, PintArgs<T> a, size_t
   // below; each loop issues all its global loads before using them, so a thread
   // waits for one memory latency per loop rather than one per element.
 
-  // x_m = V_m y_m for the team's rows (final loop of Algorithm 1), kept in the
-  // accumulator region, which this pass does not otherwise use
+  // x_m = V_m y_m for the team's rows (final loop of Algorithm 1; Algorithm 3 weights
+  // it by alpha^{1/l}), kept in the accumulator region, which this pass does not
+  // otherwise use
   T *xs = nullptr;
   if (a.xm_count && active) {
     xs = acc;
@@ -160,8 +161,9 @@ __global__ void __launch_bounds__(MAXT) k_pint(PintGeom g, PintArgs<T> a, size_t
       for (int i = 0; i < M; ++i)
         if (t + i * P < blen) v[i] += yq * vq[t + i * P];
     }
+    const T xsc = (T)a.xm_scale;
 #pragma unroll
-    for (int i = 0; i < M; ++i) xs[t + i * P] = v[i];
+    for (int i = 0; i < M; ++i) xs[t + i * P] = xsc * v[i];
     if (rr == 0 && a.xm_out) {
       double vd[M];
 #pragma unroll

@@ -148,6 +148,9 @@ struct pd_plan {
   int64_t nx = 0, ny = 1, nbar = 0, nt = 0;
   int nf = 0;
   double tau = 0.0;
+  double alpha = 1.0;  // Algorithm 3: C_alpha instead of C_1 (1 = Algorithm 1)
+  bool refined64 = false;  // FP64 plan that always refines (alpha < 1 or a batch)
+  double aroot = 1.0;  // alpha^{1/l}
   int precision = PD_FP64;
   int maxit = 32;
   double eps = 1e-13;
@@ -173,6 +176,9 @@ struct pd_plan {
 
   // device buffers
   double2 *shift = nullptr, *wg = nullptr;
+  double2 *wga = nullptr;  // alpha^{1/l} w_k gamma_k: weights of the inner system (eq. 17)
+  double *ts_d = nullptr, *tsi_d = nullptr;  // D_alpha and D_alpha^{-1} (time rows)
+  float *ts_f = nullptr, *tsi_f = nullptr;
   double *klo = nullptr, *kdiag = nullptr, *kup = nullptr;
   double *tlo_d = nullptr, *tdiag_d = nullptr, *tup_d = nullptr;
   float *tlo_f = nullptr, *tdiag_f = nullptr, *tup_f = nullptr;
@@ -235,7 +241,7 @@ pd_status validate(const pd_desc *d) {
   if (d->precision != PD_FP64 && d->precision != PD_MIXED) return fail(PD_ERR_INVALID_ARG, "bad precision");
   if (d->maxit < 0 || d->maxit > 32) return fail(PD_ERR_UNSUPPORTED, "maxit must be in [1, 32]");
   if (d->q != 0 && d->q != 1) return fail(PD_ERR_UNSUPPORTED, "only q = 1 (residual check every iteration) is built");
-  if (d->alpha != 0.0 && d->alpha != 1.0) return fail(PD_ERR_UNSUPPORTED, "only alpha = 1 (Algorithm 1) is built");
+  if (!(d->alpha >= 0.0 && d->alpha <= 1.0)) return fail(PD_ERR_INVALID_ARG, "alpha must be in (0, 1] (0 = 1)");
   if (d->eps_krylov < 0.0 || d->refine_tol < 0.0 || d->max_refine < 0)
     return fail(PD_ERR_INVALID_ARG, "negative tolerance or sweep count");
   const int64_t blen = d->nx;
@@ -300,13 +306,17 @@ void fill_geometry(pd_plan *p, const pd_desc *d) {
   if (d->nt == 1) p->nf = 1;
   // a batch folds each problem's time step into its block of K (tau = 1 below)
   p->tau = p->batch > 1 ? 1.0 : d->tau;
+  p->alpha = d->alpha > 0.0 ? d->alpha : 1.0;
+  p->aroot = std::pow(p->alpha, 1.0 / (double)d->nt);
+  p->refined64 = d->precision == PD_FP64 && (p->alpha < 1.0 || d->batch > 1);
   p->precision = d->precision;
   p->maxit = d->maxit ? d->maxit : 32;
   p->eps = d->eps_krylov > 0 ? d->eps_krylov : (d->precision == PD_FP64 ? 1e-13 : 1e-5);
-  // FP64 batches: one Krylov space serves every problem and must resolve the union of
-  // their spectral content, so a loose tolerance per solve plus FP64 refinement
-  // sweeps costs far fewer iterations than one tight solve
-  if (d->batch > 1 && d->precision == PD_FP64 && !(d->eps_krylov > 0)) p->eps = 1e-4;
+  // FP64 plans that refine anyway use a loose tolerance per solve: a batch's single
+  // Krylov space must resolve the union of its problems' spectral content, and
+  // Algorithm 3 loses up to kappa(F D_alpha) per solve, so FP64 refinement sweeps
+  // with a few Krylov steps each beat one tight solve
+  if (p->refined64 && !(d->eps_krylov > 0)) p->eps = 1e-5;
   p->max_refine = d->max_refine ? d->max_refine : 8;
   p->refine_tol = d->refine_tol > 0 ? d->refine_tol : (d->precision == PD_FP64 ? 1e-14 : 1e-11);
   p->host_io = d->host_io;
@@ -345,6 +355,13 @@ size_t layout(pd_plan *p, unsigned char *base) {
   const bool mixed = p->precision == PD_MIXED;
   p->shift = A.take<double2>(nf);
   p->wg = A.take<double2>(nf);
+  p->wga = A.take<double2>(nf);
+  p->ts_d = A.take<double>(nt);
+  p->tsi_d = A.take<double>(nt);
+  if (mixed) {
+    p->ts_f = A.take<float>(nt);
+    p->tsi_f = A.take<float>(nt);
+  }
   p->klo = A.take<double>(nbar);
   p->kdiag = A.take<double>(nbar);
   p->kup = A.take<double>(nbar);
@@ -560,6 +577,17 @@ template <>
 const cpx<double> *time_tw<double>(pd_plan *p) { return p->tw_d; }
 template <>
 const cpx<float> *time_tw<float>(pd_plan *p) { return p->tw_f; }
+// D_alpha and D_alpha^{-1} on the time rows (Algorithm 3), or null for alpha = 1
+template <typename T>
+const T *row_scale(pd_plan *p, bool inverse);
+template <>
+const double *row_scale<double>(pd_plan *p, bool inverse) {
+  return p->alpha == 1.0 ? nullptr : (inverse ? p->tsi_d : p->ts_d);
+}
+template <>
+const float *row_scale<float>(pd_plan *p, bool inverse) {
+  return p->alpha == 1.0 ? nullptr : (inverse ? p->tsi_f : p->ts_f);
+}
 
 template <typename T>
 const T *vbasis(pd_plan *p);
@@ -579,6 +607,7 @@ pd::PintArgs<T> base_args(pd_plan *p);
 template <>
 pd::PintArgs<double> base_args<double>(pd_plan *p) {
   pd::PintArgs<double> a{};
+  a.xm_scale = p->aroot;
   a.shift = p->shift;
   a.tlo = p->tlo_d;
   a.tdiag = p->tdiag_d;
@@ -588,6 +617,7 @@ pd::PintArgs<double> base_args<double>(pd_plan *p) {
 template <>
 pd::PintArgs<float> base_args<float>(pd_plan *p) {
   pd::PintArgs<float> a{};
+  a.xm_scale = p->aroot;
   a.shift = p->shift;
   a.tlo = p->tlo_f;
   a.tdiag = p->tdiag_f;
@@ -634,7 +664,8 @@ pd::KrylovCtl krylov_ctl(pd_plan *p, int kind) {
   k.eps = kind == 0 ? p->eps : std::max(p->eps, fp64 ? 1e-8 : 1e-3);
   k.stall_floor = fp64 ? 1e-6 : (kind == 0 ? 1e-3 : 1.0);
   k.win = fp64 ? 3 : 1;
-  if (fp64 && p->batch > 1) {  // refined FP64 batches: leave a stalled step at any level
+  if (p->refined64) {  // refined FP64 plans: leave a stalled step at any level
+    k.eps = std::max(p->eps, 1e-8);
     k.stall_floor = 1.0;
     k.win = 2;
   }
@@ -645,9 +676,10 @@ pd::KrylovCtl krylov_ctl(pd_plan *p, int kind) {
 pd::RefineCtl refine_ctl(pd_plan *p) {
   const bool fp64 = p->precision == PD_FP64;
   pd::RefineCtl r;
-  r.fp64 = fp64 ? 1 : 0;
+  // refined FP64 plans stop like the mixed ones (by the contraction of the updates)
+  r.fp64 = (fp64 && !p->refined64) ? 1 : 0;
   r.eps_first = p->eps;
-  r.eps_refine = std::max(p->eps, fp64 ? 1e-8 : 1e-3);
+  r.eps_refine = p->refined64 ? std::max(p->eps, 1e-8) : std::max(p->eps, fp64 ? 1e-8 : 1e-3);
   r.refine_tol = p->refine_tol;
   r.max_refine = p->max_refine;
   return r;
@@ -674,18 +706,19 @@ pd_status emit_pre(pd_plan *p, int kind, const double *G, double *U, int use_han
   T *tmp = tmp_buf<T>(p);
   if (kind == 0) {
     if (p->dim == 1) {
-      pd::launch_fft_r2c<T, double>(c, G, p->nbar, p->nbar, nt, time_tw<T>(p), S, p->lds);
+      pd::launch_fft_r2c<T, double>(c, G, p->nbar, p->nbar, nt, time_tw<T>(p), S, p->lds, row_scale<T>(p, false));
     } else {
       pd::launch_dst_y<double, T, T>(c, G, tmp, p->nt, p->ny, p->nx, dst_tw<T>(p), 0);
-      pd::launch_fft_r2c<T, T>(c, tmp, p->nbar, p->nbar, nt, time_tw<T>(p), S, p->lds);
+      pd::launch_fft_r2c<T, T>(c, tmp, p->nbar, p->nbar, nt, time_tw<T>(p), S, p->lds, row_scale<T>(p, false));
     }
   } else {
     if (p->dim == 1) {  // the FP64 residual is formed while the DFT loads its tiles
-      pd::launch_fft_r2c_residual<T>(c, G, U, p->nbar, nt, p->rxl, p->rxd, p->rxu, time_tw<T>(p), S, p->lds);
+      pd::launch_fft_r2c_residual<T>(c, G, U, p->nbar, nt, p->rxl, p->rxd, p->rxu, time_tw<T>(p), S, p->lds,
+                                     row_scale<T>(p, false));
     } else {
       pd::launch_residual<T>(c, G, U, res, p->nt, p->ny, p->nx, p->rxl, p->rxd, p->rxu, p->ryl, p->ryd, p->ryu);
       pd::launch_dst_y<T, T, T>(c, res, tmp, p->nt, p->ny, p->nx, dst_tw<T>(p), 0);
-      pd::launch_fft_r2c<T, T>(c, tmp, p->nbar, p->nbar, nt, time_tw<T>(p), S, p->lds);
+      pd::launch_fft_r2c<T, T>(c, tmp, p->nbar, p->nbar, nt, time_tw<T>(p), S, p->lds, row_scale<T>(p, false));
     }
   }
   pd::PintArgs<T> a = base_args<T>(p);
@@ -720,7 +753,7 @@ pd_status emit_iter(pd_plan *p, int kind, int use_handle, cudaGraphConditionalHa
     a.skip_flag = p->flags + pd::F_BREAK;
     pd::launch_pint<T>(c, p->geom, a);
   }
-  pd::launch_capacitance(c, kb, p->nf, p->tau, p->shift, p->wg, p->gpart, p->nblk, p->msys_part, p->k5_grid,
+  pd::launch_capacitance(c, kb, p->nf, p->tau, p->shift, p->wga, p->gpart, p->nblk, p->msys_part, p->k5_grid,
                          p->srow, p->omega, p->y);
   // z = sum_i gamma_i h_i (e_m^T S_i y_m) from the stored h_i, then eq. (13)
   pd::launch_zsum<T>(c, p->nf, p->nbar, H, p->lds, p->omega, p->z, p->flags + pd::F_BREAK);
@@ -764,11 +797,11 @@ pd_status emit_post(pd_plan *p, int kind, double *U, int use_handle, cudaGraphCo
   int nparts = 0;
   if (p->dim == 1) {
     pd::launch_fft_c2r<T>(c, S, p->lds, p->nbar, nt, time_tw<T>(p), U, p->nbar, kind == 0 ? 0 : 1, p->norm_part,
-                          &nparts, &fin);
+                          &nparts, &fin, row_scale<T>(p, true));
   } else {
     T *tmp = tmp_buf<T>(p);
     pd::launch_fft_c2r<T>(c, S, p->lds, p->nbar, nt, time_tw<T>(p), tmp, p->nbar, fp64 ? 0 : 2, p->norm_part,
-                          &nparts, &fin);
+                          &nparts, &fin, row_scale<T>(p, true));
     pd::launch_dst_y<T, double, T>(c, tmp, U, p->nt, p->ny, p->nx, dst_tw<T>(p), kind == 0 ? 0 : 1);
   }
   return PD_OK;
@@ -1050,17 +1083,29 @@ pd_status paradiag_plan(const pd_desc *desc, void *workspace, size_t workspace_b
   if (cudaEventCreate(&p->ev0) != cudaSuccess || cudaEventCreate(&p->ev1) != cudaSuccess)
     return cleanup(fail(PD_ERR_CUDA, "cudaEventCreate failed"));
 
-  // Algorithm 1, first step: pi_k = omega^k, gamma_k = pi_k / l; shifts s_k = 1 - pi_k;
-  // half-spectrum weights w_k (1 for k = 0 and k = l/2, 2 otherwise).
+  // Algorithm 1, first step: pi_k = omega^k, gamma_k = omega^k / l; shifts s_k = 1 - pi_k;
+  // half-spectrum weights w_k (1 for k = 0 and k = l/2, 2 otherwise).  Algorithm 3:
+  // pi_k = alpha^{1/l} omega^k, the same gamma_k, D_alpha = diag(alpha^{j/l}), and the
+  // inner system weighted by alpha^{1/l} (wga).
   const int nf = p->nf;
   const int64_t nt = p->nt;
-  std::vector<double2> shift(nf), wg(nf);
+  const double a = p->aroot;
+  std::vector<double2> shift(nf), wg(nf), wga(nf);
   for (int k = 0; k < nf; ++k) {
     const double ang = -2.0 * M_PI * (double)k / (double)nt;
     const double pr = std::cos(ang), pi_ = std::sin(ang);
     const double wk = (k == 0 || 2 * (int64_t)k == nt) ? 1.0 : 2.0;
-    shift[k] = make_double2(1.0 - pr, -pi_);
+    shift[k] = make_double2(1.0 - a * pr, -a * pi_);
     wg[k] = make_double2(wk * pr / (double)nt, wk * pi_ / (double)nt);
+    wga[k] = make_double2(a * wg[k].x, a * wg[k].y);
+  }
+  std::vector<double> ts(nt), tsi(nt);
+  std::vector<float> tsf(nt), tsif(nt);
+  for (int64_t j = 0; j < nt; ++j) {
+    ts[j] = std::pow(p->alpha, (double)j / (double)nt);
+    tsi[j] = 1.0 / ts[j];
+    tsf[j] = (float)ts[j];
+    tsif[j] = (float)tsi[j];
   }
   const int ntw = std::max<int>(1, (int)(nt / 2));
   std::vector<cpx<double>> tw(ntw);
@@ -1072,7 +1117,10 @@ pd_status paradiag_plan(const pd_desc *desc, void *workspace, size_t workspace_b
   }
   cudaStream_t s = p->ctx.stream;
   if ((st = upload(p->shift, shift.data(), nf, s)) || (st = upload(p->wg, wg.data(), nf, s)) ||
-      (st = upload(p->tw_d, tw.data(), ntw, s)) || (st = upload(p->tw_f, twf.data(), ntw, s)))
+      (st = upload(p->wga, wga.data(), nf, s)) || (st = upload(p->tw_d, tw.data(), ntw, s)) ||
+      (st = upload(p->tw_f, twf.data(), ntw, s)) || (st = upload(p->ts_d, ts.data(), nt, s)) ||
+      (st = upload(p->tsi_d, tsi.data(), nt, s)) || (st = upload(p->ts_f, tsf.data(), nt, s)) ||
+      (st = upload(p->tsi_f, tsif.data(), nt, s)))
     return cleanup(st);
   if (p->dim == 2) {
     const int N = (int)(2 * (p->ny + 1));

@@ -33,7 +33,7 @@ class Plan:
 
     def __init__(self, *, dim, nx, nt, tau, k_lo, k_diag, k_up, ny=1, k_lo_y=None, k_diag_y=None,
                  k_up_y=None, precision="mixed", maxit=0, eps_krylov=0.0, max_refine=0, refine_tol=0.0,
-                 host_io=False, no_graph=False, tune=None, batch=1, batch_nx=None, batch_tau=None,
+                 alpha=1.0, host_io=False, no_graph=False, tune=None, batch=1, batch_nx=None, batch_tau=None,
                  device=None, stream=None, workspace="torch"):
         import torch
 
@@ -61,7 +61,7 @@ class Plan:
         d.q = 1
         d.max_refine = int(max_refine)
         d.refine_tol = float(refine_tol)
-        d.alpha = 1.0
+        d.alpha = float(alpha)
         d.stream = ctypes.c_void_p(self.stream.cuda_stream)
         d.host_io = 1 if host_io else 0
         d.no_graph = 1 if no_graph else 0

@@ -112,6 +112,7 @@ def test_valid_descriptors_have_a_workspace(B):
                {"precision": 1, "tune_pint_rows": 16, "tune_pint_teams": 2, "tune_krylov_ctas": 8,
                 "tune_cap_ctas": 3, "tune_fft_cols": 2},
                {"batch": 3, "batch_nx": [31, 5, 1], "batch_tau": [0.1, 0.2, 1e-3]}, {"batch": 4},
+               {"alpha": 1e-4}, {"alpha": 0.5, "precision": 1},
                {"dim": 2, "ny": 7}, {"dim": 2, "ny": 255, "n": 255, "nt": 256, "precision": 1}):
         st, n = _size_status(B, _desc(B, **kw))
         assert st == 0, (kw, B.last_error())
@@ -129,7 +130,9 @@ def test_valid_descriptors_have_a_workspace(B):
     ({"precision": 7}, 1),
     ({"maxit": 40}, 2),
     ({"q": 2}, 2),
-    ({"alpha": 0.5}, 2),
+    ({"alpha": 1.5}, 1),
+    ({"alpha": -0.1}, 1),
+    ({"alpha": float("nan")}, 1),
     ({"n": 5000}, 2),
     ({"dim": 2, "ny": 6}, 2),
     ({"dim": 2, "ny": 7, "y_diag": np.array([2, 2, 2, 3, 2, 2, 2.0])}, 2),

@@ -1,0 +1,95 @@
+"""Algorithm 3 (alpha-acceleration, Sec. 4) on the GPU against the oracle.
+
+The solution must match eq. (2)'s (the refined oracle) within the usual tolerances,
+b and x_m of the first solve must match the oracle's Algorithm 3, and a small alpha
+must cut the Krylov iterations on slow diffusion."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import reference as R
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "mixed": 1e-10}
+
+
+@pytest.fixture(scope="module")
+def pd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as entry
+
+    entry.build()
+    import paper_2304_12597_gb300 as pkg
+
+    return pkg
+
+
+def dev():
+    return torch.device("cuda:0")
+
+
+def _slow_heat(n, nt, nu, seed):
+    P = W.heat1d_forced(n, nt, seed=seed)
+    lo, di, up = W.heat1d_operator(n)
+    P.k_lo, P.k_diag, P.k_up = nu * lo, nu * di, nu * up
+    return P
+
+
+CASES = [
+    lambda: _slow_heat(255, 64, 1e-3, 1),
+    lambda: W.advdiff1d_pulse(511, 128, seed=2),
+    lambda: W.heat2d_smooth(31, 32, seed=3),
+    lambda: W.random_tridiag_problem(100, 16, seed=4),
+]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("alpha", [1e-2, 1e-4])
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_alpha_solve_matches_oracle(pd, prec, alpha, case):
+    P = CASES[case]()
+    with pd.Plan.from_problem(P, precision=prec, alpha=alpha, device=dev()) as plan:
+        U, st = plan.solve(torch.from_numpy(P.G).to(dev()))
+    err = R.rel_err(U.cpu().numpy(), R.be_solve_refined(P))
+    assert err <= TOL[prec], (err, st)
+
+
+def test_alpha_first_solve_b_and_x_match_algorithm3(pd):
+    P = _slow_heat(127, 32, 1e-2, 5)
+    alpha = 1e-3
+    with pd.Plan.from_problem(P, precision="fp64", alpha=alpha, eps_krylov=1e-14, device=dev()) as plan:
+        _, st = plan.solve(torch.from_numpy(P.G).to(dev()))
+        b, x = plan.last_vectors()
+    _, info = R.paradiag_alpha(P, alpha, eps=1e-14, maxit=32)
+    assert R.rel_err(b.cpu().numpy(), info["b"]) <= 1e-12
+    # x_m of the first solve: Algorithm 2 on the GPU may leave earlier (stall rule); the
+    # inner matrix is I + O(alpha), so x differs by about the relative residual it left
+    kres = st["sweep_krylov_rel_resnorm"][0]
+    assert R.rel_err(x.cpu().numpy(), info["x"]) <= 10 * kres + 1e-12
+
+
+def test_small_alpha_needs_fewer_krylov_steps(pd):
+    P = _slow_heat(255, 64, 1e-3, 6)
+    G = torch.from_numpy(P.G).to(dev())
+    m = {}
+    for alpha in (1.0, 1e-4):
+        with pd.Plan.from_problem(P, precision="fp64", alpha=alpha, device=dev()) as plan:
+            _, st = plan.solve(G)
+            m[alpha] = st["krylov_iters_total"]
+    assert m[1e-4] < m[1.0], m
+
+
+def test_alpha_shifted_solve_uses_scaled_shifts(pd):
+    """The plan's shifted systems are ((1 - alpha^{1/l} omega^k) I + tau K) (Algorithm 3)."""
+    P = W.random_tridiag_problem(40, 16, seed=7)
+    alpha = 1e-2
+    pi, gamma, d = R.alpha_quantities(P.nt, alpha)
+    op = R.operator(P)
+    Rhs = R.dft_time(P.G)[: P.nt // 2 + 1]
+    with pd.Plan.from_problem(P, precision="fp64", alpha=alpha, device=dev()) as plan:
+        Y, _ = plan.shifted_solve(torch.from_numpy(np.ascontiguousarray(Rhs)).to(dev()))
+    Yref = np.stack([op.shifted_solve(1.0 - pi[k], P.tau, Rhs[k]) for k in range(P.nt // 2 + 1)])
+    assert R.rel_err(Y.cpu().numpy(), Yref) <= 1e-12
