@@ -26,6 +26,49 @@ __global__ void k_refine_decide(double *scal, int *flags, RefineCtl r, int use_h
   if (threadIdx.x == 0 && blockIdx.x == 0) refine_decide(scal, flags, r, use_handle, h);
 }
 
+// Batched plans: block b sums the per-column squares of problem b's n_x columns
+// (fixed order), and the last block to finish (counter; no block waits) takes the
+// refinement decision over all problems.
+__global__ void __launch_bounds__(256) k_member_decide(const double *__restrict__ colsum, int nxm,
+                                                       const int *__restrict__ nxb, int nmem, double *d2,
+                                                       double *ref2, double *prev, int *mex, int *counter, double *scal,
+                                                       int *flags, RefineCtl rc, int use_handle,
+                                                       cudaGraphConditionalHandle h) {
+  __shared__ double red[256];
+  const int b = blockIdx.x;
+  const int n = nxb[b];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += colsum[(int64_t)b * nxm + i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  __shared__ int last;
+  if (threadIdx.x == 0) {
+    d2[b] = red[0];
+    __threadfence();
+    last = atomicAdd(counter, 1) == nmem - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    *counter = 0;
+    refine_decide_members(scal, flags, rc, nmem, d2, ref2, prev, mex, use_handle, h);
+  }
+}
+
+void launch_member_decide(Ctx &c, const double *colsum, int nxm, const int *nxb, int nmem, double *d2, double *ref2,
+                          double *prev, int *mex, double *scal, int *flags, const RefineCtl &r, int use_handle,
+                          cudaGraphConditionalHandle h) {
+  int *counter = flags + F_C2RCNT;
+  c.launch("control", 0.0, [&] {
+    k_member_decide<<<nmem, 256, 0, c.stream>>>(colsum, nxm, nxb, nmem, d2, ref2, prev, mex, counter, scal, flags,
+                                                r, use_handle, h);
+  });
+}
+
 void launch_solve_reset(Ctx &c, double *scal, int *flags) {
   c.launch("control", 0.0, [&] { k_solve_reset<<<1, 32, 0, c.stream>>>(scal, flags); });
 }

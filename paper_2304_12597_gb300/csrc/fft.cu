@@ -137,7 +137,8 @@ __global__ void __launch_bounds__(256) k_fft_r2c_res(const double *__restrict__ 
                                                      const double *__restrict__ rxd,
                                                      const double *__restrict__ rxu,
                                                      const cpx<T> *__restrict__ tw, cpx<T> *__restrict__ S,
-                                                     int64_t lds, const T *__restrict__ rs) {
+                                                     int64_t lds, const T *__restrict__ rs,
+                                                     const int *__restrict__ mex, int mnx) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cpx<T> *buf = reinterpret_cast<cpx<T> *>(smraw);
   const int64_t x0 = (int64_t)blockIdx.x * TX;
@@ -151,6 +152,8 @@ __global__ void __launch_bounds__(256) k_fft_r2c_res(const double *__restrict__ 
   const double cd = live ? rxd[col] : 0.0;
   const double cu = (live && col + 1 < ncols) ? rxu[col] : 0.0;
   const int64_t ol = col > 0 ? -1 : 0, ou = col + 1 < ncols ? 1 : 0;  // in-range neighbour offsets
+  // batched plans: problem (col / mnx) scaled by 2^mex[problem] (exact)
+  const T msc = (mex && live) ? (T)ldexp(1.0, mex[col / mnx]) : T(1);
   T *col_buf = reinterpret_cast<T *>(buf + ((size_t)(c >> 1) << logn)) + (c & 1);
   constexpr int kB = kLoadBatch / 2;  // five FP64 loads per element
   for (int j0 = (int)threadIdx.x / TX; j0 < n; j0 += kB * ((int)blockDim.x / TX)) {
@@ -171,7 +174,7 @@ __global__ void __launch_bounds__(256) k_fft_r2c_res(const double *__restrict__ 
       const int j = j0 + q * ((int)blockDim.x / TX);
       if (j < n) {
         const double au = fma(cu, ur[q], fma(cl, ul[q], cd * uc[q]));
-        const T r = (T)((g[q] + um[q]) - au);
+        const T r = (T)((g[q] + um[q]) - au) * msc;
         col_buf[2 * bitrev(j, logn)] = rs ? r * rs[j] : r;
       }
     }
@@ -188,7 +191,8 @@ __global__ void __launch_bounds__(256) k_fft_c2r(const cpx<T> *__restrict__ S, i
                                                  int n, int logn, const cpx<T> *__restrict__ tw,
                                                  void *__restrict__ out, int64_t ldo, int mode,
                                                  double *__restrict__ norm_part, StepFinish fin,
-                                                 const T *__restrict__ rsi) {
+                                                 const T *__restrict__ rsi, double *__restrict__ colsum,
+                                                 const int *__restrict__ mex, int mnx) {
   extern __shared__ __align__(16) unsigned char smraw[];
   cpx<T> *buf = reinterpret_cast<cpx<T> *>(smraw);
   const int64_t x0 = (int64_t)blockIdx.x * TX;
@@ -223,7 +227,12 @@ __global__ void __launch_bounds__(256) k_fft_c2r(const cpx<T> *__restrict__ S, i
   }
   __syncthreads();
   fft_smem<T>(buf, n, logn, np, tw);
-  const T inv_n = T(1) / T(n);
+  T inv_n = T(1) / T(n);
+  if (mex) {  // batched plans: undo the problem's 2^mex scaling (every element a thread
+              // writes lies in column x0 + threadIdx.x % TX)
+    const int64_t c0 = x0 + (int64_t)(threadIdx.x % TX);
+    if (c0 < ncols) inv_n = (T)ldexp((double)inv_n, -mex[c0 / mnx]);
+  }
   float ss = 0.0f;  // a few dozen squares per thread; the stop rule needs a few digits
   const int tot2 = n * TX;
   for (int i0 = threadIdx.x; i0 < tot2; i0 += kLoadBatch * blockDim.x) {
@@ -256,6 +265,18 @@ __global__ void __launch_bounds__(256) k_fft_c2r(const cpx<T> *__restrict__ S, i
       }
       const float vf = (float)v;
       ss = fmaf(vf, vf, ss);
+    }
+  }
+  if (colsum) {
+    // per-column sums of squares: blockDim.x is a multiple of TX, so every element a
+    // thread wrote lies in column threadIdx.x % TX
+    __shared__ double cred[256];
+    cred[threadIdx.x] = (double)ss;
+    __syncthreads();
+    if ((int)threadIdx.x < TX) {
+      double t = 0.0;
+      for (int i = threadIdx.x; i < (int)blockDim.x; i += TX) t += cred[i];
+      if (x0 + threadIdx.x < ncols) colsum[x0 + threadIdx.x] = t;
     }
   }
   if (norm_part) {
@@ -415,7 +436,7 @@ void launch_fft_r2c(Ctx &c, const Tin *X, int64_t ldx, int64_t ncols, int n, con
 template <typename T>
 void launch_fft_r2c_residual(Ctx &c, const double *G, const double *U, int64_t ncols, int n, const double *rxl,
                              const double *rxd, const double *rxu, const cpx<T> *tw, cpx<T> *S, int64_t lds,
-                             const T *rs) {
+                             const T *rs, const int *mex, int mnx) {
   const int logn = ilog2(n);
   const int TX = pick_tx<T>(n, sizeof(T) == 8 ? 8 : 16, ncols, c.fft_cols);
   const size_t smem = (size_t)(TX / 2) * n * sizeof(cpx<T>);
@@ -425,7 +446,8 @@ void launch_fft_r2c_residual(Ctx &c, const double *G, const double *U, int64_t n
     PD_TX_DISPATCH(TX, {
       if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_fft_r2c_res<T, kTX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      k_fft_r2c_res<T, kTX><<<grid, 256, smem, c.stream>>>(G, U, ncols, n, logn, rxl, rxd, rxu, tw, S, lds, rs);
+      k_fft_r2c_res<T, kTX><<<grid, 256, smem, c.stream>>>(G, U, ncols, n, logn, rxl, rxd, rxu, tw, S, lds, rs, mex,
+                                                           mnx);
     })
   });
 }
@@ -433,7 +455,7 @@ void launch_fft_r2c_residual(Ctx &c, const double *G, const double *U, int64_t n
 template <typename T>
 void launch_fft_c2r(Ctx &c, const cpx<T> *S, int64_t lds, int64_t ncols, int n, const cpx<T> *tw,
                     void *out, int64_t ldo, int mode, double *norm_part, int *nparts, const StepFinish *finp,
-                    const T *rsi) {
+                    const T *rsi, double *colsum, const int *mex, int mnx) {
   StepFinish fin{};
   if (finp && norm_part) fin = *finp;
   const int logn = ilog2(n);
@@ -448,7 +470,7 @@ void launch_fft_c2r(Ctx &c, const cpx<T> *S, int64_t lds, int64_t ncols, int n, 
       if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_fft_c2r<T, kTX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       k_fft_c2r<T, kTX><<<grid, 256, smem, c.stream>>>(S, lds, ncols, n, logn, tw, out, ldo, mode, norm_part,
-                                                         fin, rsi);
+                                                         fin, rsi, colsum, mex, mnx);
     })
   });
 }
@@ -480,15 +502,17 @@ template void launch_fft_r2c<float, double>(Ctx &, const double *, int64_t, int6
 template void launch_fft_r2c<float, float>(Ctx &, const float *, int64_t, int64_t, int, const cpx<float> *,
                                            cpx<float> *, int64_t, const float *);
 template void launch_fft_c2r<double>(Ctx &, const cpx<double> *, int64_t, int64_t, int, const cpx<double> *,
-                                     void *, int64_t, int, double *, int *, const StepFinish *, const double *);
+                                     void *, int64_t, int, double *, int *, const StepFinish *, const double *,
+                                     double *, const int *, int);
 template void launch_fft_c2r<float>(Ctx &, const cpx<float> *, int64_t, int64_t, int, const cpx<float> *,
-                                    void *, int64_t, int, double *, int *, const StepFinish *, const float *);
+                                    void *, int64_t, int, double *, int *, const StepFinish *, const float *,
+                                    double *, const int *, int);
 template void launch_fft_r2c_residual<double>(Ctx &, const double *, const double *, int64_t, int, const double *,
                                               const double *, const double *, const cpx<double> *, cpx<double> *,
-                                              int64_t, const double *);
+                                              int64_t, const double *, const int *, int);
 template void launch_fft_r2c_residual<float>(Ctx &, const double *, const double *, int64_t, int, const double *,
                                              const double *, const double *, const cpx<float> *, cpx<float> *,
-                                             int64_t, const float *);
+                                             int64_t, const float *, const int *, int);
 template void launch_dst_y<double, double, double>(Ctx &, const double *, double *, int64_t, int64_t, int64_t,
                                                    const cpx<double> *, int);
 template void launch_dst_y<double, float, float>(Ctx &, const double *, float *, int64_t, int64_t, int64_t,

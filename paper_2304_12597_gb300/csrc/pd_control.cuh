@@ -80,4 +80,73 @@ __device__ __forceinline__ void refine_decide(double *scal, int *flags, const Re
   if (use_handle) cudaGraphSetConditional(h, stop ? 0u : 1u);
 }
 
+// Batched plans: the same rule per problem.  d2[b] = ||delta_s||^2 of problem b,
+// ref2[b] its ||delta_0||^2 (set at s = 0), prev[b] its previous relative update.
+// Refinement stops when every problem meets the predicted-error rule (a problem with
+// a zero first solve is done), or when any problem stops contracting (then it has
+// converged if every problem's update is at the rounding floor).  The recorded
+// update of the sweep is the largest over the problems.  mex[b] receives the power of
+// two that scales problem b's residual in the next sweep, 2^-round(log2 ||delta_s||):
+// the problems' right-hand sides stay comparable in the shared Krylov space, so one
+// problem's correction is not lost below another's.
+__device__ __forceinline__ void refine_decide_members(double *scal, int *flags, const RefineCtl &r, int nmem,
+                                                      const double *d2, double *ref2, double *prev, int *mex,
+                                                      int use_handle, cudaGraphConditionalHandle h) {
+  const int s = flags[F_SWEEP];
+  bool nonfinite = flags[F_NONFIN] != 0, all_conv = true, any_stall = false, all_floor = true;
+  double relmax = 0.0, d2sum = 0.0;
+  for (int b = 0; b < nmem; ++b) {
+    const double d = d2[b];
+    d2sum += d;
+    if (!isfinite(d)) nonfinite = true;
+    if (s == 0) ref2[b] = d;
+    const double rf = ref2[b];
+    const double rel = rf > 0.0 ? sqrt(d / rf) : 0.0;
+    if (rf > 0.0) {
+      relmax = fmax(relmax, rel);
+      const double rho = prev[b] > 0.0 ? rel / prev[b] : 0.0;
+      const bool floor_b = s > 1 && rho > 0.5;  // no longer contracting: rounding floor
+      const bool conv_b =
+          s > 0 && ((s >= 2 && rho * rel <= r.refine_tol && rel <= 1e-7) || rel <= 1e-15 || (floor_b && rel <= 1e-10));
+      if (!conv_b) all_conv = false;
+      if (!conv_b && floor_b) any_stall = true;  // stuck above the floor
+      if (rel > 1e-10) all_floor = false;
+    }
+    prev[b] = rel;
+    int e = 0;
+    if (d > 0.0 && isfinite(d)) {
+      int e2;
+      frexp(d, &e2);  // ||delta_s|| ~ 2^(e2/2)
+      e = max(-100, min(100, -(e2 / 2)));
+    }
+    mex[b] = e;
+  }
+  const double beta = scal[S_BETA];
+  if (s < 16) {
+    flags[F_SWM + s] = flags[F_M];
+    scal[S_SWRES + s] = beta > 0.0 ? scal[S_RES] / beta : 0.0;
+    scal[S_SWUPD + s] = s == 0 ? 1.0 : relmax;
+    scal[S_SWBETA + s] = beta;
+  }
+  flags[F_MTOT] += flags[F_M];
+  bool conv = false, stop = false;
+  if (nonfinite) {
+    flags[F_NONFIN] = 1;
+    stop = true;
+  } else if (all_conv && (s > 0 || relmax == 0.0)) {
+    conv = stop = true;
+  } else if (any_stall) {
+    conv = all_floor;
+    stop = true;
+  }
+  if (!stop && s + 1 > r.max_refine) stop = true;
+  scal[S_D2] = d2sum;
+  scal[S_UPD] = relmax;
+  scal[S_PREV] = relmax;
+  flags[F_SWEEP] = s + 1;
+  flags[F_RCONV] = conv ? 1 : 0;
+  flags[F_RSTOP] = stop ? 1 : 0;
+  if (use_handle) cudaGraphSetConditional(h, stop ? 0u : 1u);
+}
+
 }  // namespace pd

@@ -107,10 +107,12 @@ void launch_fft_r2c(Ctx &c, const Tin *X, int64_t ldx, int64_t ncols, int n, con
                     cpx<T> *S, int64_t lds, const T *rs = nullptr);
 // Forward DFT along time of the FP64 all-at-once residual
 // R = G - [(I + tau K) U - U Sigma_1^T] (1D), computed on load: R is never stored.
+// mex/mnx (batched plans): column c is scaled by 2^mex[c / mnx], undone by the inverse.
 template <typename T>
 void launch_fft_r2c_residual(Ctx &c, const double *G, const double *U, int64_t ncols, int n,
                              const double *rxl, const double *rxd, const double *rxu, const cpx<T> *tw,
-                             cpx<T> *S, int64_t lds, const T *rs = nullptr);
+                             cpx<T> *S, int64_t lds, const T *rs = nullptr, const int *mex = nullptr,
+                             int mnx = 1);
 // Optional epilogue of the inverse DFT: the last CTA to finish sums the per-CTA
 // squares into scal[S_D2] and runs the refinement decision.
 struct StepFinish {
@@ -124,11 +126,13 @@ struct StepFinish {
 };
 // Inverse DFT along time of a half spectrum; mode 0: store double, 1: add into
 // double, 2: store float.  norm_part (may be null) receives per-CTA sums of the
-// squared output values; *nparts = number of CTAs.
+// squared output values; *nparts = number of CTAs.  colsum (may be null) receives
+// per-column sums of the squared output values (ncols doubles).
 template <typename T>
 void launch_fft_c2r(Ctx &c, const cpx<T> *S, int64_t lds, int64_t ncols, int n, const cpx<T> *tw,
                     void *out, int64_t ldo, int mode, double *norm_part, int *nparts,
-                    const StepFinish *fin = nullptr, const T *rsi = nullptr);
+                    const StepFinish *fin = nullptr, const T *rsi = nullptr, double *colsum = nullptr,
+                    const int *mex = nullptr, int mnx = 1);
 // Orthonormal DST-I along the middle axis of (nt, ny, nx); ny + 1 a power of two.
 // mode 0: store, 1: add into (double output only).
 template <typename Tin, typename Tout, typename T>
@@ -194,6 +198,11 @@ void launch_zsum(Ctx &c, int nf, int64_t n, const cpx<T> *H, int64_t ldh, const 
 void launch_batch_normalize(Ctx &c, const double *G, double *Gs, int64_t nt, int batch, int nxm, int nc,
                             double *part, int *ex);
 void launch_batch_unscale(Ctx &c, double *U, int64_t nt, int batch, int nxm, const int *ex, const int *nxb);
+// Batched plans: per-problem ||delta||^2 from the inverse DFT's per-column sums, then the
+// refinement decision over all problems (control.cu).
+void launch_member_decide(Ctx &c, const double *colsum, int nxm, const int *nxb, int nmem, double *d2, double *ref2,
+                          double *prev, int *mex, double *scal, int *flags, const RefineCtl &r, int use_handle,
+                          cudaGraphConditionalHandle h);
 
 void launch_acc_reduce(Ctx &c, const PintGeom &g, const double *acc_part, double *out,
                        const int *skip_flag);

@@ -170,6 +170,9 @@ struct pd_plan {
   double *bpart = nullptr;      // norm partials (batch * bnc)
   int *bex = nullptr;           // per-problem power-of-two scale exponents
   int *bnx = nullptr;           // rows of each problem
+  double *colsum = nullptr;     // per-column ||delta||^2 of the last solve
+  double *md2 = nullptr, *mref2 = nullptr, *mprev = nullptr;  // per-problem refinement state
+  int *mex = nullptr;  // per-problem residual scaling 2^mex of the next refinement sweep
   pd::PintGeom geom{};
   int blas_grid = 1, k5_grid = 1;
   int64_t lds = 0;
@@ -427,6 +430,11 @@ size_t layout(pd_plan *p, unsigned char *base) {
     p->bpart = A.take<double>((size_t)p->batch * p->bnc);
     p->bex = A.take<int>(p->batch);
     p->bnx = A.take<int>(p->batch);
+    p->colsum = A.take<double>(nbar);
+    p->md2 = A.take<double>(p->batch);
+    p->mref2 = A.take<double>(p->batch);
+    p->mprev = A.take<double>(p->batch);
+    p->mex = A.take<int>(p->batch);
   }
   if (p->host_io) {
     p->G_stage = A.take<double>((size_t)nt * nbar);
@@ -668,6 +676,9 @@ pd::KrylovCtl krylov_ctl(pd_plan *p, int kind) {
     k.eps = std::max(p->eps, 1e-8);
     k.stall_floor = 1.0;
     k.win = 2;
+  } else if (p->batch > 1) {  // mixed batches: the shared space needs a few more steps
+    if (kind == 1) k.eps = std::max(p->eps, 1e-4);
+    k.win = 2;
   }
   k.maxit = p->maxit;
   return k;
@@ -714,7 +725,7 @@ pd_status emit_pre(pd_plan *p, int kind, const double *G, double *U, int use_han
   } else {
     if (p->dim == 1) {  // the FP64 residual is formed while the DFT loads its tiles
       pd::launch_fft_r2c_residual<T>(c, G, U, p->nbar, nt, p->rxl, p->rxd, p->rxu, time_tw<T>(p), S, p->lds,
-                                     row_scale<T>(p, false));
+                                     row_scale<T>(p, false), p->batch > 1 ? p->mex : nullptr, (int)p->nxm);
     } else {
       pd::launch_residual<T>(c, G, U, res, p->nt, p->ny, p->nx, p->rxl, p->rxd, p->rxu, p->ryl, p->ryd, p->ryu);
       pd::launch_dst_y<T, T, T>(c, res, tmp, p->nt, p->ny, p->nx, dst_tw<T>(p), 0);
@@ -795,7 +806,13 @@ pd_status emit_post(pd_plan *p, int kind, double *U, int use_handle, cudaGraphCo
   fin.use_handle = use_handle;
   fin.h = hr;
   int nparts = 0;
-  if (p->dim == 1) {
+  if (p->batch > 1) {  // per-problem norms and decision (every problem must converge)
+    pd::launch_fft_c2r<T>(c, S, p->lds, p->nbar, nt, time_tw<T>(p), U, p->nbar, kind == 0 ? 0 : 1, nullptr,
+                          &nparts, nullptr, row_scale<T>(p, true), p->colsum, kind == 0 ? nullptr : p->mex,
+                          (int)p->nxm);
+    pd::launch_member_decide(c, p->colsum, (int)p->nxm, p->bnx, p->batch, p->md2, p->mref2, p->mprev, p->mex,
+                             p->scal, p->flags, refine_ctl(p), use_handle, hr);
+  } else if (p->dim == 1) {
     pd::launch_fft_c2r<T>(c, S, p->lds, p->nbar, nt, time_tw<T>(p), U, p->nbar, kind == 0 ? 0 : 1, p->norm_part,
                           &nparts, &fin, row_scale<T>(p, true));
   } else {

@@ -12,6 +12,10 @@ the workspace, G and U of every batch in flight plus the cached plans.
 
 Plans are cached per (shape, capacity) and worker; a new batch swaps its operators in
 with paradiag_set_operator, so the workspace and the captured CUDA graph are reused.
+Requests span diffusion coefficients down to 1e-4, where Algorithm 1's inner system is
+ill-conditioned (kappa <= 1 + 1/(tau lambda_min), Theorem 3.1); the service therefore
+runs Algorithm 3 with alpha = 1e-4 by default (mixed precision refines away the
+kappa(F D_alpha) loss).
 All arithmetic of a solve runs in the library's kernels; this module only schedules.
 """
 from __future__ import annotations
@@ -147,7 +151,7 @@ class Server:
     """Runs a request stream in real time on one GPU with `workers` CUDA streams."""
 
     def __init__(self, device=None, precision="mixed", workers=2, budget_bytes=40 << 30, max_batch=32,
-                 keep_results=False, plan_cache_bytes=None):
+                 keep_results=False, plan_cache_bytes=None, alpha=1e-4):
         import torch
 
         from . import _binding as B
@@ -156,6 +160,7 @@ class Server:
         self.torch, self.B, self.Plan = torch, B, Plan
         self.device = torch.device(device) if device is not None else torch.device("cuda", 0)
         self.precision = precision
+        self.alpha = alpha  # Algorithm 3: slow diffusion (nu ~ 1e-4) needs it (Sec. 4)
         self.workers = workers
         self.keep_results = keep_results
         self.plan_cache_bytes = plan_cache_bytes if plan_cache_bytes is not None else budget_bytes // 2
@@ -206,14 +211,14 @@ class Server:
         if batch.key.dim == 1:
             probs = [S.request_problem_operator_only(r, batch.key.nx) for r in batch.requests]
             probs += [S.empty_slot(batch.key.nt) for _ in range(batch.cap - len(probs))]
-            plan = self.Plan.from_problems(probs, nx=batch.key.nx, precision=self.precision, device=self.device,
-                                           stream=stream)
+            plan = self.Plan.from_problems(probs, nx=batch.key.nx, precision=self.precision, alpha=self.alpha,
+                                           device=self.device, stream=stream)
             nb = batch.cap * batch.key.nx
         else:
             kx, ky = S.operator(r0)
             plan = self.Plan(dim=2, nx=r0.nx, ny=r0.ny, nt=r0.nt, tau=r0.tau, k_lo=kx[0], k_diag=kx[1],
                              k_up=kx[2], k_lo_y=ky[0], k_diag_y=ky[1], k_up_y=ky[2], precision=self.precision,
-                             device=self.device, stream=stream)
+                             alpha=self.alpha, device=self.device, stream=stream)
             nb = r0.nx * r0.ny
         with torch.cuda.stream(stream):
             G = torch.zeros((batch.key.nt, nb), dtype=torch.float64, device=self.device)

@@ -42,7 +42,7 @@ def test_served_results_equal_alone_and_oracle(pd):
     dev = torch.device("cuda:0")
     for r in reqs:
         P = S.request_problem(r)
-        with pd.Plan.from_problem(P, precision="mixed", device=dev) as plan:
+        with pd.Plan.from_problem(P, precision="mixed", alpha=server.alpha, device=dev) as plan:
             U, _ = plan.solve(S.rhs_device(r, torch, dev).contiguous())
             alone = U[-1].cpu().numpy()
         assert _rel(r.result, alone) <= 2 * TOL, (r.rid, r.kind, r.batch)
