@@ -85,7 +85,8 @@ typedef struct pd_desc {
                             at any level in its refinement sweeps; over 3 iterations in PD_FP64
                             once ||r|| <= 1e-6 ||b||) */
   int32_t q;             /* residual check period of Algorithm 2; only q = 1 is built */
-  int32_t max_refine;    /* refinement sweeps after the first solve (0 = 8).  PD_MIXED always
+  int32_t max_refine;    /* refinement sweeps after the first solve (0 = 8, 16 for batches,
+                            which stop only when every problem has converged).  PD_MIXED always
                             refines; PD_FP64 refines when Algorithm 2 stopped short of
                             eps_krylov (stall or maxit) or when eps_krylov > 1e-10, since the
                             residual of eq. (2) left by an inexact x_m is exactly -r_m in the

@@ -14,6 +14,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -37,6 +38,14 @@ pd_status fail(pd_status s, const char *fmt, ...) {
 }
 
 bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// Serialises the heavy host-side paths of different plans (plan building, graph
+// capture and instantiation, operator upload, destruction) so that callers may drive
+// plans from several threads; solves themselves run concurrently.
+std::recursive_mutex &host_mutex() {  // recursive: a failing paradiag_plan destroys its plan
+  static std::recursive_mutex m;
+  return m;
+}
 
 // Bump allocator over the workspace; the same sequence of take() calls is run
 // once for sizing (base == nullptr) and once for assignment.
@@ -320,7 +329,8 @@ void fill_geometry(pd_plan *p, const pd_desc *d) {
   // Algorithm 3 loses up to kappa(F D_alpha) per solve, so FP64 refinement sweeps
   // with a few Krylov steps each beat one tight solve
   if (p->refined64 && !(d->eps_krylov > 0)) p->eps = 1e-5;
-  p->max_refine = d->max_refine ? d->max_refine : 8;
+  // batches stop only when their slowest problem has converged: allow more sweeps
+  p->max_refine = d->max_refine ? d->max_refine : (d->batch > 1 ? 16 : 8);
   p->refine_tol = d->refine_tol > 0 ? d->refine_tol : (d->precision == PD_FP64 ? 1e-14 : 1e-11);
   p->host_io = d->host_io;
   p->nblk = p->batch > 1 ? p->batch : (int)p->ny;
@@ -968,6 +978,7 @@ pd_status solve_graph(pd_plan *p, const double *G, double *U, bool *used) {
   *used = false;
   if (p->graph_failed || p->ctx.timing) return PD_OK;
   if (!p->gexec || p->g_G != G || p->g_U != U) {
+    std::lock_guard<std::recursive_mutex> lk(host_mutex());  // one capture at a time in the process
     drop_graph(p);
     const int64_t l0 = p->ctx.launches;
     cudaGraph_t g = nullptr;
@@ -1058,6 +1069,7 @@ pd_status paradiag_workspace_size(const pd_desc *desc, size_t *bytes) {
 }
 
 pd_status paradiag_plan(const pd_desc *desc, void *workspace, size_t workspace_bytes, pd_plan **out) {
+  std::lock_guard<std::recursive_mutex> lk(host_mutex());
   g_err.clear();
   pd_status st = validate(desc);
   if (st != PD_OK) return st;
@@ -1174,11 +1186,13 @@ pd_status paradiag_set_operator(pd_plan *p, const pd_desc *desc) {
     p->tau = desc->tau;
   }
   if (p->ctx.stream) cudaStreamSynchronize(p->ctx.stream);  // no solve may still read the old operator
+  std::lock_guard<std::recursive_mutex> lk(host_mutex());
   return upload_operator(p, desc);
 }
 
 pd_status paradiag_destroy(pd_plan *p) {
   if (!p) return PD_OK;
+  std::lock_guard<std::recursive_mutex> lk(host_mutex());
   if (p->ctx.stream) cudaStreamSynchronize(p->ctx.stream);
   drop_graph(p);
   for (int i = 0; i < 3; ++i)

@@ -195,8 +195,6 @@ class Server:
 
     # -- one batch ----------------------------------------------------------------------
     def _slot(self, cache: OrderedDict, batch: Batch, stream):
-        import workloads.serving as S
-
         torch = self.torch
         k = (batch.key, batch.cap)
         if k in cache:
@@ -207,6 +205,19 @@ class Server:
         while cache and sum(s.bytes for s in cache.values()) + batch.bytes > share:
             _, old = cache.popitem(last=False)
             old.plan.close()
+        # the plan's workspace is allocated on the worker's stream, the stream its
+        # kernels run on, so the allocator reuses it in stream order
+        with torch.cuda.stream(stream):
+            plan, nb = self._new_plan(batch, stream)
+            G = torch.zeros((batch.key.nt, nb), dtype=torch.float64, device=self.device)
+            U = torch.empty_like(G)
+        slot = _Slot(plan, G, U, batch.bytes)
+        cache[k] = slot
+        return slot, True
+
+    def _new_plan(self, batch: Batch, stream):
+        import workloads.serving as S
+
         r0 = batch.requests[0]
         if batch.key.dim == 1:
             probs = [S.request_problem_operator_only(r, batch.key.nx) for r in batch.requests]
@@ -220,12 +231,7 @@ class Server:
                              k_up=kx[2], k_lo_y=ky[0], k_diag_y=ky[1], k_up_y=ky[2], precision=self.precision,
                              alpha=self.alpha, device=self.device, stream=stream)
             nb = r0.nx * r0.ny
-        with torch.cuda.stream(stream):
-            G = torch.zeros((batch.key.nt, nb), dtype=torch.float64, device=self.device)
-            U = torch.empty_like(G)
-        slot = _Slot(plan, G, U, batch.bytes)
-        cache[k] = slot
-        return slot, True
+        return plan, nb
 
     def _run(self, batch: Batch, cache: OrderedDict, stream) -> None:
         import workloads.serving as S
