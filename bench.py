@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="config2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve", action="store_true",
+                    help="full serving sweep: 10,000 requests at each of 100, 300, 1000, 3000, 5000 arrivals/s "
+                         "(the default run measures 1000 requests at 300 and 3000 arrivals/s)")
     ap.add_argument("--profile", type=int, default=0, metavar="N",
                     help="only run N mixed solves of the workload with host-driven loops, one launch per "
                          "kernel node, for a profiler's launch list (prints no benchmark line)")
@@ -319,6 +322,30 @@ def run_ours(args):
     fp.close()
     fp64_value = unknowns * nfp * world / (fp64_ms / 1e3)
 
+    # ---- batched: independent problems of the workload's shape in one plan ----------
+    batched = None
+    if P.dim == 1:
+        import workloads as W
+
+        B = 32
+        probs = [W.by_name(args.workload, seed=sd) for sd in range(B)]
+        bp = Plan.from_problems(probs, precision="mixed", device=device)
+        Gb = torch.from_numpy(bp.stack([Q.G for Q in probs])).to(device)
+        Ub = torch.empty_like(Gb)
+        for _ in range(3):
+            bp.solve(Gb, Ub)
+        nb = max(3, min(args.steps, 20))
+        tsb, lb, stb = time_steps(bp, Gb, Ub, nb, stream, flush, torch)
+        b_ms = max_over_ranks(sum(tsb), world, device)
+        parts = bp.unstack(Ub.cpu().numpy(), [Q.nx for Q in probs])
+        batched = {"batch": B, "problems": f"{B} x {args.workload} (seeds 0..{B - 1})",
+                   "value": unknowns * B * nb * world / (b_ms / 1e3), "unit": UNIT, "ms_per_step": b_ms / nb,
+                   "gpu_launches_per_step": lb / nb, "refine_sweeps": stb["refine_sweeps"],
+                   "krylov_iters_total": stb["krylov_iters_total"],
+                   "l2": "flushed before every timed step; 268 MB per array, above L2"}
+        bp.close()
+        del Gb, Ub
+
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -341,9 +368,18 @@ def run_ours(args):
         "roofline": roofline,
         "kernels": kernel_table,
         "clocks": clocks,
+        "batched": batched,
     }
+    if world == 1:
+        out["serving"] = serve_bench(args, device)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"], out["parity"] = cpu_baseline(P, args.workload, {"mixed": U_mixed, "fp64": U_fp64})
+        if batched is not None:  # first and last problem of the batch against the oracle
+            from oracle import reference as R
+
+            last = W.by_name(args.workload, seed=batched["batch"] - 1)
+            batched["parity"] = {"problem_0": R.rel_err(parts[0], R.be_solve_refined(P)),
+                                 "problem_last": R.rel_err(parts[-1], R.be_solve_refined(last)), "tolerance": 1e-10}
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
@@ -413,6 +449,48 @@ def run_reference(args):
     }
     print(json.dumps(out))
     return 0
+
+
+def serve_bench(args, device):
+    """The solver service on a seeded Poisson request stream (1D heat, 1D advection-diffusion
+    and 2D heat requests of random size, n_t and nu): p50/p99 latency and solves/s per
+    arrival rate, plus the largest relative difference between a sample of served results and
+    the same requests solved alone."""
+    import numpy as np
+    import torch
+
+    import workloads.serving as S
+    from paper_2304_12597_gb300 import Plan
+    from paper_2304_12597_gb300.serve import Server
+
+    rates, n = ((100, 300, 1000, 3000, 5000), 10000) if args.serve else ((300, 3000), 1000)
+    out = {"requests_per_rate": n, "workers": 3, "max_batch": 32, "alpha": 1e-4, "precision": "mixed",
+           "warm": "each rate after a 300-request warm-up stream through the same server (module loading, "
+                   "per-thread state, plan caches)",
+           "mix": "1D heat / 1D advection-diffusion n_x in 127..4095, 2D heat side in {63,127,255}, "
+                  "n_t in {32..2048}, nu log-uniform [1e-4, 1], Poisson arrivals", "rates": []}
+    for rate in rates:
+        reqs = S.request_stream(n, float(rate), seed=int(rate))
+        server = Server(device=device, workers=3, max_batch=32, budget_bytes=60 << 30, keep_results=True)
+        server.warmup()
+        stats = server.run(reqs)
+        server.close()
+        summ = stats.summary()
+        summ["rate"] = rate
+        # served results against the same request solved alone (a sample)
+        worst = 0.0
+        for r in reqs[:: max(1, n // 8)]:
+            if r.error:
+                continue
+            P = S.request_problem(r)
+            with Plan.from_problem(P, precision="mixed", alpha=server.alpha, device=device) as plan:
+                U, _ = plan.solve(S.rhs_device(r, torch, device).contiguous())
+                alone = U[-1].cpu().numpy()
+            worst = max(worst, float(np.linalg.norm(r.result - alone) / max(np.linalg.norm(alone), 1e-300)))
+        summ["max_rel_diff_alone_vs_served_sample"] = worst
+        out["rates"].append(summ)
+        torch.cuda.empty_cache()
+    return out
 
 
 def run_profile(args):

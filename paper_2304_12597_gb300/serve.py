@@ -167,6 +167,22 @@ class Server:
         self._ws_cache: dict = {}
         self.sched = Scheduler(budget_bytes, self._workspace_bytes, max_batch)
         self.cv = threading.Condition()
+        self._workers: list = []  # (stream, plan cache) per worker, kept across runs
+
+    def close(self) -> None:
+        """Release every cached plan."""
+        for _, cache in self._workers:
+            for s in cache.values():
+                s.plan.close()
+            cache.clear()
+
+    def warmup(self, n: int = 300, seed: int = 987654321) -> None:
+        """Serve a throw-away stream (all arriving at once) so that kernel modules are
+        loaded, per-thread library state exists and the plan caches hold the common
+        shapes before a measured run."""
+        import workloads.serving as S
+
+        self.run(S.request_stream(n, 1e6, seed=seed))
 
     # -- sizes ------------------------------------------------------------------------
     def _desc_for(self, key: BatchKey, cap: int):
@@ -289,15 +305,12 @@ class Server:
                     self.sched.add(r)
                     lock.notify_all()
 
-        def worker():
-            stream = torch.cuda.Stream(device=self.device)
-            cache: OrderedDict = OrderedDict()
+        def worker(w):
+            stream, cache = self._workers[w]
             while True:
                 with lock:
                     while True:
                         if done_count[0] >= len(reqs):
-                            for s in cache.values():
-                                s.plan.close()
                             return
                         batch = self.sched.next_batch()
                         if batch is not None:
@@ -313,7 +326,10 @@ class Server:
                     stats.batches += 1
                     lock.notify_all()
 
-        threads = [threading.Thread(target=feeder)] + [threading.Thread(target=worker) for _ in range(self.workers)]
+        if not self._workers:
+            self._workers = [(torch.cuda.Stream(device=self.device), OrderedDict()) for _ in range(self.workers)]
+        threads = [threading.Thread(target=feeder)] + [threading.Thread(target=worker, args=(w,))
+                                                        for w in range(self.workers)]
         for t in threads:
             t.start()
         for t in threads:

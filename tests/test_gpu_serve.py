@@ -36,6 +36,7 @@ def test_served_results_equal_alone_and_oracle(pd):
     reqs = S.request_stream(24, 1e5, seed=11, nx_range=(127, 700), nt_choices=(32, 64))
     server = Server(device="cuda:0", workers=2, max_batch=8, keep_results=True, budget_bytes=8 << 30)
     stats = server.run(reqs)
+    server.close()
     summ = stats.summary()
     assert summ["failed"] == 0, [r.error for r in reqs if r.error]
     assert max(r.batch for r in reqs) > 1  # some requests shared a batch
