@@ -117,6 +117,9 @@ typedef struct pd_desc {
                                 > 1 = cooperative launch of 64-thread CTAs (<= SM count) */
   int32_t tune_cap_ctas;     /* CTAs of the capacitance-term kernel, 1 .. 1024 */
   int32_t tune_fft_cols;     /* columns per CTA of the time FFTs: 2, 4, 8 or 16 */
+  int32_t tune_no_pdl;       /* nonzero: launch kernels without programmatic dependent launch
+                                (by default a kernel may be scheduled while its predecessor
+                                drains; it waits for it before reading anything) */
   /* Batching (1D only): `batch` independent problems with the same nt are solved
    * together as one block-diagonal problem (their DFTs, shifted solves, Krylov space
    * and refinement are shared; the blocks never couple).  Problem b occupies slot b:

@@ -13,6 +13,7 @@ namespace pd {
 // part[b * nc + c] = sum over time rows t = c, c + nc, ... of slot b's squares.
 __global__ void __launch_bounds__(256) k_batch_sumsq(const double *__restrict__ X, int64_t nt, int64_t ld, int nxm,
                                                      int nc, double *__restrict__ part) {
+  grid_dep_wait();
   const int c = blockIdx.x, b = blockIdx.y;
   double s = 0.0;
   for (int64_t t = c; t < nt; t += nc) {
@@ -33,6 +34,7 @@ __global__ void __launch_bounds__(256) k_batch_sumsq(const double *__restrict__ 
 // ex[b] = -round(log2 ||slot b||_F): slot b is multiplied by 2^ex[b] before the solve
 // and its solution by 2^-ex[b] after it (0 for an all-zero or non-finite slot).
 __global__ void k_batch_exponents(int batch, int nc, const double *__restrict__ part, int *__restrict__ ex) {
+  grid_dep_wait();
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= batch) return;
   double s = 0.0;
@@ -63,6 +65,7 @@ __device__ __forceinline__ double pow2_scale(double x, int k) {
 __global__ void __launch_bounds__(256) k_batch_scale(const double *X, double *Y, int ld, int nxm,
                                                      const int *__restrict__ ex, int sign,
                                                      const int *__restrict__ nxb) {
+  grid_dep_wait();
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= ld) return;
   const int b = j / nxm;
@@ -74,19 +77,21 @@ void launch_batch_normalize(Ctx &c, const double *G, double *Gs, int64_t nt, int
                             double *part, int *ex) {
   const int64_t ld = (int64_t)batch * nxm;
   c.launch("batch_scale", (double)nt * ld * 8.0, [&] {
-    k_batch_sumsq<<<dim3(nc, batch), 256, 0, c.stream>>>(G, nt, ld, nxm, nc, part);
+    pdl_launch(c.pdl, k_batch_sumsq, dim3(nc, batch), dim3(256), 0, c.stream, G, nt, ld, nxm, nc, part);
   });
-  c.launch("batch_scale", 0.0, [&] { k_batch_exponents<<<(batch + 127) / 128, 128, 0, c.stream>>>(batch, nc, part, ex); });
+  c.launch("batch_scale", 0.0, [&] { pdl_launch(c.pdl, k_batch_exponents, dim3((batch + 127) / 128), dim3(128), 0, c.stream, batch, nc, part, ex); });
   const dim3 grid((unsigned)((ld + 255) / 256), (unsigned)nt);
   c.launch("batch_scale", (double)nt * ld * 16.0,
-           [&] { k_batch_scale<<<grid, 256, 0, c.stream>>>(G, Gs, (int)ld, nxm, ex, 1, nullptr); });
+           [&] { pdl_launch(c.pdl, k_batch_scale, grid, dim3(256), 0, c.stream, G, Gs, (int)ld, nxm, (const int *)ex, 1,
+                                  (const int *)nullptr); });
 }
 
 void launch_batch_unscale(Ctx &c, double *U, int64_t nt, int batch, int nxm, const int *ex, const int *nxb) {
   const int64_t ld = (int64_t)batch * nxm;
   const dim3 grid((unsigned)((ld + 255) / 256), (unsigned)nt);
   c.launch("batch_scale", (double)nt * ld * 16.0,
-           [&] { k_batch_scale<<<grid, 256, 0, c.stream>>>(U, U, (int)ld, nxm, ex, -1, nxb); });
+           [&] { pdl_launch(c.pdl, k_batch_scale, grid, dim3(256), 0, c.stream, (const double *)U, U, (int)ld, nxm, ex, -1,
+                                  nxb); });
 }
 
 }  // namespace pd

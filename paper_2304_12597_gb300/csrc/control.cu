@@ -10,6 +10,7 @@
 namespace pd {
 
 __global__ void k_solve_reset(double *scal, int *flags) {
+  grid_dep_wait();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   for (int i = 0; i < kFlagWords; ++i) flags[i] = 0;
   for (int i = 0; i < kScalWords; ++i) scal[i] = 0.0;
@@ -18,11 +19,13 @@ __global__ void k_solve_reset(double *scal, int *flags) {
 
 __global__ void k_krylov_decide(double *scal, int *flags, KrylovCtl k, int use_handle,
                                 cudaGraphConditionalHandle h) {
+  grid_dep_wait();
   if (threadIdx.x == 0 && blockIdx.x == 0) krylov_decide(scal, flags, k, use_handle, h);
 }
 
 __global__ void k_refine_decide(double *scal, int *flags, RefineCtl r, int use_handle,
                                 cudaGraphConditionalHandle h) {
+  grid_dep_wait();
   if (threadIdx.x == 0 && blockIdx.x == 0) refine_decide(scal, flags, r, use_handle, h);
 }
 
@@ -34,6 +37,7 @@ __global__ void __launch_bounds__(256) k_member_decide(const double *__restrict_
                                                        double *ref2, double *prev, int *mex, int *counter, double *scal,
                                                        int *flags, RefineCtl rc, int use_handle,
                                                        cudaGraphConditionalHandle h) {
+  grid_dep_wait();
   __shared__ double red[256];
   const int b = blockIdx.x;
   const int n = nxb[b];
@@ -64,23 +68,24 @@ void launch_member_decide(Ctx &c, const double *colsum, int nxm, const int *nxb,
                           cudaGraphConditionalHandle h) {
   int *counter = flags + F_C2RCNT;
   c.launch("control", 0.0, [&] {
-    k_member_decide<<<nmem, 256, 0, c.stream>>>(colsum, nxm, nxb, nmem, d2, ref2, prev, mex, counter, scal, flags,
+    pdl_launch(c.pdl, k_member_decide, dim3(nmem), dim3(256), 0, c.stream, colsum, nxm, nxb, nmem, d2, ref2, prev, mex,
+               counter, scal, flags,
                                                 r, use_handle, h);
   });
 }
 
 void launch_solve_reset(Ctx &c, double *scal, int *flags) {
-  c.launch("control", 0.0, [&] { k_solve_reset<<<1, 32, 0, c.stream>>>(scal, flags); });
+  c.launch("control", 0.0, [&] { pdl_launch(c.pdl, k_solve_reset, dim3(1), dim3(32), 0, c.stream, scal, flags); });
 }
 
 void launch_krylov_decide(Ctx &c, double *scal, int *flags, const KrylovCtl &k, int use_handle,
                           cudaGraphConditionalHandle h) {
-  c.launch("control", 0.0, [&] { k_krylov_decide<<<1, 32, 0, c.stream>>>(scal, flags, k, use_handle, h); });
+  c.launch("control", 0.0, [&] { pdl_launch(c.pdl, k_krylov_decide, dim3(1), dim3(32), 0, c.stream, scal, flags, k, use_handle, h); });
 }
 
 void launch_refine_decide(Ctx &c, double *scal, int *flags, const RefineCtl &r, int use_handle,
                           cudaGraphConditionalHandle h) {
-  c.launch("control", 0.0, [&] { k_refine_decide<<<1, 32, 0, c.stream>>>(scal, flags, r, use_handle, h); });
+  c.launch("control", 0.0, [&] { pdl_launch(c.pdl, k_refine_decide, dim3(1), dim3(32), 0, c.stream, scal, flags, r, use_handle, h); });
 }
 
 }  // namespace pd

@@ -98,6 +98,7 @@ template <typename T, typename Tin, int TX>
 __global__ void __launch_bounds__(256) k_fft_r2c(const Tin *__restrict__ X, int64_t ldx, int64_t ncols,
                                                  int n, int logn, const cpx<T> *__restrict__ tw,
                                                  cpx<T> *__restrict__ S, int64_t lds, const T *__restrict__ rs) {
+  grid_dep_wait();
   extern __shared__ __align__(16) unsigned char smraw[];
   cpx<T> *buf = reinterpret_cast<cpx<T> *>(smraw);
   const int64_t x0 = (int64_t)blockIdx.x * TX;
@@ -139,6 +140,7 @@ __global__ void __launch_bounds__(256) k_fft_r2c_res(const double *__restrict__ 
                                                      const cpx<T> *__restrict__ tw, cpx<T> *__restrict__ S,
                                                      int64_t lds, const T *__restrict__ rs,
                                                      const int *__restrict__ mex, int mnx) {
+  grid_dep_wait();
   extern __shared__ __align__(16) unsigned char smraw[];
   cpx<T> *buf = reinterpret_cast<cpx<T> *>(smraw);
   const int64_t x0 = (int64_t)blockIdx.x * TX;
@@ -193,6 +195,7 @@ __global__ void __launch_bounds__(256) k_fft_c2r(const cpx<T> *__restrict__ S, i
                                                  double *__restrict__ norm_part, StepFinish fin,
                                                  const T *__restrict__ rsi, double *__restrict__ colsum,
                                                  const int *__restrict__ mex, int mnx) {
+  grid_dep_wait();
   extern __shared__ __align__(16) unsigned char smraw[];
   cpx<T> *buf = reinterpret_cast<cpx<T> *>(smraw);
   const int64_t x0 = (int64_t)blockIdx.x * TX;
@@ -320,6 +323,7 @@ template <typename Tin, typename Tout, typename T, int TX>
 __global__ void __launch_bounds__(256) k_dst_y(const Tin *__restrict__ X, Tout *__restrict__ Y, int64_t ny,
                                                int64_t nx, int N, int logN,
                                                const cpx<T> *__restrict__ tw, T scale, int mode) {
+  grid_dep_wait();
   extern __shared__ __align__(16) unsigned char smraw[];
   cpx<T> *buf = reinterpret_cast<cpx<T> *>(smraw);
   const int ntile = (int)((nx + TX - 1) / TX);
@@ -428,7 +432,8 @@ void launch_fft_r2c(Ctx &c, const Tin *X, int64_t ldx, int64_t ncols, int n, con
     PD_TX_DISPATCH(TX, {
       if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_fft_r2c<T, Tin, kTX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      k_fft_r2c<T, Tin, kTX><<<grid, 256, smem, c.stream>>>(X, ldx, ncols, n, logn, tw, S, lds, rs);
+      pdl_launch(c.pdl, k_fft_r2c<T, Tin, kTX>, dim3(grid), dim3(256), smem, c.stream, X, ldx, ncols, n, logn, tw, S, lds,
+                 rs);
     })
   });
 }
@@ -446,7 +451,8 @@ void launch_fft_r2c_residual(Ctx &c, const double *G, const double *U, int64_t n
     PD_TX_DISPATCH(TX, {
       if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_fft_r2c_res<T, kTX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      k_fft_r2c_res<T, kTX><<<grid, 256, smem, c.stream>>>(G, U, ncols, n, logn, rxl, rxd, rxu, tw, S, lds, rs, mex,
+      pdl_launch(c.pdl, k_fft_r2c_res<T, kTX>, dim3(grid), dim3(256), smem, c.stream, G, U, ncols, n, logn, rxl, rxd, rxu,
+                 tw, S, lds, rs, mex,
                                                            mnx);
     })
   });
@@ -469,7 +475,8 @@ void launch_fft_c2r(Ctx &c, const cpx<T> *S, int64_t lds, int64_t ncols, int n, 
     PD_TX_DISPATCH(TX, {
       if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_fft_c2r<T, kTX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      k_fft_c2r<T, kTX><<<grid, 256, smem, c.stream>>>(S, lds, ncols, n, logn, tw, out, ldo, mode, norm_part,
+      pdl_launch(c.pdl, k_fft_c2r<T, kTX>, dim3(grid), dim3(256), smem, c.stream, S, lds, ncols, n, logn, tw, out, ldo, mode,
+                 norm_part,
                                                          fin, rsi, colsum, mex, mnx);
     })
   });
@@ -490,7 +497,8 @@ void launch_dst_y(Ctx &c, const Tin *X, Tout *Y, int64_t nt, int64_t ny, int64_t
     PD_TX_DISPATCH(TX, {
       if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_dst_y<Tin, Tout, T, kTX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      k_dst_y<Tin, Tout, T, kTX><<<(unsigned)grid, 256, smem, c.stream>>>(X, Y, ny, nx, N, logN, tw, scale, mode);
+      pdl_launch(c.pdl, k_dst_y<Tin, Tout, T, kTX>, dim3((unsigned)grid), dim3(256), smem, c.stream, X, Y, ny, nx, N, logN,
+                 tw, scale, mode);
     })
   });
 }

@@ -123,6 +123,7 @@ __global__ void __launch_bounds__(COOP ? kBlas : kBlasSingle) k_init_v0_coop(con
                                                         double *V, float *Vf, double *scal, int *flags,
                                                         int use_handle, cudaGraphConditionalHandle h, double *T,
                                                         int nT) {
+  grid_dep_wait();
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nT; i += gridDim.x * blockDim.x) T[i] = 0.0;
   __shared__ double red[kRedWords];
   __shared__ double c[34];
@@ -166,6 +167,7 @@ __global__ void __launch_bounds__(COOP ? kBlas : kBlasSingle) k_arnoldi_coop(int
                                                         const double *__restrict__ kup, double *V, float *Vf,
                                                         double *w, double *T, int ldT, double *part, int ld,
                                                         double *scal, int *flags) {
+  grid_dep_wait();
   __shared__ double red[kRedWords];
   __shared__ double c[34];
   const int m = flags[F_M] + 1;  // the step computed here produces v_m
@@ -221,6 +223,7 @@ __global__ void __launch_bounds__(COOP ? kBlas : kBlasSingle) k_project_coop(int
                                                         double tau, double *part, int ld, double *scal,
                                                         int *flags, KrylovCtl kc, int use_handle,
                                                         cudaGraphConditionalHandle h) {
+  grid_dep_wait();
   __shared__ double red[kRedWords];
   __shared__ double c[34];
   const int m = flags[F_M] + 1;
@@ -318,6 +321,7 @@ __global__ void __launch_bounds__(kK5Warps * 32) k_capacitance_terms(
     int nf, int maxit, double tau, const double *__restrict__ T, const double2 *__restrict__ shift,
     const double2 *__restrict__ wg, const double2 *__restrict__ gpart, int nblk, double *msys_part,
     double2 *srow, const double *scal, int *flags, double2 *omega, double *y) {
+  grid_dep_wait();
   extern __shared__ __align__(16) unsigned char smraw[];
   const int m = flags[F_M] + 1;
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -430,6 +434,7 @@ __device__ void capacitance_solve_cta(int nf, int m, int nparts, const double *m
 // x = sum_q y_q V[q] (and its binary32 copy xf when requested)
 __global__ void k_xm(int n, const int *flags, const double *__restrict__ V, const double *__restrict__ y, double *x,
                      float *xf) {
+  grid_dep_wait();
   __shared__ double ys[33];
   const int m = flags[F_M];  // 0 when b == 0: x = 0
   if (threadIdx.x < m) ys[threadIdx.x] = y[threadIdx.x];
@@ -444,6 +449,7 @@ __global__ void k_xm(int n, const int *flags, const double *__restrict__ V, cons
 
 // *dst = sum of part[0..nparts) (one warp, fixed order)
 __global__ void k_sumsq_final(const double *part, int nparts, double *dst) {
+  grid_dep_wait();
   double s = 0.0;
   for (int i = threadIdx.x; i < nparts; i += 32) s += part[i];
   s = warp_sum(s);
@@ -459,6 +465,7 @@ __global__ void k_residual(const double *__restrict__ G, const double *__restric
                            int nb, int nx, const double *__restrict__ rxl, const double *__restrict__ rxd,
                            const double *__restrict__ rxu, const double *__restrict__ ryl,
                            const double *__restrict__ ryd, const double *__restrict__ ryu, int ny) {
+  grid_dep_wait();
   const int j = blockIdx.x * blockDim.x + threadIdx.x;  // spatial index
   const int64_t t = blockIdx.y;                         // time step
   if (j >= nb) return;
@@ -487,7 +494,18 @@ __global__ void k_residual(const double *__restrict__ G, const double *__restric
 static void coop_launch(Ctx &c, const char *fam, double bytes, const void *fn_single, const void *fn_coop, int grid,
                         void **args) {
   if (grid <= 1) {
-    c.launch(fam, bytes, [&] { cudaLaunchKernel(fn_single, dim3(1), dim3(kBlasSingle), args, 0, c.stream); });
+    c.launch(fam, bytes, [&] {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(1);
+      cfg.blockDim = dim3(kBlasSingle);
+      cfg.stream = c.stream;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      attr[0].val.programmaticStreamSerializationAllowed = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = c.pdl ? 1 : 0;
+      cudaLaunchKernelExC(&cfg, fn_single, args);
+    });
     return;
   }
   const void *fn = fn_coop;
@@ -539,7 +557,8 @@ void launch_capacitance(Ctx &c, KrylovBufs &k, int nf, double tau, const double2
   const size_t smem = k5a_warp_bytes(k.maxit) * kK5Warps;  // sized for the largest m
   cudaFuncSetAttribute(k_capacitance_terms, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   c.launch("capacitance", (double)nf * nblk * 16, [&] {
-    k_capacitance_terms<<<k5_grid, kK5Warps * 32, smem, c.stream>>>(nf, k.maxit, tau, k.T, shift, wg, gpart, nblk,
+    pdl_launch(c.pdl, k_capacitance_terms, dim3(k5_grid), dim3(kK5Warps * 32), smem, c.stream, nf, k.maxit, tau,
+               (const double *)k.T, shift, wg, gpart, nblk,
                                                                      msys_part, srow, k.scal, k.flags, omega, y);
   });
 }
@@ -561,11 +580,12 @@ void launch_project_resnorm(Ctx &c, KrylovBufs &k, const double *z, double tau, 
 
 void launch_xm(Ctx &c, KrylovBufs &k, const double *y, double *x, float *xf) {
   c.launch("krylov_xm", (double)k.n * 8.0 * 2,
-           [&] { k_xm<<<k.grid, kBlas, 0, c.stream>>>(k.n, k.flags, k.V, y, x, xf); });
+           [&] { pdl_launch(c.pdl, k_xm, dim3(k.grid), dim3(kBlas), 0, c.stream, k.n, (const int *)k.flags, (const double *)k.V,
+                                y, x, xf); });
 }
 
 void launch_sumsq(Ctx &c, const double *part, int nparts, double *dst) {
-  c.launch("krylov_sumsq", 0.0, [&] { k_sumsq_final<<<1, 32, 0, c.stream>>>(part, nparts, dst); });
+  c.launch("krylov_sumsq", 0.0, [&] { pdl_launch(c.pdl, k_sumsq_final, dim3(1), dim3(32), 0, c.stream, part, nparts, dst); });
 }
 
 template <typename Tout>
@@ -577,10 +597,12 @@ void launch_residual(Ctx &c, const double *G, const double *U, Tout *R, int64_t 
   c.launch(sizeof(Tout) == 8 ? "residual_f64_to_f64" : "residual_f64_to_f32",
            (double)nt * nb * (8 + 8 + sizeof(Tout)), [&] {
              if (ryl)
-               k_residual<Tout, true><<<grid, 256, 0, c.stream>>>(G, U, R, nb, (int)nx, rxl, rxd, rxu, ryl, ryd, ryu,
+               pdl_launch(c.pdl, k_residual<Tout, true>, grid, dim3(256), 0, c.stream, G, U, R, nb, (int)nx, rxl, rxd, rxu, ryl,
+                          ryd, ryu,
                                                                   (int)ny);
              else
-               k_residual<Tout, false><<<grid, 256, 0, c.stream>>>(G, U, R, nb, (int)nx, rxl, rxd, rxu, ryl, ryd,
+               pdl_launch(c.pdl, k_residual<Tout, false>, grid, dim3(256), 0, c.stream, G, U, R, nb, (int)nx, rxl, rxd, rxu, ryl,
+                          ryd,
                                                                    ryu, (int)ny);
            });
 }

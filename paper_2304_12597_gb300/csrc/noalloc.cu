@@ -44,6 +44,7 @@ void *g_scratch_ptr[128] = {};  // device address of g_scratch, per device ordin
 __global__ void k_noalloc_coeffs(int nf, int64_t nt, int64_t n, double tau, const double *__restrict__ lo,
                                  const double *__restrict__ diag, const double *__restrict__ up, double2 *shift,
                                  double2 *wg, double *tlo, double *tdiag, double *tup) {
+  pd::grid_dep_wait();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < nf) {
     double s, c;
@@ -115,7 +116,8 @@ extern "C" pd_status paradiag_smw_rhs_noalloc(int64_t nt, int64_t n, double tau,
   c.stream = static_cast<cudaStream_t>(stream);
   const int64_t cover = nf > n ? nf : n;
   c.launch("noalloc_coeffs", 0.0, [&] {
-    k_noalloc_coeffs<<<(unsigned)((cover + 255) / 256), 256, 0, c.stream>>>(nf, nt, n, tau, k_lo, k_diag, k_up,
+    pd::pdl_launch(c.pdl, k_noalloc_coeffs, dim3((unsigned)((cover + 255) / 256)), dim3(256), 0, c.stream, nf, nt, n, tau,
+                 k_lo, k_diag, k_up,
                                                                             shift, wg, tlo, tdiag, tup);
   });
   pd::PintGeom g = pd::pint_geometry(nf, 1, (int)n, 4 * pd::sm_count(), 16);

@@ -83,6 +83,11 @@ __device__ __forceinline__ void team_sync(int P, int team_in_cta) {
   }
 }
 
+// Programmatic dependent launch: every kernel of this library opens with this wait,
+// so a kernel scheduled early (while its predecessor in the stream drains) reads
+// nothing before the predecessor has completed; without such a launch it returns at once.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ int bitrev(int j, int logn) {
   return logn == 0 ? 0 : (int)(__brev((unsigned)j) >> (32 - logn));
 }

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <functional>
+#include <utility>
 #include <string>
 #include <vector>
 
@@ -48,8 +49,28 @@ enum ScalIndex {
 
 // Launch context: the stream every kernel is ordered on, a launch counter, and
 // optional per-launch timing with CUDA events recorded on that same stream.
+// Launch `kern` on stream s, with programmatic stream serialization when pdl is set:
+// the kernel may then be scheduled while its predecessor drains; it waits for it in
+// grid_dep_wait() before reading anything.
+template <typename... KArgs, typename... Args>
+cudaError_t pdl_launch(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
 struct Ctx {
   cudaStream_t stream = nullptr;
+  bool pdl = true;   // programmatic dependent launch between consecutive kernels
   int fft_cols = 0;  // columns per CTA of the time FFTs (0 = choose per launch)
   bool timing = false;
   int64_t launches = 0;

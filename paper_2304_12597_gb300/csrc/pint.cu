@@ -69,6 +69,7 @@ __device__ __forceinline__ void coef(const PintArgs<T> &a, const T *cs, int cs_s
 // registers per thread, which the FP64 variants use without spilling).
 template <typename T, int M, int MAXT>
 __global__ void __launch_bounds__(MAXT) k_pint(PintGeom g, PintArgs<T> a, size_t team_bytes) {
+  grid_dep_wait();
   if (a.skip_flag && *a.skip_flag) return;
   const int P = g.P;
   const int tic = threadIdx.x / P;
@@ -416,6 +417,7 @@ __device__ __forceinline__ double colsum_finish(double v, double (*sm)[kColW + 1
 __global__ void __launch_bounds__(kColW * kRowG) k_acc_reduce(int nblk, int blen, int R,
                                                               const double *__restrict__ part,
                                                               double *__restrict__ out, const int *skip_flag) {
+  grid_dep_wait();
   if (skip_flag && *skip_flag) return;
   __shared__ double sm[kRowG][kColW + 1];
   const int64_t n = (int64_t)nblk * blen;
@@ -451,6 +453,7 @@ template <typename T>
 __global__ void __launch_bounds__(kColW * kRowG) k_zsum(int nf, int64_t n, const cpx<T> *__restrict__ H, int64_t ldh,
                                                         const double2 *__restrict__ omega, double *__restrict__ z,
                                                         const int *skip_flag) {
+  grid_dep_wait();
   if (skip_flag && *skip_flag) return;
   __shared__ double sm[kRowG][kColW + 1];
   extern __shared__ __align__(16) unsigned char om_raw[];
@@ -491,7 +494,7 @@ void launch_zsum(Ctx &c, int nf, int64_t n, const cpx<T> *H, int64_t ldh, const 
   const size_t smem = (size_t)nf * sizeof(cpx<T>);
   c.launch("zsum", (double)nf * n * sizeof(cpx<T>) + n * 8.0, [&] {
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_zsum<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_zsum<T><<<grid, dim3(kColW, kRowG), smem, c.stream>>>(nf, n, H, ldh, omega, z, skip_flag);
+    pdl_launch(c.pdl, k_zsum<T>, dim3(grid), dim3(kColW, kRowG), smem, c.stream, nf, n, H, ldh, omega, z, skip_flag);
   });
 }
 template void launch_zsum<double>(Ctx &, int, int64_t, const cpx<double> *, int64_t, const double2 *, double *,
@@ -555,7 +558,7 @@ static void launch_pint_m(Ctx &c, const PintGeom &g, const PintArgs<T> &a) {
   const bool dots = a.mcount ? a.want_dots != 0 : a.mdots > 0;
   const char *fam = sizeof(T) == 8 ? (dots ? "pint_dots_f64" : (a.Y ? "pint_store_f64" : "pint_acc_f64"))
                                    : (dots ? "pint_dots_f32" : (a.Y ? "pint_store_f32" : "pint_acc_f32"));
-  c.launch(fam, bytes, [&] { kern<<<grid, threads, smem, c.stream>>>(g, a, tb); });
+  c.launch(fam, bytes, [&] { pdl_launch(c.pdl, kern, dim3(grid), dim3(threads), smem, c.stream, g, a, tb); });
 }
 
 template <typename T>
@@ -573,7 +576,8 @@ void launch_acc_reduce(Ctx &c, const PintGeom &g, const double *acc_part, double
   const int64_t n = (int64_t)g.nblk * g.blen;
   const int grid = (int)((n + kColW - 1) / kColW);
   c.launch("acc_reduce", (double)n * g.acc_rows * 8.0 + n * 8.0, [&] {
-    k_acc_reduce<<<grid, dim3(kColW, kRowG), 0, c.stream>>>(g.nblk, g.blen, g.acc_rows, acc_part, out, skip_flag);
+    pdl_launch(c.pdl, k_acc_reduce, dim3(grid), dim3(kColW, kRowG), 0, c.stream, g.nblk, g.blen, g.acc_rows, acc_part,
+               out, skip_flag);
   });
 }
 

@@ -357,6 +357,7 @@ void fill_geometry(pd_plan *p, const pd_desc *d) {
   if (d->tune_krylov_ctas) p->blas_grid = std::min(d->tune_krylov_ctas, sms);
   if (d->tune_cap_ctas) p->k5_grid = d->tune_cap_ctas;
   p->ctx.fft_cols = d->tune_fft_cols;
+  p->ctx.pdl = d->tune_no_pdl == 0;
 }
 
 // Assign (or size) every device buffer.
