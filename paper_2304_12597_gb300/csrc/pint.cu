@@ -345,9 +345,10 @@ __global__ void __launch_bounds__(MAXT) k_pint(PintGeom g, PintArgs<T> a, size_t
           px += vv[i] * y.x;
           py += vv[i] * y.y;
         }
-        double sx = warp_sum((double)px);
-        double sy = warp_sum((double)py);
-        if (l == 0) red[w * mdots + q] = make_double2(sx, sy);
+        // warp sums in the compute type (binary32 in the mixed path, where h_k itself is
+        // binary32); the per-warp partials are added in FP64
+        const T sx = warp_sum(px), sy = warp_sum(py);
+        if (l == 0) red[w * mdots + q] = make_double2((double)sx, (double)sy);
       }
       team_sync(P, tic);
       for (int q = t; q < mdots; q += P) {
