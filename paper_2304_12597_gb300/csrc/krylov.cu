@@ -75,10 +75,10 @@ __device__ __forceinline__ void phase_sync() {
     __syncthreads();
 }
 
-// part_row[q] = sum over this CTA's slice of V[q][j] x[j] (q < m); part_row[m] = ||x||^2.
-// kRedQ sums per pass over x.
+// part_row[q] = sum over this CTA's slice of V[q][j] x[j] (q < m); part_row[m] = ||x||^2
+// (into the shared c_local instead when it is given).  kRedQ sums per pass over x.
 __device__ void cta_dots(int n, int m, const double *__restrict__ V, const double *__restrict__ x,
-                         double *part_row, double *red) {
+                         double *part_row, double *red, double *c_local = nullptr) {
   __shared__ double out[kRedQ];
   for (int q0 = 0; q0 <= m; q0 += kRedQ) {
     const int nq = min(kRedQ, m + 1 - q0);
@@ -94,7 +94,7 @@ __device__ void cta_dots(int n, int m, const double *__restrict__ V, const doubl
       }
     }
     block_sums(s, nq, red, out);
-    if ((int)threadIdx.x < nq) part_row[q0 + threadIdx.x] = out[threadIdx.x];
+    if ((int)threadIdx.x < nq) (c_local ? c_local : part_row)[q0 + threadIdx.x] = out[threadIdx.x];
   }
 }
 
@@ -106,6 +106,36 @@ __device__ void cta_gather(const double *panel, int ld, int nparts, int m, doubl
     c[threadIdx.x] = s;
   }
   __syncthreads();
+}
+
+// c[q] = V[q] . x over the grid (q < m), c[m] = ||x||^2; shared c, valid in every thread
+// on return.  Cooperative grids combine per-CTA partials through `panel` after a grid
+// barrier; a single CTA keeps the totals in shared memory.
+template <bool COOP>
+__device__ void grid_dots(int n, int m, const double *__restrict__ V, const double *__restrict__ x, double *panel,
+                          int ld, double *red, double *c) {
+  if constexpr (COOP) {
+    cta_dots(n, m, V, x, panel + (size_t)blockIdx.x * ld, red);
+    cg::this_grid().sync();
+    cta_gather(panel, ld, gridDim.x, m, c);
+  } else {
+    cta_dots(n, m, V, x, nullptr, red, c);
+    __syncthreads();
+  }
+}
+
+// The grid total of one value per thread (valid in every thread).
+template <bool COOP>
+__device__ double grid_sum(double s, double *panel, int ld, double *red, double *c) {
+  s = block_sum(s, red);
+  if constexpr (COOP) {
+    if (threadIdx.x == 0) panel[(size_t)blockIdx.x * ld] = s;
+    cg::this_grid().sync();
+    cta_gather(panel, ld, gridDim.x, 0, c);
+    return c[0];
+  } else {
+    return s;
+  }
 }
 
 // x -= sum_{q<m} c[q] V[q] over this CTA's slice.
@@ -129,11 +159,7 @@ __global__ void __launch_bounds__(COOP ? kBlas : kBlasSingle) k_init_v0_coop(con
   __shared__ double c[34];
   double s = 0.0;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) s += b[j] * b[j];
-  s = block_sum(s, red);
-  if (threadIdx.x == 0) part[blockIdx.x * ld] = s;
-  phase_sync<COOP>();
-  cta_gather(part, ld, gridDim.x, 0, c);
-  const double beta = sqrt(c[0]);
+  const double beta = sqrt(grid_sum<COOP>(s, part, ld, red, c));
   const bool zero = !(beta > 0.0);
   const double ib = zero ? 0.0 : 1.0 / beta;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
@@ -180,25 +206,18 @@ __global__ void __launch_bounds__(COOP ? kBlas : kBlasSingle) k_arnoldi_coop(int
     if (j + 1 < n) x += kup[j] * v[j + 1];
     w[j] = x;
   }
-  cta_dots(n, m, V, w, pa + (size_t)blockIdx.x * ld, red);
-  phase_sync<COOP>();
-  cta_gather(pa, ld, G, m, c);
+  grid_dots<COOP>(n, m, V, w, pa, ld, red, c);
   const double knorm = sqrt(c[m]);
   if (blockIdx.x == 0 && (int)threadIdx.x < m) T[(int64_t)threadIdx.x * ldT + (m - 1)] = c[threadIdx.x];
   cta_axpy(n, m, V, w, c);
-  cta_dots(n, m, V, w, pb + (size_t)blockIdx.x * ld, red);
-  phase_sync<COOP>();
-  cta_gather(pb, ld, G, m, c);
+  __syncthreads();  // c is rewritten next
+  grid_dots<COOP>(n, m, V, w, pb, ld, red, c);
   if (blockIdx.x == 0 && (int)threadIdx.x < m) T[(int64_t)threadIdx.x * ldT + (m - 1)] += c[threadIdx.x];
   cta_axpy(n, m, V, w, c);
+  __syncthreads();
   double s = 0.0;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) s += w[j] * w[j];
-  s = block_sum(s, red);
-  if (threadIdx.x == 0) pc[(size_t)blockIdx.x * ld] = s;
-  phase_sync<COOP>();
-  __syncthreads();
-  cta_gather(pc, ld, G, 0, c);
-  const double t = sqrt(c[0]);
+  const double t = sqrt(grid_sum<COOP>(s, pc, ld, red, c));
   const bool bd = !(t > 1e-14 * knorm);
   const double it = bd ? 0.0 : 1.0 / t;
   double *vm = V + (int64_t)m * n;
@@ -229,26 +248,18 @@ __global__ void __launch_bounds__(COOP ? kBlas : kBlasSingle) k_project_coop(int
   const int m = flags[F_M] + 1;
   const int G = gridDim.x;
   double *pa = part, *pb = part + (size_t)G * ld, *pc = part + (size_t)2 * G * ld;
-  cta_dots(n, m, V, z, pa + (size_t)blockIdx.x * ld, red);
-  phase_sync<COOP>();
-  cta_gather(pa, ld, G, m, c);
+  grid_dots<COOP>(n, m, V, z, pa, ld, red, c);
   cta_axpy(n, m, V, z, c);
-  cta_dots(n, m, V, z, pb + (size_t)blockIdx.x * ld, red);
-  phase_sync<COOP>();
-  cta_gather(pb, ld, G, m, c);
+  __syncthreads();  // c is rewritten next
+  grid_dots<COOP>(n, m, V, z, pb, ld, red, c);
   cta_axpy(n, m, V, z, c);
+  __syncthreads();
   double s = 0.0;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) s += z[j] * z[j];
-  s = block_sum(s, red);
-  if (threadIdx.x == 0) pc[(size_t)blockIdx.x * ld] = s;
-  phase_sync<COOP>();
-  if (blockIdx.x == 0) {
-    __syncthreads();
-    cta_gather(pc, ld, G, 0, c);
-    if (threadIdx.x == 0) {
-      scal[S_RES] = flags[F_BREAK] ? 0.0 : fabs(tau * scal[S_T]) * sqrt(c[0]);
-      krylov_decide(scal, flags, kc, use_handle, h);
-    }
+  const double zz = grid_sum<COOP>(s, pc, ld, red, c);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    scal[S_RES] = flags[F_BREAK] ? 0.0 : fabs(tau * scal[S_T]) * sqrt(zz);
+    krylov_decide(scal, flags, kc, use_handle, h);
   }
 }
 
