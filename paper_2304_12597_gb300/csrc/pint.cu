@@ -388,19 +388,22 @@ __global__ void __launch_bounds__(MAXT) k_pint(PintGeom g, PintArgs<T> a, size_t
   }
 }
 
-// Column sums out[j] = sum_r X[r][j] in a fixed order.  A CTA owns kColW adjacent
-// columns (one 64-byte row segment) and kRowG row groups; group y sums rows
-// y, y + kRowG, ... with kColB loads in flight, then the groups' partials are added
-// in a fixed two-level order, so the result does not depend on scheduling.
-constexpr int kColW = 8, kRowG = 64, kColB = 8;
+// Column sums out[j] = sum_r X[r][j] in a fixed order.  A CTA of CW x RG = 512 threads
+// owns CW adjacent columns and RG row groups; group y sums rows y, y + RG, ... with
+// kColB loads in flight, then the groups' partials are added in a fixed two-level order,
+// so the result does not depend on scheduling.  Many rows: 8 columns (one 64-byte
+// segment) x 64 groups; few rows (<= 256): 32 columns x 16 groups, so that each thread
+// still has several rows and the grid is not thousands of tiny CTAs.
+constexpr int kColB = 8;
 
-__device__ __forceinline__ double colsum_finish(double v, double (*sm)[kColW + 1]) {
+template <int CW, int RG>
+__device__ __forceinline__ double colsum_finish(double v, double (*sm)[CW + 1]) {
   sm[threadIdx.y][threadIdx.x] = v;
   __syncthreads();
   double t = 0.0;
   if (threadIdx.y < 8) {
 #pragma unroll
-    for (int i = 0; i < kRowG / 8; ++i) t += sm[threadIdx.y * (kRowG / 8) + i][threadIdx.x];
+    for (int i = 0; i < RG / 8; ++i) t += sm[threadIdx.y * (RG / 8) + i][threadIdx.x];
   }
   __syncthreads();
   if (threadIdx.y < 8) sm[threadIdx.y][threadIdx.x] = t;
@@ -415,14 +418,14 @@ __device__ __forceinline__ double colsum_finish(double v, double (*sm)[kColW + 1
 
 // out[j] = sum_r part[(blk*R + r)*blen + e], j = blk*blen + e (the per-team partial
 // rows of b or z).
-__global__ void __launch_bounds__(kColW * kRowG) k_acc_reduce(int nblk, int blen, int R,
-                                                              const double *__restrict__ part,
-                                                              double *__restrict__ out, const int *skip_flag) {
+template <int CW, int RG>
+__global__ void __launch_bounds__(CW * RG) k_acc_reduce(int nblk, int blen, int R, const double *__restrict__ part,
+                                                        double *__restrict__ out, const int *skip_flag) {
   grid_dep_wait();
   if (skip_flag && *skip_flag) return;
-  __shared__ double sm[kRowG][kColW + 1];
+  __shared__ double sm[RG][CW + 1];
   const int64_t n = (int64_t)nblk * blen;
-  const int64_t j = (int64_t)blockIdx.x * kColW + threadIdx.x;
+  const int64_t j = (int64_t)blockIdx.x * CW + threadIdx.x;
   double acc[kColB];
 #pragma unroll
   for (int u = 0; u < kColB; ++u) acc[u] = 0.0;
@@ -430,11 +433,11 @@ __global__ void __launch_bounds__(kColW * kRowG) k_acc_reduce(int nblk, int blen
     const int blk = (int)(j / blen);
     const int e = (int)(j - (int64_t)blk * blen);
     const double *base = part + (int64_t)blk * R * blen + e;  // R = partial rows per block
-    for (int r0 = threadIdx.y; r0 < R; r0 += kRowG * kColB) {
+    for (int r0 = threadIdx.y; r0 < R; r0 += RG * kColB) {
       double v[kColB];
 #pragma unroll
       for (int u = 0; u < kColB; ++u) {
-        const int r = r0 + u * kRowG;
+        const int r = r0 + u * RG;
         v[u] = r < R ? base[(int64_t)r * blen] : 0.0;
       }
 #pragma unroll
@@ -444,39 +447,39 @@ __global__ void __launch_bounds__(kColW * kRowG) k_acc_reduce(int nblk, int blen
   double tot = 0.0;
 #pragma unroll
   for (int u = 0; u < kColB; ++u) tot += acc[u];
-  tot = colsum_finish(tot, sm);
+  tot = colsum_finish<CW, RG>(tot, sm);
   if (threadIdx.y == 0 && j < n) out[j] = tot;
 }
 
 // z[j] = sum_k Re(omega_k H[k][j]) over the stored h_k (eq. 13's z), j < n.  In
 // binary32 the weights are rounded once into shared memory (nf * 8 bytes).
-template <typename T>
-__global__ void __launch_bounds__(kColW * kRowG) k_zsum(int nf, int64_t n, const cpx<T> *__restrict__ H, int64_t ldh,
-                                                        const double2 *__restrict__ omega, double *__restrict__ z,
-                                                        const int *skip_flag) {
+template <typename T, int CW, int RG>
+__global__ void __launch_bounds__(CW * RG) k_zsum(int nf, int64_t n, const cpx<T> *__restrict__ H, int64_t ldh,
+                                                  const double2 *__restrict__ omega, double *__restrict__ z,
+                                                  const int *skip_flag) {
   grid_dep_wait();
   if (skip_flag && *skip_flag) return;
-  __shared__ double sm[kRowG][kColW + 1];
+  __shared__ double sm[RG][CW + 1];
   extern __shared__ __align__(16) unsigned char om_raw[];
   cpx<T> *om = reinterpret_cast<cpx<T> *>(om_raw);
-  const int tid = threadIdx.y * kColW + threadIdx.x;
-  for (int k = tid; k < nf; k += kColW * kRowG) om[k] = mk<T>((T)omega[k].x, (T)omega[k].y);
+  const int tid = threadIdx.y * CW + threadIdx.x;
+  for (int k = tid; k < nf; k += CW * RG) om[k] = mk<T>((T)omega[k].x, (T)omega[k].y);
   __syncthreads();
-  const int64_t j = (int64_t)blockIdx.x * kColW + threadIdx.x;
+  const int64_t j = (int64_t)blockIdx.x * CW + threadIdx.x;
   T acc[kColB];
 #pragma unroll
   for (int u = 0; u < kColB; ++u) acc[u] = T(0);
   if (j < n) {
-    for (int k0 = threadIdx.y; k0 < nf; k0 += kRowG * kColB) {
+    for (int k0 = threadIdx.y; k0 < nf; k0 += RG * kColB) {
       cpx<T> h[kColB];
 #pragma unroll
       for (int u = 0; u < kColB; ++u) {
-        const int k = k0 + u * kRowG;
+        const int k = k0 + u * RG;
         h[u] = k < nf ? H[(int64_t)k * ldh + j] : mk<T>(T(0), T(0));
       }
 #pragma unroll
       for (int u = 0; u < kColB; ++u) {
-        const int k = k0 + u * kRowG;
+        const int k = k0 + u * RG;
         if (k < nf) acc[u] += om[k].x * h[u].x - om[k].y * h[u].y;
       }
     }
@@ -484,18 +487,26 @@ __global__ void __launch_bounds__(kColW * kRowG) k_zsum(int nf, int64_t n, const
   double tot = 0.0;
 #pragma unroll
   for (int u = 0; u < kColB; ++u) tot += (double)acc[u];
-  tot = colsum_finish(tot, sm);
+  tot = colsum_finish<CW, RG>(tot, sm);
   if (threadIdx.y == 0 && j < n) z[j] = tot;
 }
 
 template <typename T>
 void launch_zsum(Ctx &c, int nf, int64_t n, const cpx<T> *H, int64_t ldh, const double2 *omega, double *z,
                  const int *skip_flag) {
-  const int grid = (int)((n + kColW - 1) / kColW);
   const size_t smem = (size_t)nf * sizeof(cpx<T>);
   c.launch("zsum", (double)nf * n * sizeof(cpx<T>) + n * 8.0, [&] {
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k_zsum<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    pdl_launch(c.pdl, k_zsum<T>, dim3(grid), dim3(kColW, kRowG), smem, c.stream, nf, n, H, ldh, omega, z, skip_flag);
+    if (nf <= 256) {
+      const int grid = (int)((n + 31) / 32);
+      pdl_launch(c.pdl, k_zsum<T, 32, 16>, dim3(grid), dim3(32, 16), smem, c.stream, nf, n, H, ldh, omega, z,
+                 skip_flag);
+    } else {
+      const int grid = (int)((n + 7) / 8);
+      if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_zsum<T, 8, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      pdl_launch(c.pdl, k_zsum<T, 8, 64>, dim3(grid), dim3(8, 64), smem, c.stream, nf, n, H, ldh, omega, z,
+                 skip_flag);
+    }
   });
 }
 template void launch_zsum<double>(Ctx &, int, int64_t, const cpx<double> *, int64_t, const double2 *, double *,
@@ -575,10 +586,13 @@ void launch_pint(Ctx &c, const PintGeom &g, const PintArgs<T> &a) {
 
 void launch_acc_reduce(Ctx &c, const PintGeom &g, const double *acc_part, double *out, const int *skip_flag) {
   const int64_t n = (int64_t)g.nblk * g.blen;
-  const int grid = (int)((n + kColW - 1) / kColW);
   c.launch("acc_reduce", (double)n * g.acc_rows * 8.0 + n * 8.0, [&] {
-    pdl_launch(c.pdl, k_acc_reduce, dim3(grid), dim3(kColW, kRowG), 0, c.stream, g.nblk, g.blen, g.acc_rows, acc_part,
-               out, skip_flag);
+    if (g.acc_rows <= 256)
+      pdl_launch(c.pdl, k_acc_reduce<32, 16>, dim3((int)((n + 31) / 32)), dim3(32, 16), 0, c.stream, g.nblk, g.blen,
+                 g.acc_rows, acc_part, out, skip_flag);
+    else
+      pdl_launch(c.pdl, k_acc_reduce<8, 64>, dim3((int)((n + 7) / 8)), dim3(8, 64), 0, c.stream, g.nblk, g.blen,
+                 g.acc_rows, acc_part, out, skip_flag);
   });
 }
 

@@ -687,6 +687,9 @@ pd::KrylovCtl krylov_ctl(pd_plan *p, int kind) {
     k.eps = std::max(p->eps, 1e-8);
     k.stall_floor = 1.0;
     k.win = 2;
+  } else if (fp64 && kind == 1) {  // an FP64 refinement sweep only needs a contraction
+    k.stall_floor = 1.0;
+    k.win = 2;
   } else if (p->batch > 1) {  // mixed batches: the shared space needs a few more steps
     if (kind == 1) k.eps = std::max(p->eps, 1e-4);
     k.win = 2;
