@@ -20,168 +20,17 @@
 #include <algorithm>
 #include <cmath>
 
-#include <cooperative_groups.h>
-
-#include "pd_control.cuh"
-
-namespace cg = cooperative_groups;
+#include "pd_krylov.cuh"
 
 namespace pd {
 
-constexpr int kBlas = 64;  // small CTAs: FP64 reduction trees are short per SM
-
-constexpr int kBlasSingle = 512;  // threads of the one-CTA variants (short vectors)
-constexpr int kRedQ = 4;          // sums reduced side by side
-constexpr int kRedWords = kRedQ * kBlasSingle;
-
-// out[i] = sum over the CTA of s[i], i < nq <= kRedQ (shared `out`, valid for every
-// thread on return).  The partials go through shared memory and warp i adds column
-// i (also i + warps, ... when the CTA has fewer warps than sums), so each sum costs
-// blockDim/32 + 5 dependent FP64 adds on one warp instead of a shuffle tree on every
-// warp (GB300's FP64 rate makes the instruction count matter).
-// red: kRedWords doubles of shared memory.
-__device__ void block_sums(const double *s, int nq, double *red, double *out) {
-  const int nt = blockDim.x, tid = threadIdx.x;
-  for (int i = 0; i < nq; ++i) red[i * nt + tid] = s[i];
-  __syncthreads();
-  const int l = tid & 31, nw = nt >> 5;
-  for (int w = tid >> 5; w < nq; w += nw) {  // fewer warps than sums: warps take several
-    double t = 0.0;
-    for (int i = l; i < nt; i += 32) t += red[w * nt + i];
-    t = warp_sum(t);
-    if (l == 0) out[w] = t;
-  }
-  __syncthreads();
-}
-
-__device__ __forceinline__ double block_sum(double v, double *red) {
-  __shared__ double out1[1];
-  block_sums(&v, 1, red, out1);
-  return out1[0];  // valid in every thread
-}
-
-// Cooperative kernels: one CTA per SM at most (co-residency is checked by the
-// cooperative launch), phases separated by grid-wide barriers.  `part` holds
-// three (grid, ld) panels of per-CTA partial sums; every CTA re-reduces a panel
-// in the same order, so all CTAs see identical coefficients.
-
-// Barrier between phases: grid-wide for the cooperative variant; with a single CTA
-// (short vectors) a CTA barrier is the same thing and needs no cooperative launch.
-template <bool COOP>
-__device__ __forceinline__ void phase_sync() {
-  if constexpr (COOP)
-    cg::this_grid().sync();
-  else
-    __syncthreads();
-}
-
-// part_row[q] = sum over this CTA's slice of V[q][j] x[j] (q < m); part_row[m] = ||x||^2
-// (into the shared c_local instead when it is given).  kRedQ sums per pass over x.
-__device__ void cta_dots(int n, int m, const double *__restrict__ V, const double *__restrict__ x,
-                         double *part_row, double *red, double *c_local = nullptr) {
-  __shared__ double out[kRedQ];
-  for (int q0 = 0; q0 <= m; q0 += kRedQ) {
-    const int nq = min(kRedQ, m + 1 - q0);
-    double s[kRedQ];
-#pragma unroll
-    for (int i = 0; i < kRedQ; ++i) s[i] = 0.0;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-      const double xj = x[j];
-#pragma unroll
-      for (int i = 0; i < kRedQ; ++i) {
-        const int q = q0 + i;
-        if (i < nq) s[i] += (q < m ? V[(int64_t)q * n + j] : xj) * xj;
-      }
-    }
-    block_sums(s, nq, red, out);
-    if ((int)threadIdx.x < nq) (c_local ? c_local : part_row)[q0 + threadIdx.x] = out[threadIdx.x];
-  }
-}
-
-// c[q] = sum_cta panel[cta][q], q <= m (threads 0..m), then a CTA barrier.
-__device__ void cta_gather(const double *panel, int ld, int nparts, int m, double *c) {
-  if ((int)threadIdx.x <= m) {
-    double s = 0.0;
-    for (int i = 0; i < nparts; ++i) s += panel[i * ld + threadIdx.x];
-    c[threadIdx.x] = s;
-  }
-  __syncthreads();
-}
-
-// c[q] = V[q] . x over the grid (q < m), c[m] = ||x||^2; shared c, valid in every thread
-// on return.  Cooperative grids combine per-CTA partials through `panel` after a grid
-// barrier; a single CTA keeps the totals in shared memory.
-template <bool COOP>
-__device__ void grid_dots(int n, int m, const double *__restrict__ V, const double *__restrict__ x, double *panel,
-                          int ld, double *red, double *c) {
-  if constexpr (COOP) {
-    cta_dots(n, m, V, x, panel + (size_t)blockIdx.x * ld, red);
-    cg::this_grid().sync();
-    cta_gather(panel, ld, gridDim.x, m, c);
-  } else {
-    cta_dots(n, m, V, x, nullptr, red, c);
-    __syncthreads();
-  }
-}
-
-// The grid total of one value per thread (valid in every thread).
-template <bool COOP>
-__device__ double grid_sum(double s, double *panel, int ld, double *red, double *c) {
-  s = block_sum(s, red);
-  if constexpr (COOP) {
-    if (threadIdx.x == 0) panel[(size_t)blockIdx.x * ld] = s;
-    cg::this_grid().sync();
-    cta_gather(panel, ld, gridDim.x, 0, c);
-    return c[0];
-  } else {
-    return s;
-  }
-}
-
-// x -= sum_{q<m} c[q] V[q] over this CTA's slice.
-__device__ void cta_axpy(int n, int m, const double *__restrict__ V, double *x, const double *c) {
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-    double xj = x[j];
-    for (int q = 0; q < m; ++q) xj -= c[q] * V[(int64_t)q * n + j];
-    x[j] = xj;
-  }
-}
-
 // beta = ||b||, V[0] = b / beta; resets scal/flags.
 template <bool COOP>
-__global__ void __launch_bounds__(COOP ? kBlas : kBlasSingle) k_init_v0_coop(const double *__restrict__ b, int n, double *part, int ld,
-                                                        double *V, float *Vf, double *scal, int *flags,
-                                                        int use_handle, cudaGraphConditionalHandle h, double *T,
-                                                        int nT) {
+__global__ void __launch_bounds__(COOP ? kBlas : kBlasSingle)
+    k_init_v0_coop(const double *__restrict__ b, int n, double *part, int ld, double *V, float *Vf, double *scal,
+                   int *flags, int use_handle, cudaGraphConditionalHandle h, double *T, int nT) {
   grid_dep_wait();
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nT; i += gridDim.x * blockDim.x) T[i] = 0.0;
-  __shared__ double red[kRedWords];
-  __shared__ double c[34];
-  double s = 0.0;
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) s += b[j] * b[j];
-  const double beta = sqrt(grid_sum<COOP>(s, part, ld, red, c));
-  const bool zero = !(beta > 0.0);
-  const double ib = zero ? 0.0 : 1.0 / beta;
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-    V[j] = b[j] * ib;
-    if (Vf) Vf[j] = (float)V[j];
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    const bool finite = isfinite(beta);
-    scal[S_BETA] = beta;
-    scal[S_T] = 0.0;
-    scal[S_RES] = beta;
-    scal[S_HIST] = beta;
-    flags[F_BREAK] = 0;
-    flags[F_BZERO] = zero ? 1 : 0;
-    if (!finite) flags[F_NONFIN] = 1;
-    flags[F_CAPCNT] = 0;
-    flags[F_M] = 0;
-    const bool run = finite && !zero;
-    flags[F_KSTOP] = run ? 0 : 1;
-    flags[F_KCONV] = zero ? 1 : 0;
-    if (use_handle) cudaGraphSetConditional(h, run ? 1u : 0u);
-  }
+  init_v0_body<COOP>(b, n, part, ld, V, Vf, scal, flags, use_handle, h, T, nT);
 }
 
 // One Arnoldi step (eq. 10): w = K v_{m-1}; two classical Gram-Schmidt passes
@@ -197,10 +46,10 @@ __global__ void __launch_bounds__(COOP ? kBlas : kBlasSingle) k_arnoldi_coop(int
   __shared__ double red[kRedWords];
   __shared__ double c[34];
   const int m = flags[F_M] + 1;  // the step computed here produces v_m
-  const int G = gridDim.x;
+  const int G = COOP ? (int)gridDim.x : 1;
   double *pa = part, *pb = part + (size_t)G * ld, *pc = part + (size_t)2 * G * ld;
   const double *v = V + (int64_t)(m - 1) * n;
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+  for (int j = g_first<COOP>(); j < n; j += g_stride<COOP>()) {
     double x = kdiag[j] * v[j];
     if (j > 0) x += klo[j] * v[j - 1];
     if (j + 1 < n) x += kup[j] * v[j + 1];
@@ -208,25 +57,25 @@ __global__ void __launch_bounds__(COOP ? kBlas : kBlasSingle) k_arnoldi_coop(int
   }
   grid_dots<COOP>(n, m, V, w, pa, ld, red, c);
   const double knorm = sqrt(c[m]);
-  if (blockIdx.x == 0 && (int)threadIdx.x < m) T[(int64_t)threadIdx.x * ldT + (m - 1)] = c[threadIdx.x];
-  cta_axpy(n, m, V, w, c);
+  if ((!COOP || blockIdx.x == 0) && (int)threadIdx.x < m) T[(int64_t)threadIdx.x * ldT + (m - 1)] = c[threadIdx.x];
+  cta_axpy<COOP>(n, m, V, w, c);
   __syncthreads();  // c is rewritten next
   grid_dots<COOP>(n, m, V, w, pb, ld, red, c);
-  if (blockIdx.x == 0 && (int)threadIdx.x < m) T[(int64_t)threadIdx.x * ldT + (m - 1)] += c[threadIdx.x];
-  cta_axpy(n, m, V, w, c);
+  if ((!COOP || blockIdx.x == 0) && (int)threadIdx.x < m) T[(int64_t)threadIdx.x * ldT + (m - 1)] += c[threadIdx.x];
+  cta_axpy<COOP>(n, m, V, w, c);
   __syncthreads();
   double s = 0.0;
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) s += w[j] * w[j];
+  for (int j = g_first<COOP>(); j < n; j += g_stride<COOP>()) s += w[j] * w[j];
   const double t = sqrt(grid_sum<COOP>(s, pc, ld, red, c));
   const bool bd = !(t > 1e-14 * knorm);
   const double it = bd ? 0.0 : 1.0 / t;
   double *vm = V + (int64_t)m * n;
   float *vmf = Vf ? Vf + (int64_t)m * n : nullptr;
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+  for (int j = g_first<COOP>(); j < n; j += g_stride<COOP>()) {
     vm[j] = w[j] * it;
     if (vmf) vmf[j] = (float)vm[j];
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (g_leader<COOP>()) {
     T[(int64_t)m * ldT + (m - 1)] = bd ? 0.0 : t;
     scal[S_T] = bd ? 0.0 : t;
     scal[S_KNORM] = knorm;
@@ -235,32 +84,13 @@ __global__ void __launch_bounds__(COOP ? kBlas : kBlasSingle) k_arnoldi_coop(int
   }
 }
 
-// eq. (13): ||r_m|| = |tau t_{m+1,m}| ||(I - V_m V_m^T) z|| with two CGS passes
-// (z is overwritten by its projection); zero after a breakdown.
+// eq. (13) and the stopping decision (project_body).
 template <bool COOP>
-__global__ void __launch_bounds__(COOP ? kBlas : kBlasSingle) k_project_coop(int n, const double *__restrict__ V, double *z,
-                                                        double tau, double *part, int ld, double *scal,
-                                                        int *flags, KrylovCtl kc, int use_handle,
-                                                        cudaGraphConditionalHandle h) {
+__global__ void __launch_bounds__(COOP ? kBlas : kBlasSingle)
+    k_project_coop(int n, const double *__restrict__ V, double *z, double tau, double *part, int ld, double *scal,
+                   int *flags, KrylovCtl kc, int use_handle, cudaGraphConditionalHandle h) {
   grid_dep_wait();
-  __shared__ double red[kRedWords];
-  __shared__ double c[34];
-  const int m = flags[F_M] + 1;
-  const int G = gridDim.x;
-  double *pa = part, *pb = part + (size_t)G * ld, *pc = part + (size_t)2 * G * ld;
-  grid_dots<COOP>(n, m, V, z, pa, ld, red, c);
-  cta_axpy(n, m, V, z, c);
-  __syncthreads();  // c is rewritten next
-  grid_dots<COOP>(n, m, V, z, pb, ld, red, c);
-  cta_axpy(n, m, V, z, c);
-  __syncthreads();
-  double s = 0.0;
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) s += z[j] * z[j];
-  const double zz = grid_sum<COOP>(s, pc, ld, red, c);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    scal[S_RES] = flags[F_BREAK] ? 0.0 : fabs(tau * scal[S_T]) * sqrt(zz);
-    krylov_decide(scal, flags, kc, use_handle, h);
-  }
+  project_body<COOP>(n, V, z, tau, part, ld, scal, flags, kc, use_handle, h);
 }
 
 // ---- eq. (12): capacitance-system terms, one warp per frequency -----------------

@@ -28,6 +28,8 @@ enum FlagIndex {
   F_RSTOP = 9,    // refinement loop finished
   F_MTOT = 10,    // sum of m over the solves
   F_C2RCNT = 11,  // completion counter of the inverse DFT's finishing epilogue
+  F_ACCCNT = 12,  // completion counter of the b reduction (runs the start of Algorithm 2)
+  F_ZCNT = 13,    // completion counter of the z reduction (runs eq. 13 and the decision)
   F_SWM = 16,     // [16, 32): m of each solve
   kFlagWords = 64
 };
@@ -208,11 +210,13 @@ struct PintArgs {
 };
 template <typename T>
 void launch_pint(Ctx &c, const PintGeom &g, const PintArgs<T> &a);
-// z[j] = sum_k Re(omega_k H[k][j]) over stored h_k (nf rows, leading dimension ldh)
+struct InitTail;  // pd_krylov.cuh: the start of Algorithm 2 run by a reduction's last CTA
+struct ProjTail;  // pd_krylov.cuh: eq. 13 and the step decision run by the z reduction's last CTA
+// z[j] = sum_k Re(omega_k H[k][j]) over stored h_k (nf rows, leading dimension ldh);
+// with tail, the last CTA then projects z and decides the Algorithm-2 step.
 template <typename T>
 void launch_zsum(Ctx &c, int nf, int64_t n, const cpx<T> *H, int64_t ldh, const double2 *omega, double *z,
-                 const int *skip_flag);
-// out[j] = sum_r acc_part[(blk*R + r)*blen + e], j = blk*blen + e
+                 const int *skip_flag, const ProjTail *tail = nullptr);
 // Batched plans (batch.cu): Gs = G with slot b scaled by 2^ex[b] ~ 1/||slot b||_F
 // (part: batch * nc doubles of scratch), and the inverse scaling of U in place with
 // the columns past problem b's nxb[b] rows set to zero.
@@ -225,8 +229,10 @@ void launch_member_decide(Ctx &c, const double *colsum, int nxm, const int *nxb,
                           double *prev, int *mex, double *scal, int *flags, const RefineCtl &r, int use_handle,
                           cudaGraphConditionalHandle h);
 
-void launch_acc_reduce(Ctx &c, const PintGeom &g, const double *acc_part, double *out,
-                       const int *skip_flag);
+// out[j] = sum_r acc_part[(blk*R + r)*blen + e], j = blk*blen + e; with tail, the last
+// CTA then computes beta = ||out|| and v_1 (the start of Algorithm 2).
+void launch_acc_reduce(Ctx &c, const PintGeom &g, const double *acc_part, double *out, const int *skip_flag,
+                       const InitTail *tail = nullptr);
 
 // ---- Krylov / small systems / residual (krylov.cu) -----------------------------------
 struct KrylovBufs {

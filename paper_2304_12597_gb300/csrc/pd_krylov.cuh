@@ -1,0 +1,237 @@
+// Vector building blocks of Algorithm 2 (FP64): fixed-order CTA reductions, the CGS
+// dot products and updates, and the bodies of the steps that start Algorithm 2
+// (beta = ||b||, v_1) and finish each of its iterations (eq. 13 and the stopping
+// decision).  Internal header, included by the Krylov kernels and by the kernels
+// that run those bodies in their last CTA.
+//
+// COOP = true: the vectors are spread over a cooperative grid, partial sums meet in a
+// panel after a grid barrier.  COOP = false: one CTA owns the whole vector (short
+// vectors); it may be any CTA of a larger launch, since these bodies then ignore the
+// block index.
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include "pd_control.cuh"
+
+namespace pd {
+
+constexpr int kBlas = 64;          // CTA size of the cooperative variants
+constexpr int kBlasSingle = 512;   // threads of the one-CTA variants (short vectors)
+constexpr int kRedQ = 4;           // sums reduced side by side
+constexpr int kRedWords = kRedQ * kBlasSingle;
+
+template <bool COOP>
+__device__ __forceinline__ int g_first() {
+  if constexpr (COOP) return blockIdx.x * blockDim.x + threadIdx.x;
+  return threadIdx.x;
+}
+template <bool COOP>
+__device__ __forceinline__ int g_stride() {
+  if constexpr (COOP) return gridDim.x * blockDim.x;
+  return blockDim.x;
+}
+template <bool COOP>
+__device__ __forceinline__ bool g_leader() {
+  if constexpr (COOP) return blockIdx.x == 0 && threadIdx.x == 0;
+  return threadIdx.x == 0;
+}
+
+// out[i] = sum over the CTA of s[i], i < nq <= kRedQ (shared `out`, valid for every
+// thread on return).  The partials go through shared memory and warp i adds column
+// i (also i + warps, ... when the CTA has fewer warps than sums), so each sum costs
+// blockDim/32 + 5 dependent FP64 adds on one warp instead of a shuffle tree on every
+// warp (GB300's FP64 rate makes the instruction count matter).
+// red: kRedWords doubles of shared memory; blockDim.x <= kBlasSingle.
+__device__ __forceinline__ void block_sums(const double *s, int nq, double *red, double *out) {
+  const int nt = blockDim.x, tid = threadIdx.x;
+  for (int i = 0; i < nq; ++i) red[i * nt + tid] = s[i];
+  __syncthreads();
+  const int l = tid & 31, nw = nt >> 5;
+  for (int w = tid >> 5; w < nq; w += nw) {  // fewer warps than sums: warps take several
+    double t = 0.0;
+    for (int i = l; i < nt; i += 32) t += red[w * nt + i];
+    t = warp_sum(t);
+    if (l == 0) out[w] = t;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ double block_sum(double v, double *red) {
+  __shared__ double out1[1];
+  block_sums(&v, 1, red, out1);
+  return out1[0];  // valid in every thread
+}
+
+// part_row[q] = sum over this CTA's slice of V[q][j] x[j] (q < m); part_row[m] = ||x||^2
+// (into the shared c_local instead when it is given).  kRedQ sums per pass over x.
+template <bool COOP>
+__device__ __forceinline__ void cta_dots(int n, int m, const double *__restrict__ V, const double *__restrict__ x,
+                                         double *part_row, double *red, double *c_local) {
+  __shared__ double out[kRedQ];
+  for (int q0 = 0; q0 <= m; q0 += kRedQ) {
+    const int nq = min(kRedQ, m + 1 - q0);
+    double s[kRedQ];
+#pragma unroll
+    for (int i = 0; i < kRedQ; ++i) s[i] = 0.0;
+    for (int j = g_first<COOP>(); j < n; j += g_stride<COOP>()) {
+      const double xj = x[j];
+#pragma unroll
+      for (int i = 0; i < kRedQ; ++i) {
+        const int q = q0 + i;
+        if (i < nq) s[i] += (q < m ? V[(int64_t)q * n + j] : xj) * xj;
+      }
+    }
+    block_sums(s, nq, red, out);
+    if ((int)threadIdx.x < nq) (c_local ? c_local : part_row)[q0 + threadIdx.x] = out[threadIdx.x];
+  }
+}
+
+// c[q] = sum_cta panel[cta][q], q <= m (threads 0..m), then a CTA barrier.
+__device__ __forceinline__ void cta_gather(const double *panel, int ld, int nparts, int m, double *c) {
+  if ((int)threadIdx.x <= m) {
+    double s = 0.0;
+    for (int i = 0; i < nparts; ++i) s += panel[i * ld + threadIdx.x];
+    c[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+// c[q] = V[q] . x over the grid (q < m), c[m] = ||x||^2; shared c, valid in every thread
+// on return.  Cooperative grids combine per-CTA partials through `panel` after a grid
+// barrier; a single CTA keeps the totals in shared memory.
+template <bool COOP>
+__device__ __forceinline__ void grid_dots(int n, int m, const double *__restrict__ V, const double *__restrict__ x,
+                                          double *panel, int ld, double *red, double *c) {
+  if constexpr (COOP) {
+    cta_dots<true>(n, m, V, x, panel + (size_t)blockIdx.x * ld, red, nullptr);
+    cooperative_groups::this_grid().sync();
+    cta_gather(panel, ld, gridDim.x, m, c);
+  } else {
+    cta_dots<false>(n, m, V, x, nullptr, red, c);
+    __syncthreads();
+  }
+}
+
+// The grid total of one value per thread (valid in every thread).
+template <bool COOP>
+__device__ __forceinline__ double grid_sum(double s, double *panel, int ld, double *red, double *c) {
+  s = block_sum(s, red);
+  if constexpr (COOP) {
+    if (threadIdx.x == 0) panel[(size_t)blockIdx.x * ld] = s;
+    cooperative_groups::this_grid().sync();
+    cta_gather(panel, ld, gridDim.x, 0, c);
+    return c[0];
+  } else {
+    return s;
+  }
+}
+
+// x -= sum_{q<m} c[q] V[q] over this CTA's slice.
+template <bool COOP>
+__device__ __forceinline__ void cta_axpy(int n, int m, const double *__restrict__ V, double *x, const double *c) {
+  for (int j = g_first<COOP>(); j < n; j += g_stride<COOP>()) {
+    double xj = x[j];
+    for (int q = 0; q < m; ++q) xj -= c[q] * V[(int64_t)q * n + j];
+    x[j] = xj;
+  }
+}
+
+// Algorithm 2, first step: beta = ||b||, V[0] = b / beta (and its binary32 copy), T_m
+// cleared, the control block reset, and the WHILE conditional set to run the loop
+// unless b is zero or not finite.
+template <bool COOP>
+__device__ __forceinline__ void init_v0_body(const double *__restrict__ b, int n, double *part, int ld, double *V,
+                                             float *Vf, double *scal, int *flags, int use_handle,
+                                             cudaGraphConditionalHandle h, double *T, int nT) {
+  __shared__ double red[kRedWords];
+  __shared__ double c[34];
+  for (int i = g_first<COOP>(); i < nT; i += g_stride<COOP>()) T[i] = 0.0;
+  double s = 0.0;
+  for (int j = g_first<COOP>(); j < n; j += g_stride<COOP>()) s += b[j] * b[j];
+  const double beta = sqrt(grid_sum<COOP>(s, part, ld, red, c));
+  const bool zero = !(beta > 0.0);
+  const double ib = zero ? 0.0 : 1.0 / beta;
+  for (int j = g_first<COOP>(); j < n; j += g_stride<COOP>()) {
+    V[j] = b[j] * ib;
+    if (Vf) Vf[j] = (float)V[j];
+  }
+  if (g_leader<COOP>()) {
+    const bool finite = isfinite(beta);
+    scal[S_BETA] = beta;
+    scal[S_T] = 0.0;
+    scal[S_RES] = beta;
+    scal[S_HIST] = beta;
+    flags[F_BREAK] = 0;
+    flags[F_BZERO] = zero ? 1 : 0;
+    if (!finite) flags[F_NONFIN] = 1;
+    flags[F_CAPCNT] = 0;
+    flags[F_M] = 0;
+    const bool run = finite && !zero;
+    flags[F_KSTOP] = run ? 0 : 1;
+    flags[F_KCONV] = zero ? 1 : 0;
+    if (use_handle) cudaGraphSetConditional(h, run ? 1u : 0u);
+  }
+}
+
+// eq. (13): ||r_m|| = |tau t_{m+1,m}| ||(I - V_m V_m^T) z|| with two CGS passes (z is
+// overwritten by its projection; zero after a breakdown), then the stopping decision.
+template <bool COOP>
+__device__ __forceinline__ void project_body(int n, const double *__restrict__ V, double *z, double tau, double *part,
+                                             int ld, double *scal, int *flags, const KrylovCtl &kc, int use_handle,
+                                             cudaGraphConditionalHandle h) {
+  __shared__ double red[kRedWords];
+  __shared__ double c[34];
+  const int m = flags[F_M] + 1;
+  const int G = COOP ? (int)gridDim.x : 1;
+  double *pa = part, *pb = part + (size_t)G * ld, *pc = part + (size_t)2 * G * ld;
+  grid_dots<COOP>(n, m, V, z, pa, ld, red, c);
+  cta_axpy<COOP>(n, m, V, z, c);
+  __syncthreads();  // c is rewritten next
+  grid_dots<COOP>(n, m, V, z, pb, ld, red, c);
+  cta_axpy<COOP>(n, m, V, z, c);
+  __syncthreads();
+  double s = 0.0;
+  for (int j = g_first<COOP>(); j < n; j += g_stride<COOP>()) s += z[j] * z[j];
+  const double zz = grid_sum<COOP>(s, pc, ld, red, c);
+  if (g_leader<COOP>()) {
+    scal[S_RES] = flags[F_BREAK] ? 0.0 : fabs(tau * scal[S_T]) * sqrt(zz);
+    krylov_decide(scal, flags, kc, use_handle, h);
+  }
+}
+
+// Argument bundles of those bodies when they run in the last CTA of another kernel.
+struct InitTail {
+  int enabled;
+  int *counter;  // zero on entry; reset by the last CTA
+  int n, ld, nT, use_handle;
+  double *part, *V, *scal, *T;
+  float *Vf;
+  int *flags;
+  cudaGraphConditionalHandle h;
+};
+struct ProjTail {
+  int enabled;
+  int *counter;
+  int n, ld, use_handle;
+  const double *V;
+  double tau;
+  double *part, *scal;
+  int *flags;
+  KrylovCtl kc;
+  cudaGraphConditionalHandle h;
+};
+
+// Last-block-done: every CTA calls this after its share of the work; the last one to
+// arrive (no CTA waits for another) returns true with all other CTAs' writes visible.
+__device__ __forceinline__ bool last_cta_done(int *counter) {
+  __shared__ int last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) last = atomicAdd(counter, 1) == (int)(gridDim.x * gridDim.y) - 1;
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+
+}  // namespace pd

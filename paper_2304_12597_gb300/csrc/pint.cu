@@ -26,6 +26,7 @@
 #include <algorithm>
 
 #include "pd_internal.h"
+#include "pd_krylov.cuh"
 
 namespace pd {
 
@@ -397,35 +398,39 @@ __global__ void __launch_bounds__(MAXT) k_pint(PintGeom g, PintArgs<T> a, size_t
 constexpr int kColB = 8;
 
 template <int CW, int RG>
-__device__ __forceinline__ double colsum_finish(double v, double (*sm)[CW + 1]) {
-  sm[threadIdx.y][threadIdx.x] = v;
+__device__ __forceinline__ double colsum_finish(double v, double (*sm)[CW + 1], int tx, int ty) {
+  sm[ty][tx] = v;
   __syncthreads();
   double t = 0.0;
-  if (threadIdx.y < 8) {
+  if (ty < 8) {
 #pragma unroll
-    for (int i = 0; i < RG / 8; ++i) t += sm[threadIdx.y * (RG / 8) + i][threadIdx.x];
+    for (int i = 0; i < RG / 8; ++i) t += sm[ty * (RG / 8) + i][tx];
   }
   __syncthreads();
-  if (threadIdx.y < 8) sm[threadIdx.y][threadIdx.x] = t;
+  if (ty < 8) sm[ty][tx] = t;
   __syncthreads();
   t = 0.0;
-  if (threadIdx.y == 0) {
+  if (ty == 0) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) t += sm[i][threadIdx.x];
+    for (int i = 0; i < 8; ++i) t += sm[i][tx];
   }
-  return t;  // valid for threadIdx.y == 0
+  return t;  // valid for ty == 0
 }
 
 // out[j] = sum_r part[(blk*R + r)*blen + e], j = blk*blen + e (the per-team partial
-// rows of b or z).
+// rows of b or z).  One-dimensional CTAs of CW * RG threads: column tx, group ty.
+// With tail.enabled the last CTA to finish then starts Algorithm 2 on out (beta, v_1),
+// for vectors one CTA handles.
 template <int CW, int RG>
 __global__ void __launch_bounds__(CW * RG) k_acc_reduce(int nblk, int blen, int R, const double *__restrict__ part,
-                                                        double *__restrict__ out, const int *skip_flag) {
+                                                        double *__restrict__ out, const int *skip_flag,
+                                                        InitTail tail) {
   grid_dep_wait();
-  if (skip_flag && *skip_flag) return;
+  if (skip_flag && *skip_flag && !tail.enabled) return;
   __shared__ double sm[RG][CW + 1];
-  const int64_t n = (int64_t)nblk * blen;
-  const int64_t j = (int64_t)blockIdx.x * CW + threadIdx.x;
+  const int tx = threadIdx.x % CW, ty = threadIdx.x / CW;
+  const int64_t n = (skip_flag && *skip_flag) ? 0 : (int64_t)nblk * blen;
+  const int64_t j = (int64_t)blockIdx.x * CW + tx;
   double acc[kColB];
 #pragma unroll
   for (int u = 0; u < kColB; ++u) acc[u] = 0.0;
@@ -433,7 +438,7 @@ __global__ void __launch_bounds__(CW * RG) k_acc_reduce(int nblk, int blen, int 
     const int blk = (int)(j / blen);
     const int e = (int)(j - (int64_t)blk * blen);
     const double *base = part + (int64_t)blk * R * blen + e;  // R = partial rows per block
-    for (int r0 = threadIdx.y; r0 < R; r0 += RG * kColB) {
+    for (int r0 = ty; r0 < R; r0 += RG * kColB) {
       double v[kColB];
 #pragma unroll
       for (int u = 0; u < kColB; ++u) {
@@ -447,72 +452,88 @@ __global__ void __launch_bounds__(CW * RG) k_acc_reduce(int nblk, int blen, int 
   double tot = 0.0;
 #pragma unroll
   for (int u = 0; u < kColB; ++u) tot += acc[u];
-  tot = colsum_finish<CW, RG>(tot, sm);
-  if (threadIdx.y == 0 && j < n) out[j] = tot;
+  tot = colsum_finish<CW, RG>(tot, sm, tx, ty);
+  if (ty == 0 && j < n) out[j] = tot;
+  if (tail.enabled && last_cta_done(tail.counter)) {
+    init_v0_body<false>(out, tail.n, tail.part, tail.ld, tail.V, tail.Vf, tail.scal, tail.flags, tail.use_handle,
+                        tail.h, tail.T, tail.nT);
+    if (threadIdx.x == 0) *tail.counter = 0;
+  }
 }
 
 // z[j] = sum_k Re(omega_k H[k][j]) over the stored h_k (eq. 13's z), j < n.  In
-// binary32 the weights are rounded once into shared memory (nf * 8 bytes).
+// binary32 the weights are rounded once into shared memory (nf * 8 bytes).  With
+// tail.enabled the last CTA to finish then projects z and takes the decision of the
+// Algorithm-2 step (eq. 13), for vectors one CTA handles.
 template <typename T, int CW, int RG>
 __global__ void __launch_bounds__(CW * RG) k_zsum(int nf, int64_t n, const cpx<T> *__restrict__ H, int64_t ldh,
                                                   const double2 *__restrict__ omega, double *__restrict__ z,
-                                                  const int *skip_flag) {
+                                                  const int *skip_flag, ProjTail tail) {
   grid_dep_wait();
-  if (skip_flag && *skip_flag) return;
+  const bool skip = skip_flag && *skip_flag;  // breakdown: no z (eq. 13 gives 0); the tail still decides
   __shared__ double sm[RG][CW + 1];
   extern __shared__ __align__(16) unsigned char om_raw[];
   cpx<T> *om = reinterpret_cast<cpx<T> *>(om_raw);
-  const int tid = threadIdx.y * CW + threadIdx.x;
-  for (int k = tid; k < nf; k += CW * RG) om[k] = mk<T>((T)omega[k].x, (T)omega[k].y);
-  __syncthreads();
-  const int64_t j = (int64_t)blockIdx.x * CW + threadIdx.x;
-  T acc[kColB];
+  const int tx = threadIdx.x % CW, ty = threadIdx.x / CW;
+  if (!skip) {
+    for (int k = threadIdx.x; k < nf; k += CW * RG) om[k] = mk<T>((T)omega[k].x, (T)omega[k].y);
+    __syncthreads();
+    const int64_t j = (int64_t)blockIdx.x * CW + tx;
+    T acc[kColB];
 #pragma unroll
-  for (int u = 0; u < kColB; ++u) acc[u] = T(0);
-  if (j < n) {
-    for (int k0 = threadIdx.y; k0 < nf; k0 += RG * kColB) {
-      cpx<T> h[kColB];
+    for (int u = 0; u < kColB; ++u) acc[u] = T(0);
+    if (j < n) {
+      for (int k0 = ty; k0 < nf; k0 += RG * kColB) {
+        cpx<T> h[kColB];
 #pragma unroll
-      for (int u = 0; u < kColB; ++u) {
-        const int k = k0 + u * RG;
-        h[u] = k < nf ? H[(int64_t)k * ldh + j] : mk<T>(T(0), T(0));
-      }
+        for (int u = 0; u < kColB; ++u) {
+          const int k = k0 + u * RG;
+          h[u] = k < nf ? H[(int64_t)k * ldh + j] : mk<T>(T(0), T(0));
+        }
 #pragma unroll
-      for (int u = 0; u < kColB; ++u) {
-        const int k = k0 + u * RG;
-        if (k < nf) acc[u] += om[k].x * h[u].x - om[k].y * h[u].y;
+        for (int u = 0; u < kColB; ++u) {
+          const int k = k0 + u * RG;
+          if (k < nf) acc[u] += om[k].x * h[u].x - om[k].y * h[u].y;
+        }
       }
     }
-  }
-  double tot = 0.0;
+    double tot = 0.0;
 #pragma unroll
-  for (int u = 0; u < kColB; ++u) tot += (double)acc[u];
-  tot = colsum_finish<CW, RG>(tot, sm);
-  if (threadIdx.y == 0 && j < n) z[j] = tot;
+    for (int u = 0; u < kColB; ++u) tot += (double)acc[u];
+    tot = colsum_finish<CW, RG>(tot, sm, tx, ty);
+    if (ty == 0 && j < n) z[j] = tot;
+  }
+  if (tail.enabled && last_cta_done(tail.counter)) {
+    project_body<false>(tail.n, tail.V, z, tail.tau, tail.part, tail.ld, tail.scal, tail.flags, tail.kc,
+                        tail.use_handle, tail.h);
+    if (threadIdx.x == 0) *tail.counter = 0;
+  }
 }
 
 template <typename T>
 void launch_zsum(Ctx &c, int nf, int64_t n, const cpx<T> *H, int64_t ldh, const double2 *omega, double *z,
-                 const int *skip_flag) {
+                 const int *skip_flag, const ProjTail *tailp) {
   const size_t smem = (size_t)nf * sizeof(cpx<T>);
+  ProjTail tail{};
+  if (tailp) tail = *tailp;
   c.launch("zsum", (double)nf * n * sizeof(cpx<T>) + n * 8.0, [&] {
     if (nf <= 256) {
       const int grid = (int)((n + 31) / 32);
-      pdl_launch(c.pdl, k_zsum<T, 32, 16>, dim3(grid), dim3(32, 16), smem, c.stream, nf, n, H, ldh, omega, z,
-                 skip_flag);
+      pdl_launch(c.pdl, k_zsum<T, 32, 16>, dim3(grid), dim3(512), smem, c.stream, nf, n, H, ldh, omega, z,
+                 skip_flag, tail);
     } else {
       const int grid = (int)((n + 7) / 8);
       if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_zsum<T, 8, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      pdl_launch(c.pdl, k_zsum<T, 8, 64>, dim3(grid), dim3(8, 64), smem, c.stream, nf, n, H, ldh, omega, z,
-                 skip_flag);
+      pdl_launch(c.pdl, k_zsum<T, 8, 64>, dim3(grid), dim3(512), smem, c.stream, nf, n, H, ldh, omega, z,
+                 skip_flag, tail);
     }
   });
 }
 template void launch_zsum<double>(Ctx &, int, int64_t, const cpx<double> *, int64_t, const double2 *, double *,
-                                  const int *);
+                                  const int *, const ProjTail *);
 template void launch_zsum<float>(Ctx &, int, int64_t, const cpx<float> *, int64_t, const double2 *, double *,
-                                 const int *);
+                                 const int *, const ProjTail *);
 
 static int next_pow2(int v) {
   int p = 1;
@@ -584,15 +605,18 @@ void launch_pint(Ctx &c, const PintGeom &g, const PintArgs<T> &a) {
   }
 }
 
-void launch_acc_reduce(Ctx &c, const PintGeom &g, const double *acc_part, double *out, const int *skip_flag) {
+void launch_acc_reduce(Ctx &c, const PintGeom &g, const double *acc_part, double *out, const int *skip_flag,
+                       const InitTail *tailp) {
   const int64_t n = (int64_t)g.nblk * g.blen;
+  InitTail tail{};
+  if (tailp) tail = *tailp;
   c.launch("acc_reduce", (double)n * g.acc_rows * 8.0 + n * 8.0, [&] {
     if (g.acc_rows <= 256)
-      pdl_launch(c.pdl, k_acc_reduce<32, 16>, dim3((int)((n + 31) / 32)), dim3(32, 16), 0, c.stream, g.nblk, g.blen,
-                 g.acc_rows, acc_part, out, skip_flag);
+      pdl_launch(c.pdl, k_acc_reduce<32, 16>, dim3((int)((n + 31) / 32)), dim3(512), 0, c.stream, g.nblk, g.blen,
+                 g.acc_rows, acc_part, out, skip_flag, tail);
     else
-      pdl_launch(c.pdl, k_acc_reduce<8, 64>, dim3((int)((n + 7) / 8)), dim3(8, 64), 0, c.stream, g.nblk, g.blen,
-                 g.acc_rows, acc_part, out, skip_flag);
+      pdl_launch(c.pdl, k_acc_reduce<8, 64>, dim3((int)((n + 7) / 8)), dim3(512), 0, c.stream, g.nblk, g.blen,
+                 g.acc_rows, acc_part, out, skip_flag, tail);
   });
 }
 

@@ -20,6 +20,7 @@
 
 #include "../../include/paradiag.h"
 #include "pd_internal.h"
+#include "pd_krylov.cuh"
 
 using pd::cpx;
 
@@ -752,9 +753,15 @@ pd_status emit_pre(pd_plan *p, int kind, const double *G, double *U, int use_han
   a.omega = p->wg;
   a.acc_part = p->acc_part;
   pd::launch_pint<T>(c, p->geom, a);
-  pd::launch_acc_reduce(c, p->geom, p->acc_part, p->b, nullptr);
   pd::KrylovBufs kb = kbufs<T>(p);
-  pd::launch_vec_norm_init(c, kb, p->b, use_handle, hk);
+  if (kb.grid == 1) {  // one CTA holds the vectors: beta and v_1 in the reduction's last CTA
+    const pd::InitTail t{1, p->flags + pd::F_ACCCNT, kb.n, kb.maxit + 2, (kb.maxit + 1) * kb.maxit, use_handle,
+                         kb.part, kb.V, kb.scal, kb.T, kb.Vf, kb.flags, hk};
+    pd::launch_acc_reduce(c, p->geom, p->acc_part, p->b, nullptr, &t);
+  } else {
+    pd::launch_acc_reduce(c, p->geom, p->acc_part, p->b, nullptr);
+    pd::launch_vec_norm_init(c, kb, p->b, use_handle, hk);
+  }
   return PD_OK;
 }
 
@@ -781,8 +788,14 @@ pd_status emit_iter(pd_plan *p, int kind, int use_handle, cudaGraphConditionalHa
   pd::launch_capacitance(c, kb, p->nf, p->tau, p->shift, p->wga, p->gpart, p->nblk, p->msys_part, p->k5_grid,
                          p->srow, p->omega, p->y);
   // z = sum_i gamma_i h_i (e_m^T S_i y_m) from the stored h_i, then eq. (13)
-  pd::launch_zsum<T>(c, p->nf, p->nbar, H, p->lds, p->omega, p->z, p->flags + pd::F_BREAK);
-  pd::launch_project_resnorm(c, kb, p->z, p->tau, krylov_ctl(p, kind), use_handle, hk);
+  if (kb.grid == 1) {  // eq. (13) and the decision in the z reduction's last CTA
+    const pd::ProjTail t{1, p->flags + pd::F_ZCNT, kb.n, kb.maxit + 2, use_handle, kb.V, p->tau, kb.part, kb.scal,
+                         kb.flags, krylov_ctl(p, kind), hk};
+    pd::launch_zsum<T>(c, p->nf, p->nbar, H, p->lds, p->omega, p->z, p->flags + pd::F_BREAK, &t);
+  } else {
+    pd::launch_zsum<T>(c, p->nf, p->nbar, H, p->lds, p->omega, p->z, p->flags + pd::F_BREAK);
+    pd::launch_project_resnorm(c, kb, p->z, p->tau, krylov_ctl(p, kind), use_handle, hk);
+  }
   return PD_OK;
 }
 
