@@ -120,6 +120,10 @@ typedef struct pd_desc {
   int32_t tune_no_pdl;       /* nonzero: launch kernels without programmatic dependent launch
                                 (by default a kernel may be scheduled while its predecessor
                                 drains; it waits for it before reading anything) */
+  int32_t tune_krylov_cluster; /* where one CTA would run the Krylov vector kernels: -1 =
+                                keep that single CTA; 2 .. 16 = spread them over a
+                                thread-block cluster of that many CTAs, one per SM, with the
+                                reductions through distributed shared memory */
   /* Batching (1D only): `batch` independent problems with the same nt are solved
    * together as one block-diagonal problem (their DFTs, shifted solves, Krylov space
    * and refinement are shared; the blocks never couple).  Problem b occupies slot b:

@@ -25,19 +25,19 @@
 namespace pd {
 
 // beta = ||b||, V[0] = b / beta; resets scal/flags.
-template <bool COOP>
-__global__ void __launch_bounds__(COOP ? kBlas : kBlasSingle)
+template <int MODE>
+__global__ void __launch_bounds__(MODE == kCoop ? kBlas : kBlasSingle)
     k_init_v0_coop(const double *__restrict__ b, int n, double *part, int ld, double *V, float *Vf, double *scal,
                    int *flags, int use_handle, cudaGraphConditionalHandle h, double *T, int nT) {
   grid_dep_wait();
-  init_v0_body<COOP>(b, n, part, ld, V, Vf, scal, flags, use_handle, h, T, nT);
+  init_v0_body<MODE>(b, n, part, ld, V, Vf, scal, flags, use_handle, h, T, nT);
 }
 
 // One Arnoldi step (eq. 10): w = K v_{m-1}; two classical Gram-Schmidt passes
 // against v_0..v_{m-1} (their coefficients summed into column m-1 of T_m);
 // t = ||w||; v_m = w / t, or breakdown when t <= 1e-14 ||K v_{m-1}||.
-template <bool COOP>
-__global__ void __launch_bounds__(COOP ? kBlas : kBlasSingle) k_arnoldi_coop(int n, const double *__restrict__ klo,
+template <int MODE>
+__global__ void __launch_bounds__(MODE == kCoop ? kBlas : kBlasSingle) k_arnoldi_coop(int n, const double *__restrict__ klo,
                                                         const double *__restrict__ kdiag,
                                                         const double *__restrict__ kup, double *V, float *Vf,
                                                         double *w, double *T, int ldT, double *part, int ld,
@@ -46,51 +46,58 @@ __global__ void __launch_bounds__(COOP ? kBlas : kBlasSingle) k_arnoldi_coop(int
   __shared__ double red[kRedWords];
   __shared__ double c[34];
   const int m = flags[F_M] + 1;  // the step computed here produces v_m
-  const int G = COOP ? (int)gridDim.x : 1;
+  __shared__ double cslot[MODE == kCluster ? 3 * kSlot : 1];
+  const int G = MODE == kCoop ? (int)gridDim.x : 1;
   double *pa = part, *pb = part + (size_t)G * ld, *pc = part + (size_t)2 * G * ld;
+  if constexpr (MODE == kCluster) {
+    pa = cslot;
+    pb = cslot + kSlot;
+    pc = cslot + 2 * kSlot;
+  }
   const double *v = V + (int64_t)(m - 1) * n;
-  for (int j = g_first<COOP>(); j < n; j += g_stride<COOP>()) {
+  for (int j = g_first<MODE>(); j < n; j += g_stride<MODE>()) {
     double x = kdiag[j] * v[j];
     if (j > 0) x += klo[j] * v[j - 1];
     if (j + 1 < n) x += kup[j] * v[j + 1];
     w[j] = x;
   }
-  grid_dots<COOP>(n, m, V, w, pa, ld, red, c);
+  grid_dots<MODE>(n, m, V, w, pa, ld, red, c);
   const double knorm = sqrt(c[m]);
-  if ((!COOP || blockIdx.x == 0) && (int)threadIdx.x < m) T[(int64_t)threadIdx.x * ldT + (m - 1)] = c[threadIdx.x];
-  cta_axpy<COOP>(n, m, V, w, c);
+  if ((MODE == kSingle || blockIdx.x == 0) && (int)threadIdx.x < m) T[(int64_t)threadIdx.x * ldT + (m - 1)] = c[threadIdx.x];
+  cta_axpy<MODE>(n, m, V, w, c);
   __syncthreads();  // c is rewritten next
-  grid_dots<COOP>(n, m, V, w, pb, ld, red, c);
-  if ((!COOP || blockIdx.x == 0) && (int)threadIdx.x < m) T[(int64_t)threadIdx.x * ldT + (m - 1)] += c[threadIdx.x];
-  cta_axpy<COOP>(n, m, V, w, c);
+  grid_dots<MODE>(n, m, V, w, pb, ld, red, c);
+  if ((MODE == kSingle || blockIdx.x == 0) && (int)threadIdx.x < m) T[(int64_t)threadIdx.x * ldT + (m - 1)] += c[threadIdx.x];
+  cta_axpy<MODE>(n, m, V, w, c);
   __syncthreads();
   double s = 0.0;
-  for (int j = g_first<COOP>(); j < n; j += g_stride<COOP>()) s += w[j] * w[j];
-  const double t = sqrt(grid_sum<COOP>(s, pc, ld, red, c));
+  for (int j = g_first<MODE>(); j < n; j += g_stride<MODE>()) s += w[j] * w[j];
+  const double t = sqrt(grid_sum<MODE>(s, pc, ld, red, c));
   const bool bd = !(t > 1e-14 * knorm);
   const double it = bd ? 0.0 : 1.0 / t;
   double *vm = V + (int64_t)m * n;
   float *vmf = Vf ? Vf + (int64_t)m * n : nullptr;
-  for (int j = g_first<COOP>(); j < n; j += g_stride<COOP>()) {
+  for (int j = g_first<MODE>(); j < n; j += g_stride<MODE>()) {
     vm[j] = w[j] * it;
     if (vmf) vmf[j] = (float)vm[j];
   }
-  if (g_leader<COOP>()) {
+  if (g_leader<MODE>()) {
     T[(int64_t)m * ldT + (m - 1)] = bd ? 0.0 : t;
     scal[S_T] = bd ? 0.0 : t;
     scal[S_KNORM] = knorm;
     flags[F_BREAK] = bd ? 1 : 0;
     if (!isfinite(t)) flags[F_NONFIN] = 1;
   }
+  cluster_exit<MODE>();
 }
 
 // eq. (13) and the stopping decision (project_body).
-template <bool COOP>
-__global__ void __launch_bounds__(COOP ? kBlas : kBlasSingle)
+template <int MODE>
+__global__ void __launch_bounds__(MODE == kCoop ? kBlas : kBlasSingle)
     k_project_coop(int n, const double *__restrict__ V, double *z, double tau, double *part, int ld, double *scal,
                    int *flags, KrylovCtl kc, int use_handle, cudaGraphConditionalHandle h) {
   grid_dep_wait();
-  project_body<COOP>(n, V, z, tau, part, ld, scal, flags, kc, use_handle, h);
+  project_body<MODE>(n, V, z, tau, part, ld, scal, flags, kc, use_handle, h);
 }
 
 // ---- eq. (12): capacitance-system terms, one warp per frequency -----------------
@@ -332,8 +339,60 @@ __global__ void k_residual(const double *__restrict__ G, const double *__restric
 
 // One CTA (plain launch) when the vector is short, else a cooperative launch through
 // cudaLaunchKernelEx (capturable into a CUDA graph).
-static void coop_launch(Ctx &c, const char *fam, double bytes, const void *fn_single, const void *fn_coop, int grid,
-                        void **args) {
+// Cluster variant: one CTA per SM (the dynamic shared memory request keeps a second
+// CTA off the SM), kBlasCluster threads each.
+constexpr int kBlasCluster = 128;
+constexpr int kClusterSpreadSmem = 120 * 1024;
+
+// Largest cluster size <= want (halving, down to 2) the device can co-schedule for the
+// cluster variant of the vector kernels; 0 if none.
+int krylov_cluster_size(int want) {
+  const void *fn = (const void *)k_arnoldi_coop<kCluster>;
+  cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kClusterSpreadSmem);
+  for (int cl = want; cl >= 2; cl >>= 1) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)cl);
+    cfg.blockDim = dim3(kBlasCluster);
+    cfg.dynamicSmemBytes = kClusterSpreadSmem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) == cudaSuccess && n > 0) return cl;
+    cudaGetLastError();
+  }
+  return 0;
+}
+
+static void coop_launch(Ctx &c, const char *fam, double bytes, const void *fn_single, const void *fn_coop,
+                        const void *fn_cluster, int grid, int cluster, void **args) {
+  if (grid <= 1 && cluster > 1) {
+    cudaFuncSetAttribute(fn_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(fn_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, kClusterSpreadSmem);
+    c.launch(fam, bytes, [&] {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)cluster);
+      cfg.blockDim = dim3(kBlasCluster);
+      cfg.dynamicSmemBytes = kClusterSpreadSmem;
+      cfg.stream = c.stream;
+      cudaLaunchAttribute attr[2];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = (unsigned)cluster;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      attr[1].val.programmaticStreamSerializationAllowed = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = c.pdl ? 2 : 1;
+      cudaLaunchKernelExC(&cfg, fn_cluster, args);
+    });
+    return;
+  }
   if (grid <= 1) {
     c.launch(fam, bytes, [&] {
       cudaLaunchConfig_t cfg = {};
@@ -374,8 +433,8 @@ void launch_vec_norm_init(Ctx &c, KrylovBufs &k, const double *b, int use_handle
   double *T = k.T;
   int nT = (k.maxit + 1) * k.maxit;
   void *args[] = {(void *)&b, &n, &part, (void *)&ld, &V, &Vf, &scal, &flags, &use_handle, &h, &T, &nT};
-  coop_launch(c, "krylov_init", (double)k.n * 16, (const void *)k_init_v0_coop<false>,
-              (const void *)k_init_v0_coop<true>, k.grid, args);
+  coop_launch(c, "krylov_init", (double)k.n * 16, (const void *)k_init_v0_coop<kSingle>,
+              (const void *)k_init_v0_coop<kCoop>, (const void *)k_init_v0_coop<kCluster>, k.grid, k.cluster, args);
 }
 
 // Partial buffers: k.part holds three (grid, maxit+2) panels.
@@ -388,8 +447,8 @@ void launch_arnoldi(Ctx &c, KrylovBufs &k) {
   int *flags = k.flags;
   void *args[] = {&n, (void *)&klo, (void *)&kdiag, (void *)&kup, &V, &Vf, &w, &T, &ldT, &part, (void *)&ld,
                   &scal, &flags};
-  coop_launch(c, "krylov_arnoldi", (double)k.n * 8.0 * 8, (const void *)k_arnoldi_coop<false>,
-              (const void *)k_arnoldi_coop<true>, k.grid, args);
+  coop_launch(c, "krylov_arnoldi", (double)k.n * 8.0 * 8, (const void *)k_arnoldi_coop<kSingle>,
+              (const void *)k_arnoldi_coop<kCoop>, (const void *)k_arnoldi_coop<kCluster>, k.grid, k.cluster, args);
 }
 
 void launch_capacitance(Ctx &c, KrylovBufs &k, int nf, double tau, const double2 *shift, const double2 *wg,
@@ -415,8 +474,8 @@ void launch_project_resnorm(Ctx &c, KrylovBufs &k, const double *z, double tau, 
   int *flags = k.flags;
   KrylovCtl kc = kc0;
   void *args[] = {&n, (void *)&V, &zz, &tau, &part, (void *)&ld, &scal, &flags, &kc, &use_handle, &h};
-  coop_launch(c, "krylov_project", (double)k.n * 8.0 * 6, (const void *)k_project_coop<false>,
-              (const void *)k_project_coop<true>, k.grid, args);
+  coop_launch(c, "krylov_project", (double)k.n * 8.0 * 6, (const void *)k_project_coop<kSingle>,
+              (const void *)k_project_coop<kCoop>, (const void *)k_project_coop<kCluster>, k.grid, k.cluster, args);
 }
 
 void launch_xm(Ctx &c, KrylovBufs &k, const double *y, double *x, float *xf) {

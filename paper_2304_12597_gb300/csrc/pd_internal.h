@@ -247,12 +247,16 @@ struct KrylovBufs {
   int grid;           // CTAs of the BLAS-1 kernels
   double *scal;       // scalar block (see krylov.cu)
   int *flags;         // flag block (see krylov.cu)
+  int cluster;        // grid == 1 only: > 0 runs the vector kernels on a cluster of this many CTAs
 };
 // All Algorithm-2 kernels read m from flags[F_M] (completed steps), so one captured
 // iteration serves every m.  `use_handle` / `h`: set a CUDA-graph conditional.
 void launch_vec_norm_init(Ctx &c, KrylovBufs &k, const double *b, int use_handle,
                           cudaGraphConditionalHandle h);  // also zeroes T
 void launch_arnoldi(Ctx &c, KrylovBufs &k);
+// Largest cluster size <= want (halving) the device can co-schedule for the cluster
+// variant of the vector kernels (one CTA per SM); 0 if none.
+int krylov_cluster_size(int want);
 void launch_capacitance(Ctx &c, KrylovBufs &k, int nf, double tau, const double2 *shift,
                         const double2 *wg, const double2 *gpart, int nblk, double *msys_part,
                         int k5_grid, double2 *srow, double2 *omega, double *y);

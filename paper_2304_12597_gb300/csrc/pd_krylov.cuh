@@ -4,8 +4,12 @@
 // decision).  Internal header, included by the Krylov kernels and by the kernels
 // that run those bodies in their last CTA.
 //
-// COOP = true: the vectors are spread over a cooperative grid, partial sums meet in a
-// panel after a grid barrier.  COOP = false: one CTA owns the whole vector (short
+// MODE kCoop: the vectors are spread over a cooperative grid, partial sums meet in a
+// global panel after a grid barrier.  kCluster: they are spread over one thread-block
+// cluster (the whole grid), each CTA keeps its partial sums in shared memory and the
+// others read them through distributed shared memory after a cluster barrier, so the
+// FP64 work of a vector step runs on several SMs without grid-wide barriers.
+// kSingle: one CTA owns the whole vector (short
 // vectors); it may be any CTA of a larger launch, since these bodies then ignore the
 // block index.
 #pragma once
@@ -20,20 +24,22 @@ constexpr int kBlas = 64;          // CTA size of the cooperative variants
 constexpr int kBlasSingle = 512;   // threads of the one-CTA variants (short vectors)
 constexpr int kRedQ = 4;           // sums reduced side by side
 constexpr int kRedWords = kRedQ * kBlasSingle;
+constexpr int kSingle = 0, kCoop = 1, kCluster = 2;  // MODE of the vector steps
+constexpr int kSlot = 36;  // doubles per cluster-mode partial slot (m + 1 <= 33 sums)
 
-template <bool COOP>
+template <int MODE>
 __device__ __forceinline__ int g_first() {
-  if constexpr (COOP) return blockIdx.x * blockDim.x + threadIdx.x;
+  if constexpr (MODE != kSingle) return blockIdx.x * blockDim.x + threadIdx.x;
   return threadIdx.x;
 }
-template <bool COOP>
+template <int MODE>
 __device__ __forceinline__ int g_stride() {
-  if constexpr (COOP) return gridDim.x * blockDim.x;
+  if constexpr (MODE != kSingle) return gridDim.x * blockDim.x;
   return blockDim.x;
 }
-template <bool COOP>
+template <int MODE>
 __device__ __forceinline__ bool g_leader() {
-  if constexpr (COOP) return blockIdx.x == 0 && threadIdx.x == 0;
+  if constexpr (MODE != kSingle) return blockIdx.x == 0 && threadIdx.x == 0;
   return threadIdx.x == 0;
 }
 
@@ -65,7 +71,7 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
 
 // part_row[q] = sum over this CTA's slice of V[q][j] x[j] (q < m); part_row[m] = ||x||^2
 // (into the shared c_local instead when it is given).  kRedQ sums per pass over x.
-template <bool COOP>
+template <int MODE>
 __device__ __forceinline__ void cta_dots(int n, int m, const double *__restrict__ V, const double *__restrict__ x,
                                          double *part_row, double *red, double *c_local) {
   __shared__ double out[kRedQ];
@@ -74,7 +80,7 @@ __device__ __forceinline__ void cta_dots(int n, int m, const double *__restrict_
     double s[kRedQ];
 #pragma unroll
     for (int i = 0; i < kRedQ; ++i) s[i] = 0.0;
-    for (int j = g_first<COOP>(); j < n; j += g_stride<COOP>()) {
+    for (int j = g_first<MODE>(); j < n; j += g_stride<MODE>()) {
       const double xj = x[j];
 #pragma unroll
       for (int i = 0; i < kRedQ; ++i) {
@@ -97,40 +103,70 @@ __device__ __forceinline__ void cta_gather(const double *panel, int ld, int npar
   __syncthreads();
 }
 
+// c[q] = sum over the cluster's CTAs of slot[q] (q < cnt; `slot` is this CTA's shared
+// slot, the same offset in every CTA), rank order fixed; then a CTA barrier.  The
+// cluster barrier's release/acquire makes every CTA's slot (and earlier global writes,
+// after a fence) visible.  A slot must not be rewritten in the same launch.
+__device__ __forceinline__ void cluster_gather(double *slot, int cnt, double *c) {
+  cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+  cl.sync();
+  if ((int)threadIdx.x < cnt) {
+    double s = 0.0;
+    const int nb = (int)cl.num_blocks();
+    for (int r = 0; r < nb; ++r) s += cl.map_shared_rank(slot, r)[threadIdx.x];
+    c[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
 // c[q] = V[q] . x over the grid (q < m), c[m] = ||x||^2; shared c, valid in every thread
 // on return.  Cooperative grids combine per-CTA partials through `panel` after a grid
-// barrier; a single CTA keeps the totals in shared memory.
-template <bool COOP>
+// barrier; clusters through `panel` = a shared slot of kSlot doubles (cluster_gather);
+// a single CTA keeps the totals in shared memory.
+template <int MODE>
 __device__ __forceinline__ void grid_dots(int n, int m, const double *__restrict__ V, const double *__restrict__ x,
                                           double *panel, int ld, double *red, double *c) {
-  if constexpr (COOP) {
-    cta_dots<true>(n, m, V, x, panel + (size_t)blockIdx.x * ld, red, nullptr);
+  if constexpr (MODE == kCoop) {
+    cta_dots<kCoop>(n, m, V, x, panel + (size_t)blockIdx.x * ld, red, nullptr);
     cooperative_groups::this_grid().sync();
     cta_gather(panel, ld, gridDim.x, m, c);
+  } else if constexpr (MODE == kCluster) {
+    cta_dots<kCluster>(n, m, V, x, nullptr, red, panel);
+    cluster_gather(panel, m + 1, c);
   } else {
-    cta_dots<false>(n, m, V, x, nullptr, red, c);
+    cta_dots<kSingle>(n, m, V, x, nullptr, red, c);
     __syncthreads();
   }
 }
 
 // The grid total of one value per thread (valid in every thread).
-template <bool COOP>
+template <int MODE>
 __device__ __forceinline__ double grid_sum(double s, double *panel, int ld, double *red, double *c) {
   s = block_sum(s, red);
-  if constexpr (COOP) {
+  if constexpr (MODE == kCoop) {
     if (threadIdx.x == 0) panel[(size_t)blockIdx.x * ld] = s;
     cooperative_groups::this_grid().sync();
     cta_gather(panel, ld, gridDim.x, 0, c);
+    return c[0];
+  } else if constexpr (MODE == kCluster) {
+    if (threadIdx.x == 0) panel[0] = s;
+    cluster_gather(panel, 1, c);
     return c[0];
   } else {
     return s;
   }
 }
 
+// Cluster mode: no CTA may exit while another can still read its shared slots.
+template <int MODE>
+__device__ __forceinline__ void cluster_exit() {
+  if constexpr (MODE == kCluster) cooperative_groups::this_cluster().sync();
+}
+
 // x -= sum_{q<m} c[q] V[q] over this CTA's slice.
-template <bool COOP>
+template <int MODE>
 __device__ __forceinline__ void cta_axpy(int n, int m, const double *__restrict__ V, double *x, const double *c) {
-  for (int j = g_first<COOP>(); j < n; j += g_stride<COOP>()) {
+  for (int j = g_first<MODE>(); j < n; j += g_stride<MODE>()) {
     double xj = x[j];
     for (int q = 0; q < m; ++q) xj -= c[q] * V[(int64_t)q * n + j];
     x[j] = xj;
@@ -140,23 +176,24 @@ __device__ __forceinline__ void cta_axpy(int n, int m, const double *__restrict_
 // Algorithm 2, first step: beta = ||b||, V[0] = b / beta (and its binary32 copy), T_m
 // cleared, the control block reset, and the WHILE conditional set to run the loop
 // unless b is zero or not finite.
-template <bool COOP>
+template <int MODE>
 __device__ __forceinline__ void init_v0_body(const double *__restrict__ b, int n, double *part, int ld, double *V,
                                              float *Vf, double *scal, int *flags, int use_handle,
                                              cudaGraphConditionalHandle h, double *T, int nT) {
   __shared__ double red[kRedWords];
   __shared__ double c[34];
-  for (int i = g_first<COOP>(); i < nT; i += g_stride<COOP>()) T[i] = 0.0;
+  __shared__ double cslot[MODE == kCluster ? kSlot : 1];
+  for (int i = g_first<MODE>(); i < nT; i += g_stride<MODE>()) T[i] = 0.0;
   double s = 0.0;
-  for (int j = g_first<COOP>(); j < n; j += g_stride<COOP>()) s += b[j] * b[j];
-  const double beta = sqrt(grid_sum<COOP>(s, part, ld, red, c));
+  for (int j = g_first<MODE>(); j < n; j += g_stride<MODE>()) s += b[j] * b[j];
+  const double beta = sqrt(grid_sum<MODE>(s, MODE == kCluster ? cslot : part, ld, red, c));
   const bool zero = !(beta > 0.0);
   const double ib = zero ? 0.0 : 1.0 / beta;
-  for (int j = g_first<COOP>(); j < n; j += g_stride<COOP>()) {
+  for (int j = g_first<MODE>(); j < n; j += g_stride<MODE>()) {
     V[j] = b[j] * ib;
     if (Vf) Vf[j] = (float)V[j];
   }
-  if (g_leader<COOP>()) {
+  if (g_leader<MODE>()) {
     const bool finite = isfinite(beta);
     scal[S_BETA] = beta;
     scal[S_T] = 0.0;
@@ -172,32 +209,40 @@ __device__ __forceinline__ void init_v0_body(const double *__restrict__ b, int n
     flags[F_KCONV] = zero ? 1 : 0;
     if (use_handle) cudaGraphSetConditional(h, run ? 1u : 0u);
   }
+  cluster_exit<MODE>();
 }
 
 // eq. (13): ||r_m|| = |tau t_{m+1,m}| ||(I - V_m V_m^T) z|| with two CGS passes (z is
 // overwritten by its projection; zero after a breakdown), then the stopping decision.
-template <bool COOP>
+template <int MODE>
 __device__ __forceinline__ void project_body(int n, const double *__restrict__ V, double *z, double tau, double *part,
                                              int ld, double *scal, int *flags, const KrylovCtl &kc, int use_handle,
                                              cudaGraphConditionalHandle h) {
   __shared__ double red[kRedWords];
   __shared__ double c[34];
   const int m = flags[F_M] + 1;
-  const int G = COOP ? (int)gridDim.x : 1;
+  __shared__ double cslot[MODE == kCluster ? 3 * kSlot : 1];
+  const int G = MODE == kCoop ? (int)gridDim.x : 1;
   double *pa = part, *pb = part + (size_t)G * ld, *pc = part + (size_t)2 * G * ld;
-  grid_dots<COOP>(n, m, V, z, pa, ld, red, c);
-  cta_axpy<COOP>(n, m, V, z, c);
+  if constexpr (MODE == kCluster) {
+    pa = cslot;
+    pb = cslot + kSlot;
+    pc = cslot + 2 * kSlot;
+  }
+  grid_dots<MODE>(n, m, V, z, pa, ld, red, c);
+  cta_axpy<MODE>(n, m, V, z, c);
   __syncthreads();  // c is rewritten next
-  grid_dots<COOP>(n, m, V, z, pb, ld, red, c);
-  cta_axpy<COOP>(n, m, V, z, c);
+  grid_dots<MODE>(n, m, V, z, pb, ld, red, c);
+  cta_axpy<MODE>(n, m, V, z, c);
   __syncthreads();
   double s = 0.0;
-  for (int j = g_first<COOP>(); j < n; j += g_stride<COOP>()) s += z[j] * z[j];
-  const double zz = grid_sum<COOP>(s, pc, ld, red, c);
-  if (g_leader<COOP>()) {
+  for (int j = g_first<MODE>(); j < n; j += g_stride<MODE>()) s += z[j] * z[j];
+  const double zz = grid_sum<MODE>(s, pc, ld, red, c);
+  if (g_leader<MODE>()) {
     scal[S_RES] = flags[F_BREAK] ? 0.0 : fabs(tau * scal[S_T]) * sqrt(zz);
     krylov_decide(scal, flags, kc, use_handle, h);
   }
+  cluster_exit<MODE>();
 }
 
 // Argument bundles of those bodies when they run in the last CTA of another kernel.

@@ -185,6 +185,7 @@ struct pd_plan {
   int *mex = nullptr;  // per-problem residual scaling 2^mex of the next refinement sweep
   pd::PintGeom geom{};
   int blas_grid = 1, k5_grid = 1;
+  int blas_cluster = 0;  // CTAs of the cluster variant of the one-CTA Krylov kernels (0 = off)
   int64_t lds = 0;
 
   // device buffers
@@ -287,6 +288,9 @@ pd_status validate(const pd_desc *d) {
     return fail(PD_ERR_INVALID_ARG, "tune_pint_teams must be 0 or a power of two <= 16");
   if (d->tune_krylov_ctas < 0 || d->tune_krylov_ctas > 1024 || d->tune_cap_ctas < 0 || d->tune_cap_ctas > 1024)
     return fail(PD_ERR_INVALID_ARG, "tune_krylov_ctas and tune_cap_ctas must be in [0, 1024]");
+  if (d->tune_krylov_cluster != 0 && d->tune_krylov_cluster != -1 &&
+      (d->tune_krylov_cluster < 2 || d->tune_krylov_cluster > 16))
+    return fail(PD_ERR_INVALID_ARG, "tune_krylov_cluster must be 0, -1 or in [2, 16]");
   if (d->tune_fft_cols != 0 && d->tune_fft_cols != 2 && d->tune_fft_cols != 4 && d->tune_fft_cols != 8 &&
       d->tune_fft_cols != 16)
     return fail(PD_ERR_INVALID_ARG, "tune_fft_cols must be 0, 2, 4, 8 or 16");
@@ -356,6 +360,15 @@ void fill_geometry(pd_plan *p, const pd_desc *d) {
   // capacitance terms: one frequency per warp (four warps per CTA)
   p->k5_grid = std::max(1, std::min((p->nf + 3) / 4, 1024));
   if (d->tune_krylov_ctas) p->blas_grid = std::min(d->tune_krylov_ctas, sms);
+  // Vectors one CTA would hold: a cluster of 8 (n_bar <= 2048) or 16 CTAs, one per SM,
+  // spreads their FP64 work (GB300 runs FP64 at ~1/64 of the FP32 rate) over as many
+  // SMs, with reductions through distributed shared memory
+  p->blas_cluster = 0;
+  if (p->blas_grid == 1 && d->tune_krylov_cluster >= 0 && p->nbar >= 256) {
+    const int want = d->tune_krylov_cluster > 0 ? d->tune_krylov_cluster : (p->nbar <= 2048 ? 8 : 16);
+    p->blas_cluster = pd::krylov_cluster_size(want);
+    if (p->blas_cluster < 2) p->blas_cluster = 0;
+  }
   if (d->tune_cap_ctas) p->k5_grid = d->tune_cap_ctas;
   p->ctx.fft_cols = d->tune_fft_cols;
   p->ctx.pdl = d->tune_no_pdl == 0;
@@ -667,7 +680,7 @@ const cpx<float> *dst_tw<float>(pd_plan *p) { return p->twy_f; }
 template <typename T>
 pd::KrylovBufs kbufs(pd_plan *p) {
   return pd::KrylovBufs{(int)p->nbar, p->maxit, p->klo, p->kdiag, p->kup, p->V, sizeof(T) == 4 ? p->Vf : nullptr,
-                        p->T, p->w, p->part, p->blas_grid, p->scal, p->flags};
+                        p->T, p->w, p->part, p->blas_grid, p->scal, p->flags, p->blas_cluster};
 }
 
 // Algorithm-2 stopping parameters of the first solve (kind 0) and of refinement
@@ -754,7 +767,7 @@ pd_status emit_pre(pd_plan *p, int kind, const double *G, double *U, int use_han
   a.acc_part = p->acc_part;
   pd::launch_pint<T>(c, p->geom, a);
   pd::KrylovBufs kb = kbufs<T>(p);
-  if (kb.grid == 1) {  // one CTA holds the vectors: beta and v_1 in the reduction's last CTA
+  if (kb.grid == 1 && kb.cluster == 0) {  // one CTA: beta and v_1 in the reduction's last CTA
     const pd::InitTail t{1, p->flags + pd::F_ACCCNT, kb.n, kb.maxit + 2, (kb.maxit + 1) * kb.maxit, use_handle,
                          kb.part, kb.V, kb.scal, kb.T, kb.Vf, kb.flags, hk};
     pd::launch_acc_reduce(c, p->geom, p->acc_part, p->b, nullptr, &t);
@@ -788,7 +801,7 @@ pd_status emit_iter(pd_plan *p, int kind, int use_handle, cudaGraphConditionalHa
   pd::launch_capacitance(c, kb, p->nf, p->tau, p->shift, p->wga, p->gpart, p->nblk, p->msys_part, p->k5_grid,
                          p->srow, p->omega, p->y);
   // z = sum_i gamma_i h_i (e_m^T S_i y_m) from the stored h_i, then eq. (13)
-  if (kb.grid == 1) {  // eq. (13) and the decision in the z reduction's last CTA
+  if (kb.grid == 1 && kb.cluster == 0) {  // eq. (13) and the decision in the z reduction's last CTA
     const pd::ProjTail t{1, p->flags + pd::F_ZCNT, kb.n, kb.maxit + 2, use_handle, kb.V, p->tau, kb.part, kb.scal,
                          kb.flags, krylov_ctl(p, kind), hk};
     pd::launch_zsum<T>(c, p->nf, p->nbar, H, p->lds, p->omega, p->z, p->flags + pd::F_BREAK, &t);
