@@ -113,15 +113,16 @@ typedef struct pd_desc {
   int32_t tune_pint_teams;   /* teams (one tridiagonal block each) per CTA of that kernel:
                                 a power of two with teams * threads-per-team <= 512
                                 (<= 256 with 16 rows per thread) */
-  int32_t tune_krylov_ctas;  /* CTAs of the Krylov vector kernels: 1 = one 512-thread CTA,
-                                > 1 = cooperative launch of 64-thread CTAs (<= SM count) */
+  int32_t tune_krylov_ctas;  /* CTAs of the Krylov vector kernels: 1 = one 512-thread CTA
+                                (n_bar <= 8192), > 1 = cooperative launch of 64-thread CTAs
+                                (<= SM count) */
   int32_t tune_cap_ctas;     /* CTAs of the capacitance-term kernel, 1 .. 1024 */
   int32_t tune_fft_cols;     /* columns per CTA of the time FFTs: 2, 4, 8 or 16 */
   int32_t tune_no_pdl;       /* nonzero: launch kernels without programmatic dependent launch
                                 (by default a kernel may be scheduled while its predecessor
                                 drains; it waits for it before reading anything) */
   int32_t tune_krylov_cluster; /* where one CTA would run the Krylov vector kernels: -1 =
-                                keep that single CTA; 2 .. 16 = spread them over a
+                                keep that single CTA; 4 .. 16 = spread them over a
                                 thread-block cluster of that many CTAs, one per SM, with the
                                 reductions through distributed shared memory */
   /* Batching (1D only): `batch` independent problems with the same nt are solved

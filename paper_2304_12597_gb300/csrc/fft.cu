@@ -175,8 +175,9 @@ __global__ void __launch_bounds__(256) k_fft_r2c_res(const double *__restrict__ 
     for (int q = 0; q < kB; ++q) {
       const int j = j0 + q * ((int)blockDim.x / TX);
       if (j < n) {
-        const double au = fma(cu, ur[q], fma(cl, ul[q], cd * uc[q]));
-        const T r = (T)((g[q] + um[q]) - au) * msc;
+        // four FP64 operations per element (GB300 runs FP64 at ~1/64 of the FP32 rate)
+        const double res = fma(-cu, ur[q], fma(-cl, ul[q], fma(-cd, uc[q], g[q] + um[q])));
+        const T r = (T)res * msc;
         col_buf[2 * bitrev(j, logn)] = rs ? r * rs[j] : r;
       }
     }

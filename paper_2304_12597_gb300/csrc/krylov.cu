@@ -25,19 +25,19 @@
 namespace pd {
 
 // beta = ||b||, V[0] = b / beta; resets scal/flags.
-template <int MODE>
-__global__ void __launch_bounds__(MODE == kCoop ? kBlas : kBlasSingle)
+template <int MODE, int E>
+__global__ void __launch_bounds__(MODE == kCoop ? kBlas : MODE == kCluster ? kBlasCluster : kBlasSingle)
     k_init_v0_coop(const double *__restrict__ b, int n, double *part, int ld, double *V, float *Vf, double *scal,
                    int *flags, int use_handle, cudaGraphConditionalHandle h, double *T, int nT) {
   grid_dep_wait();
-  init_v0_body<MODE>(b, n, part, ld, V, Vf, scal, flags, use_handle, h, T, nT);
+  init_v0_body<MODE, E>(b, n, part, ld, V, Vf, scal, flags, use_handle, h, T, nT);
 }
 
 // One Arnoldi step (eq. 10): w = K v_{m-1}; two classical Gram-Schmidt passes
 // against v_0..v_{m-1} (their coefficients summed into column m-1 of T_m);
 // t = ||w||; v_m = w / t, or breakdown when t <= 1e-14 ||K v_{m-1}||.
-template <int MODE>
-__global__ void __launch_bounds__(MODE == kCoop ? kBlas : kBlasSingle) k_arnoldi_coop(int n, const double *__restrict__ klo,
+template <int MODE, int E>
+__global__ void __launch_bounds__(MODE == kCoop ? kBlas : MODE == kCluster ? kBlasCluster : kBlasSingle) k_arnoldi_coop(int n, const double *__restrict__ klo,
                                                         const double *__restrict__ kdiag,
                                                         const double *__restrict__ kup, double *V, float *Vf,
                                                         double *w, double *T, int ldT, double *part, int ld,
@@ -55,31 +55,73 @@ __global__ void __launch_bounds__(MODE == kCoop ? kBlas : kBlasSingle) k_arnoldi
     pc = cslot + 2 * kSlot;
   }
   const double *v = V + (int64_t)(m - 1) * n;
-  for (int j = g_first<MODE>(); j < n; j += g_stride<MODE>()) {
-    double x = kdiag[j] * v[j];
-    if (j > 0) x += klo[j] * v[j - 1];
-    if (j + 1 < n) x += kup[j] * v[j + 1];
-    w[j] = x;
-  }
-  grid_dots<MODE>(n, m, V, w, pa, ld, red, c);
-  const double knorm = sqrt(c[m]);
-  if ((MODE == kSingle || blockIdx.x == 0) && (int)threadIdx.x < m) T[(int64_t)threadIdx.x * ldT + (m - 1)] = c[threadIdx.x];
-  cta_axpy<MODE>(n, m, V, w, c);
-  __syncthreads();  // c is rewritten next
-  grid_dots<MODE>(n, m, V, w, pb, ld, red, c);
-  if ((MODE == kSingle || blockIdx.x == 0) && (int)threadIdx.x < m) T[(int64_t)threadIdx.x * ldT + (m - 1)] += c[threadIdx.x];
-  cta_axpy<MODE>(n, m, V, w, c);
-  __syncthreads();
-  double s = 0.0;
-  for (int j = g_first<MODE>(); j < n; j += g_stride<MODE>()) s += w[j] * w[j];
-  const double t = sqrt(grid_sum<MODE>(s, pc, ld, red, c));
-  const bool bd = !(t > 1e-14 * knorm);
-  const double it = bd ? 0.0 : 1.0 / t;
-  double *vm = V + (int64_t)m * n;
-  float *vmf = Vf ? Vf + (int64_t)m * n : nullptr;
-  for (int j = g_first<MODE>(); j < n; j += g_stride<MODE>()) {
-    vm[j] = w[j] * it;
-    if (vmf) vmf[j] = (float)vm[j];
+  double knorm, t;
+  bool bd;
+  if constexpr (MODE == kCoop) {
+    for (int j = g_first<MODE>(); j < n; j += g_stride<MODE>()) {
+      double x = kdiag[j] * v[j];
+      if (j > 0) x += klo[j] * v[j - 1];
+      if (j + 1 < n) x += kup[j] * v[j + 1];
+      w[j] = x;
+    }
+    grid_dots<MODE>(n, m, V, w, pa, ld, red, c);
+    knorm = sqrt(c[m]);
+    if (blockIdx.x == 0 && (int)threadIdx.x < m) T[(int64_t)threadIdx.x * ldT + (m - 1)] = c[threadIdx.x];
+    cta_axpy<MODE>(n, m, V, w, c);
+    __syncthreads();  // c is rewritten next
+    grid_dots<MODE>(n, m, V, w, pb, ld, red, c);
+    if (blockIdx.x == 0 && (int)threadIdx.x < m) T[(int64_t)threadIdx.x * ldT + (m - 1)] += c[threadIdx.x];
+    cta_axpy<MODE>(n, m, V, w, c);
+    __syncthreads();
+    double s = 0.0;
+    for (int j = g_first<MODE>(); j < n; j += g_stride<MODE>()) s += w[j] * w[j];
+    t = sqrt(grid_sum<MODE>(s, pc, ld, red, c));
+    bd = !(t > 1e-14 * knorm);
+    const double it = bd ? 0.0 : 1.0 / t;
+    double *vm = V + (int64_t)m * n;
+    float *vmf = Vf ? Vf + (int64_t)m * n : nullptr;
+    for (int j = g_first<MODE>(); j < n; j += g_stride<MODE>()) {
+      vm[j] = w[j] * it;
+      if (vmf) vmf[j] = (float)vm[j];
+    }
+  } else {  // w = K v_m held in registers through both CGS passes
+    const int f = g_first<MODE>(), st = g_stride<MODE>();
+    double x[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int j = f + e * st;
+      double a = 0.0;
+      if (j < n) {
+        a = kdiag[j] * v[j];
+        if (j > 0) a += klo[j] * v[j - 1];
+        if (j + 1 < n) a += kup[j] * v[j + 1];
+      }
+      x[e] = a;
+    }
+    const bool wr = (MODE == kSingle || blockIdx.x == 0) && (int)threadIdx.x < m;  // writes column m-1 of T
+    reg_dots<MODE, E>(n, m, V, x, pa, red, c);
+    knorm = sqrt(c[m]);
+    double tq = wr ? c[threadIdx.x] : 0.0;
+    reg_axpy<MODE, E>(n, m, V, x, c);
+    __syncthreads();  // c is rewritten next
+    reg_dots<MODE, E>(n, m, V, x, pb, red, c);
+    if (wr) T[(int64_t)threadIdx.x * ldT + (m - 1)] = tq + c[threadIdx.x];
+    reg_axpy<MODE, E>(n, m, V, x, c);
+    __syncthreads();
+    t = sqrt(reg_norm2<MODE, E>(x, pc, red, c));
+    bd = !(t > 1e-14 * knorm);
+    const double it = bd ? 0.0 : 1.0 / t;
+    double *vm = V + (int64_t)m * n;
+    float *vmf = Vf ? Vf + (int64_t)m * n : nullptr;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int j = f + e * st;
+      if (j < n) {
+        const double y = x[e] * it;
+        vm[j] = y;
+        if (vmf) vmf[j] = (float)y;
+      }
+    }
   }
   if (g_leader<MODE>()) {
     T[(int64_t)m * ldT + (m - 1)] = bd ? 0.0 : t;
@@ -92,12 +134,12 @@ __global__ void __launch_bounds__(MODE == kCoop ? kBlas : kBlasSingle) k_arnoldi
 }
 
 // eq. (13) and the stopping decision (project_body).
-template <int MODE>
-__global__ void __launch_bounds__(MODE == kCoop ? kBlas : kBlasSingle)
+template <int MODE, int E>
+__global__ void __launch_bounds__(MODE == kCoop ? kBlas : MODE == kCluster ? kBlasCluster : kBlasSingle)
     k_project_coop(int n, const double *__restrict__ V, double *z, double tau, double *part, int ld, double *scal,
                    int *flags, KrylovCtl kc, int use_handle, cudaGraphConditionalHandle h) {
   grid_dep_wait();
-  project_body<MODE>(n, V, z, tau, part, ld, scal, flags, kc, use_handle, h);
+  project_body<MODE, E>(n, V, z, tau, part, ld, scal, flags, kc, use_handle, h);
 }
 
 // ---- eq. (12): capacitance-system terms, one warp per frequency -----------------
@@ -307,7 +349,7 @@ __global__ void k_sumsq_final(const double *part, int nparts, double *dst) {
 // ---- FP64 all-at-once residual ---------------------------------------------------
 // r = G_t + u_{t-1} - [ (I + tau T_x) u_t  (+ tau T_y u_t in 2D) ] with the coefficient
 // arrays pre-scaled on the host: rx = (tau lo_x, 1 + tau diag_x, tau up_x),
-// ry = (tau lo_y, tau diag_y, tau up_y): five FP64 operations per point in 1D.
+// ry = (tau lo_y, tau diag_y, tau up_y): four FP64 operations per point in 1D.
 template <typename Tout, bool TWO_D>
 __global__ void k_residual(const double *__restrict__ G, const double *__restrict__ U, Tout *__restrict__ R,
                            int nb, int nx, const double *__restrict__ rxl, const double *__restrict__ rxd,
@@ -321,18 +363,17 @@ __global__ void k_residual(const double *__restrict__ G, const double *__restric
   const int iy = TWO_D ? j / nx : 0;
   const int ix = TWO_D ? j - iy * nx : j;
   const double uj = u[j];
-  double au = rxd[ix] * uj;
-  if (ix > 0) au = fma(rxl[ix], u[j - 1], au);
-  if (ix + 1 < nx) au = fma(rxu[ix], u[j + 1], au);
-  if (TWO_D) {
-    au = fma(ryd[iy], uj, au);
-    if (iy > 0) au = fma(ryl[iy], u[j - nx], au);
-    if (iy + 1 < ny) au = fma(ryu[iy], u[j + nx], au);
-  }
   const int64_t idx = t * nb + j;
-  double g = G[idx];
-  if (t > 0) g += U[idx - nb];
-  R[idx] = (Tout)(g - au);
+  double r = G[idx];
+  if (t > 0) r += U[idx - nb];
+  r = fma(-(TWO_D ? rxd[ix] + ryd[iy] : rxd[ix]), uj, r);
+  if (ix > 0) r = fma(-rxl[ix], u[j - 1], r);
+  if (ix + 1 < nx) r = fma(-rxu[ix], u[j + 1], r);
+  if (TWO_D) {
+    if (iy > 0) r = fma(-ryl[iy], u[j - nx], r);
+    if (iy + 1 < ny) r = fma(-ryu[iy], u[j + nx], r);
+  }
+  R[idx] = (Tout)r;
 }
 
 // ---- launchers -------------------------------------------------------------------
@@ -341,16 +382,17 @@ __global__ void k_residual(const double *__restrict__ G, const double *__restric
 // cudaLaunchKernelEx (capturable into a CUDA graph).
 // Cluster variant: one CTA per SM (the dynamic shared memory request keeps a second
 // CTA off the SM), kBlasCluster threads each.
-constexpr int kBlasCluster = 128;
 constexpr int kClusterSpreadSmem = 120 * 1024;
 
-// Largest cluster size <= want (halving, down to 2) the device can co-schedule for the
-// cluster variant of the vector kernels; 0 if none.
+// Largest cluster size <= want (halving, down to 4: with 128 threads per CTA and at most
+// 16 register-held entries per thread, 4 CTAs cover the 8192 entries one CTA would
+// take) the device can co-schedule for the cluster variant of the vector kernels; 0 if
+// none.
 int krylov_cluster_size(int want) {
-  const void *fn = (const void *)k_arnoldi_coop<kCluster>;
+  const void *fn = (const void *)k_arnoldi_coop<kCluster, 1>;
   cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kClusterSpreadSmem);
-  for (int cl = want; cl >= 2; cl >>= 1) {
+  for (int cl = want; cl >= 4; cl >>= 1) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)cl);
     cfg.blockDim = dim3(kBlasCluster);
@@ -368,6 +410,19 @@ int krylov_cluster_size(int want) {
   }
   return 0;
 }
+
+// Entries per thread of the register-resident variants: the smallest power of two
+// with E * threads >= n (the plan keeps n <= 8192 = 16 * 512 there).
+static int reg_elems(int n, int threads) {
+  int e = 1;
+  while (e < kEMax && e * threads < n) e <<= 1;
+  return e;
+}
+#define PD_BY_E(E, KERNEL, MODE)                                                              \
+  ((E) <= 1 ? (const void *)KERNEL<MODE, 1>                                                  \
+            : (E) == 2 ? (const void *)KERNEL<MODE, 2>                                       \
+                       : (E) == 4 ? (const void *)KERNEL<MODE, 4>                            \
+                                  : (E) == 8 ? (const void *)KERNEL<MODE, 8> : (const void *)KERNEL<MODE, 16>)
 
 static void coop_launch(Ctx &c, const char *fam, double bytes, const void *fn_single, const void *fn_coop,
                         const void *fn_cluster, int grid, int cluster, void **args) {
@@ -433,8 +488,9 @@ void launch_vec_norm_init(Ctx &c, KrylovBufs &k, const double *b, int use_handle
   double *T = k.T;
   int nT = (k.maxit + 1) * k.maxit;
   void *args[] = {(void *)&b, &n, &part, (void *)&ld, &V, &Vf, &scal, &flags, &use_handle, &h, &T, &nT};
-  coop_launch(c, "krylov_init", (double)k.n * 16, (const void *)k_init_v0_coop<kSingle>,
-              (const void *)k_init_v0_coop<kCoop>, (const void *)k_init_v0_coop<kCluster>, k.grid, k.cluster, args);
+  coop_launch(c, "krylov_init", (double)k.n * 16, PD_BY_E(reg_elems(k.n, kBlasSingle), k_init_v0_coop, kSingle),
+              (const void *)k_init_v0_coop<kCoop, 1>, PD_BY_E(reg_elems(k.n, k.cluster * kBlasCluster), k_init_v0_coop, kCluster),
+              k.grid, k.cluster, args);
 }
 
 // Partial buffers: k.part holds three (grid, maxit+2) panels.
@@ -447,8 +503,9 @@ void launch_arnoldi(Ctx &c, KrylovBufs &k) {
   int *flags = k.flags;
   void *args[] = {&n, (void *)&klo, (void *)&kdiag, (void *)&kup, &V, &Vf, &w, &T, &ldT, &part, (void *)&ld,
                   &scal, &flags};
-  coop_launch(c, "krylov_arnoldi", (double)k.n * 8.0 * 8, (const void *)k_arnoldi_coop<kSingle>,
-              (const void *)k_arnoldi_coop<kCoop>, (const void *)k_arnoldi_coop<kCluster>, k.grid, k.cluster, args);
+  coop_launch(c, "krylov_arnoldi", (double)k.n * 8.0 * 8, PD_BY_E(reg_elems(k.n, kBlasSingle), k_arnoldi_coop, kSingle),
+              (const void *)k_arnoldi_coop<kCoop, 1>, PD_BY_E(reg_elems(k.n, k.cluster * kBlasCluster), k_arnoldi_coop, kCluster),
+              k.grid, k.cluster, args);
 }
 
 void launch_capacitance(Ctx &c, KrylovBufs &k, int nf, double tau, const double2 *shift, const double2 *wg,
@@ -474,8 +531,9 @@ void launch_project_resnorm(Ctx &c, KrylovBufs &k, const double *z, double tau, 
   int *flags = k.flags;
   KrylovCtl kc = kc0;
   void *args[] = {&n, (void *)&V, &zz, &tau, &part, (void *)&ld, &scal, &flags, &kc, &use_handle, &h};
-  coop_launch(c, "krylov_project", (double)k.n * 8.0 * 6, (const void *)k_project_coop<kSingle>,
-              (const void *)k_project_coop<kCoop>, (const void *)k_project_coop<kCluster>, k.grid, k.cluster, args);
+  coop_launch(c, "krylov_project", (double)k.n * 8.0 * 6, PD_BY_E(reg_elems(k.n, kBlasSingle), k_project_coop, kSingle),
+              (const void *)k_project_coop<kCoop, 1>, PD_BY_E(reg_elems(k.n, k.cluster * kBlasCluster), k_project_coop, kCluster),
+              k.grid, k.cluster, args);
 }
 
 void launch_xm(Ctx &c, KrylovBufs &k, const double *y, double *x, float *xf) {

@@ -254,8 +254,8 @@ struct KrylovBufs {
 void launch_vec_norm_init(Ctx &c, KrylovBufs &k, const double *b, int use_handle,
                           cudaGraphConditionalHandle h);  // also zeroes T
 void launch_arnoldi(Ctx &c, KrylovBufs &k);
-// Largest cluster size <= want (halving) the device can co-schedule for the cluster
-// variant of the vector kernels (one CTA per SM); 0 if none.
+// Largest cluster size <= want (halving, >= 4) the device can co-schedule for the
+// cluster variant of the vector kernels (one CTA per SM); 0 if none.
 int krylov_cluster_size(int want);
 void launch_capacitance(Ctx &c, KrylovBufs &k, int nf, double tau, const double2 *shift,
                         const double2 *wg, const double2 *gpart, int nblk, double *msys_part,

@@ -9,6 +9,8 @@
 // cluster (the whole grid), each CTA keeps its partial sums in shared memory and the
 // others read them through distributed shared memory after a cluster barrier, so the
 // FP64 work of a vector step runs on several SMs without grid-wide barriers.
+// kTail: one CTA, streaming the vectors from memory with few registers (the tail
+// of another kernel, which keeps that kernel's register budget).
 // kSingle: one CTA owns the whole vector (short
 // vectors); it may be any CTA of a larger launch, since these bodies then ignore the
 // block index.
@@ -22,24 +24,25 @@ namespace pd {
 
 constexpr int kBlas = 64;          // CTA size of the cooperative variants
 constexpr int kBlasSingle = 512;   // threads of the one-CTA variants (short vectors)
+constexpr int kBlasCluster = 128;  // threads per CTA of the cluster variants
 constexpr int kRedQ = 4;           // sums reduced side by side
 constexpr int kRedWords = kRedQ * kBlasSingle;
-constexpr int kSingle = 0, kCoop = 1, kCluster = 2;  // MODE of the vector steps
+constexpr int kSingle = 0, kCoop = 1, kCluster = 2, kTail = 3;  // MODE of the vector steps
 constexpr int kSlot = 36;  // doubles per cluster-mode partial slot (m + 1 <= 33 sums)
 
 template <int MODE>
 __device__ __forceinline__ int g_first() {
-  if constexpr (MODE != kSingle) return blockIdx.x * blockDim.x + threadIdx.x;
+  if constexpr (MODE == kCoop || MODE == kCluster) return blockIdx.x * blockDim.x + threadIdx.x;
   return threadIdx.x;
 }
 template <int MODE>
 __device__ __forceinline__ int g_stride() {
-  if constexpr (MODE != kSingle) return gridDim.x * blockDim.x;
+  if constexpr (MODE == kCoop || MODE == kCluster) return gridDim.x * blockDim.x;
   return blockDim.x;
 }
 template <int MODE>
 __device__ __forceinline__ bool g_leader() {
-  if constexpr (MODE != kSingle) return blockIdx.x == 0 && threadIdx.x == 0;
+  if constexpr (MODE == kCoop || MODE == kCluster) return blockIdx.x == 0 && threadIdx.x == 0;
   return threadIdx.x == 0;
 }
 
@@ -134,7 +137,7 @@ __device__ __forceinline__ void grid_dots(int n, int m, const double *__restrict
     cta_dots<kCluster>(n, m, V, x, nullptr, red, panel);
     cluster_gather(panel, m + 1, c);
   } else {
-    cta_dots<kSingle>(n, m, V, x, nullptr, red, c);
+    cta_dots<MODE>(n, m, V, x, nullptr, red, c);
     __syncthreads();
   }
 }
@@ -173,10 +176,85 @@ __device__ __forceinline__ void cta_axpy(int n, int m, const double *__restrict_
   }
 }
 
+// Register-resident vectors (single CTA and cluster modes): thread entries
+// j = g_first + e * g_stride, e < E, held in registers for the whole step, so a step
+// reads its input vector once and the basis V through the read-only cache.  E (at most
+// kEMax) is the smallest power of two that covers n; each E is its own kernel, so the
+// unrolled loops stay as short as the vector needs.
+constexpr int kEMax = 16;
+
+template <int MODE, int E>
+__device__ __forceinline__ void reg_load(int n, const double *__restrict__ x, double (&r)[E]) {
+  const int f = g_first<MODE>(), st = g_stride<MODE>();
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int j = f + e * st;
+    r[e] = j < n ? x[j] : 0.0;
+  }
+}
+
+// c[q] = V[q] . x over the grid (q < m), c[m] = ||x||^2 (shared c, valid in every
+// thread on return); cluster mode combines the CTAs' sums through the shared `slot`.
+template <int MODE, int E>
+__device__ __forceinline__ void reg_dots(int n, int m, const double *V, const double (&x)[E], double *slot,
+                                         double *red, double *c) {
+  static_assert(MODE == kSingle || MODE == kCluster, "register-resident steps run in one CTA or one cluster");
+  __shared__ double out[kRedQ];
+  const int f = g_first<MODE>(), st = g_stride<MODE>();
+  double *dst = MODE == kCluster ? slot : c;
+  for (int q0 = 0; q0 <= m; q0 += kRedQ) {
+    const int nq = min(kRedQ, m + 1 - q0);
+    double s[kRedQ];
+#pragma unroll
+    for (int i = 0; i < kRedQ; ++i) s[i] = 0.0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int j = f + e * st;
+      if (j < n) {
+#pragma unroll
+        for (int i = 0; i < kRedQ; ++i) {
+          const int q = q0 + i;
+          if (i < nq) s[i] += (q < m ? __ldg(V + (int64_t)q * n + j) : x[e]) * x[e];
+        }
+      }
+    }
+    block_sums(s, nq, red, out);
+    if ((int)threadIdx.x < nq) dst[q0 + threadIdx.x] = out[threadIdx.x];
+  }
+  if constexpr (MODE == kCluster) {
+    cluster_gather(slot, m + 1, c);
+  } else {
+    __syncthreads();
+  }
+}
+
+// x -= sum_{q<m} c[q] V[q] on this thread's entries.
+template <int MODE, int E>
+__device__ __forceinline__ void reg_axpy(int n, int m, const double *V, double (&x)[E], const double *c) {
+  const int f = g_first<MODE>(), st = g_stride<MODE>();
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int j = f + e * st;
+    if (j < n) {
+      double xj = x[e];
+      for (int q = 0; q < m; ++q) xj -= c[q] * __ldg(V + (int64_t)q * n + j);
+      x[e] = xj;
+    }
+  }
+}
+
+template <int MODE, int E>
+__device__ __forceinline__ double reg_norm2(const double (&x)[E], double *slot, double *red, double *c) {
+  double s = 0.0;
+#pragma unroll
+  for (int e = 0; e < E; ++e) s += x[e] * x[e];  // entries past n are zero
+  return grid_sum<MODE>(s, slot, 0, red, c);
+}
+
 // Algorithm 2, first step: beta = ||b||, V[0] = b / beta (and its binary32 copy), T_m
 // cleared, the control block reset, and the WHILE conditional set to run the loop
 // unless b is zero or not finite.
-template <int MODE>
+template <int MODE, int E = 1>
 __device__ __forceinline__ void init_v0_body(const double *__restrict__ b, int n, double *part, int ld, double *V,
                                              float *Vf, double *scal, int *flags, int use_handle,
                                              cudaGraphConditionalHandle h, double *T, int nT) {
@@ -184,15 +262,33 @@ __device__ __forceinline__ void init_v0_body(const double *__restrict__ b, int n
   __shared__ double c[34];
   __shared__ double cslot[MODE == kCluster ? kSlot : 1];
   for (int i = g_first<MODE>(); i < nT; i += g_stride<MODE>()) T[i] = 0.0;
-  double s = 0.0;
-  for (int j = g_first<MODE>(); j < n; j += g_stride<MODE>()) s += b[j] * b[j];
-  const double beta = sqrt(grid_sum<MODE>(s, MODE == kCluster ? cslot : part, ld, red, c));
-  const bool zero = !(beta > 0.0);
-  const double ib = zero ? 0.0 : 1.0 / beta;
-  for (int j = g_first<MODE>(); j < n; j += g_stride<MODE>()) {
-    V[j] = b[j] * ib;
-    if (Vf) Vf[j] = (float)V[j];
+  double beta;
+  if constexpr (MODE == kCoop || MODE == kTail) {
+    double s = 0.0;
+    for (int j = g_first<MODE>(); j < n; j += g_stride<MODE>()) s += b[j] * b[j];
+    beta = sqrt(grid_sum<MODE>(s, part, ld, red, c));
+    const double ib = beta > 0.0 ? 1.0 / beta : 0.0;
+    for (int j = g_first<MODE>(); j < n; j += g_stride<MODE>()) {
+      V[j] = b[j] * ib;
+      if (Vf) Vf[j] = (float)V[j];
+    }
+  } else {
+    double x[E];
+    reg_load<MODE, E>(n, b, x);
+    beta = sqrt(reg_norm2<MODE, E>(x, cslot, red, c));
+    const double ib = beta > 0.0 ? 1.0 / beta : 0.0;
+    const int f = g_first<MODE>(), st = g_stride<MODE>();
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int j = f + e * st;
+      if (j < n) {
+        const double v = x[e] * ib;
+        V[j] = v;
+        if (Vf) Vf[j] = (float)v;
+      }
+    }
   }
+  const bool zero = !(beta > 0.0);
   if (g_leader<MODE>()) {
     const bool finite = isfinite(beta);
     scal[S_BETA] = beta;
@@ -212,9 +308,10 @@ __device__ __forceinline__ void init_v0_body(const double *__restrict__ b, int n
   cluster_exit<MODE>();
 }
 
-// eq. (13): ||r_m|| = |tau t_{m+1,m}| ||(I - V_m V_m^T) z|| with two CGS passes (z is
-// overwritten by its projection; zero after a breakdown), then the stopping decision.
-template <int MODE>
+// eq. (13): ||r_m|| = |tau t_{m+1,m}| ||(I - V_m V_m^T) z|| with two CGS passes (zero
+// after a breakdown), then the stopping decision.  The cooperative variant overwrites z
+// with its projection.
+template <int MODE, int E = 1>
 __device__ __forceinline__ void project_body(int n, const double *__restrict__ V, double *z, double tau, double *part,
                                              int ld, double *scal, int *flags, const KrylovCtl &kc, int use_handle,
                                              cudaGraphConditionalHandle h) {
@@ -229,15 +326,28 @@ __device__ __forceinline__ void project_body(int n, const double *__restrict__ V
     pb = cslot + kSlot;
     pc = cslot + 2 * kSlot;
   }
-  grid_dots<MODE>(n, m, V, z, pa, ld, red, c);
-  cta_axpy<MODE>(n, m, V, z, c);
-  __syncthreads();  // c is rewritten next
-  grid_dots<MODE>(n, m, V, z, pb, ld, red, c);
-  cta_axpy<MODE>(n, m, V, z, c);
-  __syncthreads();
-  double s = 0.0;
-  for (int j = g_first<MODE>(); j < n; j += g_stride<MODE>()) s += z[j] * z[j];
-  const double zz = grid_sum<MODE>(s, pc, ld, red, c);
+  double zz;
+  if constexpr (MODE == kCoop || MODE == kTail) {
+    grid_dots<MODE>(n, m, V, z, pa, ld, red, c);
+    cta_axpy<MODE>(n, m, V, z, c);
+    __syncthreads();  // c is rewritten next
+    grid_dots<MODE>(n, m, V, z, pb, ld, red, c);
+    cta_axpy<MODE>(n, m, V, z, c);
+    __syncthreads();
+    double s = 0.0;
+    for (int j = g_first<MODE>(); j < n; j += g_stride<MODE>()) s += z[j] * z[j];
+    zz = grid_sum<MODE>(s, pc, ld, red, c);
+  } else {  // z projected in registers (z itself is left as it is)
+    double x[E];
+    reg_load<MODE, E>(n, z, x);
+    reg_dots<MODE, E>(n, m, V, x, pa, red, c);
+    reg_axpy<MODE, E>(n, m, V, x, c);
+    __syncthreads();  // c is rewritten next
+    reg_dots<MODE, E>(n, m, V, x, pb, red, c);
+    reg_axpy<MODE, E>(n, m, V, x, c);
+    __syncthreads();
+    zz = reg_norm2<MODE, E>(x, pc, red, c);
+  }
   if (g_leader<MODE>()) {
     scal[S_RES] = flags[F_BREAK] ? 0.0 : fabs(tau * scal[S_T]) * sqrt(zz);
     krylov_decide(scal, flags, kc, use_handle, h);

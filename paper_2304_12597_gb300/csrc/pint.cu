@@ -455,7 +455,7 @@ __global__ void __launch_bounds__(CW * RG) k_acc_reduce(int nblk, int blen, int 
   tot = colsum_finish<CW, RG>(tot, sm, tx, ty);
   if (ty == 0 && j < n) out[j] = tot;
   if (tail.enabled && last_cta_done(tail.counter)) {
-    init_v0_body<kSingle>(out, tail.n, tail.part, tail.ld, tail.V, tail.Vf, tail.scal, tail.flags, tail.use_handle,
+    init_v0_body<kTail>(out, tail.n, tail.part, tail.ld, tail.V, tail.Vf, tail.scal, tail.flags, tail.use_handle,
                         tail.h, tail.T, tail.nT);
     if (threadIdx.x == 0) *tail.counter = 0;
   }
@@ -504,7 +504,7 @@ __global__ void __launch_bounds__(CW * RG) k_zsum(int nf, int64_t n, const cpx<T
     if (ty == 0 && j < n) z[j] = tot;
   }
   if (tail.enabled && last_cta_done(tail.counter)) {
-    project_body<kSingle>(tail.n, tail.V, z, tail.tau, tail.part, tail.ld, tail.scal, tail.flags, tail.kc,
+    project_body<kTail>(tail.n, tail.V, z, tail.tau, tail.part, tail.ld, tail.scal, tail.flags, tail.kc,
                         tail.use_handle, tail.h);
     if (threadIdx.x == 0) *tail.counter = 0;
   }

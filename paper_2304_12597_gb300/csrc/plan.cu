@@ -289,8 +289,14 @@ pd_status validate(const pd_desc *d) {
   if (d->tune_krylov_ctas < 0 || d->tune_krylov_ctas > 1024 || d->tune_cap_ctas < 0 || d->tune_cap_ctas > 1024)
     return fail(PD_ERR_INVALID_ARG, "tune_krylov_ctas and tune_cap_ctas must be in [0, 1024]");
   if (d->tune_krylov_cluster != 0 && d->tune_krylov_cluster != -1 &&
-      (d->tune_krylov_cluster < 2 || d->tune_krylov_cluster > 16))
-    return fail(PD_ERR_INVALID_ARG, "tune_krylov_cluster must be 0, -1 or in [2, 16]");
+      (d->tune_krylov_cluster < 4 || d->tune_krylov_cluster > 16))
+    return fail(PD_ERR_INVALID_ARG, "tune_krylov_cluster must be 0, -1 or in [4, 16]");
+  {  // one CTA (or one cluster) holds at most 16 vector entries per thread
+    const int64_t nbar = d->nx * (d->dim == 2 ? d->ny : 1) * (d->batch > 1 ? d->batch : 1);
+    if (d->tune_krylov_ctas == 1 && nbar > 8192)
+      return fail(PD_ERR_UNSUPPORTED, "tune_krylov_ctas = 1 (one CTA) needs n_bar <= 8192, got %lld",
+                  (long long)nbar);
+  }
   if (d->tune_fft_cols != 0 && d->tune_fft_cols != 2 && d->tune_fft_cols != 4 && d->tune_fft_cols != 8 &&
       d->tune_fft_cols != 16)
     return fail(PD_ERR_INVALID_ARG, "tune_fft_cols must be 0, 2, 4, 8 or 16");
@@ -367,7 +373,7 @@ void fill_geometry(pd_plan *p, const pd_desc *d) {
   if (p->blas_grid == 1 && d->tune_krylov_cluster >= 0 && p->nbar >= 256) {
     const int want = d->tune_krylov_cluster > 0 ? d->tune_krylov_cluster : (p->nbar <= 2048 ? 8 : 16);
     p->blas_cluster = pd::krylov_cluster_size(want);
-    if (p->blas_cluster < 2) p->blas_cluster = 0;
+    if (p->blas_cluster < 4) p->blas_cluster = 0;
   }
   if (d->tune_cap_ctas) p->k5_grid = d->tune_cap_ctas;
   p->ctx.fft_cols = d->tune_fft_cols;
