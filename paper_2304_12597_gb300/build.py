@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libparadiag_gb300.so")
-SOURCES = ["fft.cu", "pint.cu", "krylov.cu", "control.cu", "plan.cu", "noalloc.cu", "batch.cu"]
+SOURCES = ["fft.cu", "pint.cu", "krylov.cu", "krylov_members.cu", "control.cu", "plan.cu", "noalloc.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

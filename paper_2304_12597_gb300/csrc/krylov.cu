@@ -99,14 +99,14 @@ __global__ void __launch_bounds__(MODE == kCoop ? kBlas : MODE == kCluster ? kBl
       x[e] = a;
     }
     const bool wr = (MODE == kSingle || blockIdx.x == 0) && (int)threadIdx.x < m;  // writes column m-1 of T
-    reg_dots<MODE, E>(n, m, V, x, pa, red, c);
+    reg_dots<MODE, E>(n, m, V, n, x, pa, red, c);
     knorm = sqrt(c[m]);
     double tq = wr ? c[threadIdx.x] : 0.0;
-    reg_axpy<MODE, E>(n, m, V, x, c);
+    reg_axpy<MODE, E>(n, m, V, n, x, c);
     __syncthreads();  // c is rewritten next
-    reg_dots<MODE, E>(n, m, V, x, pb, red, c);
+    reg_dots<MODE, E>(n, m, V, n, x, pb, red, c);
     if (wr) T[(int64_t)threadIdx.x * ldT + (m - 1)] = tq + c[threadIdx.x];
-    reg_axpy<MODE, E>(n, m, V, x, c);
+    reg_axpy<MODE, E>(n, m, V, n, x, c);
     __syncthreads();
     t = sqrt(reg_norm2<MODE, E>(x, pc, red, c));
     bd = !(t > 1e-14 * knorm);
@@ -210,9 +210,20 @@ __host__ __device__ inline size_t k5a_warp_bytes(int m) {
 __global__ void __launch_bounds__(kK5Warps * 32) k_capacitance_terms(
     int nf, int maxit, double tau, const double *__restrict__ T, const double2 *__restrict__ shift,
     const double2 *__restrict__ wg, const double2 *__restrict__ gpart, int nblk, double *msys_part,
-    double2 *srow, const double *scal, int *flags, double2 *omega, double *y) {
+    double2 *srow, const double *scal, int *flags, double2 *omega, double *y, int members) {
   grid_dep_wait();
   extern __shared__ __align__(16) unsigned char smraw[];
+  if (members) {  // member blockIdx.y of a batch: its own Algorithm-2 state (strided views)
+    const int mb = blockIdx.y;
+    T += (int64_t)mb * (maxit + 1) * maxit;
+    msys_part += (int64_t)mb * gridDim.x * maxit * maxit;
+    srow += (int64_t)mb * nf * maxit;
+    omega += (int64_t)mb * nf;
+    y += (int64_t)mb * (maxit + 1);
+    scal += (int64_t)mb * kScalWords;
+    flags += (int64_t)mb * kFlagWords;
+    if (flags[F_KSTOP]) return;  // this member's Algorithm 2 has stopped (whole CTA)
+  }
   const int m = flags[F_M] + 1;
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const size_t wb = k5a_warp_bytes(m);
@@ -234,8 +245,10 @@ __global__ void __launch_bounds__(kK5Warps * 32) k_capacitance_terms(
         H[q * m + lane] = mk<double>(tau * tq + (q == lane ? sk.x : 0.0), q == lane ? sk.y : 0.0);
       }
       double gx = 0.0, gy = 0.0;
-      // after a breakdown the dot pass was skipped and the t-term vanishes
-      for (int b = 0; b < (flags[F_BREAK] ? 0 : nblk); ++b) {
+      // after a breakdown the dot pass was skipped and the t-term vanishes; a batch
+      // member takes only its own block's dots
+      const int b0 = members ? (int)blockIdx.y : 0, b1 = members ? b0 + 1 : nblk;
+      for (int b = b0; b < (flags[F_BREAK] ? b0 : b1); ++b) {
         const double2 v = gpart[((int64_t)k * nblk + b) * m + lane];
         gx += v.x;
         gy += v.y;
@@ -275,6 +288,8 @@ __global__ void __launch_bounds__(kK5Warps * 32) k_capacitance_terms(
   if (last) {
     __threadfence();
     capacitance_solve_cta(nf, m, gridDim.x, msys_part, wg, srow, omega, y, scal, smraw);
+    if (members)  // x_m = V y_m then runs over every step of the batch: zero the rest
+      for (int q = m + threadIdx.x; q <= maxit; q += blockDim.x) y[q] = 0.0;
     if (threadIdx.x == 0) flags[F_CAPCNT] = 0;
   }
 }
@@ -411,13 +426,6 @@ int krylov_cluster_size(int want) {
   return 0;
 }
 
-// Entries per thread of the register-resident variants: the smallest power of two
-// with E * threads >= n (the plan keeps n <= 8192 = 16 * 512 there).
-static int reg_elems(int n, int threads) {
-  int e = 1;
-  while (e < kEMax && e * threads < n) e <<= 1;
-  return e;
-}
 #define PD_BY_E(E, KERNEL, MODE)                                                              \
   ((E) <= 1 ? (const void *)KERNEL<MODE, 1>                                                  \
             : (E) == 2 ? (const void *)KERNEL<MODE, 2>                                       \
@@ -510,13 +518,13 @@ void launch_arnoldi(Ctx &c, KrylovBufs &k) {
 
 void launch_capacitance(Ctx &c, KrylovBufs &k, int nf, double tau, const double2 *shift, const double2 *wg,
                         const double2 *gpart, int nblk, double *msys_part, int k5_grid, double2 *srow,
-                        double2 *omega, double *y) {
+                        double2 *omega, double *y, int members) {
   const size_t smem = k5a_warp_bytes(k.maxit) * kK5Warps;  // sized for the largest m
   cudaFuncSetAttribute(k_capacitance_terms, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   c.launch("capacitance", (double)nf * nblk * 16, [&] {
-    pdl_launch(c.pdl, k_capacitance_terms, dim3(k5_grid), dim3(kK5Warps * 32), smem, c.stream, nf, k.maxit, tau,
-               (const double *)k.T, shift, wg, gpart, nblk,
-                                                                     msys_part, srow, k.scal, k.flags, omega, y);
+    pdl_launch(c.pdl, k_capacitance_terms, dim3(k5_grid, members ? members : 1), dim3(kK5Warps * 32), smem,
+               c.stream, nf, k.maxit, tau, (const double *)k.T, shift, wg, gpart, nblk, msys_part, srow,
+               members ? k.mscal : k.scal, members ? k.mflags : k.flags, omega, y, members);
   });
 }
 

@@ -133,6 +133,9 @@ __device__ __forceinline__ void refine_decide_members(double *scal, int *flags, 
   if (nonfinite) {
     flags[F_NONFIN] = 1;
     stop = true;
+  } else if (r.fp64 && flags[F_KCONV] && (s == 0 ? r.eps_first <= 1e-10 : r.eps_refine * relmax <= r.refine_tol)) {
+    // FP64, every problem's Algorithm 2 met its tolerance (as for a single problem)
+    conv = stop = true;
   } else if (all_conv && (s > 0 || relmax == 0.0)) {
     conv = stop = true;
   } else if (any_stall) {

@@ -30,6 +30,7 @@ enum FlagIndex {
   F_C2RCNT = 11,  // completion counter of the inverse DFT's finishing epilogue
   F_ACCCNT = 12,  // completion counter of the b reduction (runs the start of Algorithm 2)
   F_ZCNT = 13,    // completion counter of the z reduction (runs eq. 13 and the decision)
+  F_MEMCNT = 14,  // batched plans: members done in a per-member Algorithm-2 step
   F_SWM = 16,     // [16, 32): m of each solve
   kFlagWords = 64
 };
@@ -207,6 +208,7 @@ struct PintArgs {
   double2 *gpart;          // (nf, nblk, mdots) dot products y_k . V[q]
   const int *skip_flag;    // if non-null and *skip_flag != 0 the kernel does nothing
   double xm_scale;         // with xm_count: subtract xm_scale * x_m (alpha^{1/l} in Algorithm 3)
+  int64_t xm_ldy;          // block blk takes y_m from xm_y + blk * xm_ldy (0: one y_m)
 };
 template <typename T>
 void launch_pint(Ctx &c, const PintGeom &g, const PintArgs<T> &a);
@@ -216,7 +218,7 @@ struct ProjTail;  // pd_krylov.cuh: eq. 13 and the step decision run by the z re
 // with tail, the last CTA then projects z and decides the Algorithm-2 step.
 template <typename T>
 void launch_zsum(Ctx &c, int nf, int64_t n, const cpx<T> *H, int64_t ldh, const double2 *omega, double *z,
-                 const int *skip_flag, const ProjTail *tail = nullptr);
+                 const int *skip_flag, const ProjTail *tail = nullptr, int mlen = 0);
 // Batched plans (batch.cu): Gs = G with slot b scaled by 2^ex[b] ~ 1/||slot b||_F
 // (part: batch * nc doubles of scratch), and the inverse scaling of U in place with
 // the columns past problem b's nxb[b] rows set to zero.
@@ -248,6 +250,16 @@ struct KrylovBufs {
   double *scal;       // scalar block (see krylov.cu)
   int *flags;         // flag block (see krylov.cu)
   int cluster;        // grid == 1 only: > 0 runs the vector kernels on a cluster of this many CTAs
+  // Batched plans: `members` problems of `mlen` rows each run their own Algorithm 2
+  // (0 = one Algorithm 2 over the whole vector).  Member b's control blocks are
+  // mscal + b kScalWords and mflags + b kFlagWords, its T_m is T + b (maxit+1) maxit, its
+  // y_m is y + b (maxit+1); scal/flags above then hold the batch totals and the loop
+  // control, and `counter` counts the members done in a step.
+  int members, mlen;
+  double *mscal;
+  int *mflags;
+  double *y;
+  int *counter;
 };
 // All Algorithm-2 kernels read m from flags[F_M] (completed steps), so one captured
 // iteration serves every m.  `use_handle` / `h`: set a CUDA-graph conditional.
@@ -259,7 +271,15 @@ void launch_arnoldi(Ctx &c, KrylovBufs &k);
 int krylov_cluster_size(int want);
 void launch_capacitance(Ctx &c, KrylovBufs &k, int nf, double tau, const double2 *shift,
                         const double2 *wg, const double2 *gpart, int nblk, double *msys_part,
-                        int k5_grid, double2 *srow, double2 *omega, double *y);
+                        int k5_grid, double2 *srow, double2 *omega, double *y, int members = 0);
+// Batched plans, one Algorithm 2 per member (one CTA each; krylov_members.cu): the
+// start (beta_b, v_1), an Arnoldi step, and eq. (13) with the per-member decision; the
+// last member of the start and of eq. (13) sets the batch's control block and the
+// WHILE conditional (run while any member runs).
+void launch_member_init(Ctx &c, KrylovBufs &k, const double *b, int use_handle, cudaGraphConditionalHandle h);
+void launch_member_arnoldi(Ctx &c, KrylovBufs &k);
+void launch_member_project(Ctx &c, KrylovBufs &k, const double *z, double tau, const KrylovCtl &kc,
+                           int use_handle, cudaGraphConditionalHandle h);
 // eq. (13) and the Algorithm-2 stopping decision (krylov_decide) in one kernel
 void launch_project_resnorm(Ctx &c, KrylovBufs &k, const double *z, double tau, const KrylovCtl &kc,
                             int use_handle, cudaGraphConditionalHandle h);

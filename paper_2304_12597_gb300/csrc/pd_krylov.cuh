@@ -183,6 +183,14 @@ __device__ __forceinline__ void cta_axpy(int n, int m, const double *__restrict_
 // unrolled loops stay as short as the vector needs.
 constexpr int kEMax = 16;
 
+// Entries per thread of the register-resident variants: the smallest power of two
+// with E * threads >= n (the plan keeps n <= 8192 = 16 * 512 there).
+inline int reg_elems(int n, int threads) {
+  int e = 1;
+  while (e < kEMax && e * threads < n) e <<= 1;
+  return e;
+}
+
 template <int MODE, int E>
 __device__ __forceinline__ void reg_load(int n, const double *__restrict__ x, double (&r)[E]) {
   const int f = g_first<MODE>(), st = g_stride<MODE>();
@@ -196,7 +204,7 @@ __device__ __forceinline__ void reg_load(int n, const double *__restrict__ x, do
 // c[q] = V[q] . x over the grid (q < m), c[m] = ||x||^2 (shared c, valid in every
 // thread on return); cluster mode combines the CTAs' sums through the shared `slot`.
 template <int MODE, int E>
-__device__ __forceinline__ void reg_dots(int n, int m, const double *V, const double (&x)[E], double *slot,
+__device__ __forceinline__ void reg_dots(int n, int m, const double *V, int64_t ldv, const double (&x)[E], double *slot,
                                          double *red, double *c) {
   static_assert(MODE == kSingle || MODE == kCluster, "register-resident steps run in one CTA or one cluster");
   __shared__ double out[kRedQ];
@@ -214,7 +222,7 @@ __device__ __forceinline__ void reg_dots(int n, int m, const double *V, const do
 #pragma unroll
         for (int i = 0; i < kRedQ; ++i) {
           const int q = q0 + i;
-          if (i < nq) s[i] += (q < m ? __ldg(V + (int64_t)q * n + j) : x[e]) * x[e];
+          if (i < nq) s[i] += (q < m ? __ldg(V + q * ldv + j) : x[e]) * x[e];
         }
       }
     }
@@ -230,14 +238,14 @@ __device__ __forceinline__ void reg_dots(int n, int m, const double *V, const do
 
 // x -= sum_{q<m} c[q] V[q] on this thread's entries.
 template <int MODE, int E>
-__device__ __forceinline__ void reg_axpy(int n, int m, const double *V, double (&x)[E], const double *c) {
+__device__ __forceinline__ void reg_axpy(int n, int m, const double *V, int64_t ldv, double (&x)[E], const double *c) {
   const int f = g_first<MODE>(), st = g_stride<MODE>();
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int j = f + e * st;
     if (j < n) {
       double xj = x[e];
-      for (int q = 0; q < m; ++q) xj -= c[q] * __ldg(V + (int64_t)q * n + j);
+      for (int q = 0; q < m; ++q) xj -= c[q] * __ldg(V + q * ldv + j);
       x[e] = xj;
     }
   }
@@ -340,11 +348,11 @@ __device__ __forceinline__ void project_body(int n, const double *__restrict__ V
   } else {  // z projected in registers (z itself is left as it is)
     double x[E];
     reg_load<MODE, E>(n, z, x);
-    reg_dots<MODE, E>(n, m, V, x, pa, red, c);
-    reg_axpy<MODE, E>(n, m, V, x, c);
+    reg_dots<MODE, E>(n, m, V, n, x, pa, red, c);
+    reg_axpy<MODE, E>(n, m, V, n, x, c);
     __syncthreads();  // c is rewritten next
-    reg_dots<MODE, E>(n, m, V, x, pb, red, c);
-    reg_axpy<MODE, E>(n, m, V, x, c);
+    reg_dots<MODE, E>(n, m, V, n, x, pb, red, c);
+    reg_axpy<MODE, E>(n, m, V, n, x, c);
     __syncthreads();
     zz = reg_norm2<MODE, E>(x, pc, red, c);
   }

@@ -153,11 +153,12 @@ __global__ void __launch_bounds__(MAXT) k_pint(PintGeom g, PintArgs<T> a, size_t
   if (a.xm_count && active) {
     xs = acc;
     const int m = *a.xm_count;
+    const double *xy = a.xm_y + (int64_t)blk * a.xm_ldy;  // per-member y_m in batched plans
     T v[M];
 #pragma unroll
     for (int i = 0; i < M; ++i) v[i] = T(0);
     for (int q = 0; q < m; ++q) {
-      const T yq = (T)a.xm_y[q];
+      const T yq = (T)xy[q];
       const T *vq = a.V + (int64_t)q * a.ldv + off;
 #pragma unroll
       for (int i = 0; i < M; ++i)
@@ -171,7 +172,7 @@ __global__ void __launch_bounds__(MAXT) k_pint(PintGeom g, PintArgs<T> a, size_t
 #pragma unroll
       for (int i = 0; i < M; ++i) vd[i] = 0.0;
       for (int q = 0; q < m; ++q) {
-        const double yq = a.xm_y[q];
+        const double yq = xy[q];
         const double *vq = a.xm_Vd + (int64_t)q * a.ldv + off;
 #pragma unroll
         for (int i = 0; i < M; ++i)
@@ -468,7 +469,7 @@ __global__ void __launch_bounds__(CW * RG) k_acc_reduce(int nblk, int blen, int 
 template <typename T, int CW, int RG>
 __global__ void __launch_bounds__(CW * RG) k_zsum(int nf, int64_t n, const cpx<T> *__restrict__ H, int64_t ldh,
                                                   const double2 *__restrict__ omega, double *__restrict__ z,
-                                                  const int *skip_flag, ProjTail tail) {
+                                                  const int *skip_flag, ProjTail tail, int mlen) {
   grid_dep_wait();
   const bool skip = skip_flag && *skip_flag;  // breakdown: no z (eq. 13 gives 0); the tail still decides
   __shared__ double sm[RG][CW + 1];
@@ -476,13 +477,24 @@ __global__ void __launch_bounds__(CW * RG) k_zsum(int nf, int64_t n, const cpx<T
   cpx<T> *om = reinterpret_cast<cpx<T> *>(om_raw);
   const int tx = threadIdx.x % CW, ty = threadIdx.x / CW;
   if (!skip) {
-    for (int k = threadIdx.x; k < nf; k += CW * RG) om[k] = mk<T>((T)omega[k].x, (T)omega[k].y);
+    // batched plans with one Algorithm 2 per member (mlen rows each): column j takes
+    // the weights of its member; those of the CTA's first member are staged
+    const int mem0 = mlen ? (int)((int64_t)blockIdx.x * CW / mlen) : 0;
+    const double2 *om0 = omega + (int64_t)mem0 * nf;
+    for (int k = threadIdx.x; k < nf; k += CW * RG) om[k] = mk<T>((T)om0[k].x, (T)om0[k].y);
     __syncthreads();
     const int64_t j = (int64_t)blockIdx.x * CW + tx;
     T acc[kColB];
 #pragma unroll
     for (int u = 0; u < kColB; ++u) acc[u] = T(0);
-    if (j < n) {
+    const int memj = (mlen && j < n) ? (int)(j / mlen) : mem0;
+    if (j < n && memj != mem0) {  // a later member in this CTA: its weights from memory
+      const double2 *omj = omega + (int64_t)memj * nf;
+      for (int k = ty; k < nf; k += RG) {
+        const cpx<T> h = H[(int64_t)k * ldh + j];
+        acc[0] += (T)omj[k].x * h.x - (T)omj[k].y * h.y;
+      }
+    } else if (j < n) {
       for (int k0 = ty; k0 < nf; k0 += RG * kColB) {
         cpx<T> h[kColB];
 #pragma unroll
@@ -512,7 +524,7 @@ __global__ void __launch_bounds__(CW * RG) k_zsum(int nf, int64_t n, const cpx<T
 
 template <typename T>
 void launch_zsum(Ctx &c, int nf, int64_t n, const cpx<T> *H, int64_t ldh, const double2 *omega, double *z,
-                 const int *skip_flag, const ProjTail *tailp) {
+                 const int *skip_flag, const ProjTail *tailp, int mlen) {
   const size_t smem = (size_t)nf * sizeof(cpx<T>);
   ProjTail tail{};
   if (tailp) tail = *tailp;
@@ -520,20 +532,20 @@ void launch_zsum(Ctx &c, int nf, int64_t n, const cpx<T> *H, int64_t ldh, const 
     if (nf <= 256) {
       const int grid = (int)((n + 31) / 32);
       pdl_launch(c.pdl, k_zsum<T, 32, 16>, dim3(grid), dim3(512), smem, c.stream, nf, n, H, ldh, omega, z,
-                 skip_flag, tail);
+                 skip_flag, tail, mlen);
     } else {
       const int grid = (int)((n + 7) / 8);
       if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_zsum<T, 8, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       pdl_launch(c.pdl, k_zsum<T, 8, 64>, dim3(grid), dim3(512), smem, c.stream, nf, n, H, ldh, omega, z,
-                 skip_flag, tail);
+                 skip_flag, tail, mlen);
     }
   });
 }
 template void launch_zsum<double>(Ctx &, int, int64_t, const cpx<double> *, int64_t, const double2 *, double *,
-                                  const int *, const ProjTail *);
+                                  const int *, const ProjTail *, int);
 template void launch_zsum<float>(Ctx &, int, int64_t, const cpx<float> *, int64_t, const double2 *, double *,
-                                 const int *, const ProjTail *);
+                                 const int *, const ProjTail *, int);
 
 static int next_pow2(int v) {
   int p = 1;

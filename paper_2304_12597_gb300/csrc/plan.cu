@@ -159,7 +159,7 @@ struct pd_plan {
   int nf = 0;
   double tau = 0.0;
   double alpha = 1.0;  // Algorithm 3: C_alpha instead of C_1 (1 = Algorithm 1)
-  bool refined64 = false;  // FP64 plan that always refines (alpha < 1 or a batch)
+  bool refined64 = false;  // FP64 plan that always refines (alpha < 1)
   double aroot = 1.0;  // alpha^{1/l}
   int precision = PD_FP64;
   int maxit = 32;
@@ -183,6 +183,9 @@ struct pd_plan {
   double *colsum = nullptr;     // per-column ||delta||^2 of the last solve
   double *md2 = nullptr, *mref2 = nullptr, *mprev = nullptr;  // per-problem refinement state
   int *mex = nullptr;  // per-problem residual scaling 2^mex of the next refinement sweep
+  int members = 0;     // batched plans: one Algorithm 2 per problem (0 = one for the plan)
+  double *mscal = nullptr;  // per-problem Algorithm-2 scalar and flag blocks
+  int *mflags = nullptr;
   pd::PintGeom geom{};
   int blas_grid = 1, k5_grid = 1;
   int blas_cluster = 0;  // CTAs of the cluster variant of the one-CTA Krylov kernels (0 = off)
@@ -331,14 +334,13 @@ void fill_geometry(pd_plan *p, const pd_desc *d) {
   p->tau = p->batch > 1 ? 1.0 : d->tau;
   p->alpha = d->alpha > 0.0 ? d->alpha : 1.0;
   p->aroot = std::pow(p->alpha, 1.0 / (double)d->nt);
-  p->refined64 = d->precision == PD_FP64 && (p->alpha < 1.0 || d->batch > 1);
+  p->refined64 = d->precision == PD_FP64 && p->alpha < 1.0;
   p->precision = d->precision;
   p->maxit = d->maxit ? d->maxit : 32;
   p->eps = d->eps_krylov > 0 ? d->eps_krylov : (d->precision == PD_FP64 ? 1e-13 : 1e-5);
-  // FP64 plans that refine anyway use a loose tolerance per solve: a batch's single
-  // Krylov space must resolve the union of its problems' spectral content, and
-  // Algorithm 3 loses up to kappa(F D_alpha) per solve, so FP64 refinement sweeps
-  // with a few Krylov steps each beat one tight solve
+  // FP64 plans that refine anyway use a loose tolerance per solve: Algorithm 3 loses
+  // up to kappa(F D_alpha) per solve, so FP64 refinement sweeps with a few Krylov
+  // steps each beat one tight solve
   if (p->refined64 && !(d->eps_krylov > 0)) p->eps = 1e-5;
   // batches stop only when their slowest problem has converged: allow more sweeps
   p->max_refine = d->max_refine ? d->max_refine : (d->batch > 1 ? 16 : 8);
@@ -370,7 +372,9 @@ void fill_geometry(pd_plan *p, const pd_desc *d) {
   // spreads their FP64 work (GB300 runs FP64 at ~1/64 of the FP32 rate) over as many
   // SMs, with reductions through distributed shared memory
   p->blas_cluster = 0;
-  if (p->blas_grid == 1 && d->tune_krylov_cluster >= 0 && p->nbar >= 256) {
+  // batched plans: one Algorithm 2 per problem, one CTA each (see krylov_members.cu)
+  p->members = p->batch > 1 ? p->batch : 0;
+  if (!p->members && p->blas_grid == 1 && d->tune_krylov_cluster >= 0 && p->nbar >= 256) {
     const int want = d->tune_krylov_cluster > 0 ? d->tune_krylov_cluster : (p->nbar <= 2048 ? 8 : 16);
     p->blas_cluster = pd::krylov_cluster_size(want);
     if (p->blas_cluster < 4) p->blas_cluster = 0;
@@ -435,7 +439,8 @@ size_t layout(pd_plan *p, unsigned char *base) {
     p->Vf = A.take<float>((size_t)(mx + 1) * nbar);
     p->xf = A.take<float>(nbar);
   }
-  p->T = A.take<double>((size_t)(mx + 1) * mx);
+  const int nmem = std::max(1, p->members);  // Algorithm-2 states (one per batch member)
+  p->T = A.take<double>((size_t)(mx + 1) * mx * nmem);
   p->w = A.take<double>(nbar);
   p->part = A.take<double>((size_t)3 * p->blas_grid * (mx + 2));
   p->scal = A.take<double>(pd::kScalWords);
@@ -445,12 +450,16 @@ size_t layout(pd_plan *p, unsigned char *base) {
   p->x = A.take<double>(nbar);
   p->b0 = A.take<double>(nbar);
   p->x0 = A.take<double>(nbar);
-  p->y = A.take<double>(mx + 1);
+  p->y = A.take<double>((size_t)(mx + 1) * nmem);
   p->acc_part = A.take<double>((size_t)p->geom.nblk * p->geom.R * p->geom.blen);
   p->gpart = A.take<double2>((size_t)nf * p->nblk * mx);
-  p->srow = A.take<double2>((size_t)nf * mx);
-  p->omega = A.take<double2>(nf);
-  p->msys_part = A.take<double>((size_t)p->k5_grid * mx * mx);
+  p->srow = A.take<double2>((size_t)nf * mx * nmem);
+  p->omega = A.take<double2>((size_t)nf * nmem);
+  p->msys_part = A.take<double>((size_t)p->k5_grid * mx * mx * nmem);
+  if (p->members) {
+    p->mscal = A.take<double>((size_t)pd::kScalWords * nmem);
+    p->mflags = A.take<int>((size_t)pd::kFlagWords * nmem);
+  }
   p->norm_part = A.take<double>((size_t)std::max<int64_t>(nbar / 2 + 2, 8 * (int64_t)pd::sm_count()));
   if (mixed) p->res_f = A.take<float>((size_t)nt * nbar);
   if (mixed && p->dim == 2) p->tmp_f = A.take<float>((size_t)nt * nbar);
@@ -686,7 +695,8 @@ const cpx<float> *dst_tw<float>(pd_plan *p) { return p->twy_f; }
 template <typename T>
 pd::KrylovBufs kbufs(pd_plan *p) {
   return pd::KrylovBufs{(int)p->nbar, p->maxit, p->klo, p->kdiag, p->kup, p->V, sizeof(T) == 4 ? p->Vf : nullptr,
-                        p->T, p->w, p->part, p->blas_grid, p->scal, p->flags, p->blas_cluster};
+                        p->T, p->w, p->part, p->blas_grid, p->scal, p->flags, p->blas_cluster,
+                        p->members, (int)p->nxm, p->mscal, p->mflags, p->y, p->flags + pd::F_MEMCNT};
 }
 
 // Algorithm-2 stopping parameters of the first solve (kind 0) and of refinement
@@ -709,9 +719,6 @@ pd::KrylovCtl krylov_ctl(pd_plan *p, int kind) {
     k.win = 2;
   } else if (fp64 && kind == 1) {  // an FP64 refinement sweep only needs a contraction
     k.stall_floor = 1.0;
-    k.win = 2;
-  } else if (p->batch > 1) {  // mixed batches: the shared space needs a few more steps
-    if (kind == 1) k.eps = std::max(p->eps, 1e-4);
     k.win = 2;
   }
   k.maxit = p->maxit;
@@ -773,7 +780,10 @@ pd_status emit_pre(pd_plan *p, int kind, const double *G, double *U, int use_han
   a.acc_part = p->acc_part;
   pd::launch_pint<T>(c, p->geom, a);
   pd::KrylovBufs kb = kbufs<T>(p);
-  if (kb.grid == 1 && kb.cluster == 0) {  // one CTA: beta and v_1 in the reduction's last CTA
+  if (kb.members) {
+    pd::launch_acc_reduce(c, p->geom, p->acc_part, p->b, nullptr);
+    pd::launch_member_init(c, kb, p->b, use_handle, hk);
+  } else if (kb.grid == 1 && kb.cluster == 0) {  // one CTA: beta and v_1 in the reduction's last CTA
     const pd::InitTail t{1, p->flags + pd::F_ACCCNT, kb.n, kb.maxit + 2, (kb.maxit + 1) * kb.maxit, use_handle,
                          kb.part, kb.V, kb.scal, kb.T, kb.Vf, kb.flags, hk};
     pd::launch_acc_reduce(c, p->geom, p->acc_part, p->b, nullptr, &t);
@@ -789,7 +799,10 @@ template <typename T>
 pd_status emit_iter(pd_plan *p, int kind, int use_handle, cudaGraphConditionalHandle hk) {
   pd::Ctx &c = p->ctx;
   pd::KrylovBufs kb = kbufs<T>(p);
-  pd::launch_arnoldi(c, kb);
+  if (kb.members)
+    pd::launch_member_arnoldi(c, kb);
+  else
+    pd::launch_arnoldi(c, kb);
   cpx<T> *H = reinterpret_cast<cpx<T> *>(p->hbuf);
   {  // h_k = ((1 - pi_k) I + tau K)^{-1} v_{m+1} (stored) and g_k = V_m^T h_k
     pd::PintArgs<T> a = base_args<T>(p);
@@ -805,9 +818,12 @@ pd_status emit_iter(pd_plan *p, int kind, int use_handle, cudaGraphConditionalHa
     pd::launch_pint<T>(c, p->geom, a);
   }
   pd::launch_capacitance(c, kb, p->nf, p->tau, p->shift, p->wga, p->gpart, p->nblk, p->msys_part, p->k5_grid,
-                         p->srow, p->omega, p->y);
+                         p->srow, p->omega, p->y, kb.members);
   // z = sum_i gamma_i h_i (e_m^T S_i y_m) from the stored h_i, then eq. (13)
-  if (kb.grid == 1 && kb.cluster == 0) {  // eq. (13) and the decision in the z reduction's last CTA
+  if (kb.members) {
+    pd::launch_zsum<T>(c, p->nf, p->nbar, H, p->lds, p->omega, p->z, p->flags + pd::F_BREAK, nullptr, kb.mlen);
+    pd::launch_member_project(c, kb, p->z, p->tau, krylov_ctl(p, kind), use_handle, hk);
+  } else if (kb.grid == 1 && kb.cluster == 0) {  // eq. (13) and the decision in the z reduction's last CTA
     const pd::ProjTail t{1, p->flags + pd::F_ZCNT, kb.n, kb.maxit + 2, use_handle, kb.V, p->tau, kb.part, kb.scal,
                          kb.flags, krylov_ctl(p, kind), hk};
     pd::launch_zsum<T>(c, p->nf, p->nbar, H, p->lds, p->omega, p->z, p->flags + pd::F_BREAK, &t);
@@ -831,6 +847,7 @@ pd_status emit_post(pd_plan *p, int kind, double *U, int use_handle, cudaGraphCo
   a.ldr = p->lds;
   a.xm_count = p->flags + pd::F_M;  // x_m = V_m y_m formed by each team
   a.xm_y = p->y;
+  a.xm_ldy = p->members ? p->maxit + 1 : 0;  // batch member blk: its own y_m
   a.V = vbasis<T>(p);
   a.ldv = p->nbar;
   a.xm_Vd = p->V;
