@@ -3,10 +3,8 @@ block-diagonal problem must give, for every problem, the oracle's solution of th
 problem alone, within the same tolerances as single solves (1e-12 FP64, 1e-10 mixed),
 whatever the mix of sizes, time steps and magnitudes in the batch.
 
-Heterogeneous batches run with Algorithm 1 (alpha = 1) in FP64 and with Algorithm 3
-(alpha = 1e-4) in both precisions.  In mixed precision with alpha = 1, the shared Krylov
-space of very different problems can leave one problem above 1e-10 (the plan then
-reports PD_ERR_NOT_CONVERGED); batches of one operator are covered at alpha = 1.
+Every problem runs its own Algorithm 2, so heterogeneous batches are covered with
+Algorithm 1 (alpha = 1) and Algorithm 3 (alpha = 1e-4) in both precisions.
 """
 import numpy as np
 import pytest
@@ -53,7 +51,7 @@ def _mix(nt):
     ]
 
 
-MIXES = [("fp64", 1.0), ("fp64", 1e-4), ("mixed", 1e-4)]
+MIXES = [("fp64", 1.0), ("fp64", 1e-4), ("mixed", 1.0), ("mixed", 1e-4)]
 
 
 @pytest.mark.parametrize("prec,alpha", MIXES)
