@@ -125,6 +125,12 @@ typedef struct pd_desc {
                                 keep that single CTA; 4 .. 16 = spread them over a
                                 thread-block cluster of that many CTAs, one per SM, with the
                                 reductions through distributed shared memory */
+  int32_t tune_pint_factor;  /* 1: factor every shifted system once per operator (plan
+                                creation, paradiag_set_operator) and keep the factors (at
+                                most 4 GiB), so each parallel-in-time loop only solves; -1:
+                                eliminate in every loop; 0: factor PD_FP64 plans only (FP64
+                                elimination is costly on GB300; binary32 elimination costs
+                                less than streaming its factors) */
   /* Batching (1D only): `batch` independent problems with the same nt are solved
    * together as one block-diagonal problem (their DFTs, shifted solves, Krylov space
    * and refinement are shared; the blocks never couple).  Problem b occupies slot b:

@@ -61,6 +61,7 @@ class PdDesc(ctypes.Structure):
         ("tune_fft_cols", ctypes.c_int32),
         ("tune_no_pdl", ctypes.c_int32),
         ("tune_krylov_cluster", ctypes.c_int32),
+        ("tune_pint_factor", ctypes.c_int32),
         ("batch", ctypes.c_int32),
         ("batch_nx", ctypes.POINTER(ctypes.c_int64)),
         ("batch_tau", ctypes.POINTER(ctypes.c_double)),

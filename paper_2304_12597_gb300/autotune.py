@@ -26,6 +26,8 @@ def _candidates(plan_kw, nf):
         ("fft_cols", [0, 2, 4, 8, 16]),
         ("cap_ctas", sorted({0, max(1, (nf + 7) // 8), max(1, (nf + 3) // 4), max(1, (nf + 1) // 2)})),
         ("krylov_ctas", [0, 8, 16]),
+        ("pint_factor", [0, 1, -1]),
+        ("krylov_cluster", [0, -1, 16]),
     ]
 
 

@@ -209,7 +209,11 @@ struct PintArgs {
   const int *skip_flag;    // if non-null and *skip_flag != 0 the kernel does nothing
   double xm_scale;         // with xm_count: subtract xm_scale * x_m (alpha^{1/l} in Algorithm 3)
   int64_t xm_ldy;          // block blk takes y_m from xm_y + blk * xm_ldy (0: one y_m)
+  const cpx<T> *fac_in;    // precomputed factors of every (k, block) system (pint.cu), or null
+  cpx<T> *fac_out;         // factor pass: store those factors (R, rvec, Y, omega, V unused)
 };
+// Complex elements of the factor array of one plan geometry (pint.cu: fac_slots).
+size_t pint_factor_elems(const PintGeom &g);
 template <typename T>
 void launch_pint(Ctx &c, const PintGeom &g, const PintArgs<T> &a);
 struct InitTail;  // pd_krylov.cuh: the start of Algorithm 2 run by a reduction's last CTA

@@ -46,6 +46,42 @@ struct TeamSmem {
   }
 };
 
+// Precomputed factors of one frequency's shifted system (they depend on k and K only,
+// not on the right-hand side): per block and team thread t, the complex values below,
+// slot s of thread t at ((k nblk + blk) NS + s) P + t, so a warp reads 256 contiguous
+// bytes per slot.  Chunk rows i = 1..M-1 and PCR levels l = 0..L-1 (P = 2^L):
+//   rd_i   pivot reciprocals of the chunk elimination          slots 0 .. M-2
+//   ccf_i  forward cc_i (i <= M-3), for the backward sweep       M-1 .. 2M-5
+//   C0     the interface row's coupling to xe_t                   2M-4
+//   aa_i, cc_i after the backward sweep (back substitution)     2M-3 .. 4M-6
+//   k1_l, k2_l  PCR multipliers (zero past the team's ends)     4M-5 + 2l, +1
+//   1/B    of the reduced interface row                           4M-5 + 2L
+template <int M>
+__host__ __device__ constexpr int fs_rd(int i) { return i - 1; }
+template <int M>
+__host__ __device__ constexpr int fs_ccf(int i) { return M - 1 + i - 1; }
+template <int M>
+__host__ __device__ constexpr int fs_c0() { return 2 * M - 4; }
+template <int M>
+__host__ __device__ constexpr int fs_aa(int i) { return 2 * M - 3 + i - 1; }
+template <int M>
+__host__ __device__ constexpr int fs_cc(int i) { return 3 * M - 4 + i - 1; }
+template <int M>
+__host__ __device__ constexpr int fs_k1(int l) { return 4 * M - 5 + 2 * l; }
+template <int M>
+__host__ __device__ constexpr int fs_binv(int L) { return 4 * M - 5 + 2 * L; }
+__host__ __device__ inline int ilog2_pow2(int P) {
+  int L = 0;
+  while ((1 << L) < P) ++L;
+  return L;
+}
+// slots per (k, block, thread)
+__host__ __device__ inline int fac_slots(int M, int P) { return 4 * M - 4 + 2 * ilog2_pow2(P); }
+
+size_t pint_factor_elems(const PintGeom &g) {
+  return (size_t)g.nf * g.nblk * fac_slots(g.M, g.P) * g.P;
+}
+
 template <typename T>
 __device__ __forceinline__ void coef(const PintArgs<T> &a, const T *cs, int cs_stride, int64_t j, int ps, bool valid,
                                      cpx<T> s, T &lo, cpx<T> &d, T &up) {
@@ -68,7 +104,9 @@ __device__ __forceinline__ void coef(const PintArgs<T> &a, const T *cs, int cs_s
 
 // MAXT: the launch's thread count is at most MAXT (256 leaves room for 255
 // registers per thread, which the FP64 variants use without spilling).
-template <typename T, int M, int MAXT>
+// FACT: solve with a.fac_in (a separate instantiation, so that its register budget is
+// its own).
+template <typename T, int M, int MAXT, bool FACT>
 __global__ void __launch_bounds__(MAXT) k_pint(PintGeom g, PintArgs<T> a, size_t team_bytes) {
   grid_dep_wait();
   if (a.skip_flag && *a.skip_flag) return;
@@ -84,6 +122,9 @@ __global__ void __launch_bounds__(MAXT) k_pint(PintGeom g, PintArgs<T> a, size_t
   const int blen = g.blen;
   const int64_t off = (int64_t)blk * blen;
   const int N = P;  // condensed interface rows
+  const cpx<T> *fin = FACT ? a.fac_in : nullptr;  // precomputed factors (right-hand side only)
+  cpx<T> *fout = a.fac_out;      // store the factors (the right-hand side is zero)
+  const int NS = fac_slots(M, P);
   // elements per batch of back-to-back loads (fewer in FP64, where registers are scarcer)
   constexpr int SB = sizeof(T) == 8 ? (M < 4 ? M : 4) : M;
 
@@ -206,7 +247,7 @@ __global__ void __launch_bounds__(MAXT) k_pint(PintGeom g, PintArgs<T> a, size_t
               sub[i] = xs[e];
             else if (rv)
               sub[i] = rv[e];
-          } else {
+          } else if (rv) {
             v[i].x = rv[e];
           }
         }
@@ -220,8 +261,57 @@ __global__ void __launch_bounds__(MAXT) k_pint(PintGeom g, PintArgs<T> a, size_t
     }
     team_sync(P, tic);
 
+    if constexpr (FACT) {
+      // 2-4 with the frequency's factors precomputed (fac_slot layout): the same
+      // elimination, PCR and back substitution applied to the right-hand side only
+      const cpx<T> *F = fin + ((int64_t)k * g.nblk + blk) * ((int64_t)NS * P) + t;
+      T lo0, up0;
+      cpx<T> d0;
+      coef(a, cs, cs_stride, off + e0, ps0, e0 < blen, s, lo0, d0, up0);
+      cpx<T> r[M];
+#pragma unroll
+      for (int i = 0; i < M; ++i) r[i] = my[i];
+      r[1] = mul(r[1], F[fs_rd<M>(1) * P]);
+#pragma unroll
+      for (int i = 2; i < M; ++i) {
+        T lo, up;
+        cpx<T> d;
+        coef(a, cs, cs_stride, off + e0 + i, ps0 + i, e0 + i < blen, s, lo, d, up);
+        r[i] = mul(fnms_r(r[i], lo, r[i - 1]), F[fs_rd<M>(i) * P]);
+      }
+#pragma unroll
+      for (int i = M - 3; i >= 1; --i) r[i] = fnms(r[i], F[fs_ccf<M>(i) * P], r[i + 1]);
+      const cpx<T> D0 = fnms_r(r[0], up0, r[1]);
+      const cpx<T> D1 = r[M - 1];
+      pd[t] = D1;
+      team_sync(P, tic);
+      const cpx<T> pD1 = t > 0 ? pd[t - 1] : mk<T>(T(0), T(0));
+      cpx<T> D = fnms(fnms_r(D0, lo0, pD1), F[fs_c0<M>() * P], D1);
+      // PCR on the right-hand side, double-buffered in pa / pb (one barrier per level)
+      int l = 0;
+      for (int sig = 1; sig < P; sig <<= 1, ++l) {
+        cpx<T> *bw = (l & 1) ? pb : pa;
+        bw[t] = D;
+        team_sync(P, tic);
+        cpx<T> nD = D;
+        if (t - sig >= 0) nD = fnms(nD, F[fs_k1<M>(l) * P], bw[t - sig]);
+        if (t + sig < P) nD = fnms(nD, F[(fs_k1<M>(l) + 1) * P], bw[t + sig]);
+        D = nD;
+      }
+      const cpx<T> xf = mul(D, F[fs_binv<M>(l) * P]);
+      pd[t] = xf;
+      team_sync(P, tic);
+      const cpx<T> xnext = t + 1 < P ? pd[t + 1] : mk<T>(T(0), T(0));
+      const cpx<T> xl = fnms(fnms(D1, F[fs_aa<M>(M - 1) * P], xf), F[fs_cc<M>(M - 1) * P], xnext);
+      my[0] = xf;
+#pragma unroll
+      for (int i = 1; i < M - 1; ++i) my[i] = fnms(fnms(r[i], F[fs_aa<M>(i) * P], xf), F[fs_cc<M>(i) * P], xl);
+      my[M - 1] = xl;
+    } else {
     // 2. chunk elimination: row i of the chunk becomes x_i + aa_i x_0 + cc_i x_{M-1} = dd_i
     cpx<T> aa[M], cc[M];
+    // with fout: this frequency's factors are stored (RHS-independent; see fac_slot)
+    cpx<T> *F = fout ? fout + ((int64_t)k * g.nblk + blk) * ((int64_t)NS * P) + t : nullptr;
     T lo0, up0;
     cpx<T> d0;
     coef(a, cs, cs_stride, off + e0, ps0, e0 < blen, s, lo0, d0, up0);
@@ -234,6 +324,10 @@ __global__ void __launch_bounds__(MAXT) k_pint(PintGeom g, PintArgs<T> a, size_t
       aa[1] = scal(lo, rb);
       cc[1] = scal(up, rb);
       my[1] = mul(my[1], rb);
+      if (F) {
+        F[fs_rd<M>(1) * P] = rb;
+        if (1 <= M - 3) F[fs_ccf<M>(1) * P] = cc[1];
+      }
     }
 #pragma unroll
     for (int i = 2; i < M; ++i) {
@@ -244,6 +338,10 @@ __global__ void __launch_bounds__(MAXT) k_pint(PintGeom g, PintArgs<T> a, size_t
       aa[i] = scal(-lo, mul(aa[i - 1], rd));
       cc[i] = scal(up, rd);
       my[i] = mul(fnms_r(my[i], lo, my[i - 1]), rd);
+      if (F) {
+        F[fs_rd<M>(i) * P] = rd;
+        if (i <= M - 3) F[fs_ccf<M>(i) * P] = cc[i];
+      }
     }
 #pragma unroll
     for (int i = M - 3; i >= 1; --i) {
@@ -260,6 +358,14 @@ __global__ void __launch_bounds__(MAXT) k_pint(PintGeom g, PintArgs<T> a, size_t
     const cpx<T> D0 = fnms_r(r0, up0, my[1]);
     const cpx<T> A1 = aa[M - 1];
     const cpx<T> C1 = cc[M - 1];
+    if (F) {
+      F[fs_c0<M>() * P] = C0;
+#pragma unroll
+      for (int i = 1; i < M; ++i) {
+        F[fs_aa<M>(i) * P] = aa[i];
+        F[fs_cc<M>(i) * P] = cc[i];
+      }
+    }
     const cpx<T> D1 = my[M - 1];
 
     // 3a. eliminate every xe with the last rows: P rows in the xs alone, one per thread
@@ -282,27 +388,35 @@ __global__ void __launch_bounds__(MAXT) k_pint(PintGeom g, PintArgs<T> a, size_t
     team_sync(P, tic);
 
     // 3b. PCR on the P condensed rows
-    for (int sig = 1; sig < P; sig <<= 1) {
+    int lvl = 0;
+    for (int sig = 1; sig < P; sig <<= 1, ++lvl) {
       pa[t] = A; pb[t] = B; pc[t] = C; pd[t] = D; pib[t] = recip(B);
       team_sync(P, tic);
       cpx<T> nA = mk<T>(T(0), T(0)), nB = B, nC = mk<T>(T(0), T(0)), nD = D;
       const int lo = t - sig, hi = t + sig;
+      cpx<T> k1 = mk<T>(T(0), T(0)), k2 = mk<T>(T(0), T(0));
       if (lo >= 0) {
-        const cpx<T> k1 = mul(A, pib[lo]);
+        k1 = mul(A, pib[lo]);
         nA = fnms(nA, k1, pa[lo]);
         nB = fnms(nB, k1, pc[lo]);
         nD = fnms(nD, k1, pd[lo]);
       }
       if (hi < P) {
-        const cpx<T> k2 = mul(C, pib[hi]);
+        k2 = mul(C, pib[hi]);
         nC = fnms(nC, k2, pc[hi]);
         nB = fnms(nB, k2, pa[hi]);
         nD = fnms(nD, k2, pd[hi]);
       }
+      if (F) {
+        F[fs_k1<M>(lvl) * P] = k1;
+        F[(fs_k1<M>(lvl) + 1) * P] = k2;
+      }
       team_sync(P, tic);
       A = nA; B = nB; C = nC; D = nD;
     }
-    const cpx<T> xf = mul(D, recip(B));
+    const cpx<T> rB = recip(B);
+    if (F) F[fs_binv<M>(lvl) * P] = rB;
+    const cpx<T> xf = mul(D, rB);
     // 3c. recover xe_t from the last row and xs_{t+1}
     pd[t] = xf;
     team_sync(P, tic);
@@ -314,6 +428,7 @@ __global__ void __launch_bounds__(MAXT) k_pint(PintGeom g, PintArgs<T> a, size_t
 #pragma unroll
     for (int i = 1; i < M - 1; ++i) my[i] = fnms(fnms(my[i], aa[i], xf), cc[i], xl);
     my[M - 1] = xl;
+    }
     if (do_acc) {
       const double2 omd = a.omega[k];
       const T ox = (T)omd.x, oy = (T)omd.y;
@@ -593,7 +708,8 @@ static void launch_pint_m(Ctx &c, const PintGeom &g, const PintArgs<T> &a) {
   const int nteams = g.nblk * g.R;
   const int grid = (nteams + g.teams_per_cta - 1) / g.teams_per_cta;
   const int threads = g.P * g.teams_per_cta;
-  auto kern = threads <= 256 ? k_pint<T, M, 256> : k_pint<T, M, (M >= 16 ? 256 : 512)>;
+  auto kern = a.fac_in ? (threads <= 256 ? k_pint<T, M, 256, true> : k_pint<T, M, (M >= 16 ? 256 : 512), true>)
+                       : (threads <= 256 ? k_pint<T, M, 256, false> : k_pint<T, M, (M >= 16 ? 256 : 512), false>);
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   // algorithmic bytes: spectrum rows read/written as requested, plus the vector rhs
   double bytes = 0.0;
@@ -603,6 +719,12 @@ static void launch_pint_m(Ctx &c, const PintGeom &g, const PintArgs<T> &a) {
   const bool dots = a.mcount ? a.want_dots != 0 : a.mdots > 0;
   const char *fam = sizeof(T) == 8 ? (dots ? "pint_dots_f64" : (a.Y ? "pint_store_f64" : "pint_acc_f64"))
                                    : (dots ? "pint_dots_f32" : (a.Y ? "pint_store_f32" : "pint_acc_f32"));
+  if (a.fac_out) {
+    fam = sizeof(T) == 8 ? "pint_factor_f64" : "pint_factor_f32";
+    bytes = (double)pint_factor_elems(g) * sizeof(cpx<T>);
+  } else if (a.fac_in) {
+    bytes += (double)pint_factor_elems(g) * sizeof(cpx<T>);
+  }
   c.launch(fam, bytes, [&] { pdl_launch(c.pdl, kern, dim3(grid), dim3(threads), smem, c.stream, g, a, tb); });
 }
 

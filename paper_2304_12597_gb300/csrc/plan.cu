@@ -159,7 +159,7 @@ struct pd_plan {
   int nf = 0;
   double tau = 0.0;
   double alpha = 1.0;  // Algorithm 3: C_alpha instead of C_1 (1 = Algorithm 1)
-  bool refined64 = false;  // FP64 plan that always refines (alpha < 1)
+  bool refined64 = false;  // FP64 plan that always refines (alpha < 1, or a batch)
   double aroot = 1.0;  // alpha^{1/l}
   int precision = PD_FP64;
   int maxit = 32;
@@ -184,6 +184,8 @@ struct pd_plan {
   double *md2 = nullptr, *mref2 = nullptr, *mprev = nullptr;  // per-problem refinement state
   int *mex = nullptr;  // per-problem residual scaling 2^mex of the next refinement sweep
   int members = 0;     // batched plans: one Algorithm 2 per problem (0 = one for the plan)
+  bool factored = false;  // the shifted systems are factored once per operator (fac)
+  void *fac = nullptr;
   double *mscal = nullptr;  // per-problem Algorithm-2 scalar and flag blocks
   int *mflags = nullptr;
   pd::PintGeom geom{};
@@ -291,6 +293,8 @@ pd_status validate(const pd_desc *d) {
     return fail(PD_ERR_INVALID_ARG, "tune_pint_teams must be 0 or a power of two <= 16");
   if (d->tune_krylov_ctas < 0 || d->tune_krylov_ctas > 1024 || d->tune_cap_ctas < 0 || d->tune_cap_ctas > 1024)
     return fail(PD_ERR_INVALID_ARG, "tune_krylov_ctas and tune_cap_ctas must be in [0, 1024]");
+  if (d->tune_pint_factor < -1 || d->tune_pint_factor > 1)
+    return fail(PD_ERR_INVALID_ARG, "tune_pint_factor must be -1, 0 or 1");
   if (d->tune_krylov_cluster != 0 && d->tune_krylov_cluster != -1 &&
       (d->tune_krylov_cluster < 4 || d->tune_krylov_cluster > 16))
     return fail(PD_ERR_INVALID_ARG, "tune_krylov_cluster must be 0, -1 or in [4, 16]");
@@ -334,13 +338,14 @@ void fill_geometry(pd_plan *p, const pd_desc *d) {
   p->tau = p->batch > 1 ? 1.0 : d->tau;
   p->alpha = d->alpha > 0.0 ? d->alpha : 1.0;
   p->aroot = std::pow(p->alpha, 1.0 / (double)d->nt);
-  p->refined64 = d->precision == PD_FP64 && p->alpha < 1.0;
+  p->refined64 = d->precision == PD_FP64 && (p->alpha < 1.0 || d->batch > 1);
   p->precision = d->precision;
   p->maxit = d->maxit ? d->maxit : 32;
   p->eps = d->eps_krylov > 0 ? d->eps_krylov : (d->precision == PD_FP64 ? 1e-13 : 1e-5);
   // FP64 plans that refine anyway use a loose tolerance per solve: Algorithm 3 loses
-  // up to kappa(F D_alpha) per solve, so FP64 refinement sweeps with a few Krylov
-  // steps each beat one tight solve
+  // up to kappa(F D_alpha) per solve, and a batch runs until its slowest problem's
+  // Algorithm 2 has converged (one problem that needs 30 steps at 1e-13 holds all of
+  // them), so FP64 refinement sweeps with a few Krylov steps each beat one tight solve
   if (p->refined64 && !(d->eps_krylov > 0)) p->eps = 1e-5;
   // batches stop only when their slowest problem has converged: allow more sweeps
   p->max_refine = d->max_refine ? d->max_refine : (d->batch > 1 ? 16 : 8);
@@ -381,6 +386,12 @@ void fill_geometry(pd_plan *p, const pd_desc *d) {
   }
   if (d->tune_cap_ctas) p->k5_grid = d->tune_cap_ctas;
   p->ctx.fft_cols = d->tune_fft_cols;
+  {  // factors of the shifted systems: computed once per operator, read by every loop
+    const size_t esz = p->precision == PD_MIXED ? sizeof(cpx<float>) : sizeof(cpx<double>);
+    const size_t fbytes = pd::pint_factor_elems(p->geom) * esz;
+    const bool want = d->tune_pint_factor == 1 || (d->tune_pint_factor == 0 && p->precision == PD_FP64);
+    p->factored = want && fbytes <= ((size_t)4 << 30);
+  }
   p->ctx.pdl = d->tune_no_pdl == 0;
 }
 
@@ -434,6 +445,9 @@ size_t layout(pd_plan *p, unsigned char *base) {
   }
   p->spec = mixed ? (void *)A.take<cpx<float>>((size_t)nf * p->lds) : (void *)A.take<cpx<double>>((size_t)nf * p->lds);
   p->hbuf = mixed ? (void *)A.take<cpx<float>>((size_t)nf * p->lds) : (void *)A.take<cpx<double>>((size_t)nf * p->lds);
+  if (p->factored)
+    p->fac = mixed ? (void *)A.take<cpx<float>>(pd::pint_factor_elems(p->geom))
+                   : (void *)A.take<cpx<double>>(pd::pint_factor_elems(p->geom));
   p->V = A.take<double>((size_t)(mx + 1) * nbar);
   if (mixed) {
     p->Vf = A.take<float>((size_t)(mx + 1) * nbar);
@@ -655,6 +669,7 @@ pd::PintArgs<T> base_args(pd_plan *p);
 template <>
 pd::PintArgs<double> base_args<double>(pd_plan *p) {
   pd::PintArgs<double> a{};
+  if (p->precision == PD_FP64) a.fac_in = reinterpret_cast<const cpx<double> *>(p->fac);
   a.xm_scale = p->aroot;
   a.shift = p->shift;
   a.tlo = p->tlo_d;
@@ -665,12 +680,30 @@ pd::PintArgs<double> base_args<double>(pd_plan *p) {
 template <>
 pd::PintArgs<float> base_args<float>(pd_plan *p) {
   pd::PintArgs<float> a{};
+  if (p->precision == PD_MIXED) a.fac_in = reinterpret_cast<const cpx<float> *>(p->fac);
   a.xm_scale = p->aroot;
   a.shift = p->shift;
   a.tlo = p->tlo_f;
   a.tdiag = p->tdiag_f;
   a.tup = p->tup_f;
   return a;
+}
+
+// Factor every (k, block) shifted system of the plan (after the operator changed).
+pd_status factorize(pd_plan *p) {
+  if (!p->fac) return PD_OK;
+  if (p->precision == PD_MIXED) {
+    pd::PintArgs<float> a = base_args<float>(p);
+    a.fac_in = nullptr;
+    a.fac_out = reinterpret_cast<cpx<float> *>(p->fac);
+    pd::launch_pint<float>(p->ctx, p->geom, a);
+  } else {
+    pd::PintArgs<double> a = base_args<double>(p);
+    a.fac_in = nullptr;
+    a.fac_out = reinterpret_cast<cpx<double> *>(p->fac);
+    pd::launch_pint<double>(p->ctx, p->geom, a);
+  }
+  return ctx_status(p);
 }
 
 template <typename T>
@@ -1217,6 +1250,7 @@ pd_status paradiag_plan(const pd_desc *desc, void *workspace, size_t workspace_b
       return cleanup(st);
   }
   if ((st = upload_operator(p, desc)) != PD_OK) return cleanup(st);
+  if ((st = factorize(p)) != PD_OK) return cleanup(st);
   if (cudaMemsetAsync(p->flags, 0, pd::kFlagWords * sizeof(int), s) != cudaSuccess)
     return cleanup(fail(PD_ERR_CUDA, "plan upload failed"));
   if (cudaStreamSynchronize(s) != cudaSuccess) return cleanup(fail(PD_ERR_CUDA, "plan upload failed"));
@@ -1240,7 +1274,11 @@ pd_status paradiag_set_operator(pd_plan *p, const pd_desc *desc) {
   }
   if (p->ctx.stream) cudaStreamSynchronize(p->ctx.stream);  // no solve may still read the old operator
   std::lock_guard<std::recursive_mutex> lk(host_mutex());
-  return upload_operator(p, desc);
+  if ((st = upload_operator(p, desc)) != PD_OK) return st;
+  if ((st = factorize(p)) != PD_OK) return st;
+  if (p->ctx.stream && cudaStreamSynchronize(p->ctx.stream) != cudaSuccess)
+    return fail(PD_ERR_CUDA, "operator factorisation failed");
+  return PD_OK;
 }
 
 pd_status paradiag_destroy(pd_plan *p) {

@@ -112,6 +112,7 @@ def test_valid_descriptors_have_a_workspace(B):
                {"precision": 1, "tune_pint_rows": 16, "tune_pint_teams": 2, "tune_krylov_ctas": 8,
                 "tune_cap_ctas": 3, "tune_fft_cols": 2},
                {"tune_krylov_cluster": 16}, {"tune_krylov_cluster": -1}, {"tune_krylov_ctas": 1, "n": 4095},
+               {"tune_pint_factor": 1, "precision": 1}, {"tune_pint_factor": -1},
                {"batch": 3, "batch_nx": [31, 5, 1], "batch_tau": [0.1, 0.2, 1e-3]}, {"batch": 4},
                {"alpha": 1e-4}, {"alpha": 0.5, "precision": 1},
                {"dim": 2, "ny": 7}, {"dim": 2, "ny": 255, "n": 255, "nt": 256, "precision": 1}):
@@ -145,6 +146,7 @@ def test_valid_descriptors_have_a_workspace(B):
     ({"tune_krylov_ctas": -1}, 1),
     ({"tune_krylov_ctas": 1, "n": 4095, "batch": 3}, 2),   # one CTA holds <= 8192 entries
     ({"tune_krylov_cluster": 2}, 1),
+    ({"tune_pint_factor": 2}, 1),
     ({"tune_krylov_cluster": 32}, 1),
     ({"tune_cap_ctas": 5000}, 1),
     ({"tune_fft_cols": 6}, 1),

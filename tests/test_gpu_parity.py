@@ -275,3 +275,53 @@ def test_graph_solve_equals_host_driven_solve(pd, prec, P):
     for key in ("refine_sweeps", "krylov_iters_total", "sweep_krylov_iters", "kernel_launches"):
         assert sg[key] == sh[key], key
     assert R.rel_err(Ug.cpu().numpy(), R.be_solve_refined(P)) <= TOL[prec]
+
+
+# ----------------------------------------------------------------------------
+# Factored shifted systems (factors computed once per operator) against the oracle
+# ----------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("factor", [-1, 1])
+@pytest.mark.parametrize("P", [W.random_tridiag_problem(129, 16, seed=9), W.heat1d_forced(255, 128, seed=3),
+                               W.random_tridiag_problem(4096, 8, seed=8), W.heat2d_smooth(15, 16, 0.1, seed=2),
+                               W.random_tridiag_problem(3, 64, seed=4)], ids=lambda p: p.name)
+def test_factored_and_eliminating_loops_match_oracle(pd, prec, factor, P):
+    """Both forms of the parallel-in-time loop: eliminating in every loop (-1) and
+    solving with factors stored per operator (1), in both precisions."""
+    Uref = R.be_solve_refined(P)
+    U, st, _, _ = _solve(pd, P, prec, tune={"pint_factor": factor})
+    assert R.rel_err(U, Uref) <= TOL[prec], st
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_factored_shifted_solves_match_definition(pd, prec):
+    """The factored shifted solves of every frequency against the oracle's (1 - pi_k) I + tau K."""
+    P = W.random_tridiag_problem(200, 32, seed=12)
+    ell = P.nt
+    nf = ell // 2 + 1
+    pi, _ = R.circulant_eigs(ell)
+    Rfull = R.dft_time(P.G)
+    op = R.operator(P)
+    L = np.stack([op.shifted_solve(1.0 - pi[i], P.tau, Rfull[i]) for i in range(nf)])
+    ctype = np.complex128 if prec == "fp64" else np.complex64
+    with pd.Plan.from_problem(P, precision=prec, device=dev(), tune={"pint_factor": 1}) as plan:
+        Y, _ = plan.shifted_solve(torch.from_numpy(Rfull[:nf].astype(ctype)).to(dev()))
+        Y = Y.cpu().numpy().astype(np.complex128)
+    assert np.linalg.norm(Y - L) / np.linalg.norm(L) < (1e-10 if prec == "fp64" else 5e-3)
+
+
+@pytest.mark.parametrize("prec,factor", [("fp64", 0), ("mixed", 1), ("mixed", 0)])
+def test_set_operator_refactors(pd, prec, factor):
+    """paradiag_set_operator swaps K (and tau): the next solve is the new problem's
+    (the stored factors are recomputed)."""
+    A = W.heat1d_forced(255, 64, seed=1)
+    B = W.advdiff1d_pulse(255, 64, seed=2)
+    with pd.Plan.from_problem(A, precision=prec, device=dev(), tune={"pint_factor": factor}) as plan:
+        Ua, _ = plan.solve(torch.from_numpy(A.G).to(dev()))
+        plan.set_operator(tau=B.tau, k_lo=B.k_lo, k_diag=B.k_diag, k_up=B.k_up)
+        Ub, st = plan.solve(torch.from_numpy(B.G).to(dev()))
+        Ub = Ub.cpu().numpy()
+    assert R.rel_err(Ua.cpu().numpy(), R.be_solve_refined(A)) <= TOL[prec]
+    assert R.rel_err(Ub, R.be_solve_refined(B)) <= TOL[prec], st
