@@ -25,6 +25,24 @@ constexpr int kLoadBatch = 8;
 template <typename T>
 __device__ void fft_smem(cpx<T> *buf, int n, int logn, int nseries, const cpx<T> *__restrict__ tw) {
   int s = 0;
+  if (logn >= 2) {  // first radix-4 pass: every twiddle is 1 (j = 0), no multiplications
+    const int lq = logn - 2;
+    const int total = nseries << lq;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+      const int ser = idx >> lq;
+      const int base = (idx & ((1 << lq) - 1)) << 2;
+      cpx<T> *p = buf + ((size_t)ser << logn) + base;
+      const cpx<T> x0 = p[0], x1 = p[1], x2 = p[2], x3 = p[3];
+      const cpx<T> a0 = add(x0, x1), a1 = sub(x0, x1), a2 = add(x2, x3), a3 = sub(x2, x3);
+      const cpx<T> mu = mk<T>(a3.y, -a3.x);  // -i * a3
+      p[0] = add(a0, a2);
+      p[2] = sub(a0, a2);
+      p[1] = add(a1, mu);
+      p[3] = sub(a1, mu);
+    }
+    __syncthreads();
+    s = 2;
+  }
   while (s + 1 < logn) {  // radix-4 pass = DIT stages with half-spans h and 2h
     const int h = 1 << s;
     const int lq = logn - 2;
