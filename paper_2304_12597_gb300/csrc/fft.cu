@@ -18,6 +18,12 @@ namespace pd {
 
 // Global loads a thread issues back to back before it uses any of them.
 constexpr int kLoadBatch = 8;
+// Threads per CTA of the forward time DFTs: 512 once a tile holds >= 4096 values (n TX),
+// so each thread issues one batch of loads and takes one butterfly per pass; else 256.
+// (The inverse DFT keeps 256: its FP64 update needs more than the 64 registers a thread
+// may hold with two 512-thread CTAs per SM.)
+constexpr int kFftMaxThreads = 512;
+static int fft_threads(int n, int tx) { return (int64_t)n * tx >= 4096 ? 512 : 256; }
 
 // In-place DIT FFT of `nseries` series of length n = 2^logn stored back to back
 // in shared memory, input in bit-reversed order, output in natural order.
@@ -113,7 +119,7 @@ __device__ void r2c_store(const cpx<T> *buf, int n, int logn, int64_t x0, int64_
 }
 
 template <typename T, typename Tin, int TX>
-__global__ void __launch_bounds__(256) k_fft_r2c(const Tin *__restrict__ X, int64_t ldx, int64_t ncols,
+__global__ void __launch_bounds__(kFftMaxThreads) k_fft_r2c(const Tin *__restrict__ X, int64_t ldx, int64_t ncols,
                                                  int n, int logn, const cpx<T> *__restrict__ tw,
                                                  cpx<T> *__restrict__ S, int64_t lds, const T *__restrict__ rs) {
   grid_dep_wait();
@@ -151,7 +157,7 @@ __global__ void __launch_bounds__(256) k_fft_r2c(const Tin *__restrict__ X, int6
 // while the tile is loaded (rx = (tau lo, 1 + tau diag, tau up)); neighbour columns
 // outside the tile come from L1/L2.
 template <typename T, int TX>
-__global__ void __launch_bounds__(256) k_fft_r2c_res(const double *__restrict__ G, const double *__restrict__ U,
+__global__ void __launch_bounds__(kFftMaxThreads, 2) k_fft_r2c_res(const double *__restrict__ G, const double *__restrict__ U,
                                                      int64_t ncols, int n, int logn, const double *__restrict__ rxl,
                                                      const double *__restrict__ rxd,
                                                      const double *__restrict__ rxu,
@@ -451,7 +457,7 @@ void launch_fft_r2c(Ctx &c, const Tin *X, int64_t ldx, int64_t ncols, int n, con
     PD_TX_DISPATCH(TX, {
       if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_fft_r2c<T, Tin, kTX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      pdl_launch(c.pdl, k_fft_r2c<T, Tin, kTX>, dim3(grid), dim3(256), smem, c.stream, X, ldx, ncols, n, logn, tw, S, lds,
+      pdl_launch(c.pdl, k_fft_r2c<T, Tin, kTX>, dim3(grid), dim3(fft_threads(n, kTX)), smem, c.stream, X, ldx, ncols, n, logn, tw, S, lds,
                  rs);
     })
   });
@@ -470,7 +476,7 @@ void launch_fft_r2c_residual(Ctx &c, const double *G, const double *U, int64_t n
     PD_TX_DISPATCH(TX, {
       if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_fft_r2c_res<T, kTX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      pdl_launch(c.pdl, k_fft_r2c_res<T, kTX>, dim3(grid), dim3(256), smem, c.stream, G, U, ncols, n, logn, rxl, rxd, rxu,
+      pdl_launch(c.pdl, k_fft_r2c_res<T, kTX>, dim3(grid), dim3(fft_threads(n, kTX)), smem, c.stream, G, U, ncols, n, logn, rxl, rxd, rxu,
                  tw, S, lds, rs, mex,
                                                            mnx);
     })
