@@ -326,12 +326,19 @@ __global__ void __launch_bounds__(256) k_fft_c2r(const cpx<T> *__restrict__ S, i
       __syncthreads();
       if (threadIdx.x == 0) last = atomicAdd(fin.counter, 1) == (int)gridDim.x - 1;
       __syncthreads();
-      if (last && threadIdx.x < 32) {
+      if (last) {
         __threadfence();
+        // every thread loads its share at once (the partials sit in L2, possibly on the
+        // other die: one round trip instead of one per partial), then a fixed-order sum
         double t = 0.0;
-        for (int i = threadIdx.x; i < (int)gridDim.x; i += 32) t += norm_part[i];
+#pragma unroll 4
+        for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) t += norm_part[i];
         t = warp_sum(t);
+        if (l == 0) red[w] = t;
+        __syncthreads();
         if (threadIdx.x == 0) {
+          t = 0.0;
+          for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
           fin.scal[S_D2] = t;
           *fin.counter = 0;
           refine_decide(fin.scal, fin.flags, fin.rc, fin.use_handle, fin.h);

@@ -261,7 +261,8 @@ __global__ void __launch_bounds__(kK5Warps * 32) k_capacitance_terms(
     const cpx<double> wk = mk<double>(w.x, w.y);
     if (lane < m) {
       const cpx<double> sl = X[(m - 1) * m + lane];  // e_m^T S_k, column `lane`
-      srow[(int64_t)k * m + lane] = make_double2(sl.x, sl.y);
+      const cpx<double> ws = mul(wk, sl);  // w_k gamma_k (e_m^T S_k): omega_k = this . y_m
+      srow[(int64_t)k * m + lane] = make_double2(ws.x, ws.y);
       for (int q = 0; q < m; ++q) {
         const cpx<double> gs = mul(gq[q], sl);
         const cpx<double> val = mk<double>(X[q * m + lane].x - tt * gs.x, X[q * m + lane].y - tt * gs.y);
@@ -295,7 +296,9 @@ __global__ void __launch_bounds__(kK5Warps * 32) k_capacitance_terms(
 }
 
 // M = I + sum of the per-CTA partials; y = beta M^{-1} e_1; omega_k = w_k gamma_k
-// (e_m^T S_k y).  Run by one CTA; smem holds H, X (m x m complex), fcol and y.
+// (e_m^T S_k y), with srow already holding the rows w_k gamma_k e_m^T S_k.  Run by one
+// CTA; smem holds H, X (m x m complex), fcol and y.  GB300 issues FP64 at ~1/64 of the
+// FP32 rate, so this serial tail keeps its FP64 instruction count small.
 __device__ void capacitance_solve_cta(int nf, int m, int nparts, const double *msys_part,
                                       const double2 *__restrict__ wg, const double2 *__restrict__ srow,
                                       double2 *omega, double *y, const double *scal, unsigned char *smem) {
@@ -315,14 +318,22 @@ __device__ void capacitance_solve_cta(int nf, int m, int nparts, const double *m
     }
   }
   __syncthreads();
-  if (threadIdx.x < 32) warp_gj_inverse(H, X, fcol, m);
-  __syncthreads();
   const double beta = scal[S_BETA];
-  if ((int)threadIdx.x < m) {
-    ys[threadIdx.x] = beta * X[threadIdx.x * m + 0].x;
-    y[threadIdx.x] = ys[threadIdx.x];
+  if (m == 1) {  // M is 1 x 1 (the common case): no elimination
+    if (threadIdx.x == 0) {
+      ys[0] = beta / H[0].x;
+      y[0] = ys[0];
+    }
+  } else {
+    if (threadIdx.x < 32) warp_gj_inverse(H, X, fcol, m);
+    __syncthreads();
+    if ((int)threadIdx.x < m) {
+      ys[threadIdx.x] = beta * X[threadIdx.x * m + 0].x;
+      y[threadIdx.x] = ys[threadIdx.x];
+    }
   }
   __syncthreads();
+  // srow holds w_k gamma_k (e_m^T S_k): two FP64 operations per step and frequency
 #pragma unroll 4
   for (int k = threadIdx.x; k < nf; k += blockDim.x) {
     double cx = 0.0, cy = 0.0;
@@ -331,8 +342,7 @@ __device__ void capacitance_solve_cta(int nf, int m, int nparts, const double *m
       cx += sv.x * ys[q];
       cy += sv.y * ys[q];
     }
-    const double2 w = wg[k];
-    omega[k] = make_double2(w.x * cx - w.y * cy, w.x * cy + w.y * cx);
+    omega[k] = make_double2(cx, cy);
   }
 }
 
