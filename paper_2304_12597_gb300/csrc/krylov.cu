@@ -236,6 +236,32 @@ __global__ void __launch_bounds__(kK5Warps * 32) k_capacitance_terms(
   const double tt = flags[F_BREAK] ? 0.0 : tau * scal[S_T];
   for (int i = lane; i < m * m; i += 32) msw[i] = 0.0;
   __syncwarp();
+  if (m == 1) {
+    // one step (the common case): S_k = 1 / ((1 - pi_k) + tau t_11) is a scalar, so a
+    // thread takes a frequency (a warp of GJ per frequency would leave 31 lanes idle on
+    // GB300's slow FP64 pipe)
+    const double t11 = tau * T[0];
+    const int b0 = members ? (int)blockIdx.y : 0, b1 = flags[F_BREAK] ? b0 : (members ? b0 + 1 : nblk);
+    double acc = 0.0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nf; k += gridDim.x * blockDim.x) {
+      const double2 sk = shift[k];
+      double gx = 0.0, gy = 0.0;
+      for (int b = b0; b < b1; ++b) {
+        const double2 v = gpart[(int64_t)k * nblk + b];
+        gx += v.x;
+        gy += v.y;
+      }
+      const cpx<double> X1 = recip(mk<double>(t11 + sk.x, sk.y));
+      const double2 w = wg[k];
+      const cpx<double> wk = mk<double>(w.x, w.y);
+      const cpx<double> ws = mul(wk, X1);
+      srow[k] = make_double2(ws.x, ws.y);
+      const cpx<double> gs = mul(mk<double>(gx, gy), X1);
+      acc += mul(wk, mk<double>(X1.x - tt * gs.x, X1.y - tt * gs.y)).x;
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) msw[0] = acc;
+  } else {
   const int gw = blockIdx.x * kK5Warps + wid, nw = gridDim.x * kK5Warps;
   for (int k = gw; k < nf; k += nw) {
     const double2 sk = shift[k];
@@ -271,6 +297,7 @@ __global__ void __launch_bounds__(kK5Warps * 32) k_capacitance_terms(
       }
     }
     __syncwarp();
+  }
   }
   __syncthreads();
   // CTA partial = sum over its warps (fixed order)
