@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(MODE == kCoop ? kBlas : MODE == kCluster ? kBl
     if (wr) T[(int64_t)threadIdx.x * ldT + (m - 1)] = tq + c[threadIdx.x];
     reg_axpy<MODE, E>(n, m, V, n, x, c);
     __syncthreads();
-    t = sqrt(reg_norm2<MODE, E>(x, pc, red, c));
+    t = sqrt(cgs2_norm2<MODE, E>(m, x, c, pc, red));
     bd = !(t > 1e-14 * knorm);
     const double it = bd ? 0.0 : 1.0 / t;
     double *vm = V + (int64_t)m * n;

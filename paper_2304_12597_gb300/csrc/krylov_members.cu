@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(kBlasSingle) k_member_arnoldi(KrylovBufs k) {
   if (wr) mv.T[(int64_t)threadIdx.x * ldT + (m - 1)] = tq + c[threadIdx.x];
   reg_axpy<kSingle, E>(len, m, Vb, ldv, x, c);
   __syncthreads();
-  const double t = sqrt(reg_norm2<kSingle, E>(x, nullptr, red, c));
+  const double t = sqrt(cgs2_norm2<kSingle, E>(m, x, c, nullptr, red));
   const bool bd = !(t > 1e-14 * knorm);
   const double it = bd ? 0.0 : 1.0 / t;
 #pragma unroll
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(kBlasSingle) k_member_project(KrylovBufs k, co
     reg_dots<kSingle, E>(len, m, Vb, ldv, x, nullptr, red, c);
     reg_axpy<kSingle, E>(len, m, Vb, ldv, x, c);
     __syncthreads();
-    const double zz = reg_norm2<kSingle, E>(x, nullptr, red, c);
+    const double zz = cgs2_norm2<kSingle, E>(m, x, c, nullptr, red);
     if (threadIdx.x == 0) {
       mv.scal[S_RES] = mv.flags[F_BREAK] ? 0.0 : fabs(tau * mv.scal[S_T]) * sqrt(zz);
       krylov_decide(mv.scal, mv.flags, kc, 0, h);

@@ -259,6 +259,20 @@ __device__ __forceinline__ double reg_norm2(const double (&x)[E], double *slot, 
   return grid_sum<MODE>(s, slot, 0, red, c);
 }
 
+// ||x2||^2 after the second Gram-Schmidt pass x2 = x1 - V c, from that pass's dots
+// (c[q] = V_q . x1, c[m] = ||x1||^2): ||x2||^2 = ||x1||^2 - sum_q c[q]^2 for orthonormal
+// V, which saves a reduction.  The second pass removes only rounding-level components, so
+// the difference keeps its digits; if it removed more than 1e-4 of ||x1||^2 the explicit
+// reduction runs instead (every thread and CTA holds the same c: a uniform branch).
+template <int MODE, int E>
+__device__ __forceinline__ double cgs2_norm2(int m, const double (&x)[E], double *c, double *slot, double *red) {
+  double r = 0.0;
+  for (int q = 0; q < m; ++q) r += c[q] * c[q];
+  const double a = c[m];
+  if (r <= 1e-4 * a) return a - r;
+  return reg_norm2<MODE, E>(x, slot, red, c);
+}
+
 // Algorithm 2, first step: beta = ||b||, V[0] = b / beta (and its binary32 copy), T_m
 // cleared, the control block reset, and the WHILE conditional set to run the loop
 // unless b is zero or not finite.
@@ -354,7 +368,7 @@ __device__ __forceinline__ void project_body(int n, const double *__restrict__ V
     reg_dots<MODE, E>(n, m, V, n, x, pb, red, c);
     reg_axpy<MODE, E>(n, m, V, n, x, c);
     __syncthreads();
-    zz = reg_norm2<MODE, E>(x, pc, red, c);
+    zz = cgs2_norm2<MODE, E>(m, x, c, pc, red);
   }
   if (g_leader<MODE>()) {
     scal[S_RES] = flags[F_BREAK] ? 0.0 : fabs(tau * scal[S_T]) * sqrt(zz);
