@@ -56,10 +56,11 @@ __global__ void __launch_bounds__(256) k_member_decide(const double *__restrict_
     last = atomicAdd(counter, 1) == nmem - 1;
   }
   __syncthreads();
-  if (last && threadIdx.x == 0) {
+  if (last) {
     __threadfence();
-    *counter = 0;
-    refine_decide_members(scal, flags, rc, nmem, d2, ref2, prev, mex, use_handle, h);
+    if (threadIdx.x == 0) *counter = 0;
+    __syncthreads();  // red is reused
+    refine_decide_members(scal, flags, rc, nmem, d2, ref2, prev, mex, use_handle, h, red);
   }
 }
 

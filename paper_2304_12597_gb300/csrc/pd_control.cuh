@@ -89,13 +89,17 @@ __device__ __forceinline__ void refine_decide(double *scal, int *flags, const Re
 // two that scales problem b's residual in the next sweep, 2^-round(log2 ||delta_s||):
 // the problems' right-hand sides stay comparable in the shared Krylov space, so one
 // problem's correction is not lost below another's.
+// Run by every thread of one CTA (red: blockDim.x doubles of shared memory): the
+// problems are spread over the threads, so the per-problem loads overlap instead of
+// following one another through L2; the batch totals are then reduced in a fixed order.
 __device__ __forceinline__ void refine_decide_members(double *scal, int *flags, const RefineCtl &r, int nmem,
                                                       const double *d2, double *ref2, double *prev, int *mex,
-                                                      int use_handle, cudaGraphConditionalHandle h) {
+                                                      int use_handle, cudaGraphConditionalHandle h,
+                                                      double *red) {
   const int s = flags[F_SWEEP];
   bool nonfinite = flags[F_NONFIN] != 0, all_conv = true, any_stall = false, all_floor = true;
   double relmax = 0.0, d2sum = 0.0;
-  for (int b = 0; b < nmem; ++b) {
+  for (int b = threadIdx.x; b < nmem; b += blockDim.x) {
     const double d = d2[b];
     d2sum += d;
     if (!isfinite(d)) nonfinite = true;
@@ -121,6 +125,27 @@ __device__ __forceinline__ void refine_decide_members(double *scal, int *flags, 
     }
     mex[b] = e;
   }
+  nonfinite = __syncthreads_or(nonfinite);
+  all_conv = __syncthreads_and(all_conv);
+  any_stall = __syncthreads_or(any_stall);
+  all_floor = __syncthreads_and(all_floor);
+  // relmax: a maximum (order-free); d2sum: a fixed-order tree over the threads
+  red[threadIdx.x] = relmax;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  relmax = red[0];
+  __syncthreads();
+  red[threadIdx.x] = d2sum;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  d2sum = red[0];
+  if (threadIdx.x != 0) return;
   const double beta = scal[S_BETA];
   if (s < 16) {
     flags[F_SWM + s] = flags[F_M];
