@@ -190,6 +190,7 @@ struct pd_plan {
   int *mflags = nullptr;
   pd::PintGeom geom{};
   int blas_grid = 1, k5_grid = 1;
+  int k5_grid_members = 1;  // capacitance CTAs per problem of a batched plan
   int blas_cluster = 0;  // CTAs of the cluster variant of the one-CTA Krylov kernels (0 = off)
   int64_t lds = 0;
 
@@ -385,6 +386,12 @@ void fill_geometry(pd_plan *p, const pd_desc *d) {
     if (p->blas_cluster < 4) p->blas_cluster = 0;
   }
   if (d->tune_cap_ctas) p->k5_grid = d->tune_cap_ctas;
+  // batched plans run one capacitance system per problem: about two waves of CTAs over
+  // all problems (each CTA sized for maxit-step Gauss-Jordan holds one SM), so a warp
+  // takes several frequencies instead of the grid taking many waves
+  p->k5_grid_members = p->k5_grid;
+  if (p->batch > 1 && !d->tune_cap_ctas)
+    p->k5_grid_members = std::max(1, std::min(p->k5_grid, (2 * sms + p->batch - 1) / p->batch));
   p->ctx.fft_cols = d->tune_fft_cols;
   {  // factors of the shifted systems: computed once per operator, read by every loop
     const size_t esz = p->precision == PD_MIXED ? sizeof(cpx<float>) : sizeof(cpx<double>);
@@ -850,7 +857,8 @@ pd_status emit_iter(pd_plan *p, int kind, int use_handle, cudaGraphConditionalHa
     a.skip_flag = p->flags + pd::F_BREAK;
     pd::launch_pint<T>(c, p->geom, a);
   }
-  pd::launch_capacitance(c, kb, p->nf, p->tau, p->shift, p->wga, p->gpart, p->nblk, p->msys_part, p->k5_grid,
+  pd::launch_capacitance(c, kb, p->nf, p->tau, p->shift, p->wga, p->gpart, p->nblk, p->msys_part,
+                         kb.members ? p->k5_grid_members : p->k5_grid,
                          p->srow, p->omega, p->y, kb.members);
   // z = sum_i gamma_i h_i (e_m^T S_i y_m) from the stored h_i, then eq. (13)
   if (kb.members) {
