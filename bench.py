@@ -338,11 +338,31 @@ def run_ours(args):
         tsb, lb, stb = time_steps(bp, Gb, Ub, nb, stream, flush, torch)
         b_ms = max_over_ranks(sum(tsb), world, device)
         parts = bp.unstack(Ub.cpu().numpy(), [Q.nx for Q in probs])
+        # per-kernel rooflines of the batched solve (arrays above L2): CUDA events per launch
+        bp.set_timing(True)
+        for _ in range(3):
+            flush()
+            bp.solve(Gb, Ub)
+        bkt = bp.kernel_times()
+        bp.set_timing(False)
+        peak_b, _ = peaks()
+        bkern = {}
+        for r in sorted(bkt, key=lambda r: -r["total_ms"]):
+            if r["launches"] == 0:
+                continue
+            ms = r["total_ms"] / r["launches"]
+            gbs = (r["bytes"] / r["launches"]) / (ms / 1e3) / 1e9 if r["bytes"] > 0 else None
+            bkern[r["name"]] = {"launches_per_step": r["launches"] / 3, "us_per_launch": round(ms * 1e3, 1),
+                                "achieved_gbs": round(gbs, 1) if gbs else None,
+                                "frac_of_hbm": round(gbs / peak_b, 3) if gbs else None}
         batched = {"batch": B, "problems": f"{B} x {args.workload} (seeds 0..{B - 1})",
                    "value": unknowns * B * nb * world / (b_ms / 1e3), "unit": UNIT, "ms_per_step": b_ms / nb,
                    "gpu_launches_per_step": lb / nb, "refine_sweeps": stb["refine_sweeps"],
                    "krylov_iters_total": stb["krylov_iters_total"],
-                   "l2": "flushed before every timed step; 268 MB per array, above L2"}
+                   "l2": "flushed before every timed step; 268 MB per array, above L2",
+                   "kernels": bkern,
+                   "kernels_note": "algorithmic bytes per launch / CUDA-event duration (host-driven timing pass); "
+                                   "frac against the measured HBM copy bandwidth"}
         bp.close()
         del Gb, Ub
 

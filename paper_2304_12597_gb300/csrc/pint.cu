@@ -596,31 +596,41 @@ __global__ void __launch_bounds__(CW * RG) k_zsum(int nf, int64_t n, const cpx<T
     // the weights of its member; those of the CTA's first member are staged
     const int mem0 = mlen ? (int)((int64_t)blockIdx.x * CW / mlen) : 0;
     const double2 *om0 = omega + (int64_t)mem0 * nf;
+    const int64_t j = (int64_t)blockIdx.x * CW + tx;
+    const int memj = (mlen && j < n) ? (int)(j / mlen) : mem0;
+    const bool own = j < n && memj == mem0;
+    // the first batch of h_k loads is issued before the weights are staged, so the two
+    // memory round trips overlap
+    cpx<T> h[kColB];
+#pragma unroll
+    for (int u = 0; u < kColB; ++u) {
+      const int k = ty + u * RG;
+      h[u] = (own && k < nf) ? H[(int64_t)k * ldh + j] : mk<T>(T(0), T(0));
+    }
     for (int k = threadIdx.x; k < nf; k += CW * RG) om[k] = mk<T>((T)om0[k].x, (T)om0[k].y);
     __syncthreads();
-    const int64_t j = (int64_t)blockIdx.x * CW + tx;
     T acc[kColB];
 #pragma unroll
     for (int u = 0; u < kColB; ++u) acc[u] = T(0);
-    const int memj = (mlen && j < n) ? (int)(j / mlen) : mem0;
-    if (j < n && memj != mem0) {  // a later member in this CTA: its weights from memory
+    if (j < n && !own) {  // a later member in this CTA: its weights from memory
       const double2 *omj = omega + (int64_t)memj * nf;
       for (int k = ty; k < nf; k += RG) {
-        const cpx<T> h = H[(int64_t)k * ldh + j];
-        acc[0] += (T)omj[k].x * h.x - (T)omj[k].y * h.y;
+        const cpx<T> hk = H[(int64_t)k * ldh + j];
+        acc[0] += (T)omj[k].x * hk.x - (T)omj[k].y * hk.y;
       }
-    } else if (j < n) {
-      for (int k0 = ty; k0 < nf; k0 += RG * kColB) {
-        cpx<T> h[kColB];
-#pragma unroll
-        for (int u = 0; u < kColB; ++u) {
-          const int k = k0 + u * RG;
-          h[u] = k < nf ? H[(int64_t)k * ldh + j] : mk<T>(T(0), T(0));
-        }
+    } else if (own) {
+      for (int k0 = ty;;) {
 #pragma unroll
         for (int u = 0; u < kColB; ++u) {
           const int k = k0 + u * RG;
           if (k < nf) acc[u] += om[k].x * h[u].x - om[k].y * h[u].y;
+        }
+        k0 += RG * kColB;
+        if (k0 >= nf) break;
+#pragma unroll
+        for (int u = 0; u < kColB; ++u) {
+          const int k = k0 + u * RG;
+          h[u] = k < nf ? H[(int64_t)k * ldh + j] : mk<T>(T(0), T(0));
         }
       }
     }
