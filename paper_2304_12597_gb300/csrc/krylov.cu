@@ -3,15 +3,19 @@
 //    (CGS2) against V_m, t_{m+1,m} = ||w||, v_{m+1} = w / t_{m+1,m};
 //  - the projected m x m system of eq. (12): for every frequency k a warp forms
 //    S_k = ((1 - pi_k) I_m + tau T_m)^{-1} by Gauss-Jordan elimination with
-//    partial pivoting and accumulates w_k Re(gamma_k (S_k - tau t g_k e_m^T S_k));
-//    one CTA then solves for y_m and forms c_k = e_m^T S_k y_m;
+//    partial pivoting (a thread per frequency when m = 1) and accumulates
+//    w_k Re(gamma_k (S_k - tau t g_k e_m^T S_k)); the last CTA then solves for y_m and
+//    forms c_k = e_m^T S_k y_m;
 //  - the residual norm of eq. (13): ||r_m|| = |tau t_{m+1,m}| ||(I - V_m V_m^T) z||,
 //    z = sum_i gamma_i h_i c_i (z itself is accumulated by the shifted-solve pass);
 //  - x_m = V_m y_m;
 //  - the FP64 all-at-once residual G - [(I + tau K) U - U Sigma_1^T] used by the
 //    mixed-precision refinement.
-// Cross-CTA reductions write one partial per CTA; every consumer sums the
-// partials in the same fixed order, so results do not depend on scheduling.
+// The vector steps (init, Arnoldi, eq. 13) run in one CTA, one thread-block cluster
+// or a cooperative grid (pd_krylov.cuh); batched plans run one CTA per problem
+// (krylov_members.cu).  Cross-CTA reductions write one partial per CTA (or per
+// cluster rank); every consumer sums the partials in the same fixed order, so results
+// do not depend on scheduling.
 //
 // Scalar block `scal`: [0] beta = ||b||, [1] t_{m+1,m}, [2] ||r_m|| (eq. 13),
 // [3] ||K v_m|| (breakdown reference), [4] last sum-of-squares result.
@@ -197,8 +201,8 @@ __device__ void warp_gj_inverse(cpx<double> *H, cpx<double> *X, cpx<double> *fco
 constexpr int kK5Warps = 4;
 
 __device__ void capacitance_solve_cta(int nf, int m, int nparts, const double *msys_part,
-                                      const double2 *__restrict__ wg, const double2 *__restrict__ srow,
-                                      double2 *omega, double *y, const double *scal, unsigned char *smem);
+                                      const double2 *__restrict__ srow, double2 *omega, double *y,
+                                      const double *scal, unsigned char *smem);
 
 // Per-warp shared-memory slice, rounded up to 16 bytes so that every warp's
 // complex (16-byte) arrays stay aligned for any m.
@@ -315,7 +319,7 @@ __global__ void __launch_bounds__(kK5Warps * 32) k_capacitance_terms(
   __syncthreads();
   if (last) {
     __threadfence();
-    capacitance_solve_cta(nf, m, gridDim.x, msys_part, wg, srow, omega, y, scal, smraw);
+    capacitance_solve_cta(nf, m, gridDim.x, msys_part, srow, omega, y, scal, smraw);
     if (members)  // x_m = V y_m then runs over every step of the batch: zero the rest
       for (int q = m + threadIdx.x; q <= maxit; q += blockDim.x) y[q] = 0.0;
     if (threadIdx.x == 0) flags[F_CAPCNT] = 0;
@@ -327,8 +331,8 @@ __global__ void __launch_bounds__(kK5Warps * 32) k_capacitance_terms(
 // CTA; smem holds H, X (m x m complex), fcol and y.  GB300 issues FP64 at ~1/64 of the
 // FP32 rate, so this serial tail keeps its FP64 instruction count small.
 __device__ void capacitance_solve_cta(int nf, int m, int nparts, const double *msys_part,
-                                      const double2 *__restrict__ wg, const double2 *__restrict__ srow,
-                                      double2 *omega, double *y, const double *scal, unsigned char *smem) {
+                                      const double2 *__restrict__ srow, double2 *omega, double *y,
+                                      const double *scal, unsigned char *smem) {
   cpx<double> *H = reinterpret_cast<cpx<double> *>(smem);
   cpx<double> *X = H + m * m;
   cpx<double> *fcol = X + m * m;

@@ -368,10 +368,11 @@ void fill_geometry(pd_plan *p, const pd_desc *d) {
   const int ctas_per_sm = std::max(1, std::min(by_smem, by_threads));
   const int target = sms * ctas_per_sm * g0.teams_per_cta;
   p->geom = pd::pint_geometry(p->nf, p->nblk, p->blen, target, esz, d->tune_pint_rows, d->tune_pint_teams);
-  // Krylov vector kernels: one 512-thread CTA (plain launch) for vectors up to 8192
-  // entries; beyond, cooperative 64-thread CTAs, at most one per SM (co-resident)
+  // Krylov vector kernels: vectors up to 8192 entries run in one 512-thread CTA or (see
+  // below) a cluster; beyond, cooperative 64-thread CTAs, at most one per SM (co-resident)
   p->blas_grid = p->nbar <= 8192 ? 1 : (int)std::max<int64_t>(1, std::min<int64_t>((p->nbar + 63) / 64, (int64_t)sms));
-  // capacitance terms: one frequency per warp (four warps per CTA)
+  // capacitance terms: one frequency per warp (four warps per CTA; a thread per
+  // frequency when m = 1)
   p->k5_grid = std::max(1, std::min((p->nf + 3) / 4, 1024));
   if (d->tune_krylov_ctas) p->blas_grid = std::min(d->tune_krylov_ctas, sms);
   // Vectors one CTA would hold: a cluster of 8 (n_bar <= 2048) or 16 CTAs, one per SM,
