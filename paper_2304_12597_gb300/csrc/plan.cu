@@ -221,6 +221,12 @@ struct pd_plan {
   float *res_f = nullptr, *tmp_f = nullptr;
   double *res_d = nullptr, *tmp_d = nullptr;
   double *G_stage = nullptr, *U_stage = nullptr;
+  // paradiag_solve_host: the device-to-host copy of U, queued behind a graph solve's
+  // control-block read so that one host synchronisation covers both
+  void *tail_dst = nullptr;
+  const void *tail_src = nullptr;
+  size_t tail_bytes = 0;
+  bool tail_done = false;
   // pinned host mirrors of the scalar and flag blocks
   double *h_scal = nullptr;
   int *h_flags = nullptr;
@@ -634,9 +640,13 @@ pd_status ctx_status(pd_plan *p) {
   return PD_OK;
 }
 
-pd_status sync_read(pd_plan *p) {
+pd_status sync_read(pd_plan *p, bool with_tail = false) {
   CK(cudaMemcpyAsync(p->h_scal, p->scal, pd::kScalWords * sizeof(double), cudaMemcpyDeviceToHost, p->ctx.stream));
   CK(cudaMemcpyAsync(p->h_flags, p->flags, pd::kFlagWords * sizeof(int), cudaMemcpyDeviceToHost, p->ctx.stream));
+  if (with_tail && p->tail_dst) {
+    CK(cudaMemcpyAsync(p->tail_dst, p->tail_src, p->tail_bytes, cudaMemcpyDeviceToHost, p->ctx.stream));
+    p->tail_done = true;
+  }
   CK(cudaStreamSynchronize(p->ctx.stream));
   return ctx_status(p);
 }
@@ -1093,7 +1103,7 @@ pd_status solve_graph(pd_plan *p, const double *G, double *U, bool *used) {
     p->g_U = U;
   }
   CK(cudaGraphLaunch(p->gexec, p->ctx.stream));
-  pd_status st = sync_read(p);
+  pd_status st = sync_read(p, true);
   if (st != PD_OK) return st;
   // kernels run = fixed segments + m steps of Algorithm 2 per solve
   const int sweeps = p->h_flags[pd::F_SWEEP];
@@ -1346,10 +1356,22 @@ pd_status paradiag_solve_host(pd_plan *p, const double *G_host, double *U_host, 
   if (!G_host || !U_host) return fail(PD_ERR_INVALID_ARG, "G_host and U_host must be non-NULL");
   const size_t bytes = (size_t)p->nt * p->nbar * sizeof(double);
   CK(cudaMemcpyAsync(p->G_stage, G_host, bytes, cudaMemcpyHostToDevice, p->ctx.stream));
+  if (p->batch <= 1) {  // no kernel follows the graph: its final read can carry U back
+    p->tail_dst = U_host;
+    p->tail_src = p->U_stage;
+    p->tail_bytes = bytes;
+    p->tail_done = false;
+  }
   st = paradiag_solve(p, p->G_stage, p->U_stage, stats);
+  const bool done = p->tail_done;
+  p->tail_dst = nullptr;
+  p->tail_src = nullptr;
+  p->tail_done = false;
   if (st != PD_OK && st != PD_ERR_NOT_CONVERGED) return st;
-  CK(cudaMemcpyAsync(U_host, p->U_stage, bytes, cudaMemcpyDeviceToHost, p->ctx.stream));
-  CK(cudaStreamSynchronize(p->ctx.stream));
+  if (!done) {
+    CK(cudaMemcpyAsync(U_host, p->U_stage, bytes, cudaMemcpyDeviceToHost, p->ctx.stream));
+    CK(cudaStreamSynchronize(p->ctx.stream));
+  }
   return st;
 }
 
