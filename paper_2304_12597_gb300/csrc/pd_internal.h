@@ -176,9 +176,10 @@ struct PintGeom {
   int acc_rows;  // partial rows per block in acc_part (R, or CTAs when cta_sum)
   int stage;     // 1: tau K staged in shared memory once per launch
 };
-// m_req / teams_req: rows per thread and teams per CTA requested by the caller (0 = choose)
+// m_req / teams_req: rows per thread and teams per CTA requested by the caller (0 = choose);
+// fact: the loops will use stored factors (a smaller shared-memory footprint)
 PintGeom pint_geometry(int nf, int nblk, int blen, int target_teams, int elem_bytes, int m_req = 0,
-                       int teams_req = 0);
+                       int teams_req = 0, bool fact = false);
 void set_acc_rows(PintGeom &g);  // recompute cta_sum / acc_rows after changing R
 
 template <typename T>

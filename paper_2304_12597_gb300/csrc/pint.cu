@@ -36,10 +36,14 @@ struct TeamSmem {
   __host__ __device__ static size_t stage_bytes(int P, int stage) {
     return stage ? (((size_t)3 * P * (M + 1) * sizeof(T) + 15) & ~(size_t)15) : 0;
   }
-  static size_t bytes(int P, int mdots, int stage) {
+  // exchange rows of P: the eliminating loop double-buffers its PCR (8) unless its team
+  // is one warp; the factored loop needs one buffer (5)
+  __host__ __device__ static int xrows(int P, bool fact) { return (fact || P < 64) ? 5 : 8; }
+  // fact: the factored loop
+  static size_t bytes(int P, int mdots, int stage, bool fact = false) {
     size_t b = stage_bytes(P, stage);
     b += (size_t)P * (M + 1) * sizeof(cpx<T>);   // rhs / dd, padded one slot per chunk
-    b += (size_t)P * 5 * sizeof(cpx<T>);         // condensed rows a, b, c, d and 1/b
+    b += (size_t)P * xrows(P, fact) * sizeof(cpx<T>);  // condensed rows a, c, d, 1/b
     b += ((size_t)P * M * sizeof(T) + 15) & ~(size_t)15;  // per-team accumulators (compute type)
     b += (size_t)(P / 32) * std::max(mdots, 1) * sizeof(double2);  // dot reductions
     return (b + 15) & ~(size_t)15;
@@ -138,7 +142,9 @@ __global__ void __launch_bounds__(MAXT) k_pint(PintGeom g, PintArgs<T> a, size_t
   cpx<T> *pc = pb + N;
   cpx<T> *pd = pc + N;
   cpx<T> *pib = pd + N;
-  T *acc = reinterpret_cast<T *>(pib + N);
+  // second PCR buffer (a, c, d, 1/b): levels alternate buffers, one barrier per level
+  cpx<T> *qa = pb, *qc = pib + N, *qd = qc + N, *qib = qd + N;
+  T *acc = reinterpret_cast<T *>(pa + (size_t)N * TeamSmem<T, M>::xrows(P, FACT));
   double2 *red = reinterpret_cast<double2 *>(reinterpret_cast<unsigned char *>(acc) +
                                              (((size_t)P * M * sizeof(T) + 15) & ~(size_t)15));
 
@@ -385,42 +391,51 @@ __global__ void __launch_bounds__(MAXT) k_pint(PintGeom g, PintArgs<T> a, size_t
       C = mk<T>(-C.x, -C.y);
       D = fnms(fnms(D0, A0, pD1), C0, D1);
     }
-    team_sync(P, tic);
+    // one-warp teams synchronise with __syncwarp: they keep one buffer and two barriers
+    const bool dbl = P >= 64;
+    if (!dbl) team_sync(P, tic);
 
-    // 3b. PCR on the P condensed rows
+    // 3b. PCR on the P condensed rows.  Level l writes buffer q when l is even and p
+    // when odd (level 0 must not overwrite the 3a exchange in p while a thread still
+    // reads it); a buffer is rewritten two levels later, after every thread has passed
+    // the barrier between, so one barrier per level suffices
     int lvl = 0;
     for (int sig = 1; sig < P; sig <<= 1, ++lvl) {
-      pa[t] = A; pb[t] = B; pc[t] = C; pd[t] = D; pib[t] = recip(B);
+      const bool odd = !dbl || (lvl & 1);
+      cpx<T> *ba = odd ? pa : qa, *bc = odd ? pc : qc, *bd = odd ? pd : qd, *bi = odd ? pib : qib;
+      ba[t] = A; bc[t] = C; bd[t] = D; bi[t] = recip(B);
       team_sync(P, tic);
       cpx<T> nA = mk<T>(T(0), T(0)), nB = B, nC = mk<T>(T(0), T(0)), nD = D;
       const int lo = t - sig, hi = t + sig;
       cpx<T> k1 = mk<T>(T(0), T(0)), k2 = mk<T>(T(0), T(0));
       if (lo >= 0) {
-        k1 = mul(A, pib[lo]);
-        nA = fnms(nA, k1, pa[lo]);
-        nB = fnms(nB, k1, pc[lo]);
-        nD = fnms(nD, k1, pd[lo]);
+        k1 = mul(A, bi[lo]);
+        nA = fnms(nA, k1, ba[lo]);
+        nB = fnms(nB, k1, bc[lo]);
+        nD = fnms(nD, k1, bd[lo]);
       }
       if (hi < P) {
-        k2 = mul(C, pib[hi]);
-        nC = fnms(nC, k2, pc[hi]);
-        nB = fnms(nB, k2, pa[hi]);
-        nD = fnms(nD, k2, pd[hi]);
+        k2 = mul(C, bi[hi]);
+        nC = fnms(nC, k2, bc[hi]);
+        nB = fnms(nB, k2, ba[hi]);
+        nD = fnms(nD, k2, bd[hi]);
       }
       if (F) {
         F[fs_k1<M>(lvl) * P] = k1;
         F[(fs_k1<M>(lvl) + 1) * P] = k2;
       }
-      team_sync(P, tic);
+      if (!dbl) team_sync(P, tic);
       A = nA; B = nB; C = nC; D = nD;
     }
     const cpx<T> rB = recip(B);
     if (F) F[fs_binv<M>(lvl) * P] = rB;
     const cpx<T> xf = mul(D, rB);
-    // 3c. recover xe_t from the last row and xs_{t+1}
-    pd[t] = xf;
+    // 3c. recover xe_t from the last row and xs_{t+1}, through the buffer the last PCR
+    // level did not use
+    cpx<T> *x3 = (dbl && ((lvl - 1) & 1)) ? qd : pd;
+    x3[t] = xf;
     team_sync(P, tic);
-    const cpx<T> xnext = t + 1 < P ? pd[t + 1] : mk<T>(T(0), T(0));
+    const cpx<T> xnext = t + 1 < P ? x3[t + 1] : mk<T>(T(0), T(0));
     const cpx<T> xl = fnms(fnms(D1, A1, xf), C1, xnext);
 
     // 4. back substitution of the interior rows
@@ -683,7 +698,8 @@ void set_acc_rows(PintGeom &g) {
   g.acc_rows = g.cta_sum ? (g.R + g.teams_per_cta - 1) / g.teams_per_cta : g.R;
 }
 
-PintGeom pint_geometry(int nf, int nblk, int blen, int target_teams, int elem_bytes, int m_req, int teams_req) {
+PintGeom pint_geometry(int nf, int nblk, int blen, int target_teams, int elem_bytes, int m_req, int teams_req,
+                       bool fact) {
   PintGeom g;
   g.nf = nf;
   g.nblk = nblk;
@@ -703,7 +719,8 @@ PintGeom pint_geometry(int nf, int nblk, int blen, int target_teams, int elem_by
   if (teams_req) g.teams_per_cta = std::max(1, std::min(teams_req, max_threads / g.P));
   // stage tau K in shared memory when the CTA stays within ~160 KB
   const size_t esz = elem_bytes == 16 ? 8 : 4;  // real type of the compute precision
-  const size_t rest = (size_t)g.P * (g.M + 1) * 2 * esz + (size_t)g.P * 5 * 2 * esz + (size_t)g.P * g.M * esz +
+  const size_t rest = (size_t)g.P * (g.M + 1) * 2 * esz + (size_t)g.P * ((fact || g.P < 64) ? 5 : 8) * 2 * esz +
+                      (size_t)g.P * g.M * esz +
                       (size_t)(g.P / 32) * 33 * 16;
   const size_t stage = (size_t)3 * g.P * (g.M + 1) * esz;
   g.stage = (rest + stage) * g.teams_per_cta <= 160 * 1024 ? 1 : 0;
@@ -713,7 +730,8 @@ PintGeom pint_geometry(int nf, int nblk, int blen, int target_teams, int elem_by
 
 template <typename T, int M>
 static void launch_pint_m(Ctx &c, const PintGeom &g, const PintArgs<T> &a) {
-  const size_t tb = TeamSmem<T, M>::bytes(g.P, a.mcount ? (a.want_dots ? a.mdots_max : 0) : a.mdots, g.stage);
+  const size_t tb =
+      TeamSmem<T, M>::bytes(g.P, a.mcount ? (a.want_dots ? a.mdots_max : 0) : a.mdots, g.stage, a.fac_in != nullptr);
   const size_t smem = tb * g.teams_per_cta;
   const int nteams = g.nblk * g.R;
   const int grid = (nteams + g.teams_per_cta - 1) / g.teams_per_cta;

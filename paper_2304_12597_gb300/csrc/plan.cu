@@ -364,16 +364,21 @@ void fill_geometry(pd_plan *p, const pd_desc *d) {
   p->lds = (p->nbar + 31) / 32 * 32;
   const int sms = pd::sm_count();
   const int esz = d->precision == PD_FP64 ? 16 : 8;
-  pd::PintGeom g0 = pd::pint_geometry(p->nf, p->nblk, p->blen, 1, esz, d->tune_pint_rows, d->tune_pint_teams);
+  // factored loops (FP64 by default) need one PCR exchange buffer, eliminating loops two
+  const bool want_fac = d->tune_pint_factor == 1 || (d->tune_pint_factor == 0 && d->precision == PD_FP64);
+  pd::PintGeom g0 =
+      pd::pint_geometry(p->nf, p->nblk, p->blen, 1, esz, d->tune_pint_rows, d->tune_pint_teams, want_fac);
   // one wave of resident teams: occupancy estimated from shared memory and threads
-  const size_t team_bytes = (size_t)g0.P * (g0.M + 1) * esz + (size_t)2 * g0.P * 5 * esz + (size_t)g0.P * g0.M * 8 +
+  const size_t team_bytes = (size_t)g0.P * (g0.M + 1) * esz + (size_t)2 * g0.P * ((want_fac || g0.P < 64) ? 5 : 8) * esz +
+                            (size_t)g0.P * g0.M * 8 +
                             (size_t)(g0.P / 32) * 33 * 16;
   const size_t cta_bytes = team_bytes * g0.teams_per_cta;
   int by_smem = (int)std::max<size_t>(1, (228 * 1024) / (cta_bytes + 1024));
   int by_threads = std::max(1, 2048 / (g0.P * g0.teams_per_cta));
   const int ctas_per_sm = std::max(1, std::min(by_smem, by_threads));
   const int target = sms * ctas_per_sm * g0.teams_per_cta;
-  p->geom = pd::pint_geometry(p->nf, p->nblk, p->blen, target, esz, d->tune_pint_rows, d->tune_pint_teams);
+  p->geom =
+      pd::pint_geometry(p->nf, p->nblk, p->blen, target, esz, d->tune_pint_rows, d->tune_pint_teams, want_fac);
   // Krylov vector kernels: vectors up to 8192 entries run in one 512-thread CTA or (see
   // below) a cluster; beyond, cooperative 64-thread CTAs, at most one per SM (co-resident)
   p->blas_grid = p->nbar <= 8192 ? 1 : (int)std::max<int64_t>(1, std::min<int64_t>((p->nbar + 63) / 64, (int64_t)sms));
@@ -403,8 +408,7 @@ void fill_geometry(pd_plan *p, const pd_desc *d) {
   {  // factors of the shifted systems: computed once per operator, read by every loop
     const size_t esz = p->precision == PD_MIXED ? sizeof(cpx<float>) : sizeof(cpx<double>);
     const size_t fbytes = pd::pint_factor_elems(p->geom) * esz;
-    const bool want = d->tune_pint_factor == 1 || (d->tune_pint_factor == 0 && p->precision == PD_FP64);
-    p->factored = want && fbytes <= ((size_t)4 << 30);
+    p->factored = want_fac && fbytes <= ((size_t)4 << 30);
   }
   p->ctx.pdl = d->tune_no_pdl == 0;
 }
