@@ -225,17 +225,17 @@ __global__ void __launch_bounds__(256) k_fft_c2r(const cpx<T> *__restrict__ S, i
   cpx<T> *buf = reinterpret_cast<cpx<T> *>(smraw);
   const int64_t x0 = (int64_t)blockIdx.x * TX;
   const int np = TX >> 1;
-  const int total = n * np;
   const int half = n >> 1;
+  // each stored row kk <= n/2 is loaded once and fills both Z[kk] and Z[n - kk]
+  const int total = (half + 1) * np;
   for (int i0 = threadIdx.x; i0 < total; i0 += kLoadBatch * blockDim.x) {
     cpx<T> A[kLoadBatch], B[kLoadBatch];
 #pragma unroll
     for (int u = 0; u < kLoadBatch; ++u) {
       const int idx = i0 + u * (int)blockDim.x;
-      const int k = idx / np;
-      const int p = idx - k * np;
+      const int kk = idx / np;
+      const int p = idx - kk * np;
       const int64_t ca = x0 + 2 * p, cb = ca + 1;
-      const int kk = (k <= half) ? k : n - k;
       A[u] = mk<T>(T(0), T(0));
       B[u] = mk<T>(T(0), T(0));
       if (idx < total && ca < ncols) A[u] = S[(int64_t)kk * lds + ca];
@@ -245,11 +245,13 @@ __global__ void __launch_bounds__(256) k_fft_c2r(const cpx<T> *__restrict__ S, i
     for (int u = 0; u < kLoadBatch; ++u) {
       const int idx = i0 + u * (int)blockDim.x;
       if (idx < total) {
-        const int k = idx / np;
-        const int p = idx - k * np;
-        const T sg = k > half ? T(-1) : T(1);  // conjugate half
-        // conj(A + i B) = (A.x - B.y) - i (A.y + B.x)
-        buf[((size_t)p << logn) + bitrev(k, logn)] = mk<T>(A[u].x - sg * B[u].y, -(sg * A[u].y + B[u].x));
+        const int kk = idx / np;
+        const int p = idx - kk * np;
+        cpx<T> *ser = buf + ((size_t)p << logn);
+        // conj(A + i B) = (A.x - B.y) - i (A.y + B.x); at n - kk the conjugate half
+        // gives (A.x + B.y) + i (A.y - B.x)
+        ser[bitrev(kk, logn)] = mk<T>(A[u].x - B[u].y, -(A[u].y + B[u].x));
+        if (kk > 0 && kk < half) ser[bitrev(n - kk, logn)] = mk<T>(A[u].x + B[u].y, A[u].y - B[u].x);
       }
     }
   }
