@@ -8,10 +8,14 @@ What each function follows (paper sections/equations):
 
 * ``be_solve``          eq. (2) by its plain definition: sequential backward Euler
                         (C routines in be_oracle.c).  ParaDiag with alpha = 1 and
-                        exact inner solves reaches exactly this solution.
+                        exact inner solves reaches exactly this solution.  With a
+                        diagonal mass matrix M (``problem.m_diag``) each step solves
+                        (M + tau K) u_j = M u_{j-1} + G_j, the all-at-once system
+                        (B (x) M + I (x) K) u = f of the method's general form.
 * ``be_solve_refined``  ``be_solve`` plus one correction on its extended-precision
                         residual (the reference for FP64 comparisons).
-* ``aao_apply``         left-hand side of eq. (2), (I + tau K) U - U Sigma_1^T.
+* ``aao_apply``         left-hand side of eq. (2), (I + tau K) U - U Sigma_1^T (M in place
+                        of I when the problem has a mass matrix).
 * ``sigma1``, ``c_alpha``  Sigma_1 and the (alpha-)circulant C_alpha, eqs. (3), (15).
 * ``dft_matrix``        F, F_{jk} = omega^{(j-1)(k-1)}, omega = exp(-2 pi i / l)
                         (appendix, proof of Theorem 3.1).
@@ -150,8 +154,11 @@ def operator(problem, dense_limit: int = 4096):
 
 
 def be_solve(problem, G=None, mdiag=None):
-    """Exact solution of eq. (2): sequential backward Euler, u_0 := 0, G_1 = u0 + tau f_1."""
+    """Exact solution of eq. (2): sequential backward Euler, u_0 := 0, G_1 = u0 + tau f_1
+    (G_1 = M u0 + tau f_1 with a mass matrix)."""
     G = problem.G if G is None else G
+    if mdiag is None:
+        mdiag = getattr(problem, "m_diag", None)
     if problem.dim == 1:
         return native.be_tridiag(problem.tau, problem.k_lo, problem.k_diag, problem.k_up, G, mdiag)
     kl, ku, B = k_band(problem)
@@ -178,8 +185,10 @@ def residual_extended(problem, U, G=None):
         KU[:, 1:, :] += problem.k_lo_y[1:].astype(L)[None, :, None] * X[:, :-1, :]
         KU[:, :-1, :] += problem.k_up_y[:-1].astype(L)[None, :, None] * X[:, 1:, :]
         KU = KU.reshape(nt, -1)
-    Rl = np.asarray(G, dtype=np.float64).astype(L) - (Ul + L(problem.tau) * KU)
-    Rl[1:] += Ul[:-1]
+    md = getattr(problem, "m_diag", None)
+    MU = Ul if md is None else np.asarray(md, dtype=np.float64).astype(L)[None, :] * Ul
+    Rl = np.asarray(G, dtype=np.float64).astype(L) - (MU + L(problem.tau) * KU)
+    Rl[1:] += MU[:-1]
     return Rl.astype(np.float64)
 
 
@@ -216,8 +225,10 @@ def aao_apply(problem, U):
         KU[:, 1:, :] += problem.k_lo_y[None, 1:, None] * X[:, :-1, :]
         KU[:, :-1, :] += problem.k_up_y[None, :-1, None] * X[:, 1:, :]
         KU = KU.reshape(U.shape)
-    R = U + tau * KU
-    R[1:] -= U[:-1]
+    md = getattr(problem, "m_diag", None)
+    MU = U if md is None else np.asarray(md, dtype=np.float64)[None, :] * U
+    R = MU + tau * KU
+    R[1:] -= MU[:-1]
     return R
 
 
@@ -457,6 +468,13 @@ def aao_matrix(K, tau, ell, circulant=False):
     n = K.shape[0]
     S = c_alpha(ell, 1.0) if circulant else sigma1(ell)
     return np.kron(np.eye(ell), np.eye(n) + tau * K) - np.kron(S, np.eye(n))
+
+
+def aao_matrix_mass(K, tau, ell, mdiag):
+    """I_l (x) (M + tau K) - Sigma_1 (x) M on vec(U): eq. (2) with a diagonal mass matrix."""
+    n = K.shape[0]
+    M = np.diag(np.asarray(mdiag, dtype=np.float64))
+    return np.kron(np.eye(ell), M + tau * np.asarray(K)) - np.kron(sigma1(ell), M)
 
 
 def periodic_solve_dense(K, tau, R):

@@ -22,5 +22,6 @@ from .gen import (  # noqa: F401
     heat2d_smooth,
     advdiff1d_pulse,
     random_tridiag_problem,
+    with_mass,
     by_name,
 )

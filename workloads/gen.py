@@ -96,6 +96,7 @@ class Problem:
     k_lo_y: Optional[np.ndarray] = None
     k_diag_y: Optional[np.ndarray] = None
     k_up_y: Optional[np.ndarray] = None
+    m_diag: Optional[np.ndarray] = None  # diagonal mass matrix (1D), None = identity
     extra: dict = field(default_factory=dict)
 
     @property
@@ -256,6 +257,19 @@ def random_tridiag_problem(n: int, nt: int, T: float = 1.0, seed: int = 0,
     return Problem(name=f"random_tridiag_n{n}_nt{nt}", dim=1, nx=n, ny=1, nt=nt, T=T,
                    tau=T / nt, k_lo=s * lo, k_diag=s * diag, k_up=s * up, G=G, seed=seed,
                    recipe="random diagonally dominant tridiagonal K, G ~ N(0,1)")
+
+
+def with_mass(P: Problem, seed: int = 0, lo: float = 0.5, hi: float = 2.0) -> Problem:
+    """A copy of the 1D problem P with a diagonal mass matrix, entries uniform in [lo, hi)
+    (a lumped mass of a non-uniform mesh); G is kept as the right-hand side of
+    (M + tau K) u_j = M u_{j-1} + G_j."""
+    if P.dim != 1:
+        raise ValueError("mass matrices are generated for 1D problems")
+    rng = SplitMix64(seed)
+    m = lo + (hi - lo) * rng.uniforms(P.nx)
+    return Problem(name=f"{P.name}_mass{seed}", dim=1, nx=P.nx, ny=1, nt=P.nt, T=P.T, tau=P.tau,
+                   k_lo=P.k_lo.copy(), k_diag=P.k_diag.copy(), k_up=P.k_up.copy(), G=P.G.copy(), seed=P.seed,
+                   recipe=P.recipe + f"; diagonal mass matrix U[{lo}, {hi}) (seed {seed})", m_diag=m)
 
 
 def config1(seed: int = 0) -> Problem:
