@@ -73,6 +73,14 @@ typedef struct pd_desc {
    * Toeplitz (constant diagonal and constant off-diagonal) and ny + 1 to be a power
    * of two <= 4096, so that T_y is diagonalised by the orthonormal DST-I. */
   const double *k_lo_y, *k_diag_y, *k_up_y;
+  /* Diagonal mass matrix M (1D only; NULL = identity), host memory, length nx (batch *
+   * nx for a batch, one entry per row of every slot), every entry > 0 and finite.  The
+   * system is then (B (x) M + I (x) K) u = f: each step solves (M + tau K) u_j =
+   * M u_{j-1} + G_j, with G_1 = M u_0 + tau f_1.  The plan solves for w = M^{1/2} u with
+   * K' = M^{-1/2} K M^{-1/2} (symmetric scaling, so K' stays tridiagonal and Algorithm 1
+   * applies unchanged) and scales G and U on the device.  The stage entry points work
+   * in those scaled variables. */
+  const double *m_diag;
   int32_t precision;     /* pd_precision */
   int32_t maxit;         /* Algorithm 2 iteration limit, 1 <= maxit <= 32 (0 = 32) */
   double eps_krylov;     /* Algorithm 2 tolerance epsilon (stop when ||r|| <= eps * ||b||);

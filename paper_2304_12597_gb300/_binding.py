@@ -44,6 +44,7 @@ class PdDesc(ctypes.Structure):
         ("k_lo_y", _dp),
         ("k_diag_y", _dp),
         ("k_up_y", _dp),
+        ("m_diag", _dp),
         ("precision", ctypes.c_int32),
         ("maxit", ctypes.c_int32),
         ("eps_krylov", ctypes.c_double),

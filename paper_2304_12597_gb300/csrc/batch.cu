@@ -94,4 +94,20 @@ void launch_batch_unscale(Ctx &c, double *U, int64_t nt, int batch, int nxm, con
                                   nxb); });
 }
 
+// out[t][j] = in[t][j] * s[j] (in place allowed): the diagonal mass matrix's symmetric
+// scaling of G (s = M^{-1/2}) and of U (s = M^{-1/2}, from w = M^{1/2} u).
+__global__ void k_col_scale(const double *in, double *out, int nb, const double *__restrict__ s) {
+  grid_dep_wait();
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nb) return;
+  const int64_t o = (int64_t)blockIdx.y * nb + j;
+  out[o] = in[o] * s[j];
+}
+
+void launch_col_scale(Ctx &c, const double *in, double *out, int64_t nt, int64_t nb, const double *s) {
+  const dim3 grid((unsigned)((nb + 255) / 256), (unsigned)nt);
+  c.launch("mass_scale", (double)nt * nb * 16.0,
+           [&] { pdl_launch(c.pdl, k_col_scale, grid, dim3(256), 0, c.stream, in, out, (int)nb, s); });
+}
+
 }  // namespace pd

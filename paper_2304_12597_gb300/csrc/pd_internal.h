@@ -230,6 +230,8 @@ void launch_zsum(Ctx &c, int nf, int64_t n, const cpx<T> *H, int64_t ldh, const 
 void launch_batch_normalize(Ctx &c, const double *G, double *Gs, int64_t nt, int batch, int nxm, int nc,
                             double *part, int *ex);
 void launch_batch_unscale(Ctx &c, double *U, int64_t nt, int batch, int nxm, const int *ex, const int *nxb);
+// out[t][j] = in[t][j] * s[j] over nt rows of nb columns (in place allowed; batch.cu)
+void launch_col_scale(Ctx &c, const double *in, double *out, int64_t nt, int64_t nb, const double *s);
 // Batched plans: per-problem ||delta||^2 from the inverse DFT's per-column sums, then the
 // refinement decision over all problems (control.cu).
 void launch_member_decide(Ctx &c, const double *colsum, int nxm, const int *nxb, int nmem, double *d2, double *ref2,

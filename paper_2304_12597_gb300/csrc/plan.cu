@@ -184,6 +184,9 @@ struct pd_plan {
   double *md2 = nullptr, *mref2 = nullptr, *mprev = nullptr;  // per-problem refinement state
   int *mex = nullptr;  // per-problem residual scaling 2^mex of the next refinement sweep
   int members = 0;     // batched plans: one Algorithm 2 per problem (0 = one for the plan)
+  bool mass = false;   // diagonal mass matrix: solve for w = M^{1/2} u with K' = M^{-1/2} K M^{-1/2}
+  double *msc = nullptr;  // M^{-1/2} (n_bar)
+  double *Gm = nullptr;   // M^{-1/2} G (nt, n_bar)
   bool factored = false;  // the shifted systems are factored once per operator (fac)
   void *fac = nullptr;
   double *mscal = nullptr;  // per-problem Algorithm-2 scalar and flag blocks
@@ -272,6 +275,14 @@ pd_status validate(const pd_desc *d) {
     return fail(PD_ERR_INVALID_ARG, "negative tolerance or sweep count");
   const int64_t blen = d->nx;
   if (blen > 4096) return fail(PD_ERR_UNSUPPORTED, "tridiagonal blocks longer than 4096 rows are not built");
+  if (d->m_diag) {  // diagonal mass matrix: symmetric scaling keeps K tridiagonal (1D only)
+    if (d->dim != 1)
+      return fail(PD_ERR_UNSUPPORTED, "a mass matrix is built for 1D problems (2D needs M (x) structure for the DST)");
+    const int64_t nm = d->nx * (d->batch > 1 ? d->batch : 1);
+    for (int64_t i = 0; i < nm; ++i)
+      if (!(d->m_diag[i] > 0.0) || !std::isfinite(d->m_diag[i]))
+        return fail(PD_ERR_INVALID_ARG, "m_diag[%lld] = %g must be finite and > 0", (long long)i, d->m_diag[i]);
+  }
   if (d->dim == 2) {
     if (!d->k_lo_y || !d->k_diag_y || !d->k_up_y) return fail(PD_ERR_INVALID_ARG, "T_y arrays are NULL");
     if (!is_pow2(d->ny + 1) || d->ny + 1 > 4096)
@@ -405,6 +416,7 @@ void fill_geometry(pd_plan *p, const pd_desc *d) {
   if (p->batch > 1 && !d->tune_cap_ctas)
     p->k5_grid_members = std::max(1, std::min(p->k5_grid, (2 * sms + p->batch - 1) / p->batch));
   p->ctx.fft_cols = d->tune_fft_cols;
+  p->mass = d->m_diag != nullptr;
   {  // factors of the shifted systems: computed once per operator, read by every loop
     const size_t esz = p->precision == PD_MIXED ? sizeof(cpx<float>) : sizeof(cpx<double>);
     const size_t fbytes = pd::pint_factor_elems(p->geom) * esz;
@@ -497,6 +509,10 @@ size_t layout(pd_plan *p, unsigned char *base) {
   if (mixed && p->dim == 2) p->tmp_f = A.take<float>((size_t)nt * nbar);
   if (!mixed) p->res_d = A.take<double>((size_t)nt * nbar);
   if (!mixed && p->dim == 2) p->tmp_d = A.take<double>((size_t)nt * nbar);
+  if (p->mass) {
+    p->msc = A.take<double>(nbar);
+    p->Gm = A.take<double>((size_t)nt * nbar);
+  }
   if (p->batch > 1) {
     p->Gs = A.take<double>((size_t)nt * nbar);
     p->bpart = A.take<double>((size_t)p->batch * p->bnc);
@@ -539,7 +555,31 @@ HostOp build_batched_operator(const pd_desc *d) {
   return h;
 }
 
+// K' = M^{-1/2} K M^{-1/2} for a diagonal mass matrix (1D rows; the batch's blocks stay
+// decoupled since only existing couplings are scaled).
+void scale_by_mass(HostOp &h, const double *m) {
+  const int64_t n = (int64_t)h.xdiag.size();
+  std::vector<double> s(n);
+  for (int64_t j = 0; j < n; ++j) s[j] = 1.0 / std::sqrt(m[j]);
+  for (int64_t j = 0; j < n; ++j) {
+    h.xdiag[j] *= s[j] * s[j];
+    if (j > 0) h.xlo[j] *= s[j] * s[j - 1];
+    if (j + 1 < n) h.xup[j] *= s[j] * s[j + 1];
+  }
+  h.lo = h.xlo;
+  h.diag = h.xdiag;
+  h.up = h.xup;
+}
+
+HostOp build_operator_plain(const pd_desc *d);
+
 HostOp build_operator(const pd_desc *d) {
+  HostOp h = build_operator_plain(d);
+  if (d->m_diag && d->dim == 1) scale_by_mass(h, d->m_diag);
+  return h;
+}
+
+HostOp build_operator_plain(const pd_desc *d) {
   if (d->batch > 1) return build_batched_operator(d);
   HostOp h;
   const int64_t nx = d->nx, ny = d->dim == 2 ? d->ny : 1;
@@ -632,6 +672,13 @@ pd_status upload_operator(pd_plan *p, const pd_desc *desc) {
     std::vector<int> bnx(p->batch);
     for (int b = 0; b < p->batch; ++b) bnx[b] = (int)(desc->batch_nx ? desc->batch_nx[b] : desc->nx);
     if ((st = upload(p->bnx, bnx.data(), p->batch, s))) return st;
+  }
+  std::vector<double> msc;
+  if (p->mass) {  // M^{-1/2}; identity when the descriptor carries no mass matrix
+    msc.assign(nbar, 1.0);
+    if (desc->m_diag)
+      for (int64_t j = 0; j < nbar; ++j) msc[j] = 1.0 / std::sqrt(desc->m_diag[j]);
+    if ((st = upload(p->msc, msc.data(), nbar, s))) return st;
   }
   // the host vectors die on return: wait for the copies
   if (cudaStreamSynchronize(s) != cudaSuccess) return fail(PD_ERR_CUDA, "operator upload failed");
@@ -1290,6 +1337,8 @@ pd_status paradiag_set_operator(pd_plan *p, const pd_desc *desc) {
   if (desc->dim != p->dim || desc->nx != p->nxm || ny != p->ny || desc->nt != p->nt || batch != p->batch ||
       desc->precision != p->precision)
     return fail(PD_ERR_INVALID_ARG, "paradiag_set_operator: desc has a different shape or precision than the plan");
+  if (desc->m_diag && !p->mass)
+    return fail(PD_ERR_INVALID_ARG, "paradiag_set_operator: the plan was built without a mass matrix");
   if (batch == 1 && desc->tau != p->tau) {  // tau reaches some kernels by value: re-capture
     if (p->ctx.stream) cudaStreamSynchronize(p->ctx.stream);
     drop_graph(p);
@@ -1333,13 +1382,18 @@ pd_status paradiag_solve(pd_plan *p, const double *G, double *U, pd_stats *stats
   CK(cudaEventRecord(p->ev0, p->ctx.stream));
   pd_stats s{};
   const double *Gin = G;
+  if (p->mass) {  // G' = M^{-1/2} G: the system for w = M^{1/2} u
+    pd::launch_col_scale(p->ctx, G, p->Gm, p->nt, p->nbar, p->msc);
+    Gin = p->Gm;
+  }
   if (p->batch > 1) {  // every problem of the batch scaled to unit norm (exactly, by 2^k)
-    pd::launch_batch_normalize(p->ctx, G, p->Gs, p->nt, p->batch, (int)p->nxm, p->bnc, p->bpart, p->bex);
+    pd::launch_batch_normalize(p->ctx, Gin, p->Gs, p->nt, p->batch, (int)p->nxm, p->bnc, p->bpart, p->bex);
     Gin = p->Gs;
   }
   st = p->precision == PD_FP64 ? solve_refined<double>(p, Gin, U, s) : solve_refined<float>(p, Gin, U, s);
   if (st == PD_ERR_CUDA) return st;
   if (p->batch > 1) pd::launch_batch_unscale(p->ctx, U, p->nt, p->batch, (int)p->nxm, p->bex, p->bnx);
+  if (p->mass) pd::launch_col_scale(p->ctx, U, U, p->nt, p->nbar, p->msc);  // u = M^{-1/2} w
   CK(cudaEventRecord(p->ev1, p->ctx.stream));
   CK(cudaEventSynchronize(p->ev1));
   float ms = 0.f;
@@ -1360,7 +1414,7 @@ pd_status paradiag_solve_host(pd_plan *p, const double *G_host, double *U_host, 
   if (!G_host || !U_host) return fail(PD_ERR_INVALID_ARG, "G_host and U_host must be non-NULL");
   const size_t bytes = (size_t)p->nt * p->nbar * sizeof(double);
   CK(cudaMemcpyAsync(p->G_stage, G_host, bytes, cudaMemcpyHostToDevice, p->ctx.stream));
-  if (p->batch <= 1) {  // no kernel follows the graph: its final read can carry U back
+  if (p->batch <= 1 && !p->mass) {  // no kernel follows the graph: its final read can carry U back
     p->tail_dst = U_host;
     p->tail_src = p->U_stage;
     p->tail_bytes = bytes;

@@ -32,7 +32,7 @@ class Plan:
     """
 
     def __init__(self, *, dim, nx, nt, tau, k_lo, k_diag, k_up, ny=1, k_lo_y=None, k_diag_y=None,
-                 k_up_y=None, precision="mixed", maxit=0, eps_krylov=0.0, max_refine=0, refine_tol=0.0,
+                 k_up_y=None, m_diag=None, precision="mixed", maxit=0, eps_krylov=0.0, max_refine=0, refine_tol=0.0,
                  alpha=1.0, host_io=False, no_graph=False, tune=None, batch=1, batch_nx=None, batch_tau=None,
                  device=None, stream=None, workspace="torch"):
         import torch
@@ -44,7 +44,8 @@ class Plan:
         self.batch = max(int(batch), 1)
         self.nbar = self.nx * self.ny * self.batch
         self.precision = precision
-        self._arrays = [_f64(k_lo), _f64(k_diag), _f64(k_up), _f64(k_lo_y), _f64(k_diag_y), _f64(k_up_y)]
+        self._arrays = [_f64(k_lo), _f64(k_diag), _f64(k_up), _f64(k_lo_y), _f64(k_diag_y), _f64(k_up_y),
+                        _f64(m_diag)]
         self._batch_nx = None if batch_nx is None else np.ascontiguousarray(batch_nx, dtype=np.int64)
         self._batch_tau = _f64(batch_tau)
         d = B.PdDesc()
@@ -54,7 +55,7 @@ class Plan:
         d.ny = self.ny
         d.nt = self.nt
         d.tau = float(tau)
-        d.k_lo, d.k_diag, d.k_up, d.k_lo_y, d.k_diag_y, d.k_up_y = [_ptr(a) for a in self._arrays]
+        d.k_lo, d.k_diag, d.k_up, d.k_lo_y, d.k_diag_y, d.k_up_y, d.m_diag = [_ptr(a) for a in self._arrays]
         d.precision = {"fp64": B.PD_FP64, "mixed": B.PD_MIXED}[precision]
         d.maxit = int(maxit)
         d.eps_krylov = float(eps_krylov)
@@ -96,9 +97,14 @@ class Plan:
         nx = max(max(P.nx for P in problems), int(kw.pop("nx", 0) or 0))  # slot length
         B = len(problems)
         lo, di, up = np.zeros((B, nx)), np.ones((B, nx)), np.zeros((B, nx))
+        md = np.ones((B, nx))
         for b, P in enumerate(problems):
             lo[b, :P.nx], di[b, :P.nx], up[b, :P.nx] = P.k_lo, P.k_diag, P.k_up
+            if getattr(P, "m_diag", None) is not None:
+                md[b, :P.nx] = P.m_diag
+        any_mass = any(getattr(P, "m_diag", None) is not None for P in problems)
         args = dict(dim=1, nx=nx, nt=nt, tau=problems[0].tau, k_lo=lo.ravel(), k_diag=di.ravel(), k_up=up.ravel(),
+                    m_diag=md.ravel() if any_mass else None,
                     batch=B, batch_nx=[P.nx for P in problems], batch_tau=[P.tau for P in problems])
         args.update(kw)
         return cls(**args)
@@ -120,20 +126,21 @@ class Plan:
         """Build from any object with the fields of workloads.Problem."""
         args = dict(dim=problem.dim, nx=problem.nx, ny=problem.ny, nt=problem.nt, tau=problem.tau,
                     k_lo=problem.k_lo, k_diag=problem.k_diag, k_up=problem.k_up,
-                    k_lo_y=problem.k_lo_y, k_diag_y=problem.k_diag_y, k_up_y=problem.k_up_y)
+                    k_lo_y=problem.k_lo_y, k_diag_y=problem.k_diag_y, k_up_y=problem.k_up_y,
+                    m_diag=getattr(problem, "m_diag", None))
         args.update(kw)
         return cls(**args)
 
-    def set_operator(self, *, tau, k_lo, k_diag, k_up, k_lo_y=None, k_diag_y=None, k_up_y=None, batch_nx=None,
-                     batch_tau=None):
-        """Swap in a new operator of the same shape (paradiag_set_operator)."""
-        arrays = [_f64(k_lo), _f64(k_diag), _f64(k_up), _f64(k_lo_y), _f64(k_diag_y), _f64(k_up_y)]
+    def set_operator(self, *, tau, k_lo, k_diag, k_up, k_lo_y=None, k_diag_y=None, k_up_y=None, m_diag=None,
+                     batch_nx=None, batch_tau=None):
+        """Swap in a new operator (and mass matrix) of the same shape (paradiag_set_operator)."""
+        arrays = [_f64(k_lo), _f64(k_diag), _f64(k_up), _f64(k_lo_y), _f64(k_diag_y), _f64(k_up_y), _f64(m_diag)]
         bnx = None if batch_nx is None else np.ascontiguousarray(batch_nx, dtype=np.int64)
         btau = _f64(batch_tau)
         d = B.PdDesc()
         ctypes.pointer(d)[0] = self.desc  # copy of the plan's descriptor
         d.tau = float(tau)
-        d.k_lo, d.k_diag, d.k_up, d.k_lo_y, d.k_diag_y, d.k_up_y = [_ptr(a) for a in arrays]
+        d.k_lo, d.k_diag, d.k_up, d.k_lo_y, d.k_diag_y, d.k_up_y, d.m_diag = [_ptr(a) for a in arrays]
         d.batch_nx = bnx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)) if bnx is not None else None
         d.batch_tau = _ptr(btau) if btau is not None else None
         B.paradiag_set_operator(self.handle, d)

@@ -75,7 +75,7 @@ def _desc(B, **kw):
     d.k_lo, d.k_diag, d.k_up = p(lo), p(di), p(up)
     d.precision = 0
     for k, v in kw.items():
-        if k.startswith("y_") or k in ("batch_nx", "batch_tau", "batch_k"):
+        if k.startswith("y_") or k in ("batch_nx", "batch_tau", "batch_k", "mass"):
             continue
         setattr(d, k, v)
     if kw.get("batch", 0) > 1:  # K arrays hold batch * nx rows
@@ -91,6 +91,10 @@ def _desc(B, **kw):
             bt = np.asarray(kw["batch_tau"], dtype=np.float64)
             keep.append(bt)
             d.batch_tau = p(bt)
+    if "mass" in kw:  # diagonal mass matrix, one entry per row (of every slot)
+        m = np.asarray(kw["mass"], dtype=np.float64)
+        keep.append(m)
+        d.m_diag = p(m)
     if kw.get("dim") == 2:
         ny = kw.get("ny", 7)
         ylo = kw.get("y_lo", np.full(ny, -1.0))
@@ -113,6 +117,7 @@ def test_valid_descriptors_have_a_workspace(B):
                 "tune_cap_ctas": 3, "tune_fft_cols": 2},
                {"tune_krylov_cluster": 16}, {"tune_krylov_cluster": -1}, {"tune_krylov_ctas": 1, "n": 4095},
                {"tune_pint_factor": 1, "precision": 1}, {"tune_pint_factor": -1},
+               {"mass": np.full(31, 0.5)}, {"mass": np.linspace(0.5, 2.0, 62), "batch": 2},
                {"batch": 3, "batch_nx": [31, 5, 1], "batch_tau": [0.1, 0.2, 1e-3]}, {"batch": 4},
                {"alpha": 1e-4}, {"alpha": 0.5, "precision": 1},
                {"dim": 2, "ny": 7}, {"dim": 2, "ny": 255, "n": 255, "nt": 256, "precision": 1}):
@@ -147,6 +152,9 @@ def test_valid_descriptors_have_a_workspace(B):
     ({"tune_krylov_ctas": 1, "n": 4095, "batch": 3}, 2),   # one CTA holds <= 8192 entries
     ({"tune_krylov_cluster": 2}, 1),
     ({"tune_pint_factor": 2}, 1),
+    ({"mass": np.full(31, 1.0), "dim": 2, "ny": 7}, 2),        # mass matrices: 1D only
+    ({"mass": np.concatenate([np.ones(30), [0.0]])}, 1),       # entries must be > 0
+    ({"mass": np.concatenate([np.ones(30), [np.nan]])}, 1),
     ({"tune_krylov_cluster": 32}, 1),
     ({"tune_cap_ctas": 5000}, 1),
     ({"tune_fft_cols": 6}, 1),
@@ -169,3 +177,11 @@ def test_null_arguments_are_rejected(B):
     assert L.paradiag_solve(None, None, None, None) == 1
     assert L.paradiag_destroy(None) == 0
     assert "sm_103a" in B.paradiag_version()
+
+
+def test_mass_matrix_adds_its_scaling_buffers(B):
+    """A mass matrix adds M^{-1/2} and a scaled copy of G to the workspace."""
+    st0, n0 = _size_status(B, _desc(B))
+    st1, n1 = _size_status(B, _desc(B, mass=np.full(31, 2.0)))
+    assert st0 == 0 and st1 == 0
+    assert n1 >= n0 + (16 * 31 + 31) * 8
