@@ -102,6 +102,12 @@ def max_over_ranks(value, world, device=None):
     return float(t.item())
 
 
+def replica_throughput(unknowns_per_step, steps, world, max_ms):
+    """Whole-job unknowns/s of `world` independent replicas that each ran `steps` solves,
+    timed by the slowest rank (max_ms over the timed region)."""
+    return unknowns_per_step * steps * world / (max_ms / 1e3)
+
+
 def barrier(world):
     if world > 1:
         import torch.distributed as dist
@@ -262,7 +268,7 @@ def run_ours(args):
     barrier(world)
     total_ms = max_over_ranks(sum(ts), world, device)
     U_mixed = U.cpu().numpy()
-    value = unknowns * args.steps * world / (total_ms / 1e3)
+    value = replica_throughput(unknowns, args.steps, world, total_ms)
 
     # ---- per-kernel timing pass (same workload, CUDA events on the plan's stream) ----
     mixed.set_timing(True)
