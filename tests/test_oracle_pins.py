@@ -468,3 +468,24 @@ def test_algorithm3_early_exit_on_u1():
     assert R.rel_err(U, R.be_solve(P)) <= 1e-6
     _, info = R.paradiag_alpha(P, 1e-12, early_exit_eps=1e-6)
     assert not info["exited_early"]
+
+
+@pytest.mark.parametrize("mass", [False, True])
+def test_build_rhs_steps_backward_euler(mass):
+    """G from build_rhs (eq. 2: G_1 = M u0 + tau f_1, G_j = tau f_j) makes the oracle's solve
+    equal to backward Euler stepped by hand from u0 with dense solves of (M + tau K)."""
+    P = W.random_tridiag_problem(23, 12, seed=4)
+    rng = np.random.default_rng(8)
+    u0, f = rng.standard_normal(P.nx), rng.standard_normal((P.nt, P.nx))
+    m = 0.5 + 1.5 * rng.random(P.nx) if mass else None
+    Mm = np.diag(m) if mass else np.eye(P.nx)
+    A = Mm + P.tau * R.k_dense(P)
+    u, Ue = u0, np.empty((P.nt, P.nx))
+    for j in range(P.nt):
+        u = np.linalg.solve(A, Mm @ u + P.tau * f[j])
+        Ue[j] = u
+    G = W.build_rhs(u0, f, P.tau, m)
+    assert R.rel_err(R.be_solve(P, G=G, mdiag=m), Ue) < 1e-13
+    # the generators' f = 0 right-hand sides are build_rhs of their initial values
+    S = W.heat1d_sine_modes(31, 8)
+    assert np.array_equal(W.build_rhs(S.G[0], np.zeros_like(S.G), S.tau), S.G)

@@ -23,5 +23,6 @@ from .gen import (  # noqa: F401
     advdiff1d_pulse,
     random_tridiag_problem,
     with_mass,
+    build_rhs,
     by_name,
 )

@@ -144,6 +144,26 @@ def advdiff1d_operator(n: int, a: float, nu: float):
     return lo, diag, up
 
 
+def build_rhs(u0: np.ndarray, f, tau: float, m_diag=None) -> np.ndarray:
+    """Right-hand side G of the all-at-once system (eq. 2) from an initial value and a forcing.
+
+    u0: (n_x,) initial value.  f: (n_t, n_x) forcing sampled at t_1..t_l (zeros for f = 0).
+    tau: time step.
+    m_diag: optional (n_x,) diagonal mass matrix.  Returns G with G_1 = M u0 + tau f_1 and
+    G_j = tau f_j for j > 1, so that (M + tau K) u_j = M u_{j-1} + G_j with u_0 = 0 steps the
+    scheme.  The right-hand side printed with eq. 4 drops the factor tau on f; eq. 2 carries it.
+    """
+    f = np.asarray(f, dtype=np.float64)
+    if f.ndim != 2:
+        raise ValueError("f must be (n_t, n_x)")
+    u0 = np.asarray(u0, dtype=np.float64).reshape(-1)
+    if u0.shape[0] != f.shape[1]:
+        raise ValueError("u0 and f disagree on n_x")
+    G = tau * f
+    G[0] += u0 if m_diag is None else np.asarray(m_diag, dtype=np.float64) * u0
+    return G
+
+
 def heat1d_sine_modes(n: int = 127, nt: int = 64, T: float = 1.0, seed: int = 0,
                       modes: int = 8) -> Problem:
     """1D heat, f = 0, u0 = sin(pi x) + sum_q a_q sin(k_q pi x), a_q ~ N(0, 0.1).
