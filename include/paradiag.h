@@ -139,9 +139,12 @@ typedef struct pd_desc {
                                 eliminate in every loop; 0: factor PD_FP64 plans only (FP64
                                 elimination is costly on GB300; binary32 elimination costs
                                 less than streaming its factors) */
-  /* Batching (1D only): `batch` independent problems with the same nt are solved
-   * together as one block-diagonal problem (their DFTs, shifted solves, Krylov space
-   * and refinement are shared; the blocks never couple).  Problem b occupies slot b:
+  /* Batching (1D only): `batch` independent problems are solved together as one
+   * block-diagonal problem (their DFTs, shifted solves and refinement sweeps are shared,
+   * each problem runs its own Algorithm 2, and the blocks never couple).  A problem with
+   * fewer time steps nt_b < nt rides along exactly: backward Euler is causal, so rows
+   * 1..nt_b of the solution depend on rows 1..nt_b of G alone; give it zero rows
+   * nt_b+1..nt in G and read the first nt_b rows of U.  Problem b occupies slot b:
    * columns [b*nx, b*nx + nx_b) of G and U, rows [b*nx, b*nx + nx_b) of k_lo/k_diag/
    * k_up (so those arrays have length batch*nx); columns nx_b..nx-1 of a slot must be
    * zero in G and are returned as zero.  Each problem is scaled to unit Frobenius norm

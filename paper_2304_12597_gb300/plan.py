@@ -88,12 +88,16 @@ class Plan:
 
     @classmethod
     def from_problems(cls, problems, **kw):
-        """One batched plan for a list of 1D problems with the same nt (fields of
-        workloads.Problem).  Slot b holds problem b, padded to the largest n_x (or to
-        the keyword nx, if larger)."""
-        nt = problems[0].nt
-        if any(P.dim != 1 or P.nt != nt for P in problems):
-            raise ValueError("a batch needs 1D problems with one common nt")
+        """One batched plan for a list of 1D problems (fields of workloads.Problem).  Slot b
+        holds problem b, padded to the largest n_x (or to the keyword nx, if larger).
+
+        The plan's n_t is the largest n_t,b.  Backward Euler is causal: rows 1..l_b of the
+        all-at-once solution depend only on rows 1..l_b of G.  So a problem with fewer time
+        steps is solved exactly by the longer system with its G extended by zero rows
+        (stack), and its answer is the first n_t,b rows of its slot (unstack)."""
+        nt = max(P.nt for P in problems)
+        if any(P.dim != 1 for P in problems):
+            raise ValueError("a batch needs 1D problems")
         nx = max(max(P.nx for P in problems), int(kw.pop("nx", 0) or 0))  # slot length
         B = len(problems)
         lo, di, up = np.zeros((B, nx)), np.ones((B, nx)), np.zeros((B, nx))
@@ -110,16 +114,21 @@ class Plan:
         return cls(**args)
 
     def stack(self, arrays):
-        """(nt, batch * nx) float64 array with array b (nt, n_x,b) in slot b, zero-padded."""
+        """(nt, batch * nx) float64 array with array b (n_t,b, n_x,b) in slot b, zero-padded
+        in space and, past row n_t,b, in time."""
         out = np.zeros((self.nt, self.batch, self.nx))
         for b, a in enumerate(arrays):
-            out[:, b, :a.shape[1]] = a
+            if a.shape[0] > self.nt or a.shape[1] > self.nx:
+                raise ValueError("array does not fit its slot")
+            out[:a.shape[0], b, :a.shape[1]] = a
         return out.reshape(self.nt, self.batch * self.nx)
 
-    def unstack(self, U, nxs):
-        """Slot b of a (nt, batch * nx) array, cut to n_x,b columns."""
+    def unstack(self, U, nxs, nts=None):
+        """Slot b of a (nt, batch * nx) array, cut to n_x,b columns and its first n_t,b rows
+        (all rows when nts is None)."""
         V = U.reshape(self.nt, self.batch, self.nx)
-        return [V[:, b, :n] for b, n in enumerate(nxs)]
+        nts = [self.nt] * len(nxs) if nts is None else nts
+        return [V[:t, b, :n] for b, (n, t) in enumerate(zip(nxs, nts))]
 
     @classmethod
     def from_problem(cls, problem, **kw):
@@ -148,9 +157,9 @@ class Plan:
         self.desc = d
 
     def set_problems(self, problems):
-        """Swap in the operators of a list of 1D problems (same batch size, n_t and
-        n_x <= the plan's slot length); see from_problems."""
-        if len(problems) != self.batch or any(P.dim != 1 or P.nt != self.nt or P.nx > self.nx for P in problems):
+        """Swap in the operators of a list of 1D problems (same batch size, n_t,b <= the
+        plan's n_t and n_x,b <= its slot length); see from_problems."""
+        if len(problems) != self.batch or any(P.dim != 1 or P.nt > self.nt or P.nx > self.nx for P in problems):
             raise ValueError("problems do not fit this plan's slots")
         nx = self.nx
         lo, di, up = np.zeros((self.batch, nx)), np.ones((self.batch, nx)), np.zeros((self.batch, nx))

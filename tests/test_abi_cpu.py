@@ -185,3 +185,23 @@ def test_mass_matrix_adds_its_scaling_buffers(B):
     st1, n1 = _size_status(B, _desc(B, mass=np.full(31, 2.0)))
     assert st0 == 0 and st1 == 0
     assert n1 >= n0 + (16 * 31 + 31) * 8
+
+
+def test_batch_stack_pads_time_and_unstack_cuts_it():
+    """Host side of uneven-n_t batches: stack zero-pads each problem's G past its n_t and
+    n_x; unstack returns each problem's first n_t,b rows and n_x,b columns."""
+    from types import SimpleNamespace
+    from paper_2304_12597_gb300.plan import Plan
+    slots = SimpleNamespace(nt=8, batch=3, nx=5)
+    arrays = [np.full((8, 5), 1.0), np.full((2, 3), 2.0), np.full((4, 1), 3.0)]
+    S = Plan.stack(slots, arrays)
+    assert S.shape == (8, 15)
+    V = S.reshape(8, 3, 5)
+    assert np.all(V[:, 0] == 1.0)
+    assert np.all(V[:2, 1, :3] == 2.0) and not np.any(V[2:, 1]) and not np.any(V[:, 1, 3:])
+    assert np.all(V[:4, 2, :1] == 3.0) and not np.any(V[4:, 2]) and not np.any(V[:, 2, 1:])
+    parts = Plan.unstack(slots, S, [5, 3, 1], [8, 2, 4])
+    for a, b in zip(arrays, parts):
+        assert np.array_equal(a, b)
+    with pytest.raises(ValueError):
+        Plan.stack(slots, [np.zeros((9, 5))])

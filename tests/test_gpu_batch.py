@@ -124,3 +124,32 @@ def test_batch_of_identical_problems_is_deterministic(pd):
     ref = R.be_solve_refined(P)
     for Ub in parts:
         assert R.rel_err(Ub, ref) <= TOL["mixed"]
+
+
+def _uneven_nt_mix():
+    """Uneven n_x and n_t (16..256) with different tau, operators and magnitudes."""
+    return [
+        _scaled(W.heat1d_forced(255, 256, seed=1), 1.0),
+        _scaled(W.heat1d_forced(127, 64, T=0.5, seed=2), 1e-6),
+        _scaled(W.advdiff1d_pulse(300, 128, seed=3), 1e4),
+        W.random_tridiag_problem(33, 16, seed=4),
+        _scaled(W.heat1d_sine_modes(63, 32, seed=5), 3e-3),
+        W.random_tridiag_problem(1, 256, seed=6),
+    ]
+
+
+@pytest.mark.parametrize("prec,alpha", MIXES)
+def test_batch_of_uneven_nt_matches_oracle_per_problem(pd, prec, alpha):
+    """Problems with fewer time steps ride in the longest problem's plan (zero rows of G
+    past their n_t, causality of backward Euler): each one's first n_t,b rows match the
+    oracle on its own n_t,b."""
+    probs = _uneven_nt_mix()
+    with pd.Plan.from_problems(probs, precision=prec, alpha=alpha, device=dev()) as plan:
+        assert plan.nt == 256
+        G = torch.from_numpy(plan.stack([P.G for P in probs])).to(dev())
+        U, st = plan.solve(G)
+        parts = plan.unstack(U.cpu().numpy(), [P.nx for P in probs], [P.nt for P in probs])
+    for P, Ub in zip(probs, parts):
+        assert Ub.shape == (P.nt, P.nx)
+        err = R.rel_err(Ub, R.be_solve_refined(P))
+        assert err <= TOL[prec], (P.name, err, st)

@@ -489,3 +489,18 @@ def test_build_rhs_steps_backward_euler(mass):
     # the generators' f = 0 right-hand sides are build_rhs of their initial values
     S = W.heat1d_sine_modes(31, 8)
     assert np.array_equal(W.build_rhs(S.G[0], np.zeros_like(S.G), S.tau), S.G)
+
+
+def test_backward_euler_is_causal_under_time_padding():
+    """Rows 1..l of the all-at-once solution depend on rows 1..l of G only: extending G by
+    zero rows leaves those rows of the oracle's solution unchanged (the reading that lets
+    a batch carry problems of fewer time steps), and the dense all-at-once solve agrees."""
+    P = W.random_tridiag_problem(9, 8, seed=11)
+    U = R.be_solve(P)
+    Q = W.random_tridiag_problem(9, 8, seed=11)
+    Q.nt, Q.G = 32, np.vstack([P.G, np.zeros((24, P.nx))])
+    V = R.be_solve(Q)
+    assert np.array_equal(V[:8], U)
+    A = R.aao_matrix_mass(R.k_dense(Q), Q.tau, Q.nt, np.ones(Q.nx))
+    Vd = np.linalg.solve(A, Q.G.reshape(-1)).reshape(Q.nt, Q.nx)
+    assert R.rel_err(Vd[:8], U) < 1e-13
