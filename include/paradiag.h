@@ -92,7 +92,11 @@ typedef struct pd_desc {
                             halving over 1 iteration in PD_MIXED once ||r|| <= 1e-3 ||b||, and
                             at any level in its refinement sweeps; over 3 iterations in PD_FP64
                             once ||r|| <= 1e-6 ||b||) */
-  int32_t q;             /* residual check period of Algorithm 2; only q = 1 is built */
+  int32_t q;             /* residual check period of Algorithm 2 (Sec. 3, the frozen residual):
+                            the shifted solves h_k, eq. (12) and eq. (13) run only at steps
+                            m with m mod q = 0, at m = maxit and at a breakdown, so a solve
+                            runs about m/q + 2 parallel-in-time loops.  0 or 1 = every step;
+                            at most 32; q > 1 is built for single problems (batch <= 1) */
   int32_t max_refine;    /* refinement sweeps after the first solve (0 = 8, 16 for batches,
                             which stop only when every problem has converged).  PD_MIXED always
                             refines; PD_FP64 refines when Algorithm 2 stopped short of
@@ -161,7 +165,8 @@ typedef struct pd_stats {
   int32_t krylov_iters;        /* m of the last Algorithm-2 run */
   int32_t krylov_iters_total;  /* sum of m over all refinement sweeps */
   int32_t pint_loops;          /* parallel-in-time loops in the paper's count, m/q + 2 per solve */
-  int32_t shifted_sweeps;      /* passes over all l/2+1 shifted systems actually executed */
+  int32_t shifted_sweeps;      /* passes over all l/2+1 shifted systems executed (h_k is stored,
+                                  so the residual of eq. (13) needs no second pass) */
   int32_t refine_sweeps;       /* solves performed (first solve + refinement sweeps) */
   int32_t breakdown;           /* 1 if Algorithm 2 met an invariant Krylov space */
   int32_t graph;               /* 1 if the solve ran as one CUDA-graph launch */

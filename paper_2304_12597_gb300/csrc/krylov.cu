@@ -39,13 +39,16 @@ __global__ void __launch_bounds__(MODE == kCoop ? kBlas : MODE == kCluster ? kBl
 
 // One Arnoldi step (eq. 10): w = K v_{m-1}; two classical Gram-Schmidt passes
 // against v_0..v_{m-1} (their coefficients summed into column m-1 of T_m);
-// t = ||w||; v_m = w / t, or breakdown when t <= 1e-14 ||K v_{m-1}||.
+// t = ||w||; v_m = w / t, or breakdown when t <= 1e-14 ||K v_{m-1}||.  With q > 1
+// (Sec. 3: the residual is frozen for q steps) the step is marked frozen unless
+// m is a multiple of q, m = maxit or the space broke down; a frozen step forms no
+// h_k, no eq. (12) system and no eq. (13) residual.
 template <int MODE, int E>
 __global__ void __launch_bounds__(MODE == kCoop ? kBlas : MODE == kCluster ? kBlasCluster : kBlasSingle) k_arnoldi_coop(int n, const double *__restrict__ klo,
                                                         const double *__restrict__ kdiag,
                                                         const double *__restrict__ kup, double *V, float *Vf,
                                                         double *w, double *T, int ldT, double *part, int ld,
-                                                        double *scal, int *flags) {
+                                                        double *scal, int *flags, int q, int maxit) {
   grid_dep_wait();
   __shared__ double red[kRedWords];
   __shared__ double c[34];
@@ -132,6 +135,9 @@ __global__ void __launch_bounds__(MODE == kCoop ? kBlas : MODE == kCluster ? kBl
     scal[S_T] = bd ? 0.0 : t;
     scal[S_KNORM] = knorm;
     flags[F_BREAK] = bd ? 1 : 0;
+    const bool frozen = !bd && q > 1 && m % q != 0 && m < maxit;
+    flags[F_FROZEN] = frozen ? 1 : 0;
+    flags[F_NOH] = (bd || frozen) ? 1 : 0;
     if (!isfinite(t)) flags[F_NONFIN] = 1;
   }
   cluster_exit<MODE>();
@@ -227,6 +233,8 @@ __global__ void __launch_bounds__(kK5Warps * 32) k_capacitance_terms(
     scal += (int64_t)mb * kScalWords;
     flags += (int64_t)mb * kFlagWords;
     if (flags[F_KSTOP]) return;  // this member's Algorithm 2 has stopped (whole CTA)
+  } else if (flags[F_FROZEN]) {
+    return;  // a frozen step (q > 1): no eq. (12) system (every CTA leaves; the counter stays 0)
   }
   const int m = flags[F_M] + 1;
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -550,8 +558,9 @@ void launch_arnoldi(Ctx &c, KrylovBufs &k) {
   double *V = k.V, *w = k.w, *T = k.T, *part = k.part, *scal = k.scal;
   float *Vf = k.Vf;
   int *flags = k.flags;
+  int q = k.q, maxit = k.maxit;
   void *args[] = {&n, (void *)&klo, (void *)&kdiag, (void *)&kup, &V, &Vf, &w, &T, &ldT, &part, (void *)&ld,
-                  &scal, &flags};
+                  &scal, &flags, &q, &maxit};
   coop_launch(c, "krylov_arnoldi", (double)k.n * 8.0 * 8, PD_BY_E(reg_elems(k.n, kBlasSingle), k_arnoldi_coop, kSingle),
               (const void *)k_arnoldi_coop<kCoop, 1>, PD_BY_E(reg_elems(k.n, k.cluster * kBlasCluster), k_arnoldi_coop, kCluster),
               k.grid, k.cluster, args);

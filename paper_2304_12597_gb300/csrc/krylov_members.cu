@@ -118,6 +118,8 @@ __global__ void __launch_bounds__(kBlasSingle) k_member_init(KrylovBufs k, const
     flags[F_NONFIN] = finite ? 0 : 1;
     flags[F_CAPCNT] = 0;
     flags[F_M] = 0;
+    flags[F_FROZEN] = 0;  // no step is frozen until an Arnoldi step says so (q > 1)
+    flags[F_NOH] = 0;
     flags[F_KSTOP] = (finite && !zero) ? 0 : 1;
     flags[F_KCONV] = zero ? 1 : 0;
   }

@@ -11,16 +11,27 @@ namespace pd {
 
 // After an Algorithm-2 step (Sec. 3): record ||r_m||, decide whether to continue:
 // stop at ||r_m|| <= eps beta, at maxit, at a breakdown, or at a stall near the
-// precision floor (no halving over `win` steps once ||r_m|| <= stall_floor beta).
+// precision floor (no halving over `win` checks once ||r_m|| <= stall_floor beta).
+// A frozen step (q > 1, flags[F_FROZEN]) has no residual: it only advances m.
 __device__ __forceinline__ void krylov_decide(double *scal, int *flags, const KrylovCtl &k, int use_handle,
                                               cudaGraphConditionalHandle h) {
   const int m = flags[F_M] + 1;
+  if (flags[F_FROZEN]) {
+    flags[F_M] = m;
+    flags[F_KCONV] = 0;
+    flags[F_KSTOP] = 0;
+    if (use_handle) cudaGraphSetConditional(h, 1u);
+    return;
+  }
   const double res = scal[S_RES], beta = scal[S_BETA];
   if (m < 33) scal[S_HIST + m] = res;
   const bool nonfinite = flags[F_NONFIN] || !isfinite(res);
   if (nonfinite) flags[F_NONFIN] = 1;
   const bool conv = flags[F_BREAK] || res <= k.eps * beta;
-  const bool stall = m >= k.win + 1 && res <= k.stall_floor * beta && res > 0.5 * scal[S_HIST + m - k.win];
+  // checks are q steps apart (the last one may be closer: maxit or a breakdown)
+  const int back = k.win * (k.q > 1 ? k.q : 1);
+  const bool stall = m >= back + 1 && m % (k.q > 1 ? k.q : 1) == 0 && res <= k.stall_floor * beta &&
+                     res > 0.5 * scal[S_HIST + m - back];
   const bool stop = nonfinite || conv || stall || m >= k.maxit;
   flags[F_M] = m;
   flags[F_KCONV] = conv ? 1 : 0;

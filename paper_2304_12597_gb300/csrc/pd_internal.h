@@ -32,6 +32,8 @@ enum FlagIndex {
   F_ZCNT = 13,    // completion counter of the z reduction (runs eq. 13 and the decision)
   F_MEMCNT = 14,  // batched plans: members done in a per-member Algorithm-2 step
   F_SWM = 16,     // [16, 32): m of each solve
+  F_FROZEN = 32,  // this Algorithm-2 step skips the residual check (q > 1, Sec. 3)
+  F_NOH = 33,     // this step forms no h_k: breakdown or a frozen step
   kFlagWords = 64
 };
 enum ScalIndex {
@@ -113,8 +115,9 @@ void set_last_error(const char *msg);
 struct KrylovCtl {
   double eps;          // stop when ||r_m|| <= eps * beta
   double stall_floor;  // stall exit only once ||r_m|| <= stall_floor * beta
-  int win;             // stall: no halving over `win` steps
+  int win;             // stall: no halving over `win` checks
   int maxit;
+  int q;               // residual check every q steps (and at maxit or a breakdown)
 };
 struct RefineCtl {
   int fp64;
@@ -267,6 +270,7 @@ struct KrylovBufs {
   int *mflags;
   double *y;
   int *counter;
+  int q;             // residual check period of Algorithm 2 (single problems; batches use 1)
 };
 // All Algorithm-2 kernels read m from flags[F_M] (completed steps), so one captured
 // iteration serves every m.  `use_handle` / `h`: set a CUDA-graph conditional.

@@ -322,6 +322,8 @@ __device__ __forceinline__ void init_v0_body(const double *__restrict__ b, int n
     if (!finite) flags[F_NONFIN] = 1;
     flags[F_CAPCNT] = 0;
     flags[F_M] = 0;
+    flags[F_FROZEN] = 0;  // no step is frozen until an Arnoldi step says so (q > 1)
+    flags[F_NOH] = 0;
     const bool run = finite && !zero;
     flags[F_KSTOP] = run ? 0 : 1;
     flags[F_KCONV] = zero ? 1 : 0;
@@ -348,8 +350,11 @@ __device__ __forceinline__ void project_body(int n, const double *__restrict__ V
     pb = cslot + kSlot;
     pc = cslot + 2 * kSlot;
   }
-  double zz;
-  if constexpr (MODE == kCoop || MODE == kTail) {
+  double zz = 0.0;
+  // a frozen step (q > 1) forms no z: the decision only advances m (uniform over the grid)
+  const bool frozen = flags[F_FROZEN] != 0;
+  if (frozen) {
+  } else if constexpr (MODE == kCoop || MODE == kTail) {
     grid_dots<MODE>(n, m, V, z, pa, ld, red, c);
     cta_axpy<MODE>(n, m, V, z, c);
     __syncthreads();  // c is rewritten next
@@ -371,7 +376,7 @@ __device__ __forceinline__ void project_body(int n, const double *__restrict__ V
     zz = cgs2_norm2<MODE, E>(m, x, c, pc, red);
   }
   if (g_leader<MODE>()) {
-    scal[S_RES] = flags[F_BREAK] ? 0.0 : fabs(tau * scal[S_T]) * sqrt(zz);
+    if (!frozen) scal[S_RES] = flags[F_BREAK] ? 0.0 : fabs(tau * scal[S_T]) * sqrt(zz);
     krylov_decide(scal, flags, kc, use_handle, h);
   }
   cluster_exit<MODE>();

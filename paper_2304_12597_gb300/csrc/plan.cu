@@ -163,6 +163,7 @@ struct pd_plan {
   double aroot = 1.0;  // alpha^{1/l}
   int precision = PD_FP64;
   int maxit = 32;
+  int q = 1;  // Algorithm 2 checks its residual every q steps (Sec. 3)
   double eps = 1e-13;
   int max_refine = 6;
   double refine_tol = 1e-13;
@@ -269,7 +270,9 @@ pd_status validate(const pd_desc *d) {
   if (!d->k_lo || !d->k_diag || !d->k_up) return fail(PD_ERR_INVALID_ARG, "K coefficient arrays are NULL");
   if (d->precision != PD_FP64 && d->precision != PD_MIXED) return fail(PD_ERR_INVALID_ARG, "bad precision");
   if (d->maxit < 0 || d->maxit > 32) return fail(PD_ERR_UNSUPPORTED, "maxit must be in [1, 32]");
-  if (d->q != 0 && d->q != 1) return fail(PD_ERR_UNSUPPORTED, "only q = 1 (residual check every iteration) is built");
+  if (d->q < 0 || d->q > 32) return fail(PD_ERR_INVALID_ARG, "q must be in [0, 32] (0 = 1)");
+  if (d->q > 1 && d->batch > 1)
+    return fail(PD_ERR_UNSUPPORTED, "a frozen residual (q > 1) is built for single problems, not batches");
   if (!(d->alpha >= 0.0 && d->alpha <= 1.0)) return fail(PD_ERR_INVALID_ARG, "alpha must be in (0, 1] (0 = 1)");
   if (d->eps_krylov < 0.0 || d->refine_tol < 0.0 || d->max_refine < 0)
     return fail(PD_ERR_INVALID_ARG, "negative tolerance or sweep count");
@@ -359,6 +362,7 @@ void fill_geometry(pd_plan *p, const pd_desc *d) {
   p->refined64 = d->precision == PD_FP64 && (p->alpha < 1.0 || d->batch > 1);
   p->precision = d->precision;
   p->maxit = d->maxit ? d->maxit : 32;
+  p->q = d->q > 1 ? d->q : 1;
   p->eps = d->eps_krylov > 0 ? d->eps_krylov : (d->precision == PD_FP64 ? 1e-13 : 1e-5);
   // FP64 plans that refine anyway use a loose tolerance per solve: Algorithm 3 loses
   // up to kappa(F D_alpha) per solve, and a batch runs until its slowest problem's
@@ -798,7 +802,7 @@ template <typename T>
 pd::KrylovBufs kbufs(pd_plan *p) {
   return pd::KrylovBufs{(int)p->nbar, p->maxit, p->klo, p->kdiag, p->kup, p->V, sizeof(T) == 4 ? p->Vf : nullptr,
                         p->T, p->w, p->part, p->blas_grid, p->scal, p->flags, p->blas_cluster,
-                        p->members, (int)p->nxm, p->mscal, p->mflags, p->y, p->flags + pd::F_MEMCNT};
+                        p->members, (int)p->nxm, p->mscal, p->mflags, p->y, p->flags + pd::F_MEMCNT, p->q};
 }
 
 // Algorithm-2 stopping parameters of the first solve (kind 0) and of refinement
@@ -824,6 +828,7 @@ pd::KrylovCtl krylov_ctl(pd_plan *p, int kind) {
     k.win = 2;
   }
   k.maxit = p->maxit;
+  k.q = p->q;
   return k;
 }
 
@@ -906,6 +911,9 @@ pd_status emit_iter(pd_plan *p, int kind, int use_handle, cudaGraphConditionalHa
   else
     pd::launch_arnoldi(c, kb);
   cpx<T> *H = reinterpret_cast<cpx<T> *>(p->hbuf);
+  // no h_k at a breakdown (eq. 12 loses its t-term) or on a frozen step (q > 1); batches
+  // run q = 1 and read the batch-level breakdown flag
+  const int *noh = kb.members ? p->flags + pd::F_BREAK : p->flags + pd::F_NOH;
   {  // h_k = ((1 - pi_k) I + tau K)^{-1} v_{m+1} (stored) and g_k = V_m^T h_k
     pd::PintArgs<T> a = base_args<T>(p);
     a.mcount = p->flags + pd::F_M;
@@ -916,7 +924,7 @@ pd_status emit_iter(pd_plan *p, int kind, int use_handle, cudaGraphConditionalHa
     a.gpart = p->gpart;
     a.Y = H;
     a.ldy = p->lds;
-    a.skip_flag = p->flags + pd::F_BREAK;
+    a.skip_flag = noh;
     pd::launch_pint<T>(c, p->geom, a);
   }
   pd::launch_capacitance(c, kb, p->nf, p->tau, p->shift, p->wga, p->gpart, p->nblk, p->msys_part,
@@ -924,14 +932,14 @@ pd_status emit_iter(pd_plan *p, int kind, int use_handle, cudaGraphConditionalHa
                          p->srow, p->omega, p->y, kb.members);
   // z = sum_i gamma_i h_i (e_m^T S_i y_m) from the stored h_i, then eq. (13)
   if (kb.members) {
-    pd::launch_zsum<T>(c, p->nf, p->nbar, H, p->lds, p->omega, p->z, p->flags + pd::F_BREAK, nullptr, kb.mlen);
+    pd::launch_zsum<T>(c, p->nf, p->nbar, H, p->lds, p->omega, p->z, noh, nullptr, kb.mlen);
     pd::launch_member_project(c, kb, p->z, p->tau, krylov_ctl(p, kind), use_handle, hk);
   } else if (kb.grid == 1 && kb.cluster == 0) {  // eq. (13) and the decision in the z reduction's last CTA
     const pd::ProjTail t{1, p->flags + pd::F_ZCNT, kb.n, kb.maxit + 2, use_handle, kb.V, p->tau, kb.part, kb.scal,
                          kb.flags, krylov_ctl(p, kind), hk};
-    pd::launch_zsum<T>(c, p->nf, p->nbar, H, p->lds, p->omega, p->z, p->flags + pd::F_BREAK, &t);
+    pd::launch_zsum<T>(c, p->nf, p->nbar, H, p->lds, p->omega, p->z, noh, &t);
   } else {
-    pd::launch_zsum<T>(c, p->nf, p->nbar, H, p->lds, p->omega, p->z, p->flags + pd::F_BREAK);
+    pd::launch_zsum<T>(c, p->nf, p->nbar, H, p->lds, p->omega, p->z, noh);
     pd::launch_project_resnorm(c, kb, p->z, p->tau, krylov_ctl(p, kind), use_handle, hk);
   }
   return PD_OK;
@@ -1187,8 +1195,11 @@ pd_status solve_refined(pd_plan *p, const double *G, double *U, pd_stats &s) {
     s.sweep_krylov_iters[i] = f[pd::F_SWM + i];
     s.sweep_krylov_rel_resnorm[i] = sc[pd::S_SWRES + i];
     s.sweep_rel_update[i] = sc[pd::S_SWUPD + i];
-    s.pint_loops += f[pd::F_SWM + i] + 2;
-    s.shifted_sweeps += 2 * f[pd::F_SWM + i] + 2;
+    // a residual check (one pass over the shifted systems) every q steps and at the last
+    // step, plus the b and final passes
+    const int checks = (f[pd::F_SWM + i] + p->q - 1) / p->q;
+    s.pint_loops += checks + 2;
+    s.shifted_sweeps += checks + 2;
   }
   s.breakdown = f[pd::F_BREAK];
   s.beta = sc[pd::S_SWBETA + last];

@@ -33,7 +33,7 @@ class Plan:
 
     def __init__(self, *, dim, nx, nt, tau, k_lo, k_diag, k_up, ny=1, k_lo_y=None, k_diag_y=None,
                  k_up_y=None, m_diag=None, precision="mixed", maxit=0, eps_krylov=0.0, max_refine=0, refine_tol=0.0,
-                 alpha=1.0, host_io=False, no_graph=False, tune=None, batch=1, batch_nx=None, batch_tau=None,
+                 alpha=1.0, q=1, host_io=False, no_graph=False, tune=None, batch=1, batch_nx=None, batch_tau=None,
                  device=None, stream=None, workspace="torch"):
         import torch
 
@@ -59,7 +59,7 @@ class Plan:
         d.precision = {"fp64": B.PD_FP64, "mixed": B.PD_MIXED}[precision]
         d.maxit = int(maxit)
         d.eps_krylov = float(eps_krylov)
-        d.q = 1
+        d.q = int(q)  # Algorithm 2 checks its residual every q steps (frozen residual, Sec. 3)
         d.max_refine = int(max_refine)
         d.refine_tol = float(refine_tol)
         d.alpha = float(alpha)

@@ -119,7 +119,7 @@ def test_valid_descriptors_have_a_workspace(B):
                {"tune_pint_factor": 1, "precision": 1}, {"tune_pint_factor": -1},
                {"mass": np.full(31, 0.5)}, {"mass": np.linspace(0.5, 2.0, 62), "batch": 2},
                {"batch": 3, "batch_nx": [31, 5, 1], "batch_tau": [0.1, 0.2, 1e-3]}, {"batch": 4},
-               {"alpha": 1e-4}, {"alpha": 0.5, "precision": 1},
+               {"alpha": 1e-4}, {"alpha": 0.5, "precision": 1}, {"q": 3}, {"q": 32, "precision": 1},
                {"dim": 2, "ny": 7}, {"dim": 2, "ny": 255, "n": 255, "nt": 256, "precision": 1}):
         st, n = _size_status(B, _desc(B, **kw))
         assert st == 0, (kw, B.last_error())
@@ -136,7 +136,9 @@ def test_valid_descriptors_have_a_workspace(B):
     ({"tau": float("nan")}, 1),
     ({"precision": 7}, 1),
     ({"maxit": 40}, 2),
-    ({"q": 2}, 2),
+    ({"q": 2, "batch": 2}, 2),             # frozen residual: single problems only
+    ({"q": 33}, 1),
+    ({"q": -1}, 1),
     ({"alpha": 1.5}, 1),
     ({"alpha": -0.1}, 1),
     ({"alpha": float("nan")}, 1),

@@ -504,3 +504,32 @@ def test_backward_euler_is_causal_under_time_padding():
     A = R.aao_matrix_mass(R.k_dense(Q), Q.tau, Q.nt, np.ones(Q.nx))
     Vd = np.linalg.solve(A, Q.G.reshape(-1)).reshape(Q.nt, Q.nx)
     assert R.rel_err(Vd[:8], U) < 1e-13
+
+
+def _slow_krylov_heat(n=127, nt=64, c=1e-4):
+    """1D heat with K scaled by c: tau lambda_min(K) ~ 1.5e-6, so J_l is far from I and
+    Algorithm 2 needs about a dozen steps (the bound of eq. 14)."""
+    P = W.heat1d_forced(n, nt, seed=1)
+    P.k_lo, P.k_diag, P.k_up = P.k_lo * c, P.k_diag * c, P.k_up * c
+    return P
+
+
+@pytest.mark.parametrize("q", [2, 3, 5])
+def test_frozen_residual_stops_at_the_first_checked_step(q):
+    """Sec. 3, frozen residual: y_m and ||r_m|| of step m do not depend on q, so checking
+    only every q steps stops at the first multiple of q (or maxit) whose q = 1 residual is
+    <= eps beta, with the same x_m as a q = 1 run stopped there."""
+    P = _slow_krylov_heat()
+    eps, maxit = 1e-10, 32
+    _, full = R.paradiag(P, eps=0.0, maxit=maxit, q=1)
+    r1 = full["krylov"]["resnorms"]  # r_1 .. r_maxit
+    beta = full["krylov"]["beta"]
+    want = next(m for m in range(1, maxit + 1) if (m % q == 0 or m == maxit) and r1[m - 1] <= eps * beta)
+    Uq, iq = R.paradiag(P, eps=eps, maxit=maxit, q=q)
+    assert iq["krylov"]["m"] == want
+    # one residual per checked step, equal to the q = 1 residual there
+    checked = [m for m in range(1, want + 1) if m % q == 0 or m == want]
+    assert np.allclose(iq["krylov"]["resnorms"], [r1[m - 1] for m in checked], rtol=1e-12, atol=0)
+    U1, _ = R.paradiag(P, eps=0.0, maxit=want, q=1)
+    assert R.rel_err(Uq, U1) < 1e-15
+    assert R.rel_err(Uq, R.be_solve(P)) < 1e-9
