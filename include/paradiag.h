@@ -119,6 +119,13 @@ typedef struct pd_desc {
   int32_t no_graph;      /* nonzero: drive the Algorithm-2 and refinement loops from the host
                             instead of running each solve as one CUDA graph with device-side
                             conditionals (also the behaviour while kernel timing is enabled) */
+  int32_t loops;         /* fixed-cost variants of Algorithms 1 and 3 (Sec. 6, Table 3), one
+                            solve with no refinement and no Algorithm 2: 2 = x_m = b (the
+                            inner matrix of eq. 17 approximated by the identity: the b loop
+                            and the final loop); 1 = U = U_1 (the first loop alone, no
+                            correction).  The result is the variant's approximation, so the
+                            solve returns PD_OK without a convergence test.  0 = the full
+                            method.  Single problems only (batch <= 1) */
   /* Launch geometry; 0 selects the built-in choice (paradiag_autotune fills these). */
   int32_t tune_pint_rows;    /* rows per thread of the shifted-solve kernel: 4, 8, or 16
                                 (16 with PD_MIXED only) */

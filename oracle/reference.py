@@ -407,10 +407,16 @@ def alpha_quantities(ell, alpha):
     return a * pi1, gamma, d
 
 
-def paradiag_alpha(problem, alpha, G=None, eps=1e-8, maxit=50, q=1, op=None, early_exit_eps=None, **kw):
+def paradiag_alpha(problem, alpha, G=None, eps=1e-8, maxit=50, q=1, op=None, early_exit_eps=None, loops=None,
+                   **kw):
     """Algorithm 3 on the row layout (row j of G = column j of [u0 + tau f_1, ...]).
     Returns (U, info).  early_exit_eps: the optional residual test on U_1 of the
-    algorithm (None = always run the correction)."""
+    algorithm (None = always run the correction).
+
+    loops: the fixed-cost variants the paper compares at equal numbers of
+    parallel-in-time loops (Sec. 6, Table 3).  1 returns U_1 (one loop, no correction);
+    2 skips Algorithm 2 and takes x_m = b, i.e. the inner matrix of eq. (17) approximated
+    by the identity (two loops); None runs Algorithm 3 in full."""
     G = problem.G if G is None else np.asarray(G, dtype=np.float64)
     op = operator(problem) if op is None else op
     ell = G.shape[0]
@@ -421,6 +427,8 @@ def paradiag_alpha(problem, alpha, G=None, eps=1e-8, maxit=50, q=1, op=None, ear
     L = np.stack([op.shifted_solve(1.0 - pi[i], tau, Ghat[i]) for i in range(ell)])
     U1 = (idft_time(L) / d[:, None])  # L F^{-T} D_alpha^{-1}
     info = {"pi": pi, "gamma": gamma, "d": d, "L": L, "exited_early": False}
+    if loops == 1:
+        return U1.real, info
     if early_exit_eps is not None:
         res = np.linalg.norm(aao_apply(problem, U1.real) - G)
         if res <= early_exit_eps * np.linalg.norm(U1.real):
@@ -428,7 +436,10 @@ def paradiag_alpha(problem, alpha, G=None, eps=1e-8, maxit=50, q=1, op=None, ear
             return U1.real, info
     b_c = gamma @ L  # L F^{-T} e_l
     b = b_c.real
-    x, kinfo = fom_like(op, tau, b, pi, gamma, eps=eps, maxit=maxit, q=q, weight=a, **kw)
+    if loops == 2:
+        x, kinfo = b.copy(), {"m": 0}
+    else:
+        x, kinfo = fom_like(op, tau, b, pi, gamma, eps=eps, maxit=maxit, q=q, weight=a, **kw)
     W = np.stack([op.shifted_solve(1.0 - pi[i], tau, x) for i in range(ell)])
     Uc = U1 - a * idft_time(W) / d[:, None]
     info.update(b=b, x=x, krylov=kinfo, U_imag=float(np.linalg.norm(Uc.imag)))

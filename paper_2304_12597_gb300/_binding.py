@@ -55,6 +55,7 @@ class PdDesc(ctypes.Structure):
         ("stream", ctypes.c_void_p),
         ("host_io", ctypes.c_int32),
         ("no_graph", ctypes.c_int32),
+        ("loops", ctypes.c_int32),
         ("tune_pint_rows", ctypes.c_int32),
         ("tune_pint_teams", ctypes.c_int32),
         ("tune_krylov_ctas", ctypes.c_int32),

@@ -23,6 +23,23 @@ __global__ void k_krylov_decide(double *scal, int *flags, KrylovCtl k, int use_h
   if (threadIdx.x == 0 && blockIdx.x == 0) krylov_decide(scal, flags, k, use_handle, h);
 }
 
+// The fixed-cost variants of Table 3 run no Algorithm 2.  loops = 2: x_m = b, i.e. the
+// inner matrix of eq. (17) taken as I, which the final loop forms as V_1 y_1 with
+// v_1 = b / beta from the initialisation and y_1 = beta; loops = 1: x_m = 0, so the final
+// loop returns U_1.  Closes the Algorithm-2 loop before it starts.
+__global__ void k_inner_fixed(double *scal, int *flags, double *y, int loops, int use_handle,
+                              cudaGraphConditionalHandle h) {
+  grid_dep_wait();
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double beta = scal[S_BETA];
+  const bool take_b = loops == 2 && !flags[F_BZERO] && isfinite(beta) && beta > 0.0;
+  y[0] = take_b ? beta : 0.0;
+  flags[F_M] = take_b ? 1 : 0;
+  flags[F_KSTOP] = 1;
+  flags[F_KCONV] = 1;
+  if (use_handle) cudaGraphSetConditional(h, 0u);
+}
+
 __global__ void k_refine_decide(double *scal, int *flags, RefineCtl r, int use_handle,
                                 cudaGraphConditionalHandle h) {
   grid_dep_wait();
@@ -82,6 +99,11 @@ void launch_solve_reset(Ctx &c, double *scal, int *flags) {
 void launch_krylov_decide(Ctx &c, double *scal, int *flags, const KrylovCtl &k, int use_handle,
                           cudaGraphConditionalHandle h) {
   c.launch("control", 0.0, [&] { pdl_launch(c.pdl, k_krylov_decide, dim3(1), dim3(32), 0, c.stream, scal, flags, k, use_handle, h); });
+}
+
+void launch_inner_fixed(Ctx &c, double *scal, int *flags, double *y, int loops, int use_handle,
+                        cudaGraphConditionalHandle h) {
+  c.launch("control", 0.0, [&] { pdl_launch(c.pdl, k_inner_fixed, dim3(1), dim3(32), 0, c.stream, scal, flags, y, loops, use_handle, h); });
 }
 
 void launch_refine_decide(Ctx &c, double *scal, int *flags, const RefineCtl &r, int use_handle,

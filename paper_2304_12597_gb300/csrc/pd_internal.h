@@ -299,6 +299,8 @@ void launch_xm(Ctx &c, KrylovBufs &k, const double *y, double *x, float *xf);
 void launch_solve_reset(Ctx &c, double *scal, int *flags);
 void launch_krylov_decide(Ctx &c, double *scal, int *flags, const KrylovCtl &k, int use_handle,
                           cudaGraphConditionalHandle h);
+void launch_inner_fixed(Ctx &c, double *scal, int *flags, double *y, int loops, int use_handle,
+                        cudaGraphConditionalHandle h);  // Table 3 variants: no Algorithm 2
 void launch_refine_decide(Ctx &c, double *scal, int *flags, const RefineCtl &r, int use_handle,
                           cudaGraphConditionalHandle h);
 void launch_sumsq(Ctx &c, const double *part, int nparts, double *dst);

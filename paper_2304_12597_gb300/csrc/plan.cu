@@ -164,6 +164,7 @@ struct pd_plan {
   int precision = PD_FP64;
   int maxit = 32;
   int q = 1;  // Algorithm 2 checks its residual every q steps (Sec. 3)
+  int loops = 0;  // fixed-cost variant (Table 3): 2 = x_m = b, 1 = U_1; 0 = the full method
   double eps = 1e-13;
   int max_refine = 6;
   double refine_tol = 1e-13;
@@ -271,6 +272,9 @@ pd_status validate(const pd_desc *d) {
   if (d->precision != PD_FP64 && d->precision != PD_MIXED) return fail(PD_ERR_INVALID_ARG, "bad precision");
   if (d->maxit < 0 || d->maxit > 32) return fail(PD_ERR_UNSUPPORTED, "maxit must be in [1, 32]");
   if (d->q < 0 || d->q > 32) return fail(PD_ERR_INVALID_ARG, "q must be in [0, 32] (0 = 1)");
+  if (d->loops < 0 || d->loops > 2) return fail(PD_ERR_INVALID_ARG, "loops must be 0, 1 or 2");
+  if (d->loops > 0 && d->batch > 1)
+    return fail(PD_ERR_UNSUPPORTED, "the fixed-loop variants (loops > 0) are built for single problems");
   if (d->q > 1 && d->batch > 1)
     return fail(PD_ERR_UNSUPPORTED, "a frozen residual (q > 1) is built for single problems, not batches");
   if (!(d->alpha >= 0.0 && d->alpha <= 1.0)) return fail(PD_ERR_INVALID_ARG, "alpha must be in (0, 1] (0 = 1)");
@@ -371,6 +375,8 @@ void fill_geometry(pd_plan *p, const pd_desc *d) {
   if (p->refined64 && !(d->eps_krylov > 0)) p->eps = 1e-5;
   // batches stop only when their slowest problem has converged: allow more sweeps
   p->max_refine = d->max_refine ? d->max_refine : (d->batch > 1 ? 16 : 8);
+  p->loops = d->loops;
+  if (p->loops) p->max_refine = 0;  // one solve: the variant's approximation
   p->refine_tol = d->refine_tol > 0 ? d->refine_tol : (d->precision == PD_FP64 ? 1e-14 : 1e-11);
   p->host_io = d->host_io;
   p->nblk = p->batch > 1 ? p->batch : (int)p->ny;
@@ -880,6 +886,10 @@ pd_status emit_pre(pd_plan *p, int kind, const double *G, double *U, int use_han
       pd::launch_fft_r2c<T, T>(c, tmp, p->nbar, p->nbar, nt, time_tw<T>(p), S, p->lds, row_scale<T>(p, false));
     }
   }
+  if (p->loops == 1) {  // U = U_1: no b and no Algorithm 2; the final loop runs with x_m = 0
+    pd::launch_inner_fixed(c, p->scal, p->flags, p->y, 1, use_handle, hk);
+    return PD_OK;
+  }
   pd::PintArgs<T> a = base_args<T>(p);
   a.R = S;
   a.ldr = p->lds;
@@ -898,6 +908,8 @@ pd_status emit_pre(pd_plan *p, int kind, const double *G, double *U, int use_han
     pd::launch_acc_reduce(c, p->geom, p->acc_part, p->b, nullptr);
     pd::launch_vec_norm_init(c, kb, p->b, use_handle, hk);
   }
+  // x_m = b: the inner matrix of eq. (17) taken as I (two loops in all)
+  if (p->loops == 2) pd::launch_inner_fixed(c, p->scal, p->flags, p->y, 2, use_handle, hk);
   return PD_OK;
 }
 
@@ -1198,8 +1210,9 @@ pd_status solve_refined(pd_plan *p, const double *G, double *U, pd_stats &s) {
     // a residual check (one pass over the shifted systems) every q steps and at the last
     // step, plus the b and final passes
     const int checks = (f[pd::F_SWM + i] + p->q - 1) / p->q;
-    s.pint_loops += checks + 2;
-    s.shifted_sweeps += checks + 2;
+    s.pint_loops += p->loops ? p->loops : checks + 2;
+    s.shifted_sweeps += p->loops ? p->loops : checks + 2;
+    if (p->loops) s.sweep_krylov_iters[i] = 0;  // m = 1 only carries x_m = b
   }
   s.breakdown = f[pd::F_BREAK];
   s.beta = sc[pd::S_SWBETA + last];
@@ -1207,6 +1220,10 @@ pd_status solve_refined(pd_plan *p, const double *G, double *U, pd_stats &s) {
   s.rel_update = sweeps > 1 ? sc[pd::S_UPD] : 0.0;
   s.graph = used ? 1 : 0;
   if (f[pd::F_NONFIN]) return fail(PD_ERR_NONFINITE, "non-finite value met (input contains NaN/Inf?)");
+  if (p->loops) {  // the variant's approximation: no convergence claim
+    s.krylov_iters = s.krylov_iters_total = 0;
+    return PD_OK;
+  }
   return f[pd::F_RCONV] ? PD_OK
                         : fail(PD_ERR_NOT_CONVERGED, "refinement did not reach refine_tol in %d solves", sweeps);
 }

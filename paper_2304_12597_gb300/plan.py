@@ -33,7 +33,7 @@ class Plan:
 
     def __init__(self, *, dim, nx, nt, tau, k_lo, k_diag, k_up, ny=1, k_lo_y=None, k_diag_y=None,
                  k_up_y=None, m_diag=None, precision="mixed", maxit=0, eps_krylov=0.0, max_refine=0, refine_tol=0.0,
-                 alpha=1.0, q=1, host_io=False, no_graph=False, tune=None, batch=1, batch_nx=None, batch_tau=None,
+                 alpha=1.0, q=1, loops=0, host_io=False, no_graph=False, tune=None, batch=1, batch_nx=None, batch_tau=None,
                  device=None, stream=None, workspace="torch"):
         import torch
 
@@ -66,6 +66,7 @@ class Plan:
         d.stream = ctypes.c_void_p(self.stream.cuda_stream)
         d.host_io = 1 if host_io else 0
         d.no_graph = 1 if no_graph else 0
+        d.loops = int(loops)  # 1: U = U_1; 2: x_m = b (fixed-cost variants, Table 3)
         for key, val in (tune or {}).items():  # launch geometry: pint_rows, pint_teams, krylov_ctas, ...
             setattr(d, "tune_" + key, int(val))
         d.batch = self.batch if self.batch > 1 else 0

@@ -93,3 +93,37 @@ def test_alpha_shifted_solve_uses_scaled_shifts(pd):
         Y, _ = plan.shifted_solve(torch.from_numpy(np.ascontiguousarray(Rhs)).to(dev()))
     Yref = np.stack([op.shifted_solve(1.0 - pi[k], P.tau, Rhs[k]) for k in range(P.nt // 2 + 1)])
     assert R.rel_err(Y.cpu().numpy(), Yref) <= 1e-12
+
+
+# The fixed-cost variants of Sec. 6, Table 3 (pd_desc.loops): one solve, no refinement.
+LOOP_CASES = [(2, 1e-4), (1, 1e-6), (2, 1.0), (1, 1e-2)]
+
+
+@pytest.mark.parametrize("loops,alpha", LOOP_CASES)
+def test_fixed_loop_variants_match_oracle(pd, loops, alpha):
+    """loops = 2 (x_m = b) and loops = 1 (U = U_1) in FP64 equal the oracle's variants within
+    50 kappa(F D_alpha) eps, and cost exactly that many parallel-in-time loops."""
+    P = W.advdiff1d_pulse(511, 64, nu=1e-2, seed=1)
+    ref, _ = R.paradiag_alpha(P, alpha, loops=loops)
+    with pd.Plan.from_problem(P, precision="fp64", alpha=alpha, loops=loops, device=dev()) as plan:
+        U, st = plan.solve(torch.from_numpy(P.G).to(dev()))
+    kappa = alpha ** (-(P.nt - 1) / P.nt)
+    assert R.rel_err(U.cpu().numpy(), ref) <= max(50 * kappa * 2.2e-16, 1e-12), st
+    assert st["refine_sweeps"] == 1 and st["pint_loops"] == loops and st["krylov_iters"] == 0
+
+
+@pytest.mark.parametrize("nu", [1e-1, 1e-2, 1e-3])
+def test_fixed_loop_variants_reach_table3_orders(pd, nu):
+    """Table 3's orders of magnitude on 1D advection-diffusion (the paper's problem is 2D):
+    two loops at alpha = 1e-4 leave a relative residual near 1e-10 (at most 1e-8) and one
+    loop at alpha = 1e-6 near 1e-7 (1e-9 .. 1e-6); the two-loop variant is the more accurate."""
+    P = W.advdiff1d_pulse(511, 64, nu=nu, seed=1)
+    G = torch.from_numpy(P.G).to(dev())
+    res = {}
+    for loops, alpha in ((2, 1e-4), (1, 1e-6)):
+        with pd.Plan.from_problem(P, precision="fp64", alpha=alpha, loops=loops, device=dev()) as plan:
+            U, _ = plan.solve(G)
+        res[loops] = np.linalg.norm(R.residual_extended(P, U.cpu().numpy())) / np.linalg.norm(P.G)
+    assert res[2] <= 1e-8
+    assert 1e-9 <= res[1] <= 1e-6
+    assert res[2] < res[1]

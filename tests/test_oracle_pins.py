@@ -533,3 +533,41 @@ def test_frozen_residual_stops_at_the_first_checked_step(q):
     U1, _ = R.paradiag(P, eps=0.0, maxit=want, q=1)
     assert R.rel_err(Uq, U1) < 1e-15
     assert R.rel_err(Uq, R.be_solve(P)) < 1e-9
+
+
+@pytest.mark.parametrize("alpha", [1e-2, 0.3, 1.0])
+def test_fixed_loop_variants_equal_their_dense_forms(alpha):
+    """Sec. 6, Table 3 variants of Algorithm 3, against the dense operators.  With
+    A = I (x) (I + tau K) - Sigma_1 (x) I and P_alpha = A - alpha (e_1 e_l^T (x) I) (the
+    alpha-circulant of eq. 15), Sherman-Morrison-Woodbury gives
+    A^{-1} g = U_1 - alpha P^{-1} E_1 (I + alpha E_l^T P^{-1} E_1)^{-1} E_l^T U_1 with
+    U_1 = P^{-1} g: one loop returns U_1, and two loops (x_m = b) drop the inner inverse."""
+    P = W.random_tridiag_problem(5, 8, seed=3)
+    n, ell = P.nx, P.nt
+    A = R.aao_matrix_mass(R.k_dense(P), P.tau, ell, np.ones(n))
+    E = np.zeros((ell, ell))
+    E[0, ell - 1] = 1.0
+    Pa = A - alpha * np.kron(E, np.eye(n))
+    U1 = np.linalg.solve(Pa, P.G.reshape(-1)).reshape(ell, n)
+    r = np.zeros((ell, n))
+    r[0] = U1[-1]
+    U2 = U1 - alpha * np.linalg.solve(Pa, r.reshape(-1)).reshape(ell, n)
+    V1, _ = R.paradiag_alpha(P, alpha, loops=1)
+    V2, info = R.paradiag_alpha(P, alpha, loops=2)
+    assert R.rel_err(V1, U1) < 1e-13 and R.rel_err(V2, U2) < 1e-13
+    assert info["krylov"]["m"] == 0
+    # the full method recovers the exact solution; the variants are approximations of it
+    assert R.rel_err(R.paradiag_alpha(P, alpha, eps=1e-14)[0], R.be_solve(P)) < 1e-11
+    assert R.rel_err(V2, R.be_solve(P)) > 1e-14
+
+
+@pytest.mark.parametrize("nu", [1e-1, 1e-2, 1e-3])
+def test_fixed_loop_variants_reach_table3_orders(nu):
+    """Table 3's orders of magnitude, on 1D advection-diffusion (the paper's problem is 2D):
+    two loops at alpha = 1e-4 leave a relative residual of at most 1e-8, one loop at
+    alpha = 1e-6 one in 1e-9 .. 1e-6, and two loops are the more accurate."""
+    P = W.advdiff1d_pulse(255, 32, nu=nu, seed=1)
+    rr = lambda U: np.linalg.norm(R.residual_extended(P, U)) / np.linalg.norm(P.G)
+    r2 = rr(R.paradiag_alpha(P, 1e-4, loops=2)[0])
+    r1 = rr(R.paradiag_alpha(P, 1e-6, loops=1)[0])
+    assert r2 <= 1e-8 and 1e-9 <= r1 <= 1e-6 and r2 < r1
