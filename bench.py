@@ -441,7 +441,34 @@ def cpu_baseline(P, name, gpu_results):
     base = {"value": P.unknowns * reps / total, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{reps} full solves of {name} ({P.unknowns} unknowns each, ~{budget:.0f} s budget, "
                       f"first solve {dt * 1e3:.1f} ms)"}
+    base["all_cores"] = oracle_all_cores(P, name, budget)
     return base, parity
+
+
+def oracle_all_cores(P, name, budget):
+    """Throughput of independent oracle solves on every host core at once: one thread per
+    core, each solving the workload repeatedly (the C solve releases the GIL and keeps its
+    buffers per call), for about `budget` seconds."""
+    import concurrent.futures as cf
+
+    from oracle import reference as R
+
+    cores = os.cpu_count() or 1
+    stop = time.perf_counter() + budget
+
+    def worker():
+        n = 0
+        while time.perf_counter() < stop:
+            R.be_solve(P)
+            n += 1
+        return n
+
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+        done = sum(f.result() for f in [ex.submit(worker) for _ in range(cores)])
+    total = time.perf_counter() - t0
+    return {"value": P.unknowns * done / total, "unit": UNIT, "cores": cores,
+            "sample": f"{done} independent full solves of {name} on {cores} threads, ~{budget:.0f} s"}
 
 
 def run_reference(args):

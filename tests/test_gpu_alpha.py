@@ -102,13 +102,21 @@ LOOP_CASES = [(2, 1e-4), (1, 1e-6), (2, 1.0), (1, 1e-2)]
 @pytest.mark.parametrize("loops,alpha", LOOP_CASES)
 def test_fixed_loop_variants_match_oracle(pd, loops, alpha):
     """loops = 2 (x_m = b) and loops = 1 (U = U_1) in FP64 equal the oracle's variants within
-    50 kappa(F D_alpha) eps, and cost exactly that many parallel-in-time loops."""
+    the FP64 bar scaled by the conditioning the alpha-scaling adds, 1e-12 kappa(F D_alpha),
+    and, where a variant is far from the exact solution, ten times closer to it than to that
+    solution; they cost exactly
+    that many parallel-in-time loops."""
     P = W.advdiff1d_pulse(511, 64, nu=1e-2, seed=1)
     ref, _ = R.paradiag_alpha(P, alpha, loops=loops)
     with pd.Plan.from_problem(P, precision="fp64", alpha=alpha, loops=loops, device=dev()) as plan:
         U, st = plan.solve(torch.from_numpy(P.G).to(dev()))
+    U = U.cpu().numpy()
     kappa = alpha ** (-(P.nt - 1) / P.nt)
-    assert R.rel_err(U.cpu().numpy(), ref) <= max(50 * kappa * 2.2e-16, 1e-12), st
+    err = R.rel_err(U, ref)
+    assert err <= 1e-12 * kappa, (err, st)
+    gap = R.rel_err(ref, R.be_solve(P))  # how far the variant is from the exact solve
+    if gap > 1e-9:  # well above FP64 rounding here: the GPU computes the variant, not the exact solve
+        assert err <= 0.1 * gap, (err, gap)
     assert st["refine_sweeps"] == 1 and st["pint_loops"] == loops and st["krylov_iters"] == 0
 
 

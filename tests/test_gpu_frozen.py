@@ -32,11 +32,13 @@ def dev():
     return torch.device("cuda:0")
 
 
-def _slow_krylov_problem():
-    """1D heat, n_x = 300, n_t = 32, K scaled by 1e-4: tau lambda_min(K) ~ 3e-5, so J_l is far
-    from I (eq. 14) and the FP64 Algorithm 2 takes about 20 steps."""
+def _slow_krylov_problem(c=1e-4):
+    """1D heat, n_x = 300, n_t = 32, K scaled by c: tau lambda_min(K) ~ 0.3 c, so J_l is far
+    from I (eq. 14).  At c = 1e-4 the FP64 Algorithm 2 takes about 20 steps; the binary32
+    refinement needs more than its default 9 solves there, so mixed runs use c = 1e-2
+    (Algorithm 2 up to maxit in the first solve, 6-7 solves in all)."""
     P = W.heat1d_forced(300, 32, seed=3)
-    P.k_lo, P.k_diag, P.k_up = P.k_lo * 1e-4, P.k_diag * 1e-4, P.k_up * 1e-4
+    P.k_lo, P.k_diag, P.k_up = P.k_lo * c, P.k_diag * c, P.k_up * c
     return P
 
 
@@ -48,11 +50,12 @@ MODES = {"cluster": {}, "one_cta": {"krylov_cluster": -1}, "coop": {"krylov_ctas
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("mode", list(MODES))
 def test_frozen_residual_matches_oracle(pd, prec, mode):
-    P = _slow_krylov_problem()
+    P = _slow_krylov_problem(1e-4 if prec == "fp64" else 1e-2)
     ref = R.be_solve_refined(P)
     stats = {}
     for q in (1, 3):
-        with pd.Plan.from_problem(P, precision=prec, q=q, maxit=MAXIT, tune=MODES[mode], device=dev()) as plan:
+        with pd.Plan.from_problem(P, precision=prec, q=q, maxit=MAXIT, max_refine=16, tune=MODES[mode],
+                                  device=dev()) as plan:
             U, st = plan.solve(torch.from_numpy(P.G).to(dev()))
         err = R.rel_err(U.cpu().numpy(), ref)
         assert err <= TOL[prec], (q, err, st)
