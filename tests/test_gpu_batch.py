@@ -1,5 +1,5 @@
-"""Batched plans (GPU, through the C ABI): many 1D problems with one n_t solved as one
-block-diagonal problem must give, for every problem, the oracle's solution of that
+"""Batched plans (GPU, through the C ABI): many 1D problems (uneven n_x; fewer time steps
+padded causally to the plan's n_t) solved as one block-diagonal problem must give, for every problem, the oracle's solution of that
 problem alone, within the same tolerances as single solves (1e-12 FP64, 1e-10 mixed),
 whatever the mix of sizes, time steps and magnitudes in the batch.
 
