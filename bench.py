@@ -186,8 +186,8 @@ def csrc_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(family, workload_name):
-    """DRAM bytes per launch from a committed ncu summary, if taken on the current kernels."""
+def ncu_summary(family, workload_name, key):
+    """A per-launch figure from a committed ncu summary, if taken on the current kernels."""
     path = os.path.join(ROOT, "profiles", f"traffic_{family}_{workload_name}.txt")
     if not os.path.exists(path):
         return None
@@ -200,9 +200,30 @@ def ncu_traffic(family, workload_name):
     if kv.get("csrc_sha256_16") != csrc_hash():
         return None
     try:
-        return float(kv["dram_bytes_per_launch"])
-    except (KeyError, ValueError):
+        return float(kv[key].split()[0])
+    except (KeyError, ValueError, IndexError):
         return None
+
+
+def ncu_traffic(family, workload_name):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)."""
+    return ncu_summary(family, workload_name, "dram_bytes_per_launch")
+
+
+def issue_roofline(family, workload_name, ms_per_launch, clocks, sms):
+    """The dominant kernel against the warp-instruction issue rate: warp instructions per
+    launch (smsp__inst_executed.sum from the committed capture) over the event-timed launch
+    duration, against 4 schedulers x 1 instruction per cycle x SMs x the SM clock sampled
+    during the timed region."""
+    inst = ncu_summary(family, workload_name, "warp_inst_per_launch")
+    mhz = (clocks or {}).get("sm_mhz")
+    if not inst or not mhz or not ms_per_launch:
+        return None
+    achieved = inst / (ms_per_launch / 1e3)
+    peak = 4.0 * sms * mhz * 1e6
+    return {"bound": "issue", "kernel": family, "achieved": achieved, "peak": peak, "unit": "warp-instructions/s",
+            "frac": round(achieved / peak, 4), "warp_inst_per_launch": inst,
+            "peak_basis": f"4 schedulers x {sms} SMs x {mhz:.0f} MHz (sampled), one warp instruction per cycle"}
 
 
 def flush_l2(buf):
@@ -392,6 +413,8 @@ def run_ours(args):
                    "sweep_rel_update": [float(f"{v:.3e}") for v in st_mixed["sweep_rel_update"]],
                    "sweep_krylov_rel_resnorm": [float(f"{v:.3e}") for v in st_mixed["sweep_krylov_rel_resnorm"]]},
         "roofline": roofline,
+        "roofline_issue": issue_roofline(dom_name, args.workload, roofline["ms_per_launch"], clocks,
+                                         torch.cuda.get_device_properties(device).multi_processor_count),
         "kernels": kernel_table,
         "clocks": clocks,
         "batched": batched,
