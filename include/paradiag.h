@@ -150,6 +150,11 @@ typedef struct pd_desc {
                                 eliminate in every loop; 0: factor PD_FP64 plans only (FP64
                                 elimination is costly on GB300; binary32 elimination costs
                                 less than streaming its factors) */
+  int32_t tune_krylov_tails; /* single-CTA vector work (the start of Algorithm 2: beta and v_1;
+                                the eq. (13) projection and decision) in the last CTA of the
+                                reduction before it (b, z) instead of separate launches: 1 =
+                                also when the Arnoldi step runs on a cluster; -1 = only with
+                                the single CTA; 0 = built-in choice */
   /* Batching (1D only): `batch` independent problems are solved together as one
    * block-diagonal problem (their DFTs, shifted solves and refinement sweeps are shared,
    * each problem runs its own Algorithm 2, and the blocks never couple).  A problem with

@@ -64,6 +64,7 @@ class PdDesc(ctypes.Structure):
         ("tune_no_pdl", ctypes.c_int32),
         ("tune_krylov_cluster", ctypes.c_int32),
         ("tune_pint_factor", ctypes.c_int32),
+        ("tune_krylov_tails", ctypes.c_int32),
         ("batch", ctypes.c_int32),
         ("batch_nx", ctypes.POINTER(ctypes.c_int64)),
         ("batch_tau", ctypes.POINTER(ctypes.c_double)),

@@ -197,6 +197,7 @@ struct pd_plan {
   int blas_grid = 1, k5_grid = 1;
   int k5_grid_members = 1;  // capacitance CTAs per problem of a batched plan
   int blas_cluster = 0;  // CTAs of the cluster variant of the one-CTA Krylov kernels (0 = off)
+  bool krylov_tails = false;  // beta / v_1 and eq. (13) in the last CTA of the b and z reductions
   int64_t lds = 0;
 
   // device buffers
@@ -320,6 +321,8 @@ pd_status validate(const pd_desc *d) {
     return fail(PD_ERR_INVALID_ARG, "tune_krylov_ctas and tune_cap_ctas must be in [0, 1024]");
   if (d->tune_pint_factor < -1 || d->tune_pint_factor > 1)
     return fail(PD_ERR_INVALID_ARG, "tune_pint_factor must be -1, 0 or 1");
+  if (d->tune_krylov_tails < -1 || d->tune_krylov_tails > 1)
+    return fail(PD_ERR_INVALID_ARG, "tune_krylov_tails must be -1, 0 or 1");
   if (d->tune_krylov_cluster != 0 && d->tune_krylov_cluster != -1 &&
       (d->tune_krylov_cluster < 4 || d->tune_krylov_cluster > 16))
     return fail(PD_ERR_INVALID_ARG, "tune_krylov_cluster must be 0, -1 or in [4, 16]");
@@ -418,6 +421,10 @@ void fill_geometry(pd_plan *p, const pd_desc *d) {
     p->blas_cluster = pd::krylov_cluster_size(want);
     if (p->blas_cluster < 4) p->blas_cluster = 0;
   }
+  // the start of Algorithm 2 and its eq. (13) decision are single-CTA work: with one CTA
+  // they run in the last CTA of the reduction before them; with a cluster, on request
+  p->krylov_tails = !p->members && p->blas_grid == 1 && d->tune_krylov_tails >= 0 &&
+                    (p->blas_cluster == 0 || d->tune_krylov_tails == 1);
   if (d->tune_cap_ctas) p->k5_grid = d->tune_cap_ctas;
   // batched plans run one capacitance system per problem: about two waves of CTAs over
   // all problems (each CTA sized for maxit-step Gauss-Jordan holds one SM), so a warp
@@ -900,7 +907,7 @@ pd_status emit_pre(pd_plan *p, int kind, const double *G, double *U, int use_han
   if (kb.members) {
     pd::launch_acc_reduce(c, p->geom, p->acc_part, p->b, nullptr);
     pd::launch_member_init(c, kb, p->b, use_handle, hk);
-  } else if (kb.grid == 1 && kb.cluster == 0) {  // one CTA: beta and v_1 in the reduction's last CTA
+  } else if (p->krylov_tails) {  // beta and v_1 in the b reduction's last CTA
     const pd::InitTail t{1, p->flags + pd::F_ACCCNT, kb.n, kb.maxit + 2, (kb.maxit + 1) * kb.maxit, use_handle,
                          kb.part, kb.V, kb.scal, kb.T, kb.Vf, kb.flags, hk};
     pd::launch_acc_reduce(c, p->geom, p->acc_part, p->b, nullptr, &t);
@@ -946,7 +953,7 @@ pd_status emit_iter(pd_plan *p, int kind, int use_handle, cudaGraphConditionalHa
   if (kb.members) {
     pd::launch_zsum<T>(c, p->nf, p->nbar, H, p->lds, p->omega, p->z, noh, nullptr, kb.mlen);
     pd::launch_member_project(c, kb, p->z, p->tau, krylov_ctl(p, kind), use_handle, hk);
-  } else if (kb.grid == 1 && kb.cluster == 0) {  // eq. (13) and the decision in the z reduction's last CTA
+  } else if (p->krylov_tails) {  // eq. (13) and the decision in the z reduction's last CTA
     const pd::ProjTail t{1, p->flags + pd::F_ZCNT, kb.n, kb.maxit + 2, use_handle, kb.V, p->tau, kb.part, kb.scal,
                          kb.flags, krylov_ctl(p, kind), hk};
     pd::launch_zsum<T>(c, p->nf, p->nbar, H, p->lds, p->omega, p->z, noh, &t);

@@ -119,7 +119,7 @@ def test_valid_descriptors_have_a_workspace(B):
                {"tune_pint_factor": 1, "precision": 1}, {"tune_pint_factor": -1},
                {"mass": np.full(31, 0.5)}, {"mass": np.linspace(0.5, 2.0, 62), "batch": 2},
                {"batch": 3, "batch_nx": [31, 5, 1], "batch_tau": [0.1, 0.2, 1e-3]}, {"batch": 4},
-               {"alpha": 1e-4}, {"alpha": 0.5, "precision": 1}, {"q": 3}, {"q": 32, "precision": 1},
+               {"alpha": 1e-4}, {"alpha": 0.5, "precision": 1}, {"q": 3}, {"q": 32, "precision": 1}, {"tune_krylov_tails": 1}, {"tune_krylov_tails": -1},
                {"dim": 2, "ny": 7}, {"dim": 2, "ny": 255, "n": 255, "nt": 256, "precision": 1}):
         st, n = _size_status(B, _desc(B, **kw))
         assert st == 0, (kw, B.last_error())
@@ -154,6 +154,7 @@ def test_valid_descriptors_have_a_workspace(B):
     ({"tune_krylov_ctas": 1, "n": 4095, "batch": 3}, 2),   # one CTA holds <= 8192 entries
     ({"tune_krylov_cluster": 2}, 1),
     ({"tune_pint_factor": 2}, 1),
+    ({"tune_krylov_tails": 2}, 1),
     ({"mass": np.full(31, 1.0), "dim": 2, "ny": 7}, 2),        # mass matrices: 1D only
     ({"mass": np.concatenate([np.ones(30), [0.0]])}, 1),       # entries must be > 0
     ({"mass": np.concatenate([np.ones(30), [np.nan]])}, 1),
