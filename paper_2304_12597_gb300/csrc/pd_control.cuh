@@ -98,8 +98,8 @@ __device__ __forceinline__ void refine_decide(double *scal, int *flags, const Re
 // converged if every problem's update is at the rounding floor).  The recorded
 // update of the sweep is the largest over the problems.  mex[b] receives the power of
 // two that scales problem b's residual in the next sweep, 2^-round(log2 ||delta_s||):
-// the problems' right-hand sides stay comparable in the shared Krylov space, so one
-// problem's correction is not lost below another's.
+// every problem's residual enters the binary32 DFTs and shifted solves, and its own
+// Algorithm 2, near unit norm however far its earlier sweeps have shrunk it.
 // Run by every thread of one CTA (red: blockDim.x doubles of shared memory): the
 // problems are spread over the threads, so the per-problem loads overlap instead of
 // following one another through L2; the batch totals are then reduced in a fixed order.
