@@ -27,7 +27,7 @@ def _candidates(plan_kw, nf):
         ("cap_ctas", sorted({0, max(1, (nf + 7) // 8), max(1, (nf + 3) // 4), max(1, (nf + 1) // 2)})),
         ("krylov_ctas", [0, 8, 16]),
         ("pint_factor", [0, 1, -1]),
-        ("krylov_cluster", [0, -1, 16]),
+        ("krylov_cluster", [0, -1, 16]), ("krylov_tails", [0, 1]),
     ]
 
 
