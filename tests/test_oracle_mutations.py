@@ -162,3 +162,62 @@ def test_py_mutation_alpha_weight_dropped(monkeypatch):
     kappa = alpha ** (-(P.nt - 1) / P.nt)
     # the bound test_algorithm3_equals_sequential_stepping holds the unmutated oracle to
     assert R.rel_err(U, R.be_solve(P)) > 1e3 * 50 * kappa * 2.2e-16
+
+
+def _mutant_reference(old, new):
+    """A copy of oracle/reference.py with one planted mistake, loaded as a module of the
+    oracle package (so its relative imports resolve); the file on disk is not touched."""
+    import types
+
+    src = open(R.__file__).read()
+    assert src.count(old) == 1, old
+    mod = types.ModuleType("oracle._mutant_reference")
+    mod.__package__ = "oracle"
+    mod.__file__ = R.__file__
+    exec(compile(src.replace(old, new), R.__file__, "exec"), mod.__dict__)
+    return mod
+
+
+def test_py_mutation_frozen_check_off_by_one():
+    """Checking at m mod q = 1 instead of 0 is caught by the frozen-residual pin: the q-run no
+    longer stops at the first multiple of q whose q = 1 residual is below eps beta."""
+    M = _mutant_reference("if m % q == 0 or breakdown or m == maxit:",
+                          "if (m - 1) % q == 0 or breakdown or m == maxit:")
+    P = W.heat1d_forced(127, 64, seed=1)
+    P.k_lo, P.k_diag, P.k_up = P.k_lo * 1e-4, P.k_diag * 1e-4, P.k_up * 1e-4
+    eps, maxit, q = 1e-10, 32, 3
+    _, full = M.paradiag(P, eps=0.0, maxit=maxit, q=1)
+    r1, beta = full["krylov"]["resnorms"], full["krylov"]["beta"]
+    want = next(m for m in range(1, maxit + 1) if (m % q == 0 or m == maxit) and r1[m - 1] <= eps * beta)
+    _, iq = M.paradiag(P, eps=eps, maxit=maxit, q=q)
+    assert iq["krylov"]["m"] != want
+
+
+def _dense_variants(P, alpha):
+    n, ell = P.nx, P.nt
+    A = R.aao_matrix_mass(R.k_dense(P), P.tau, ell, np.ones(n))
+    E = np.zeros((ell, ell))
+    E[0, ell - 1] = 1.0
+    Pa = A - alpha * np.kron(E, np.eye(n))
+    U1 = np.linalg.solve(Pa, P.G.reshape(-1)).reshape(ell, n)
+    r = np.zeros((ell, n))
+    r[0] = U1[-1]
+    return U1, U1 - alpha * np.linalg.solve(Pa, r.reshape(-1)).reshape(ell, n)
+
+
+def test_py_mutation_two_loop_weight_dropped():
+    """The correction without its weight alpha^{1/l} fails the dense SMW pin of two loops."""
+    M = _mutant_reference("Uc = U1 - a * idft_time(W) / d[:, None]", "Uc = U1 - idft_time(W) / d[:, None]")
+    P = W.random_tridiag_problem(5, 8, seed=3)
+    _, U2 = _dense_variants(P, 1e-2)
+    V2, _ = M.paradiag_alpha(P, 1e-2, loops=2)
+    assert R.rel_err(V2, U2) > 1e-6
+
+
+def test_py_mutation_u1_without_d_alpha_inverse():
+    """U_1 without D_alpha^{-1} after the inverse DFT fails the dense pin of one loop."""
+    M = _mutant_reference("U1 = (idft_time(L) / d[:, None])", "U1 = idft_time(L)")
+    P = W.random_tridiag_problem(5, 8, seed=3)
+    U1, _ = _dense_variants(P, 1e-2)
+    V1, _ = M.paradiag_alpha(P, 1e-2, loops=1)
+    assert R.rel_err(V1, U1) > 1e-6
