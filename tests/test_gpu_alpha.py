@@ -135,3 +135,20 @@ def test_fixed_loop_variants_reach_table3_orders(pd, nu):
     assert res[2] <= 1e-8
     assert 1e-9 <= res[1] <= 1e-6
     assert res[2] < res[1]
+
+
+def test_one_loop_residual_scales_with_alpha(pd):
+    """Fig. 1: the residual of U_1 (one parallel-in-time loop, loops = 1) falls linearly with
+    alpha, and ||U_1|| hardly moves (1D advection-diffusion, nu = 2^-5, l = 64)."""
+    P = W.advdiff1d_pulse(511, 64, nu=2.0 ** -5, seed=1)
+    G = torch.from_numpy(P.G).to(dev())
+    res, nrm = {}, {}
+    for alpha in (1e-1, 1e-2, 1e-3, 1e-4):
+        with pd.Plan.from_problem(P, precision="fp64", alpha=alpha, loops=1, device=dev()) as plan:
+            U, _ = plan.solve(G)
+        U = U.cpu().numpy()
+        res[alpha] = np.linalg.norm(R.residual_extended(P, U)) / np.linalg.norm(P.G)
+        nrm[alpha] = np.linalg.norm(U)
+    q = [res[a] / a for a in res]
+    assert max(q) / min(q) < 1.05, res
+    assert max(nrm.values()) / min(nrm.values()) < 1.02

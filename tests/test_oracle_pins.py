@@ -571,3 +571,34 @@ def test_fixed_loop_variants_reach_table3_orders(nu):
     r2 = rr(R.paradiag_alpha(P, 1e-4, loops=2)[0])
     r1 = rr(R.paradiag_alpha(P, 1e-6, loops=1)[0])
     assert r2 <= 1e-8 and 1e-9 <= r1 <= 1e-6 and r2 < r1
+
+
+def test_algorithm3_reproduces_figure1_trends():
+    """Sec. 6, Fig. 1 (one FOM step, maxit = 1), on 1D advection-diffusion with the figure's
+    nu = 2^-5 and l = 64 (its 2D operator is not separable):
+    - ||U_1|| hardly moves with alpha, ||U_2|| follows alpha;
+    - the error and residual of U = U_1 + U_2 scale like alpha^2, the residual of U_1 like alpha;
+    - alpha ~ 1e-7 leaves U_1 alone a residual of order 1e-7;
+    - below alpha ~ 1e-4 the conditioning of F D_alpha takes over and the error grows again."""
+    P = W.advdiff1d_pulse(511, 64, nu=2.0 ** -5, seed=1)
+    ex = R.be_solve_refined(P)
+    rr = lambda X: np.linalg.norm(R.residual_extended(P, X)) / np.linalg.norm(P.G)
+    alphas = [1.0, 1e-1, 1e-2, 1e-3, 1e-4, 1e-5, 1e-6, 1e-7, 1e-8, 1e-10]
+    n1, n2, err, res, res1 = {}, {}, {}, {}, {}
+    for a in alphas:
+        U, _ = R.paradiag_alpha(P, a, eps=0.0, maxit=1)
+        U1, _ = R.paradiag_alpha(P, a, loops=1)
+        n1[a], n2[a] = np.linalg.norm(U1), np.linalg.norm(U - U1)
+        err[a], res[a], res1[a] = R.rel_err(U, ex), rr(U), rr(U1)
+    assert max(n1.values()) / min(n1.values()) < 1.02
+    c2 = [n2[a] / a for a in alphas if a <= 1e-1]
+    assert max(c2) / min(c2) < 1.05
+    for d in (err, res):  # alpha^2 while rounding is negligible
+        q = [d[a] / a ** 2 for a in (1.0, 1e-1, 1e-2)]
+        assert max(q) / min(q) < 1.1
+    q1 = [res1[a] / a for a in (1.0, 1e-1, 1e-2, 1e-3, 1e-4, 1e-5)]
+    assert max(q1) / min(q1) < 1.05
+    assert 1e-8 < res1[1e-7] < 1e-6
+    best = min(alphas, key=lambda a: err[a])
+    assert 1e-4 <= best <= 1e-2
+    assert err[1e-10] > 100 * err[best] and err[1e-6] > err[1e-4]
