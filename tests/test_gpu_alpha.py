@@ -152,3 +152,16 @@ def test_one_loop_residual_scales_with_alpha(pd):
     q = [res[a] / a for a in res]
     assert max(q) / min(q) < 1.05, res
     assert max(nrm.values()) / min(nrm.values()) < 1.02
+
+
+@pytest.mark.parametrize("loops,alpha", [(2, 1e-2), (1, 1e-2)])
+def test_fixed_loop_variants_in_2d(pd, loops, alpha):
+    """The fixed-loop variants on the 2D path (DST along y, then the same loops): 2D heat,
+    15 x 15, against the oracle's variant within 1e-12 kappa(F D_alpha)."""
+    P = W.heat2d_smooth(15, 16, T=0.1, seed=2)
+    ref, _ = R.paradiag_alpha(P, alpha, loops=loops)
+    with pd.Plan.from_problem(P, precision="fp64", alpha=alpha, loops=loops, device=dev()) as plan:
+        U, st = plan.solve(torch.from_numpy(P.G).to(dev()))
+    kappa = alpha ** (-(P.nt - 1) / P.nt)
+    assert R.rel_err(U.cpu().numpy(), ref) <= 1e-12 * kappa, st
+    assert st["pint_loops"] == loops
