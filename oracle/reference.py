@@ -30,11 +30,11 @@ What each function follows (paper sections/equations):
                         all-at-once system (I + tau K) U - U C_1^T = R.
 * ``kappa_bound``       eq. (14), Theorem 3.1.
 * ``alpha_quantities``, ``paradiag_alpha``, ``j_alpha_dense``  Algorithm 3 and
-                        eqs. (15)-(17) (alpha-circulant C_alpha, scaled DFT).
+                        eqs. (15)-(17) (alpha-circulant C_alpha, scaled DFT), with
+                        the U_1 early exit and the fixed-loop variants of Table 3.
 * ``j_extreme_eigs``    the extreme eigenvalues of J_l for SPD K (Sec. 6.1).
 
-Readings of points where the paper is silent or inconsistent (all listed in
-the design doc with their justification):
+Readings of points where the paper is silent or inconsistent:
 
 1. eq. (11)-(13) and Algorithm 2 write t_{m+1,m} where the shifted Arnoldi
    relation for (1 - pi_i) I + tau K carries tau * t_{m+1,m}; the factor tau is
@@ -45,6 +45,11 @@ the design doc with their justification):
 4. Breakdown t_{m+1,m} ~ 0 (silent in the paper): K_m(K, b) is invariant, the
    t-term of eq. (12) vanishes, the residual is zero and the iteration stops.
 5. U = Re((L - W) F^{-T}); the imaginary part is roundoff for real data.
+6. Frozen residual (q > 1, Sec. 3): the paper checks only at m mod q = 0; a step
+   also checks at m = maxit and at a breakdown, so a run always ends on a checked
+   step and x_m = V_m y_m uses that step's y_m.
+7. Fixed-loop variants (Sec. 6, Table 3): two loops take x_m = b (the inner matrix
+   of eq. (17) replaced by the identity); one loop returns U_1.
 """
 from __future__ import annotations
 
