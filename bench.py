@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="config2")
+    ap.add_argument("--workload", default="heat1d_1023x1024")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve", action="store_true",
                     help="full serving sweep: 10,000 requests at each of 100, 300, 1000, 3000, 5000 arrivals/s "
@@ -75,10 +75,10 @@ def workload(name):
 
     P = W.by_name(name)
     desc = {
-        "config1": "1D heat n_x=127 n_t=64 T=1 sine-mode u0",
-        "config2": "1D heat n_x=1023 n_t=1024 T=1, 16 seeded space-time sine-mode forcing terms",
-        "config3": "2D heat 255x255 n_t=256 T=0.1 smooth random u0",
-        "config4": "1D advection-diffusion a=1 nu=1e-3 n_x=4095 n_t=2048 T=1 Gaussian pulse",
+        "heat1d_127x64": "1D heat n_x=127 n_t=64 T=1 sine-mode u0",
+        "heat1d_1023x1024": "1D heat n_x=1023 n_t=1024 T=1, 16 seeded space-time sine-mode forcing terms",
+        "heat2d_255x255x256": "2D heat 255x255 n_t=256 T=0.1 smooth random u0",
+        "advdiff1d_4095x2048": "1D advection-diffusion a=1 nu=1e-3 n_x=4095 n_t=2048 T=1 Gaussian pulse",
     }[name]
     return P, desc
 

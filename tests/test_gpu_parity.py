@@ -110,7 +110,7 @@ def test_shifted_solves_and_b(pd, prec, P):
 
 def _full_problems():
     return [
-        W.config1(),
+        W.heat1d_127x64(),
         W.heat1d_forced(255, 128, seed=3),
         W.advdiff1d_pulse(511, 256, seed=4),
         W.random_tridiag_problem(1, 1, seed=1),
@@ -236,9 +236,9 @@ def test_dst_y_matches_definition(pd):
 # ----------------------------------------------------------------------------
 
 
-@pytest.mark.parametrize("name", ["config2", "config4"])
+@pytest.mark.parametrize("name", ["heat1d_1023x1024", "advdiff1d_4095x2048"])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_full_size_1d_configs(pd, name, prec):
+def test_full_size_1d_workloads(pd, name, prec):
     P = W.by_name(name)
     Uref = R.be_solve_refined(P)
     U, st, _, x = _solve(pd, P, prec)
@@ -246,14 +246,14 @@ def test_full_size_1d_configs(pd, name, prec):
 
 
 @pytest.fixture(scope="module")
-def cfg3_ref():
-    P = W.config3()
+def heat2d_ref():
+    P = W.heat2d_255x255x256()
     return P, R.be_solve_refined(P)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_full_size_2d_config3(pd, cfg3_ref, prec):
-    P, Uref = cfg3_ref
+def test_full_size_2d_heat(pd, heat2d_ref, prec):
+    P, Uref = heat2d_ref
     U, st, _, _ = _solve(pd, P, prec)
     assert R.rel_err(U, Uref) <= TOL[prec], st
 

@@ -81,7 +81,7 @@ def test_be_equals_dense_all_at_once_solve(P):
     assert R.rel_err(R.be_solve(P), Ud) < 1e-13
 
 
-@pytest.mark.parametrize("name", ["config1", "config2", "config4"])
+@pytest.mark.parametrize("name", ["heat1d_127x64", "heat1d_1023x1024", "advdiff1d_4095x2048"])
 def test_be_solution_satisfies_eq2(name):
     """The oracle's U makes the left side of eq. (2) equal G (full-size 1D configs)."""
     P = W.by_name(name)
@@ -370,7 +370,7 @@ def test_refined_oracle_closed_form():
     assert R.rel_err(R.be_solve_refined(P), Uc) < 2e-15
 
 
-@pytest.mark.parametrize("P", [W.heat2d_smooth(63, 64, 0.1, seed=1), W.config2(), W.advdiff1d_pulse(511, 256, seed=2)],
+@pytest.mark.parametrize("P", [W.heat2d_smooth(63, 64, 0.1, seed=1), W.heat1d_1023x1024(), W.advdiff1d_pulse(511, 256, seed=2)],
                          ids=lambda p: p.name)
 def test_refined_oracle_converges(P):
     """A second correction on the extended residual is negligible next to the first

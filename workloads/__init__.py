@@ -13,10 +13,10 @@ from .gen import (  # noqa: F401
     heat1d_operator,
     advdiff1d_operator,
     heat2d_axis_operator,
-    config1,
-    config2,
-    config3,
-    config4,
+    heat1d_127x64,
+    heat1d_1023x1024,
+    heat2d_255x255x256,
+    advdiff1d_4095x2048,
     heat1d_sine_modes,
     heat1d_forced,
     heat2d_smooth,

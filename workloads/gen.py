@@ -292,27 +292,27 @@ def with_mass(P: Problem, seed: int = 0, lo: float = 0.5, hi: float = 2.0) -> Pr
                    recipe=P.recipe + f"; diagonal mass matrix U[{lo}, {hi}) (seed {seed})", m_diag=m)
 
 
-def config1(seed: int = 0) -> Problem:
+def heat1d_127x64(seed: int = 0) -> Problem:
     """1D heat, n_x = 127, n_t = 64, T = 1, f = 0, sine-mode u0 (FP64 everywhere)."""
     return heat1d_sine_modes(127, 64, 1.0, seed)
 
 
-def config2(seed: int = 0) -> Problem:
+def heat1d_1023x1024(seed: int = 0) -> Problem:
     """1D heat, n_x = 1023, n_t = 1024, T = 1, 16 space-time sine-mode forcing terms."""
     return heat1d_forced(1023, 1024, 1.0, seed)
 
 
-def config3(seed: int = 0) -> Problem:
+def heat2d_255x255x256(seed: int = 0) -> Problem:
     """2D heat, 255 x 255 interior grid, n_t = 256, T = 0.1, smooth random u0."""
     return heat2d_smooth(255, 256, 0.1, seed)
 
 
-def config4(seed: int = 0) -> Problem:
+def advdiff1d_4095x2048(seed: int = 0) -> Problem:
     """1D advection-diffusion a = 1, nu = 1e-3, n_x = 4095, n_t = 2048, T = 1."""
     return advdiff1d_pulse(4095, 2048, 1.0, seed)
 
 
-_BY_NAME = {"config1": config1, "config2": config2, "config3": config3, "config4": config4}
+_BY_NAME = {f.__name__: f for f in (heat1d_127x64, heat1d_1023x1024, heat2d_255x255x256, advdiff1d_4095x2048)}
 
 
 def by_name(name: str, seed: int = 0) -> Problem:

@@ -6,7 +6,7 @@ Each request is one all-at-once backward-Euler problem (eq. 2):
   accepts);
 - n_t a power of two in {32..2048}, T = 1;
 - diffusion nu log-uniform in [1e-4, 1];
-- forcing of 16 space-time sine modes with N(0, 1) amplitudes, as in config 2 (2D: a
+- forcing of 16 space-time sine modes with N(0, 1) amplitudes, as in the 1D heat workload heat1d_1023x1024 (2D: a
   product sine in x and y);
 - arrival times of a Poisson process of the given rate.
 
