@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--profile", type=int, default=0, metavar="N",
                     help="only run N mixed solves of the workload with host-driven loops, one launch per "
                          "kernel node, for a profiler's launch list (prints no benchmark line)")
+    ap.add_argument("--profile-precision", default="mixed", choices=["mixed", "fp64"],
+                    help="precision of the --profile solves")
     return ap.parse_args()
 
 
@@ -570,7 +572,8 @@ def serve_bench(args, device):
 
 
 def run_profile(args):
-    """N mixed solves with host-driven loops (each kernel node its own launch), for ncu."""
+    """N solves (mixed, or FP64 with --profile-precision fp64) with host-driven loops (each
+    kernel node its own launch), for ncu."""
     import torch
 
     import __graft_entry__ as entry
@@ -582,11 +585,12 @@ def run_profile(args):
     device = torch.device("cuda", 0)
     G = torch.from_numpy(P.G).to(device)
     U = torch.empty_like(G)
-    with Plan.from_problem(P, precision="mixed", device=device, no_graph=True) as plan:
+    with Plan.from_problem(P, precision=args.profile_precision, device=device, no_graph=True) as plan:
         for _ in range(args.profile):
             _, st = plan.solve(G, U)
     torch.cuda.synchronize()
-    print(json.dumps({"profile": args.workload, "solves": args.profile, "launches_per_solve": st["kernel_launches"]}))
+    print(json.dumps({"profile": args.workload, "precision": args.profile_precision, "solves": args.profile,
+                      "launches_per_solve": st["kernel_launches"]}))
     return 0
 
 
