@@ -71,3 +71,34 @@ def test_scheduler_admission_waits_for_memory():
 def test_key_of():
     assert key_of(_req(0, "heat2d", 127, 256, 0)) == BatchKey(2, 256, 127, 127)
     assert key_of(_req(0, "advdiff1d", 1025, 256, 0)) == BatchKey(1, 256, 2048, 1)
+
+
+def test_device_rhs_equals_the_host_problem():
+    """The service builds G with torch on its device; on the CPU device it must equal the
+    numpy right-hand side of request_problem (which the parity tests give the oracle), for
+    every request kind, also when written into the first columns of a wider buffer."""
+    import numpy as np
+    import torch
+
+    reqs = [_req(1, "heat1d", 300, 32, 0.0), _req(2, "advdiff1d", 257, 64, 0.0), _req(3, "heat2d", 63, 32, 0.0)]
+    for r in reqs:
+        G = S.request_problem(r).G
+        Gd = S.rhs_device(r, torch, torch.device("cpu")).numpy()
+        assert Gd.shape == G.shape
+        assert np.linalg.norm(Gd - G) <= 1e-13 * np.linalg.norm(G)
+        out = torch.full((r.nt, G.shape[1] + 5), 7.0, dtype=torch.float64)
+        S.rhs_device(r, torch, torch.device("cpu"), out=out)
+        assert np.linalg.norm(out[:, : G.shape[1]].numpy() - G) <= 1e-13 * np.linalg.norm(G)
+        assert bool((out[:, G.shape[1]:] == 7.0).all())  # columns past the request untouched
+
+
+def test_slot_operators():
+    r = _req(4, "heat1d", 200, 64, 0.0)
+    op = S.request_problem_operator_only(r, 256)
+    assert (op.nx, op.nt) == (200, 64) and op.k_diag.shape == (200,)
+    import pytest
+
+    with pytest.raises(ValueError):
+        S.request_problem_operator_only(r, 128)
+    e = S.empty_slot(64)
+    assert (e.nx, e.nt) == (1, 64) and e.k_diag[0] == 1.0 and e.k_lo[0] == 0.0 and e.k_up[0] == 0.0
