@@ -67,7 +67,11 @@ typedef struct pd_desc {
   int64_t nt;            /* l, number of time steps: a power of two, 1 <= l <= 8192 */
   double tau;            /* time step tau = T / l > 0 */
   /* K (1D) or T_x (2D): tridiagonal, row i = lo[i] u[i-1] + diag[i] u[i] + up[i] u[i+1];
-   * lo[0] and up[n-1] are ignored.  Length nx, host memory. */
+   * lo[0] and up[n-1] are ignored.  Length nx, host memory.  The shifted systems are
+   * eliminated without pivoting, so every block must be weakly diagonally dominant by rows
+   * (diag[i] >= |lo[i]| + |up[i]|; in 2D with the smallest eigenvalue of T_y added to
+   * diag) or symmetric positive definite; otherwise PD_ERR_UNSUPPORTED (e.g. centred
+   * advection at cell Peclet number > 2). */
   const double *k_lo, *k_diag, *k_up;
   /* 2D only: T_y, length ny, host memory.  This build requires T_y to be symmetric
    * Toeplitz (constant diagonal and constant off-diagonal) and ny + 1 to be a power
@@ -133,7 +137,7 @@ typedef struct pd_desc {
                                 a power of two with teams * threads-per-team <= 512
                                 (<= 256 with 16 rows per thread) */
   int32_t tune_krylov_ctas;  /* CTAs of the Krylov vector kernels: 1 = one 512-thread CTA
-                                (n_bar <= 8192), > 1 = cooperative launch of 64-thread CTAs
+                                (n_bar <= 8192), > 1 = cooperative launch of 512-thread CTAs
                                 (<= SM count) */
   int32_t tune_cap_ctas;     /* CTAs of the capacitance-term kernel, 1 .. 1024 */
   int32_t tune_fft_cols;     /* columns per CTA of the time FFTs: 2, 4, 8 or 16 */
@@ -272,6 +276,15 @@ pd_status paradiag_dst_y(pd_plan *plan, const double *X_dev, double *Y_dev);
  * n_bar, device.  Either may be NULL. */
 pd_status paradiag_last_vectors(pd_plan *plan, double *b_dev, double *x_dev);
 
+/* The binary32 reciprocal 1/v that the PD_MIXED shifted solves use inside the complex
+ * division 1/a = conj(a) / |a|^2 (Smith-free: the operands are bounded away from zero and
+ * overflow): the hardware approximation refined by one Newton-Raphson step.  It is within
+ * 1 ulp of 1/v for normal-range v, not always correctly rounded, and flushes subnormals to
+ * zero.  x, r: device, n float32 each (r[i] = that reciprocal of x[i]); stream: cudaStream_t.
+ * Returns after the stream has synchronised.  A verification entry point: the paper's
+ * arithmetic is not specified to this level. */
+pd_status paradiag_recip_f32(const float *x, float *r, int64_t n, void *stream);
+
 /* ---- Allocation-free variant ---------------------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers that cannot
  * call cudaMalloc when they need this step (an arena or pool that owns all device
@@ -284,7 +297,9 @@ pd_status paradiag_last_vectors(pd_plan *plan, double *b_dev, double *x_dev);
  *   nt      time steps l (power of two, 1 <= nt <= 8192), n rows of K (1 <= n <= 4096);
  *           larger sizes return PD_ERR_UNSUPPORTED with a message in paradiag_last_error().
  *   tau     time step; k_lo, k_diag, k_up: device, length n, the tridiagonal K
- *           (k_lo[0], k_up[n-1] ignored).
+ *           (k_lo[0], k_up[n-1] ignored); K must be weakly diagonally dominant by rows or
+ *           symmetric positive definite, as for paradiag_plan (not checked here: the
+ *           arrays are on the device).
  *   R       device, (nt/2+1, n) complex128 right-hand sides (half spectrum of real data).
  *   Y       device, (nt/2+1, n) complex128 solutions, or NULL to skip the store.
  *   b       device, length n float64: b = sum_{i=0}^{l-1} gamma_i Y_i.

@@ -132,6 +132,7 @@ SIGNATURES = {
     "paradiag_time_idft": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "paradiag_shifted_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "paradiag_dst_y": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "paradiag_recip_f32": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]),
     "paradiag_last_vectors": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "paradiag_smw_rhs_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p,
                                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -222,6 +223,10 @@ def paradiag_shifted_solve(plan: int, R_ptr: int, Y_ptr, b_ptr) -> None:
 
 def paradiag_dst_y(plan: int, X_ptr: int, Y_ptr: int) -> None:
     check("paradiag_dst_y", load().paradiag_dst_y(plan, X_ptr, Y_ptr))
+
+
+def paradiag_recip_f32(x_ptr: int, r_ptr: int, n: int, stream_ptr) -> None:
+    check("paradiag_recip_f32", load().paradiag_recip_f32(x_ptr, r_ptr, n, stream_ptr))
 
 
 def paradiag_last_vectors(plan: int, b_ptr, x_ptr) -> None:

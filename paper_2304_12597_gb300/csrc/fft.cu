@@ -25,11 +25,17 @@ constexpr int kLoadBatch = 8;
 constexpr int kFftMaxThreads = 512;
 static int fft_threads(int n, int tx) { return (int64_t)n * tx >= 4096 ? 512 : 256; }
 
+// Series of length n sit n + 1 complex values apart in shared memory: the columns of a
+// tile (two per series) then fall into different banks when a warp writes one time row
+// (or reads one frequency) of every series, instead of all series mapping to one bank.
+__host__ __device__ inline int series_stride(int n) { return n + 1; }
+
 // In-place DIT FFT of `nseries` series of length n = 2^logn stored back to back
 // in shared memory, input in bit-reversed order, output in natural order.
 // All threads of the CTA take part; the caller synchronises before the call.
 template <typename T>
 __device__ void fft_smem(cpx<T> *buf, int n, int logn, int nseries, const cpx<T> *__restrict__ tw) {
+  const int sst = series_stride(n);
   int s = 0;
   if (logn >= 2) {  // first radix-4 pass: every twiddle is 1 (j = 0), no multiplications
     const int lq = logn - 2;
@@ -37,7 +43,7 @@ __device__ void fft_smem(cpx<T> *buf, int n, int logn, int nseries, const cpx<T>
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
       const int ser = idx >> lq;
       const int base = (idx & ((1 << lq) - 1)) << 2;
-      cpx<T> *p = buf + ((size_t)ser << logn) + base;
+      cpx<T> *p = buf + (size_t)ser * sst + base;
       const cpx<T> x0 = p[0], x1 = p[1], x2 = p[2], x3 = p[3];
       const cpx<T> a0 = add(x0, x1), a1 = sub(x0, x1), a2 = add(x2, x3), a3 = sub(x2, x3);
       const cpx<T> mu = mk<T>(a3.y, -a3.x);  // -i * a3
@@ -58,7 +64,7 @@ __device__ void fft_smem(cpx<T> *buf, int n, int logn, int nseries, const cpx<T>
       const int q = idx & ((1 << lq) - 1);
       const int j = q & (h - 1);
       const int base = ((q >> s) << (s + 2)) + j;
-      cpx<T> *p = buf + ((size_t)ser << logn);
+      cpx<T> *p = buf + (size_t)ser * sst;
       const cpx<T> w1 = tw[j << (logn - s - 1)];
       const cpx<T> w2 = tw[j << (logn - s - 2)];
       cpx<T> x0 = p[base], x1 = p[base + h], x2 = p[base + 2 * h], x3 = p[base + 3 * h];
@@ -84,7 +90,7 @@ __device__ void fft_smem(cpx<T> *buf, int n, int logn, int nseries, const cpx<T>
       const int b = idx & ((1 << lh) - 1);
       const int j = b & (h - 1);
       const int i0 = ((b >> s) << (s + 1)) + j;
-      cpx<T> *p = buf + ((size_t)ser << logn);
+      cpx<T> *p = buf + (size_t)ser * sst;
       const cpx<T> w = tw[j << (logn - s - 1)];
       cpx<T> x0 = p[i0], x1 = p[i0 + h];
       cpx<T> t = mul(w, x1);
@@ -106,7 +112,7 @@ __device__ void r2c_store(const cpx<T> *buf, int n, int logn, int64_t x0, int64_
     const int c = idx - k * TX;
     const int64_t col = x0 + c;
     if (col >= ncols) continue;
-    const cpx<T> *z = buf + ((size_t)(c >> 1) << logn);
+    const cpx<T> *z = buf + (size_t)(c >> 1) * series_stride(n);
     const cpx<T> zk = z[k], zm = z[(n - k) & (n - 1)];
     cpx<T> r;
     if ((c & 1) == 0) {
@@ -118,15 +124,51 @@ __device__ void r2c_store(const cpx<T> *buf, int n, int logn, int64_t x0, int64_
   }
 }
 
+// Sum of squares of the transformed data (per thread: ss), reduced over the launch: each
+// CTA stores its partial, and the last CTA to finish (no CTA waits for another) adds the
+// partials in a fixed order and stores the square root into *rn.dst.
+__device__ void rhs_norm_finish(double ss, const RhsNorm &rn) {
+  __shared__ double red[32];
+  __shared__ int last;
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  ss = warp_sum(ss);
+  if (l == 0) red[w] = ss;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < nw; ++i) t += red[i];
+    rn.part[blockIdx.x] = t;
+    __threadfence();
+    last = atomicAdd(rn.counter, 1) == (int)gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double t = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) t += __ldcg(rn.part + i);
+  t = warp_sum(t);
+  __syncthreads();  // red is reused
+  if (l == 0) red[w] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s2 = 0.0;
+    for (int i = 0; i < nw; ++i) s2 += red[i];
+    *rn.dst = sqrt(s2);
+    *rn.counter = 0;
+  }
+}
+
 template <typename T, typename Tin, int TX>
 __global__ void __launch_bounds__(kFftMaxThreads) k_fft_r2c(const Tin *__restrict__ X, int64_t ldx, int64_t ncols,
                                                  int n, int logn, const cpx<T> *__restrict__ tw,
-                                                 cpx<T> *__restrict__ S, int64_t lds, const T *__restrict__ rs) {
+                                                 cpx<T> *__restrict__ S, int64_t lds, const T *__restrict__ rs,
+                                                 RhsNorm rn) {
   grid_dep_wait();
   extern __shared__ __align__(16) unsigned char smraw[];
   cpx<T> *buf = reinterpret_cast<cpx<T> *>(smraw);
   const int64_t x0 = (int64_t)blockIdx.x * TX;
   const int total = n * TX;
+  T ss = T(0);  // squares of the loaded values (rn)
   // kLoadBatch loads in flight per thread before any is used
   for (int i0 = threadIdx.x; i0 < total; i0 += kLoadBatch * blockDim.x) {
     T v[kLoadBatch];
@@ -143,14 +185,16 @@ __global__ void __launch_bounds__(kFftMaxThreads) k_fft_r2c(const Tin *__restric
       if (idx < total) {
         const int j = idx / TX;
         const int c = idx - j * TX;
-        T *slot = reinterpret_cast<T *>(&buf[((size_t)(c >> 1) << logn) + bitrev(j, logn)]);
+        T *slot = reinterpret_cast<T *>(&buf[(size_t)(c >> 1) * series_stride(n) + bitrev(j, logn)]);
         slot[c & 1] = rs ? v[u] * rs[j] : v[u];
+        ss += v[u] * v[u];
       }
     }
   }
   __syncthreads();
   fft_smem<T>(buf, n, logn, TX >> 1, tw);
   r2c_store<T, TX>(buf, n, logn, x0, ncols, S, lds);
+  if (rn.part) rhs_norm_finish((double)ss, rn);
 }
 
 // Same transform of the 1D FP64 residual r = G_t + u_{t-1} - (I + tau K) u_t, formed
@@ -163,7 +207,7 @@ __global__ void __launch_bounds__(kFftMaxThreads, 2) k_fft_r2c_res(const double 
                                                      const double *__restrict__ rxu,
                                                      const cpx<T> *__restrict__ tw, cpx<T> *__restrict__ S,
                                                      int64_t lds, const T *__restrict__ rs,
-                                                     const int *__restrict__ mex, int mnx) {
+                                                     const int *__restrict__ mex, int mnx, RhsNorm rn) {
   grid_dep_wait();
   extern __shared__ __align__(16) unsigned char smraw[];
   cpx<T> *buf = reinterpret_cast<cpx<T> *>(smraw);
@@ -180,8 +224,9 @@ __global__ void __launch_bounds__(kFftMaxThreads, 2) k_fft_r2c_res(const double 
   const int64_t ol = col > 0 ? -1 : 0, ou = col + 1 < ncols ? 1 : 0;  // in-range neighbour offsets
   // batched plans: problem (col / mnx) scaled by 2^mex[problem] (exact)
   const T msc = (mex && live) ? (T)ldexp(1.0, mex[col / mnx]) : T(1);
-  T *col_buf = reinterpret_cast<T *>(buf + ((size_t)(c >> 1) << logn)) + (c & 1);
+  T *col_buf = reinterpret_cast<T *>(buf + (size_t)(c >> 1) * series_stride(n)) + (c & 1);
   constexpr int kB = kLoadBatch / 2;  // five FP64 loads per element
+  T ss = T(0);  // squares of the residual (rn)
   for (int j0 = (int)threadIdx.x / TX; j0 < n; j0 += kB * ((int)blockDim.x / TX)) {
     double g[kB], um[kB], ul[kB], uc[kB], ur[kB];
 #pragma unroll
@@ -203,12 +248,14 @@ __global__ void __launch_bounds__(kFftMaxThreads, 2) k_fft_r2c_res(const double 
         const double res = fma(-cu, ur[q], fma(-cl, ul[q], fma(-cd, uc[q], g[q] + um[q])));
         const T r = (T)res * msc;
         col_buf[2 * bitrev(j, logn)] = rs ? r * rs[j] : r;
+        ss += r * r;
       }
     }
   }
   __syncthreads();
   fft_smem<T>(buf, n, logn, TX >> 1, tw);
   r2c_store<T, TX>(buf, n, logn, x0, ncols, S, lds);
+  if (rn.part) rhs_norm_finish((double)ss, rn);
 }
 
 // Inverse: Z[k] = A[k] + i B[k] over the full spectrum (A[n-k] = conj A[k]);
@@ -247,7 +294,7 @@ __global__ void __launch_bounds__(256) k_fft_c2r(const cpx<T> *__restrict__ S, i
       if (idx < total) {
         const int kk = idx / np;
         const int p = idx - kk * np;
-        cpx<T> *ser = buf + ((size_t)p << logn);
+        cpx<T> *ser = buf + (size_t)p * series_stride(n);
         // conj(A + i B) = (A.x - B.y) - i (A.y + B.x); at n - kk the conjugate half
         // gives (A.x + B.y) + i (A.y - B.x)
         ser[bitrev(kk, logn)] = mk<T>(A[u].x - B[u].y, -(A[u].y + B[u].x));
@@ -282,7 +329,7 @@ __global__ void __launch_bounds__(256) k_fft_c2r(const cpx<T> *__restrict__ S, i
       const int c = idx - j * TX;
       const int64_t col = x0 + c;
       if (idx >= tot2 || col >= ncols) continue;
-      const cpx<T> r = buf[((size_t)(c >> 1) << logn) + j];
+      const cpx<T> r = buf[(size_t)(c >> 1) * series_stride(n) + j];
       const T sc = rsi ? inv_n * rsi[j] : inv_n;
       const T v = ((c & 1) == 0) ? r.x * sc : -r.y * sc;
       const int64_t o = (int64_t)j * ldo + col;
@@ -366,9 +413,10 @@ __global__ void __launch_bounds__(256) k_dst_y(const Tin *__restrict__ X, Tout *
   const Tin *Xt = X + t * ny * nx;
   Tout *Yt = Y + t * ny * nx;
   const int np = TX >> 1;
-  // zero the whole extension, then scatter the odd extension
-  for (int idx = threadIdx.x; idx < np * N; idx += blockDim.x) buf[idx] = mk<T>(T(0), T(0));
-  __syncthreads();
+  // the odd extension: entries 0 and ny + 1 = N/2 are zero (bit-reversed slots 0 and 1),
+  // the scatter below writes the rest
+  for (int idx = threadIdx.x; idx < 2 * np; idx += blockDim.x)
+    buf[(size_t)(idx >> 1) * series_stride(N) + bitrev((idx & 1) ? (N >> 1) : 0, logN)] = mk<T>(T(0), T(0));
   const int total = (int)ny * TX;
   for (int i0 = threadIdx.x; i0 < total; i0 += kLoadBatch * blockDim.x) {
     T v[kLoadBatch];
@@ -385,7 +433,7 @@ __global__ void __launch_bounds__(256) k_dst_y(const Tin *__restrict__ X, Tout *
       if (idx >= total) continue;
       const int y = idx / TX;
       const int c = idx - y * TX;
-      cpx<T> *ser = buf + ((size_t)(c >> 1) << logN);
+      cpx<T> *ser = buf + (size_t)(c >> 1) * series_stride(N);
       T *pos = reinterpret_cast<T *>(&ser[bitrev(y + 1, logN)]);
       T *neg = reinterpret_cast<T *>(&ser[bitrev(N - (y + 1), logN)]);
       pos[c & 1] = v[u];
@@ -410,7 +458,7 @@ __global__ void __launch_bounds__(256) k_dst_y(const Tin *__restrict__ X, Tout *
       const int c = idx - l * TX;
       const int64_t col = x0 + c;
       if (idx >= total || col >= nx) continue;
-      const cpx<T> z = buf[((size_t)(c >> 1) << logN) + l + 1];
+      const cpx<T> z = buf[(size_t)(c >> 1) * series_stride(N) + l + 1];
       const T v = ((c & 1) == 0) ? (T(-0.5) * scale) * z.y : (T(0.5) * scale) * z.x;
       const int64_t o = (int64_t)l * nx + col;
       if (mode == 0) {
@@ -434,13 +482,14 @@ static int ilog2(int n) {
 template <typename T>
 static int pick_tx(int n, int cap, int64_t ncols, int req = 0) {
   const size_t budget = 96 * 1024;
+  const size_t sst = (size_t)series_stride(n);
   if (req) {  // the caller's choice, within the shared-memory budget of one CTA
     int tx = std::min(req, cap);
-    while (tx > 2 && (size_t)(tx / 2) * n * sizeof(cpx<T>) > 2 * budget) tx >>= 1;
+    while (tx > 2 && (size_t)(tx / 2) * sst * sizeof(cpx<T>) > 2 * budget) tx >>= 1;
     return tx;
   }
   int tx = cap;
-  while (tx > 2 && (size_t)(tx / 2) * n * sizeof(cpx<T>) > budget) tx >>= 1;
+  while (tx > 2 && (size_t)(tx / 2) * sst * sizeof(cpx<T>) > budget) tx >>= 1;
   while (tx > 4 && (ncols + tx - 1) / tx < 4 * (int64_t)sm_count()) tx >>= 1;
   return tx;
 }
@@ -456,10 +505,11 @@ static int pick_tx(int n, int cap, int64_t ncols, int req = 0) {
 
 template <typename T, typename Tin>
 void launch_fft_r2c(Ctx &c, const Tin *X, int64_t ldx, int64_t ncols, int n, const cpx<T> *tw,
-                    cpx<T> *S, int64_t lds, const T *rs) {
+                    cpx<T> *S, int64_t lds, const T *rs, const RhsNorm *rnp) {
+  const RhsNorm rn = rnp ? *rnp : RhsNorm{nullptr, nullptr, nullptr};
   const int logn = ilog2(n);
   const int TX = pick_tx<T>(n, sizeof(T) == 8 ? 8 : 16, ncols, c.fft_cols);
-  const size_t smem = (size_t)(TX / 2) * n * sizeof(cpx<T>);
+  const size_t smem = (size_t)(TX / 2) * series_stride(n) * sizeof(cpx<T>);
   const int grid = (int)((ncols + TX - 1) / TX);
   const double bytes = (double)n * ncols * sizeof(Tin) + (double)(n / 2 + 1) * ncols * sizeof(cpx<T>);
   c.launch(sizeof(T) == 8 ? "fft_r2c_f64" : "fft_r2c_f32", bytes, [&] {
@@ -467,7 +517,7 @@ void launch_fft_r2c(Ctx &c, const Tin *X, int64_t ldx, int64_t ncols, int n, con
       if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_fft_r2c<T, Tin, kTX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       pdl_launch(c.pdl, k_fft_r2c<T, Tin, kTX>, dim3(grid), dim3(fft_threads(n, kTX)), smem, c.stream, X, ldx, ncols, n, logn, tw, S, lds,
-                 rs);
+                 rs, rn);
     })
   });
 }
@@ -475,10 +525,11 @@ void launch_fft_r2c(Ctx &c, const Tin *X, int64_t ldx, int64_t ncols, int n, con
 template <typename T>
 void launch_fft_r2c_residual(Ctx &c, const double *G, const double *U, int64_t ncols, int n, const double *rxl,
                              const double *rxd, const double *rxu, const cpx<T> *tw, cpx<T> *S, int64_t lds,
-                             const T *rs, const int *mex, int mnx) {
+                             const T *rs, const int *mex, int mnx, const RhsNorm *rnp) {
+  const RhsNorm rn = rnp ? *rnp : RhsNorm{nullptr, nullptr, nullptr};
   const int logn = ilog2(n);
   const int TX = pick_tx<T>(n, sizeof(T) == 8 ? 8 : 16, ncols, c.fft_cols);
-  const size_t smem = (size_t)(TX / 2) * n * sizeof(cpx<T>);
+  const size_t smem = (size_t)(TX / 2) * series_stride(n) * sizeof(cpx<T>);
   const int grid = (int)((ncols + TX - 1) / TX);
   const double bytes = (double)n * ncols * 16.0 + (double)(n / 2 + 1) * ncols * sizeof(cpx<T>);
   c.launch(sizeof(T) == 8 ? "fft_r2c_res_f64" : "fft_r2c_res_f32", bytes, [&] {
@@ -486,8 +537,7 @@ void launch_fft_r2c_residual(Ctx &c, const double *G, const double *U, int64_t n
       if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_fft_r2c_res<T, kTX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       pdl_launch(c.pdl, k_fft_r2c_res<T, kTX>, dim3(grid), dim3(fft_threads(n, kTX)), smem, c.stream, G, U, ncols, n, logn, rxl, rxd, rxu,
-                 tw, S, lds, rs, mex,
-                                                           mnx);
+                 tw, S, lds, rs, mex, mnx, rn);
     })
   });
 }
@@ -500,7 +550,7 @@ void launch_fft_c2r(Ctx &c, const cpx<T> *S, int64_t lds, int64_t ncols, int n, 
   if (finp && norm_part) fin = *finp;
   const int logn = ilog2(n);
   const int TX = pick_tx<T>(n, sizeof(T) == 8 ? 8 : 16, ncols, c.fft_cols);
-  const size_t smem = (size_t)(TX / 2) * n * sizeof(cpx<T>);
+  const size_t smem = (size_t)(TX / 2) * series_stride(n) * sizeof(cpx<T>);
   const int grid = (int)((ncols + TX - 1) / TX);
   if (nparts) *nparts = grid;
   const double obytes = (mode == 2) ? 4.0 : (mode == 1 ? 16.0 : 8.0);
@@ -522,7 +572,7 @@ void launch_dst_y(Ctx &c, const Tin *X, Tout *Y, int64_t nt, int64_t ny, int64_t
   const int N = (int)(2 * (ny + 1));
   const int logN = ilog2(N);
   const int TX = pick_tx<T>(N, sizeof(T) == 8 ? 8 : 16, nt * nx);
-  const size_t smem = (size_t)(TX / 2) * N * sizeof(cpx<T>);
+  const size_t smem = (size_t)(TX / 2) * series_stride(N) * sizeof(cpx<T>);
   const int ntile = (int)((nx + TX - 1) / TX);
   const int64_t grid = nt * ntile;
   const T scale = (T)sqrt(2.0 / (double)(ny + 1));
@@ -538,11 +588,11 @@ void launch_dst_y(Ctx &c, const Tin *X, Tout *Y, int64_t nt, int64_t ny, int64_t
 }
 
 template void launch_fft_r2c<double, double>(Ctx &, const double *, int64_t, int64_t, int, const cpx<double> *,
-                                             cpx<double> *, int64_t, const double *);
+                                             cpx<double> *, int64_t, const double *, const RhsNorm *);
 template void launch_fft_r2c<float, double>(Ctx &, const double *, int64_t, int64_t, int, const cpx<float> *,
-                                            cpx<float> *, int64_t, const float *);
+                                            cpx<float> *, int64_t, const float *, const RhsNorm *);
 template void launch_fft_r2c<float, float>(Ctx &, const float *, int64_t, int64_t, int, const cpx<float> *,
-                                           cpx<float> *, int64_t, const float *);
+                                           cpx<float> *, int64_t, const float *, const RhsNorm *);
 template void launch_fft_c2r<double>(Ctx &, const cpx<double> *, int64_t, int64_t, int, const cpx<double> *,
                                      void *, int64_t, int, double *, int *, const StepFinish *, const double *,
                                      double *, const int *, int);
@@ -551,10 +601,10 @@ template void launch_fft_c2r<float>(Ctx &, const cpx<float> *, int64_t, int64_t,
                                     double *, const int *, int);
 template void launch_fft_r2c_residual<double>(Ctx &, const double *, const double *, int64_t, int, const double *,
                                               const double *, const double *, const cpx<double> *, cpx<double> *,
-                                              int64_t, const double *, const int *, int);
+                                              int64_t, const double *, const int *, int, const RhsNorm *);
 template void launch_fft_r2c_residual<float>(Ctx &, const double *, const double *, int64_t, int, const double *,
                                              const double *, const double *, const cpx<float> *, cpx<float> *,
-                                             int64_t, const float *, const int *, int);
+                                             int64_t, const float *, const int *, int, const RhsNorm *);
 template void launch_dst_y<double, double, double>(Ctx &, const double *, double *, int64_t, int64_t, int64_t,
                                                    const cpx<double> *, int);
 template void launch_dst_y<double, float, float>(Ctx &, const double *, float *, int64_t, int64_t, int64_t,

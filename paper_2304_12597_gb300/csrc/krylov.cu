@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(MODE == kCoop ? kBlas : MODE == kCluster ? kBl
   const double *v = V + (int64_t)(m - 1) * n;
   double knorm, t;
   bool bd;
-  if constexpr (MODE == kCoop) {
+  if constexpr (MODE == kCoop && E == 0) {
     for (int j = g_first<MODE>(); j < n; j += g_stride<MODE>()) {
       double x = kdiag[j] * v[j];
       if (j > 0) x += klo[j] * v[j - 1];
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(MODE == kCoop ? kBlas : MODE == kCluster ? kBl
     }
   } else {  // w = K v_m held in registers through both CGS passes
     const int f = g_first<MODE>(), st = g_stride<MODE>();
-    double x[E];
+    double x[E > 0 ? E : 1];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int j = f + e * st;
@@ -106,16 +106,16 @@ __global__ void __launch_bounds__(MODE == kCoop ? kBlas : MODE == kCluster ? kBl
       x[e] = a;
     }
     const bool wr = (MODE == kSingle || blockIdx.x == 0) && (int)threadIdx.x < m;  // writes column m-1 of T
-    reg_dots<MODE, E>(n, m, V, n, x, pa, red, c);
+    reg_dots<MODE, E>(n, m, V, n, x, pa, ld, red, c);
     knorm = sqrt(c[m]);
     double tq = wr ? c[threadIdx.x] : 0.0;
     reg_axpy<MODE, E>(n, m, V, n, x, c);
     __syncthreads();  // c is rewritten next
-    reg_dots<MODE, E>(n, m, V, n, x, pb, red, c);
+    reg_dots<MODE, E>(n, m, V, n, x, pb, ld, red, c);
     if (wr) T[(int64_t)threadIdx.x * ldT + (m - 1)] = tq + c[threadIdx.x];
     reg_axpy<MODE, E>(n, m, V, n, x, c);
     __syncthreads();
-    t = sqrt(cgs2_norm2<MODE, E>(m, x, c, pc, red));
+    t = sqrt(cgs2_norm2<MODE, E>(m, x, c, pc, ld, red));
     bd = !(t > 1e-14 * knorm);
     const double it = bd ? 0.0 : 1.0 / t;
     double *vm = V + (int64_t)m * n;
@@ -255,21 +255,42 @@ __global__ void __launch_bounds__(kK5Warps * 32) k_capacitance_terms(
     const double t11 = tau * T[0];
     const int b0 = members ? (int)blockIdx.y : 0, b1 = flags[F_BREAK] ? b0 : (members ? b0 + 1 : nblk);
     double acc = 0.0;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nf; k += gridDim.x * blockDim.x) {
+    auto term = [&](int k, double gx, double gy) {
       const double2 sk = shift[k];
-      double gx = 0.0, gy = 0.0;
-      for (int b = b0; b < b1; ++b) {
-        const double2 v = gpart[(int64_t)k * nblk + b];
-        gx += v.x;
-        gy += v.y;
-      }
       const cpx<double> X1 = recip(mk<double>(t11 + sk.x, sk.y));
       const double2 w = wg[k];
       const cpx<double> wk = mk<double>(w.x, w.y);
       const cpx<double> ws = mul(wk, X1);
       srow[k] = make_double2(ws.x, ws.y);
       const cpx<double> gs = mul(mk<double>(gx, gy), X1);
-      acc += mul(wk, mk<double>(X1.x - tt * gs.x, X1.y - tt * gs.y)).x;
+      return mul(wk, mk<double>(X1.x - tt * gs.x, X1.y - tt * gs.y)).x;
+    };
+    if (b1 - b0 >= 32) {
+      // many blocks (2D: one per mode of T_y): a warp per frequency, its lanes split the
+      // blocks' partial dots, so the loads are in flight together rather than one after
+      // another along a chain of adds
+      const int gw = blockIdx.x * kK5Warps + wid, nw = gridDim.x * kK5Warps;
+      for (int k = gw; k < nf; k += nw) {
+        double gx = 0.0, gy = 0.0;
+        for (int b = b0 + lane; b < b1; b += 32) {
+          const double2 v = gpart[(int64_t)k * nblk + b];
+          gx += v.x;
+          gy += v.y;
+        }
+        gx = warp_sum(gx);
+        gy = warp_sum(gy);
+        if (lane == 0) acc += term(k, gx, gy);
+      }
+    } else {
+      for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nf; k += gridDim.x * blockDim.x) {
+        double gx = 0.0, gy = 0.0;
+        for (int b = b0; b < b1; ++b) {
+          const double2 v = gpart[(int64_t)k * nblk + b];
+          gx += v.x;
+          gy += v.y;
+        }
+        acc += term(k, gx, gy);
+      }
     }
     acc = warp_sum(acc);
     if (lane == 0) msw[0] = acc;
@@ -282,16 +303,32 @@ __global__ void __launch_bounds__(kK5Warps * 32) k_capacitance_terms(
         const double tq = (q <= lane + 1) ? T[(int64_t)q * maxit + lane] : 0.0;
         H[q * m + lane] = mk<double>(tau * tq + (q == lane ? sk.x : 0.0), q == lane ? sk.y : 0.0);
       }
-      double gx = 0.0, gy = 0.0;
-      // after a breakdown the dot pass was skipped and the t-term vanishes; a batch
-      // member takes only its own block's dots
-      const int b0 = members ? (int)blockIdx.y : 0, b1 = members ? b0 + 1 : nblk;
-      for (int b = b0; b < (flags[F_BREAK] ? b0 : b1); ++b) {
-        const double2 v = gpart[((int64_t)k * nblk + b) * m + lane];
-        gx += v.x;
-        gy += v.y;
+    }
+    {
+      // g_k = sum over blocks of the partial dots; after a breakdown the dot pass was
+      // skipped and the t-term vanishes; a batch member takes only its own block's dots
+      const int b0 = members ? (int)blockIdx.y : 0, b1 = flags[F_BREAK] ? b0 : (members ? b0 + 1 : nblk);
+      if (b1 - b0 >= 32) {  // many blocks: the lanes split them, one warp sum per dot
+        for (int q = 0; q < m; ++q) {
+          double gx = 0.0, gy = 0.0;
+          for (int b = b0 + lane; b < b1; b += 32) {
+            const double2 v = gpart[((int64_t)k * nblk + b) * m + q];
+            gx += v.x;
+            gy += v.y;
+          }
+          gx = warp_sum(gx);
+          gy = warp_sum(gy);
+          if (lane == 0) gq[q] = mk<double>(gx, gy);
+        }
+      } else if (lane < m) {
+        double gx = 0.0, gy = 0.0;
+        for (int b = b0; b < b1; ++b) {
+          const double2 v = gpart[((int64_t)k * nblk + b) * m + lane];
+          gx += v.x;
+          gy += v.y;
+        }
+        gq[lane] = mk<double>(gx, gy);
       }
-      gq[lane] = mk<double>(gx, gy);
     }
     __syncwarp();
     warp_gj_inverse(H, X, fcol, m);
@@ -475,6 +512,14 @@ int krylov_cluster_size(int want) {
   return 0;
 }
 
+// Cooperative grids: entries per thread held in registers (0 = stream from memory when the
+// grid's registers cannot hold the vector).
+static int coop_elems(int n, int grid) {
+  const int64_t threads = (int64_t)grid * kBlas;
+  return (int64_t)n > threads * kEMax ? 0 : reg_elems(n, (int)threads);
+}
+#define PD_COOP_E(E, KERNEL) ((E) == 0 ? (const void *)KERNEL<kCoop, 0> : PD_BY_E(E, KERNEL, kCoop))
+
 #define PD_BY_E(E, KERNEL, MODE)                                                              \
   ((E) <= 1 ? (const void *)KERNEL<MODE, 1>                                                  \
             : (E) == 2 ? (const void *)KERNEL<MODE, 2>                                       \
@@ -546,7 +591,8 @@ void launch_vec_norm_init(Ctx &c, KrylovBufs &k, const double *b, int use_handle
   int nT = (k.maxit + 1) * k.maxit;
   void *args[] = {(void *)&b, &n, &part, (void *)&ld, &V, &Vf, &scal, &flags, &use_handle, &h, &T, &nT};
   coop_launch(c, "krylov_init", (double)k.n * 16, PD_BY_E(reg_elems(k.n, kBlasSingle), k_init_v0_coop, kSingle),
-              (const void *)k_init_v0_coop<kCoop, 1>, PD_BY_E(reg_elems(k.n, k.cluster * kBlasCluster), k_init_v0_coop, kCluster),
+              PD_COOP_E(coop_elems(k.n, k.grid), k_init_v0_coop),
+              PD_BY_E(reg_elems(k.n, k.cluster * kBlasCluster), k_init_v0_coop, kCluster),
               k.grid, k.cluster, args);
 }
 
@@ -562,7 +608,8 @@ void launch_arnoldi(Ctx &c, KrylovBufs &k) {
   void *args[] = {&n, (void *)&klo, (void *)&kdiag, (void *)&kup, &V, &Vf, &w, &T, &ldT, &part, (void *)&ld,
                   &scal, &flags, &q, &maxit};
   coop_launch(c, "krylov_arnoldi", (double)k.n * 8.0 * 8, PD_BY_E(reg_elems(k.n, kBlasSingle), k_arnoldi_coop, kSingle),
-              (const void *)k_arnoldi_coop<kCoop, 1>, PD_BY_E(reg_elems(k.n, k.cluster * kBlasCluster), k_arnoldi_coop, kCluster),
+              PD_COOP_E(coop_elems(k.n, k.grid), k_arnoldi_coop),
+              PD_BY_E(reg_elems(k.n, k.cluster * kBlasCluster), k_arnoldi_coop, kCluster),
               k.grid, k.cluster, args);
 }
 
@@ -590,7 +637,8 @@ void launch_project_resnorm(Ctx &c, KrylovBufs &k, const double *z, double tau, 
   KrylovCtl kc = kc0;
   void *args[] = {&n, (void *)&V, &zz, &tau, &part, (void *)&ld, &scal, &flags, &kc, &use_handle, &h};
   coop_launch(c, "krylov_project", (double)k.n * 8.0 * 6, PD_BY_E(reg_elems(k.n, kBlasSingle), k_project_coop, kSingle),
-              (const void *)k_project_coop<kCoop, 1>, PD_BY_E(reg_elems(k.n, k.cluster * kBlasCluster), k_project_coop, kCluster),
+              PD_COOP_E(coop_elems(k.n, k.grid), k_project_coop),
+              PD_BY_E(reg_elems(k.n, k.cluster * kBlasCluster), k_project_coop, kCluster),
               k.grid, k.cluster, args);
 }
 

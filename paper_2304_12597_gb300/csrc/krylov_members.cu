@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(kBlasSingle) k_member_init(KrylovBufs k, const
   for (int i = threadIdx.x; i <= k.maxit; i += blockDim.x) mv.y[i] = 0.0;
   double x[E];
   reg_load<kSingle, E>(len, b + mv.off, x);
-  const double beta = sqrt(reg_norm2<kSingle, E>(x, nullptr, red, c));
+  const double beta = sqrt(reg_norm2<kSingle, E>(x, nullptr, 0, red, c));
   const double ib = beta > 0.0 ? 1.0 / beta : 0.0;
 #pragma unroll
   for (int e = 0; e < E; ++e) {
@@ -162,16 +162,16 @@ __global__ void __launch_bounds__(kBlasSingle) k_member_arnoldi(KrylovBufs k) {
     x[e] = a;
   }
   const bool wr = (int)threadIdx.x < m;  // writes column m-1 of T
-  reg_dots<kSingle, E>(len, m, Vb, ldv, x, nullptr, red, c);
+  reg_dots<kSingle, E>(len, m, Vb, ldv, x, nullptr, 0, red, c);
   const double knorm = sqrt(c[m]);
   const double tq = wr ? c[threadIdx.x] : 0.0;
   reg_axpy<kSingle, E>(len, m, Vb, ldv, x, c);
   __syncthreads();  // c is rewritten next
-  reg_dots<kSingle, E>(len, m, Vb, ldv, x, nullptr, red, c);
+  reg_dots<kSingle, E>(len, m, Vb, ldv, x, nullptr, 0, red, c);
   if (wr) mv.T[(int64_t)threadIdx.x * ldT + (m - 1)] = tq + c[threadIdx.x];
   reg_axpy<kSingle, E>(len, m, Vb, ldv, x, c);
   __syncthreads();
-  const double t = sqrt(cgs2_norm2<kSingle, E>(m, x, c, nullptr, red));
+  const double t = sqrt(cgs2_norm2<kSingle, E>(m, x, c, nullptr, 0, red));
   const bool bd = !(t > 1e-14 * knorm);
   const double it = bd ? 0.0 : 1.0 / t;
 #pragma unroll
@@ -209,13 +209,13 @@ __global__ void __launch_bounds__(kBlasSingle) k_member_project(KrylovBufs k, co
     const double *Vb = k.V + mv.off;
     double x[E];
     reg_load<kSingle, E>(len, z + mv.off, x);
-    reg_dots<kSingle, E>(len, m, Vb, ldv, x, nullptr, red, c);
+    reg_dots<kSingle, E>(len, m, Vb, ldv, x, nullptr, 0, red, c);
     reg_axpy<kSingle, E>(len, m, Vb, ldv, x, c);
     __syncthreads();  // c is rewritten next
-    reg_dots<kSingle, E>(len, m, Vb, ldv, x, nullptr, red, c);
+    reg_dots<kSingle, E>(len, m, Vb, ldv, x, nullptr, 0, red, c);
     reg_axpy<kSingle, E>(len, m, Vb, ldv, x, c);
     __syncthreads();
-    const double zz = cgs2_norm2<kSingle, E>(m, x, c, nullptr, red);
+    const double zz = cgs2_norm2<kSingle, E>(m, x, c, nullptr, 0, red);
     if (threadIdx.x == 0) {
       mv.scal[S_RES] = mv.flags[F_BREAK] ? 0.0 : fabs(tau * mv.scal[S_T]) * sqrt(zz);
       krylov_decide(mv.scal, mv.flags, kc, 0, h);

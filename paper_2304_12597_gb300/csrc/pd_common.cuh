@@ -43,19 +43,22 @@ template <typename T>
 __device__ __forceinline__ cpx<T> fnms_r(cpx<T> a, T s, cpx<T> c) { return mk<T>(a.x - s * c.x, a.y - s * c.y); }
 // 1 / a  =  conj(a) / |a|^2.  The operands met here are bounded away from zero and
 // from overflow (|a| between ~1e-3 and ~1e8), so no Smith-style scaling is needed.
-// binary32: the hardware approximation refined by one Newton-Raphson step,
-// r + r (1 - v r), which brings it to within rounding of 1/v for the normal-range
-// operands met here without the range checks of a correctly rounded reciprocal;
-// binary64: correctly rounded.
-__device__ __forceinline__ float rcp_rn(float v) {
+// binary32: the hardware approximation (rcp.approx.ftz, at most 1 ulp from 1/v) refined
+// by one Newton-Raphson step, r + r (1 - v r).  The step roughly squares the relative
+// error of the approximation and adds the rounding of two fused operations, so the
+// result is within 1 ulp of 1/v but NOT always correctly rounded; .ftz flushes
+// subnormal operands and results to zero, which normal-range operands never produce.
+// paradiag_recip_f32 exposes this function so that a test can bound its error against
+// the correctly rounded reciprocal.  binary64: __drcp_rn, correctly rounded.
+__device__ __forceinline__ float rcp_nr(float v) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
   return fmaf(r, fmaf(-v, r, 1.0f), r);
 }
-__device__ __forceinline__ double rcp_rn(double v) { return __drcp_rn(v); }
+__device__ __forceinline__ double rcp_nr(double v) { return __drcp_rn(v); }
 template <typename T>
 __device__ __forceinline__ cpx<T> recip(cpx<T> a) {
-  const T d = rcp_rn(a.x * a.x + a.y * a.y);  // correctly rounded reciprocal
+  const T d = rcp_nr(a.x * a.x + a.y * a.y);  // 1 / |a|^2 (within 1 ulp in binary32)
   return mk<T>(a.x * d, -a.y * d);
 }
 template <typename T>

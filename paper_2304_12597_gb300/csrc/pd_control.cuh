@@ -10,8 +10,16 @@
 namespace pd {
 
 // After an Algorithm-2 step (Sec. 3): record ||r_m||, decide whether to continue:
-// stop at ||r_m|| <= eps beta, at maxit, at a breakdown, or at a stall near the
-// precision floor (no halving over `win` checks once ||r_m|| <= stall_floor beta).
+// stop at ||r_m|| <= eps ref, at maxit, at a breakdown, or at a stall near the
+// precision floor (no halving over `win` checks once ||r_m|| <= stall_floor ref).
+// ref = beta = ||b|| as in the paper; plans that refine (k.rrel) use ||R||_F, the norm of
+// the solve's right-hand side (G, or the residual a refinement sweep corrects): the
+// residual of eq. (2) a solve leaves behind is exactly -r_m in the first time step, so
+// a sweep contracts by about ||r_m|| / ||R||.  Measured against beta this can fail both
+// ways: for damped problems ||b|| (~ the final state) << ||R|| and the steps past
+// eps ||R|| buy nothing; when J_l is ill-conditioned (Theorem 3.1: kappa up to
+// 1 + 1/(tau lambda_min)) b lies along its large eigenvalues, ||b|| >> ||R||, and eps beta
+// would leave ||r_m|| as large as the sweep's input.
 // A frozen step (q > 1, flags[F_FROZEN]) has no residual: it only advances m.
 __device__ __forceinline__ void krylov_decide(double *scal, int *flags, const KrylovCtl &k, int use_handle,
                                               cudaGraphConditionalHandle h) {
@@ -24,13 +32,15 @@ __device__ __forceinline__ void krylov_decide(double *scal, int *flags, const Kr
     return;
   }
   const double res = scal[S_RES], beta = scal[S_BETA];
+  const double rn = scal[S_RNORM];
+  const double ref = (k.rrel && rn > 0.0) ? rn : beta;
   if (m < 33) scal[S_HIST + m] = res;
   const bool nonfinite = flags[F_NONFIN] || !isfinite(res);
   if (nonfinite) flags[F_NONFIN] = 1;
-  const bool conv = flags[F_BREAK] || res <= k.eps * beta;
+  const bool conv = flags[F_BREAK] || res <= k.eps * ref;
   // checks are q steps apart (the last one may be closer: maxit or a breakdown)
   const int back = k.win * (k.q > 1 ? k.q : 1);
-  const bool stall = m >= back + 1 && m % (k.q > 1 ? k.q : 1) == 0 && res <= k.stall_floor * beta &&
+  const bool stall = m >= back + 1 && m % (k.q > 1 ? k.q : 1) == 0 && res <= k.stall_floor * ref &&
                      res > 0.5 * scal[S_HIST + m - back];
   const bool stop = nonfinite || conv || stall || m >= k.maxit;
   flags[F_M] = m;
@@ -71,10 +81,14 @@ __device__ __forceinline__ void refine_decide(double *scal, int *flags, const Re
     if (r.fp64 && flags[F_KCONV] && (s == 0 ? eps <= 1e-10 : eps * rel <= r.refine_tol)) conv = stop = true;
     // Refinement contracts the error by rho ~ ||delta_s|| / ||delta_{s-1}|| (s >= 2:
     // delta_1 / delta_0 is the first solve's error, not a contraction), so about
-    // rho * ||delta_s|| remains after sweep s.
+    // rho * ||delta_s|| remains after sweep s.  The contraction varies from sweep to sweep
+    // (each sweep's Algorithm 2 stops at a different point), so the prediction takes the
+    // larger of the last two ratios where there are two.
     if (!stop && s > 0) {
       const double rho = prev > 0.0 ? rel / prev : 0.0;
-      if ((s >= 2 && rho * rel <= r.refine_tol && rel <= 1e-7) || rel <= 1e-15) {
+      const double pp = (s >= 3 && s < 16) ? scal[S_SWUPD + s - 2] : 0.0;
+      const double rho_pred = pp > 0.0 ? fmax(rho, prev / pp) : rho;
+      if ((s >= 2 && rho_pred * rel <= r.refine_tol && rel <= 1e-7) || rel <= 1e-15) {
         conv = stop = true;
       } else if (s > 1 && rho > 0.5) {  // no longer contracting: rounding floor reached
         conv = rel <= 1e-10;

@@ -31,11 +31,15 @@ enum FlagIndex {
   F_ACCCNT = 12,  // completion counter of the b reduction (runs the start of Algorithm 2)
   F_ZCNT = 13,    // completion counter of the z reduction (runs eq. 13 and the decision)
   F_MEMCNT = 14,  // batched plans: members done in a per-member Algorithm-2 step
+  F_RNCNT = 15,   // completion counter of the forward DFT's right-hand-side norm
   F_SWM = 16,     // [16, 32): m of each solve
   F_FROZEN = 32,  // this Algorithm-2 step skips the residual check (q > 1, Sec. 3)
   F_NOH = 33,     // this step forms no h_k: breakdown or a frozen step
   kFlagWords = 64
 };
+// CTA size of the cooperative Krylov vector kernels (pd_krylov.cuh, kCoop mode).
+constexpr int kBlas = 512;
+
 enum ScalIndex {
   S_BETA = 0,     // ||b|| of the current solve
   S_T = 1,        // t_{m+1,m}
@@ -45,6 +49,7 @@ enum ScalIndex {
   S_REF2 = 5,     // ||delta_0||_F^2
   S_PREV = 6,     // previous relative update
   S_UPD = 7,      // last relative update
+  S_RNORM = 8,    // ||R||_F of the current solve's right-hand side (G, or the residual)
   S_HIST = 16,    // [16, 49): ||r_m|| history of the current solve
   S_SWRES = 64,   // [64, 80): eq. (13) residual / ||b|| at exit of each solve
   S_SWUPD = 80,   // [80, 96): ||delta_s|| / ||delta_0|| of each solve
@@ -113,8 +118,10 @@ void set_last_error(const char *msg);
 
 // Device-side control of Algorithm 2 and of the refinement loop (control.cu).
 struct KrylovCtl {
-  double eps;          // stop when ||r_m|| <= eps * beta
-  double stall_floor;  // stall exit only once ||r_m|| <= stall_floor * beta
+  double eps;          // stop when ||r_m|| <= eps * ref, ref = beta (or ||R||_F with rrel)
+  double stall_floor;  // stall exit only once ||r_m|| <= stall_floor * ref
+  int rrel;            // 1: ref = ||R||_F of the solve's right-hand side (refining plans;
+                       // see krylov_decide)
   int win;             // stall: no halving over `win` checks
   int maxit;
   int q;               // residual check every q steps (and at maxit or a breakdown)
@@ -129,9 +136,16 @@ struct RefineCtl {
 // Forward DFT along time of real (n, ncols) rows -> half spectrum (n/2+1, ncols).
 // rs (may be null): row j of X is multiplied by rs[j] on load (the D_alpha of
 // Algorithm 3); rsi in the inverse: output row j multiplied by rsi[j].
+// rn (optional): ||X||_F (or ||R||_F) of the transformed data, reduced over the CTAs by
+// the last one to finish into *rn.dst (before the D_alpha scaling).
+struct RhsNorm {
+  double *part;  // one partial sum of squares per CTA
+  int *counter;  // zero on entry; reset by the last CTA
+  double *dst;
+};
 template <typename T, typename Tin>
 void launch_fft_r2c(Ctx &c, const Tin *X, int64_t ldx, int64_t ncols, int n, const cpx<T> *tw,
-                    cpx<T> *S, int64_t lds, const T *rs = nullptr);
+                    cpx<T> *S, int64_t lds, const T *rs = nullptr, const RhsNorm *rn = nullptr);
 // Forward DFT along time of the FP64 all-at-once residual
 // R = G - [(I + tau K) U - U Sigma_1^T] (1D), computed on load: R is never stored.
 // mex/mnx (batched plans): column c is scaled by 2^mex[c / mnx], undone by the inverse.
@@ -139,7 +153,7 @@ template <typename T>
 void launch_fft_r2c_residual(Ctx &c, const double *G, const double *U, int64_t ncols, int n,
                              const double *rxl, const double *rxd, const double *rxu, const cpx<T> *tw,
                              cpx<T> *S, int64_t lds, const T *rs = nullptr, const int *mex = nullptr,
-                             int mnx = 1);
+                             int mnx = 1, const RhsNorm *rn = nullptr);
 // Optional epilogue of the inverse DFT: the last CTA to finish sums the per-CTA
 // squares into scal[S_D2] and runs the refinement decision.
 struct StepFinish {
@@ -215,18 +229,36 @@ struct PintArgs {
   int64_t xm_ldy;          // block blk takes y_m from xm_y + blk * xm_ldy (0: one y_m)
   const cpx<T> *fac_in;    // precomputed factors of every (k, block) system (pint.cu), or null
   cpx<T> *fac_out;         // factor pass: store those factors (R, rvec, Y, omega, V unused)
+  // Zero-frequency lane of the binary32 path.  A_0 = (1 - pi_0) I + tau K has the real
+  // shift 1 - alpha^{1/l} (0 for Algorithm 1) and is the only ill-conditioned shifted
+  // system (|1 - pi_k| >= 2 sin(pi / l) for k >= 1); its inverse (norm up to
+  // 1 / (tau lambda_min(K))) dominates b (eq. 7) and J_l (eq. 8).  With k0_fp64 the team
+  // owning k = 0 solves it in FP64 from FP64 coefficients (tlo_d, ...), takes v_{m+1} and
+  // x_m from the FP64 basis Vd, and writes its FP64 share of b into acc0 (added by the
+  // reduction), h_0 into h0 (added by the z sum) and its dots g_0 in FP64.
+  int k0_fp64;
+  const double *tlo_d, *tdiag_d, *tup_d;
+  const double *Vd;
+  double *acc0;            // (nblk * blen) omega_0 y_0 of the acc pass, or null
+  double *h0;              // (nblk * blen) h_0 of the dots pass, or null
+  const double *fac0_in;   // the lane's stored FP64 factors (pint_k0_factor_elems), or null
+  double *fac0_out;        // factor pass of the lane: store them (frequency 0 only)
 };
+// Doubles of the zero-frequency lane's factors (one real system per block).
+size_t pint_k0_factor_elems(const PintGeom &g);
 // Complex elements of the factor array of one plan geometry (pint.cu: fac_slots).
 size_t pint_factor_elems(const PintGeom &g);
 template <typename T>
 void launch_pint(Ctx &c, const PintGeom &g, const PintArgs<T> &a);
+void launch_recip_f32(cudaStream_t s, const float *x, float *r, int64_t n);
 struct InitTail;  // pd_krylov.cuh: the start of Algorithm 2 run by a reduction's last CTA
 struct ProjTail;  // pd_krylov.cuh: eq. 13 and the step decision run by the z reduction's last CTA
 // z[j] = sum_k Re(omega_k H[k][j]) over stored h_k (nf rows, leading dimension ldh);
 // with tail, the last CTA then projects z and decides the Algorithm-2 step.
+// h0 (or null): the FP64 h_0 of the zero-frequency lane, which replaces row 0 of H.
 template <typename T>
 void launch_zsum(Ctx &c, int nf, int64_t n, const cpx<T> *H, int64_t ldh, const double2 *omega, double *z,
-                 const int *skip_flag, const ProjTail *tail = nullptr, int mlen = 0);
+                 const int *skip_flag, const ProjTail *tail = nullptr, int mlen = 0, const double *h0 = nullptr);
 // Batched plans (batch.cu): Gs = G with slot b scaled by 2^ex[b] ~ 1/||slot b||_F
 // (part: batch * nc doubles of scratch), and the inverse scaling of U in place with
 // the columns past problem b's nxb[b] rows set to zero.
@@ -241,10 +273,10 @@ void launch_member_decide(Ctx &c, const double *colsum, int nxm, const int *nxb,
                           double *prev, int *mex, double *scal, int *flags, const RefineCtl &r, int use_handle,
                           cudaGraphConditionalHandle h);
 
-// out[j] = sum_r acc_part[(blk*R + r)*blen + e], j = blk*blen + e; with tail, the last
-// CTA then computes beta = ||out|| and v_1 (the start of Algorithm 2).
+// out[j] = sum_r acc_part[(blk*R + r)*blen + e] (+ extra[j]), j = blk*blen + e; with tail,
+// the last CTA then computes beta = ||out|| and v_1 (the start of Algorithm 2).
 void launch_acc_reduce(Ctx &c, const PintGeom &g, const double *acc_part, double *out, const int *skip_flag,
-                       const InitTail *tail = nullptr);
+                       const InitTail *tail = nullptr, const double *extra = nullptr);
 
 // ---- Krylov / small systems / residual (krylov.cu) -----------------------------------
 struct KrylovBufs {

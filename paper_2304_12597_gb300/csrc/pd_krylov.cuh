@@ -4,8 +4,10 @@
 // decision).  Internal header, included by the Krylov kernels and by the kernels
 // that run those bodies in their last CTA.
 //
-// MODE kCoop: the vectors are spread over a cooperative grid, partial sums meet in a
-// global panel after a grid barrier.  kCluster: they are spread over one thread-block
+// MODE kCoop: the vectors are spread over a cooperative grid of kBlas-thread CTAs (at
+// most one per SM), partial sums meet in a global panel after a grid barrier; with E >= 1
+// each thread holds its E entries in registers through a step (as in the cluster mode),
+// with E = 0 (vectors longer than the grid's registers hold) they stream from memory.  kCluster: they are spread over one thread-block
 // cluster (the whole grid), each CTA keeps its partial sums in shared memory and the
 // others read them through distributed shared memory after a cluster barrier, so the
 // FP64 work of a vector step runs on several SMs without grid-wide barriers.
@@ -22,7 +24,6 @@
 
 namespace pd {
 
-constexpr int kBlas = 64;          // CTA size of the cooperative variants
 constexpr int kBlasSingle = 512;   // threads of the one-CTA variants (short vectors)
 constexpr int kBlasCluster = 128;  // threads per CTA of the cluster variants
 constexpr int kRedQ = 4;           // sums reduced side by side
@@ -96,12 +97,16 @@ __device__ __forceinline__ void cta_dots(int n, int m, const double *__restrict_
   }
 }
 
-// c[q] = sum_cta panel[cta][q], q <= m (threads 0..m), then a CTA barrier.
+// c[q] = sum_cta panel[cta][q], q <= m, then a CTA barrier.  Warp w sums column q = w
+// (w + warps, ...): its lanes load the CTAs' partials side by side and a fixed-order warp
+// sum adds them, so the panel is read in one round trip rather than one per partial.
 __device__ __forceinline__ void cta_gather(const double *panel, int ld, int nparts, int m, double *c) {
-  if ((int)threadIdx.x <= m) {
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int q = threadIdx.x >> 5; q <= m; q += nw) {
     double s = 0.0;
-    for (int i = 0; i < nparts; ++i) s += panel[i * ld + threadIdx.x];
-    c[threadIdx.x] = s;
+    for (int i = lane; i < nparts; i += 32) s += panel[i * ld + q];
+    s = warp_sum(s);
+    if (lane == 0) c[q] = s;
   }
   __syncthreads();
 }
@@ -203,13 +208,15 @@ __device__ __forceinline__ void reg_load(int n, const double *__restrict__ x, do
 
 // c[q] = V[q] . x over the grid (q < m), c[m] = ||x||^2 (shared c, valid in every
 // thread on return); cluster mode combines the CTAs' sums through the shared `slot`.
+// slot: cluster mode, this CTA's shared slot; cooperative mode, the global panel whose row
+// blockIdx.x (leading dimension ld) receives this CTA's partials.
 template <int MODE, int E>
 __device__ __forceinline__ void reg_dots(int n, int m, const double *V, int64_t ldv, const double (&x)[E], double *slot,
-                                         double *red, double *c) {
-  static_assert(MODE == kSingle || MODE == kCluster, "register-resident steps run in one CTA or one cluster");
+                                         int ld, double *red, double *c) {
+  static_assert(MODE == kSingle || MODE == kCluster || MODE == kCoop, "register-resident steps");
   __shared__ double out[kRedQ];
   const int f = g_first<MODE>(), st = g_stride<MODE>();
-  double *dst = MODE == kCluster ? slot : c;
+  double *dst = MODE == kCluster ? slot : MODE == kCoop ? slot + (size_t)blockIdx.x * ld : c;
   for (int q0 = 0; q0 <= m; q0 += kRedQ) {
     const int nq = min(kRedQ, m + 1 - q0);
     double s[kRedQ];
@@ -231,6 +238,9 @@ __device__ __forceinline__ void reg_dots(int n, int m, const double *V, int64_t 
   }
   if constexpr (MODE == kCluster) {
     cluster_gather(slot, m + 1, c);
+  } else if constexpr (MODE == kCoop) {
+    cooperative_groups::this_grid().sync();
+    cta_gather(slot, ld, gridDim.x, m, c);
   } else {
     __syncthreads();
   }
@@ -252,11 +262,11 @@ __device__ __forceinline__ void reg_axpy(int n, int m, const double *V, int64_t 
 }
 
 template <int MODE, int E>
-__device__ __forceinline__ double reg_norm2(const double (&x)[E], double *slot, double *red, double *c) {
+__device__ __forceinline__ double reg_norm2(const double (&x)[E], double *slot, int ld, double *red, double *c) {
   double s = 0.0;
 #pragma unroll
   for (int e = 0; e < E; ++e) s += x[e] * x[e];  // entries past n are zero
-  return grid_sum<MODE>(s, slot, 0, red, c);
+  return grid_sum<MODE>(s, slot, ld, red, c);
 }
 
 // ||x2||^2 after the second Gram-Schmidt pass x2 = x1 - V c, from that pass's dots
@@ -265,12 +275,13 @@ __device__ __forceinline__ double reg_norm2(const double (&x)[E], double *slot, 
 // the difference keeps its digits; if it removed more than 1e-4 of ||x1||^2 the explicit
 // reduction runs instead (every thread and CTA holds the same c: a uniform branch).
 template <int MODE, int E>
-__device__ __forceinline__ double cgs2_norm2(int m, const double (&x)[E], double *c, double *slot, double *red) {
+__device__ __forceinline__ double cgs2_norm2(int m, const double (&x)[E], double *c, double *slot, int ld,
+                                             double *red) {
   double r = 0.0;
   for (int q = 0; q < m; ++q) r += c[q] * c[q];
   const double a = c[m];
   if (r <= 1e-4 * a) return a - r;
-  return reg_norm2<MODE, E>(x, slot, red, c);
+  return reg_norm2<MODE, E>(x, slot, ld, red, c);
 }
 
 // Algorithm 2, first step: beta = ||b||, V[0] = b / beta (and its binary32 copy), T_m
@@ -285,7 +296,7 @@ __device__ __forceinline__ void init_v0_body(const double *__restrict__ b, int n
   __shared__ double cslot[MODE == kCluster ? kSlot : 1];
   for (int i = g_first<MODE>(); i < nT; i += g_stride<MODE>()) T[i] = 0.0;
   double beta;
-  if constexpr (MODE == kCoop || MODE == kTail) {
+  if constexpr ((MODE == kCoop && E == 0) || MODE == kTail) {
     double s = 0.0;
     for (int j = g_first<MODE>(); j < n; j += g_stride<MODE>()) s += b[j] * b[j];
     beta = sqrt(grid_sum<MODE>(s, part, ld, red, c));
@@ -295,9 +306,9 @@ __device__ __forceinline__ void init_v0_body(const double *__restrict__ b, int n
       if (Vf) Vf[j] = (float)V[j];
     }
   } else {
-    double x[E];
+    double x[E > 0 ? E : 1];
     reg_load<MODE, E>(n, b, x);
-    beta = sqrt(reg_norm2<MODE, E>(x, cslot, red, c));
+    beta = sqrt(reg_norm2<MODE, E>(x, MODE == kCoop ? part : cslot, ld, red, c));
     const double ib = beta > 0.0 ? 1.0 / beta : 0.0;
     const int f = g_first<MODE>(), st = g_stride<MODE>();
 #pragma unroll
@@ -354,7 +365,7 @@ __device__ __forceinline__ void project_body(int n, const double *__restrict__ V
   // a frozen step (q > 1) forms no z: the decision only advances m (uniform over the grid)
   const bool frozen = flags[F_FROZEN] != 0;
   if (frozen) {
-  } else if constexpr (MODE == kCoop || MODE == kTail) {
+  } else if constexpr ((MODE == kCoop && E == 0) || MODE == kTail) {
     grid_dots<MODE>(n, m, V, z, pa, ld, red, c);
     cta_axpy<MODE>(n, m, V, z, c);
     __syncthreads();  // c is rewritten next
@@ -365,15 +376,15 @@ __device__ __forceinline__ void project_body(int n, const double *__restrict__ V
     for (int j = g_first<MODE>(); j < n; j += g_stride<MODE>()) s += z[j] * z[j];
     zz = grid_sum<MODE>(s, pc, ld, red, c);
   } else {  // z projected in registers (z itself is left as it is)
-    double x[E];
+    double x[E > 0 ? E : 1];
     reg_load<MODE, E>(n, z, x);
-    reg_dots<MODE, E>(n, m, V, n, x, pa, red, c);
+    reg_dots<MODE, E>(n, m, V, n, x, pa, ld, red, c);
     reg_axpy<MODE, E>(n, m, V, n, x, c);
     __syncthreads();  // c is rewritten next
-    reg_dots<MODE, E>(n, m, V, n, x, pb, red, c);
+    reg_dots<MODE, E>(n, m, V, n, x, pb, ld, red, c);
     reg_axpy<MODE, E>(n, m, V, n, x, c);
     __syncthreads();
-    zz = cgs2_norm2<MODE, E>(m, x, c, pc, red);
+    zz = cgs2_norm2<MODE, E>(m, x, c, pc, ld, red);
   }
   if (g_leader<MODE>()) {
     if (!frozen) scal[S_RES] = flags[F_BREAK] ? 0.0 : fabs(tau * scal[S_T]) * sqrt(zz);

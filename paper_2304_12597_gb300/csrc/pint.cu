@@ -85,6 +85,7 @@ __host__ __device__ inline int fac_slots(int M, int P) { return 4 * M - 4 + 2 * 
 size_t pint_factor_elems(const PintGeom &g) {
   return (size_t)g.nf * g.nblk * fac_slots(g.M, g.P) * g.P;
 }
+size_t pint_k0_factor_elems(const PintGeom &g) { return (size_t)g.nblk * fac_slots(g.M, g.P) * g.P; }
 
 template <typename T>
 __device__ __forceinline__ void coef(const PintArgs<T> &a, const T *cs, int cs_stride, int64_t j, int ps, bool valid,
@@ -106,6 +107,246 @@ __device__ __forceinline__ void coef(const PintArgs<T> &a, const T *cs, int cs_s
   }
 }
 
+// Zero-frequency lane of the binary32 path (PintArgs::k0_fp64): the team's block of
+// (s_0 I + tau K) y = r in FP64, with the real shift s_0 = 1 - pi_0 = 1 - alpha^{1/l} and
+// real data (the zero frequency of real time series is real).  Same partitioned Thomas +
+// PCR as the complex solve below, in real FP64 arithmetic, reusing the team's shared
+// memory: a double takes the bytes of a cpx<float>.  Its factors depend on K only, so a
+// factor pass (fac0_out) stores them once per operator in the slot layout of the complex
+// factors (fs_*), and every loop (fac0_in) applies them to its right-hand side: about six
+// FP64 operations per row and no division, so the lane stays off the kernel's critical
+// path on GB300's slow FP64 pipe.  The right-hand side: the spectrum row R[0] (its real
+// part) minus xm_scale x_m with x_m = V_m y_m in FP64 (final loop), or v_{m+1} of the FP64
+// basis (dots pass).  Epilogues in FP64: acc0 = omega_0 y (b of eq. 7), h0 = y and the dots
+// g_0 = V_m^T y (eq. 12), and the binary32 store of y into Y[0].
+template <int M>
+__device__ void pint_k0_lane(const PintGeom &g, const PintArgs<float> &a, int P, int t, int tic, int64_t off,
+                             int blen, int blk, cpx<float> *dd_f, cpx<float> *px_f, double2 *red) {
+  double *dd = reinterpret_cast<double *>(dd_f);
+  double *pa = reinterpret_cast<double *>(px_f), *pc = pa + P, *pd = pc + P, *pib = pd + P;
+  const double s0 = a.shift[0].x;
+  const int NS = fac_slots(M, P);
+  double *Fo = a.fac0_out ? a.fac0_out + (int64_t)blk * NS * P + t : nullptr;
+  const double *Fi = a.fac0_in ? a.fac0_in + (int64_t)blk * NS * P + t : nullptr;
+  // 1. stage the right-hand side (element e at dd[e + e/M])
+  const double *vrhs = nullptr;
+  int mdots = 0;
+  if (a.mcount) {
+    const int m = *a.mcount + 1;
+    vrhs = a.Vd + (int64_t)m * a.ldv + off;
+    mdots = a.want_dots ? m : 0;
+  } else if (a.V) {
+    mdots = a.mdots;
+  }
+  if (!a.Vd) mdots = 0;
+  const int mx = a.xm_count ? *a.xm_count : 0;
+  const double *xy = a.xm_count ? a.xm_y + (int64_t)blk * a.xm_ldy : nullptr;
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    const int e = t + i * P;
+    double v = 0.0;
+    if (e < blen) {
+      if (a.R) {
+        v = (double)a.R[off + e].x;
+        if (xy) {
+          double xm = 0.0;
+          for (int q = 0; q < mx; ++q) xm += xy[q] * a.Vd[(int64_t)q * a.ldv + off + e];
+          v -= a.xm_scale * xm;
+        } else if (a.rvec) {
+          v -= (double)a.rvec[off + e];
+        }
+      } else if (vrhs) {
+        v = vrhs[e];
+      } else if (a.rvec) {
+        v = (double)a.rvec[off + e];
+      }
+    }
+    dd[e + e / M] = v;
+  }
+  team_sync(P, tic);
+  double *my = dd + (size_t)t * (M + 1);
+  const int e0 = t * M;
+  auto lo_of = [&](int i) { return e0 + i < blen ? a.tlo_d[off + e0 + i] : 0.0; };
+  auto up_of = [&](int i) { return e0 + i < blen ? a.tup_d[off + e0 + i] : 0.0; };
+  auto d_of = [&](int i) { return e0 + i < blen ? s0 + a.tdiag_d[off + e0 + i] : 1.0; };
+  double r[M];
+#pragma unroll
+  for (int i = 0; i < M; ++i) r[i] = my[i];
+  const double lo0 = lo_of(0), up0 = up_of(0);
+  double xf, xl, D1, A1, C1;
+  double aa[M], cc[M];
+  if (Fi) {
+    // 2-4 with the stored factors: the same elimination, PCR and back substitution applied
+    // to the right-hand side only
+    r[1] *= Fi[fs_rd<M>(1) * P];
+#pragma unroll
+    for (int i = 2; i < M; ++i) r[i] = (r[i] - lo_of(i) * r[i - 1]) * Fi[fs_rd<M>(i) * P];
+#pragma unroll
+    for (int i = M - 3; i >= 1; --i) r[i] -= Fi[fs_ccf<M>(i) * P] * r[i + 1];
+    const double D0 = r[0] - up0 * r[1];
+    D1 = r[M - 1];
+    pd[t] = D1;
+    team_sync(P, tic);
+    const double pD1 = t > 0 ? pd[t - 1] : 0.0;
+    double D = D0 - lo0 * pD1 - Fi[fs_c0<M>() * P] * D1;
+    team_sync(P, tic);
+    int l = 0;
+    for (int sig = 1; sig < P; sig <<= 1, ++l) {
+      pd[t] = D;
+      team_sync(P, tic);
+      double nD = D;
+      if (t - sig >= 0) nD -= Fi[fs_k1<M>(l) * P] * pd[t - sig];
+      if (t + sig < P) nD -= Fi[(fs_k1<M>(l) + 1) * P] * pd[t + sig];
+      team_sync(P, tic);
+      D = nD;
+    }
+    xf = D * Fi[fs_binv<M>(l) * P];
+    pd[t] = xf;
+    team_sync(P, tic);
+    const double xnext = t + 1 < P ? pd[t + 1] : 0.0;
+    xl = D1 - Fi[fs_aa<M>(M - 1) * P] * xf - Fi[fs_cc<M>(M - 1) * P] * xnext;
+    my[0] = xf;
+#pragma unroll
+    for (int i = 1; i < M - 1; ++i) my[i] = r[i] - Fi[fs_aa<M>(i) * P] * xf - Fi[fs_cc<M>(i) * P] * xl;
+    my[M - 1] = xl;
+  } else {
+    // 2. chunk elimination: row i becomes x_i + aa_i x_0 + cc_i x_{M-1} = r_i (factors
+    // stored when Fo is set)
+    const double d0 = d_of(0);
+    {
+      const double rb = 1.0 / d_of(1);
+      aa[1] = lo_of(1) * rb;
+      cc[1] = up_of(1) * rb;
+      r[1] *= rb;
+      if (Fo) {
+        Fo[fs_rd<M>(1) * P] = rb;
+        if (1 <= M - 3) Fo[fs_ccf<M>(1) * P] = cc[1];
+      }
+    }
+#pragma unroll
+    for (int i = 2; i < M; ++i) {
+      const double lo = lo_of(i);
+      const double rd = 1.0 / (d_of(i) - lo * cc[i - 1]);
+      aa[i] = -lo * aa[i - 1] * rd;
+      cc[i] = up_of(i) * rd;
+      r[i] = (r[i] - lo * r[i - 1]) * rd;
+      if (Fo) {
+        Fo[fs_rd<M>(i) * P] = rd;
+        if (i <= M - 3) Fo[fs_ccf<M>(i) * P] = cc[i];
+      }
+    }
+#pragma unroll
+    for (int i = M - 3; i >= 1; --i) {
+      aa[i] -= cc[i] * aa[i + 1];
+      r[i] -= cc[i] * r[i + 1];
+      cc[i] = -cc[i] * cc[i + 1];
+    }
+    const double A0 = lo0, B0 = d0 - up0 * aa[1], C0 = -up0 * cc[1], D0 = r[0] - up0 * r[1];
+    A1 = aa[M - 1];
+    C1 = cc[M - 1];
+    D1 = r[M - 1];
+    if (Fo) {
+      Fo[fs_c0<M>() * P] = C0;
+#pragma unroll
+      for (int i = 1; i < M; ++i) {
+        Fo[fs_aa<M>(i) * P] = aa[i];
+        Fo[fs_cc<M>(i) * P] = cc[i];
+      }
+    }
+    // 3a. eliminate the chunks' last unknowns: P interface rows in the first unknowns
+    pa[t] = A1;
+    pc[t] = C1;
+    pd[t] = D1;
+    team_sync(P, tic);
+    double A, B, C, D;
+    {
+      const double pA1 = t > 0 ? pa[t - 1] : 0.0, pC1 = t > 0 ? pc[t - 1] : 0.0, pD1 = t > 0 ? pd[t - 1] : 0.0;
+      A = -A0 * pA1;
+      B = B0 - A0 * pC1 - C0 * A1;
+      C = -C0 * C1;
+      D = D0 - A0 * pD1 - C0 * D1;
+    }
+    team_sync(P, tic);
+    // 3b. PCR on the interface rows (one buffer, two barriers per level)
+    int l = 0;
+    for (int sig = 1; sig < P; sig <<= 1, ++l) {
+      pa[t] = A;
+      pc[t] = C;
+      pd[t] = D;
+      pib[t] = 1.0 / B;
+      team_sync(P, tic);
+      double nA = 0.0, nB = B, nC = 0.0, nD = D, k1 = 0.0, k2 = 0.0;
+      if (t - sig >= 0) {
+        k1 = A * pib[t - sig];
+        nA = -k1 * pa[t - sig];
+        nB -= k1 * pc[t - sig];
+        nD -= k1 * pd[t - sig];
+      }
+      if (t + sig < P) {
+        k2 = C * pib[t + sig];
+        nC = -k2 * pc[t + sig];
+        nB -= k2 * pa[t + sig];
+        nD -= k2 * pd[t + sig];
+      }
+      if (Fo) {
+        Fo[fs_k1<M>(l) * P] = k1;
+        Fo[(fs_k1<M>(l) + 1) * P] = k2;
+      }
+      team_sync(P, tic);
+      A = nA;
+      B = nB;
+      C = nC;
+      D = nD;
+    }
+    const double rB = 1.0 / B;
+    if (Fo) Fo[fs_binv<M>(l) * P] = rB;
+    xf = D * rB;
+    pd[t] = xf;
+    team_sync(P, tic);
+    const double xnext = t + 1 < P ? pd[t + 1] : 0.0;
+    xl = D1 - A1 * xf - C1 * xnext;
+    // 4. back substitution
+    my[0] = xf;
+#pragma unroll
+    for (int i = 1; i < M - 1; ++i) my[i] = r[i] - aa[i] * xf - cc[i] * xl;
+    my[M - 1] = xl;
+  }
+  team_sync(P, tic);
+  // 5. epilogues, coalesced
+  const double om = a.omega ? a.omega[0].x : 0.0;
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    const int e = t + i * P;
+    if (e < blen) {
+      const double y = dd[e + e / M];
+      if (a.omega && a.acc0) a.acc0[off + e] = om * y;
+      if (a.h0) a.h0[off + e] = y;
+      if (a.Y) a.Y[off + e] = mk<float>((float)y, 0.0f);
+    }
+  }
+  if (mdots > 0) {
+    const int nw = P >> 5, w = t >> 5, l = t & 31;
+    for (int q = 0; q < mdots; ++q) {
+      const double *vq = a.Vd + (int64_t)q * a.ldv + off;
+      double sq = 0.0;
+#pragma unroll
+      for (int i = 0; i < M; ++i) {
+        const int e = t + i * P;
+        if (e < blen) sq += vq[e] * dd[e + e / M];
+      }
+      sq = warp_sum(sq);
+      if (l == 0) red[w * mdots + q] = make_double2(sq, 0.0);
+    }
+    team_sync(P, tic);
+    for (int q = t; q < mdots; q += P) {
+      double sx = 0.0;
+      for (int i = 0; i < nw; ++i) sx += red[i * mdots + q].x;
+      a.gpart[((int64_t)0 * g.nblk + blk) * mdots + q] = make_double2(sx, 0.0);
+    }
+  }
+  team_sync(P, tic);
+}
+
 // MAXT: the launch's thread count is at most MAXT (256 leaves room for 255
 // registers per thread, which the FP64 variants use without spilling).
 // FACT: solve with a.fac_in (a separate instantiation, so that its register budget is
@@ -121,8 +362,15 @@ __global__ void __launch_bounds__(MAXT) k_pint(PintGeom g, PintArgs<T> a, size_t
   const bool active = team < g.nblk * g.R;  // idle teams stay for the CTA-level sum
   const int blk = active ? team / g.R : 0;
   const int rr = team - blk * g.R;
-  const int k0 = active ? (int)((int64_t)rr * g.nf / g.R) : 0;
-  const int k1 = active ? (int)((int64_t)(rr + 1) * g.nf / g.R) : 0;
+  int k0 = active ? (int)((int64_t)rr * g.nf / g.R) : 0;
+  int k1 = active ? (int)((int64_t)(rr + 1) * g.nf / g.R) : 0;
+  if (active && a.k0_fp64 && g.R >= 2 && g.nf >= 2) {
+    // the zero-frequency lane (FP64) is a team's whole share; the other teams split
+    // k = 1..nf-1
+    k0 = rr == 0 ? 0 : 1 + (int)((int64_t)(rr - 1) * (g.nf - 1) / (g.R - 1));
+    k1 = rr == 0 ? 1 : 1 + (int)((int64_t)rr * (g.nf - 1) / (g.R - 1));
+  }
+  if (a.fac0_out) k1 = (k0 == 0 && k1 > 0) ? 1 : k0;  // the lane's factor pass: frequency 0 only
   const int blen = g.blen;
   const int64_t off = (int64_t)blk * blen;
   const int N = P;  // condensed interface rows
@@ -232,6 +480,12 @@ __global__ void __launch_bounds__(MAXT) k_pint(PintGeom g, PintArgs<T> a, size_t
   }
 
   for (int k = k0; k < k1; ++k) {
+    if constexpr (sizeof(T) == 4) {
+      if (k == 0 && a.k0_fp64) {
+        pint_k0_lane<M>(g, a, P, t, tic, off, blen, blk, dd, pa, red);
+        continue;
+      }
+    }
     const double2 sk = a.shift[k];
     const cpx<T> s = mk<T>((T)sk.x, (T)sk.y);
     const cpx<T> *Rk = a.R ? a.R + (int64_t)k * a.ldr + off : nullptr;  // this block's row of R
@@ -555,7 +809,7 @@ __device__ __forceinline__ double colsum_finish(double v, double (*sm)[CW + 1], 
 template <int CW, int RG>
 __global__ void __launch_bounds__(CW * RG) k_acc_reduce(int nblk, int blen, int R, const double *__restrict__ part,
                                                         double *__restrict__ out, const int *skip_flag,
-                                                        InitTail tail) {
+                                                        InitTail tail, const double *__restrict__ extra) {
   grid_dep_wait();
   if (skip_flag && *skip_flag && !tail.enabled) return;
   __shared__ double sm[RG][CW + 1];
@@ -584,7 +838,7 @@ __global__ void __launch_bounds__(CW * RG) k_acc_reduce(int nblk, int blen, int 
 #pragma unroll
   for (int u = 0; u < kColB; ++u) tot += acc[u];
   tot = colsum_finish<CW, RG>(tot, sm, tx, ty);
-  if (ty == 0 && j < n) out[j] = tot;
+  if (ty == 0 && j < n) out[j] = extra ? tot + extra[j] : tot;
   if (tail.enabled && last_cta_done(tail.counter)) {
     init_v0_body<kTail>(out, tail.n, tail.part, tail.ld, tail.V, tail.Vf, tail.scal, tail.flags, tail.use_handle,
                         tail.h, tail.T, tail.nT);
@@ -599,7 +853,8 @@ __global__ void __launch_bounds__(CW * RG) k_acc_reduce(int nblk, int blen, int 
 template <typename T, int CW, int RG>
 __global__ void __launch_bounds__(CW * RG) k_zsum(int nf, int64_t n, const cpx<T> *__restrict__ H, int64_t ldh,
                                                   const double2 *__restrict__ omega, double *__restrict__ z,
-                                                  const int *skip_flag, ProjTail tail, int mlen) {
+                                                  const int *skip_flag, ProjTail tail, int mlen,
+                                                  const double *__restrict__ h0) {
   grid_dep_wait();
   const bool skip = skip_flag && *skip_flag;  // breakdown: no z (eq. 13 gives 0); the tail still decides
   __shared__ double sm[RG][CW + 1];
@@ -616,11 +871,13 @@ __global__ void __launch_bounds__(CW * RG) k_zsum(int nf, int64_t n, const cpx<T
     const bool own = j < n && memj == mem0;
     // the first batch of h_k loads is issued before the weights are staged, so the two
     // memory round trips overlap
+    // with h0 the zero frequency comes from the FP64 lane (added below), not from row 0
+    const int kfirst = h0 ? 1 : 0;
     cpx<T> h[kColB];
 #pragma unroll
     for (int u = 0; u < kColB; ++u) {
       const int k = ty + u * RG;
-      h[u] = (own && k < nf) ? H[(int64_t)k * ldh + j] : mk<T>(T(0), T(0));
+      h[u] = (own && k < nf && k >= kfirst) ? H[(int64_t)k * ldh + j] : mk<T>(T(0), T(0));
     }
     for (int k = threadIdx.x; k < nf; k += CW * RG) om[k] = mk<T>((T)om0[k].x, (T)om0[k].y);
     __syncthreads();
@@ -629,7 +886,7 @@ __global__ void __launch_bounds__(CW * RG) k_zsum(int nf, int64_t n, const cpx<T
     for (int u = 0; u < kColB; ++u) acc[u] = T(0);
     if (j < n && !own) {  // a later member in this CTA: its weights from memory
       const double2 *omj = omega + (int64_t)memj * nf;
-      for (int k = ty; k < nf; k += RG) {
+      for (int k = ty < kfirst ? ty + RG : ty; k < nf; k += RG) {
         const cpx<T> hk = H[(int64_t)k * ldh + j];
         acc[0] += (T)omj[k].x * hk.x - (T)omj[k].y * hk.y;
       }
@@ -645,7 +902,7 @@ __global__ void __launch_bounds__(CW * RG) k_zsum(int nf, int64_t n, const cpx<T
 #pragma unroll
         for (int u = 0; u < kColB; ++u) {
           const int k = k0 + u * RG;
-          h[u] = k < nf ? H[(int64_t)k * ldh + j] : mk<T>(T(0), T(0));
+          h[u] = (k < nf && k >= kfirst) ? H[(int64_t)k * ldh + j] : mk<T>(T(0), T(0));
         }
       }
     }
@@ -653,7 +910,7 @@ __global__ void __launch_bounds__(CW * RG) k_zsum(int nf, int64_t n, const cpx<T
 #pragma unroll
     for (int u = 0; u < kColB; ++u) tot += (double)acc[u];
     tot = colsum_finish<CW, RG>(tot, sm, tx, ty);
-    if (ty == 0 && j < n) z[j] = tot;
+    if (ty == 0 && j < n) z[j] = h0 ? tot + omega[(int64_t)memj * nf].x * h0[j] : tot;
   }
   if (tail.enabled && last_cta_done(tail.counter)) {
     project_body<kTail>(tail.n, tail.V, z, tail.tau, tail.part, tail.ld, tail.scal, tail.flags, tail.kc,
@@ -664,7 +921,7 @@ __global__ void __launch_bounds__(CW * RG) k_zsum(int nf, int64_t n, const cpx<T
 
 template <typename T>
 void launch_zsum(Ctx &c, int nf, int64_t n, const cpx<T> *H, int64_t ldh, const double2 *omega, double *z,
-                 const int *skip_flag, const ProjTail *tailp, int mlen) {
+                 const int *skip_flag, const ProjTail *tailp, int mlen, const double *h0) {
   const size_t smem = (size_t)nf * sizeof(cpx<T>);
   ProjTail tail{};
   if (tailp) tail = *tailp;
@@ -672,20 +929,20 @@ void launch_zsum(Ctx &c, int nf, int64_t n, const cpx<T> *H, int64_t ldh, const 
     if (nf <= 256) {
       const int grid = (int)((n + 31) / 32);
       pdl_launch(c.pdl, k_zsum<T, 32, 16>, dim3(grid), dim3(512), smem, c.stream, nf, n, H, ldh, omega, z,
-                 skip_flag, tail, mlen);
+                 skip_flag, tail, mlen, h0);
     } else {
       const int grid = (int)((n + 7) / 8);
       if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_zsum<T, 8, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       pdl_launch(c.pdl, k_zsum<T, 8, 64>, dim3(grid), dim3(512), smem, c.stream, nf, n, H, ldh, omega, z,
-                 skip_flag, tail, mlen);
+                 skip_flag, tail, mlen, h0);
     }
   });
 }
 template void launch_zsum<double>(Ctx &, int, int64_t, const cpx<double> *, int64_t, const double2 *, double *,
-                                  const int *, const ProjTail *, int);
+                                  const int *, const ProjTail *, int, const double *);
 template void launch_zsum<float>(Ctx &, int, int64_t, const cpx<float> *, int64_t, const double2 *, double *,
-                                 const int *, const ProjTail *, int);
+                                 const int *, const ProjTail *, int, const double *);
 
 static int next_pow2(int v) {
   int p = 1;
@@ -768,18 +1025,30 @@ void launch_pint(Ctx &c, const PintGeom &g, const PintArgs<T> &a) {
 }
 
 void launch_acc_reduce(Ctx &c, const PintGeom &g, const double *acc_part, double *out, const int *skip_flag,
-                       const InitTail *tailp) {
+                       const InitTail *tailp, const double *extra) {
   const int64_t n = (int64_t)g.nblk * g.blen;
   InitTail tail{};
   if (tailp) tail = *tailp;
   c.launch("acc_reduce", (double)n * g.acc_rows * 8.0 + n * 8.0, [&] {
     if (g.acc_rows <= 256)
       pdl_launch(c.pdl, k_acc_reduce<32, 16>, dim3((int)((n + 31) / 32)), dim3(512), 0, c.stream, g.nblk, g.blen,
-                 g.acc_rows, acc_part, out, skip_flag, tail);
+                 g.acc_rows, acc_part, out, skip_flag, tail, extra);
     else
       pdl_launch(c.pdl, k_acc_reduce<8, 64>, dim3((int)((n + 7) / 8)), dim3(512), 0, c.stream, g.nblk, g.blen,
-                 g.acc_rows, acc_part, out, skip_flag, tail);
+                 g.acc_rows, acc_part, out, skip_flag, tail, extra);
   });
+}
+
+// r[i] = the binary32 reciprocal of the mixed-precision shifted solves (rcp_nr), for the
+// verification entry point paradiag_recip_f32.
+__global__ void k_recip_f32(const float *__restrict__ x, float *__restrict__ r, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) r[i] = rcp_nr(x[i]);
+}
+
+void launch_recip_f32(cudaStream_t s, const float *x, float *r, int64_t n) {
+  const int64_t grid = (n + 255) / 256;
+  if (grid > 0) k_recip_f32<<<(unsigned)grid, 256, 0, s>>>(x, r, n);
 }
 
 template void launch_pint<double>(Ctx &, const PintGeom &, const PintArgs<double> &);

@@ -221,6 +221,8 @@ struct pd_plan {
   double *b = nullptr, *z = nullptr, *x = nullptr, *y = nullptr;
   double *b0 = nullptr, *x0 = nullptr;  // b and x_m of the first solve (for paradiag_last_vectors)
   double *acc_part = nullptr;
+  double *acc0 = nullptr, *h0 = nullptr;  // PD_MIXED: FP64 zero-frequency lane outputs (b share, h_0)
+  double *fac0 = nullptr;                 // PD_MIXED: the lane's FP64 factors (per operator)
   double2 *gpart = nullptr, *srow = nullptr, *omega = nullptr;
   double *msys_part = nullptr;
   double *norm_part = nullptr;
@@ -257,6 +259,67 @@ struct HostOp {
   std::vector<double> lo, diag, up;  // K~ (length nbar), block-decoupled
   std::vector<double> xlo, xdiag, xup, ylo, ydiag, yup;
 };
+
+// The shifted solves eliminate without pivoting (partitioned Thomas + PCR).  Every
+// shift of Algorithms 1 and 3 has Re(1 - pi_k) >= 0 (|pi_k| = alpha^{1/l} <= 1).  Either
+// of two conditions on each block of K then makes elimination in any order safe for
+// every shifted matrix (1 - pi_k) I + tau K (in 2D, after the DST along y, the blocks
+// T_x + mu_j I with mu_j = d_y + 2 c_y cos(j pi / (ny + 1)); the smallest mu_j is added
+// to the diagonal of T_x):
+//  (a) weak row diagonal dominance, k_ii >= |lo_i| + |up_i|: the shifted matrix is
+//      dominant as well, |(1 - pi_k) + tau k_ii| >= tau k_ii;
+//  (b) K symmetric positive definite: the Hermitian part Re(1 - pi_k) I + tau K is
+//      positive definite, a property every Schur complement keeps, so every pivot has a
+//      real part at least the corresponding pivot of the real LDL^T of tau K.
+// A diagonal mass matrix changes neither: (1 - pi_k) M + tau K is dominant when K is
+// (and has a positive definite Hermitian part when K is SPD), and the plan's symmetric
+// scaling M^{-1/2} (.) M^{-1/2} only rescales the rows and columns of its LU factors.
+// A centred advection term at cell Peclet number above 2 satisfies neither condition;
+// such operators are rejected rather than solved without pivoting.  The relative slack
+// 1e-12 absorbs the rounding of operators that are dominant with equality (upwind).
+pd_status check_dominance(const pd_desc *d) {
+  const int nb = d->batch > 1 ? d->batch : 1;
+  double mu = 0.0;  // smallest eigenvalue of T_y (2D)
+  if (d->dim == 2) {
+    const double dy = d->k_diag_y[0], cy = d->ny > 1 ? d->k_up_y[0] : 0.0;
+    mu = dy - 2.0 * std::fabs(cy) * std::cos(M_PI / (double)(d->ny + 1));
+  }
+  for (int b = 0; b < nb; ++b) {
+    const int64_t n = (nb > 1 && d->batch_nx) ? d->batch_nx[b] : d->nx;
+    const double *lo = d->k_lo + (int64_t)b * d->nx, *di = d->k_diag + (int64_t)b * d->nx,
+                 *up = d->k_up + (int64_t)b * d->nx;
+    bool dominant = true, symmetric = true;
+    int64_t bad = -1;
+    double bad_off = 0.0, bad_di = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+      const double l = i > 0 ? lo[i] : 0.0, u = i + 1 < n ? up[i] : 0.0, dd = di[i] + mu;
+      if (!std::isfinite(dd) || !std::isfinite(l) || !std::isfinite(u))
+        return fail(PD_ERR_INVALID_ARG, "K has a non-finite coefficient in row %lld", (long long)(b * d->nx + i));
+      const double off = std::fabs(l) + std::fabs(u);
+      if (dominant && dd < off - 1e-12 * (std::fabs(dd) + off)) {
+        dominant = false;
+        bad = (int64_t)b * d->nx + i;
+        bad_off = off;
+        bad_di = dd;
+      }
+      if (i + 1 < n && std::fabs(lo[i + 1] - u) > 1e-12 * (std::fabs(lo[i + 1]) + std::fabs(u))) symmetric = false;
+    }
+    if (dominant) continue;
+    bool spd = symmetric;
+    double h = 0.0;  // LDL^T pivots of the symmetric block
+    for (int64_t i = 0; spd && i < n; ++i) {
+      const double dd = di[i] + mu;
+      h = i == 0 ? dd : dd - lo[i] * lo[i] / h;
+      if (!(h > 1e-13 * std::fabs(dd))) spd = false;
+    }
+    if (!spd)
+      return fail(PD_ERR_UNSUPPORTED,
+                  "K is neither diagonally dominant (row %lld: |lo| + |up| = %.17g > diag = %.17g%s) nor symmetric "
+                  "positive definite: the shifted systems are eliminated without pivoting, which needs one of the two",
+                  (long long)bad, bad_off, bad_di, d->dim == 2 ? " incl. the smallest eigenvalue of T_y" : "");
+  }
+  return PD_OK;
+}
 
 pd_status validate(const pd_desc *d) {
   if (!d) return fail(PD_ERR_INVALID_ARG, "desc is NULL");
@@ -349,7 +412,7 @@ pd_status validate(const pd_desc *d) {
   const int64_t nbar = d->nx * (d->dim == 2 ? d->ny : 1) * (d->batch > 1 ? d->batch : 1);
   if (nbar > (int64_t)1 << 28 || d->nt * nbar > (int64_t)1 << 34)
     return fail(PD_ERR_UNSUPPORTED, "problem too large for this build");
-  return PD_OK;
+  return check_dominance(d);
 }
 
 void fill_geometry(pd_plan *p, const pd_desc *d) {
@@ -405,7 +468,8 @@ void fill_geometry(pd_plan *p, const pd_desc *d) {
       pd::pint_geometry(p->nf, p->nblk, p->blen, target, esz, d->tune_pint_rows, d->tune_pint_teams, want_fac);
   // Krylov vector kernels: vectors up to 8192 entries run in one 512-thread CTA or (see
   // below) a cluster; beyond, cooperative 64-thread CTAs, at most one per SM (co-resident)
-  p->blas_grid = p->nbar <= 8192 ? 1 : (int)std::max<int64_t>(1, std::min<int64_t>((p->nbar + 63) / 64, (int64_t)sms));
+  p->blas_grid =
+      p->nbar <= 8192 ? 1 : (int)std::max<int64_t>(1, std::min<int64_t>((p->nbar + pd::kBlas - 1) / pd::kBlas, (int64_t)sms));
   // capacitance terms: one frequency per warp (four warps per CTA; a thread per
   // frequency when m = 1)
   p->k5_grid = std::max(1, std::min((p->nf + 3) / 4, 1024));
@@ -513,6 +577,11 @@ size_t layout(pd_plan *p, unsigned char *base) {
   p->x0 = A.take<double>(nbar);
   p->y = A.take<double>((size_t)(mx + 1) * nmem);
   p->acc_part = A.take<double>((size_t)p->geom.nblk * p->geom.R * p->geom.blen);
+  if (mixed) {
+    p->acc0 = A.take<double>(nbar);
+    p->h0 = A.take<double>(nbar);
+    p->fac0 = A.take<double>(pd::pint_k0_factor_elems(p->geom));
+  }
   p->gpart = A.take<double2>((size_t)nf * p->nblk * mx);
   p->srow = A.take<double2>((size_t)nf * mx * nmem);
   p->omega = A.take<double2>((size_t)nf * nmem);
@@ -772,15 +841,40 @@ pd::PintArgs<float> base_args<float>(pd_plan *p) {
   a.tlo = p->tlo_f;
   a.tdiag = p->tdiag_f;
   a.tup = p->tup_f;
+  // the zero frequency, whose shifted system carries the ill-conditioning of tau K, in FP64
+  a.k0_fp64 = 1;
+  a.tlo_d = p->tlo_d;
+  a.tdiag_d = p->tdiag_d;
+  a.tup_d = p->tup_d;
+  a.Vd = p->V;
+  a.fac0_in = p->fac0;
   return a;
+}
+// FP64 zero-frequency lane outputs of the binary32 path (null for FP64 plans)
+template <typename T>
+double *lane_acc0(pd_plan *p) {
+  return sizeof(T) == 4 ? p->acc0 : nullptr;
+}
+template <typename T>
+double *lane_h0(pd_plan *p) {
+  return sizeof(T) == 4 ? p->h0 : nullptr;
 }
 
 // Factor every (k, block) shifted system of the plan (after the operator changed).
 pd_status factorize(pd_plan *p) {
-  if (!p->fac) return PD_OK;
+  if (p->precision == PD_MIXED) {  // the FP64 factors of the zero-frequency lane
+    pd::PintArgs<float> a = base_args<float>(p);
+    a.fac_in = nullptr;
+    a.fac0_in = nullptr;
+    a.fac0_out = p->fac0;
+    pd::launch_pint<float>(p->ctx, p->geom, a);
+  }
+  if (!p->fac) return ctx_status(p);
   if (p->precision == PD_MIXED) {
     pd::PintArgs<float> a = base_args<float>(p);
     a.fac_in = nullptr;
+    a.k0_fp64 = 0;  // every frequency's binary32 factors are stored
+    a.fac0_in = nullptr;
     a.fac_out = reinterpret_cast<cpx<float> *>(p->fac);
     pd::launch_pint<float>(p->ctx, p->geom, a);
   } else {
@@ -824,14 +918,17 @@ pd::KrylovBufs kbufs(pd_plan *p) {
 // levels off at the rounding noise of the shifted solves, and in FP64 the polynomial
 // space K_m(K, b) can stall for many steps when J_l is far from I.  A binary32
 // refinement sweep contracts the error by ~1e-3 at best (rounding noise of the
-// residual, amplified by the solution operator), so its Algorithm 2 asks for 1e-3 and
-// stops at its first stall; FP64 refinement sweeps (only after a stall) ask for 1e-8.
+// residual, amplified by the solution operator), so its Algorithm 2 asks for 1e-3; FOM
+// residuals are not monotone, so it leaves on a stall only after two checks without
+// halving and once ||r_m|| <= 1e-2 ref (far above the binary32 noise floor of eq. 13, far
+// below a residual that would keep the refinement from contracting).  FP64 refinement
+// sweeps (only after a stall) ask for 1e-8.
 pd::KrylovCtl krylov_ctl(pd_plan *p, int kind) {
   const bool fp64 = p->precision == PD_FP64;
   pd::KrylovCtl k;
   k.eps = kind == 0 ? p->eps : std::max(p->eps, fp64 ? 1e-8 : 1e-3);
-  k.stall_floor = fp64 ? 1e-6 : (kind == 0 ? 1e-3 : 1.0);
-  k.win = fp64 ? 3 : 1;
+  k.stall_floor = fp64 ? 1e-6 : (kind == 0 ? 1e-3 : 1e-2);
+  k.win = fp64 ? 3 : (kind == 0 ? 1 : 2);
   if (p->refined64) {  // refined FP64 plans: leave a stalled step at any level
     k.eps = std::max(p->eps, 1e-8);
     k.stall_floor = 1.0;
@@ -840,6 +937,9 @@ pd::KrylovCtl krylov_ctl(pd_plan *p, int kind) {
     k.stall_floor = 1.0;
     k.win = 2;
   }
+  // plans that refine measure ||r_m|| against ||R||_F of the solve's right-hand side
+  // (krylov_decide); single problems only (batches keep each problem's beta)
+  k.rrel = (!p->members && (!fp64 || p->refined64 || kind == 1)) ? 1 : 0;
   k.maxit = p->maxit;
   k.q = p->q;
   return k;
@@ -876,21 +976,26 @@ pd_status emit_pre(pd_plan *p, int kind, const double *G, double *U, int use_han
   const int nt = (int)p->nt;
   T *res = res_buf<T>(p);
   T *tmp = tmp_buf<T>(p);
+  // ||R||_F of this solve's right-hand side, the reference of the refining plans' Algorithm-2
+  // stop (krylov_decide); batches measure each problem against its own beta instead
+  const pd::RhsNorm rn{p->norm_part, p->flags + pd::F_RNCNT, p->scal + pd::S_RNORM};
+  const pd::RhsNorm *rnp = p->members ? nullptr : &rn;
   if (kind == 0) {
     if (p->dim == 1) {
-      pd::launch_fft_r2c<T, double>(c, G, p->nbar, p->nbar, nt, time_tw<T>(p), S, p->lds, row_scale<T>(p, false));
+      pd::launch_fft_r2c<T, double>(c, G, p->nbar, p->nbar, nt, time_tw<T>(p), S, p->lds, row_scale<T>(p, false),
+                                    rnp);
     } else {
       pd::launch_dst_y<double, T, T>(c, G, tmp, p->nt, p->ny, p->nx, dst_tw<T>(p), 0);
-      pd::launch_fft_r2c<T, T>(c, tmp, p->nbar, p->nbar, nt, time_tw<T>(p), S, p->lds, row_scale<T>(p, false));
+      pd::launch_fft_r2c<T, T>(c, tmp, p->nbar, p->nbar, nt, time_tw<T>(p), S, p->lds, row_scale<T>(p, false), rnp);
     }
   } else {
     if (p->dim == 1) {  // the FP64 residual is formed while the DFT loads its tiles
       pd::launch_fft_r2c_residual<T>(c, G, U, p->nbar, nt, p->rxl, p->rxd, p->rxu, time_tw<T>(p), S, p->lds,
-                                     row_scale<T>(p, false), p->batch > 1 ? p->mex : nullptr, (int)p->nxm);
+                                     row_scale<T>(p, false), p->batch > 1 ? p->mex : nullptr, (int)p->nxm, rnp);
     } else {
       pd::launch_residual<T>(c, G, U, res, p->nt, p->ny, p->nx, p->rxl, p->rxd, p->rxu, p->ryl, p->ryd, p->ryu);
       pd::launch_dst_y<T, T, T>(c, res, tmp, p->nt, p->ny, p->nx, dst_tw<T>(p), 0);
-      pd::launch_fft_r2c<T, T>(c, tmp, p->nbar, p->nbar, nt, time_tw<T>(p), S, p->lds, row_scale<T>(p, false));
+      pd::launch_fft_r2c<T, T>(c, tmp, p->nbar, p->nbar, nt, time_tw<T>(p), S, p->lds, row_scale<T>(p, false), rnp);
     }
   }
   if (p->loops == 1) {  // U = U_1: no b and no Algorithm 2; the final loop runs with x_m = 0
@@ -902,17 +1007,19 @@ pd_status emit_pre(pd_plan *p, int kind, const double *G, double *U, int use_han
   a.ldr = p->lds;
   a.omega = p->wg;
   a.acc_part = p->acc_part;
+  a.acc0 = lane_acc0<T>(p);
   pd::launch_pint<T>(c, p->geom, a);
   pd::KrylovBufs kb = kbufs<T>(p);
+  double *acc0 = lane_acc0<T>(p);
   if (kb.members) {
-    pd::launch_acc_reduce(c, p->geom, p->acc_part, p->b, nullptr);
+    pd::launch_acc_reduce(c, p->geom, p->acc_part, p->b, nullptr, nullptr, acc0);
     pd::launch_member_init(c, kb, p->b, use_handle, hk);
   } else if (p->krylov_tails) {  // beta and v_1 in the b reduction's last CTA
     const pd::InitTail t{1, p->flags + pd::F_ACCCNT, kb.n, kb.maxit + 2, (kb.maxit + 1) * kb.maxit, use_handle,
                          kb.part, kb.V, kb.scal, kb.T, kb.Vf, kb.flags, hk};
-    pd::launch_acc_reduce(c, p->geom, p->acc_part, p->b, nullptr, &t);
+    pd::launch_acc_reduce(c, p->geom, p->acc_part, p->b, nullptr, &t, acc0);
   } else {
-    pd::launch_acc_reduce(c, p->geom, p->acc_part, p->b, nullptr);
+    pd::launch_acc_reduce(c, p->geom, p->acc_part, p->b, nullptr, nullptr, acc0);
     pd::launch_vec_norm_init(c, kb, p->b, use_handle, hk);
   }
   // x_m = b: the inner matrix of eq. (17) taken as I (two loops in all)
@@ -944,21 +1051,23 @@ pd_status emit_iter(pd_plan *p, int kind, int use_handle, cudaGraphConditionalHa
     a.Y = H;
     a.ldy = p->lds;
     a.skip_flag = noh;
+    a.h0 = lane_h0<T>(p);
     pd::launch_pint<T>(c, p->geom, a);
   }
+  const double *h0 = lane_h0<T>(p);
   pd::launch_capacitance(c, kb, p->nf, p->tau, p->shift, p->wga, p->gpart, p->nblk, p->msys_part,
                          kb.members ? p->k5_grid_members : p->k5_grid,
                          p->srow, p->omega, p->y, kb.members);
   // z = sum_i gamma_i h_i (e_m^T S_i y_m) from the stored h_i, then eq. (13)
   if (kb.members) {
-    pd::launch_zsum<T>(c, p->nf, p->nbar, H, p->lds, p->omega, p->z, noh, nullptr, kb.mlen);
+    pd::launch_zsum<T>(c, p->nf, p->nbar, H, p->lds, p->omega, p->z, noh, nullptr, kb.mlen, h0);
     pd::launch_member_project(c, kb, p->z, p->tau, krylov_ctl(p, kind), use_handle, hk);
   } else if (p->krylov_tails) {  // eq. (13) and the decision in the z reduction's last CTA
     const pd::ProjTail t{1, p->flags + pd::F_ZCNT, kb.n, kb.maxit + 2, use_handle, kb.V, p->tau, kb.part, kb.scal,
                          kb.flags, krylov_ctl(p, kind), hk};
-    pd::launch_zsum<T>(c, p->nf, p->nbar, H, p->lds, p->omega, p->z, noh, &t);
+    pd::launch_zsum<T>(c, p->nf, p->nbar, H, p->lds, p->omega, p->z, noh, &t, 0, h0);
   } else {
-    pd::launch_zsum<T>(c, p->nf, p->nbar, H, p->lds, p->omega, p->z, noh);
+    pd::launch_zsum<T>(c, p->nf, p->nbar, H, p->lds, p->omega, p->z, noh, nullptr, 0, h0);
     pd::launch_project_resnorm(c, kb, p->z, p->tau, krylov_ctl(p, kind), use_handle, hk);
   }
   return PD_OK;
@@ -1514,6 +1623,7 @@ pd_status paradiag_shifted_solve(pd_plan *p, const void *R, void *Y, double *b) 
     pd::launch_pint<double>(p->ctx, p->geom, a);
   } else {
     pd::PintArgs<float> a = base_args<float>(p);
+    a.k0_fp64 = 0;  // the stage entry point solves every frequency of arbitrary complex data in binary32
     a.R = reinterpret_cast<const cpx<float> *>(R);
     a.ldr = p->nbar;
     a.Y = reinterpret_cast<cpx<float> *>(Y);
@@ -1554,6 +1664,17 @@ pd_status paradiag_last_vectors(pd_plan *p, double *b, double *x) {
   }
   CK(cudaStreamSynchronize(p->ctx.stream));
   return ctx_status(p);
+}
+
+pd_status paradiag_recip_f32(const float *x, float *r, int64_t n, void *stream) {
+  if (n < 0) return fail(PD_ERR_INVALID_ARG, "n must be >= 0");
+  if (n > 0 && (!x || !r)) return fail(PD_ERR_INVALID_ARG, "NULL pointer");
+  if (n > ((int64_t)1 << 31) * 256) return fail(PD_ERR_UNSUPPORTED, "n too large");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  pd::launch_recip_f32(s, x, r, n);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  return PD_OK;
 }
 
 pd_status paradiag_set_timing(pd_plan *p, int enable) {

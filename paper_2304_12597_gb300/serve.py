@@ -199,13 +199,15 @@ class Server:
         k = (key, cap)
         if k not in self._ws_cache:
             n = key.nx * (cap if key.dim == 1 else key.ny)
-            one = np.ones(n)
+            # a placeholder operator of the right shape (the size depends on the shape only);
+            # tridiag(-1, 2, -1) passes the plan's diagonal-dominance check
+            off, two = -np.ones(n), np.full(n, 2.0)
             d = self._desc_for(key, cap)
             p = lambda a: a.ctypes.data_as(self.B.ctypes.POINTER(self.B.ctypes.c_double))  # noqa: E731
-            d.k_lo = d.k_diag = d.k_up = p(one)
+            d.k_lo, d.k_diag, d.k_up = p(off), p(two), p(off)
             if key.dim == 2:
-                y = np.ones(key.ny)
-                d.k_lo_y = d.k_diag_y = d.k_up_y = p(y)
+                yoff, ytwo = -np.ones(key.ny), np.full(key.ny, 2.0)
+                d.k_lo_y, d.k_diag_y, d.k_up_y = p(yoff), p(ytwo), p(yoff)
             self._ws_cache[k] = self.B.paradiag_workspace_size(d)
         return self._ws_cache[k]
 
@@ -277,14 +279,21 @@ class Server:
                 err = None
             except Exception as e:  # a failed solve fails its requests, not the service
                 err = str(e)
-            last = slot.U[-1]
-            final = last.view(batch.cap, batch.key.nx) if batch.key.dim == 1 else last.view(1, -1)
-            host = final.cpu().numpy() if self.keep_results else None
+            host = None
+            if self.keep_results == "full":  # the whole trajectory U (nt, n_bar) of each request
+                full = slot.U.view(batch.key.nt, batch.cap, batch.key.nx) if batch.key.dim == 1 else slot.U.view(
+                    batch.key.nt, 1, -1)
+                host = full.cpu().numpy()
+            elif self.keep_results:  # the final state u_l of each request
+                last = slot.U[-1]
+                final = last.view(1, batch.cap, batch.key.nx) if batch.key.dim == 1 else last.view(1, 1, -1)
+                host = final.cpu().numpy()
         now = time.perf_counter() - self.t0
         for b, r in enumerate(reqs):
             r.done, r.batch, r.error = now, len(reqs), err
             if host is not None:
-                r.result = host[b, : r.nx].copy() if batch.key.dim == 1 else host[0].copy()
+                res = host[:, b, : r.nx] if batch.key.dim == 1 else host[:, 0]
+                r.result = (res if self.keep_results == "full" else res[0]).copy()
 
     # -- the run ------------------------------------------------------------------------
     def run(self, requests: list) -> ServeStats:

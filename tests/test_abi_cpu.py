@@ -63,6 +63,9 @@ def _desc(B, **kw):
     lo = np.full(n, -1.0)
     di = np.full(n, 2.0)
     up = np.full(n, -1.0)
+    if "k" in kw:  # (lo, diag, up) of K
+        lo, di, up = (np.ascontiguousarray(a, dtype=np.float64) for a in kw.pop("k"))
+        n = len(di)
     keep = [lo, di, up]
     d = B.PdDesc()
     d.abi_version = 1
@@ -172,6 +175,62 @@ def test_bad_descriptors_are_rejected(B, kw, code):
     st, _ = _size_status(B, _desc(B, **kw))
     assert st == code, B.last_error()
     assert B.last_error()
+
+
+def _centred_advdiff(n, peclet, nu=1e-2):
+    """1D advection-diffusion nu u_xx - a u_x by centred differences (the discretisation of
+    the paper's Sec. 6.2 example, in 1D) at cell Peclet number a h / nu = peclet."""
+    h = 1.0 / (n + 1)
+    a = peclet * nu / h
+    lo = np.full(n, -nu / h**2 - a / (2 * h))
+    di = np.full(n, 2 * nu / h**2)
+    up = np.full(n, -nu / h**2 + a / (2 * h))
+    lo[0] = up[-1] = 0.0
+    return lo, di, up
+
+
+def test_pivot_free_elimination_needs_dominance_or_spd(B):
+    """The shifted solves eliminate without pivoting.  The plan accepts K when each block is
+    weakly diagonally dominant by rows or symmetric positive definite (in the solve basis)
+    and rejects it otherwise with PD_ERR_UNSUPPORTED: centred advection at cell Peclet
+    number 4 is neither; at 1.5 (and at exactly 2) it is dominant."""
+    st, _ = _size_status(B, _desc(B, k=_centred_advdiff(63, 4.0)))
+    assert st == 2 and "diagonally dominant" in B.last_error()
+    for pe in (1.5, 2.0):
+        st, _ = _size_status(B, _desc(B, k=_centred_advdiff(63, pe)))
+        assert st == 0, (pe, B.last_error())
+    # symmetric positive definite but not dominant: accepted
+    n = 40
+    lo, di, up = np.full(n, -1.0), np.full(n, 1.999), np.full(n, -1.0)  # eigenvalues 1.999 - 2 cos(j pi/41) > 0
+    lo[0] = up[-1] = 0.0
+    assert np.linalg.eigvalsh(np.diag(di) + np.diag(lo[1:], -1) + np.diag(up[:-1], 1)).min() > 0
+    st, _ = _size_status(B, _desc(B, k=(lo, di, up)))
+    assert st == 0, B.last_error()
+    # symmetric but indefinite (and not dominant): rejected
+    di2 = np.full(n, 1.99)
+    st, _ = _size_status(B, _desc(B, k=(lo, di2, up)))
+    assert st == 2
+    # a diagonal mass matrix keeps (1 - pi_k) M + tau K dominant: accepted with a dominant K
+    # (even where the symmetrically scaled operator is not), rejected with a bad one
+    st, _ = _size_status(B, _desc(B, k=_centred_advdiff(31, 1.0), mass=np.linspace(0.5, 2.0, 31)))
+    assert st == 0, B.last_error()
+    st, _ = _size_status(B, _desc(B, k=_centred_advdiff(31, 3.0), mass=np.linspace(0.5, 2.0, 31)))
+    assert st == 2
+    # one bad slot of a batch is found
+    good, bad = _centred_advdiff(31, 1.0), _centred_advdiff(31, 3.0)
+    kk = [np.concatenate([g, b]) for g, b in zip(good, bad)]
+    d = _desc(B, k=kk)
+    d.nx, d.batch = 31, 2
+    st, _ = _size_status(B, d)
+    assert st == 2 and "row 3" in B.last_error()
+    # 2D: T_x dominant only with the smallest eigenvalue of T_y added (2 - 2 cos(pi/8) = 0.152)
+    lo2, di2, up2 = np.full(7, -1.0), np.full(7, 1.9), np.full(7, -1.0)
+    lo2[0] = up2[-1] = 0.0
+    lo2[3] = -1.05  # non-symmetric, so only dominance can accept it
+    st, _ = _size_status(B, _desc(B, k=(lo2, di2, up2), dim=2, ny=7))
+    assert st == 0, B.last_error()
+    st, _ = _size_status(B, _desc(B, k=(lo2, di2 - 0.2, up2), dim=2, ny=7))
+    assert st == 2
 
 
 def test_null_arguments_are_rejected(B):

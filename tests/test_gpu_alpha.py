@@ -99,21 +99,37 @@ def test_alpha_shifted_solve_uses_scaled_shifts(pd):
 LOOP_CASES = [(2, 1e-4), (1, 1e-6), (2, 1.0), (1, 1e-2)]
 
 
+def _shifted_condition(P, alpha):
+    """max_k kappa_2(A_k) over the shifted systems A_k = (1 - pi_k) I + tau K of Algorithm 3."""
+    pi, _, _ = R.alpha_quantities(P.nt, alpha)
+    K = R.k_dense(P)
+    eye = np.eye(K.shape[0])
+    return max(np.linalg.cond((1.0 - pi[k]) * eye + P.tau * K) for k in range(P.nt // 2 + 1))
+
+
+def _variant_bound(P, alpha):
+    """First-order rounding bound of a fixed-loop variant computed in FP64, on either side:
+    each shifted solve returns its frequency component with a relative error of about
+    kappa(A_k) eps, and the back transform D_alpha^{-1} F^{-1} amplifies relative errors by
+    up to kappa(F D_alpha) = alpha^{-(l-1)/l} (Sec. 4).  So the GPU and the oracle may each
+    lie kappa(F D_alpha) max_k kappa(A_k) eps from the exact variant (measured: 0.002 to 0.03
+    of that, on advection-diffusion with kappa(A_k) up to 7e3 and on 2D heat)."""
+    return alpha ** (-(P.nt - 1) / P.nt) * _shifted_condition(P, alpha) * np.finfo(np.float64).eps
+
+
 @pytest.mark.parametrize("loops,alpha", LOOP_CASES)
 def test_fixed_loop_variants_match_oracle(pd, loops, alpha):
     """loops = 2 (x_m = b) and loops = 1 (U = U_1) in FP64 equal the oracle's variants within
-    the FP64 bar scaled by the conditioning the alpha-scaling adds, 1e-12 kappa(F D_alpha),
-    and, where a variant is far from the exact solution, ten times closer to it than to that
-    solution; they cost exactly
-    that many parallel-in-time loops."""
+    the rounding bound kappa(F D_alpha) max_k kappa(A_k) eps (_variant_bound) and, where a
+    variant is far from the exact solution, ten times closer to it than to that solution;
+    they cost exactly that many parallel-in-time loops."""
     P = W.advdiff1d_pulse(511, 64, nu=1e-2, seed=1)
     ref, _ = R.paradiag_alpha(P, alpha, loops=loops)
     with pd.Plan.from_problem(P, precision="fp64", alpha=alpha, loops=loops, device=dev()) as plan:
         U, st = plan.solve(torch.from_numpy(P.G).to(dev()))
     U = U.cpu().numpy()
-    kappa = alpha ** (-(P.nt - 1) / P.nt)
     err = R.rel_err(U, ref)
-    assert err <= 1e-12 * kappa, (err, st)
+    assert err <= _variant_bound(P, alpha), (err, _variant_bound(P, alpha), st)
     gap = R.rel_err(ref, R.be_solve(P))  # how far the variant is from the exact solve
     if gap > 1e-9:  # well above FP64 rounding here: the GPU computes the variant, not the exact solve
         assert err <= 0.1 * gap, (err, gap)
@@ -157,11 +173,10 @@ def test_one_loop_residual_scales_with_alpha(pd):
 @pytest.mark.parametrize("loops,alpha", [(2, 1e-2), (1, 1e-2)])
 def test_fixed_loop_variants_in_2d(pd, loops, alpha):
     """The fixed-loop variants on the 2D path (DST along y, then the same loops): 2D heat,
-    15 x 15, against the oracle's variant within 1e-12 kappa(F D_alpha)."""
+    15 x 15, against the oracle's variant within the rounding bound of _variant_bound."""
     P = W.heat2d_smooth(15, 16, T=0.1, seed=2)
     ref, _ = R.paradiag_alpha(P, alpha, loops=loops)
     with pd.Plan.from_problem(P, precision="fp64", alpha=alpha, loops=loops, device=dev()) as plan:
         U, st = plan.solve(torch.from_numpy(P.G).to(dev()))
-    kappa = alpha ** (-(P.nt - 1) / P.nt)
-    assert R.rel_err(U.cpu().numpy(), ref) <= 1e-12 * kappa, st
+    assert R.rel_err(U.cpu().numpy(), ref) <= _variant_bound(P, alpha), st
     assert st["pint_loops"] == loops

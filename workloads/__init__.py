@@ -12,6 +12,8 @@ from .gen import (  # noqa: F401
     Problem,
     heat1d_operator,
     advdiff1d_operator,
+    advdiff1d_centred_operator,
+    advdiff1d_centred,
     heat2d_axis_operator,
     heat1d_127x64,
     heat1d_1023x1024,

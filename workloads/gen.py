@@ -144,6 +144,20 @@ def advdiff1d_operator(n: int, a: float, nu: float):
     return lo, diag, up
 
 
+def advdiff1d_centred_operator(n: int, a: float, nu: float):
+    """K for u_t + a u_x = nu u_xx with centred differences for both terms (the discretisation
+    of the paper's Sec. 6.2 example, in 1D): nu tridiag(-1,2,-1)/h^2 + (a/(2h)) tridiag(-1,0,1).
+    Weakly diagonally dominant exactly when the cell Peclet number |a| h / nu is at most 2."""
+    h = 1.0 / (n + 1)
+    d = nu / (h * h)
+    lo = np.full(n, -d - a / (2.0 * h))
+    diag = np.full(n, 2.0 * d)
+    up = np.full(n, -d + a / (2.0 * h))
+    lo[0] = 0.0
+    up[-1] = 0.0
+    return lo, diag, up
+
+
 def build_rhs(u0: np.ndarray, f, tau: float, m_diag=None) -> np.ndarray:
     """Right-hand side G of the all-at-once system (eq. 2) from an initial value and a forcing.
 
@@ -254,6 +268,24 @@ def advdiff1d_pulse(n: int = 4095, nt: int = 2048, T: float = 1.0, seed: int = 0
                    k_lo=lo, k_diag=diag, k_up=up, G=G, seed=seed,
                    recipe="1D adv-diff a=1 nu=1e-3 upwind, Gaussian pulse + N(0,1e-3) noise",
                    extra={"a": a, "nu": nu})
+
+
+def advdiff1d_centred(n: int = 255, nt: int = 64, T: float = 1.0, peclet: float = 1.5, nu: float = 1e-2,
+                      seed: int = 0) -> Problem:
+    """1D advection-diffusion with centred advection at cell Peclet number `peclet`
+    (a = peclet nu / h), f = 0, u0 = Gaussian pulse at x = 0.3 (std 0.05) + N(0, 1e-3) noise."""
+    rng = SplitMix64(seed)
+    h = 1.0 / (n + 1)
+    a = peclet * nu / h
+    lo, diag, up = advdiff1d_centred_operator(n, a, nu)
+    x = _grid(n)
+    u0 = np.exp(-((x - 0.3) ** 2) / (2 * 0.05 ** 2)) + rng.normals(n, 1e-3)
+    tau = T / nt
+    G = build_rhs(u0, np.zeros((nt, n)), tau)
+    return Problem(name=f"advdiff1d_centred_n{n}_nt{nt}_pe{peclet:g}", dim=1, nx=n, ny=1, nt=nt, T=T, tau=tau,
+                   k_lo=lo, k_diag=diag, k_up=up, G=G, seed=seed,
+                   recipe=f"1D adv-diff, centred advection at cell Peclet {peclet:g}, nu={nu:g}, Gaussian pulse",
+                   extra={"a": a, "nu": nu, "peclet": peclet})
 
 
 def random_tridiag_problem(n: int, nt: int, T: float = 1.0, seed: int = 0,
