@@ -195,6 +195,13 @@ typedef struct pd_stats {
   int32_t sweep_krylov_iters[16];        /* m of Algorithm 2 */
   double sweep_krylov_rel_resnorm[16];   /* eq. (13) residual / ||b|| at exit */
   double sweep_rel_update[16];           /* ||delta_s||_F / ||delta_0||_F */
+  /* PD_MIXED: 1 if the zero frequency (the shifted system (1 - alpha^{1/l}) I + tau K) was
+     solved in FP64 inside the binary32 loops, which the plan chooses when J_l's
+     zero-frequency term is large: zero_freq_weight = ||(l A_0)^{-1}||_inf (estimated) > 4,
+     about 1 / (T lambda_min(K)) for Algorithm 1 (Theorem 3.1), where binary32 solves of A_0
+     would keep refinement from contracting */
+  int32_t zero_freq_fp64;
+  double zero_freq_weight;
 } pd_stats;
 
 typedef struct pd_plan pd_plan;

@@ -88,6 +88,8 @@ class PdStats(ctypes.Structure):
         ("sweep_krylov_iters", ctypes.c_int32 * 16),
         ("sweep_krylov_rel_resnorm", ctypes.c_double * 16),
         ("sweep_rel_update", ctypes.c_double * 16),
+        ("zero_freq_fp64", ctypes.c_int32),
+        ("zero_freq_weight", ctypes.c_double),
     ]
 
     def as_dict(self):

@@ -127,12 +127,12 @@ __device__ void r2c_store(const cpx<T> *buf, int n, int logn, int64_t x0, int64_
 // Sum of squares of the transformed data (per thread: ss), reduced over the launch: each
 // CTA stores its partial, and the last CTA to finish (no CTA waits for another) adds the
 // partials in a fixed order and stores the square root into *rn.dst.
-__device__ void rhs_norm_finish(double ss, const RhsNorm &rn) {
+__device__ void rhs_norm_finish(float ss, const RhsNorm &rn) {
   __shared__ double red[32];
   __shared__ int last;
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
-  ss = warp_sum(ss);
-  if (l == 0) red[w] = ss;
+  ss = warp_sum(ss);  // binary32 within a warp (a reference scale; FP64 adds cost GB300's FP64 pipe)
+  if (l == 0) red[w] = (double)ss;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
@@ -156,6 +156,189 @@ __device__ void rhs_norm_finish(double ss, const RhsNorm &rn) {
     *rn.dst = sqrt(s2);
     *rn.counter = 0;
   }
+}
+
+// ---- Radix-16 first stage in registers (series of n >= 16 points) -------------------
+// With bit-reversed input, the first four DIT stages (half-spans 1..8) act within blocks of
+// 16 consecutive positions: block g holds the times r + i n/16, r = bitrev_{L-4}(g) (i =
+// 0..15, bit-reversed), and after those stages their natural-order 16-point DFT.  A thread
+// therefore loads a block's 16 time samples straight from global memory, transforms them
+// in registers (dft16) and writes the block to shared memory; fft_smem16 runs the
+// remaining stages.  In shared memory a series keeps one pad slot after every 16 values
+// (element i at pz(i) = i + i/16) and series are series_stride16(n) = 2 (mod 16) complex
+// values apart, so that the block writes (lanes over column pairs and blocks), the
+// butterflies of the later stages and the column-wise reads of the output are free of
+// bank conflicts.
+__host__ __device__ inline int pz(int i) { return i + (i >> 4); }
+__host__ __device__ inline int series_stride16(int n) {
+  const int s0 = n + n / 16;
+  return s0 + (((2 - s0) % 16) + 16) % 16;
+}
+
+// X[k] = sum_i x[i] w^{ik}, w = exp(-2 pi i / 16), in place, natural order in and out:
+// radix-4 over i = 4 i1 + i2 (i1 first), twiddles w^{i2 k1}, radix-4 over i2.
+template <typename T>
+__device__ __forceinline__ void radix4_fwd(cpx<T> &a0, cpx<T> &a1, cpx<T> &a2, cpx<T> &a3) {
+  const cpx<T> t0 = add(a0, a2), t1 = sub(a0, a2), t2 = add(a1, a3), t3 = sub(a1, a3);
+  const cpx<T> mt3 = mk<T>(t3.y, -t3.x);  // -i t3
+  a0 = add(t0, t2);
+  a2 = sub(t0, t2);
+  a1 = add(t1, mt3);
+  a3 = sub(t1, mt3);
+}
+template <typename T>
+__device__ __forceinline__ cpx<T> w16(int m) {  // w^m for the products m of i2, k1 < 4
+  constexpr double c = 0.92387953251128675613;  // cos(pi/8)
+  constexpr double s = 0.38268343236508977173;  // sin(pi/8)
+  constexpr double r = 0.70710678118654752440;  // cos(pi/4)
+  switch (m) {
+    case 1: return mk<T>((T)c, (T)-s);
+    case 2: return mk<T>((T)r, (T)-r);
+    case 3: return mk<T>((T)s, (T)-c);
+    case 4: return mk<T>(T(0), T(-1));
+    case 6: return mk<T>((T)-r, (T)-r);
+    case 9: return mk<T>((T)-c, (T)s);
+    default: return mk<T>(T(1), T(0));
+  }
+}
+template <typename T>
+__device__ __forceinline__ void dft16(cpx<T> (&x)[16]) {
+#pragma unroll
+  for (int i2 = 0; i2 < 4; ++i2) radix4_fwd(x[i2], x[4 + i2], x[8 + i2], x[12 + i2]);  // x[4 k1 + i2]
+#pragma unroll
+  for (int k1 = 1; k1 < 4; ++k1)
+#pragma unroll
+    for (int i2 = 1; i2 < 4; ++i2) x[4 * k1 + i2] = mul(w16<T>(i2 * k1), x[4 * k1 + i2]);
+  cpx<T> y[16];
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    cpx<T> b0 = x[4 * k1], b1 = x[4 * k1 + 1], b2 = x[4 * k1 + 2], b3 = x[4 * k1 + 3];
+    radix4_fwd(b0, b1, b2, b3);
+    y[k1] = b0;
+    y[k1 + 4] = b1;
+    y[k1 + 8] = b2;
+    y[k1 + 12] = b3;
+  }
+#pragma unroll
+  for (int k = 0; k < 16; ++k) x[k] = y[k];
+}
+
+// The DIT stages of half-span 16 and up (the radix-16 first stage done), on series held
+// with pz padding, series S apart.  Same butterflies and twiddles as fft_smem.
+template <typename T>
+__device__ void fft_smem16(cpx<T> *buf, int n, int logn, int nseries, int S, const cpx<T> *__restrict__ tw) {
+  int s = 4;
+  const int lq = logn - 2;
+  while (s + 1 < logn) {  // radix-4 pass = DIT stages with half-spans h and 2h
+    const int h = 1 << s;
+    const int total = nseries << lq;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+      const int ser = idx >> lq;
+      const int q = idx & ((1 << lq) - 1);
+      const int j = q & (h - 1);
+      const int base = ((q >> s) << (s + 2)) + j;
+      cpx<T> *p = buf + (size_t)ser * S;
+      const cpx<T> w1 = tw[j << (logn - s - 1)];
+      const cpx<T> w2 = tw[j << (logn - s - 2)];
+      const int i0 = pz(base), i1 = pz(base + h), i2 = pz(base + 2 * h), i3 = pz(base + 3 * h);
+      cpx<T> x0 = p[i0], x1 = p[i1], x2 = p[i2], x3 = p[i3];
+      cpx<T> t1 = mul(w1, x1), t3 = mul(w1, x3);
+      cpx<T> a0 = add(x0, t1), a1 = sub(x0, t1), a2 = add(x2, t3), a3 = sub(x2, t3);
+      cpx<T> t2 = mul(w2, a2);
+      cpx<T> u = mul(w2, a3);
+      cpx<T> mu = mk<T>(u.y, -u.x);  // omega_{4h}^{j+h} a3 = -i * (omega_{4h}^j a3)
+      p[i0] = add(a0, t2);
+      p[i2] = sub(a0, t2);
+      p[i1] = add(a1, mu);
+      p[i3] = sub(a1, mu);
+    }
+    __syncthreads();
+    s += 2;
+  }
+  if (s < logn) {  // last radix-2 stage, half-span h = n/2
+    const int h = 1 << s;
+    const int lh = logn - 1;
+    const int total = nseries << lh;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+      const int ser = idx >> lh;
+      const int b = idx & ((1 << lh) - 1);
+      const int j = b & (h - 1);
+      const int i0 = ((b >> s) << (s + 1)) + j;
+      cpx<T> *p = buf + (size_t)ser * S;
+      const cpx<T> w = tw[j << (logn - s - 1)];
+      const int a = pz(i0), c = pz(i0 + h);
+      cpx<T> x0 = p[a], x1 = p[c];
+      cpx<T> t = mul(w, x1);
+      p[a] = add(x0, t);
+      p[c] = sub(x0, t);
+    }
+    __syncthreads();
+  }
+}
+
+// r2c_store on the padded layout
+template <typename T, int TX>
+__device__ void r2c_store16(const cpx<T> *buf, int n, int64_t x0, int64_t ncols, cpx<T> *__restrict__ S, int64_t lds,
+                            int SS) {
+  const int nf = (n >> 1) + 1;
+  const int tot2 = nf * TX;
+  for (int idx = threadIdx.x; idx < tot2; idx += blockDim.x) {
+    const int k = idx / TX;
+    const int c = idx - k * TX;
+    const int64_t col = x0 + c;
+    if (col >= ncols) continue;
+    const cpx<T> *z = buf + (size_t)(c >> 1) * SS;
+    const cpx<T> zk = z[pz(k)], zm = z[pz((n - k) & (n - 1))];
+    cpx<T> r;
+    if ((c & 1) == 0) {
+      r = mk<T>(T(0.5) * (zk.x + zm.x), T(0.5) * (zk.y - zm.y));
+    } else {
+      r = mk<T>(T(0.5) * (zk.y + zm.y), T(-0.5) * (zk.x - zm.x));
+    }
+    S[(int64_t)k * lds + col] = r;
+  }
+}
+
+// Forward DFT of TX columns per CTA (n >= 16): each thread takes a (column pair, block)
+// item: loads the block's 16 time samples of both columns (packed z = a + i b), dft16,
+// writes the block; then the later stages and the separated half spectra.
+template <typename T, typename Tin, int TX>
+__global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512)
+    k_fft_r2c16(const Tin *__restrict__ X, int64_t ldx, int64_t ncols, int n, int logn, const cpx<T> *__restrict__ tw,
+                cpx<T> *__restrict__ S, int64_t lds, const T *__restrict__ rs, RhsNorm rn) {
+  grid_dep_wait();
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cpx<T> *buf = reinterpret_cast<cpx<T> *>(smraw);
+  constexpr int NP = TX / 2;
+  const int64_t x0 = (int64_t)blockIdx.x * TX;
+  const int SS = series_stride16(n), nb = n >> 4, lb = logn - 4;
+  T ss = T(0);
+  for (int it = threadIdx.x; it < NP * nb; it += blockDim.x) {
+    const int p = it % NP, g = it / NP;
+    const int r = bitrev(g, lb);
+    const int64_t ca = x0 + 2 * p, cb = ca + 1;
+    const bool va = ca < ncols, vb = cb < ncols;
+    cpx<T> z[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int64_t j = r + i * nb;
+      const Tin *row = X + j * ldx;
+      z[i] = mk<T>(va ? (T)row[ca] : T(0), vb ? (T)row[cb] : T(0));
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      ss += z[i].x * z[i].x + z[i].y * z[i].y;
+      if (rs) z[i] = scal(rs[r + i * nb], z[i]);
+    }
+    dft16(z);
+    cpx<T> *blk = buf + (size_t)p * SS + 17 * g;  // pz(16 g + k) = 17 g + k
+#pragma unroll
+    for (int k = 0; k < 16; ++k) blk[k] = z[k];
+  }
+  __syncthreads();
+  fft_smem16<T>(buf, n, logn, NP, SS, tw);
+  r2c_store16<T, TX>(buf, n, x0, ncols, S, lds, SS);
+  if (rn.part) rhs_norm_finish((float)ss, rn);
 }
 
 template <typename T, typename Tin, int TX>
@@ -194,7 +377,7 @@ __global__ void __launch_bounds__(kFftMaxThreads) k_fft_r2c(const Tin *__restric
   __syncthreads();
   fft_smem<T>(buf, n, logn, TX >> 1, tw);
   r2c_store<T, TX>(buf, n, logn, x0, ncols, S, lds);
-  if (rn.part) rhs_norm_finish((double)ss, rn);
+  if (rn.part) rhs_norm_finish((float)ss, rn);
 }
 
 // Same transform of the 1D FP64 residual r = G_t + u_{t-1} - (I + tau K) u_t, formed
@@ -255,12 +438,12 @@ __global__ void __launch_bounds__(kFftMaxThreads, 2) k_fft_r2c_res(const double 
   __syncthreads();
   fft_smem<T>(buf, n, logn, TX >> 1, tw);
   r2c_store<T, TX>(buf, n, logn, x0, ncols, S, lds);
-  if (rn.part) rhs_norm_finish((double)ss, rn);
+  if (rn.part) rhs_norm_finish((float)ss, rn);
 }
 
 // Inverse: Z[k] = A[k] + i B[k] over the full spectrum (A[n-k] = conj A[k]);
 // z = IDFT(Z) = conj(DFT(conj Z)) / n; column 2p = Re z, column 2p+1 = Im z.
-template <typename T, int TX>
+template <typename T, int TX, bool R16>
 __global__ void __launch_bounds__(256) k_fft_c2r(const cpx<T> *__restrict__ S, int64_t lds, int64_t ncols,
                                                  int n, int logn, const cpx<T> *__restrict__ tw,
                                                  void *__restrict__ out, int64_t ldo, int mode,
@@ -273,37 +456,62 @@ __global__ void __launch_bounds__(256) k_fft_c2r(const cpx<T> *__restrict__ S, i
   const int64_t x0 = (int64_t)blockIdx.x * TX;
   const int np = TX >> 1;
   const int half = n >> 1;
-  // each stored row kk <= n/2 is loaded once and fills both Z[kk] and Z[n - kk]
-  const int total = (half + 1) * np;
-  for (int i0 = threadIdx.x; i0 < total; i0 += kLoadBatch * blockDim.x) {
-    cpx<T> A[kLoadBatch], B[kLoadBatch];
-#pragma unroll
-    for (int u = 0; u < kLoadBatch; ++u) {
-      const int idx = i0 + u * (int)blockDim.x;
-      const int kk = idx / np;
-      const int p = idx - kk * np;
+  if constexpr (R16) {  // radix-16 first stage in registers (see k_fft_r2c16)
+    const int SS = series_stride16(n), nb = n >> 4, lb = logn - 4;
+    for (int it = threadIdx.x; it < np * nb; it += blockDim.x) {
+      const int p = it % np, g = it / np;
+      const int r = bitrev(g, lb);
       const int64_t ca = x0 + 2 * p, cb = ca + 1;
-      A[u] = mk<T>(T(0), T(0));
-      B[u] = mk<T>(T(0), T(0));
-      if (idx < total && ca < ncols) A[u] = S[(int64_t)kk * lds + ca];
-      if (idx < total && cb < ncols) B[u] = S[(int64_t)kk * lds + cb];
-    }
+      cpx<T> z[16];
 #pragma unroll
-    for (int u = 0; u < kLoadBatch; ++u) {
-      const int idx = i0 + u * (int)blockDim.x;
-      if (idx < total) {
+      for (int i = 0; i < 16; ++i) {
+        const int idx = r + i * nb;
+        const int kk = idx <= half ? idx : n - idx;
+        const cpx<T> A = ca < ncols ? S[(int64_t)kk * lds + ca] : mk<T>(T(0), T(0));
+        const cpx<T> B = cb < ncols ? S[(int64_t)kk * lds + cb] : mk<T>(T(0), T(0));
+        // conj(A + i B) at kk <= n/2; the conjugate half at n - kk
+        z[i] = idx <= half ? mk<T>(A.x - B.y, -(A.y + B.x)) : mk<T>(A.x + B.y, A.y - B.x);
+      }
+      dft16(z);
+      cpx<T> *blk = buf + (size_t)p * SS + 17 * g;
+#pragma unroll
+      for (int k = 0; k < 16; ++k) blk[k] = z[k];
+    }
+    __syncthreads();
+    fft_smem16<T>(buf, n, logn, np, SS, tw);
+  } else {
+    // each stored row kk <= n/2 is loaded once and fills both Z[kk] and Z[n - kk]
+    const int total = (half + 1) * np;
+    for (int i0 = threadIdx.x; i0 < total; i0 += kLoadBatch * blockDim.x) {
+      cpx<T> A[kLoadBatch], B[kLoadBatch];
+#pragma unroll
+      for (int u = 0; u < kLoadBatch; ++u) {
+        const int idx = i0 + u * (int)blockDim.x;
         const int kk = idx / np;
         const int p = idx - kk * np;
-        cpx<T> *ser = buf + (size_t)p * series_stride(n);
-        // conj(A + i B) = (A.x - B.y) - i (A.y + B.x); at n - kk the conjugate half
-        // gives (A.x + B.y) + i (A.y - B.x)
-        ser[bitrev(kk, logn)] = mk<T>(A[u].x - B[u].y, -(A[u].y + B[u].x));
-        if (kk > 0 && kk < half) ser[bitrev(n - kk, logn)] = mk<T>(A[u].x + B[u].y, A[u].y - B[u].x);
+        const int64_t ca = x0 + 2 * p, cb = ca + 1;
+        A[u] = mk<T>(T(0), T(0));
+        B[u] = mk<T>(T(0), T(0));
+        if (idx < total && ca < ncols) A[u] = S[(int64_t)kk * lds + ca];
+        if (idx < total && cb < ncols) B[u] = S[(int64_t)kk * lds + cb];
+      }
+#pragma unroll
+      for (int u = 0; u < kLoadBatch; ++u) {
+        const int idx = i0 + u * (int)blockDim.x;
+        if (idx < total) {
+          const int kk = idx / np;
+          const int p = idx - kk * np;
+          cpx<T> *ser = buf + (size_t)p * series_stride(n);
+          // conj(A + i B) = (A.x - B.y) - i (A.y + B.x); at n - kk the conjugate half
+          // gives (A.x + B.y) + i (A.y - B.x)
+          ser[bitrev(kk, logn)] = mk<T>(A[u].x - B[u].y, -(A[u].y + B[u].x));
+          if (kk > 0 && kk < half) ser[bitrev(n - kk, logn)] = mk<T>(A[u].x + B[u].y, A[u].y - B[u].x);
+        }
       }
     }
+    __syncthreads();
+    fft_smem<T>(buf, n, logn, np, tw);
   }
-  __syncthreads();
-  fft_smem<T>(buf, n, logn, np, tw);
   T inv_n = T(1) / T(n);
   if (mex) {  // batched plans: undo the problem's 2^mex scaling (every element a thread
               // writes lies in column x0 + threadIdx.x % TX)
@@ -329,7 +537,8 @@ __global__ void __launch_bounds__(256) k_fft_c2r(const cpx<T> *__restrict__ S, i
       const int c = idx - j * TX;
       const int64_t col = x0 + c;
       if (idx >= tot2 || col >= ncols) continue;
-      const cpx<T> r = buf[(size_t)(c >> 1) * series_stride(n) + j];
+      const cpx<T> r = R16 ? buf[(size_t)(c >> 1) * series_stride16(n) + pz(j)]
+                           : buf[(size_t)(c >> 1) * series_stride(n) + j];
       const T sc = rsi ? inv_n * rsi[j] : inv_n;
       const T v = ((c & 1) == 0) ? r.x * sc : -r.y * sc;
       const int64_t o = (int64_t)j * ldo + col;
@@ -400,7 +609,7 @@ __global__ void __launch_bounds__(256) k_fft_c2r(const cpx<T> *__restrict__ S, i
 // Orthonormal DST-I along y via a length N = 2(ny+1) complex FFT of the odd
 // extension, two x-columns packed per series (a + i b):
 //   DST_l(a) = -Im Z[l] / 2,  DST_l(b) = Re Z[l] / 2,  scaled by sqrt(2/(ny+1)).
-template <typename Tin, typename Tout, typename T, int TX>
+template <typename Tin, typename Tout, typename T, int TX, bool R16>
 __global__ void __launch_bounds__(256) k_dst_y(const Tin *__restrict__ X, Tout *__restrict__ Y, int64_t ny,
                                                int64_t nx, int N, int logN,
                                                const cpx<T> *__restrict__ tw, T scale, int mode) {
@@ -413,35 +622,62 @@ __global__ void __launch_bounds__(256) k_dst_y(const Tin *__restrict__ X, Tout *
   const Tin *Xt = X + t * ny * nx;
   Tout *Yt = Y + t * ny * nx;
   const int np = TX >> 1;
-  // the odd extension: entries 0 and ny + 1 = N/2 are zero (bit-reversed slots 0 and 1),
-  // the scatter below writes the rest
-  for (int idx = threadIdx.x; idx < 2 * np; idx += blockDim.x)
-    buf[(size_t)(idx >> 1) * series_stride(N) + bitrev((idx & 1) ? (N >> 1) : 0, logN)] = mk<T>(T(0), T(0));
   const int total = (int)ny * TX;
-  for (int i0 = threadIdx.x; i0 < total; i0 += kLoadBatch * blockDim.x) {
-    T v[kLoadBatch];
+  if constexpr (R16) {  // radix-16 first stage in registers (see k_fft_r2c16)
+    const int SS = series_stride16(N), nb = N >> 4, lb = logN - 4, half = N >> 1;
+    for (int it = threadIdx.x; it < np * nb; it += blockDim.x) {
+      const int p = it % np, g = it / np;
+      const int r = bitrev(g, lb);
+      const int64_t ca = x0 + 2 * p, cb = ca + 1;
+      cpx<T> z[16];
 #pragma unroll
-    for (int u = 0; u < kLoadBatch; ++u) {
-      const int idx = i0 + u * (int)blockDim.x;
-      const int y = idx / TX;
-      const int64_t col = x0 + (idx - y * TX);
-      v[u] = (idx < total && col < nx) ? (T)Xt[(int64_t)y * nx + col] : T(0);
-    }
+      for (int i = 0; i < 16; ++i) {
+        // odd extension of length N = 2 (ny + 1): 0 at 0 and N/2, x_{idx-1} below N/2,
+        // -x_{N-idx-1} above
+        const int idx = r + i * nb;
+        const bool zero = idx == 0 || idx == half;
+        const int y = idx < half ? idx - 1 : N - idx - 1;
+        const T sg = idx < half ? T(1) : T(-1);
+        const Tin *row = Xt + (int64_t)(zero ? 0 : y) * nx;
+        z[i] = mk<T>((!zero && ca < nx) ? sg * (T)row[ca] : T(0), (!zero && cb < nx) ? sg * (T)row[cb] : T(0));
+      }
+      dft16(z);
+      cpx<T> *blk = buf + (size_t)p * SS + 17 * g;
 #pragma unroll
-    for (int u = 0; u < kLoadBatch; ++u) {
-      const int idx = i0 + u * (int)blockDim.x;
-      if (idx >= total) continue;
-      const int y = idx / TX;
-      const int c = idx - y * TX;
-      cpx<T> *ser = buf + (size_t)(c >> 1) * series_stride(N);
-      T *pos = reinterpret_cast<T *>(&ser[bitrev(y + 1, logN)]);
-      T *neg = reinterpret_cast<T *>(&ser[bitrev(N - (y + 1), logN)]);
-      pos[c & 1] = v[u];
-      neg[c & 1] = -v[u];
+      for (int k = 0; k < 16; ++k) blk[k] = z[k];
     }
+    __syncthreads();
+    fft_smem16<T>(buf, N, logN, np, SS, tw);
+  } else {
+    // the odd extension: entries 0 and ny + 1 = N/2 are zero (bit-reversed slots 0 and 1),
+    // the scatter below writes the rest
+    for (int idx = threadIdx.x; idx < 2 * np; idx += blockDim.x)
+      buf[(size_t)(idx >> 1) * series_stride(N) + bitrev((idx & 1) ? (N >> 1) : 0, logN)] = mk<T>(T(0), T(0));
+    for (int i0 = threadIdx.x; i0 < total; i0 += kLoadBatch * blockDim.x) {
+      T v[kLoadBatch];
+#pragma unroll
+      for (int u = 0; u < kLoadBatch; ++u) {
+        const int idx = i0 + u * (int)blockDim.x;
+        const int y = idx / TX;
+        const int64_t col = x0 + (idx - y * TX);
+        v[u] = (idx < total && col < nx) ? (T)Xt[(int64_t)y * nx + col] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < kLoadBatch; ++u) {
+        const int idx = i0 + u * (int)blockDim.x;
+        if (idx >= total) continue;
+        const int y = idx / TX;
+        const int c = idx - y * TX;
+        cpx<T> *ser = buf + (size_t)(c >> 1) * series_stride(N);
+        T *pos = reinterpret_cast<T *>(&ser[bitrev(y + 1, logN)]);
+        T *neg = reinterpret_cast<T *>(&ser[bitrev(N - (y + 1), logN)]);
+        pos[c & 1] = v[u];
+        neg[c & 1] = -v[u];
+      }
+    }
+    __syncthreads();
+    fft_smem<T>(buf, N, logN, np, tw);
   }
-  __syncthreads();
-  fft_smem<T>(buf, N, logN, np, tw);
   for (int i0 = threadIdx.x; i0 < total; i0 += kLoadBatch * blockDim.x) {
     Tout old[kLoadBatch];  // Y before the update (mode 1)
 #pragma unroll
@@ -458,7 +694,8 @@ __global__ void __launch_bounds__(256) k_dst_y(const Tin *__restrict__ X, Tout *
       const int c = idx - l * TX;
       const int64_t col = x0 + c;
       if (idx >= total || col >= nx) continue;
-      const cpx<T> z = buf[(size_t)(c >> 1) * series_stride(N) + l + 1];
+      const cpx<T> z = R16 ? buf[(size_t)(c >> 1) * series_stride16(N) + pz(l + 1)]
+                           : buf[(size_t)(c >> 1) * series_stride(N) + l + 1];
       const T v = ((c & 1) == 0) ? (T(-0.5) * scale) * z.y : (T(0.5) * scale) * z.x;
       const int64_t o = (int64_t)l * nx + col;
       if (mode == 0) {
@@ -479,10 +716,25 @@ static int ilog2(int n) {
 // Columns per CTA: as many as fit ~96 KB of series (two CTAs per SM), capped,
 // then narrowed (down to 4 columns = one 32-byte sector of doubles per row) until
 // the grid covers every SM four times.
+// The radix-16 first stage serves the binary32 transforms of n >= 16 points; the FP64 ones
+// (bound by GB300's FP64 pipe, where the register stage lowered occupancy) keep the
+// in-place radix-4 passes.
+template <typename T>
+static bool use_r16(int n) {
+  return sizeof(T) == 4 && n >= 16;
+}
+// Series stride of a tile in shared memory: the radix-16 layout or n + 1.
+template <typename T>
+static int fft_sst(int n) {
+  return use_r16<T>(n) ? series_stride16(n) : series_stride(n);
+}
+// Threads of a radix-16 launch: one (column pair, block) item each, within [64, maxt].
+static int fft16_threads(int items, int maxt) { return std::max(64, std::min(maxt, (items + 31) / 32 * 32)); }
+
 template <typename T>
 static int pick_tx(int n, int cap, int64_t ncols, int req = 0) {
   const size_t budget = 96 * 1024;
-  const size_t sst = (size_t)series_stride(n);
+  const size_t sst = (size_t)fft_sst<T>(n);
   if (req) {  // the caller's choice, within the shared-memory budget of one CTA
     int tx = std::min(req, cap);
     while (tx > 2 && (size_t)(tx / 2) * sst * sizeof(cpx<T>) > 2 * budget) tx >>= 1;
@@ -509,15 +761,23 @@ void launch_fft_r2c(Ctx &c, const Tin *X, int64_t ldx, int64_t ncols, int n, con
   const RhsNorm rn = rnp ? *rnp : RhsNorm{nullptr, nullptr, nullptr};
   const int logn = ilog2(n);
   const int TX = pick_tx<T>(n, sizeof(T) == 8 ? 8 : 16, ncols, c.fft_cols);
-  const size_t smem = (size_t)(TX / 2) * series_stride(n) * sizeof(cpx<T>);
+  const size_t smem = (size_t)(TX / 2) * fft_sst<T>(n) * sizeof(cpx<T>);
   const int grid = (int)((ncols + TX - 1) / TX);
   const double bytes = (double)n * ncols * sizeof(Tin) + (double)(n / 2 + 1) * ncols * sizeof(cpx<T>);
   c.launch(sizeof(T) == 8 ? "fft_r2c_f64" : "fft_r2c_f32", bytes, [&] {
     PD_TX_DISPATCH(TX, {
-      if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_fft_r2c<T, Tin, kTX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      pdl_launch(c.pdl, k_fft_r2c<T, Tin, kTX>, dim3(grid), dim3(fft_threads(n, kTX)), smem, c.stream, X, ldx, ncols, n, logn, tw, S, lds,
-                 rs, rn);
+      if (use_r16<T>(n)) {
+        const int thr = fft16_threads((kTX / 2) * (n / 16), 512);
+        if (smem > 48 * 1024)
+          cudaFuncSetAttribute(k_fft_r2c16<T, Tin, kTX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        pdl_launch(c.pdl, k_fft_r2c16<T, Tin, kTX>, dim3(grid), dim3(thr), smem, c.stream, X, ldx, ncols, n, logn, tw,
+                   S, lds, rs, rn);
+      } else {
+        if (smem > 48 * 1024)
+          cudaFuncSetAttribute(k_fft_r2c<T, Tin, kTX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        pdl_launch(c.pdl, k_fft_r2c<T, Tin, kTX>, dim3(grid), dim3(fft_threads(n, kTX)), smem, c.stream, X, ldx, ncols,
+                   n, logn, tw, S, lds, rs, rn);
+      }
     })
   });
 }
@@ -536,8 +796,8 @@ void launch_fft_r2c_residual(Ctx &c, const double *G, const double *U, int64_t n
     PD_TX_DISPATCH(TX, {
       if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_fft_r2c_res<T, kTX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      pdl_launch(c.pdl, k_fft_r2c_res<T, kTX>, dim3(grid), dim3(fft_threads(n, kTX)), smem, c.stream, G, U, ncols, n, logn, rxl, rxd, rxu,
-                 tw, S, lds, rs, mex, mnx, rn);
+      pdl_launch(c.pdl, k_fft_r2c_res<T, kTX>, dim3(grid), dim3(fft_threads(n, kTX)), smem, c.stream, G, U, ncols, n,
+                 logn, rxl, rxd, rxu, tw, S, lds, rs, mex, mnx, rn);
     })
   });
 }
@@ -550,18 +810,25 @@ void launch_fft_c2r(Ctx &c, const cpx<T> *S, int64_t lds, int64_t ncols, int n, 
   if (finp && norm_part) fin = *finp;
   const int logn = ilog2(n);
   const int TX = pick_tx<T>(n, sizeof(T) == 8 ? 8 : 16, ncols, c.fft_cols);
-  const size_t smem = (size_t)(TX / 2) * series_stride(n) * sizeof(cpx<T>);
+  const size_t smem = (size_t)(TX / 2) * fft_sst<T>(n) * sizeof(cpx<T>);
   const int grid = (int)((ncols + TX - 1) / TX);
   if (nparts) *nparts = grid;
   const double obytes = (mode == 2) ? 4.0 : (mode == 1 ? 16.0 : 8.0);
   const double bytes = (double)(n / 2 + 1) * ncols * sizeof(cpx<T>) + (double)n * ncols * obytes;
   c.launch(sizeof(T) == 8 ? "fft_c2r_f64" : "fft_c2r_f32", bytes, [&] {
     PD_TX_DISPATCH(TX, {
-      if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_fft_c2r<T, kTX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      pdl_launch(c.pdl, k_fft_c2r<T, kTX>, dim3(grid), dim3(256), smem, c.stream, S, lds, ncols, n, logn, tw, out, ldo, mode,
-                 norm_part,
-                                                         fin, rsi, colsum, mex, mnx);
+      if (use_r16<T>(n)) {
+        const int thr = fft16_threads((kTX / 2) * (n / 16), 256);
+        if (smem > 48 * 1024)
+          cudaFuncSetAttribute(k_fft_c2r<T, kTX, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        pdl_launch(c.pdl, k_fft_c2r<T, kTX, true>, dim3(grid), dim3(thr), smem, c.stream, S, lds, ncols, n, logn, tw, out,
+                   ldo, mode, norm_part, fin, rsi, colsum, mex, mnx);
+      } else {
+        if (smem > 48 * 1024)
+          cudaFuncSetAttribute(k_fft_c2r<T, kTX, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        pdl_launch(c.pdl, k_fft_c2r<T, kTX, false>, dim3(grid), dim3(256), smem, c.stream, S, lds, ncols, n, logn, tw,
+                   out, ldo, mode, norm_part, fin, rsi, colsum, mex, mnx);
+      }
     })
   });
 }
@@ -572,17 +839,25 @@ void launch_dst_y(Ctx &c, const Tin *X, Tout *Y, int64_t nt, int64_t ny, int64_t
   const int N = (int)(2 * (ny + 1));
   const int logN = ilog2(N);
   const int TX = pick_tx<T>(N, sizeof(T) == 8 ? 8 : 16, nt * nx);
-  const size_t smem = (size_t)(TX / 2) * series_stride(N) * sizeof(cpx<T>);
+  const size_t smem = (size_t)(TX / 2) * fft_sst<T>(N) * sizeof(cpx<T>);
   const int ntile = (int)((nx + TX - 1) / TX);
   const int64_t grid = nt * ntile;
   const T scale = (T)sqrt(2.0 / (double)(ny + 1));
   const double bytes = (double)nt * ny * nx * (sizeof(Tin) + sizeof(Tout) * (mode ? 2 : 1));
   c.launch(sizeof(T) == 8 ? "dst_y_f64" : "dst_y_f32", bytes, [&] {
     PD_TX_DISPATCH(TX, {
-      if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_dst_y<Tin, Tout, T, kTX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      pdl_launch(c.pdl, k_dst_y<Tin, Tout, T, kTX>, dim3((unsigned)grid), dim3(256), smem, c.stream, X, Y, ny, nx, N, logN,
-                 tw, scale, mode);
+      if (use_r16<T>(N)) {
+        if (smem > 48 * 1024)
+          cudaFuncSetAttribute(k_dst_y<Tin, Tout, T, kTX, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        pdl_launch(c.pdl, k_dst_y<Tin, Tout, T, kTX, true>, dim3((unsigned)grid), dim3(256), smem, c.stream, X, Y, ny, nx,
+                   N, logN, tw, scale, mode);
+      } else {
+        if (smem > 48 * 1024)
+          cudaFuncSetAttribute(k_dst_y<Tin, Tout, T, kTX, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
+        pdl_launch(c.pdl, k_dst_y<Tin, Tout, T, kTX, false>, dim3((unsigned)grid), dim3(256), smem, c.stream, X, Y, ny,
+                   nx, N, logN, tw, scale, mode);
+      }
     })
   });
 }

@@ -715,26 +715,49 @@ __global__ void __launch_bounds__(MAXT) k_pint(PintGeom g, PintArgs<T> a, size_t
         if (e < blen) Yk[e] = dd[e + e / M];
       }
     }
-    // 6. dots with the Krylov basis
+    // 6. dots with the Krylov basis: y_k in registers, four basis vectors per pass, and
+    // their eight partial sums (re, im) reduced over the warp together by a reduce-scatter
+    // (9 shuffles instead of 40); warp sums in the compute type (binary32 in the mixed
+    // path, where h_k itself is binary32), the per-warp partials added in FP64
     if (mdots > 0) {
       const int nw = P >> 5, w = t >> 5, l = t & 31;
-      for (int q = 0; q < mdots; ++q) {
-        T px = T(0), py = T(0);
-        const T *vq = a.V + (int64_t)q * a.ldv + off;
-        T vv[M];
+      cpx<T> yv[M];
 #pragma unroll
-        for (int i = 0; i < M; ++i) vv[i] = (t + i * P < blen) ? vq[t + i * P] : T(0);
+      for (int i = 0; i < M; ++i) {
+        const int e = t + i * P;
+        yv[i] = dd[e + e / M];  // zero beyond blen
+      }
+      const bool b4 = l & 16, b3 = l & 8, b2 = l & 4;
+      for (int q0 = 0; q0 < mdots; q0 += 4) {
+        T s8[8];
 #pragma unroll
-        for (int i = 0; i < M; ++i) {
-          const int e = t + i * P;
-          const cpx<T> y = dd[e + e / M];  // zero beyond blen
-          px += vv[i] * y.x;
-          py += vv[i] * y.y;
+        for (int j = 0; j < 8; ++j) s8[j] = T(0);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (q0 + j < mdots) {
+            const T *vq = a.V + (int64_t)(q0 + j) * a.ldv + off;
+            T vv[M];
+#pragma unroll
+            for (int i = 0; i < M; ++i) vv[i] = (t + i * P < blen) ? vq[t + i * P] : T(0);
+#pragma unroll
+            for (int i = 0; i < M; ++i) {
+              s8[2 * j] += vv[i] * yv[i].x;
+              s8[2 * j + 1] += vv[i] * yv[i].y;
+            }
+          }
         }
-        // warp sums in the compute type (binary32 in the mixed path, where h_k itself is
-        // binary32); the per-warp partials are added in FP64
-        const T sx = warp_sum(px), sy = warp_sum(py);
-        if (l == 0) red[w * mdots + q] = make_double2((double)sx, (double)sy);
+        // lane l ends with value (b4, b3, b2) of the eight, summed over the warp
+        T r4[4], r2[2];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) r4[i] = (b4 ? s8[i + 4] : s8[i]) + shfl_xor(b4 ? s8[i] : s8[i + 4], 16);
+#pragma unroll
+        for (int i = 0; i < 2; ++i) r2[i] = (b3 ? r4[i + 2] : r4[i]) + shfl_xor(b3 ? r4[i] : r4[i + 2], 8);
+        T r1 = (b2 ? r2[1] : r2[0]) + shfl_xor(b2 ? r2[0] : r2[1], 4);
+        r1 += shfl_xor(r1, 2);
+        r1 += shfl_xor(r1, 1);
+        const int vi = (b4 ? 4 : 0) | (b3 ? 2 : 0) | (b2 ? 1 : 0);
+        if ((l & 3) == 0 && q0 + (vi >> 1) < mdots)
+          reinterpret_cast<double *>(&red[w * mdots + q0 + (vi >> 1)])[vi & 1] = (double)r1;
       }
       team_sync(P, tic);
       for (int q = t; q < mdots; q += P) {
@@ -782,22 +805,23 @@ __global__ void __launch_bounds__(MAXT) k_pint(PintGeom g, PintArgs<T> a, size_t
 // still has several rows and the grid is not thousands of tiny CTAs.
 constexpr int kColB = 8;
 
-template <int CW, int RG>
-__device__ __forceinline__ double colsum_finish(double v, double (*sm)[CW + 1], int tx, int ty) {
+template <typename V, int CW, int RG>
+__device__ __forceinline__ V colsum_finish(V v, V (*sm)[CW + 1], int tx, int ty) {
+  constexpr int G = RG < 8 ? RG : 8;  // second-level groups
   sm[ty][tx] = v;
   __syncthreads();
-  double t = 0.0;
-  if (ty < 8) {
+  V t = V(0);
+  if (ty < G) {
 #pragma unroll
-    for (int i = 0; i < RG / 8; ++i) t += sm[ty * (RG / 8) + i][tx];
+    for (int i = 0; i < RG / G; ++i) t += sm[ty * (RG / G) + i][tx];
   }
   __syncthreads();
-  if (ty < 8) sm[ty][tx] = t;
+  if (ty < G) sm[ty][tx] = t;
   __syncthreads();
-  t = 0.0;
+  t = V(0);
   if (ty == 0) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) t += sm[i][tx];
+    for (int i = 0; i < G; ++i) t += sm[i][tx];
   }
   return t;  // valid for ty == 0
 }
@@ -837,7 +861,7 @@ __global__ void __launch_bounds__(CW * RG) k_acc_reduce(int nblk, int blen, int 
   double tot = 0.0;
 #pragma unroll
   for (int u = 0; u < kColB; ++u) tot += acc[u];
-  tot = colsum_finish<CW, RG>(tot, sm, tx, ty);
+  tot = colsum_finish<double, CW, RG>(tot, sm, tx, ty);
   if (ty == 0 && j < n) out[j] = extra ? tot + extra[j] : tot;
   if (tail.enabled && last_cta_done(tail.counter)) {
     init_v0_body<kTail>(out, tail.n, tail.part, tail.ld, tail.V, tail.Vf, tail.scal, tail.flags, tail.use_handle,
@@ -857,7 +881,10 @@ __global__ void __launch_bounds__(CW * RG) k_zsum(int nf, int64_t n, const cpx<T
                                                   const double *__restrict__ h0) {
   grid_dep_wait();
   const bool skip = skip_flag && *skip_flag;  // breakdown: no z (eq. 13 gives 0); the tail still decides
-  __shared__ double sm[RG][CW + 1];
+  // z only feeds the eq. (13) estimate, so the column sums stay in the compute type (FP64
+  // adds would bound this kernel on GB300's FP64 pipe); the zero-frequency lane's FP64
+  // term (h0) is added in FP64
+  __shared__ T sm[RG][CW + 1];
   extern __shared__ __align__(16) unsigned char om_raw[];
   cpx<T> *om = reinterpret_cast<cpx<T> *>(om_raw);
   const int tx = threadIdx.x % CW, ty = threadIdx.x / CW;
@@ -906,11 +933,11 @@ __global__ void __launch_bounds__(CW * RG) k_zsum(int nf, int64_t n, const cpx<T
         }
       }
     }
-    double tot = 0.0;
+    T tot = T(0);
 #pragma unroll
-    for (int u = 0; u < kColB; ++u) tot += (double)acc[u];
-    tot = colsum_finish<CW, RG>(tot, sm, tx, ty);
-    if (ty == 0 && j < n) z[j] = h0 ? tot + omega[(int64_t)memj * nf].x * h0[j] : tot;
+    for (int u = 0; u < kColB; ++u) tot += acc[u];
+    tot = colsum_finish<T, CW, RG>(tot, sm, tx, ty);
+    if (ty == 0 && j < n) z[j] = h0 ? (double)tot + omega[(int64_t)memj * nf].x * h0[j] : (double)tot;
   }
   if (tail.enabled && last_cta_done(tail.counter)) {
     project_body<kTail>(tail.n, tail.V, z, tail.tau, tail.part, tail.ld, tail.scal, tail.flags, tail.kc,
@@ -1030,7 +1057,10 @@ void launch_acc_reduce(Ctx &c, const PintGeom &g, const double *acc_part, double
   InitTail tail{};
   if (tailp) tail = *tailp;
   c.launch("acc_reduce", (double)n * g.acc_rows * 8.0 + n * 8.0, [&] {
-    if (g.acc_rows <= 256)
+    if (g.acc_rows <= 32)  // few partial rows (2D, batches): 128 columns x 4 row groups
+      pdl_launch(c.pdl, k_acc_reduce<128, 4>, dim3((int)((n + 127) / 128)), dim3(512), 0, c.stream, g.nblk, g.blen,
+                 g.acc_rows, acc_part, out, skip_flag, tail, extra);
+    else if (g.acc_rows <= 256)
       pdl_launch(c.pdl, k_acc_reduce<32, 16>, dim3((int)((n + 31) / 32)), dim3(512), 0, c.stream, g.nblk, g.blen,
                  g.acc_rows, acc_part, out, skip_flag, tail, extra);
     else

@@ -223,6 +223,8 @@ struct pd_plan {
   double *acc_part = nullptr;
   double *acc0 = nullptr, *h0 = nullptr;  // PD_MIXED: FP64 zero-frequency lane outputs (b share, h_0)
   double *fac0 = nullptr;                 // PD_MIXED: the lane's FP64 factors (per operator)
+  bool lane = false;                      // PD_MIXED: the zero frequency runs in the FP64 lane
+  double nu0 = 0.0;                       // ||(l A_0)^{-1}||_inf estimate (lane criterion)
   double2 *gpart = nullptr, *srow = nullptr, *omega = nullptr;
   double *msys_part = nullptr;
   double *norm_part = nullptr;
@@ -714,6 +716,43 @@ pd_status upload(X *dst, const X *src, size_t n, cudaStream_t s) {
 // K in the solve basis and every array derived from it (tau K in both precisions,
 // the residual coefficients, the per-problem row counts of a batch), uploaded on the
 // plan's stream.  Shared by paradiag_plan and paradiag_set_operator.
+// The binary32 path solves the zero frequency in FP64 (the lane, pint.cu) when J_l's
+// zero-frequency term gamma_0 A_0^{-1}, A_0 = (1 - alpha^{1/l}) I + tau K, is large:
+// nu_0 = ||(l A_0)^{-1}|| ~ 1 / (T lambda_min(K)) for Algorithm 1 (its eigenvalue
+// z^l / (z^l - 1) - 1, z = 1 + tau lambda_min, Theorem 3.1).  Then A_0^{-1} dominates b
+// (eq. 7) and J_l (eq. 8), and binary32 solves of A_0 (relative error kappa(A_0) eps)
+// would keep refinement from contracting.  Every other shift has |1 - pi_k| >= 2 sin(pi/l)
+// and a well-conditioned system.  nu_0 is estimated per block by FP64 Thomas solves of
+// A_0 x = 1 and A_0 x = (-1)^i (exact for M-matrices such as the heat and upwind operators,
+// whose inverses are nonnegative), the largest |x_i| over the blocks, divided by l.
+constexpr double kLaneWeight = 4.0;
+double zero_frequency_weight(const pd_plan *p, const std::vector<double> &tlo, const std::vector<double> &tdiag,
+                             const std::vector<double> &tup) {
+  const double s0 = 1.0 - p->aroot;  // 1 - pi_0
+  const int64_t nb = p->nblk, bl = p->blen;
+  std::vector<double> cp(bl), dp(bl);
+  double worst = 0.0;
+  for (int64_t b = 0; b < nb; ++b) {
+    const int64_t o = b * bl;
+    for (int sign = 0; sign < 2; ++sign) {
+      for (int64_t i = 0; i < bl; ++i) {
+        const double lo = i > 0 ? tlo[o + i] : 0.0, up = i + 1 < bl ? tup[o + i] : 0.0;
+        const double r = (sign && (i & 1)) ? -1.0 : 1.0;
+        const double m = s0 + tdiag[o + i] - (i > 0 ? lo * cp[i - 1] : 0.0);
+        cp[i] = up / m;
+        dp[i] = (r - (i > 0 ? lo * dp[i - 1] : 0.0)) / m;
+      }
+      double x = dp[bl - 1];
+      worst = std::max(worst, std::fabs(x));
+      for (int64_t i = bl - 2; i >= 0; --i) {
+        x = dp[i] - cp[i] * x;
+        worst = std::max(worst, std::fabs(x));
+      }
+    }
+  }
+  return std::isfinite(worst) ? worst / (double)p->nt : 1e300;
+}
+
 pd_status upload_operator(pd_plan *p, const pd_desc *desc) {
   pd_status st = PD_OK;
   HostOp h = build_operator(desc);
@@ -740,6 +779,10 @@ pd_status upload_operator(pd_plan *p, const pd_desc *desc) {
       ryd[i] = p->tau * h.ydiag[i];
       ryu[i] = p->tau * h.yup[i];
     }
+  if (p->precision == PD_MIXED) {
+    p->nu0 = zero_frequency_weight(p, tlo, tdiag, tup);
+    p->lane = p->nu0 > kLaneWeight;
+  }
   cudaStream_t s = p->ctx.stream;
   if ((st = upload(p->klo, h.lo.data(), nbar, s)) || (st = upload(p->kdiag, h.diag.data(), nbar, s)) ||
       (st = upload(p->kup, h.up.data(), nbar, s)) || (st = upload(p->tlo_d, tlo.data(), nbar, s)) ||
@@ -842,27 +885,28 @@ pd::PintArgs<float> base_args<float>(pd_plan *p) {
   a.tdiag = p->tdiag_f;
   a.tup = p->tup_f;
   // the zero frequency, whose shifted system carries the ill-conditioning of tau K, in FP64
-  a.k0_fp64 = 1;
+  a.k0_fp64 = p->lane ? 1 : 0;
   a.tlo_d = p->tlo_d;
   a.tdiag_d = p->tdiag_d;
   a.tup_d = p->tup_d;
   a.Vd = p->V;
-  a.fac0_in = p->fac0;
+  a.fac0_in = p->lane ? p->fac0 : nullptr;
   return a;
 }
-// FP64 zero-frequency lane outputs of the binary32 path (null for FP64 plans)
+// FP64 zero-frequency lane outputs of the binary32 path (null for FP64 plans and when the
+// lane is off)
 template <typename T>
 double *lane_acc0(pd_plan *p) {
-  return sizeof(T) == 4 ? p->acc0 : nullptr;
+  return (sizeof(T) == 4 && p->lane) ? p->acc0 : nullptr;
 }
 template <typename T>
 double *lane_h0(pd_plan *p) {
-  return sizeof(T) == 4 ? p->h0 : nullptr;
+  return (sizeof(T) == 4 && p->lane) ? p->h0 : nullptr;
 }
 
 // Factor every (k, block) shifted system of the plan (after the operator changed).
 pd_status factorize(pd_plan *p) {
-  if (p->precision == PD_MIXED) {  // the FP64 factors of the zero-frequency lane
+  if (p->precision == PD_MIXED && p->lane) {  // the FP64 factors of the zero-frequency lane
     pd::PintArgs<float> a = base_args<float>(p);
     a.fac_in = nullptr;
     a.fac0_in = nullptr;
@@ -1335,6 +1379,8 @@ pd_status solve_refined(pd_plan *p, const double *G, double *U, pd_stats &s) {
   s.krylov_rel_resnorm = sc[pd::S_SWRES + last];
   s.rel_update = sweeps > 1 ? sc[pd::S_UPD] : 0.0;
   s.graph = used ? 1 : 0;
+  s.zero_freq_fp64 = p->lane ? 1 : 0;
+  s.zero_freq_weight = p->nu0;
   if (f[pd::F_NONFIN]) return fail(PD_ERR_NONFINITE, "non-finite value met (input contains NaN/Inf?)");
   if (p->loops) {  // the variant's approximation: no convergence claim
     s.krylov_iters = s.krylov_iters_total = 0;
@@ -1490,7 +1536,9 @@ pd_status paradiag_set_operator(pd_plan *p, const pd_desc *desc) {
   }
   if (p->ctx.stream) cudaStreamSynchronize(p->ctx.stream);  // no solve may still read the old operator
   std::lock_guard<std::recursive_mutex> lk(host_mutex());
+  const bool lane_before = p->lane;
   if ((st = upload_operator(p, desc)) != PD_OK) return st;
+  if (p->lane != lane_before) drop_graph(p);  // the lane's arguments are captured in the graph
   if ((st = factorize(p)) != PD_OK) return st;
   if (p->ctx.stream && cudaStreamSynchronize(p->ctx.stream) != cudaSuccess)
     return fail(PD_ERR_CUDA, "operator factorisation failed");

@@ -95,3 +95,10 @@ def test_mixed_refinement_converges_when_j_is_ill_conditioned(pd, c):
     with pd.Plan.from_problem(P, precision="mixed", device=dev()) as plan:
         U, st = plan.solve(torch.from_numpy(P.G).to(dev()))
     assert R.rel_err(U.cpu().numpy(), R.be_solve_refined(P)) <= TOL["mixed"], st
+    # the plan's estimate of ||(l A_0)^{-1}||_inf = ||(T K)^{-1}||_inf: for K = c (-d^2/dx^2)
+    # on (0, 1) with Dirichlet ends, K^{-1} 1 = x (1 - x) / (2 c), whose maximum is 1 / (8 c)
+    # (exact for the finite-difference matrix, whose inverse is nonnegative); the FP64 lane
+    # is switched on above 4
+    w = 1.0 / (8.0 * P.T * c)
+    assert abs(st["zero_freq_weight"] - w) <= 1e-3 * w, st["zero_freq_weight"]
+    assert st["zero_freq_fp64"] == (1 if w > 4 else 0)
