@@ -174,6 +174,11 @@ typedef struct pd_desc {
   const int64_t *batch_nx;   /* host, length batch: rows of problem b, 1 <= nx_b <= nx
                                 (NULL = nx for all) */
   const double *batch_tau;   /* host, length batch: time step of problem b (NULL = tau) */
+  int32_t tune_fft_radix;    /* first stages of the time DFTs and the DST along y: 16 = one
+                                radix-16 stage in registers (n >= 16), then radix-4 passes in
+                                shared memory; 4 = radix-4 (and one radix-2) passes only;
+                                0 = built-in choice (16 for binary32 transforms of n >= 16, 4
+                                otherwise; the residual-on-load DFT always uses 4) */
 } pd_desc;
 
 /* Statistics of the last paradiag_solve / paradiag_solve_host. */

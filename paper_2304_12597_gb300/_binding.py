@@ -68,6 +68,7 @@ class PdDesc(ctypes.Structure):
         ("batch", ctypes.c_int32),
         ("batch_nx", ctypes.POINTER(ctypes.c_int64)),
         ("batch_tau", ctypes.POINTER(ctypes.c_double)),
+        ("tune_fft_radix", ctypes.c_int32),
     ]
 
 

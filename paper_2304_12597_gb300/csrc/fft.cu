@@ -719,22 +719,24 @@ static int ilog2(int n) {
 // The radix-16 first stage serves the binary32 transforms of n >= 16 points; the FP64 ones
 // (bound by GB300's FP64 pipe, where the register stage lowered occupancy) keep the
 // in-place radix-4 passes.
+// Ctx::fft_radix (pd_desc.tune_fft_radix) overrides the choice.
 template <typename T>
-static bool use_r16(int n) {
-  return sizeof(T) == 4 && n >= 16;
+static bool use_r16(const Ctx &c, int n) {
+  if (n < 16 || c.fft_radix == 4) return false;
+  return c.fft_radix == 16 || sizeof(T) == 4;
 }
 // Series stride of a tile in shared memory: the radix-16 layout or n + 1.
 template <typename T>
-static int fft_sst(int n) {
-  return use_r16<T>(n) ? series_stride16(n) : series_stride(n);
+static int fft_sst(const Ctx &c, int n) {
+  return use_r16<T>(c, n) ? series_stride16(n) : series_stride(n);
 }
 // Threads of a radix-16 launch: one (column pair, block) item each, within [64, maxt].
 static int fft16_threads(int items, int maxt) { return std::max(64, std::min(maxt, (items + 31) / 32 * 32)); }
 
 template <typename T>
-static int pick_tx(int n, int cap, int64_t ncols, int req = 0) {
+static int pick_tx(const Ctx &c, int n, int cap, int64_t ncols, int req = 0) {
   const size_t budget = 96 * 1024;
-  const size_t sst = (size_t)fft_sst<T>(n);
+  const size_t sst = (size_t)fft_sst<T>(c, n);
   if (req) {  // the caller's choice, within the shared-memory budget of one CTA
     int tx = std::min(req, cap);
     while (tx > 2 && (size_t)(tx / 2) * sst * sizeof(cpx<T>) > 2 * budget) tx >>= 1;
@@ -760,13 +762,13 @@ void launch_fft_r2c(Ctx &c, const Tin *X, int64_t ldx, int64_t ncols, int n, con
                     cpx<T> *S, int64_t lds, const T *rs, const RhsNorm *rnp) {
   const RhsNorm rn = rnp ? *rnp : RhsNorm{nullptr, nullptr, nullptr};
   const int logn = ilog2(n);
-  const int TX = pick_tx<T>(n, sizeof(T) == 8 ? 8 : 16, ncols, c.fft_cols);
-  const size_t smem = (size_t)(TX / 2) * fft_sst<T>(n) * sizeof(cpx<T>);
+  const int TX = pick_tx<T>(c, n, sizeof(T) == 8 ? 8 : 16, ncols, c.fft_cols);
+  const size_t smem = (size_t)(TX / 2) * fft_sst<T>(c, n) * sizeof(cpx<T>);
   const int grid = (int)((ncols + TX - 1) / TX);
   const double bytes = (double)n * ncols * sizeof(Tin) + (double)(n / 2 + 1) * ncols * sizeof(cpx<T>);
   c.launch(sizeof(T) == 8 ? "fft_r2c_f64" : "fft_r2c_f32", bytes, [&] {
     PD_TX_DISPATCH(TX, {
-      if (use_r16<T>(n)) {
+      if (use_r16<T>(c, n)) {
         const int thr = fft16_threads((kTX / 2) * (n / 16), 512);
         if (smem > 48 * 1024)
           cudaFuncSetAttribute(k_fft_r2c16<T, Tin, kTX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -788,7 +790,7 @@ void launch_fft_r2c_residual(Ctx &c, const double *G, const double *U, int64_t n
                              const T *rs, const int *mex, int mnx, const RhsNorm *rnp) {
   const RhsNorm rn = rnp ? *rnp : RhsNorm{nullptr, nullptr, nullptr};
   const int logn = ilog2(n);
-  const int TX = pick_tx<T>(n, sizeof(T) == 8 ? 8 : 16, ncols, c.fft_cols);
+  const int TX = pick_tx<T>(c, n, sizeof(T) == 8 ? 8 : 16, ncols, c.fft_cols);
   const size_t smem = (size_t)(TX / 2) * series_stride(n) * sizeof(cpx<T>);
   const int grid = (int)((ncols + TX - 1) / TX);
   const double bytes = (double)n * ncols * 16.0 + (double)(n / 2 + 1) * ncols * sizeof(cpx<T>);
@@ -809,15 +811,15 @@ void launch_fft_c2r(Ctx &c, const cpx<T> *S, int64_t lds, int64_t ncols, int n, 
   StepFinish fin{};
   if (finp && norm_part) fin = *finp;
   const int logn = ilog2(n);
-  const int TX = pick_tx<T>(n, sizeof(T) == 8 ? 8 : 16, ncols, c.fft_cols);
-  const size_t smem = (size_t)(TX / 2) * fft_sst<T>(n) * sizeof(cpx<T>);
+  const int TX = pick_tx<T>(c, n, sizeof(T) == 8 ? 8 : 16, ncols, c.fft_cols);
+  const size_t smem = (size_t)(TX / 2) * fft_sst<T>(c, n) * sizeof(cpx<T>);
   const int grid = (int)((ncols + TX - 1) / TX);
   if (nparts) *nparts = grid;
   const double obytes = (mode == 2) ? 4.0 : (mode == 1 ? 16.0 : 8.0);
   const double bytes = (double)(n / 2 + 1) * ncols * sizeof(cpx<T>) + (double)n * ncols * obytes;
   c.launch(sizeof(T) == 8 ? "fft_c2r_f64" : "fft_c2r_f32", bytes, [&] {
     PD_TX_DISPATCH(TX, {
-      if (use_r16<T>(n)) {
+      if (use_r16<T>(c, n)) {
         const int thr = fft16_threads((kTX / 2) * (n / 16), 256);
         if (smem > 48 * 1024)
           cudaFuncSetAttribute(k_fft_c2r<T, kTX, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -838,15 +840,15 @@ void launch_dst_y(Ctx &c, const Tin *X, Tout *Y, int64_t nt, int64_t ny, int64_t
                   int mode) {
   const int N = (int)(2 * (ny + 1));
   const int logN = ilog2(N);
-  const int TX = pick_tx<T>(N, sizeof(T) == 8 ? 8 : 16, nt * nx);
-  const size_t smem = (size_t)(TX / 2) * fft_sst<T>(N) * sizeof(cpx<T>);
+  const int TX = pick_tx<T>(c, N, sizeof(T) == 8 ? 8 : 16, nt * nx);
+  const size_t smem = (size_t)(TX / 2) * fft_sst<T>(c, N) * sizeof(cpx<T>);
   const int ntile = (int)((nx + TX - 1) / TX);
   const int64_t grid = nt * ntile;
   const T scale = (T)sqrt(2.0 / (double)(ny + 1));
   const double bytes = (double)nt * ny * nx * (sizeof(Tin) + sizeof(Tout) * (mode ? 2 : 1));
   c.launch(sizeof(T) == 8 ? "dst_y_f64" : "dst_y_f32", bytes, [&] {
     PD_TX_DISPATCH(TX, {
-      if (use_r16<T>(N)) {
+      if (use_r16<T>(c, N)) {
         if (smem > 48 * 1024)
           cudaFuncSetAttribute(k_dst_y<Tin, Tout, T, kTX, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         pdl_launch(c.pdl, k_dst_y<Tin, Tout, T, kTX, true>, dim3((unsigned)grid), dim3(256), smem, c.stream, X, Y, ny, nx,

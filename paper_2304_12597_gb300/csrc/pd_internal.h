@@ -82,6 +82,7 @@ struct Ctx {
   cudaStream_t stream = nullptr;
   bool pdl = true;   // programmatic dependent launch between consecutive kernels
   int fft_cols = 0;  // columns per CTA of the time FFTs (0 = choose per launch)
+  int fft_radix = 0;  // first stage of the FFTs: 16, 4, or 0 = built-in (fft.cu: use_r16)
   bool timing = false;
   int64_t launches = 0;
   cudaError_t err = cudaSuccess;

@@ -400,6 +400,8 @@ pd_status validate(const pd_desc *d) {
   if (d->tune_fft_cols != 0 && d->tune_fft_cols != 2 && d->tune_fft_cols != 4 && d->tune_fft_cols != 8 &&
       d->tune_fft_cols != 16)
     return fail(PD_ERR_INVALID_ARG, "tune_fft_cols must be 0, 2, 4, 8 or 16");
+  if (d->tune_fft_radix != 0 && d->tune_fft_radix != 4 && d->tune_fft_radix != 16)
+    return fail(PD_ERR_INVALID_ARG, "tune_fft_radix must be 0, 4 or 16");
   if (d->batch < 0) return fail(PD_ERR_INVALID_ARG, "batch must be >= 0");
   if (d->batch > 1) {
     if (d->dim != 1) return fail(PD_ERR_UNSUPPORTED, "batching is built for 1D problems only");
@@ -499,6 +501,7 @@ void fill_geometry(pd_plan *p, const pd_desc *d) {
   if (p->batch > 1 && !d->tune_cap_ctas)
     p->k5_grid_members = std::max(1, std::min(p->k5_grid, (2 * sms + p->batch - 1) / p->batch));
   p->ctx.fft_cols = d->tune_fft_cols;
+  p->ctx.fft_radix = d->tune_fft_radix;
   p->mass = d->m_diag != nullptr;
   {  // factors of the shifted systems: computed once per operator, read by every loop
     const size_t esz = p->precision == PD_MIXED ? sizeof(cpx<float>) : sizeof(cpx<double>);

@@ -58,6 +58,41 @@ def test_noalloc_matches_plan_entry_point_call_after_call(pd):
     _compare(pd, W.heat1d_forced(1023, 64, seed=1))
 
 
+def _periodic_last_slice(P, sweeps=8):
+    """b of eq. (7), the last slice of the periodic (circulant) solution, from the oracle's
+    sequential backward Euler: the periodic solution is the one whose start value is its own
+    final state, u_0 = u_l, the fixed point of u_l <- BE(G with u_0 = u_l)[-1] (G_1 carries
+    u_0), a contraction by ||(I + tau K)^{-l}|| = (1 + tau lambda_min)^{-l}."""
+    from oracle import reference as R
+
+    y = np.zeros(P.nbar)
+    for _ in range(sweeps):
+        G = P.G.copy()
+        G[0] += y
+        y = R.be_solve(P, G=G)[-1]
+    return y
+
+
+def test_noalloc_clamped_partial_rows_match_plan_and_oracle(pd):
+    """n near the limit and a long time axis (n = 4095, l = 4096): the per-team partial rows
+    of b no longer fit the static scratch at the default split, so the entry point clamps the
+    number of frequency ranges; Y and b still equal the plan entry point's, and b equals the
+    oracle's eq. (7) vector."""
+    P = W.heat1d_forced(4095, 4096, seed=3)
+    _compare(pd, P)
+    dev = torch.device("cuda:0")
+    with pd.Plan.from_problem(P, precision="fp64", device=dev) as plan:
+        R = plan.time_dft(torch.from_numpy(P.G).to(dev))
+    k = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (P.k_lo, P.k_diag, P.k_up)]
+    b = torch.empty(P.nbar, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    pd._binding.paradiag_smw_rhs_noalloc(P.nt, P.nbar, P.tau, k[0].data_ptr(), k[1].data_ptr(), k[2].data_ptr(),
+                                         R.data_ptr(), 0, b.data_ptr(), stream.cuda_stream)
+    torch.cuda.synchronize()
+    ref = _periodic_last_slice(P)
+    assert np.linalg.norm(b.cpu().numpy() - ref) <= FWD_TOL * np.linalg.norm(ref)
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch(pd):
     dev = torch.device("cuda:0")
     x = torch.zeros(8, dtype=torch.float64, device=dev)
