@@ -47,7 +47,9 @@ typedef enum pd_status {
   PD_ERR_CUDA = 4,          /* a CUDA runtime call failed; destroy the plan */
   PD_ERR_NOT_CONVERGED = 5, /* Krylov or refinement limit reached; U holds the last iterate */
   PD_ERR_NONFINITE = 6,     /* NaN/Inf met in the input or an intermediate norm */
-  PD_ERR_TIMEOUT = 7        /* reserved for bounded device-side waits */
+  PD_ERR_TIMEOUT = 7        /* a bounded device-side wait (a grid barrier of the persistent
+                               Algorithm-2 step) ran out; U is unspecified, the plan stays
+                               usable */
 } pd_status;
 
 typedef enum pd_precision {
@@ -179,6 +181,23 @@ typedef struct pd_desc {
                                 shared memory; 4 = radix-4 (and one radix-2) passes only;
                                 0 = built-in choice (16 for binary32 transforms of n >= 16, 4
                                 otherwise; the residual-on-load DFT always uses 4) */
+  int32_t tune_persistent;   /* single problems: run each Algorithm-2 step after its shifted
+                                solves as one persistent cooperative launch (the eq. (12)
+                                terms and system, z, eq. (13) with the stopping decision, and
+                                the next Arnoldi step, separated by grid barriers whose waits
+                                are bounded, see barrier_polls) instead of one launch per
+                                phase: 1 = on where it applies, -1 or 0 = off (the built-in
+                                choice: inside one CUDA graph the per-phase launches overlap
+                                their launch latency with programmatic dependent launch, and
+                                measured 1-11 % faster per solve on GB300).  Batches always
+                                use the per-phase launches. */
+  int64_t barrier_polls;     /* polls of a grid barrier of the persistent step before it gives
+                                up: the solve then returns PD_ERR_TIMEOUT (0 = 4194304, some
+                                seconds) */
+  int32_t tune_persist_ctas; /* CTAs of the persistent step, 1 .. one per SM (0 = one per SM) */
+  int32_t barrier_extra;     /* testing the bounded wait: every grid barrier of the persistent
+                                step waits for this many more CTAs than the launch has, so no
+                                barrier completes and every wait runs out; 0 in normal use */
 } pd_desc;
 
 /* Statistics of the last paradiag_solve / paradiag_solve_host. */
@@ -207,6 +226,8 @@ typedef struct pd_stats {
      would keep refinement from contracting */
   int32_t zero_freq_fp64;
   double zero_freq_weight;
+  int32_t persistent_step;  /* 1 if each Algorithm-2 step ran as the persistent launch
+                               (pd_desc.tune_persistent) */
 } pd_stats;
 
 typedef struct pd_plan pd_plan;

@@ -69,6 +69,10 @@ class PdDesc(ctypes.Structure):
         ("batch_nx", ctypes.POINTER(ctypes.c_int64)),
         ("batch_tau", ctypes.POINTER(ctypes.c_double)),
         ("tune_fft_radix", ctypes.c_int32),
+        ("tune_persistent", ctypes.c_int32),
+        ("barrier_polls", ctypes.c_int64),
+        ("tune_persist_ctas", ctypes.c_int32),
+        ("barrier_extra", ctypes.c_int32),
     ]
 
 
@@ -91,6 +95,7 @@ class PdStats(ctypes.Structure):
         ("sweep_rel_update", ctypes.c_double * 16),
         ("zero_freq_fp64", ctypes.c_int32),
         ("zero_freq_weight", ctypes.c_double),
+        ("persistent_step", ctypes.c_int32),
     ]
 
     def as_dict(self):

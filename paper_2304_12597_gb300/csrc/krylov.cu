@@ -44,17 +44,15 @@ __global__ void __launch_bounds__(MODE == kCoop ? kBlas : MODE == kCluster ? kBl
 // m is a multiple of q, m = maxit or the space broke down; a frozen step forms no
 // h_k, no eq. (12) system and no eq. (13) residual.
 template <int MODE, int E>
-__global__ void __launch_bounds__(MODE == kCoop ? kBlas : MODE == kCluster ? kBlasCluster : kBlasSingle) k_arnoldi_coop(int n, const double *__restrict__ klo,
-                                                        const double *__restrict__ kdiag,
-                                                        const double *__restrict__ kup, double *V, float *Vf,
-                                                        double *w, double *T, int ldT, double *part, int ld,
-                                                        double *scal, int *flags, int q, int maxit) {
-  grid_dep_wait();
+__device__ __forceinline__ void arnoldi_body(int n, const double *__restrict__ klo, const double *__restrict__ kdiag,
+                                             const double *__restrict__ kup, double *V, float *Vf, double *w,
+                                             double *T, int ldT, double *part, int ld, double *scal, int *flags,
+                                             int q, int maxit) {
   __shared__ double red[kRedWords];
   __shared__ double c[34];
   const int m = flags[F_M] + 1;  // the step computed here produces v_m
   __shared__ double cslot[MODE == kCluster ? 3 * kSlot : 1];
-  const int G = MODE == kCoop ? (int)gridDim.x : 1;
+  const int G = g_ctas<MODE>();
   double *pa = part, *pb = part + (size_t)G * ld, *pc = part + (size_t)2 * G * ld;
   if constexpr (MODE == kCluster) {
     pa = cslot;
@@ -105,7 +103,8 @@ __global__ void __launch_bounds__(MODE == kCoop ? kBlas : MODE == kCluster ? kBl
       }
       x[e] = a;
     }
-    const bool wr = (MODE == kSingle || blockIdx.x == 0) && (int)threadIdx.x < m;  // writes column m-1 of T
+    // writes column m-1 of T
+    const bool wr = (MODE == kSingle || MODE == kTail || blockIdx.x == 0) && (int)threadIdx.x < m;
     reg_dots<MODE, E>(n, m, V, n, x, pa, ld, red, c);
     knorm = sqrt(c[m]);
     double tq = wr ? c[threadIdx.x] : 0.0;
@@ -141,6 +140,19 @@ __global__ void __launch_bounds__(MODE == kCoop ? kBlas : MODE == kCluster ? kBl
     if (!isfinite(t)) flags[F_NONFIN] = 1;
   }
   cluster_exit<MODE>();
+}
+
+// The Arnoldi step as a kernel of its own (nothing to do once Algorithm 2 has stopped:
+// the first step of the persistent form follows the start unconditionally).
+template <int MODE, int E>
+__global__ void __launch_bounds__(MODE == kCoop ? kBlas : MODE == kCluster ? kBlasCluster : kBlasSingle) k_arnoldi_coop(int n, const double *__restrict__ klo,
+                                                        const double *__restrict__ kdiag,
+                                                        const double *__restrict__ kup, double *V, float *Vf,
+                                                        double *w, double *T, int ldT, double *part, int ld,
+                                                        double *scal, int *flags, int q, int maxit) {
+  grid_dep_wait();
+  if (flags[F_KSTOP]) return;  // uniform over the grid (and the cluster)
+  arnoldi_body<MODE, E>(n, klo, kdiag, kup, V, Vf, w, T, ldT, part, ld, scal, flags, q, maxit);
 }
 
 // eq. (13) and the stopping decision (project_body).
@@ -217,43 +229,37 @@ __host__ __device__ inline size_t k5a_warp_bytes(int m) {
   return (b + 15) & ~(size_t)15;
 }
 
-__global__ void __launch_bounds__(kK5Warps * 32) k_capacitance_terms(
-    int nf, int maxit, double tau, const double *__restrict__ T, const double2 *__restrict__ shift,
-    const double2 *__restrict__ wg, const double2 *__restrict__ gpart, int nblk, double *msys_part,
-    double2 *srow, const double *scal, int *flags, double2 *omega, double *y, int members) {
-  grid_dep_wait();
-  extern __shared__ __align__(16) unsigned char smraw[];
-  if (members) {  // member blockIdx.y of a batch: its own Algorithm-2 state (strided views)
-    const int mb = blockIdx.y;
-    T += (int64_t)mb * (maxit + 1) * maxit;
-    msys_part += (int64_t)mb * gridDim.x * maxit * maxit;
-    srow += (int64_t)mb * nf * maxit;
-    omega += (int64_t)mb * nf;
-    y += (int64_t)mb * (maxit + 1);
-    scal += (int64_t)mb * kScalWords;
-    flags += (int64_t)mb * kFlagWords;
-    if (flags[F_KSTOP]) return;  // this member's Algorithm 2 has stopped (whole CTA)
-  } else if (flags[F_FROZEN]) {
-    return;  // a frozen step (q > 1): no eq. (12) system (every CTA leaves; the counter stays 0)
-  }
-  const int m = flags[F_M] + 1;
+// The eq. (12) terms of CTA `cta` of `ncta`: each of its first `nwk` warps owns a
+// shared-memory slice of k5a_warp_bytes(m) bytes at smraw and accumulates the terms of
+// its frequencies there (a thread per frequency, every warp, when m = 1); the CTA's sum
+// over those warps (fixed order) goes to row `cta` of msys_part.  `mb` selects a batch
+// member's block of partial dots (members != 0).  Ends with a CTA barrier.
+__device__ void capacitance_terms_body(int cta, int ncta, int nwk, int m, int nf, int maxit, double tau,
+                                       const double *__restrict__ T, const double2 *__restrict__ shift,
+                                       const double2 *__restrict__ wg, const double2 *__restrict__ gpart,
+                                       int nblk, double *msys_part, double2 *srow, const double *scal,
+                                       const int *flags, int members, int mb, unsigned char *smraw) {
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const size_t wb = k5a_warp_bytes(m);
-  unsigned char *base = smraw + wid * wb;
+  const bool busy = wid < nwk;
+  unsigned char *base = smraw + (busy ? wid : 0) * wb;
   cpx<double> *H = reinterpret_cast<cpx<double> *>(base);
   cpx<double> *X = H + m * m;
   cpx<double> *fcol = X + m * m;
   cpx<double> *gq = fcol + m;
   double *msw = reinterpret_cast<double *>(gq + m);
   const double tt = flags[F_BREAK] ? 0.0 : tau * scal[S_T];
-  for (int i = lane; i < m * m; i += 32) msw[i] = 0.0;
+  if (busy)
+    for (int i = lane; i < m * m; i += 32) msw[i] = 0.0;
   __syncwarp();
+  // g_k = sum over blocks of the partial dots; after a breakdown the dot pass was skipped
+  // and the t-term vanishes; a batch member takes only its own block's dots
+  const int b0 = members ? mb : 0, b1 = flags[F_BREAK] ? b0 : (members ? b0 + 1 : nblk);
   if (m == 1) {
     // one step (the common case): S_k = 1 / ((1 - pi_k) + tau t_11) is a scalar, so a
     // thread takes a frequency (a warp of GJ per frequency would leave 31 lanes idle on
     // GB300's slow FP64 pipe)
     const double t11 = tau * T[0];
-    const int b0 = members ? (int)blockIdx.y : 0, b1 = flags[F_BREAK] ? b0 : (members ? b0 + 1 : nblk);
     double acc = 0.0;
     auto term = [&](int k, double gx, double gy) {
       const double2 sk = shift[k];
@@ -269,8 +275,8 @@ __global__ void __launch_bounds__(kK5Warps * 32) k_capacitance_terms(
       // many blocks (2D: one per mode of T_y): a warp per frequency, its lanes split the
       // blocks' partial dots, so the loads are in flight together rather than one after
       // another along a chain of adds
-      const int gw = blockIdx.x * kK5Warps + wid, nw = gridDim.x * kK5Warps;
-      for (int k = gw; k < nf; k += nw) {
+      const int gw = cta * nwk + wid, nw = ncta * nwk;
+      for (int k = gw; busy && k < nf; k += nw) {
         double gx = 0.0, gy = 0.0;
         for (int b = b0 + lane; b < b1; b += 32) {
           const double2 v = gpart[(int64_t)k * nblk + b];
@@ -282,7 +288,7 @@ __global__ void __launch_bounds__(kK5Warps * 32) k_capacitance_terms(
         if (lane == 0) acc += term(k, gx, gy);
       }
     } else {
-      for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nf; k += gridDim.x * blockDim.x) {
+      for (int k = cta * blockDim.x + threadIdx.x; busy && k < nf; k += ncta * blockDim.x) {
         double gx = 0.0, gy = 0.0;
         for (int b = b0; b < b1; ++b) {
           const double2 v = gpart[(int64_t)k * nblk + b];
@@ -293,21 +299,17 @@ __global__ void __launch_bounds__(kK5Warps * 32) k_capacitance_terms(
       }
     }
     acc = warp_sum(acc);
-    if (lane == 0) msw[0] = acc;
-  } else {
-  const int gw = blockIdx.x * kK5Warps + wid, nw = gridDim.x * kK5Warps;
-  for (int k = gw; k < nf; k += nw) {
-    const double2 sk = shift[k];
-    if (lane < m) {
-      for (int q = 0; q < m; ++q) {
-        const double tq = (q <= lane + 1) ? T[(int64_t)q * maxit + lane] : 0.0;
-        H[q * m + lane] = mk<double>(tau * tq + (q == lane ? sk.x : 0.0), q == lane ? sk.y : 0.0);
+    if (busy && lane == 0) msw[0] = acc;
+  } else if (busy) {
+    const int gw = cta * nwk + wid, nw = ncta * nwk;
+    for (int k = gw; k < nf; k += nw) {
+      const double2 sk = shift[k];
+      if (lane < m) {
+        for (int q = 0; q < m; ++q) {
+          const double tq = (q <= lane + 1) ? T[(int64_t)q * maxit + lane] : 0.0;
+          H[q * m + lane] = mk<double>(tau * tq + (q == lane ? sk.x : 0.0), q == lane ? sk.y : 0.0);
+        }
       }
-    }
-    {
-      // g_k = sum over blocks of the partial dots; after a breakdown the dot pass was
-      // skipped and the t-term vanishes; a batch member takes only its own block's dots
-      const int b0 = members ? (int)blockIdx.y : 0, b1 = flags[F_BREAK] ? b0 : (members ? b0 + 1 : nblk);
       if (b1 - b0 >= 32) {  // many blocks: the lanes split them, one warp sum per dot
         for (int q = 0; q < m; ++q) {
           double gx = 0.0, gy = 0.0;
@@ -329,33 +331,58 @@ __global__ void __launch_bounds__(kK5Warps * 32) k_capacitance_terms(
         }
         gq[lane] = mk<double>(gx, gy);
       }
-    }
-    __syncwarp();
-    warp_gj_inverse(H, X, fcol, m);
-    const double2 w = wg[k];
-    const cpx<double> wk = mk<double>(w.x, w.y);
-    if (lane < m) {
-      const cpx<double> sl = X[(m - 1) * m + lane];  // e_m^T S_k, column `lane`
-      const cpx<double> ws = mul(wk, sl);  // w_k gamma_k (e_m^T S_k): omega_k = this . y_m
-      srow[(int64_t)k * m + lane] = make_double2(ws.x, ws.y);
-      for (int q = 0; q < m; ++q) {
-        const cpx<double> gs = mul(gq[q], sl);
-        const cpx<double> val = mk<double>(X[q * m + lane].x - tt * gs.x, X[q * m + lane].y - tt * gs.y);
-        const cpx<double> c = mul(wk, val);
-        msw[q * m + lane] += c.x;
+      __syncwarp();
+      warp_gj_inverse(H, X, fcol, m);
+      const double2 w = wg[k];
+      const cpx<double> wk = mk<double>(w.x, w.y);
+      if (lane < m) {
+        const cpx<double> sl = X[(m - 1) * m + lane];  // e_m^T S_k, column `lane`
+        const cpx<double> ws = mul(wk, sl);  // w_k gamma_k (e_m^T S_k): omega_k = this . y_m
+        srow[(int64_t)k * m + lane] = make_double2(ws.x, ws.y);
+        for (int q = 0; q < m; ++q) {
+          const cpx<double> gs = mul(gq[q], sl);
+          const cpx<double> val = mk<double>(X[q * m + lane].x - tt * gs.x, X[q * m + lane].y - tt * gs.y);
+          const cpx<double> c = mul(wk, val);
+          msw[q * m + lane] += c.x;
+        }
       }
+      __syncwarp();
     }
-    __syncwarp();
-  }
   }
   __syncthreads();
   // CTA partial = sum over its warps (fixed order)
+  const size_t msw_off = (size_t)(2 * m * m + 2 * m) * sizeof(cpx<double>);
   for (int i = threadIdx.x; i < m * m; i += blockDim.x) {
     double s = 0.0;
-    for (int wv = 0; wv < kK5Warps; ++wv) s += reinterpret_cast<double *>(smraw + wv * wb + (size_t)(2 * m * m + 2 * m) * sizeof(cpx<double>))[i];
-    msys_part[(int64_t)blockIdx.x * m * m + i] = s;
+    for (int wv = 0; wv < nwk; ++wv) s += reinterpret_cast<double *>(smraw + wv * wb + msw_off)[i];
+    msys_part[(int64_t)cta * m * m + i] = s;
   }
-  // The last CTA to finish (counted in flags[3]; no CTA waits for another) sums the
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kK5Warps * 32) k_capacitance_terms(
+    int nf, int maxit, double tau, const double *__restrict__ T, const double2 *__restrict__ shift,
+    const double2 *__restrict__ wg, const double2 *__restrict__ gpart, int nblk, double *msys_part,
+    double2 *srow, const double *scal, int *flags, double2 *omega, double *y, int members) {
+  grid_dep_wait();
+  extern __shared__ __align__(16) unsigned char smraw[];
+  if (members) {  // member blockIdx.y of a batch: its own Algorithm-2 state (strided views)
+    const int mb = blockIdx.y;
+    T += (int64_t)mb * (maxit + 1) * maxit;
+    msys_part += (int64_t)mb * gridDim.x * maxit * maxit;
+    srow += (int64_t)mb * nf * maxit;
+    omega += (int64_t)mb * nf;
+    y += (int64_t)mb * (maxit + 1);
+    scal += (int64_t)mb * kScalWords;
+    flags += (int64_t)mb * kFlagWords;
+    if (flags[F_KSTOP]) return;  // this member's Algorithm 2 has stopped (whole CTA)
+  } else if (flags[F_FROZEN]) {
+    return;  // a frozen step (q > 1): no eq. (12) system (every CTA leaves; the counter stays 0)
+  }
+  const int m = flags[F_M] + 1;
+  capacitance_terms_body(blockIdx.x, gridDim.x, kK5Warps, m, nf, maxit, tau, T, shift, wg, gpart, nblk, msys_part,
+                         srow, scal, flags, members, (int)blockIdx.y, smraw);
+  // The last CTA to finish (counted in flags[F_CAPCNT]; no CTA waits for another) sums the
   // partials and solves the m x m system, then resets the counter.
   __shared__ int last;
   __threadfence();
@@ -475,6 +502,117 @@ __global__ void k_residual(const double *__restrict__ G, const double *__restric
     if (iy + 1 < ny) r = fma(-ryu[iy], u[j + nx], r);
   }
   R[idx] = (Tout)r;
+}
+
+// ---- persistent Algorithm-2 step ---------------------------------------------------
+
+// z[j] = sum_k Re(omega_k H[k][j]) (eq. 13's z) over the whole grid: tiles of cw = 512 / rg
+// adjacent columns, rg row groups per tile (thread (tx, ty) sums rows ty, ty + rg, ...
+// with kZB loads in flight), the groups' partials added pairwise in a fixed order.  The
+// weights are rounded once into shared memory (om, nf entries).  With h0 the zero
+// frequency comes from the FP64 lane, added in FP64.
+constexpr int kZB = 16;
+template <typename T>
+__device__ void step_zsum(int nf, int n, const cpx<T> *__restrict__ H, int64_t ldh,
+                          const double2 *__restrict__ omega, double *z, const double *__restrict__ h0, int rg,
+                          cpx<T> *om, T *sm) {
+  for (int k = threadIdx.x; k < nf; k += blockDim.x) om[k] = mk<T>((T)omega[k].x, (T)omega[k].y);
+  __syncthreads();
+  const int cw = (int)blockDim.x / rg;
+  const int tx = threadIdx.x % cw, ty = threadIdx.x / cw;
+  const int kfirst = h0 ? 1 : 0;
+  const int ntile = (n + cw - 1) / cw;
+  for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+    const int j = tile * cw + tx;
+    T acc = T(0), acc2 = T(0);
+    if (j < n) {
+      for (int k0 = ty; k0 < nf; k0 += kZB * rg) {
+        cpx<T> hv[kZB];
+#pragma unroll
+        for (int u = 0; u < kZB; ++u) {
+          const int k = k0 + u * rg;
+          hv[u] = (k < nf && k >= kfirst) ? H[(int64_t)k * ldh + j] : mk<T>(T(0), T(0));
+        }
+#pragma unroll
+        for (int u = 0; u < kZB; u += 2) {
+          const int k = k0 + u * rg, k2 = k + rg;
+          if (k < nf) acc += om[k].x * hv[u].x - om[k].y * hv[u].y;
+          if (k2 < nf) acc2 += om[k2].x * hv[u + 1].x - om[k2].y * hv[u + 1].y;
+        }
+      }
+    }
+    sm[threadIdx.x] = acc + acc2;
+    for (int w = rg >> 1; w >= 1; w >>= 1) {
+      __syncthreads();
+      if (ty < w) sm[threadIdx.x] += sm[threadIdx.x + w * cw];
+    }
+    __syncthreads();
+    if (ty == 0 && j < n) z[j] = h0 ? (double)sm[tx] + omega[0].x * h0[j] : (double)sm[tx];
+    __syncthreads();  // sm is rewritten by the next tile
+  }
+}
+
+// One Algorithm-2 step after its shifted solves (see StepArgs).  The vector phases (eq.
+// 13, Arnoldi) run in the first a.nv CTAs, which hold E entries per thread in registers
+// (VMODE kSingle: nv = 1, no grid barrier; kPersist: bounded barriers among the nv CTAs
+// inside each reduction); the other CTAs leave once z is written.
+template <typename T, int VMODE, int E>
+__global__ void __launch_bounds__(kBlasSingle, 1) k_step_tail(StepArgs<T> a) {
+  BarCtx &bc = bar_ctx();
+  int *flags = a.flags;
+  if (threadIdx.x == 0) {
+    bc.flags = flags;
+    bc.limit = a.bar_polls;
+    bc.expect = (int)gridDim.x + a.bar_extra;
+    bc.use_handle = a.use_handle;
+    bc.h = a.h;
+    bc.failed = 0;
+    bc.nv = a.nv;
+  }
+  __syncthreads();
+  // after a timeout the loop only winds down (a CTA of the failed launch may have set the
+  // conditional to run once more before another CTA's timeout set it to stop)
+  if (flags[F_TIMEOUT]) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      flags[F_KSTOP] = 1;
+      if (a.use_handle) cudaGraphSetConditional(a.h, 0u);
+    }
+    return;
+  }
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ T zsm[kBlasSingle];
+  bool ok = true;
+  if (!flags[F_FROZEN]) {  // a frozen step (q > 1) forms no eq. (12) system and no z
+    const int m = flags[F_M] + 1;
+    const int nwall = (int)blockDim.x >> 5;
+    const int nwk = m == 1 ? nwall : max(1, min(nwall, (int)(a.smem / k5a_warp_bytes(m))));
+    capacitance_terms_body(blockIdx.x, gridDim.x, nwk, m, a.nf, a.maxit, a.tau, a.T, a.shift, a.wg, a.gpart, a.nblk,
+                           a.msys_part, a.srow, a.scal, flags, 0, 0, smraw);
+    if (last_cta_done(flags + F_CAPCNT)) {
+      capacitance_solve_cta(a.nf, m, gridDim.x, a.msys_part, a.srow, a.omega, a.y, a.scal, smraw);
+      if (threadIdx.x == 0) flags[F_CAPCNT] = 0;
+    }
+    ok = bounded_grid_sync();  // omega
+    if (ok && !flags[F_NOH])   // no z after a breakdown (eq. 13 gives 0)
+      step_zsum<T>(a.nf, a.n, a.H, a.ldh, a.omega, a.z, a.h0, a.zrg, reinterpret_cast<cpx<T> *>(smraw), zsm);
+    if (ok) ok = bounded_grid_sync((int)blockIdx.x < a.nv);  // z
+  }
+  if (threadIdx.x == 0) bc.expect = a.nv + a.bar_extra;  // the vector phases' barriers
+  if (ok && (int)blockIdx.x < a.nv) {
+    project_body<VMODE, E>(a.n, a.V, a.z, a.tau, a.part, a.ld, a.scal, flags, a.kc, a.use_handle, a.h);
+    __syncthreads();  // the decision (thread 0 of CTA 0) is read by the whole CTA
+    ok = !bc.failed;
+    if (VMODE == kPersist && ok) ok = bounded_grid_sync();  // ... and by every vector CTA
+    if (ok && !*(volatile int *)(flags + F_KSTOP)) {
+      arnoldi_body<VMODE, E>(a.n, a.klo, a.kdiag, a.kup, a.V, a.Vf, a.w, a.T, a.maxit, a.part, a.ld, a.scal, flags,
+                             a.q, a.maxit);
+      ok = !bc.failed;
+    }
+  }
+  if (!ok && threadIdx.x == 0) {  // the last word on the loop: stop
+    flags[F_KSTOP] = 1;
+    if (a.use_handle) cudaGraphSetConditional(a.h, 0u);
+  }
 }
 
 // ---- launchers -------------------------------------------------------------------
@@ -641,6 +779,68 @@ void launch_project_resnorm(Ctx &c, KrylovBufs &k, const double *z, double tau, 
               PD_BY_E(reg_elems(k.n, k.cluster * kBlasCluster), k_project_coop, kCluster),
               k.grid, k.cluster, args);
 }
+
+// Dynamic shared memory of the persistent step: the capacitance phase's warp slices (up to
+// four sized for the largest m, within 150 KB; more warps join while m is small), its m x m
+// solve, and the z weights.
+size_t step_tail_smem(int maxit, int nf, int elem_bytes) {
+  const size_t solve = (size_t)(2 * maxit * maxit + maxit) * sizeof(cpx<double>) + (size_t)(maxit + 1) * 8;
+  const size_t wb = k5a_warp_bytes(maxit);
+  const size_t terms = wb * std::max<size_t>(1, std::min<size_t>(kK5Warps, (150 * 1024) / wb));
+  const size_t om = (size_t)nf * 2 * elem_bytes;
+  return (std::max(std::max(solve, terms), om) + 15) & ~(size_t)15;
+}
+
+// nv = 1: the vector phases in one CTA without grid barriers (E = 1: n_bar <= 512)
+template <typename T>
+static const void *step_tail_fn(int nv, int E) {
+  if (nv <= 1) return (const void *)k_step_tail<T, kSingle, 1>;
+  return E <= 1 ? (const void *)k_step_tail<T, kPersist, 1>
+       : E == 2 ? (const void *)k_step_tail<T, kPersist, 2>
+                : (const void *)k_step_tail<T, kPersist, 4>;
+}
+
+static const void *step_tail_pick(int nv, int E, int elem_bytes) {
+  return elem_bytes == 8 ? step_tail_fn<double>(nv, E) : step_tail_fn<float>(nv, E);
+}
+
+int step_tail_max_grid(int nv, int E, int elem_bytes, size_t smem) {
+  const void *fn = step_tail_pick(nv, E, elem_bytes);
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlasSingle, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return per_sm * sm_count();
+}
+
+template <typename T>
+void launch_step_tail(Ctx &c, const StepArgs<T> &a0, int grid, int E) {
+  const void *fn = step_tail_pick(a0.nv, E, (int)sizeof(T));
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a0.smem);
+  StepArgs<T> a = a0;
+  void *args[] = {&a};
+  // algorithmic bytes: the stored h_k read once by the z sum
+  c.launch("krylov_step", (double)a.nf * a.n * sizeof(cpx<T>), [&] {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kBlasSingle);
+    cfg.dynamicSmemBytes = a.smem;
+    cfg.stream = c.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelExC(&cfg, fn, args);
+  });
+}
+template void launch_step_tail<float>(Ctx &, const StepArgs<float> &, int, int);
+template void launch_step_tail<double>(Ctx &, const StepArgs<double> &, int, int);
 
 void launch_xm(Ctx &c, KrylovBufs &k, const double *y, double *x, float *xf) {
   c.launch("krylov_xm", (double)k.n * 8.0 * 2,

@@ -68,7 +68,9 @@ __device__ __forceinline__ void refine_decide(double *scal, int *flags, const Re
   }
   flags[F_MTOT] += flags[F_M];
   bool conv = false, stop = false;
-  if (!isfinite(d2) || flags[F_NONFIN]) {
+  if (flags[F_TIMEOUT]) {  // a bounded wait of the persistent step ran out: stop
+    stop = true;
+  } else if (!isfinite(d2) || flags[F_NONFIN]) {
     flags[F_NONFIN] = 1;
     stop = true;
   } else if (ref2 == 0.0) {

@@ -35,6 +35,9 @@ enum FlagIndex {
   F_SWM = 16,     // [16, 32): m of each solve
   F_FROZEN = 32,  // this Algorithm-2 step skips the residual check (q > 1, Sec. 3)
   F_NOH = 33,     // this step forms no h_k: breakdown or a frozen step
+  F_TIMEOUT = 34, // a bounded device-side wait ran out (persistent Algorithm-2 step)
+  F_BARCNT = 35,  // grid barrier of the persistent step: arrivals
+  F_BARGEN = 36,  // grid barrier of the persistent step: generation
   kFlagWords = 64
 };
 // CTA size of the cooperative Krylov vector kernels (pd_krylov.cuh, kCoop mode).
@@ -324,6 +327,52 @@ void launch_member_init(Ctx &c, KrylovBufs &k, const double *b, int use_handle, 
 void launch_member_arnoldi(Ctx &c, KrylovBufs &k);
 void launch_member_project(Ctx &c, KrylovBufs &k, const double *z, double tau, const KrylovCtl &kc,
                            int use_handle, cudaGraphConditionalHandle h);
+// Persistent form of one Algorithm-2 step (single problems): one cooperative launch runs
+// the eq. (12) terms and system, z = sum_k gamma_k h_k c_k, eq. (13) with the stopping
+// decision and, unless Algorithm 2 stops there, the next Arnoldi step (eq. 10), with
+// grid barriers between the phases instead of kernel boundaries.  The shifted solves of
+// the step (h_k and their dots) stay a launch of their own, with their own CTA shape.
+// Every barrier waits at most bar_polls polls; one that runs out sets flags[F_TIMEOUT],
+// sets the WHILE conditional to 0 and the kernel returns (the solve then reports
+// PD_ERR_TIMEOUT).  bar_extra > 0 makes every barrier wait for that many CTAs that do
+// not exist (a wait that cannot complete: the bounded wait's own test).
+template <typename TC>
+struct StepArgs {
+  // Algorithm 2 state (as KrylovBufs)
+  int n, maxit, q, ld;
+  const double *klo, *kdiag, *kup;
+  double *V, *w, *T, *part, *scal, *z;
+  float *Vf;
+  int *flags;
+  double tau;
+  KrylovCtl kc;
+  // eq. (12)
+  int nf, nblk;
+  const double2 *shift, *wg, *gpart;
+  double *msys_part, *y;
+  double2 *srow, *omega;
+  // z from the stored h_k (the zero frequency from the FP64 lane h0 when it is on)
+  const cpx<TC> *H;
+  int64_t ldh;
+  const double *h0;
+  int zrg;  // row groups of the z sum (power of two <= 64)
+  int nv;   // CTAs of the vector phases (eq. 13, Arnoldi): the first nv of the grid
+  // launch
+  size_t smem;  // dynamic shared memory of the launch
+  long long bar_polls;
+  int bar_extra;
+  int use_handle;
+  cudaGraphConditionalHandle h;
+};
+// grid = co-resident CTAs of 512 threads; the vector phases hold E entries per thread over
+// a.nv of them.
+template <typename T>
+void launch_step_tail(Ctx &c, const StepArgs<T> &a, int grid, int E);
+// Dynamic shared memory and the largest co-resident grid of the persistent step (0 if it
+// cannot run: its shared memory does not fit).
+size_t step_tail_smem(int maxit, int nf, int elem_bytes);
+int step_tail_max_grid(int nv, int E, int elem_bytes, size_t smem);
+
 // eq. (13) and the Algorithm-2 stopping decision (krylov_decide) in one kernel
 void launch_project_resnorm(Ctx &c, KrylovBufs &k, const double *z, double tau, const KrylovCtl &kc,
                             int use_handle, cudaGraphConditionalHandle h);

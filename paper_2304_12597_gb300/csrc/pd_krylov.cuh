@@ -29,21 +29,80 @@ constexpr int kBlasCluster = 128;  // threads per CTA of the cluster variants
 constexpr int kRedQ = 4;           // sums reduced side by side
 constexpr int kRedWords = kRedQ * kBlasSingle;
 constexpr int kSingle = 0, kCoop = 1, kCluster = 2, kTail = 3;  // MODE of the vector steps
+// kPersist: as kCoop (register-resident entries over a cooperative grid), inside the
+// persistent Algorithm-2 step, whose grid barriers wait a bounded number of polls
+constexpr int kPersist = 4;
+
+// Grid barrier with a bounded wait (cooperative launches of the persistent step).  Every
+// CTA arrives on flags[F_BARCNT]; the last of `expect` arrivals resets the count and bumps
+// the generation flags[F_BARGEN]; the others poll the generation at most `limit` times.  A
+// wait that runs out records flags[F_TIMEOUT], sets the step's WHILE conditional to 0 and
+// marks the CTA failed: its later barriers return false at once, and the kernel leaves
+// after the phase it is in.  The counters start at zero in every solve (k_solve_reset),
+// and no launch of the persistent step runs once flags[F_TIMEOUT] is set.
+struct BarCtx {
+  int *flags;
+  long long limit;
+  int expect;  // arrivals that complete a barrier: the grid, plus any test-only phantoms
+  int nv;      // CTAs of the vector phases (kPersist), the first nv of the grid
+  int use_handle;
+  cudaGraphConditionalHandle h;
+  int failed;
+};
+__device__ __forceinline__ BarCtx &bar_ctx() {
+  __shared__ BarCtx c;
+  return c;
+}
+// wait = false: arrive only (a CTA with nothing left to do after this barrier).
+__device__ inline bool bounded_grid_sync(bool wait = true) {
+  BarCtx &bc = bar_ctx();
+  __syncthreads();
+  if (threadIdx.x == 0 && !bc.failed) {
+    volatile int *gen = bc.flags + F_BARGEN;
+    const int g = *gen;
+    __threadfence();
+    const int arrived = atomicAdd(bc.flags + F_BARCNT, 1) + 1;
+    if (arrived == bc.expect) {
+      bc.flags[F_BARCNT] = 0;
+      __threadfence();
+      atomicAdd(bc.flags + F_BARGEN, 1);
+    } else if (wait) {
+      long long polls = 0;
+      while (*gen == g && polls < bc.limit) ++polls;
+      if (*gen == g) {
+        bc.failed = 1;
+        atomicExch(bc.flags + F_TIMEOUT, 1);
+        if (bc.use_handle) cudaGraphSetConditional(bc.h, 0u);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return !bc.failed;
+}
 constexpr int kSlot = 36;  // doubles per cluster-mode partial slot (m + 1 <= 33 sums)
 
 template <int MODE>
 __device__ __forceinline__ int g_first() {
-  if constexpr (MODE == kCoop || MODE == kCluster) return blockIdx.x * blockDim.x + threadIdx.x;
+  if constexpr (MODE == kCoop || MODE == kCluster || MODE == kPersist) return blockIdx.x * blockDim.x + threadIdx.x;
   return threadIdx.x;
 }
 template <int MODE>
 __device__ __forceinline__ int g_stride() {
   if constexpr (MODE == kCoop || MODE == kCluster) return gridDim.x * blockDim.x;
+  if constexpr (MODE == kPersist) return bar_ctx().nv * blockDim.x;
   return blockDim.x;
+}
+// CTAs that hold partials of a grid reduction (one panel row each)
+template <int MODE>
+__device__ __forceinline__ int g_ctas() {
+  if constexpr (MODE == kCoop) return gridDim.x;
+  if constexpr (MODE == kPersist) return bar_ctx().nv;
+  return 1;
 }
 template <int MODE>
 __device__ __forceinline__ bool g_leader() {
-  if constexpr (MODE == kCoop || MODE == kCluster) return blockIdx.x == 0 && threadIdx.x == 0;
+  if constexpr (MODE == kCoop || MODE == kCluster || MODE == kPersist) return blockIdx.x == 0 && threadIdx.x == 0;
   return threadIdx.x == 0;
 }
 
@@ -151,10 +210,13 @@ __device__ __forceinline__ void grid_dots(int n, int m, const double *__restrict
 template <int MODE>
 __device__ __forceinline__ double grid_sum(double s, double *panel, int ld, double *red, double *c) {
   s = block_sum(s, red);
-  if constexpr (MODE == kCoop) {
+  if constexpr (MODE == kCoop || MODE == kPersist) {
     if (threadIdx.x == 0) panel[(size_t)blockIdx.x * ld] = s;
-    cooperative_groups::this_grid().sync();
-    cta_gather(panel, ld, gridDim.x, 0, c);
+    if constexpr (MODE == kCoop)
+      cooperative_groups::this_grid().sync();
+    else
+      bounded_grid_sync();
+    cta_gather(panel, ld, g_ctas<MODE>(), 0, c);
     return c[0];
   } else if constexpr (MODE == kCluster) {
     if (threadIdx.x == 0) panel[0] = s;
@@ -213,10 +275,10 @@ __device__ __forceinline__ void reg_load(int n, const double *__restrict__ x, do
 template <int MODE, int E>
 __device__ __forceinline__ void reg_dots(int n, int m, const double *V, int64_t ldv, const double (&x)[E], double *slot,
                                          int ld, double *red, double *c) {
-  static_assert(MODE == kSingle || MODE == kCluster || MODE == kCoop, "register-resident steps");
+  static_assert(MODE == kSingle || MODE == kCluster || MODE == kCoop || MODE == kPersist, "register-resident steps");
   __shared__ double out[kRedQ];
   const int f = g_first<MODE>(), st = g_stride<MODE>();
-  double *dst = MODE == kCluster ? slot : MODE == kCoop ? slot + (size_t)blockIdx.x * ld : c;
+  double *dst = MODE == kCluster ? slot : (MODE == kCoop || MODE == kPersist) ? slot + (size_t)blockIdx.x * ld : c;
   for (int q0 = 0; q0 <= m; q0 += kRedQ) {
     const int nq = min(kRedQ, m + 1 - q0);
     double s[kRedQ];
@@ -241,6 +303,9 @@ __device__ __forceinline__ void reg_dots(int n, int m, const double *V, int64_t 
   } else if constexpr (MODE == kCoop) {
     cooperative_groups::this_grid().sync();
     cta_gather(slot, ld, gridDim.x, m, c);
+  } else if constexpr (MODE == kPersist) {
+    bounded_grid_sync();
+    cta_gather(slot, ld, g_ctas<MODE>(), m, c);
   } else {
     __syncthreads();
   }
@@ -308,7 +373,7 @@ __device__ __forceinline__ void init_v0_body(const double *__restrict__ b, int n
   } else {
     double x[E > 0 ? E : 1];
     reg_load<MODE, E>(n, b, x);
-    beta = sqrt(reg_norm2<MODE, E>(x, MODE == kCoop ? part : cslot, ld, red, c));
+    beta = sqrt(reg_norm2<MODE, E>(x, (MODE == kCoop || MODE == kPersist) ? part : cslot, ld, red, c));
     const double ib = beta > 0.0 ? 1.0 / beta : 0.0;
     const int f = g_first<MODE>(), st = g_stride<MODE>();
 #pragma unroll
@@ -354,7 +419,7 @@ __device__ __forceinline__ void project_body(int n, const double *__restrict__ V
   __shared__ double c[34];
   const int m = flags[F_M] + 1;
   __shared__ double cslot[MODE == kCluster ? 3 * kSlot : 1];
-  const int G = MODE == kCoop ? (int)gridDim.x : 1;
+  const int G = g_ctas<MODE>();
   double *pa = part, *pb = part + (size_t)G * ld, *pc = part + (size_t)2 * G * ld;
   if constexpr (MODE == kCluster) {
     pa = cslot;

@@ -198,6 +198,16 @@ struct pd_plan {
   int k5_grid_members = 1;  // capacitance CTAs per problem of a batched plan
   int blas_cluster = 0;  // CTAs of the cluster variant of the one-CTA Krylov kernels (0 = off)
   bool krylov_tails = false;  // beta / v_1 and eq. (13) in the last CTA of the b and z reductions
+  // persistent Algorithm-2 step (single problems): one cooperative launch after each
+  // step's shifted solves (see pd::StepArgs)
+  bool persist = false;
+  int persist_grid = 0;     // CTAs (co-resident)
+  int persist_nv = 1;       // CTAs of the vector phases (the first of the grid)
+  int persist_E = 1;        // vector entries per thread
+  int persist_zrg = 1;      // row groups of the z sum
+  size_t persist_smem = 0;  // dynamic shared memory
+  long long bar_polls = 0;  // bounded wait of its grid barriers
+  int bar_extra = 0;        // test only: arrivals that never come
   int64_t lds = 0;
 
   // device buffers
@@ -402,6 +412,10 @@ pd_status validate(const pd_desc *d) {
     return fail(PD_ERR_INVALID_ARG, "tune_fft_cols must be 0, 2, 4, 8 or 16");
   if (d->tune_fft_radix != 0 && d->tune_fft_radix != 4 && d->tune_fft_radix != 16)
     return fail(PD_ERR_INVALID_ARG, "tune_fft_radix must be 0, 4 or 16");
+  if (d->tune_persistent < -1 || d->tune_persistent > 1)
+    return fail(PD_ERR_INVALID_ARG, "tune_persistent must be -1, 0 or 1");
+  if (d->barrier_polls < 0 || d->tune_persist_ctas < 0 || d->barrier_extra < 0 || d->barrier_extra > 1024)
+    return fail(PD_ERR_INVALID_ARG, "barrier_polls, tune_persist_ctas must be >= 0; barrier_extra in 0..1024");
   if (d->batch < 0) return fail(PD_ERR_INVALID_ARG, "batch must be >= 0");
   if (d->batch > 1) {
     if (d->dim != 1) return fail(PD_ERR_UNSUPPORTED, "batching is built for 1D problems only");
@@ -509,6 +523,38 @@ void fill_geometry(pd_plan *p, const pd_desc *d) {
     p->factored = want_fac && fbytes <= ((size_t)4 << 30);
   }
   p->ctx.pdl = d->tune_no_pdl == 0;
+  // persistent Algorithm-2 step: single problems that run Algorithm 2.  The vector phases
+  // take one entry per thread on as few CTAs as that needs (up to four entries once the
+  // grid is full): few CTAs keep their barriers short, one entry per thread spreads the
+  // FP64 work over as many SMs as there are 512-entry slices.
+  p->persist = false;
+  p->persist_grid = std::max(1, std::min(d->tune_persist_ctas > 0 ? d->tune_persist_ctas : sms, sms));
+  p->bar_polls = d->barrier_polls > 0 ? (long long)d->barrier_polls : (1LL << 22);
+  p->bar_extra = d->barrier_extra;
+  if (!p->members && !p->loops && d->tune_persistent > 0) {
+    const int elem = p->precision == PD_MIXED ? 4 : 8;
+    const int G = p->persist_grid;
+    const int64_t slices = (p->nbar + 511) / 512;
+    p->persist_nv = (int)std::min<int64_t>(slices, G);
+    p->persist_E = pd::reg_elems((int)p->nbar, p->persist_nv * 512);
+    const bool fits = p->nbar <= (int64_t)p->persist_nv * 512 * 4;
+    p->persist_smem = pd::step_tail_smem(p->maxit, p->nf, elem);
+    if (fits && p->persist_smem <= 180 * 1024 &&
+        pd::step_tail_max_grid(p->persist_nv, p->persist_E, elem, p->persist_smem) >= G)
+      p->persist = true;
+    // z sum: the row-group count that needs the fewest dependent memory round trips per
+    // CTA (tiles per CTA x batches of 16 loads per tile)
+    int64_t best = -1;
+    for (int rg = 1; rg <= 64; rg <<= 1) {
+      const int64_t cw = 512 / rg, tiles = (p->nbar + cw - 1) / cw;
+      const int64_t rows = (p->nf + rg - 1) / rg;
+      const int64_t cost = ((tiles + G - 1) / G) * ((rows + 15) / 16);
+      if (best < 0 || cost < best) {
+        best = cost;
+        p->persist_zrg = rg;
+      }
+    }
+  }
 }
 
 // Assign (or size) every device buffer.
@@ -572,7 +618,7 @@ size_t layout(pd_plan *p, unsigned char *base) {
   const int nmem = std::max(1, p->members);  // Algorithm-2 states (one per batch member)
   p->T = A.take<double>((size_t)(mx + 1) * mx * nmem);
   p->w = A.take<double>(nbar);
-  p->part = A.take<double>((size_t)3 * p->blas_grid * (mx + 2));
+  p->part = A.take<double>((size_t)3 * std::max(p->blas_grid, p->persist_grid) * (mx + 2));
   p->scal = A.take<double>(pd::kScalWords);
   p->flags = A.take<int>(pd::kFlagWords);
   p->b = A.take<double>(nbar);
@@ -590,7 +636,7 @@ size_t layout(pd_plan *p, unsigned char *base) {
   p->gpart = A.take<double2>((size_t)nf * p->nblk * mx);
   p->srow = A.take<double2>((size_t)nf * mx * nmem);
   p->omega = A.take<double2>((size_t)nf * nmem);
-  p->msys_part = A.take<double>((size_t)p->k5_grid * mx * mx * nmem);
+  p->msys_part = A.take<double>((size_t)std::max(p->k5_grid, p->persist_grid) * mx * mx * nmem);
   if (p->members) {
     p->mscal = A.take<double>((size_t)pd::kScalWords * nmem);
     p->mflags = A.take<int>((size_t)pd::kFlagWords * nmem);
@@ -1071,7 +1117,51 @@ pd_status emit_pre(pd_plan *p, int kind, const double *G, double *U, int use_han
   }
   // x_m = b: the inner matrix of eq. (17) taken as I (two loops in all)
   if (p->loops == 2) pd::launch_inner_fixed(c, p->scal, p->flags, p->y, 2, use_handle, hk);
+  // the persistent step ends with the next step's Arnoldi step: the first one runs here
+  if (p->persist) pd::launch_arnoldi(c, kb);
   return PD_OK;
+}
+
+template <typename T>
+pd::StepArgs<T> step_args(pd_plan *p, int kind, int use_handle, cudaGraphConditionalHandle hk) {
+  pd::StepArgs<T> a{};
+  a.n = (int)p->nbar;
+  a.maxit = p->maxit;
+  a.q = p->q;
+  a.ld = p->maxit + 2;
+  a.klo = p->klo;
+  a.kdiag = p->kdiag;
+  a.kup = p->kup;
+  a.V = p->V;
+  a.w = p->w;
+  a.T = p->T;
+  a.part = p->part;
+  a.scal = p->scal;
+  a.z = p->z;
+  a.Vf = sizeof(T) == 4 ? p->Vf : nullptr;
+  a.flags = p->flags;
+  a.tau = p->tau;
+  a.kc = krylov_ctl(p, kind);
+  a.nf = p->nf;
+  a.nblk = p->nblk;
+  a.shift = p->shift;
+  a.wg = p->wga;
+  a.gpart = p->gpart;
+  a.msys_part = p->msys_part;
+  a.y = p->y;
+  a.srow = p->srow;
+  a.omega = p->omega;
+  a.H = reinterpret_cast<const cpx<T> *>(p->hbuf);
+  a.ldh = p->lds;
+  a.h0 = lane_h0<T>(p);
+  a.zrg = p->persist_zrg;
+  a.nv = p->persist_nv;
+  a.smem = p->persist_smem;
+  a.bar_polls = p->bar_polls;
+  a.bar_extra = p->bar_extra;
+  a.use_handle = use_handle;
+  a.h = hk;
+  return a;
 }
 
 // one step of Algorithm 2 (m read on the device)
@@ -1081,7 +1171,7 @@ pd_status emit_iter(pd_plan *p, int kind, int use_handle, cudaGraphConditionalHa
   pd::KrylovBufs kb = kbufs<T>(p);
   if (kb.members)
     pd::launch_member_arnoldi(c, kb);
-  else
+  else if (!p->persist)  // the persistent step ran this Arnoldi step at its end
     pd::launch_arnoldi(c, kb);
   cpx<T> *H = reinterpret_cast<cpx<T> *>(p->hbuf);
   // no h_k at a breakdown (eq. 12 loses its t-term) or on a frozen step (q > 1); batches
@@ -1100,6 +1190,10 @@ pd_status emit_iter(pd_plan *p, int kind, int use_handle, cudaGraphConditionalHa
     a.skip_flag = noh;
     a.h0 = lane_h0<T>(p);
     pd::launch_pint<T>(c, p->geom, a);
+  }
+  if (p->persist) {
+    pd::launch_step_tail<T>(c, step_args<T>(p, kind, use_handle, hk), p->persist_grid, p->persist_E);
+    return PD_OK;
   }
   const double *h0 = lane_h0<T>(p);
   pd::launch_capacitance(c, kb, p->nf, p->tau, p->shift, p->wga, p->gpart, p->nblk, p->msys_part,
@@ -1173,6 +1267,13 @@ pd_status emit_post(pd_plan *p, int kind, double *U, int use_handle, cudaGraphCo
   return PD_OK;
 }
 
+pd_status timeout_status(pd_plan *p) {
+  return fail(PD_ERR_TIMEOUT,
+              "a grid barrier of the persistent Algorithm-2 step waited %lld polls without the other CTAs; "
+              "U is unspecified, the plan stays usable",
+              p->bar_polls);
+}
+
 // Host-driven loops (timing mode, or when graphs are unavailable): the same kernels,
 // with the host reading the control block after each step.
 template <typename T>
@@ -1186,6 +1287,7 @@ pd_status solve_hostloop(pd_plan *p, const double *G, double *U) {
     while (!p->h_flags[pd::F_KSTOP]) {
       if ((st = emit_iter<T>(p, kind, 0, 0)) != PD_OK) return st;
       if ((st = sync_read(p)) != PD_OK) return st;
+      if (p->h_flags[pd::F_TIMEOUT]) return timeout_status(p);
     }
     if ((st = emit_post<T>(p, kind, U, 0, 0)) != PD_OK) return st;
     if ((st = sync_read(p)) != PD_OK) return st;
@@ -1384,6 +1486,8 @@ pd_status solve_refined(pd_plan *p, const double *G, double *U, pd_stats &s) {
   s.graph = used ? 1 : 0;
   s.zero_freq_fp64 = p->lane ? 1 : 0;
   s.zero_freq_weight = p->nu0;
+  s.persistent_step = p->persist ? 1 : 0;
+  if (f[pd::F_TIMEOUT]) return timeout_status(p);
   if (f[pd::F_NONFIN]) return fail(PD_ERR_NONFINITE, "non-finite value met (input contains NaN/Inf?)");
   if (p->loops) {  // the variant's approximation: no convergence claim
     s.krylov_iters = s.krylov_iters_total = 0;

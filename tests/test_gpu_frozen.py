@@ -42,8 +42,10 @@ def _slow_krylov_problem(c=1e-4):
 
 
 # launch modes of the Krylov vector kernels: a thread-block cluster (n_bar >= 256), one CTA
-# with eq. (13) in the z reduction's last CTA, a cooperative grid of 4 CTAs
-MODES = {"cluster": {}, "one_cta": {"krylov_cluster": -1}, "coop": {"krylov_ctas": 4}}
+# with eq. (13) in the z reduction's last CTA, a cooperative grid of 4 CTAs (one launch per
+# phase of an Algorithm-2 step), and the persistent step (one launch after the shifted solves)
+MODES = {"cluster": {"persistent": -1}, "one_cta": {"krylov_cluster": -1, "persistent": -1},
+         "coop": {"krylov_ctas": 4, "persistent": -1}, "persistent": {"persistent": 1}}
 
 
 @pytest.mark.parametrize("c", [1e-4, 1e-2])

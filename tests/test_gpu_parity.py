@@ -358,13 +358,16 @@ def test_set_operator_refactors(pd, prec, factor):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-@pytest.mark.parametrize("tune", [{"krylov_cluster": -1}, {"krylov_cluster": 4}, {"krylov_cluster": 16},
-                                  {"krylov_ctas": 8}], ids=lambda t: "-".join(f"{k}{v}" for k, v in t.items()))
+@pytest.mark.parametrize("tune", [{"krylov_cluster": -1, "persistent": -1}, {"krylov_cluster": 4, "persistent": -1},
+                                  {"krylov_cluster": 16, "persistent": -1}, {"krylov_ctas": 8, "persistent": -1},
+                                  {"persistent": 1}],
+                         ids=lambda t: "-".join(f"{k}{v}" for k, v in t.items()))
 @pytest.mark.parametrize("P", [W.heat1d_forced(1023, 64, seed=5), W.advdiff1d_pulse(2047, 32, seed=6),
                                W.random_tridiag_problem(300, 16, seed=13)], ids=lambda p: p.name)
 def test_krylov_variants_match_oracle(pd, prec, tune, P):
     """The Algorithm-2 vector steps in one CTA, in clusters of 4 and 16 CTAs (one per SM,
-    reductions through distributed shared memory), and on a cooperative grid."""
+    reductions through distributed shared memory), on a cooperative grid (one launch per
+    phase of a step), and in the persistent step."""
     Uref = R.be_solve_refined(P)
     U, st, _, _ = _solve(pd, P, prec, tune=tune)
     assert R.rel_err(U, Uref) <= TOL[prec], st
