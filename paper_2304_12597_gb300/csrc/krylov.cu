@@ -233,12 +233,13 @@ __host__ __device__ inline size_t k5a_warp_bytes(int m) {
 // shared-memory slice of k5a_warp_bytes(m) bytes at smraw and accumulates the terms of
 // its frequencies there (a thread per frequency, every warp, when m = 1); the CTA's sum
 // over those warps (fixed order) goes to row `cta` of msys_part.  `mb` selects a batch
-// member's block of partial dots (members != 0).  Ends with a CTA barrier.
+// member's blocks of partial dots (members != 0; bpm blocks per member).  Ends with a CTA
+// barrier.
 __device__ void capacitance_terms_body(int cta, int ncta, int nwk, int m, int nf, int maxit, double tau,
                                        const double *__restrict__ T, const double2 *__restrict__ shift,
                                        const double2 *__restrict__ wg, const double2 *__restrict__ gpart,
                                        int nblk, double *msys_part, double2 *srow, const double *scal,
-                                       const int *flags, int members, int mb, unsigned char *smraw) {
+                                       const int *flags, int members, int mb, unsigned char *smraw, int bpm = 1) {
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const size_t wb = k5a_warp_bytes(m);
   const bool busy = wid < nwk;
@@ -253,8 +254,8 @@ __device__ void capacitance_terms_body(int cta, int ncta, int nwk, int m, int nf
     for (int i = lane; i < m * m; i += 32) msw[i] = 0.0;
   __syncwarp();
   // g_k = sum over blocks of the partial dots; after a breakdown the dot pass was skipped
-  // and the t-term vanishes; a batch member takes only its own block's dots
-  const int b0 = members ? mb : 0, b1 = flags[F_BREAK] ? b0 : (members ? b0 + 1 : nblk);
+  // and the t-term vanishes; a batch member takes only its own blocks' dots (bpm of them)
+  const int b0 = members ? mb * bpm : 0, b1 = flags[F_BREAK] ? b0 : (members ? b0 + bpm : nblk);
   if (m == 1) {
     // one step (the common case): S_k = 1 / ((1 - pi_k) + tau t_11) is a scalar, so a
     // thread takes a frequency (a warp of GJ per frequency would leave 31 lanes idle on
@@ -363,7 +364,7 @@ __device__ void capacitance_terms_body(int cta, int ncta, int nwk, int m, int nf
 __global__ void __launch_bounds__(kK5Warps * 32) k_capacitance_terms(
     int nf, int maxit, double tau, const double *__restrict__ T, const double2 *__restrict__ shift,
     const double2 *__restrict__ wg, const double2 *__restrict__ gpart, int nblk, double *msys_part,
-    double2 *srow, const double *scal, int *flags, double2 *omega, double *y, int members) {
+    double2 *srow, const double *scal, int *flags, double2 *omega, double *y, int members, int bpm) {
   grid_dep_wait();
   extern __shared__ __align__(16) unsigned char smraw[];
   if (members) {  // member blockIdx.y of a batch: its own Algorithm-2 state (strided views)
@@ -381,7 +382,7 @@ __global__ void __launch_bounds__(kK5Warps * 32) k_capacitance_terms(
   }
   const int m = flags[F_M] + 1;
   capacitance_terms_body(blockIdx.x, gridDim.x, kK5Warps, m, nf, maxit, tau, T, shift, wg, gpart, nblk, msys_part,
-                         srow, scal, flags, members, (int)blockIdx.y, smraw);
+                         srow, scal, flags, members, (int)blockIdx.y, smraw, bpm);
   // The last CTA to finish (counted in flags[F_CAPCNT]; no CTA waits for another) sums the
   // partials and solves the m x m system, then resets the counter.
   __shared__ int last;
@@ -477,12 +478,16 @@ __global__ void k_sumsq_final(const double *part, int nparts, double *dst) {
 // ---- FP64 all-at-once residual ---------------------------------------------------
 // r = G_t + u_{t-1} - [ (I + tau T_x) u_t  (+ tau T_y u_t in 2D) ] with the coefficient
 // arrays pre-scaled on the host: rx = (tau lo_x, 1 + tau diag_x, tau up_x),
-// ry = (tau lo_y, tau diag_y, tau up_y): four FP64 operations per point in 1D.
+// ry = (tau lo_y, tau diag_y, tau up_y): four FP64 operations per point in 1D.  In 2D the
+// grid has ny rows of nx points; a batch stacks its problems along y, nym rows each, and
+// row iy takes the x-coefficients of problem iy / nym (its T_y has no coupling across
+// problems).  mex (batches): problem j / mlen's residual is scaled by 2^mex (exact).
 template <typename Tout, bool TWO_D>
 __global__ void k_residual(const double *__restrict__ G, const double *__restrict__ U, Tout *__restrict__ R,
                            int nb, int nx, const double *__restrict__ rxl, const double *__restrict__ rxd,
                            const double *__restrict__ rxu, const double *__restrict__ ryl,
-                           const double *__restrict__ ryd, const double *__restrict__ ryu, int ny) {
+                           const double *__restrict__ ryd, const double *__restrict__ ryu, int ny, int nym,
+                           const int *__restrict__ mex, int mlen) {
   grid_dep_wait();
   const int j = blockIdx.x * blockDim.x + threadIdx.x;  // spatial index
   const int64_t t = blockIdx.y;                         // time step
@@ -490,19 +495,45 @@ __global__ void k_residual(const double *__restrict__ G, const double *__restric
   const double *u = U + t * nb;
   const int iy = TWO_D ? j / nx : 0;
   const int ix = TWO_D ? j - iy * nx : j;
+  const int cx = TWO_D ? (iy / nym) * nx + ix : ix;  // x-coefficients of this row's problem
   const double uj = u[j];
   const int64_t idx = t * nb + j;
   double r = G[idx];
   if (t > 0) r += U[idx - nb];
-  r = fma(-(TWO_D ? rxd[ix] + ryd[iy] : rxd[ix]), uj, r);
-  if (ix > 0) r = fma(-rxl[ix], u[j - 1], r);
-  if (ix + 1 < nx) r = fma(-rxu[ix], u[j + 1], r);
+  r = fma(-(TWO_D ? rxd[cx] + ryd[iy] : rxd[cx]), uj, r);
+  if (ix > 0) r = fma(-rxl[cx], u[j - 1], r);
+  if (ix + 1 < nx) r = fma(-rxu[cx], u[j + 1], r);
   if (TWO_D) {
     if (iy > 0) r = fma(-ryl[iy], u[j - nx], r);
     if (iy + 1 < ny) r = fma(-ryu[iy], u[j + nx], r);
   }
+  if (mex) r = ldexp(r, mex[j / mlen]);
   R[idx] = (Tout)r;
 }
+
+template <typename Tout>
+void launch_residual(Ctx &c, const double *G, const double *U, Tout *R, int64_t nt, int64_t ny, int64_t nx,
+                     const double *rxl, const double *rxd, const double *rxu, const double *ryl, const double *ryd,
+                     const double *ryu, int64_t nym, const int *mex, int mlen) {
+  const int nb = (int)(ny * nx);
+  const dim3 grid((unsigned)((nb + 255) / 256), (unsigned)nt);
+  c.launch(sizeof(Tout) == 8 ? "residual_f64_to_f64" : "residual_f64_to_f32",
+           (double)nt * nb * (8 + 8 + sizeof(Tout)), [&] {
+             if (ryl)
+               pdl_launch(c.pdl, k_residual<Tout, true>, grid, dim3(256), 0, c.stream, G, U, R, nb, (int)nx, rxl, rxd,
+                          rxu, ryl, ryd, ryu, (int)ny, (int)nym, mex, mlen);
+             else
+               pdl_launch(c.pdl, k_residual<Tout, false>, grid, dim3(256), 0, c.stream, G, U, R, nb, (int)nx, rxl, rxd,
+                          rxu, ryl, ryd, ryu, (int)ny, (int)nym, mex, mlen);
+           });
+}
+
+template void launch_residual<float>(Ctx &, const double *, const double *, float *, int64_t, int64_t, int64_t,
+                                     const double *, const double *, const double *, const double *, const double *,
+                                     const double *, int64_t, const int *, int);
+template void launch_residual<double>(Ctx &, const double *, const double *, double *, int64_t, int64_t, int64_t,
+                                      const double *, const double *, const double *, const double *, const double *,
+                                      const double *, int64_t, const int *, int);
 
 // ---- persistent Algorithm-2 step ---------------------------------------------------
 
@@ -753,13 +784,13 @@ void launch_arnoldi(Ctx &c, KrylovBufs &k) {
 
 void launch_capacitance(Ctx &c, KrylovBufs &k, int nf, double tau, const double2 *shift, const double2 *wg,
                         const double2 *gpart, int nblk, double *msys_part, int k5_grid, double2 *srow,
-                        double2 *omega, double *y, int members) {
+                        double2 *omega, double *y, int members, int bpm) {
   const size_t smem = k5a_warp_bytes(k.maxit) * kK5Warps;  // sized for the largest m
   cudaFuncSetAttribute(k_capacitance_terms, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   c.launch("capacitance", (double)nf * nblk * 16, [&] {
     pdl_launch(c.pdl, k_capacitance_terms, dim3(k5_grid, members ? members : 1), dim3(kK5Warps * 32), smem,
                c.stream, nf, k.maxit, tau, (const double *)k.T, shift, wg, gpart, nblk, msys_part, srow,
-               members ? k.mscal : k.scal, members ? k.mflags : k.flags, omega, y, members);
+               members ? k.mscal : k.scal, members ? k.mflags : k.flags, omega, y, members, bpm);
   });
 }
 
@@ -851,31 +882,5 @@ void launch_xm(Ctx &c, KrylovBufs &k, const double *y, double *x, float *xf) {
 void launch_sumsq(Ctx &c, const double *part, int nparts, double *dst) {
   c.launch("krylov_sumsq", 0.0, [&] { pdl_launch(c.pdl, k_sumsq_final, dim3(1), dim3(32), 0, c.stream, part, nparts, dst); });
 }
-
-template <typename Tout>
-void launch_residual(Ctx &c, const double *G, const double *U, Tout *R, int64_t nt, int64_t ny, int64_t nx,
-                     const double *rxl, const double *rxd, const double *rxu, const double *ryl, const double *ryd,
-                     const double *ryu) {
-  const int nb = (int)(ny * nx);
-  const dim3 grid((unsigned)((nb + 255) / 256), (unsigned)nt);
-  c.launch(sizeof(Tout) == 8 ? "residual_f64_to_f64" : "residual_f64_to_f32",
-           (double)nt * nb * (8 + 8 + sizeof(Tout)), [&] {
-             if (ryl)
-               pdl_launch(c.pdl, k_residual<Tout, true>, grid, dim3(256), 0, c.stream, G, U, R, nb, (int)nx, rxl, rxd, rxu, ryl,
-                          ryd, ryu,
-                                                                  (int)ny);
-             else
-               pdl_launch(c.pdl, k_residual<Tout, false>, grid, dim3(256), 0, c.stream, G, U, R, nb, (int)nx, rxl, rxd, rxu, ryl,
-                          ryd,
-                                                                   ryu, (int)ny);
-           });
-}
-
-template void launch_residual<float>(Ctx &, const double *, const double *, float *, int64_t, int64_t, int64_t,
-                                     const double *, const double *, const double *, const double *, const double *,
-                                     const double *);
-template void launch_residual<double>(Ctx &, const double *, const double *, double *, int64_t, int64_t, int64_t,
-                                      const double *, const double *, const double *, const double *, const double *,
-                                      const double *);
 
 }  // namespace pd

@@ -231,6 +231,7 @@ struct PintArgs {
   const int *skip_flag;    // if non-null and *skip_flag != 0 the kernel does nothing
   double xm_scale;         // with xm_count: subtract xm_scale * x_m (alpha^{1/l} in Algorithm 3)
   int64_t xm_ldy;          // block blk takes y_m from xm_y + blk * xm_ldy (0: one y_m)
+  int xm_bpm;              // blocks per batch member (2D batches: the modes of its T_y; 0 = 1)
   const cpx<T> *fac_in;    // precomputed factors of every (k, block) system (pint.cu), or null
   cpx<T> *fac_out;         // factor pass: store those factors (R, rvec, Y, omega, V unused)
   // Zero-frequency lane of the binary32 path.  A_0 = (1 - pi_0) I + tau K has the real
@@ -318,7 +319,7 @@ void launch_arnoldi(Ctx &c, KrylovBufs &k);
 int krylov_cluster_size(int want);
 void launch_capacitance(Ctx &c, KrylovBufs &k, int nf, double tau, const double2 *shift,
                         const double2 *wg, const double2 *gpart, int nblk, double *msys_part,
-                        int k5_grid, double2 *srow, double2 *omega, double *y, int members = 0);
+                        int k5_grid, double2 *srow, double2 *omega, double *y, int members = 0, int bpm = 1);
 // Batched plans, one Algorithm 2 per member (one CTA each; krylov_members.cu): the
 // start (beta_b, v_1), an Arnoldi step, and eq. (13) with the per-member decision; the
 // last member of the start and of eq. (13) sets the batch's control block and the
@@ -388,11 +389,13 @@ void launch_refine_decide(Ctx &c, double *scal, int *flags, const RefineCtl &r, 
 void launch_sumsq(Ctx &c, const double *part, int nparts, double *dst);
 // FP64 all-at-once residual R = G - [(I + tau K) U - U Sigma_1^T], stored as Tout
 // (float for the mixed path, double for the FP64 path).  rx = (tau lo_x, 1 + tau diag_x,
-// tau up_x) of length nx; 2D adds ry = (tau lo_y, tau diag_y, tau up_y) along the middle
-// axis (ryl == null in 1D).
+// tau up_x) of length nx per problem; 2D adds ry = (tau lo_y, tau diag_y, tau up_y) along
+// the middle axis (ryl == null in 1D), ny rows in all, nym per problem (batches stack
+// their problems along y).  mex (batches, or null): problem j / mlen's residual scaled by
+// 2^mex[problem].
 template <typename Tout>
 void launch_residual(Ctx &c, const double *G, const double *U, Tout *R, int64_t nt, int64_t ny, int64_t nx,
                      const double *rxl, const double *rxd, const double *rxu, const double *ryl, const double *ryd,
-                     const double *ryu);
+                     const double *ryu, int64_t nym, const int *mex, int mlen);
 
 }  // namespace pd

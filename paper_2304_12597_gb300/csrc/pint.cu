@@ -140,7 +140,7 @@ __device__ void pint_k0_lane(const PintGeom &g, const PintArgs<float> &a, int P,
   }
   if (!a.Vd) mdots = 0;
   const int mx = a.xm_count ? *a.xm_count : 0;
-  const double *xy = a.xm_count ? a.xm_y + (int64_t)blk * a.xm_ldy : nullptr;
+  const double *xy = a.xm_count ? a.xm_y + (int64_t)(blk / (a.xm_bpm > 1 ? a.xm_bpm : 1)) * a.xm_ldy : nullptr;
 #pragma unroll
   for (int i = 0; i < M; ++i) {
     const int e = t + i * P;
@@ -448,7 +448,8 @@ __global__ void __launch_bounds__(MAXT) k_pint(PintGeom g, PintArgs<T> a, size_t
   if (a.xm_count && active) {
     xs = acc;
     const int m = *a.xm_count;
-    const double *xy = a.xm_y + (int64_t)blk * a.xm_ldy;  // per-member y_m in batched plans
+    // per-member y_m in batched plans (a member owns xm_bpm consecutive blocks)
+    const double *xy = a.xm_y + (int64_t)(blk / (a.xm_bpm > 1 ? a.xm_bpm : 1)) * a.xm_ldy;
     T v[M];
 #pragma unroll
     for (int i = 0; i < M; ++i) v[i] = T(0);

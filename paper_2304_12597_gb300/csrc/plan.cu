@@ -174,8 +174,12 @@ struct pd_plan {
   size_t ws_bytes = 0;
 
   int nblk = 1, blen = 0;
-  // batched plans: `batch` problems of up to nxm rows (slot b = columns [b nxm, (b+1) nxm))
+  // batched plans: `batch` problems of up to nxm unknowns (slot b = columns [b nxm, (b+1) nxm));
+  // in 2D every problem is nx x nym and the stacked grid is nx x (batch nym), ny = batch nym
   int batch = 1;
+  int64_t nym = 1;   // rows of T_y per problem (the DST length); 1 in 1D
+  int64_t nrx = 0;   // length of the x-coefficient arrays: T_x of every problem
+  int64_t nxd = 0;   // the descriptor's nx
   int64_t nxm = 0;
   int bnc = 0;                  // time-row groups of the per-problem norm pass
   double *Gs = nullptr;         // G with every problem scaled to unit norm
@@ -291,12 +295,12 @@ struct HostOp {
 // 1e-12 absorbs the rounding of operators that are dominant with equality (upwind).
 pd_status check_dominance(const pd_desc *d) {
   const int nb = d->batch > 1 ? d->batch : 1;
-  double mu = 0.0;  // smallest eigenvalue of T_y (2D)
-  if (d->dim == 2) {
-    const double dy = d->k_diag_y[0], cy = d->ny > 1 ? d->k_up_y[0] : 0.0;
-    mu = dy - 2.0 * std::fabs(cy) * std::cos(M_PI / (double)(d->ny + 1));
-  }
   for (int b = 0; b < nb; ++b) {
+    double mu = 0.0;  // smallest eigenvalue of the problem's T_y (2D)
+    if (d->dim == 2) {
+      const double dy = d->k_diag_y[(int64_t)b * d->ny], cy = d->ny > 1 ? d->k_up_y[(int64_t)b * d->ny] : 0.0;
+      mu = dy - 2.0 * std::fabs(cy) * std::cos(M_PI / (double)(d->ny + 1));
+    }
     const int64_t n = (nb > 1 && d->batch_nx) ? d->batch_nx[b] : d->nx;
     const double *lo = d->k_lo + (int64_t)b * d->nx, *di = d->k_diag + (int64_t)b * d->nx,
                  *up = d->k_up + (int64_t)b * d->nx;
@@ -370,13 +374,18 @@ pd_status validate(const pd_desc *d) {
     if (!d->k_lo_y || !d->k_diag_y || !d->k_up_y) return fail(PD_ERR_INVALID_ARG, "T_y arrays are NULL");
     if (!is_pow2(d->ny + 1) || d->ny + 1 > 4096)
       return fail(PD_ERR_UNSUPPORTED, "2D needs ny + 1 to be a power of two <= 4096 (DST-I by FFT)");
-    const double dd = d->k_diag_y[0];
-    const double c = d->ny > 1 ? d->k_up_y[0] : 0.0;
-    const double tol = 1e-12 * (std::fabs(dd) + std::fabs(c));
-    for (int64_t i = 0; i < d->ny; ++i) {
-      if (std::fabs(d->k_diag_y[i] - dd) > tol) return fail(PD_ERR_UNSUPPORTED, "T_y must be Toeplitz");
-      if (i + 1 < d->ny && (std::fabs(d->k_up_y[i] - c) > tol || std::fabs(d->k_lo_y[i + 1] - c) > tol))
-        return fail(PD_ERR_UNSUPPORTED, "T_y must be symmetric Toeplitz");
+    for (int b = 0; b < (d->batch > 1 ? d->batch : 1); ++b) {  // T_y of every problem
+      const double *ylo = d->k_lo_y + (int64_t)b * d->ny, *ydi = d->k_diag_y + (int64_t)b * d->ny,
+                   *yup = d->k_up_y + (int64_t)b * d->ny;
+      const double dd = ydi[0];
+      const double c = d->ny > 1 ? yup[0] : 0.0;
+      const double tol = 1e-12 * (std::fabs(dd) + std::fabs(c));
+      for (int64_t i = 0; i < d->ny; ++i) {
+        if (!std::isfinite(ydi[i]) || std::fabs(ydi[i] - dd) > tol)
+          return fail(PD_ERR_UNSUPPORTED, "T_y must be Toeplitz");
+        if (i + 1 < d->ny && (std::fabs(yup[i] - c) > tol || std::fabs(ylo[i + 1] - c) > tol))
+          return fail(PD_ERR_UNSUPPORTED, "T_y must be symmetric Toeplitz");
+      }
     }
   }
   if (d->tune_pint_rows != 0 && d->tune_pint_rows != 4 && d->tune_pint_rows != 8 && d->tune_pint_rows != 16)
@@ -418,7 +427,12 @@ pd_status validate(const pd_desc *d) {
     return fail(PD_ERR_INVALID_ARG, "barrier_polls, tune_persist_ctas must be >= 0; barrier_extra in 0..1024");
   if (d->batch < 0) return fail(PD_ERR_INVALID_ARG, "batch must be >= 0");
   if (d->batch > 1) {
-    if (d->dim != 1) return fail(PD_ERR_UNSUPPORTED, "batching is built for 1D problems only");
+    if (d->dim == 2) {  // every problem nx x ny; its Algorithm 2 runs in one CTA
+      if (d->batch_nx) return fail(PD_ERR_UNSUPPORTED, "2D batches share nx and ny (batch_nx must be NULL)");
+      if (d->nx * d->ny > 8192)
+        return fail(PD_ERR_UNSUPPORTED, "2D batches need nx * ny <= 8192 per problem (got %lld)",
+                    (long long)(d->nx * d->ny));
+    }
     if (d->batch > 65535) return fail(PD_ERR_UNSUPPORTED, "at most 65535 problems per batch");
     for (int b = 0; b < d->batch; ++b) {
       if (d->batch_nx && (d->batch_nx[b] < 1 || d->batch_nx[b] > d->nx))
@@ -436,9 +450,18 @@ pd_status validate(const pd_desc *d) {
 void fill_geometry(pd_plan *p, const pd_desc *d) {
   p->dim = d->dim;
   p->batch = d->batch > 1 ? d->batch : 1;
-  p->nxm = d->nx;
-  p->nx = d->nx * p->batch;  // 1D: the stacked spatial length
-  p->ny = d->dim == 2 ? d->ny : 1;
+  p->nxd = d->nx;
+  p->nrx = d->nx * p->batch;
+  if (d->dim == 2) {  // problems stacked along y: nx x (batch ny)
+    p->nym = d->ny;
+    p->nxm = d->nx * d->ny;
+    p->nx = d->nx;
+  } else {
+    p->nym = 1;
+    p->nxm = d->nx;
+    p->nx = d->nx * p->batch;  // 1D: the stacked spatial length
+  }
+  p->ny = d->dim == 2 ? d->ny * p->batch : 1;
   p->nbar = p->nx * p->ny;
   p->nt = d->nt;
   p->nf = (int)(d->nt / 2 + 1);
@@ -463,8 +486,9 @@ void fill_geometry(pd_plan *p, const pd_desc *d) {
   if (p->loops) p->max_refine = 0;  // one solve: the variant's approximation
   p->refine_tol = d->refine_tol > 0 ? d->refine_tol : (d->precision == PD_FP64 ? 1e-14 : 1e-11);
   p->host_io = d->host_io;
-  p->nblk = p->batch > 1 ? p->batch : (int)p->ny;
-  p->blen = (int)p->nxm;
+  // tridiagonal blocks of nx rows: one per problem (1D) or per mode of T_y (2D)
+  p->nblk = p->dim == 2 ? (int)p->ny : p->batch;
+  p->blen = (int)d->nx;
   p->bnc = (int)std::min<int64_t>(p->nt, 64);
   p->lds = (p->nbar + 31) / 32 * 32;
   const int sms = pd::sm_count();
@@ -584,12 +608,12 @@ size_t layout(pd_plan *p, unsigned char *base) {
     p->tdiag_f = A.take<float>(nbar);
     p->tup_f = A.take<float>(nbar);
   }
-  p->xlo = A.take<double>(p->nx);
-  p->xdiag = A.take<double>(p->nx);
-  p->xup = A.take<double>(p->nx);
-  p->rxl = A.take<double>(p->nx);
-  p->rxd = A.take<double>(p->nx);
-  p->rxu = A.take<double>(p->nx);
+  p->xlo = A.take<double>(p->nrx);
+  p->xdiag = A.take<double>(p->nrx);
+  p->xup = A.take<double>(p->nrx);
+  p->rxl = A.take<double>(p->nrx);
+  p->rxd = A.take<double>(p->nrx);
+  p->rxu = A.take<double>(p->nrx);
   if (p->dim == 2) {
     p->ylo = A.take<double>(p->ny);
     p->ydiag = A.take<double>(p->ny);
@@ -602,8 +626,8 @@ size_t layout(pd_plan *p, unsigned char *base) {
   p->tw_d = A.take<cpx<double>>(ntw);
   if (mixed) p->tw_f = A.take<cpx<float>>(ntw);
   if (p->dim == 2) {
-    p->twy_d = A.take<cpx<double>>(p->ny + 1);
-    if (mixed) p->twy_f = A.take<cpx<float>>(p->ny + 1);
+    p->twy_d = A.take<cpx<double>>(p->nym + 1);
+    if (mixed) p->twy_f = A.take<cpx<float>>(p->nym + 1);
   }
   p->spec = mixed ? (void *)A.take<cpx<float>>((size_t)nf * p->lds) : (void *)A.take<cpx<double>>((size_t)nf * p->lds);
   p->hbuf = mixed ? (void *)A.take<cpx<float>>((size_t)nf * p->lds) : (void *)A.take<cpx<double>>((size_t)nf * p->lds);
@@ -670,7 +694,49 @@ size_t layout(pd_plan *p, unsigned char *base) {
 
 // Batched plans: K~ = diag(tau_b K_b), each block padded to nx rows with decoupled
 // identity rows (their unknowns are zero); blocks never couple.
+// 2D batch: problem b is nx x ny with its own T_x, T_y and tau_b, stacked along y (rows
+// [b ny, (b+1) ny) of the nx x (batch ny) grid).  Its blocks (one per mode l of its T_y)
+// carry tau_b (T_x + mu_{b,l} I); the stacked T_y has no coupling across problems.
+HostOp build_batched_operator_2d(const pd_desc *d) {
+  HostOp h;
+  const int64_t nx = d->nx, ny = d->ny, B = d->batch;
+  h.xlo.assign(nx * B, 0.0);
+  h.xdiag.assign(nx * B, 1.0);
+  h.xup.assign(nx * B, 0.0);
+  h.ylo.assign(ny * B, 0.0);
+  h.ydiag.assign(ny * B, 0.0);
+  h.yup.assign(ny * B, 0.0);
+  h.lo.resize(nx * ny * B);
+  h.diag.resize(nx * ny * B);
+  h.up.resize(nx * ny * B);
+  for (int64_t b = 0; b < B; ++b) {
+    const double tb = d->batch_tau ? d->batch_tau[b] : d->tau;
+    for (int64_t i = 0; i < nx; ++i) {
+      const int64_t j = b * nx + i;
+      h.xlo[j] = i > 0 ? tb * d->k_lo[j] : 0.0;
+      h.xdiag[j] = tb * d->k_diag[j];
+      h.xup[j] = i + 1 < nx ? tb * d->k_up[j] : 0.0;
+    }
+    const double dd = d->k_diag_y[b * ny], c = ny > 1 ? d->k_up_y[b * ny] : 0.0;
+    for (int64_t l = 0; l < ny; ++l) {
+      const int64_t r = b * ny + l;
+      h.ylo[r] = l > 0 ? tb * d->k_lo_y[r] : 0.0;
+      h.ydiag[r] = tb * d->k_diag_y[r];
+      h.yup[r] = l + 1 < ny ? tb * d->k_up_y[r] : 0.0;
+      const double mu = tb * (dd + 2.0 * c * std::cos(M_PI * (double)(l + 1) / (double)(ny + 1)));
+      for (int64_t ix = 0; ix < nx; ++ix) {
+        const int64_t j = r * nx + ix;
+        h.lo[j] = h.xlo[b * nx + ix];
+        h.diag[j] = h.xdiag[b * nx + ix] + mu;
+        h.up[j] = h.xup[b * nx + ix];
+      }
+    }
+  }
+  return h;
+}
+
 HostOp build_batched_operator(const pd_desc *d) {
+  if (d->dim == 2) return build_batched_operator_2d(d);
   HostOp h;
   const int64_t nx = d->nx, B = d->batch, n = nx * B;
   h.xlo.assign(n, 0.0);
@@ -816,8 +882,8 @@ pd_status upload_operator(pd_plan *p, const pd_desc *desc) {
     fdiag[j] = (float)tdiag[j];
     fup[j] = (float)tup[j];
   }
-  std::vector<double> rxl(p->nx), rxd(p->nx), rxu(p->nx), ryl(p->ny), ryd(p->ny), ryu(p->ny);
-  for (int64_t i = 0; i < p->nx; ++i) {
+  std::vector<double> rxl(p->nrx), rxd(p->nrx), rxu(p->nrx), ryl(p->ny), ryd(p->ny), ryu(p->ny);
+  for (int64_t i = 0; i < p->nrx; ++i) {
     rxl[i] = p->tau * h.xlo[i];
     rxd[i] = 1.0 + p->tau * h.xdiag[i];
     rxu[i] = p->tau * h.xup[i];
@@ -837,10 +903,10 @@ pd_status upload_operator(pd_plan *p, const pd_desc *desc) {
       (st = upload(p->kup, h.up.data(), nbar, s)) || (st = upload(p->tlo_d, tlo.data(), nbar, s)) ||
       (st = upload(p->tdiag_d, tdiag.data(), nbar, s)) || (st = upload(p->tup_d, tup.data(), nbar, s)) ||
       (st = upload(p->tlo_f, flo.data(), nbar, s)) || (st = upload(p->tdiag_f, fdiag.data(), nbar, s)) ||
-      (st = upload(p->tup_f, fup.data(), nbar, s)) || (st = upload(p->xlo, h.xlo.data(), p->nx, s)) ||
-      (st = upload(p->xdiag, h.xdiag.data(), p->nx, s)) || (st = upload(p->xup, h.xup.data(), p->nx, s)) ||
-      (st = upload(p->rxl, rxl.data(), p->nx, s)) || (st = upload(p->rxd, rxd.data(), p->nx, s)) ||
-      (st = upload(p->rxu, rxu.data(), p->nx, s)))
+      (st = upload(p->tup_f, fup.data(), nbar, s)) || (st = upload(p->xlo, h.xlo.data(), p->nrx, s)) ||
+      (st = upload(p->xdiag, h.xdiag.data(), p->nrx, s)) || (st = upload(p->xup, h.xup.data(), p->nrx, s)) ||
+      (st = upload(p->rxl, rxl.data(), p->nrx, s)) || (st = upload(p->rxd, rxd.data(), p->nrx, s)) ||
+      (st = upload(p->rxu, rxu.data(), p->nrx, s)))
     return st;
   if (p->dim == 2 && ((st = upload(p->ryl, ryl.data(), p->ny, s)) || (st = upload(p->ryd, ryd.data(), p->ny, s)) ||
                       (st = upload(p->ryu, ryu.data(), p->ny, s)) || (st = upload(p->ylo, h.ylo.data(), p->ny, s)) ||
@@ -848,7 +914,9 @@ pd_status upload_operator(pd_plan *p, const pd_desc *desc) {
     return st;
   if (p->batch > 1) {
     std::vector<int> bnx(p->batch);
-    for (int b = 0; b < p->batch; ++b) bnx[b] = (int)(desc->batch_nx ? desc->batch_nx[b] : desc->nx);
+    // unknowns of problem b inside its slot (2D: the whole nx x ny grid)
+    for (int b = 0; b < p->batch; ++b)
+      bnx[b] = p->dim == 2 ? (int)p->nxm : (int)(desc->batch_nx ? desc->batch_nx[b] : desc->nx);
     if ((st = upload(p->bnx, bnx.data(), p->batch, s))) return st;
   }
   std::vector<double> msc;
@@ -1078,7 +1146,7 @@ pd_status emit_pre(pd_plan *p, int kind, const double *G, double *U, int use_han
       pd::launch_fft_r2c<T, double>(c, G, p->nbar, p->nbar, nt, time_tw<T>(p), S, p->lds, row_scale<T>(p, false),
                                     rnp);
     } else {
-      pd::launch_dst_y<double, T, T>(c, G, tmp, p->nt, p->ny, p->nx, dst_tw<T>(p), 0);
+      pd::launch_dst_y<double, T, T>(c, G, tmp, p->nt * p->batch, p->nym, p->nx, dst_tw<T>(p), 0);
       pd::launch_fft_r2c<T, T>(c, tmp, p->nbar, p->nbar, nt, time_tw<T>(p), S, p->lds, row_scale<T>(p, false), rnp);
     }
   } else {
@@ -1086,8 +1154,9 @@ pd_status emit_pre(pd_plan *p, int kind, const double *G, double *U, int use_han
       pd::launch_fft_r2c_residual<T>(c, G, U, p->nbar, nt, p->rxl, p->rxd, p->rxu, time_tw<T>(p), S, p->lds,
                                      row_scale<T>(p, false), p->batch > 1 ? p->mex : nullptr, (int)p->nxm, rnp);
     } else {
-      pd::launch_residual<T>(c, G, U, res, p->nt, p->ny, p->nx, p->rxl, p->rxd, p->rxu, p->ryl, p->ryd, p->ryu);
-      pd::launch_dst_y<T, T, T>(c, res, tmp, p->nt, p->ny, p->nx, dst_tw<T>(p), 0);
+      pd::launch_residual<T>(c, G, U, res, p->nt, p->ny, p->nx, p->rxl, p->rxd, p->rxu, p->ryl, p->ryd, p->ryu,
+                             p->nym, p->batch > 1 ? p->mex : nullptr, (int)p->nxm);
+      pd::launch_dst_y<T, T, T>(c, res, tmp, p->nt * p->batch, p->nym, p->nx, dst_tw<T>(p), 0);
       pd::launch_fft_r2c<T, T>(c, tmp, p->nbar, p->nbar, nt, time_tw<T>(p), S, p->lds, row_scale<T>(p, false), rnp);
     }
   }
@@ -1198,7 +1267,7 @@ pd_status emit_iter(pd_plan *p, int kind, int use_handle, cudaGraphConditionalHa
   const double *h0 = lane_h0<T>(p);
   pd::launch_capacitance(c, kb, p->nf, p->tau, p->shift, p->wga, p->gpart, p->nblk, p->msys_part,
                          kb.members ? p->k5_grid_members : p->k5_grid,
-                         p->srow, p->omega, p->y, kb.members);
+                         p->srow, p->omega, p->y, kb.members, (int)p->nym);
   // z = sum_i gamma_i h_i (e_m^T S_i y_m) from the stored h_i, then eq. (13)
   if (kb.members) {
     pd::launch_zsum<T>(c, p->nf, p->nbar, H, p->lds, p->omega, p->z, noh, nullptr, kb.mlen, h0);
@@ -1227,7 +1296,8 @@ pd_status emit_post(pd_plan *p, int kind, double *U, int use_handle, cudaGraphCo
   a.ldr = p->lds;
   a.xm_count = p->flags + pd::F_M;  // x_m = V_m y_m formed by each team
   a.xm_y = p->y;
-  a.xm_ldy = p->members ? p->maxit + 1 : 0;  // batch member blk: its own y_m
+  a.xm_ldy = p->members ? p->maxit + 1 : 0;  // batch member: its own y_m
+  a.xm_bpm = (int)p->nym;                     // blocks per member (2D: one per mode of T_y)
   a.V = vbasis<T>(p);
   a.ldv = p->nbar;
   a.xm_Vd = p->V;
@@ -1250,9 +1320,16 @@ pd_status emit_post(pd_plan *p, int kind, double *U, int use_handle, cudaGraphCo
   fin.h = hr;
   int nparts = 0;
   if (p->batch > 1) {  // per-problem norms and decision (every problem must converge)
-    pd::launch_fft_c2r<T>(c, S, p->lds, p->nbar, nt, time_tw<T>(p), U, p->nbar, kind == 0 ? 0 : 1, nullptr,
-                          &nparts, nullptr, row_scale<T>(p, true), p->colsum, kind == 0 ? nullptr : p->mex,
-                          (int)p->nxm);
+    if (p->dim == 2) {  // the DST is orthonormal: the column norms of its input are delta's
+      T *tmp = tmp_buf<T>(p);
+      pd::launch_fft_c2r<T>(c, S, p->lds, p->nbar, nt, time_tw<T>(p), tmp, p->nbar, fp64 ? 0 : 2, nullptr, &nparts,
+                            nullptr, row_scale<T>(p, true), p->colsum, kind == 0 ? nullptr : p->mex, (int)p->nxm);
+      pd::launch_dst_y<T, double, T>(c, tmp, U, p->nt * p->batch, p->nym, p->nx, dst_tw<T>(p), kind == 0 ? 0 : 1);
+    } else {
+      pd::launch_fft_c2r<T>(c, S, p->lds, p->nbar, nt, time_tw<T>(p), U, p->nbar, kind == 0 ? 0 : 1, nullptr,
+                            &nparts, nullptr, row_scale<T>(p, true), p->colsum, kind == 0 ? nullptr : p->mex,
+                            (int)p->nxm);
+    }
     pd::launch_member_decide(c, p->colsum, (int)p->nxm, p->bnx, p->batch, p->md2, p->mref2, p->mprev, p->mex,
                              p->scal, p->flags, refine_ctl(p), use_handle, hr);
   } else if (p->dim == 1) {
@@ -1262,7 +1339,7 @@ pd_status emit_post(pd_plan *p, int kind, double *U, int use_handle, cudaGraphCo
     T *tmp = tmp_buf<T>(p);
     pd::launch_fft_c2r<T>(c, S, p->lds, p->nbar, nt, time_tw<T>(p), tmp, p->nbar, fp64 ? 0 : 2, p->norm_part,
                           &nparts, &fin, row_scale<T>(p, true));
-    pd::launch_dst_y<T, double, T>(c, tmp, U, p->nt, p->ny, p->nx, dst_tw<T>(p), kind == 0 ? 0 : 1);
+    pd::launch_dst_y<T, double, T>(c, tmp, U, p->nt, p->nym, p->nx, dst_tw<T>(p), kind == 0 ? 0 : 1);
   }
   return PD_OK;
 }
@@ -1605,7 +1682,7 @@ pd_status paradiag_plan(const pd_desc *desc, void *workspace, size_t workspace_b
       (st = upload(p->tsi_f, tsif.data(), nt, s)))
     return cleanup(st);
   if (p->dim == 2) {
-    const int N = (int)(2 * (p->ny + 1));
+    const int N = (int)(2 * (p->nym + 1));
     std::vector<cpx<double>> ty(N / 2);
     std::vector<cpx<float>> tyf(N / 2);
     for (int k = 0; k < N / 2; ++k) {
@@ -1631,7 +1708,7 @@ pd_status paradiag_set_operator(pd_plan *p, const pd_desc *desc) {
   if ((st = validate(desc)) != PD_OK) return st;
   const int batch = desc->batch > 1 ? desc->batch : 1;
   const int64_t ny = desc->dim == 2 ? desc->ny : 1;
-  if (desc->dim != p->dim || desc->nx != p->nxm || ny != p->ny || desc->nt != p->nt || batch != p->batch ||
+  if (desc->dim != p->dim || desc->nx != p->nxd || ny != p->nym || desc->nt != p->nt || batch != p->batch ||
       desc->precision != p->precision)
     return fail(PD_ERR_INVALID_ARG, "paradiag_set_operator: desc has a different shape or precision than the plan");
   if (desc->m_diag && !p->mass)
@@ -1799,7 +1876,7 @@ pd_status paradiag_dst_y(pd_plan *p, const double *X, double *Y) {
   if (st != PD_OK) return st;
   if (p->dim != 2) return fail(PD_ERR_INVALID_ARG, "paradiag_dst_y needs a 2D plan");
   if (!X || !Y) return fail(PD_ERR_INVALID_ARG, "NULL pointer");
-  pd::launch_dst_y<double, double, double>(p->ctx, X, Y, p->nt, p->ny, p->nx, p->twy_d, 0);
+  pd::launch_dst_y<double, double, double>(p->ctx, X, Y, p->nt * p->batch, p->nym, p->nx, p->twy_d, 0);
   CK(cudaStreamSynchronize(p->ctx.stream));
   return ctx_status(p);
 }
@@ -1814,7 +1891,7 @@ pd_status paradiag_last_vectors(pd_plan *p, double *b, double *x) {
     if (p->dim == 1) {
       CK(cudaMemcpyAsync(dst[i], src[i], sizeof(double) * p->nbar, cudaMemcpyDeviceToDevice, p->ctx.stream));
     } else {
-      pd::launch_dst_y<double, double, double>(p->ctx, src[i], dst[i], 1, p->ny, p->nx, p->twy_d, 0);
+      pd::launch_dst_y<double, double, double>(p->ctx, src[i], dst[i], p->batch, p->nym, p->nx, p->twy_d, 0);
     }
   }
   CK(cudaStreamSynchronize(p->ctx.stream));

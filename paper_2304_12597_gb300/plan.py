@@ -92,16 +92,21 @@ class Plan:
 
     @classmethod
     def from_problems(cls, problems, **kw):
-        """One batched plan for a list of 1D problems (fields of workloads.Problem).  Slot b
-        holds problem b, padded to the largest n_x (or to the keyword nx, if larger).
+        """One batched plan for a list of problems (fields of workloads.Problem).  1D: slot b
+        holds problem b, padded to the largest n_x (or to the keyword nx, if larger).  2D:
+        every problem has the same nx x ny grid (nx ny <= 8192), its own T_x, T_y and tau,
+        and slot b is its nx ny unknowns.
 
         The plan's n_t is the largest n_t,b.  Backward Euler is causal: rows 1..l_b of the
         all-at-once solution depend only on rows 1..l_b of G.  So a problem with fewer time
         steps is solved exactly by the longer system with its G extended by zero rows
         (stack), and its answer is the first n_t,b rows of its slot (unstack)."""
         nt = max(P.nt for P in problems)
-        if any(P.dim != 1 for P in problems):
-            raise ValueError("a batch needs 1D problems")
+        dims = {P.dim for P in problems}
+        if dims == {2}:
+            return cls._from_problems_2d(problems, nt, **kw)
+        if dims != {1}:
+            raise ValueError("a batch needs problems of one dimension")
         nx = max(max(P.nx for P in problems), int(kw.pop("nx", 0) or 0))  # slot length
         B = len(problems)
         lo, di, up = np.zeros((B, nx)), np.ones((B, nx)), np.zeros((B, nx))
@@ -117,20 +122,37 @@ class Plan:
         args.update(kw)
         return cls(**args)
 
+    @classmethod
+    def _from_problems_2d(cls, problems, nt, **kw):
+        nx, ny = problems[0].nx, problems[0].ny
+        if any(P.nx != nx or P.ny != ny for P in problems):
+            raise ValueError("a 2D batch needs problems of one grid size")
+        cat = lambda name: np.concatenate([np.asarray(getattr(P, name), dtype=np.float64) for P in problems])
+        args = dict(dim=2, nx=nx, ny=ny, nt=nt, tau=problems[0].tau, k_lo=cat("k_lo"), k_diag=cat("k_diag"),
+                    k_up=cat("k_up"), k_lo_y=cat("k_lo_y"), k_diag_y=cat("k_diag_y"), k_up_y=cat("k_up_y"),
+                    batch=len(problems), batch_tau=[P.tau for P in problems])
+        args.update(kw)
+        return cls(**args)
+
+    @property
+    def slot(self):
+        """Unknowns per problem slot of a batched plan (n_x in 1D, n_x n_y in 2D)."""
+        return self.nx * self.ny
+
     def stack(self, arrays):
-        """(nt, batch * nx) float64 array with array b (n_t,b, n_x,b) in slot b, zero-padded
-        in space and, past row n_t,b, in time."""
-        out = np.zeros((self.nt, self.batch, self.nx))
+        """(nt, batch * slot) float64 array with array b (n_t,b, n_x,b) in slot b, zero-padded
+        in space and, past row n_t,b, in time (2D: arrays of n_x n_y columns)."""
+        out = np.zeros((self.nt, self.batch, self.slot))
         for b, a in enumerate(arrays):
-            if a.shape[0] > self.nt or a.shape[1] > self.nx:
+            if a.shape[0] > self.nt or a.shape[1] > self.slot:
                 raise ValueError("array does not fit its slot")
             out[:a.shape[0], b, :a.shape[1]] = a
-        return out.reshape(self.nt, self.batch * self.nx)
+        return out.reshape(self.nt, self.batch * self.slot)
 
     def unstack(self, U, nxs, nts=None):
-        """Slot b of a (nt, batch * nx) array, cut to n_x,b columns and its first n_t,b rows
-        (all rows when nts is None)."""
-        V = U.reshape(self.nt, self.batch, self.nx)
+        """Slot b of a (nt, batch * slot) array, cut to n_x,b columns (2D: n_x n_y) and its
+        first n_t,b rows (all rows when nts is None)."""
+        V = U.reshape(self.nt, self.batch, self.slot)
         nts = [self.nt] * len(nxs) if nts is None else nts
         return [V[:t, b, :n] for b, (n, t) in enumerate(zip(nxs, nts))]
 

@@ -100,9 +100,10 @@ def _desc(B, **kw):
         d.m_diag = p(m)
     if kw.get("dim") == 2:
         ny = kw.get("ny", 7)
-        ylo = kw.get("y_lo", np.full(ny, -1.0))
-        ydi = kw.get("y_diag", np.full(ny, 2.0))
-        yup = kw.get("y_up", np.full(ny, -1.0))
+        nb = max(kw.get("batch", 1), 1)  # T_y of every problem of a batch
+        ylo = kw.get("y_lo", np.full(ny * nb, -1.0))
+        ydi = kw.get("y_diag", np.full(ny * nb, 2.0))
+        yup = kw.get("y_up", np.full(ny * nb, -1.0))
         keep += [ylo, ydi, yup]
         d.k_lo_y, d.k_diag_y, d.k_up_y = p(ylo), p(ydi), p(yup)
     d._keep = keep
@@ -165,7 +166,7 @@ def test_valid_descriptors_have_a_workspace(B):
     ({"tune_cap_ctas": 5000}, 1),
     ({"tune_fft_cols": 6}, 1),
     ({"batch": -1}, 1),
-    ({"batch": 2, "dim": 2, "ny": 7}, 2),
+    ({"batch": 2, "dim": 2, "n": 127, "ny": 127}, 2),         # 2D batches: nx ny <= 8192
     ({"batch": 3, "batch_nx": [31, 32, 1]}, 1),
     ({"batch": 3, "batch_nx": [31, 0, 1]}, 1),
     ({"batch": 2, "batch_tau": [0.1, 0.0]}, 1),
@@ -254,7 +255,7 @@ def test_batch_stack_pads_time_and_unstack_cuts_it():
     n_x; unstack returns each problem's first n_t,b rows and n_x,b columns."""
     from types import SimpleNamespace
     from paper_2304_12597_gb300.plan import Plan
-    slots = SimpleNamespace(nt=8, batch=3, nx=5)
+    slots = SimpleNamespace(nt=8, batch=3, nx=5, slot=5)  # slot: unknowns per problem (1D: n_x)
     arrays = [np.full((8, 5), 1.0), np.full((2, 3), 2.0), np.full((4, 1), 3.0)]
     S = Plan.stack(slots, arrays)
     assert S.shape == (8, 15)
@@ -267,3 +268,20 @@ def test_batch_stack_pads_time_and_unstack_cuts_it():
         assert np.array_equal(a, b)
     with pytest.raises(ValueError):
         Plan.stack(slots, [np.zeros((9, 5))])
+
+
+
+def test_2d_batch_limits_are_checked(B):
+    """2D batches share one grid (batch_nx must be NULL) and run each problem's Algorithm 2
+    in one CTA (nx ny <= 8192); both are checked before any device work, and T_y must be
+    symmetric Toeplitz in every problem."""
+    st, _ = _size_status(B, _desc(B, dim=2, n=127, ny=127, batch=2, precision=1))
+    assert st == 2 and "8192" in B.last_error()
+    st, _ = _size_status(B, _desc(B, dim=2, n=31, ny=31, batch=2, batch_nx=[31, 31]))
+    assert st == 2 and "batch_nx" in B.last_error()
+    y_diag = np.concatenate([np.full(7, 2.0), np.full(7, 3.0)])
+    y_diag[10] = 3.5  # problem 1's T_y is not Toeplitz
+    st, _ = _size_status(B, _desc(B, dim=2, n=31, ny=7, batch=2, y_diag=y_diag))
+    assert st == 2 and "Toeplitz" in B.last_error()
+    st, n = _size_status(B, _desc(B, dim=2, n=63, ny=63, batch=3, batch_tau=[0.1, 0.2, 0.3], precision=1))
+    assert st == 0 and n > 0, B.last_error()

@@ -153,3 +153,55 @@ def test_batch_of_uneven_nt_matches_oracle_per_problem(pd, prec, alpha):
         assert Ub.shape == (P.nt, P.nx)
         err = R.rel_err(Ub, R.be_solve_refined(P))
         assert err <= TOL[prec], (P.name, err, st)
+
+
+# ----------------------------------------------------------------------------
+# 2D batches: problems of one grid stacked along y (nx x (batch ny)); each keeps its own
+# T_x, T_y (diffusion nu_b) and tau_b, its own DST blocks and its own Algorithm 2
+# ----------------------------------------------------------------------------
+
+
+def _heat2d(n, nt, T, seed, nu=1.0, scale=1.0):
+    P = W.heat2d_smooth(n, nt, T=T, seed=seed)
+    for name in ("k_lo", "k_diag", "k_up", "k_lo_y", "k_diag_y", "k_up_y"):
+        setattr(P, name, getattr(P, name) * nu)
+    P.G = P.G * scale
+    return P
+
+
+def _mix2d(nt, n=31):
+    """One grid, different T (tau), diffusion (1e-3..1), magnitudes (1e-5..1e3) and steps."""
+    return [
+        _heat2d(n, nt, 0.1, seed=1),
+        _heat2d(n, nt, 0.5, seed=2, nu=1e-2, scale=1e-5),
+        _heat2d(n, nt // 2, 0.05, seed=3, nu=0.3, scale=1e3),
+        _heat2d(n, nt, 1.0, seed=4, nu=1e-3),
+    ]
+
+
+@pytest.mark.parametrize("prec,alpha", MIXES)
+def test_batch_2d_matches_oracle_per_problem(pd, prec, alpha):
+    probs = _mix2d(32)
+    with pd.Plan.from_problems(probs, precision=prec, alpha=alpha, device=dev()) as plan:
+        G = torch.from_numpy(plan.stack([P.G for P in probs])).to(dev())
+        U, st = plan.solve(G)
+        parts = plan.unstack(U.cpu().numpy(), [P.nx * P.ny for P in probs], [P.nt for P in probs])
+    for P, Ub in zip(probs, parts):
+        err = R.rel_err(Ub, R.be_solve_refined(P))
+        assert err <= TOL[prec], (P.name, err, st)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_2d_member_equals_its_single_solve(pd, prec):
+    """A 63 x 63 problem (its Algorithm 2 on 3969 entries in one CTA) gives the same U in a
+    batch as alone."""
+    probs = [_heat2d(63, 32, 0.1, seed=7), _heat2d(63, 32, 0.2, seed=8, nu=0.05)]
+    with pd.Plan.from_problems(probs, precision=prec, device=dev()) as plan:
+        G = torch.from_numpy(plan.stack([P.G for P in probs])).to(dev())
+        U, _ = plan.solve(G)
+        parts = plan.unstack(U.cpu().numpy(), [P.nx * P.ny for P in probs])
+    for P, Ub in zip(probs, parts):
+        with pd.Plan.from_problem(P, precision=prec, device=dev()) as single:
+            Us, _ = single.solve(torch.from_numpy(P.G).to(dev()))
+        assert R.rel_err(Ub, Us.cpu().numpy()) <= 2 * TOL[prec], P.name
+        assert R.rel_err(Ub, R.be_solve_refined(P)) <= TOL[prec], P.name
