@@ -598,8 +598,10 @@ def serve_bench(args, device):
     from paper_2304_12597_gb300 import Plan
     from paper_2304_12597_gb300.serve import Server
 
-    rates, n = ((100, 300, 1000, 3000, 5000), 10000) if args.serve else ((300, 3000), 1000)
-    out = {"requests_per_rate": n, "workers": 3, "max_batch": 32, "alpha": 1e-4, "precision": "mixed",
+    # the five arrival rates of the serving workload; 10,000 requests each with --serve,
+    # 2,000 by default (the sweep then takes about a minute)
+    rates, n = (100, 300, 1000, 3000, 5000), (10000 if args.serve else 2000)
+    out = {"requests_per_rate": n, "workers": 3, "max_batch": 32, "precision": "mixed",
            "warm": "each rate after a 300-request warm-up stream through the same server (module loading, "
                    "per-thread state, plan caches)",
            "mix": "1D heat / 1D advection-diffusion n_x in 127..4095, 2D heat side in {63,127,255}, "
@@ -612,10 +614,12 @@ def serve_bench(args, device):
         server.close()
         summ = stats.summary()
         summ["rate"] = rate
-        # served results against the same request solved alone: a sample of 1D requests
-        # that shared a batch (2D requests run alone, with bit-identical results)
+        out["alpha"] = server.alpha
+        # served results against the same request solved alone: a sample of the requests
+        # that shared a batch (1D, and 2D on the 63 x 63 grid)
         diffs = []
-        for r in [q for q in reqs if q.dim == 1 and q.batch > 1 and not q.error][:8]:
+        shared = [q for q in reqs if q.batch > 1 and not q.error]
+        for r in [q for q in shared if q.dim == 1][:6] + [q for q in shared if q.dim == 2][:2]:
             P = S.request_problem(r)
             with Plan.from_problem(P, precision="mixed", alpha=server.alpha, device=device) as plan:
                 U, _ = plan.solve(S.rhs_device(r, torch, device).contiguous())

@@ -1,4 +1,4 @@
-// Per-problem scaling for batched plans: `batch` independent 1D problems share one
+// Per-problem scaling for batched plans: `batch` independent problems share one
 // plan as a block-diagonal problem (slot b = columns [b*nxm, (b+1)*nxm) of every
 // time row).  The Krylov and refinement stopping rules measure the whole stack, so
 // every problem is first scaled to unit Frobenius norm (up to a factor of two) and
@@ -33,7 +33,11 @@ __global__ void __launch_bounds__(256) k_batch_sumsq(const double *__restrict__ 
 
 // ex[b] = -round(log2 ||slot b||_F): slot b is multiplied by 2^ex[b] before the solve
 // and its solution by 2^-ex[b] after it (0 for an all-zero or non-finite slot).
-__global__ void k_batch_exponents(int batch, int nc, const double *__restrict__ part, int *__restrict__ ex) {
+// zero[b] = 1 for an all-zero slot: its solution is exactly zero, whatever rounding-level
+// values the paired real DFTs leave in its columns, and it takes no part in the
+// refinement decision.
+__global__ void k_batch_exponents(int batch, int nc, const double *__restrict__ part, int *__restrict__ ex,
+                                  int *__restrict__ zero) {
   grid_dep_wait();
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= batch) return;
@@ -46,6 +50,7 @@ __global__ void k_batch_exponents(int batch, int nc, const double *__restrict__ 
     e = -(e2 / 2);
   }
   ex[b] = e;
+  zero[b] = s == 0.0 ? 1 : 0;
 }
 
 // x * 2^k exactly: an exponent-field add for normal x whose result stays normal
@@ -59,39 +64,41 @@ __device__ __forceinline__ double pow2_scale(double x, int k) {
 }
 
 // Y = X * 2^(sign * ex[slot]) over the (nt, ld) array, one time row per blockIdx.y;
-// Y may alias X.  With nxb != NULL, columns past problem b's n_x are set to zero
-// (they are decoupled from the problem, but the paired real-to-complex DFT leaves
-// rounding-level values there).
+// Y may alias X.  With nxb != NULL, columns past problem b's n_x, and every column of an
+// all-zero problem (zero[b]), are set to zero (they are decoupled from the problem, but
+// the paired real-to-complex DFT leaves rounding-level values there).
 __global__ void __launch_bounds__(256) k_batch_scale(const double *X, double *Y, int ld, int nxm,
                                                      const int *__restrict__ ex, int sign,
-                                                     const int *__restrict__ nxb) {
+                                                     const int *__restrict__ nxb, const int *__restrict__ zero) {
   grid_dep_wait();
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= ld) return;
   const int b = j / nxm;
   const int64_t i = (int64_t)blockIdx.y * ld + j;
-  Y[i] = (nxb && j - b * nxm >= nxb[b]) ? 0.0 : pow2_scale(X[i], sign * ex[b]);
+  Y[i] = (nxb && (j - b * nxm >= nxb[b] || zero[b])) ? 0.0 : pow2_scale(X[i], sign * ex[b]);
 }
 
 void launch_batch_normalize(Ctx &c, const double *G, double *Gs, int64_t nt, int batch, int nxm, int nc,
-                            double *part, int *ex) {
+                            double *part, int *ex, int *zero) {
   const int64_t ld = (int64_t)batch * nxm;
   c.launch("batch_scale", (double)nt * ld * 8.0, [&] {
     pdl_launch(c.pdl, k_batch_sumsq, dim3(nc, batch), dim3(256), 0, c.stream, G, nt, ld, nxm, nc, part);
   });
-  c.launch("batch_scale", 0.0, [&] { pdl_launch(c.pdl, k_batch_exponents, dim3((batch + 127) / 128), dim3(128), 0, c.stream, batch, nc, part, ex); });
+  c.launch("batch_scale", 0.0, [&] { pdl_launch(c.pdl, k_batch_exponents, dim3((batch + 127) / 128), dim3(128), 0, c.stream, batch, nc, part, ex,
+                                                        zero); });
   const dim3 grid((unsigned)((ld + 255) / 256), (unsigned)nt);
   c.launch("batch_scale", (double)nt * ld * 16.0,
            [&] { pdl_launch(c.pdl, k_batch_scale, grid, dim3(256), 0, c.stream, G, Gs, (int)ld, nxm, (const int *)ex, 1,
-                                  (const int *)nullptr); });
+                                  (const int *)nullptr, (const int *)nullptr); });
 }
 
-void launch_batch_unscale(Ctx &c, double *U, int64_t nt, int batch, int nxm, const int *ex, const int *nxb) {
+void launch_batch_unscale(Ctx &c, double *U, int64_t nt, int batch, int nxm, const int *ex, const int *nxb,
+                          const int *zero) {
   const int64_t ld = (int64_t)batch * nxm;
   const dim3 grid((unsigned)((ld + 255) / 256), (unsigned)nt);
   c.launch("batch_scale", (double)nt * ld * 16.0,
            [&] { pdl_launch(c.pdl, k_batch_scale, grid, dim3(256), 0, c.stream, (const double *)U, U, (int)ld, nxm, ex, -1,
-                                  nxb); });
+                                  nxb, zero); });
 }
 
 // out[t][j] = in[t][j] * s[j] (in place allowed): the diagonal mass matrix's symmetric

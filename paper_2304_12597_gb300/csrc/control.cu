@@ -51,7 +51,8 @@ __global__ void k_refine_decide(double *scal, int *flags, RefineCtl r, int use_h
 // refinement decision over all problems.
 __global__ void __launch_bounds__(256) k_member_decide(const double *__restrict__ colsum, int nxm,
                                                        const int *__restrict__ nxb, int nmem, double *d2,
-                                                       double *ref2, double *prev, int *mex, int *counter, double *scal,
+                                                       double *ref2, double *prev, int *mex,
+                                                       const int *__restrict__ zero, int *counter, double *scal,
                                                        int *flags, RefineCtl rc, int use_handle,
                                                        cudaGraphConditionalHandle h) {
   grid_dep_wait();
@@ -77,18 +78,17 @@ __global__ void __launch_bounds__(256) k_member_decide(const double *__restrict_
     __threadfence();
     if (threadIdx.x == 0) *counter = 0;
     __syncthreads();  // red is reused
-    refine_decide_members(scal, flags, rc, nmem, d2, ref2, prev, mex, use_handle, h, red);
+    refine_decide_members(scal, flags, rc, nmem, d2, ref2, prev, mex, zero, use_handle, h, red);
   }
 }
 
 void launch_member_decide(Ctx &c, const double *colsum, int nxm, const int *nxb, int nmem, double *d2, double *ref2,
-                          double *prev, int *mex, double *scal, int *flags, const RefineCtl &r, int use_handle,
-                          cudaGraphConditionalHandle h) {
+                          double *prev, int *mex, const int *zero, double *scal, int *flags, const RefineCtl &r,
+                          int use_handle, cudaGraphConditionalHandle h) {
   int *counter = flags + F_C2RCNT;
   c.launch("control", 0.0, [&] {
     pdl_launch(c.pdl, k_member_decide, dim3(nmem), dim3(256), 0, c.stream, colsum, nxm, nxb, nmem, d2, ref2, prev, mex,
-               counter, scal, flags,
-                                                r, use_handle, h);
+               zero, counter, scal, flags, r, use_handle, h);
   });
 }
 

@@ -110,7 +110,8 @@ __device__ __forceinline__ void refine_decide(double *scal, int *flags, const Re
 // Batched plans: the same rule per problem.  d2[b] = ||delta_s||^2 of problem b,
 // ref2[b] its ||delta_0||^2 (set at s = 0), prev[b] its previous relative update.
 // Refinement stops when every problem meets the predicted-error rule (a problem with
-// a zero first solve is done), or when any problem stops contracting (then it has
+// a zero first solve, or an all-zero right-hand side, is done), or when any problem stops
+// contracting (then it has
 // converged if every problem's update is at the rounding floor).  The recorded
 // update of the sweep is the largest over the problems.  mex[b] receives the power of
 // two that scales problem b's residual in the next sweep, 2^-round(log2 ||delta_s||):
@@ -121,12 +122,18 @@ __device__ __forceinline__ void refine_decide(double *scal, int *flags, const Re
 // following one another through L2; the batch totals are then reduced in a fixed order.
 __device__ __forceinline__ void refine_decide_members(double *scal, int *flags, const RefineCtl &r, int nmem,
                                                       const double *d2, double *ref2, double *prev, int *mex,
-                                                      int use_handle, cudaGraphConditionalHandle h,
+                                                      const int *zero, int use_handle, cudaGraphConditionalHandle h,
                                                       double *red) {
   const int s = flags[F_SWEEP];
   bool nonfinite = flags[F_NONFIN] != 0, all_conv = true, any_stall = false, all_floor = true;
   double relmax = 0.0, d2sum = 0.0;
   for (int b = threadIdx.x; b < nmem; b += blockDim.x) {
+    if (zero[b]) {  // an all-zero problem (an unused slot): solved exactly by U = 0
+      ref2[b] = 0.0;
+      prev[b] = 0.0;
+      mex[b] = 0;
+      continue;
+    }
     const double d = d2[b];
     d2sum += d;
     if (!isfinite(d)) nonfinite = true;

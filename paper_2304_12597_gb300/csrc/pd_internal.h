@@ -265,18 +265,20 @@ template <typename T>
 void launch_zsum(Ctx &c, int nf, int64_t n, const cpx<T> *H, int64_t ldh, const double2 *omega, double *z,
                  const int *skip_flag, const ProjTail *tail = nullptr, int mlen = 0, const double *h0 = nullptr);
 // Batched plans (batch.cu): Gs = G with slot b scaled by 2^ex[b] ~ 1/||slot b||_F
-// (part: batch * nc doubles of scratch), and the inverse scaling of U in place with
-// the columns past problem b's nxb[b] rows set to zero.
+// (part: batch * nc doubles of scratch; zero[b] = 1 marks an all-zero slot), and the
+// inverse scaling of U in place with the columns past problem b's nxb[b] rows, and every
+// column of an all-zero problem, set to zero.
 void launch_batch_normalize(Ctx &c, const double *G, double *Gs, int64_t nt, int batch, int nxm, int nc,
-                            double *part, int *ex);
-void launch_batch_unscale(Ctx &c, double *U, int64_t nt, int batch, int nxm, const int *ex, const int *nxb);
+                            double *part, int *ex, int *zero);
+void launch_batch_unscale(Ctx &c, double *U, int64_t nt, int batch, int nxm, const int *ex, const int *nxb,
+                          const int *zero);
 // out[t][j] = in[t][j] * s[j] over nt rows of nb columns (in place allowed; batch.cu)
 void launch_col_scale(Ctx &c, const double *in, double *out, int64_t nt, int64_t nb, const double *s);
 // Batched plans: per-problem ||delta||^2 from the inverse DFT's per-column sums, then the
-// refinement decision over all problems (control.cu).
+// refinement decision over all problems but the all-zero ones (zero[b]; control.cu).
 void launch_member_decide(Ctx &c, const double *colsum, int nxm, const int *nxb, int nmem, double *d2, double *ref2,
-                          double *prev, int *mex, double *scal, int *flags, const RefineCtl &r, int use_handle,
-                          cudaGraphConditionalHandle h);
+                          double *prev, int *mex, const int *zero, double *scal, int *flags, const RefineCtl &r,
+                          int use_handle, cudaGraphConditionalHandle h);
 
 // out[j] = sum_r acc_part[(blk*R + r)*blen + e] (+ extra[j]), j = blk*blen + e; with tail,
 // the last CTA then computes beta = ||out|| and v_1 (the start of Algorithm 2).

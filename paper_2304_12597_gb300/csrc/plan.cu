@@ -185,6 +185,7 @@ struct pd_plan {
   double *Gs = nullptr;         // G with every problem scaled to unit norm
   double *bpart = nullptr;      // norm partials (batch * bnc)
   int *bex = nullptr;           // per-problem power-of-two scale exponents
+  int *bzero = nullptr;         // per-problem flag: all-zero right-hand side (unused slot)
   int *bnx = nullptr;           // rows of each problem
   double *colsum = nullptr;     // per-column ||delta||^2 of the last solve
   double *md2 = nullptr, *mref2 = nullptr, *mprev = nullptr;  // per-problem refinement state
@@ -678,6 +679,7 @@ size_t layout(pd_plan *p, unsigned char *base) {
     p->Gs = A.take<double>((size_t)nt * nbar);
     p->bpart = A.take<double>((size_t)p->batch * p->bnc);
     p->bex = A.take<int>(p->batch);
+    p->bzero = A.take<int>(p->batch);
     p->bnx = A.take<int>(p->batch);
     p->colsum = A.take<double>(nbar);
     p->md2 = A.take<double>(p->batch);
@@ -692,8 +694,6 @@ size_t layout(pd_plan *p, unsigned char *base) {
   return (A.off + 255) & ~(size_t)255;
 }
 
-// Batched plans: K~ = diag(tau_b K_b), each block padded to nx rows with decoupled
-// identity rows (their unknowns are zero); blocks never couple.
 // 2D batch: problem b is nx x ny with its own T_x, T_y and tau_b, stacked along y (rows
 // [b ny, (b+1) ny) of the nx x (batch ny) grid).  Its blocks (one per mode l of its T_y)
 // carry tau_b (T_x + mu_{b,l} I); the stacked T_y has no coupling across problems.
@@ -735,6 +735,8 @@ HostOp build_batched_operator_2d(const pd_desc *d) {
   return h;
 }
 
+// Batched plans: K~ = diag(tau_b K_b), each block padded to nx rows with decoupled
+// identity rows (their unknowns are zero); blocks never couple.
 HostOp build_batched_operator(const pd_desc *d) {
   if (d->dim == 2) return build_batched_operator_2d(d);
   HostOp h;
@@ -1330,7 +1332,7 @@ pd_status emit_post(pd_plan *p, int kind, double *U, int use_handle, cudaGraphCo
                             &nparts, nullptr, row_scale<T>(p, true), p->colsum, kind == 0 ? nullptr : p->mex,
                             (int)p->nxm);
     }
-    pd::launch_member_decide(c, p->colsum, (int)p->nxm, p->bnx, p->batch, p->md2, p->mref2, p->mprev, p->mex,
+    pd::launch_member_decide(c, p->colsum, (int)p->nxm, p->bnx, p->batch, p->md2, p->mref2, p->mprev, p->mex, p->bzero,
                              p->scal, p->flags, refine_ctl(p), use_handle, hr);
   } else if (p->dim == 1) {
     pd::launch_fft_c2r<T>(c, S, p->lds, p->nbar, nt, time_tw<T>(p), U, p->nbar, kind == 0 ? 0 : 1, p->norm_part,
@@ -1763,12 +1765,12 @@ pd_status paradiag_solve(pd_plan *p, const double *G, double *U, pd_stats *stats
     Gin = p->Gm;
   }
   if (p->batch > 1) {  // every problem of the batch scaled to unit norm (exactly, by 2^k)
-    pd::launch_batch_normalize(p->ctx, Gin, p->Gs, p->nt, p->batch, (int)p->nxm, p->bnc, p->bpart, p->bex);
+    pd::launch_batch_normalize(p->ctx, Gin, p->Gs, p->nt, p->batch, (int)p->nxm, p->bnc, p->bpart, p->bex, p->bzero);
     Gin = p->Gs;
   }
   st = p->precision == PD_FP64 ? solve_refined<double>(p, Gin, U, s) : solve_refined<float>(p, Gin, U, s);
   if (st == PD_ERR_CUDA) return st;
-  if (p->batch > 1) pd::launch_batch_unscale(p->ctx, U, p->nt, p->batch, (int)p->nxm, p->bex, p->bnx);
+  if (p->batch > 1) pd::launch_batch_unscale(p->ctx, U, p->nt, p->batch, (int)p->nxm, p->bex, p->bnx, p->bzero);
   if (p->mass) pd::launch_col_scale(p->ctx, U, U, p->nt, p->nbar, p->msc);  // u = M^{-1/2} w
   CK(cudaEventRecord(p->ev1, p->ctx.stream));
   CK(cudaEventSynchronize(p->ev1));

@@ -125,6 +125,7 @@ class Plan:
     @classmethod
     def _from_problems_2d(cls, problems, nt, **kw):
         nx, ny = problems[0].nx, problems[0].ny
+        kw.pop("nx", None)  # the slot is the grid itself
         if any(P.nx != nx or P.ny != ny for P in problems):
             raise ValueError("a 2D batch needs problems of one grid size")
         cat = lambda name: np.concatenate([np.asarray(getattr(P, name), dtype=np.float64) for P in problems])
@@ -183,8 +184,17 @@ class Plan:
         self.desc = d
 
     def set_problems(self, problems):
-        """Swap in the operators of a list of 1D problems (same batch size, n_t,b <= the
-        plan's n_t and n_x,b <= its slot length); see from_problems."""
+        """Swap in the operators of a list of problems (same batch size, n_t,b <= the plan's
+        n_t; 1D: n_x,b <= its slot length; 2D: the plan's grid); see from_problems."""
+        if self.dim == 2:
+            if len(problems) != self.batch or any(P.dim != 2 or P.nt > self.nt or P.nx != self.nx or P.ny != self.ny
+                                                  for P in problems):
+                raise ValueError("problems do not fit this plan's slots")
+            cat = lambda name: np.concatenate([np.asarray(getattr(P, name), dtype=np.float64) for P in problems])
+            self.set_operator(tau=problems[0].tau, k_lo=cat("k_lo"), k_diag=cat("k_diag"), k_up=cat("k_up"),
+                              k_lo_y=cat("k_lo_y"), k_diag_y=cat("k_diag_y"), k_up_y=cat("k_up_y"),
+                              batch_tau=[P.tau for P in problems])
+            return
         if len(problems) != self.batch or any(P.dim != 1 or P.nt > self.nt or P.nx > self.nx for P in problems):
             raise ValueError("problems do not fit this plan's slots")
         nx = self.nx

@@ -5,7 +5,8 @@ over time.  The scheduler groups the waiting ones into batches, and worker threa
 (one CUDA stream each) run them, so several batches are on the device at once:
 - 1D requests with one n_t and n_x in one size class share a batched plan (problem b in
   slot b, zero-padded to the class's n_x);
-- 2D requests run one per plan.
+- 2D requests with one n_t and grid share a batched plan when the grid has at most 8192
+  points (each problem's Algorithm 2 then runs in one CTA); larger grids run one per plan.
 Requests that arrive while batches are running join the next batch as soon as a
 worker and enough device memory are free.  Admission is by an HBM budget that counts
 the workspace, G and U of every batch in flight plus the cached plans.
@@ -29,6 +30,7 @@ from typing import Callable, Optional
 import numpy as np
 
 NX_CLASSES = (128, 256, 512, 1024, 2048, 4096)
+GRID_2D_BATCHED = 8192  # largest 2D grid (n_x n_y) that shares a batched plan
 
 
 def size_class(nx: int) -> int:
@@ -102,7 +104,7 @@ class Scheduler:
             return None
         head = self.waiting[0]
         key = key_of(head)
-        if key.dim == 2:
+        if key.dim == 2 and key.nx * key.ny > GRID_2D_BATCHED:
             group = [head]
             cap = 1
         else:
@@ -192,21 +194,21 @@ class Server:
         d.dim, d.nx, d.ny, d.nt, d.tau = key.dim, key.nx, key.ny, key.nt, 1.0 / key.nt
         d.precision = B.PD_MIXED if self.precision == "mixed" else B.PD_FP64
         d.q, d.alpha = 1, 1.0
-        d.batch = cap if key.dim == 1 else 0
+        d.batch = cap if (key.dim == 1 or cap > 1) else 0
         return d
 
     def _workspace_bytes(self, key: BatchKey, cap: int) -> int:
         k = (key, cap)
         if k not in self._ws_cache:
-            n = key.nx * (cap if key.dim == 1 else key.ny)
+            n = key.nx * cap  # T_x of every problem
             # a placeholder operator of the right shape (the size depends on the shape only);
             # tridiag(-1, 2, -1) passes the plan's diagonal-dominance check
             off, two = -np.ones(n), np.full(n, 2.0)
             d = self._desc_for(key, cap)
             p = lambda a: a.ctypes.data_as(self.B.ctypes.POINTER(self.B.ctypes.c_double))  # noqa: E731
             d.k_lo, d.k_diag, d.k_up = p(off), p(two), p(off)
-            if key.dim == 2:
-                yoff, ytwo = -np.ones(key.ny), np.full(key.ny, 2.0)
+            if key.dim == 2:  # T_y of every problem
+                yoff, ytwo = -np.ones(key.ny * cap), np.full(key.ny * cap, 2.0)
                 d.k_lo_y, d.k_diag_y, d.k_up_y = p(yoff), p(ytwo), p(yoff)
             self._ws_cache[k] = self.B.paradiag_workspace_size(d)
         return self._ws_cache[k]
@@ -237,12 +239,11 @@ class Server:
         import workloads.serving as S
 
         r0 = batch.requests[0]
-        if batch.key.dim == 1:
-            probs = [S.request_problem_operator_only(r, batch.key.nx) for r in batch.requests]
-            probs += [S.empty_slot(batch.key.nt) for _ in range(batch.cap - len(probs))]
-            plan = self.Plan.from_problems(probs, nx=batch.key.nx, precision=self.precision, alpha=self.alpha,
-                                           device=self.device, stream=stream)
-            nb = batch.cap * batch.key.nx
+        if batch.key.dim == 1 or batch.cap > 1:
+            plan = self.Plan.from_problems(self._slot_problems(batch, batch.requests), nx=batch.key.nx,
+                                           precision=self.precision, alpha=self.alpha, device=self.device,
+                                           stream=stream)
+            nb = batch.cap * batch.key.nx * batch.key.ny
         else:
             kx, ky = S.operator(r0)
             plan = self.Plan(dim=2, nx=r0.nx, ny=r0.ny, nt=r0.nt, tau=r0.tau, k_lo=kx[0], k_diag=kx[1],
@@ -251,20 +252,31 @@ class Server:
             nb = r0.nx * r0.ny
         return plan, nb
 
+    @staticmethod
+    def _slot_problems(batch: Batch, reqs):
+        """The operators of a batched plan's slots: the requests', then empty slots."""
+        import workloads.serving as S
+
+        k = batch.key
+        probs = [S.request_problem_operator_only(r, k.nx) for r in reqs]
+        probs += [S.empty_slot(k.nt, k.nx, k.ny) if k.dim == 2 else S.empty_slot(k.nt)
+                  for _ in range(batch.cap - len(probs))]
+        return probs
+
     def _run(self, batch: Batch, cache: OrderedDict, stream) -> None:
         import workloads.serving as S
 
         torch = self.torch
         slot, fresh = self._slot(cache, batch, stream)
         reqs = batch.requests
+        batched = batch.key.dim == 1 or batch.cap > 1
+        width = batch.key.nx * batch.key.ny  # unknowns per slot
         with torch.cuda.stream(stream):
-            if batch.key.dim == 1:
+            if batched:
                 if not fresh:
-                    probs = [S.request_problem_operator_only(r, batch.key.nx) for r in reqs]
-                    probs += [S.empty_slot(batch.key.nt) for _ in range(batch.cap - len(probs))]
-                    slot.plan.set_problems(probs)
+                    slot.plan.set_problems(self._slot_problems(batch, reqs))
                 slot.G.zero_()
-                Gv = slot.G.view(batch.key.nt, batch.cap, batch.key.nx)
+                Gv = slot.G.view(batch.key.nt, batch.cap, width)
                 for b, r in enumerate(reqs):
                     S.rhs_device(r, torch, self.device, out=Gv[:, b, :])
             else:
@@ -281,18 +293,14 @@ class Server:
                 err = str(e)
             host = None
             if self.keep_results == "full":  # the whole trajectory U (nt, n_bar) of each request
-                full = slot.U.view(batch.key.nt, batch.cap, batch.key.nx) if batch.key.dim == 1 else slot.U.view(
-                    batch.key.nt, 1, -1)
-                host = full.cpu().numpy()
+                host = slot.U.view(batch.key.nt, batch.cap, width).cpu().numpy()
             elif self.keep_results:  # the final state u_l of each request
-                last = slot.U[-1]
-                final = last.view(1, batch.cap, batch.key.nx) if batch.key.dim == 1 else last.view(1, 1, -1)
-                host = final.cpu().numpy()
+                host = slot.U[-1].view(1, batch.cap, width).cpu().numpy()
         now = time.perf_counter() - self.t0
         for b, r in enumerate(reqs):
             r.done, r.batch, r.error = now, len(reqs), err
             if host is not None:
-                res = host[:, b, : r.nx] if batch.key.dim == 1 else host[:, 0]
+                res = host[:, b, : r.nx * r.ny]
                 r.result = (res if self.keep_results == "full" else res[0]).copy()
 
     # -- the run ------------------------------------------------------------------------

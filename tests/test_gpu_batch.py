@@ -205,3 +205,35 @@ def test_batch_2d_member_equals_its_single_solve(pd, prec):
             Us, _ = single.solve(torch.from_numpy(P.G).to(dev()))
         assert R.rel_err(Ub, Us.cpu().numpy()) <= 2 * TOL[prec], P.name
         assert R.rel_err(Ub, R.be_solve_refined(P)) <= TOL[prec], P.name
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_unused_slots_leave_the_refinement_decision_alone(pd, dim):
+    """An unused slot (zero right-hand side) is solved exactly by zero; the rounding-level
+    values the paired real DFTs leave in its columns must not enter the refinement decision:
+    a problem with an unused slot beside it refines like the problem alone (same sweeps,
+    same recorded updates) and its slot stays exactly zero."""
+    import workloads.serving as S
+
+    if dim == 1:
+        P = W.heat1d_forced(1023, 256, seed=1)
+        empty = S.empty_slot(P.nt)
+        kw = {"nx": P.nx}
+    else:
+        P = _heat2d(63, 32, 0.1, seed=9, nu=0.1)
+        empty = S.empty_slot(P.nt, P.nx, P.ny)
+        kw = {}
+    with pd.Plan.from_problem(P, precision="mixed", device=dev()) as plan:
+        _, st1 = plan.solve(torch.from_numpy(P.G).to(dev()))
+    with pd.Plan.from_problems([P, empty], precision="mixed", device=dev(), **kw) as plan:
+        G = torch.from_numpy(plan.stack([P.G])).to(dev())
+        U, st = plan.solve(G)
+        Ub = U.cpu().numpy().reshape(plan.nt, 2, plan.slot)
+    assert R.rel_err(Ub[:, 0, :P.nx * P.ny], R.be_solve_refined(P)) <= TOL["mixed"], st
+    assert not np.any(Ub[:, 1])
+    n = st["refine_sweeps"]
+    upd, upd1 = st["sweep_rel_update"][:n], st1["sweep_rel_update"][:st1["refine_sweeps"]]
+    assert n <= st1["refine_sweeps"] + 1, (upd, upd1)
+    # each refinement sweep records the problem's own contraction (the unused slot's
+    # rounding noise, relative to its own noise, would record ~1 and stall the decision)
+    assert all(u < 1e-2 for u in upd[1:]), (upd, upd1)

@@ -56,3 +56,25 @@ def test_served_results_equal_alone_and_oracle(pd, alpha):
         ref = R.be_solve_refined(P).reshape(r.result.shape)
         assert _rel(r.result, ref) <= TOL, (r.rid, r.kind)
     assert summ["p99_ms"] >= summ["p50_ms"] > 0
+
+
+def test_served_2d_requests_share_a_batch(pd):
+    """2D requests on one 63 x 63 grid (different nu, n_t and forcing) share a batched plan;
+    each request's trajectory equals its solve alone and the oracle's."""
+    from paper_2304_12597_gb300.serve import Server
+
+    reqs = S.request_stream(6, 1e5, seed=21, kinds=("heat2d",), nt_choices=(32,), sides_2d=(63,))
+    server = Server(device="cuda:0", workers=1, max_batch=8, keep_results="full", budget_bytes=8 << 30, alpha=1.0)
+    stats = server.run(reqs)
+    server.close()
+    assert stats.summary()["failed"] == 0, [r.error for r in reqs if r.error]
+    assert max(r.batch for r in reqs) > 1
+    dev = torch.device("cuda:0")
+    for r in reqs:
+        P = S.request_problem(r)
+        with pd.Plan.from_problem(P, precision="mixed", alpha=1.0, device=dev) as plan:
+            U, _ = plan.solve(S.rhs_device(r, torch, dev).contiguous())
+        assert _rel(r.result, U.cpu().numpy().reshape(r.result.shape)) <= 2 * TOL, (r.rid, r.batch)
+        ref = R.be_solve_refined(P).reshape(r.result.shape)
+        assert _rel(r.result, ref) <= TOL, r.rid
+

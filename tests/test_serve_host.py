@@ -43,7 +43,8 @@ def test_scheduler_groups_by_key_in_arrival_order():
     # key of request 0: 1D, nt 64, class 512 -> 0, 1, 2, 5 (first four of that key)
     assert b1.key == BatchKey(1, 64, 512, 1) and [r.rid for r in b1.requests] == [0, 1, 2, 5] and b1.cap == 4
     b2 = sch.next_batch()
-    assert b2.key.dim == 2 and [r.rid for r in b2.requests] == [3] and b2.cap == 1
+    # a 63 x 63 grid shares a batched plan (capacity 2 at least); 127 x 127 runs alone
+    assert b2.key.dim == 2 and [r.rid for r in b2.requests] == [3] and b2.cap == 2
     b3 = sch.next_batch()
     assert [r.rid for r in b3.requests] == [4] and b3.cap == 2
     b4 = sch.next_batch()
@@ -102,3 +103,24 @@ def test_slot_operators():
         S.request_problem_operator_only(r, 128)
     e = S.empty_slot(64)
     assert (e.nx, e.nt) == (1, 64) and e.k_diag[0] == 1.0 and e.k_lo[0] == 0.0 and e.k_up[0] == 0.0
+    r2 = _req(5, "heat2d", 63, 32, 0.0)
+    op2 = S.request_problem_operator_only(r2, 63)
+    assert (op2.dim, op2.nx, op2.ny) == (2, 63, 63) and op2.k_diag_y.shape == (63,)
+    with pytest.raises(ValueError):
+        S.request_problem_operator_only(r2, 127)
+    e2 = S.empty_slot(32, 63, 63)
+    assert (e2.dim, e2.nx, e2.ny, e2.nt) == (2, 63, 63, 32) and e2.k_diag_y.shape == (63,)
+
+
+def test_scheduler_batches_small_2d_grids_only():
+    from paper_2304_12597_gb300.serve import Scheduler
+
+    sch = Scheduler(budget=1 << 40, workspace_bytes=lambda k, c: 1000, max_batch=8)
+    for i, side in enumerate((63, 127, 63, 127, 63)):
+        sch.add(_req(i, "heat2d", side, 32, 0.1 * i))
+    b1 = sch.next_batch()
+    assert [r.rid for r in b1.requests] == [0, 2, 4] and b1.cap == 4
+    b2 = sch.next_batch()
+    assert [r.rid for r in b2.requests] == [1] and b2.cap == 1  # 16129 points: one per plan
+    b3 = sch.next_batch()
+    assert [r.rid for r in b3.requests] == [3] and b3.cap == 1

@@ -60,7 +60,7 @@ class Request:
 
 
 def request_stream(n: int, rate: float, seed: int = 0, kinds=KINDS, nx_range=(127, 4095),
-                   nt_choices=(32, 64, 128, 256, 512, 1024, 2048)) -> list:
+                   nt_choices=(32, 64, 128, 256, 512, 1024, 2048), sides_2d=SIDES_2D) -> list:
     """n requests with exponential inter-arrival times of mean 1/rate seconds."""
     rng = SplitMix64(seed)
     t = 0.0
@@ -69,7 +69,7 @@ def request_stream(n: int, rate: float, seed: int = 0, kinds=KINDS, nx_range=(12
         t += -math.log(1.0 - rng.uniform()) / rate
         kind = kinds[rng.randint(0, len(kinds) - 1)]
         if kind == "heat2d":
-            nx = ny = SIDES_2D[rng.randint(0, len(SIDES_2D) - 1)]
+            nx = ny = sides_2d[rng.randint(0, len(sides_2d) - 1)]
         else:
             nx, ny = rng.randint(nx_range[0], nx_range[1]), 1
         nt = nt_choices[rng.randint(0, len(nt_choices) - 1)]
@@ -146,7 +146,8 @@ def rhs_device(req: Request, torch, device, out=None):
 
 @dataclass
 class SlotOperator:
-    """The operator fields of a 1D problem (no right-hand side), for batched plans."""
+    """The operator fields of a problem (no right-hand side), for batched plans; 2D slots
+    also carry T_y."""
 
     dim: int
     nx: int
@@ -155,15 +156,29 @@ class SlotOperator:
     k_lo: np.ndarray
     k_diag: np.ndarray
     k_up: np.ndarray
+    ny: int = 1
+    k_lo_y: Optional[np.ndarray] = None
+    k_diag_y: Optional[np.ndarray] = None
+    k_up_y: Optional[np.ndarray] = None
 
 
 def request_problem_operator_only(req: Request, slot_nx: int) -> SlotOperator:
-    if req.dim != 1 or req.nx > slot_nx:
+    if req.dim == 2:  # 2D slots are the request's own grid
+        if req.nx != slot_nx:
+            raise ValueError("a 2D request of the slot's grid is needed")
+        (lo, di, up), (ylo, ydi, yup) = operator(req)
+        return SlotOperator(2, req.nx, req.nt, req.tau, lo, di, up, req.ny, ylo, ydi, yup)
+    if req.nx > slot_nx:
         raise ValueError("a 1D request no longer than the slot is needed")
     (lo, di, up), _ = operator(req)
     return SlotOperator(1, req.nx, req.nt, req.tau, lo, di, up)
 
 
-def empty_slot(nt: int) -> SlotOperator:
-    """An unused slot of a batch: one decoupled row, zero right-hand side."""
+def empty_slot(nt: int, nx: int = 1, ny: int = 1) -> SlotOperator:
+    """An unused slot of a batch, zero right-hand side: one decoupled row (1D), or the 2D
+    heat operator on the batch's grid (2D: ny > 1)."""
+    if ny > 1:
+        lo, di, up = heat1d_operator(nx)
+        ylo, ydi, yup = heat1d_operator(ny)
+        return SlotOperator(2, nx, nt, 1.0 / nt, lo, di, up, ny, ylo, ydi, yup)
     return SlotOperator(1, 1, nt, 1.0 / nt, np.zeros(1), np.ones(1), np.zeros(1))
