@@ -56,7 +56,7 @@ def parse():
                     help="seconds of oracle solves per CPU-baseline leg (at least one full solve)")
     ap.add_argument("--serve", action="store_true",
                     help="full serving sweep: 10,000 requests at each of 100, 300, 1000, 3000, 5000 arrivals/s "
-                         "(the default run measures 1000 requests at 300 and 3000 arrivals/s)")
+                         "(the default run measures 2000 requests at each of those rates)")
     ap.add_argument("--profile", type=int, default=0, metavar="N",
                     help="only run N mixed solves of the workload with host-driven loops, one launch per "
                          "kernel node, for a profiler's launch list (prints no benchmark line)")
