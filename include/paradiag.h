@@ -198,6 +198,18 @@ typedef struct pd_desc {
   int32_t barrier_extra;     /* testing the bounded wait: every grid barrier of the persistent
                                 step waits for this many more CTAs than the launch has, so no
                                 barrier completes and every wait runs out; 0 in normal use */
+  int32_t tune_zero_lane;    /* PD_MIXED: solve the zero frequency in FP64 inside the binary32
+                                loops: 1 = always, -1 = never, 0 = built-in choice (see
+                                pd_stats.zero_freq_fp64) */
+  double early_exit_eps;     /* Algorithm 3's optional test on U_1 (single problems, loops = 0):
+                                after the first parallel-in-time loop, U_1 = L F^{-T} D_alpha^{-1}
+                                is formed and, if ||(I + tau K) U_1 - U_1 Sigma_1^T - G||_F <=
+                                early_exit_eps ||U_1||_F, the solve returns U = U_1 without
+                                Algorithm 2, the final loop or refinement (pd_stats.early_exit).
+                                0 = off (the test costs an inverse DFT and a residual pass) */
+  double eps_krylov_refine;  /* PD_MIXED: Algorithm 2 tolerance of the refinement sweeps (0 = 1e-3);
+                                a sweep's Algorithm 2 also leaves once its residual is below
+                                10 eps_krylov_refine and stops halving */
 } pd_desc;
 
 /* Statistics of the last paradiag_solve / paradiag_solve_host. */
@@ -228,6 +240,9 @@ typedef struct pd_stats {
   double zero_freq_weight;
   int32_t persistent_step;  /* 1 if each Algorithm-2 step ran as the persistent launch
                                (pd_desc.tune_persistent) */
+  int32_t early_exit;       /* 1 if Algorithm 3's test on U_1 passed and U = U_1 */
+  double u1_rel_residual;   /* ||(I + tau K) U_1 - U_1 Sigma_1^T - G||_F / ||U_1||_F of that test
+                               (0 when early_exit_eps = 0) */
 } pd_stats;
 
 typedef struct pd_plan pd_plan;

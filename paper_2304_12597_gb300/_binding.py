@@ -73,6 +73,9 @@ class PdDesc(ctypes.Structure):
         ("barrier_polls", ctypes.c_int64),
         ("tune_persist_ctas", ctypes.c_int32),
         ("barrier_extra", ctypes.c_int32),
+        ("tune_zero_lane", ctypes.c_int32),
+        ("early_exit_eps", ctypes.c_double),
+        ("eps_krylov_refine", ctypes.c_double),
     ]
 
 
@@ -96,6 +99,8 @@ class PdStats(ctypes.Structure):
         ("zero_freq_fp64", ctypes.c_int32),
         ("zero_freq_weight", ctypes.c_double),
         ("persistent_step", ctypes.c_int32),
+        ("early_exit", ctypes.c_int32),
+        ("u1_rel_residual", ctypes.c_double),
     ]
 
     def as_dict(self):

@@ -92,6 +92,27 @@ void launch_member_decide(Ctx &c, const double *colsum, int nxm, const int *nxb,
   });
 }
 
+// Algorithm 3's U_1 exit: the solve is U_1 itself; record it as one solve with no
+// Algorithm-2 step and stop the refinement loop (the inverse DFT, which otherwise
+// decides, was skipped).
+__global__ void k_early_finish(double *scal, int *flags, int use_handle, cudaGraphConditionalHandle h) {
+  grid_dep_wait();
+  if (threadIdx.x != 0 || blockIdx.x != 0 || !flags[F_EARLY]) return;
+  flags[F_SWM] = 0;
+  scal[S_SWRES] = 0.0;
+  scal[S_SWUPD] = 1.0;
+  scal[S_SWBETA] = scal[S_BETA];
+  scal[S_UPD] = 0.0;
+  flags[F_SWEEP] = 1;
+  flags[F_RCONV] = 1;
+  flags[F_RSTOP] = 1;
+  if (use_handle) cudaGraphSetConditional(h, 0u);
+}
+
+void launch_early_finish(Ctx &c, double *scal, int *flags, int use_handle, cudaGraphConditionalHandle h) {
+  c.launch("control", 0.0, [&] { pdl_launch(c.pdl, k_early_finish, dim3(1), dim3(32), 0, c.stream, scal, flags, use_handle, h); });
+}
+
 void launch_solve_reset(Ctx &c, double *scal, int *flags) {
   c.launch("control", 0.0, [&] { pdl_launch(c.pdl, k_solve_reset, dim3(1), dim3(32), 0, c.stream, scal, flags); });
 }

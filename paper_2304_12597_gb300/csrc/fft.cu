@@ -449,8 +449,9 @@ __global__ void __launch_bounds__(256) k_fft_c2r(const cpx<T> *__restrict__ S, i
                                                  void *__restrict__ out, int64_t ldo, int mode,
                                                  double *__restrict__ norm_part, StepFinish fin,
                                                  const T *__restrict__ rsi, double *__restrict__ colsum,
-                                                 const int *__restrict__ mex, int mnx) {
+                                                 const int *__restrict__ mex, int mnx, const int *skip) {
   grid_dep_wait();
+  if (skip && *skip) return;  // U already holds the result (Algorithm 3's U_1 exit)
   extern __shared__ __align__(16) unsigned char smraw[];
   cpx<T> *buf = reinterpret_cast<cpx<T> *>(smraw);
   const int64_t x0 = (int64_t)blockIdx.x * TX;
@@ -612,8 +613,9 @@ __global__ void __launch_bounds__(256) k_fft_c2r(const cpx<T> *__restrict__ S, i
 template <typename Tin, typename Tout, typename T, int TX, bool R16>
 __global__ void __launch_bounds__(256) k_dst_y(const Tin *__restrict__ X, Tout *__restrict__ Y, int64_t ny,
                                                int64_t nx, int N, int logN,
-                                               const cpx<T> *__restrict__ tw, T scale, int mode) {
+                                               const cpx<T> *__restrict__ tw, T scale, int mode, const int *skip) {
   grid_dep_wait();
+  if (skip && *skip) return;  // U already holds the result (Algorithm 3's U_1 exit)
   extern __shared__ __align__(16) unsigned char smraw[];
   cpx<T> *buf = reinterpret_cast<cpx<T> *>(smraw);
   const int ntile = (int)((nx + TX - 1) / TX);
@@ -807,7 +809,7 @@ void launch_fft_r2c_residual(Ctx &c, const double *G, const double *U, int64_t n
 template <typename T>
 void launch_fft_c2r(Ctx &c, const cpx<T> *S, int64_t lds, int64_t ncols, int n, const cpx<T> *tw,
                     void *out, int64_t ldo, int mode, double *norm_part, int *nparts, const StepFinish *finp,
-                    const T *rsi, double *colsum, const int *mex, int mnx) {
+                    const T *rsi, double *colsum, const int *mex, int mnx, const int *skip) {
   StepFinish fin{};
   if (finp && norm_part) fin = *finp;
   const int logn = ilog2(n);
@@ -824,12 +826,12 @@ void launch_fft_c2r(Ctx &c, const cpx<T> *S, int64_t lds, int64_t ncols, int n, 
         if (smem > 48 * 1024)
           cudaFuncSetAttribute(k_fft_c2r<T, kTX, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         pdl_launch(c.pdl, k_fft_c2r<T, kTX, true>, dim3(grid), dim3(thr), smem, c.stream, S, lds, ncols, n, logn, tw, out,
-                   ldo, mode, norm_part, fin, rsi, colsum, mex, mnx);
+                   ldo, mode, norm_part, fin, rsi, colsum, mex, mnx, skip);
       } else {
         if (smem > 48 * 1024)
           cudaFuncSetAttribute(k_fft_c2r<T, kTX, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         pdl_launch(c.pdl, k_fft_c2r<T, kTX, false>, dim3(grid), dim3(256), smem, c.stream, S, lds, ncols, n, logn, tw,
-                   out, ldo, mode, norm_part, fin, rsi, colsum, mex, mnx);
+                   out, ldo, mode, norm_part, fin, rsi, colsum, mex, mnx, skip);
       }
     })
   });
@@ -837,7 +839,7 @@ void launch_fft_c2r(Ctx &c, const cpx<T> *S, int64_t lds, int64_t ncols, int n, 
 
 template <typename Tin, typename Tout, typename T>
 void launch_dst_y(Ctx &c, const Tin *X, Tout *Y, int64_t nt, int64_t ny, int64_t nx, const cpx<T> *tw,
-                  int mode) {
+                  int mode, const int *skip) {
   const int N = (int)(2 * (ny + 1));
   const int logN = ilog2(N);
   const int TX = pick_tx<T>(c, N, sizeof(T) == 8 ? 8 : 16, nt * nx);
@@ -852,13 +854,13 @@ void launch_dst_y(Ctx &c, const Tin *X, Tout *Y, int64_t nt, int64_t ny, int64_t
         if (smem > 48 * 1024)
           cudaFuncSetAttribute(k_dst_y<Tin, Tout, T, kTX, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         pdl_launch(c.pdl, k_dst_y<Tin, Tout, T, kTX, true>, dim3((unsigned)grid), dim3(256), smem, c.stream, X, Y, ny, nx,
-                   N, logN, tw, scale, mode);
+                   N, logN, tw, scale, mode, skip);
       } else {
         if (smem > 48 * 1024)
           cudaFuncSetAttribute(k_dst_y<Tin, Tout, T, kTX, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)smem);
         pdl_launch(c.pdl, k_dst_y<Tin, Tout, T, kTX, false>, dim3((unsigned)grid), dim3(256), smem, c.stream, X, Y, ny,
-                   nx, N, logN, tw, scale, mode);
+                   nx, N, logN, tw, scale, mode, skip);
       }
     })
   });
@@ -872,10 +874,10 @@ template void launch_fft_r2c<float, float>(Ctx &, const float *, int64_t, int64_
                                            cpx<float> *, int64_t, const float *, const RhsNorm *);
 template void launch_fft_c2r<double>(Ctx &, const cpx<double> *, int64_t, int64_t, int, const cpx<double> *,
                                      void *, int64_t, int, double *, int *, const StepFinish *, const double *,
-                                     double *, const int *, int);
+                                     double *, const int *, int, const int *);
 template void launch_fft_c2r<float>(Ctx &, const cpx<float> *, int64_t, int64_t, int, const cpx<float> *,
                                     void *, int64_t, int, double *, int *, const StepFinish *, const float *,
-                                    double *, const int *, int);
+                                    double *, const int *, int, const int *);
 template void launch_fft_r2c_residual<double>(Ctx &, const double *, const double *, int64_t, int, const double *,
                                               const double *, const double *, const cpx<double> *, cpx<double> *,
                                               int64_t, const double *, const int *, int, const RhsNorm *);
@@ -883,12 +885,12 @@ template void launch_fft_r2c_residual<float>(Ctx &, const double *, const double
                                              const double *, const double *, const cpx<float> *, cpx<float> *,
                                              int64_t, const float *, const int *, int, const RhsNorm *);
 template void launch_dst_y<double, double, double>(Ctx &, const double *, double *, int64_t, int64_t, int64_t,
-                                                   const cpx<double> *, int);
+                                                   const cpx<double> *, int, const int *);
 template void launch_dst_y<double, float, float>(Ctx &, const double *, float *, int64_t, int64_t, int64_t,
-                                                 const cpx<float> *, int);
+                                                 const cpx<float> *, int, const int *);
 template void launch_dst_y<float, float, float>(Ctx &, const float *, float *, int64_t, int64_t, int64_t,
-                                                const cpx<float> *, int);
+                                                const cpx<float> *, int, const int *);
 template void launch_dst_y<float, double, float>(Ctx &, const float *, double *, int64_t, int64_t, int64_t,
-                                                 const cpx<float> *, int);
+                                                 const cpx<float> *, int, const int *);
 
 }  // namespace pd

@@ -535,6 +535,87 @@ template void launch_residual<double>(Ctx &, const double *, const double *, dou
                                       const double *, const double *, const double *, const double *, const double *,
                                       const double *, int64_t, const int *, int);
 
+// Algorithm 3's test on U_1 (see launch_early_check): a grid-stride pass over the residual
+// of k_residual's stencil, sums of r^2 and u^2 per CTA in FP64, combined in a fixed order by
+// the last CTA to finish, which takes the decision.
+template <bool TWO_D>
+__global__ void __launch_bounds__(256) k_early_check(const double *__restrict__ G, const double *__restrict__ U,
+                                                     int64_t nt, int nb, int nx, const double *__restrict__ rxl,
+                                                     const double *__restrict__ rxd, const double *__restrict__ rxu,
+                                                     const double *__restrict__ ryl, const double *__restrict__ ryd,
+                                                     const double *__restrict__ ryu, int ny, int nym, double eps,
+                                                     double *part, double *scal, int *flags, int use_handle,
+                                                     cudaGraphConditionalHandle h) {
+  grid_dep_wait();
+  double rr = 0.0, uu = 0.0;
+  const int64_t total = nt * nb;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = idx / nb;
+    const int j = (int)(idx - t * nb);
+    const double *u = U + t * nb;
+    const int iy = TWO_D ? j / nx : 0;
+    const int ix = TWO_D ? j - iy * nx : j;
+    const int cx = TWO_D ? (iy / nym) * nx + ix : ix;
+    const double uj = u[j];
+    double r = G[idx];
+    if (t > 0) r += U[idx - nb];
+    r = fma(-(TWO_D ? rxd[cx] + ryd[iy] : rxd[cx]), uj, r);
+    if (ix > 0) r = fma(-rxl[cx], u[j - 1], r);
+    if (ix + 1 < nx) r = fma(-rxu[cx], u[j + 1], r);
+    if (TWO_D) {
+      if (iy > 0) r = fma(-ryl[iy], u[j - nx], r);
+      if (iy + 1 < ny) r = fma(-ryu[iy], u[j + nx], r);
+    }
+    rr = fma(r, r, rr);
+    uu = fma(uj, uj, uu);
+  }
+  __shared__ double red[kRedWords];
+  __shared__ double out[2];
+  const double s2[2] = {rr, uu};
+  block_sums(s2, 2, red, out);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = out[0];
+    part[2 * blockIdx.x + 1] = out[1];
+  }
+  if (!last_cta_done(flags + F_EARLYCNT)) return;
+  if (threadIdx.x == 0) {
+    double r2 = 0.0, u2 = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) {
+      r2 += __ldcg(part + 2 * b);
+      u2 += __ldcg(part + 2 * b + 1);
+    }
+    const double res = sqrt(r2), un = sqrt(u2);
+    scal[S_U1RES] = res;
+    scal[S_U1NORM] = un;
+    const bool exit = isfinite(res) && res <= eps * un;
+    flags[F_EARLY] = exit ? 1 : 0;
+    if (exit) {  // U = U_1: no Algorithm 2, no final loop
+      flags[F_KSTOP] = 1;
+      flags[F_KCONV] = 1;
+      flags[F_M] = 0;
+      if (use_handle) cudaGraphSetConditional(h, 0u);
+    }
+    flags[F_EARLYCNT] = 0;
+  }
+}
+
+void launch_early_check(Ctx &c, const double *G, const double *U, int64_t nt, int64_t ny, int64_t nx,
+                        const double *rxl, const double *rxd, const double *rxu, const double *ryl,
+                        const double *ryd, const double *ryu, int64_t nym, double eps, double *part, double *scal,
+                        int *flags, int use_handle, cudaGraphConditionalHandle h) {
+  const int nb = (int)(ny * nx);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((nt * nb + 255) / 256, 4 * (int64_t)sm_count()));
+  c.launch("early_check", (double)nt * nb * 16.0, [&] {
+    if (ryl)
+      pdl_launch(c.pdl, k_early_check<true>, dim3(grid), dim3(256), 0, c.stream, G, U, nt, nb, (int)nx, rxl, rxd, rxu,
+                 ryl, ryd, ryu, (int)ny, (int)nym, eps, part, scal, flags, use_handle, h);
+    else
+      pdl_launch(c.pdl, k_early_check<false>, dim3(grid), dim3(256), 0, c.stream, G, U, nt, nb, (int)nx, rxl, rxd, rxu,
+                 ryl, ryd, ryu, (int)ny, (int)nym, eps, part, scal, flags, use_handle, h);
+  });
+}
+
 // ---- persistent Algorithm-2 step ---------------------------------------------------
 
 // z[j] = sum_k Re(omega_k H[k][j]) (eq. 13's z) over the whole grid: tiles of cw = 512 / rg

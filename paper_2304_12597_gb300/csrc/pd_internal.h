@@ -38,6 +38,8 @@ enum FlagIndex {
   F_TIMEOUT = 34, // a bounded device-side wait ran out (persistent Algorithm-2 step)
   F_BARCNT = 35,  // grid barrier of the persistent step: arrivals
   F_BARGEN = 36,  // grid barrier of the persistent step: generation
+  F_EARLY = 37,   // Algorithm 3's residual test on U_1 passed: U = U_1
+  F_EARLYCNT = 38,  // completion counter of that test
   kFlagWords = 64
 };
 // CTA size of the cooperative Krylov vector kernels (pd_krylov.cuh, kCoop mode).
@@ -53,6 +55,8 @@ enum ScalIndex {
   S_PREV = 6,     // previous relative update
   S_UPD = 7,      // last relative update
   S_RNORM = 8,    // ||R||_F of the current solve's right-hand side (G, or the residual)
+  S_U1RES = 9,    // ||(I + tau K) U_1 - U_1 Sigma_1^T - G||_F (Algorithm 3's test on U_1)
+  S_U1NORM = 10,  // ||U_1||_F
   S_HIST = 16,    // [16, 49): ||r_m|| history of the current solve
   S_SWRES = 64,   // [64, 80): eq. (13) residual / ||b|| at exit of each solve
   S_SWUPD = 80,   // [80, 96): ||delta_s|| / ||delta_0|| of each solve
@@ -177,12 +181,12 @@ template <typename T>
 void launch_fft_c2r(Ctx &c, const cpx<T> *S, int64_t lds, int64_t ncols, int n, const cpx<T> *tw,
                     void *out, int64_t ldo, int mode, double *norm_part, int *nparts,
                     const StepFinish *fin = nullptr, const T *rsi = nullptr, double *colsum = nullptr,
-                    const int *mex = nullptr, int mnx = 1);
+                    const int *mex = nullptr, int mnx = 1, const int *skip = nullptr);
 // Orthonormal DST-I along the middle axis of (nt, ny, nx); ny + 1 a power of two.
 // mode 0: store, 1: add into (double output only).
 template <typename Tin, typename Tout, typename T>
 void launch_dst_y(Ctx &c, const Tin *X, Tout *Y, int64_t nt, int64_t ny, int64_t nx,
-                  const cpx<T> *tw, int mode);
+                  const cpx<T> *tw, int mode, const int *skip = nullptr);
 
 // ---- shifted tridiagonal solves (pint.cu) ------------------------------------------
 struct PintGeom {
@@ -375,6 +379,19 @@ void launch_step_tail(Ctx &c, const StepArgs<T> &a, int grid, int E);
 // cannot run: its shared memory does not fit).
 size_t step_tail_smem(int maxit, int nf, int elem_bytes);
 int step_tail_max_grid(int nv, int E, int elem_bytes, size_t smem);
+
+// Algorithm 3's optional test on U_1: r = ||(I + tau K) U_1 - U_1 Sigma_1^T - G||_F against
+// eps ||U_1||_F (the residual of the original system, as in the refinement).  If it passes,
+// flags[F_EARLY] is set, Algorithm 2 does not run (flags[F_KSTOP], F_M = 0, the WHILE
+// conditional set to 0) and the final loop and inverse transforms are skipped: U = U_1.
+// part: 2 * (4 * SMs) doubles of scratch.  Geometry as launch_residual.
+void launch_early_check(Ctx &c, const double *G, const double *U, int64_t nt, int64_t ny, int64_t nx,
+                        const double *rxl, const double *rxd, const double *rxu, const double *ryl,
+                        const double *ryd, const double *ryu, int64_t nym, double eps, double *part, double *scal,
+                        int *flags, int use_handle, cudaGraphConditionalHandle h);
+// After the (skipped) final loop: with flags[F_EARLY], record the solve and stop the
+// refinement loop.
+void launch_early_finish(Ctx &c, double *scal, int *flags, int use_handle, cudaGraphConditionalHandle h);
 
 // eq. (13) and the Algorithm-2 stopping decision (krylov_decide) in one kernel
 void launch_project_resnorm(Ctx &c, KrylovBufs &k, const double *z, double tau, const KrylovCtl &kc,

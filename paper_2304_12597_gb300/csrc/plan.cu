@@ -166,6 +166,8 @@ struct pd_plan {
   int q = 1;  // Algorithm 2 checks its residual every q steps (Sec. 3)
   int loops = 0;  // fixed-cost variant (Table 3): 2 = x_m = b, 1 = U_1; 0 = the full method
   double eps = 1e-13;
+  double eps_refine = 1e-3;  // PD_MIXED: Algorithm 2 tolerance of the refinement sweeps
+  double early_eps = 0.0;    // Algorithm 3's residual test on U_1 (0 = off)
   int max_refine = 6;
   double refine_tol = 1e-13;
   int host_io = 0;
@@ -359,7 +361,7 @@ pd_status validate(const pd_desc *d) {
   if (d->q > 1 && d->batch > 1)
     return fail(PD_ERR_UNSUPPORTED, "a frozen residual (q > 1) is built for single problems, not batches");
   if (!(d->alpha >= 0.0 && d->alpha <= 1.0)) return fail(PD_ERR_INVALID_ARG, "alpha must be in (0, 1] (0 = 1)");
-  if (d->eps_krylov < 0.0 || d->refine_tol < 0.0 || d->max_refine < 0)
+  if (d->eps_krylov < 0.0 || d->refine_tol < 0.0 || d->max_refine < 0 || !(d->eps_krylov_refine >= 0.0))
     return fail(PD_ERR_INVALID_ARG, "negative tolerance or sweep count");
   const int64_t blen = d->nx;
   if (blen > 4096) return fail(PD_ERR_UNSUPPORTED, "tridiagonal blocks longer than 4096 rows are not built");
@@ -422,6 +424,13 @@ pd_status validate(const pd_desc *d) {
     return fail(PD_ERR_INVALID_ARG, "tune_fft_cols must be 0, 2, 4, 8 or 16");
   if (d->tune_fft_radix != 0 && d->tune_fft_radix != 4 && d->tune_fft_radix != 16)
     return fail(PD_ERR_INVALID_ARG, "tune_fft_radix must be 0, 4 or 16");
+  if (!(d->early_exit_eps >= 0.0) || !std::isfinite(d->early_exit_eps))
+    return fail(PD_ERR_INVALID_ARG, "early_exit_eps must be finite and >= 0");
+  if (d->early_exit_eps > 0.0 && (d->batch > 1 || d->loops > 0))
+    return fail(PD_ERR_UNSUPPORTED, "the residual test on U_1 (early_exit_eps) is built for single problems that "
+                                    "run Algorithm 2 (no batch, loops = 0)");
+  if (d->tune_zero_lane < -1 || d->tune_zero_lane > 1)
+    return fail(PD_ERR_INVALID_ARG, "tune_zero_lane must be -1, 0 or 1");
   if (d->tune_persistent < -1 || d->tune_persistent > 1)
     return fail(PD_ERR_INVALID_ARG, "tune_persistent must be -1, 0 or 1");
   if (d->barrier_polls < 0 || d->tune_persist_ctas < 0 || d->barrier_extra < 0 || d->barrier_extra > 1024)
@@ -486,6 +495,8 @@ void fill_geometry(pd_plan *p, const pd_desc *d) {
   p->loops = d->loops;
   if (p->loops) p->max_refine = 0;  // one solve: the variant's approximation
   p->refine_tol = d->refine_tol > 0 ? d->refine_tol : (d->precision == PD_FP64 ? 1e-14 : 1e-11);
+  p->eps_refine = d->eps_krylov_refine > 0 ? d->eps_krylov_refine : 1e-3;
+  p->early_eps = d->early_exit_eps;
   p->host_io = d->host_io;
   // tridiagonal blocks of nx rows: one per problem (1D) or per mode of T_y (2D)
   p->nblk = p->dim == 2 ? (int)p->ny : p->batch;
@@ -898,7 +909,7 @@ pd_status upload_operator(pd_plan *p, const pd_desc *desc) {
     }
   if (p->precision == PD_MIXED) {
     p->nu0 = zero_frequency_weight(p, tlo, tdiag, tup);
-    p->lane = p->nu0 > kLaneWeight;
+    p->lane = desc->tune_zero_lane > 0 || (desc->tune_zero_lane == 0 && p->nu0 > kLaneWeight);
   }
   cudaStream_t s = p->ctx.stream;
   if ((st = upload(p->klo, h.lo.data(), nbar, s)) || (st = upload(p->kdiag, h.diag.data(), nbar, s)) ||
@@ -1089,8 +1100,8 @@ pd::KrylovBufs kbufs(pd_plan *p) {
 pd::KrylovCtl krylov_ctl(pd_plan *p, int kind) {
   const bool fp64 = p->precision == PD_FP64;
   pd::KrylovCtl k;
-  k.eps = kind == 0 ? p->eps : std::max(p->eps, fp64 ? 1e-8 : 1e-3);
-  k.stall_floor = fp64 ? 1e-6 : (kind == 0 ? 1e-3 : 1e-2);
+  k.eps = kind == 0 ? p->eps : std::max(p->eps, fp64 ? 1e-8 : p->eps_refine);
+  k.stall_floor = fp64 ? 1e-6 : (kind == 0 ? 1e-3 : 10.0 * p->eps_refine);
   k.win = fp64 ? 3 : (kind == 0 ? 1 : 2);
   if (p->refined64) {  // refined FP64 plans: leave a stalled step at any level
     k.eps = std::max(p->eps, 1e-8);
@@ -1114,7 +1125,7 @@ pd::RefineCtl refine_ctl(pd_plan *p) {
   // refined FP64 plans stop like the mixed ones (by the contraction of the updates)
   r.fp64 = (fp64 && !p->refined64) ? 1 : 0;
   r.eps_first = p->eps;
-  r.eps_refine = p->refined64 ? std::max(p->eps, 1e-8) : std::max(p->eps, fp64 ? 1e-8 : 1e-3);
+  r.eps_refine = p->refined64 ? std::max(p->eps, 1e-8) : std::max(p->eps, fp64 ? 1e-8 : p->eps_refine);
   r.refine_tol = p->refine_tol;
   r.max_refine = p->max_refine;
   return r;
@@ -1166,12 +1177,20 @@ pd_status emit_pre(pd_plan *p, int kind, const double *G, double *U, int use_han
     pd::launch_inner_fixed(c, p->scal, p->flags, p->y, 1, use_handle, hk);
     return PD_OK;
   }
+  // Algorithm 3's test on U_1 (first solve): the first loop also stores L (in the h_k
+  // buffer, free until Algorithm 2 starts)
+  const bool early = kind == 0 && p->early_eps > 0.0;
+  cpx<T> *L = reinterpret_cast<cpx<T> *>(p->hbuf);
   pd::PintArgs<T> a = base_args<T>(p);
   a.R = S;
   a.ldr = p->lds;
   a.omega = p->wg;
   a.acc_part = p->acc_part;
   a.acc0 = lane_acc0<T>(p);
+  if (early) {
+    a.Y = L;
+    a.ldy = p->lds;
+  }
   pd::launch_pint<T>(c, p->geom, a);
   pd::KrylovBufs kb = kbufs<T>(p);
   double *acc0 = lane_acc0<T>(p);
@@ -1188,6 +1207,19 @@ pd_status emit_pre(pd_plan *p, int kind, const double *G, double *U, int use_han
   }
   // x_m = b: the inner matrix of eq. (17) taken as I (two loops in all)
   if (p->loops == 2) pd::launch_inner_fixed(c, p->scal, p->flags, p->y, 2, use_handle, hk);
+  if (early) {  // U_1 = L F^{-T} D_alpha^{-1} into U, then its residual against eps ||U_1||
+    int nparts = 0;
+    if (p->dim == 1) {
+      pd::launch_fft_c2r<T>(c, L, p->lds, p->nbar, nt, time_tw<T>(p), U, p->nbar, 0, nullptr, &nparts, nullptr,
+                            row_scale<T>(p, true));
+    } else {
+      pd::launch_fft_c2r<T>(c, L, p->lds, p->nbar, nt, time_tw<T>(p), tmp, p->nbar, sizeof(T) == 8 ? 0 : 2, nullptr,
+                            &nparts, nullptr, row_scale<T>(p, true));
+      pd::launch_dst_y<T, double, T>(c, tmp, U, p->nt, p->nym, p->nx, dst_tw<T>(p), 0);
+    }
+    pd::launch_early_check(c, G, U, p->nt, p->ny, p->nx, p->rxl, p->rxd, p->rxu, p->ryl, p->ryd, p->ryu, p->nym,
+                           p->early_eps, p->norm_part, p->scal, p->flags, use_handle, hk);
+  }
   // the persistent step ends with the next step's Arnoldi step: the first one runs here
   if (p->persist) pd::launch_arnoldi(c, kb);
   return PD_OK;
@@ -1306,6 +1338,9 @@ pd_status emit_post(pd_plan *p, int kind, double *U, int use_handle, cudaGraphCo
   a.xm_out = p->x;
   a.Y = S;
   a.ldy = p->lds;
+  const bool early = kind == 0 && p->early_eps > 0.0;
+  const int *skip = early ? p->flags + pd::F_EARLY : nullptr;  // U = U_1 already
+  a.skip_flag = skip;
   pd::launch_pint<T>(c, p->geom, a);
   if (kind == 0) {
     CK(cudaMemcpyAsync(p->b0, p->b, sizeof(double) * p->nbar, cudaMemcpyDeviceToDevice, c.stream));
@@ -1336,13 +1371,14 @@ pd_status emit_post(pd_plan *p, int kind, double *U, int use_handle, cudaGraphCo
                              p->scal, p->flags, refine_ctl(p), use_handle, hr);
   } else if (p->dim == 1) {
     pd::launch_fft_c2r<T>(c, S, p->lds, p->nbar, nt, time_tw<T>(p), U, p->nbar, kind == 0 ? 0 : 1, p->norm_part,
-                          &nparts, &fin, row_scale<T>(p, true));
+                          &nparts, &fin, row_scale<T>(p, true), nullptr, nullptr, 1, skip);
   } else {
     T *tmp = tmp_buf<T>(p);
     pd::launch_fft_c2r<T>(c, S, p->lds, p->nbar, nt, time_tw<T>(p), tmp, p->nbar, fp64 ? 0 : 2, p->norm_part,
-                          &nparts, &fin, row_scale<T>(p, true));
-    pd::launch_dst_y<T, double, T>(c, tmp, U, p->nt, p->nym, p->nx, dst_tw<T>(p), kind == 0 ? 0 : 1);
+                          &nparts, &fin, row_scale<T>(p, true), nullptr, nullptr, 1, skip);
+    pd::launch_dst_y<T, double, T>(c, tmp, U, p->nt, p->nym, p->nx, dst_tw<T>(p), kind == 0 ? 0 : 1, skip);
   }
+  if (early) pd::launch_early_finish(c, p->scal, p->flags, use_handle, hr);
   return PD_OK;
 }
 
@@ -1566,6 +1602,13 @@ pd_status solve_refined(pd_plan *p, const double *G, double *U, pd_stats &s) {
   s.zero_freq_fp64 = p->lane ? 1 : 0;
   s.zero_freq_weight = p->nu0;
   s.persistent_step = p->persist ? 1 : 0;
+  s.early_exit = f[pd::F_EARLY];
+  s.u1_rel_residual = sc[pd::S_U1NORM] > 0.0 ? sc[pd::S_U1RES] / sc[pd::S_U1NORM] : 0.0;
+  if (f[pd::F_EARLY]) {  // U = U_1: one parallel-in-time loop, no Algorithm 2
+    s.pint_loops = s.shifted_sweeps = 1;
+    s.krylov_iters = s.krylov_iters_total = 0;
+    s.sweep_krylov_iters[0] = 0;
+  }
   if (f[pd::F_TIMEOUT]) return timeout_status(p);
   if (f[pd::F_NONFIN]) return fail(PD_ERR_NONFINITE, "non-finite value met (input contains NaN/Inf?)");
   if (p->loops) {  // the variant's approximation: no convergence claim

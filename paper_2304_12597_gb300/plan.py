@@ -34,7 +34,8 @@ class Plan:
     def __init__(self, *, dim, nx, nt, tau, k_lo, k_diag, k_up, ny=1, k_lo_y=None, k_diag_y=None,
                  k_up_y=None, m_diag=None, precision="mixed", maxit=0, eps_krylov=0.0, max_refine=0, refine_tol=0.0,
                  alpha=1.0, q=1, loops=0, host_io=False, no_graph=False, tune=None, batch=1, batch_nx=None, batch_tau=None,
-                 barrier_polls=0, barrier_extra=0, device=None, stream=None, workspace="torch"):
+                 barrier_polls=0, barrier_extra=0, eps_krylov_refine=0.0, early_exit_eps=0.0, device=None,
+                 stream=None, workspace="torch"):
         import torch
 
         self._torch = torch
@@ -72,6 +73,8 @@ class Plan:
         # bounded waits of the persistent Algorithm-2 step; barrier_extra > 0 only to test them
         d.barrier_polls = int(barrier_polls)
         d.barrier_extra = int(barrier_extra)
+        d.eps_krylov_refine = float(eps_krylov_refine)
+        d.early_exit_eps = float(early_exit_eps)  # Algorithm 3's residual test on U_1 (0 = off)
         d.batch = self.batch if self.batch > 1 else 0
         if self._batch_nx is not None:
             d.batch_nx = self._batch_nx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))

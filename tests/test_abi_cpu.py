@@ -285,3 +285,14 @@ def test_2d_batch_limits_are_checked(B):
     assert st == 2 and "Toeplitz" in B.last_error()
     st, n = _size_status(B, _desc(B, dim=2, n=63, ny=63, batch=3, batch_tau=[0.1, 0.2, 0.3], precision=1))
     assert st == 0 and n > 0, B.last_error()
+
+
+def test_u1_test_limits_are_checked(B):
+    """The residual test on U_1 needs a single problem that runs Algorithm 2."""
+    assert _size_status(B, _desc(B, early_exit_eps=1e-6, alpha=1e-4))[0] == 0, B.last_error()
+    st, _ = _size_status(B, _desc(B, early_exit_eps=1e-6, batch=2))
+    assert st == 2 and "early_exit_eps" in B.last_error()
+    st, _ = _size_status(B, _desc(B, early_exit_eps=1e-6, loops=1))
+    assert st == 2
+    st, _ = _size_status(B, _desc(B, early_exit_eps=-1.0))
+    assert st == 1

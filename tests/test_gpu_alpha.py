@@ -180,3 +180,52 @@ def test_fixed_loop_variants_in_2d(pd, loops, alpha):
         U, st = plan.solve(torch.from_numpy(P.G).to(dev()))
     assert R.rel_err(U.cpu().numpy(), ref) <= _variant_bound(P, alpha), st
     assert st["pint_loops"] == loops
+
+
+def _u1_rel_residual(P, U1):
+    return np.linalg.norm(R.residual_extended(P, U1)) / np.linalg.norm(U1)
+
+
+U1_CASES = [
+    lambda: W.advdiff1d_pulse(511, 64, nu=2.0 ** -5, seed=1),
+    lambda: W.heat2d_smooth(15, 16, T=0.1, seed=2),
+]
+
+
+@pytest.mark.parametrize("case", range(len(U1_CASES)), ids=["advdiff1d", "heat2d"])
+def test_u1_exit_returns_u1_when_its_residual_passes(pd, case):
+    """Algorithm 3's test on U_1: with alpha = 1e-6 the residual of U_1 is small (Fig. 1:
+    linear in alpha), so with eps ten times that ratio the solve returns U_1 itself (the
+    oracle's, within the variant's rounding bound) after one parallel-in-time loop, without
+    Algorithm 2 or refinement, and reports the test's ratio."""
+    P = U1_CASES[case]()
+    alpha = 1e-6
+    U1, _ = R.paradiag_alpha(P, alpha, loops=1)
+    r1 = _u1_rel_residual(P, U1)
+    eps = 10.0 * r1
+    ref, info = R.paradiag_alpha(P, alpha, early_exit_eps=eps)
+    assert info["exited_early"]
+    with pd.Plan.from_problem(P, precision="fp64", alpha=alpha, early_exit_eps=eps, device=dev()) as plan:
+        U, st = plan.solve(torch.from_numpy(P.G).to(dev()))
+    assert st["early_exit"] == 1 and st["pint_loops"] == 1 and st["krylov_iters"] == 0 and st["refine_sweeps"] == 1
+    assert R.rel_err(U.cpu().numpy(), ref) <= _variant_bound(P, alpha), st
+    assert abs(st["u1_rel_residual"] - r1) <= 0.05 * r1, (st["u1_rel_residual"], r1)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", range(len(U1_CASES)), ids=["advdiff1d", "heat2d"])
+def test_u1_test_failing_runs_the_correction(pd, prec, case):
+    """With eps a tenth of U_1's residual ratio the test fails: Algorithm 3 runs in full
+    (and refines), the solution meets the usual bar, and the ratio is still reported."""
+    P = U1_CASES[case]()
+    alpha = 1e-2
+    U1, _ = R.paradiag_alpha(P, alpha, loops=1)
+    r1 = _u1_rel_residual(P, U1)
+    with pd.Plan.from_problem(P, precision=prec, alpha=alpha, early_exit_eps=0.1 * r1, device=dev()) as plan:
+        U, st = plan.solve(torch.from_numpy(P.G).to(dev()))
+    assert st["early_exit"] == 0 and st["krylov_iters_total"] >= 1
+    assert R.rel_err(U.cpu().numpy(), R.be_solve_refined(P)) <= TOL[prec], st
+    if prec == "fp64":
+        assert abs(st["u1_rel_residual"] - r1) <= 0.05 * r1, (st["u1_rel_residual"], r1)
+    else:  # a binary32 U_1: its residual carries the rounding of the binary32 loop as well
+        assert st["u1_rel_residual"] > 0.1 * r1, (st["u1_rel_residual"], r1)
