@@ -607,13 +607,28 @@ __global__ void __launch_bounds__(256) k_fft_c2r(const cpx<T> *__restrict__ S, i
   }
 }
 
+// The FP64 all-at-once residual as the DST's input (ResIn.G != null): element (row y, column
+// col) of slab s (time t = s / batch, problem b = s % batch) is
+// r = G_t + u_{t-1} - [(I + tau T_x) u_t + tau T_y u_t] at row b nym + y of the stacked grid
+// (ny = batch nym rows, x-coefficients of problem b), times 2^mex[b] for batches: five
+// FMAs in FP64 per element after G_t + u_{t-1}, formed while the DST loads its tile.
+struct ResIn {
+  const double *G, *U;
+  const double *rxl, *rxd, *rxu, *ryl, *ryd, *ryu;
+  int ny, nym, batch;
+  const int *mex;
+};
+
 // Orthonormal DST-I along y via a length N = 2(ny+1) complex FFT of the odd
 // extension, two x-columns packed per series (a + i b):
 //   DST_l(a) = -Im Z[l] / 2,  DST_l(b) = Re Z[l] / 2,  scaled by sqrt(2/(ny+1)).
-template <typename Tin, typename Tout, typename T, int TX, bool R16>
+// RES: the input is the residual of ResIn, staged once per element in shared memory
+// (TX columns x ny rows of T after the series), so that its FP64 work is done once.
+template <typename Tin, typename Tout, typename T, int TX, bool R16, bool RES>
 __global__ void __launch_bounds__(256) k_dst_y(const Tin *__restrict__ X, Tout *__restrict__ Y, int64_t ny,
                                                int64_t nx, int N, int logN,
-                                               const cpx<T> *__restrict__ tw, T scale, int mode, const int *skip) {
+                                               const cpx<T> *__restrict__ tw, T scale, int mode, const int *skip,
+                                               ResIn rin, size_t res_off) {
   grid_dep_wait();
   if (skip && *skip) return;  // U already holds the result (Algorithm 3's U_1 exit)
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -625,6 +640,51 @@ __global__ void __launch_bounds__(256) k_dst_y(const Tin *__restrict__ X, Tout *
   Tout *Yt = Y + t * ny * nx;
   const int np = TX >> 1;
   const int total = (int)ny * TX;
+  T *rt = reinterpret_cast<T *>(smraw + res_off);  // RES: the residual tile, [y][c]
+  if constexpr (RES) {
+    const int64_t tt = t / rin.batch;                // time step
+    const int b = (int)(t - tt * rin.batch);         // problem
+    const int64_t nb = (int64_t)rin.ny * nx;         // unknowns per time row
+    const double msc = rin.mex ? ldexp(1.0, rin.mex[b]) : 1.0;
+    for (int i0 = threadIdx.x; i0 < total; i0 += kLoadBatch * blockDim.x) {
+      double rv[kLoadBatch];
+#pragma unroll
+      for (int u = 0; u < kLoadBatch; ++u) {
+        const int idx = i0 + u * (int)blockDim.x;
+        const int y = idx / TX;
+        const int c = idx - y * TX;
+        const int64_t col = x0 + c;
+        double r = 0.0;
+        if (idx < total && col < nx) {
+          const int iy = b * rin.nym + y;
+          const int64_t j = (int64_t)iy * nx + col;
+          const int64_t cx = (int64_t)b * nx + col;  // x-coefficients of problem b
+          const double *u = rin.U + tt * nb;
+          r = rin.G[tt * nb + j];
+          if (tt > 0) r += u[j - nb];
+          r = fma(-(rin.rxd[cx] + rin.ryd[iy]), u[j], r);
+          if (col > 0) r = fma(-rin.rxl[cx], u[j - 1], r);
+          if (col + 1 < nx) r = fma(-rin.rxu[cx], u[j + 1], r);
+          if (iy > 0) r = fma(-rin.ryl[iy], u[j - nx], r);
+          if (iy + 1 < rin.ny) r = fma(-rin.ryu[iy], u[j + nx], r);
+        }
+        rv[u] = r;
+      }
+#pragma unroll
+      for (int u = 0; u < kLoadBatch; ++u) {
+        const int idx = i0 + u * (int)blockDim.x;
+        if (idx < total) rt[idx] = (T)(rv[u] * msc);
+      }
+    }
+    __syncthreads();
+  }
+  // element (y, col) of the tile's input
+  auto in_at = [&](int y, int64_t col) -> T {
+    if constexpr (RES)
+      return rt[y * TX + (int)(col - x0)];
+    else
+      return (T)Xt[(int64_t)y * nx + col];
+  };
   if constexpr (R16) {  // radix-16 first stage in registers (see k_fft_r2c16)
     const int SS = series_stride16(N), nb = N >> 4, lb = logN - 4, half = N >> 1;
     for (int it = threadIdx.x; it < np * nb; it += blockDim.x) {
@@ -640,8 +700,8 @@ __global__ void __launch_bounds__(256) k_dst_y(const Tin *__restrict__ X, Tout *
         const bool zero = idx == 0 || idx == half;
         const int y = idx < half ? idx - 1 : N - idx - 1;
         const T sg = idx < half ? T(1) : T(-1);
-        const Tin *row = Xt + (int64_t)(zero ? 0 : y) * nx;
-        z[i] = mk<T>((!zero && ca < nx) ? sg * (T)row[ca] : T(0), (!zero && cb < nx) ? sg * (T)row[cb] : T(0));
+        const int yy = zero ? 0 : y;
+        z[i] = mk<T>((!zero && ca < nx) ? sg * in_at(yy, ca) : T(0), (!zero && cb < nx) ? sg * in_at(yy, cb) : T(0));
       }
       dft16(z);
       cpx<T> *blk = buf + (size_t)p * SS + 17 * g;
@@ -662,7 +722,7 @@ __global__ void __launch_bounds__(256) k_dst_y(const Tin *__restrict__ X, Tout *
         const int idx = i0 + u * (int)blockDim.x;
         const int y = idx / TX;
         const int64_t col = x0 + (idx - y * TX);
-        v[u] = (idx < total && col < nx) ? (T)Xt[(int64_t)y * nx + col] : T(0);
+        v[u] = (idx < total && col < nx) ? in_at(y, col) : T(0);
       }
 #pragma unroll
       for (int u = 0; u < kLoadBatch; ++u) {
@@ -837,33 +897,54 @@ void launch_fft_c2r(Ctx &c, const cpx<T> *S, int64_t lds, int64_t ncols, int n, 
   });
 }
 
-template <typename Tin, typename Tout, typename T>
-void launch_dst_y(Ctx &c, const Tin *X, Tout *Y, int64_t nt, int64_t ny, int64_t nx, const cpx<T> *tw,
-                  int mode, const int *skip) {
+template <typename Tin, typename Tout, typename T, bool RES>
+static void dst_launch(Ctx &c, const Tin *X, Tout *Y, int64_t nslab, int64_t ny, int64_t nx, const cpx<T> *tw,
+                       int mode, const int *skip, const ResIn &rin, const char *fam, double bytes) {
   const int N = (int)(2 * (ny + 1));
   const int logN = ilog2(N);
-  const int TX = pick_tx<T>(c, N, sizeof(T) == 8 ? 8 : 16, nt * nx);
-  const size_t smem = (size_t)(TX / 2) * fft_sst<T>(c, N) * sizeof(cpx<T>);
+  const int TX = pick_tx<T>(c, N, sizeof(T) == 8 ? 8 : 16, nslab * nx);
+  const size_t ser = (size_t)(TX / 2) * fft_sst<T>(c, N) * sizeof(cpx<T>);
+  const size_t res_off = (ser + 15) & ~(size_t)15;
+  const size_t smem = RES ? res_off + (size_t)ny * TX * sizeof(T) : ser;
   const int ntile = (int)((nx + TX - 1) / TX);
-  const int64_t grid = nt * ntile;
+  const int64_t grid = nslab * ntile;
   const T scale = (T)sqrt(2.0 / (double)(ny + 1));
-  const double bytes = (double)nt * ny * nx * (sizeof(Tin) + sizeof(Tout) * (mode ? 2 : 1));
-  c.launch(sizeof(T) == 8 ? "dst_y_f64" : "dst_y_f32", bytes, [&] {
+  c.launch(fam, bytes, [&] {
     PD_TX_DISPATCH(TX, {
       if (use_r16<T>(c, N)) {
         if (smem > 48 * 1024)
-          cudaFuncSetAttribute(k_dst_y<Tin, Tout, T, kTX, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        pdl_launch(c.pdl, k_dst_y<Tin, Tout, T, kTX, true>, dim3((unsigned)grid), dim3(256), smem, c.stream, X, Y, ny, nx,
-                   N, logN, tw, scale, mode, skip);
+          cudaFuncSetAttribute(k_dst_y<Tin, Tout, T, kTX, true, RES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
+        pdl_launch(c.pdl, k_dst_y<Tin, Tout, T, kTX, true, RES>, dim3((unsigned)grid), dim3(256), smem, c.stream, X, Y,
+                   ny, nx, N, logN, tw, scale, mode, skip, rin, res_off);
       } else {
         if (smem > 48 * 1024)
-          cudaFuncSetAttribute(k_dst_y<Tin, Tout, T, kTX, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+          cudaFuncSetAttribute(k_dst_y<Tin, Tout, T, kTX, false, RES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)smem);
-        pdl_launch(c.pdl, k_dst_y<Tin, Tout, T, kTX, false>, dim3((unsigned)grid), dim3(256), smem, c.stream, X, Y, ny,
-                   nx, N, logN, tw, scale, mode, skip);
+        pdl_launch(c.pdl, k_dst_y<Tin, Tout, T, kTX, false, RES>, dim3((unsigned)grid), dim3(256), smem, c.stream, X,
+                   Y, ny, nx, N, logN, tw, scale, mode, skip, rin, res_off);
       }
     })
   });
+}
+
+template <typename Tin, typename Tout, typename T>
+void launch_dst_y(Ctx &c, const Tin *X, Tout *Y, int64_t nt, int64_t ny, int64_t nx, const cpx<T> *tw,
+                  int mode, const int *skip) {
+  const double bytes = (double)nt * ny * nx * (sizeof(Tin) + sizeof(Tout) * (mode ? 2 : 1));
+  dst_launch<Tin, Tout, T, false>(c, X, Y, nt, ny, nx, tw, mode, skip, ResIn{}, sizeof(T) == 8 ? "dst_y_f64" : "dst_y_f32",
+                                  bytes);
+}
+
+template <typename T>
+void launch_dst_y_residual(Ctx &c, const double *G, const double *U, T *Y, int64_t nt, int batch, int64_t nym,
+                           int64_t nx, const double *rxl, const double *rxd, const double *rxu, const double *ryl,
+                           const double *ryd, const double *ryu, const int *mex, const cpx<T> *tw) {
+  ResIn rin{G, U, rxl, rxd, rxu, ryl, ryd, ryu, (int)(nym * batch), (int)nym, batch, mex};
+  // G and U read once (neighbours from the caches), the binary32 / FP64 transform written
+  const double bytes = (double)nt * batch * nym * nx * (16.0 + sizeof(T));
+  dst_launch<double, T, T, true>(c, (const double *)nullptr, Y, nt * batch, nym, nx, tw, 0, nullptr, rin,
+                                 sizeof(T) == 8 ? "dst_y_res_f64" : "dst_y_res_f32", bytes);
 }
 
 template void launch_fft_r2c<double, double>(Ctx &, const double *, int64_t, int64_t, int, const cpx<double> *,
@@ -892,5 +973,11 @@ template void launch_dst_y<float, float, float>(Ctx &, const float *, float *, i
                                                 const cpx<float> *, int, const int *);
 template void launch_dst_y<float, double, float>(Ctx &, const float *, double *, int64_t, int64_t, int64_t,
                                                  const cpx<float> *, int, const int *);
+template void launch_dst_y_residual<float>(Ctx &, const double *, const double *, float *, int64_t, int, int64_t,
+                                           int64_t, const double *, const double *, const double *, const double *,
+                                           const double *, const double *, const int *, const cpx<float> *);
+template void launch_dst_y_residual<double>(Ctx &, const double *, const double *, double *, int64_t, int, int64_t,
+                                            int64_t, const double *, const double *, const double *, const double *,
+                                            const double *, const double *, const int *, const cpx<double> *);
 
 }  // namespace pd

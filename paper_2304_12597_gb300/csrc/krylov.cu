@@ -475,69 +475,10 @@ __global__ void k_sumsq_final(const double *part, int nparts, double *dst) {
   if (threadIdx.x == 0) *dst = s;
 }
 
-// ---- FP64 all-at-once residual ---------------------------------------------------
-// r = G_t + u_{t-1} - [ (I + tau T_x) u_t  (+ tau T_y u_t in 2D) ] with the coefficient
-// arrays pre-scaled on the host: rx = (tau lo_x, 1 + tau diag_x, tau up_x),
-// ry = (tau lo_y, tau diag_y, tau up_y): four FP64 operations per point in 1D.  In 2D the
-// grid has ny rows of nx points; a batch stacks its problems along y, nym rows each, and
-// row iy takes the x-coefficients of problem iy / nym (its T_y has no coupling across
-// problems).  mex (batches): problem j / mlen's residual is scaled by 2^mex (exact).
-template <typename Tout, bool TWO_D>
-__global__ void k_residual(const double *__restrict__ G, const double *__restrict__ U, Tout *__restrict__ R,
-                           int nb, int nx, const double *__restrict__ rxl, const double *__restrict__ rxd,
-                           const double *__restrict__ rxu, const double *__restrict__ ryl,
-                           const double *__restrict__ ryd, const double *__restrict__ ryu, int ny, int nym,
-                           const int *__restrict__ mex, int mlen) {
-  grid_dep_wait();
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;  // spatial index
-  const int64_t t = blockIdx.y;                         // time step
-  if (j >= nb) return;
-  const double *u = U + t * nb;
-  const int iy = TWO_D ? j / nx : 0;
-  const int ix = TWO_D ? j - iy * nx : j;
-  const int cx = TWO_D ? (iy / nym) * nx + ix : ix;  // x-coefficients of this row's problem
-  const double uj = u[j];
-  const int64_t idx = t * nb + j;
-  double r = G[idx];
-  if (t > 0) r += U[idx - nb];
-  r = fma(-(TWO_D ? rxd[cx] + ryd[iy] : rxd[cx]), uj, r);
-  if (ix > 0) r = fma(-rxl[cx], u[j - 1], r);
-  if (ix + 1 < nx) r = fma(-rxu[cx], u[j + 1], r);
-  if (TWO_D) {
-    if (iy > 0) r = fma(-ryl[iy], u[j - nx], r);
-    if (iy + 1 < ny) r = fma(-ryu[iy], u[j + nx], r);
-  }
-  if (mex) r = ldexp(r, mex[j / mlen]);
-  R[idx] = (Tout)r;
-}
-
-template <typename Tout>
-void launch_residual(Ctx &c, const double *G, const double *U, Tout *R, int64_t nt, int64_t ny, int64_t nx,
-                     const double *rxl, const double *rxd, const double *rxu, const double *ryl, const double *ryd,
-                     const double *ryu, int64_t nym, const int *mex, int mlen) {
-  const int nb = (int)(ny * nx);
-  const dim3 grid((unsigned)((nb + 255) / 256), (unsigned)nt);
-  c.launch(sizeof(Tout) == 8 ? "residual_f64_to_f64" : "residual_f64_to_f32",
-           (double)nt * nb * (8 + 8 + sizeof(Tout)), [&] {
-             if (ryl)
-               pdl_launch(c.pdl, k_residual<Tout, true>, grid, dim3(256), 0, c.stream, G, U, R, nb, (int)nx, rxl, rxd,
-                          rxu, ryl, ryd, ryu, (int)ny, (int)nym, mex, mlen);
-             else
-               pdl_launch(c.pdl, k_residual<Tout, false>, grid, dim3(256), 0, c.stream, G, U, R, nb, (int)nx, rxl, rxd,
-                          rxu, ryl, ryd, ryu, (int)ny, (int)nym, mex, mlen);
-           });
-}
-
-template void launch_residual<float>(Ctx &, const double *, const double *, float *, int64_t, int64_t, int64_t,
-                                     const double *, const double *, const double *, const double *, const double *,
-                                     const double *, int64_t, const int *, int);
-template void launch_residual<double>(Ctx &, const double *, const double *, double *, int64_t, int64_t, int64_t,
-                                      const double *, const double *, const double *, const double *, const double *,
-                                      const double *, int64_t, const int *, int);
-
 // Algorithm 3's test on U_1 (see launch_early_check): a grid-stride pass over the residual
-// of k_residual's stencil, sums of r^2 and u^2 per CTA in FP64, combined in a fixed order by
-// the last CTA to finish, which takes the decision.
+// r = G_t + u_{t-1} - [(I + tau T_x) u_t (+ tau T_y u_t)] (the refinement's stencil), sums of
+// r^2 and u^2 per CTA in FP64, combined in a fixed order by the last CTA to finish, which
+// takes the decision.
 template <bool TWO_D>
 __global__ void __launch_bounds__(256) k_early_check(const double *__restrict__ G, const double *__restrict__ U,
                                                      int64_t nt, int nb, int nx, const double *__restrict__ rxl,

@@ -187,6 +187,15 @@ void launch_fft_c2r(Ctx &c, const cpx<T> *S, int64_t lds, int64_t ncols, int n, 
 template <typename Tin, typename Tout, typename T>
 void launch_dst_y(Ctx &c, const Tin *X, Tout *Y, int64_t nt, int64_t ny, int64_t nx,
                   const cpx<T> *tw, int mode, const int *skip = nullptr);
+// The same transform of the FP64 all-at-once residual of the 2D path, formed while each tile
+// loads (nt time rows of batch problems, nym rows of T_y each, stacked along y; rx
+// per problem, ry over the stacked rows; mex: the batches' residual scaling, or null):
+// the residual and the DST in one pass.  rx = (tau lo_x, 1 + tau diag_x, tau up_x),
+// ry = (tau lo_y, tau diag_y, tau up_y).
+template <typename T>
+void launch_dst_y_residual(Ctx &c, const double *G, const double *U, T *Y, int64_t nt, int batch, int64_t nym,
+                           int64_t nx, const double *rxl, const double *rxd, const double *rxu, const double *ryl,
+                           const double *ryd, const double *ryu, const int *mex, const cpx<T> *tw);
 
 // ---- shifted tridiagonal solves (pint.cu) ------------------------------------------
 struct PintGeom {
@@ -384,7 +393,8 @@ int step_tail_max_grid(int nv, int E, int elem_bytes, size_t smem);
 // eps ||U_1||_F (the residual of the original system, as in the refinement).  If it passes,
 // flags[F_EARLY] is set, Algorithm 2 does not run (flags[F_KSTOP], F_M = 0, the WHILE
 // conditional set to 0) and the final loop and inverse transforms are skipped: U = U_1.
-// part: 2 * (4 * SMs) doubles of scratch.  Geometry as launch_residual.
+// part: 2 * (4 * SMs) doubles of scratch.  Coefficients as launch_dst_y_residual (1D:
+// ryl == null, ny = 1).
 void launch_early_check(Ctx &c, const double *G, const double *U, int64_t nt, int64_t ny, int64_t nx,
                         const double *rxl, const double *rxd, const double *rxu, const double *ryl,
                         const double *ryd, const double *ryu, int64_t nym, double eps, double *part, double *scal,
@@ -406,15 +416,6 @@ void launch_inner_fixed(Ctx &c, double *scal, int *flags, double *y, int loops, 
 void launch_refine_decide(Ctx &c, double *scal, int *flags, const RefineCtl &r, int use_handle,
                           cudaGraphConditionalHandle h);
 void launch_sumsq(Ctx &c, const double *part, int nparts, double *dst);
-// FP64 all-at-once residual R = G - [(I + tau K) U - U Sigma_1^T], stored as Tout
-// (float for the mixed path, double for the FP64 path).  rx = (tau lo_x, 1 + tau diag_x,
-// tau up_x) of length nx per problem; 2D adds ry = (tau lo_y, tau diag_y, tau up_y) along
-// the middle axis (ryl == null in 1D), ny rows in all, nym per problem (batches stack
-// their problems along y).  mex (batches, or null): problem j / mlen's residual scaled by
-// 2^mex[problem].
-template <typename Tout>
-void launch_residual(Ctx &c, const double *G, const double *U, Tout *R, int64_t nt, int64_t ny, int64_t nx,
-                     const double *rxl, const double *rxd, const double *rxu, const double *ryl, const double *ryd,
-                     const double *ryu, int64_t nym, const int *mex, int mlen);
+
 
 }  // namespace pd

@@ -245,8 +245,8 @@ struct pd_plan {
   double2 *gpart = nullptr, *srow = nullptr, *omega = nullptr;
   double *msys_part = nullptr;
   double *norm_part = nullptr;
-  float *res_f = nullptr, *tmp_f = nullptr;
-  double *res_d = nullptr, *tmp_d = nullptr;
+  float *tmp_f = nullptr;
+  double *tmp_d = nullptr;
   double *G_stage = nullptr, *U_stage = nullptr;
   // paradiag_solve_host: the device-to-host copy of U, queued behind a graph solve's
   // control-block read so that one host synchronisation covers both
@@ -678,9 +678,7 @@ size_t layout(pd_plan *p, unsigned char *base) {
     p->mflags = A.take<int>((size_t)pd::kFlagWords * nmem);
   }
   p->norm_part = A.take<double>((size_t)std::max<int64_t>(nbar / 2 + 2, 8 * (int64_t)pd::sm_count()));
-  if (mixed) p->res_f = A.take<float>((size_t)nt * nbar);
   if (mixed && p->dim == 2) p->tmp_f = A.take<float>((size_t)nt * nbar);
-  if (!mixed) p->res_d = A.take<double>((size_t)nt * nbar);
   if (!mixed && p->dim == 2) p->tmp_d = A.take<double>((size_t)nt * nbar);
   if (p->mass) {
     p->msc = A.take<double>(nbar);
@@ -1061,12 +1059,6 @@ pd_status factorize(pd_plan *p) {
 }
 
 template <typename T>
-T *res_buf(pd_plan *p);
-template <>
-double *res_buf<double>(pd_plan *p) { return p->res_d; }
-template <>
-float *res_buf<float>(pd_plan *p) { return p->res_f; }
-template <typename T>
 T *tmp_buf(pd_plan *p);
 template <>
 double *tmp_buf<double>(pd_plan *p) { return p->tmp_d; }
@@ -1148,7 +1140,6 @@ pd_status emit_pre(pd_plan *p, int kind, const double *G, double *U, int use_han
   pd::Ctx &c = p->ctx;
   cpx<T> *S = reinterpret_cast<cpx<T> *>(p->spec);
   const int nt = (int)p->nt;
-  T *res = res_buf<T>(p);
   T *tmp = tmp_buf<T>(p);
   // ||R||_F of this solve's right-hand side, the reference of the refining plans' Algorithm-2
   // stop (krylov_decide); batches measure each problem against its own beta instead
@@ -1167,9 +1158,9 @@ pd_status emit_pre(pd_plan *p, int kind, const double *G, double *U, int use_han
       pd::launch_fft_r2c_residual<T>(c, G, U, p->nbar, nt, p->rxl, p->rxd, p->rxu, time_tw<T>(p), S, p->lds,
                                      row_scale<T>(p, false), p->batch > 1 ? p->mex : nullptr, (int)p->nxm, rnp);
     } else {
-      pd::launch_residual<T>(c, G, U, res, p->nt, p->ny, p->nx, p->rxl, p->rxd, p->rxu, p->ryl, p->ryd, p->ryu,
-                             p->nym, p->batch > 1 ? p->mex : nullptr, (int)p->nxm);
-      pd::launch_dst_y<T, T, T>(c, res, tmp, p->nt * p->batch, p->nym, p->nx, dst_tw<T>(p), 0);
+      // the FP64 residual is formed while the DST along y loads its tiles
+      pd::launch_dst_y_residual<T>(c, G, U, tmp, p->nt, p->batch, p->nym, p->nx, p->rxl, p->rxd, p->rxu, p->ryl,
+                                   p->ryd, p->ryu, p->batch > 1 ? p->mex : nullptr, dst_tw<T>(p));
       pd::launch_fft_r2c<T, T>(c, tmp, p->nbar, p->nbar, nt, time_tw<T>(p), S, p->lds, row_scale<T>(p, false), rnp);
     }
   }
