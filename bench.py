@@ -71,15 +71,16 @@ KERNEL_OF = {
     "pint_acc_f64": "k_pint", "pint_dots_f64": "k_pint", "pint_store_f64": "k_pint",
     "fft_r2c_f32": "k_fft_r2c", "fft_r2c_f64": "k_fft_r2c", "fft_r2c_res_f32": "k_fft_r2c_res",
     "fft_r2c_res_f64": "k_fft_r2c_res", "fft_c2r_f32": "k_fft_c2r", "fft_c2r_f64": "k_fft_c2r",
-    "dst_y_f32": "k_dst_y", "dst_y_f64": "k_dst_y", "residual": "k_residual",
+    "dst_y_f32": "k_dst_y", "dst_y_f64": "k_dst_y", "dst_y_res_f32": "k_dst_y", "dst_y_res_f64": "k_dst_y",
+    "krylov_step": "k_step_tail", "early_check": "k_early_check",
     "krylov_init": "k_init_v0_coop", "krylov_arnoldi": "k_arnoldi_coop", "krylov_project": "k_project_coop",
     "krylov_xm": "k_xm", "krylov_sumsq": "k_sumsq_final", "capacitance": "k_capacitance_terms",
     "zsum": "k_zsum", "acc_reduce": "k_acc_reduce", "control": "k_solve_reset",
 }
 # kernels that stream the space-time arrays (bounded by memory); the rest are small
 # FP64 kernels bounded by latency and GB300's FP64 rate
-STREAMING = {"k_pint", "k_fft_r2c", "k_fft_r2c_res", "k_fft_c2r", "k_dst_y", "k_residual", "k_zsum",
-             "k_acc_reduce"}
+STREAMING = {"k_pint", "k_fft_r2c", "k_fft_r2c_res", "k_fft_c2r", "k_dst_y", "k_zsum", "k_acc_reduce",
+             "k_early_check"}
 
 
 def workload(name):

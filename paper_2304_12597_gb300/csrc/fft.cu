@@ -356,20 +356,23 @@ __global__ void __launch_bounds__(kFftMaxThreads) k_fft_r2c(const Tin *__restric
   for (int i0 = threadIdx.x; i0 < total; i0 += kLoadBatch * blockDim.x) {
     T v[kLoadBatch];
 #pragma unroll
+    // element idx = (slot s, column c): time row j = bitrev(s), so that consecutive threads
+    // store to consecutive shared-memory slots (distinct banks)
     for (int u = 0; u < kLoadBatch; ++u) {
       const int idx = i0 + u * (int)blockDim.x;
-      const int j = idx / TX;
-      const int64_t col = x0 + (idx - j * TX);
+      const int sl = idx / TX;
+      const int j = idx < total ? bitrev(sl, logn) : 0;
+      const int64_t col = x0 + (idx - sl * TX);
       v[u] = (idx < total && col < ncols) ? (T)X[(int64_t)j * ldx + col] : T(0);
     }
 #pragma unroll
     for (int u = 0; u < kLoadBatch; ++u) {
       const int idx = i0 + u * (int)blockDim.x;
       if (idx < total) {
-        const int j = idx / TX;
-        const int c = idx - j * TX;
-        T *slot = reinterpret_cast<T *>(&buf[(size_t)(c >> 1) * series_stride(n) + bitrev(j, logn)]);
-        slot[c & 1] = rs ? v[u] * rs[j] : v[u];
+        const int sl = idx / TX;
+        const int c = idx - sl * TX;
+        T *slot = reinterpret_cast<T *>(&buf[(size_t)(c >> 1) * series_stride(n) + sl]);
+        slot[c & 1] = rs ? v[u] * rs[bitrev(sl, logn)] : v[u];
         ss += v[u] * v[u];
       }
     }
@@ -410,11 +413,14 @@ __global__ void __launch_bounds__(kFftMaxThreads, 2) k_fft_r2c_res(const double 
   T *col_buf = reinterpret_cast<T *>(buf + (size_t)(c >> 1) * series_stride(n)) + (c & 1);
   constexpr int kB = kLoadBatch / 2;  // five FP64 loads per element
   T ss = T(0);  // squares of the residual (rn)
-  for (int j0 = (int)threadIdx.x / TX; j0 < n; j0 += kB * ((int)blockDim.x / TX)) {
+  // the threads of a warp take consecutive bit-reversed slots s (time row j = bitrev(s)), so
+  // their shared-memory stores hit distinct banks; each row is its own sector either way
+  for (int s0 = (int)threadIdx.x / TX; s0 < n; s0 += kB * ((int)blockDim.x / TX)) {
     double g[kB], um[kB], ul[kB], uc[kB], ur[kB];
 #pragma unroll
     for (int q = 0; q < kB; ++q) {
-      const int j = j0 + q * ((int)blockDim.x / TX);
+      const int sq = s0 + q * ((int)blockDim.x / TX);
+      const int j = sq < n ? bitrev(sq, logn) : n;
       const bool in = live && j < n;
       const double *u = U + (int64_t)j * ncols + col;
       g[q] = in ? G[(int64_t)j * ncols + col] : 0.0;
@@ -425,12 +431,13 @@ __global__ void __launch_bounds__(kFftMaxThreads, 2) k_fft_r2c_res(const double 
     }
 #pragma unroll
     for (int q = 0; q < kB; ++q) {
-      const int j = j0 + q * ((int)blockDim.x / TX);
-      if (j < n) {
+      const int sq = s0 + q * ((int)blockDim.x / TX);
+      if (sq < n) {
+        const int j = bitrev(sq, logn);
         // four FP64 operations per element (GB300 runs FP64 at ~1/64 of the FP32 rate)
         const double res = fma(-cu, ur[q], fma(-cl, ul[q], fma(-cd, uc[q], g[q] + um[q])));
         const T r = (T)res * msc;
-        col_buf[2 * bitrev(j, logn)] = rs ? r * rs[j] : r;
+        col_buf[2 * sq] = rs ? r * rs[j] : r;
         ss += r * r;
       }
     }
