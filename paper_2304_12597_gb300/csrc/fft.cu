@@ -680,7 +680,7 @@ __global__ void __launch_bounds__(256) k_dst_y(const Tin *__restrict__ X, Tout *
 #pragma unroll
       for (int u = 0; u < kLoadBatch; ++u) {
         const int idx = i0 + u * (int)blockDim.x;
-        if (idx < total) rt[idx] = (T)(rv[u] * msc);
+        if (idx < total) rt[idx] = rin.mex ? (T)(rv[u] * msc) : (T)rv[u];
       }
     }
     __syncthreads();

@@ -227,6 +227,8 @@ struct PintArgs {
   const double *xm_Vd;     // starting at k = 0 also store x_m in FP64 (from xm_Vd) into xm_out
   double *xm_out;
   const double2 *shift;    // s_k = 1 - pi_k, length nf
+  const cpx<T> *shift_t;   // the same in the compute type (binary32 plans; null = convert)
+  const cpx<T> *omega_t;   // omega in the compute type (null = convert)
   const T *tlo, *tdiag, *tup;  // tau * K (block-decoupled), length nblk*blen
   const cpx<T> *R;         // spectrum right-hand sides (nf, ldr) or null
   int64_t ldr;

@@ -487,8 +487,15 @@ __global__ void __launch_bounds__(MAXT) k_pint(PintGeom g, PintArgs<T> a, size_t
         continue;
       }
     }
-    const double2 sk = a.shift[k];
-    const cpx<T> s = mk<T>((T)sk.x, (T)sk.y);
+    // the shift in the compute type (binary32 plans keep a converted copy: no FP64-pipe
+    // conversion per frequency on GB300)
+    cpx<T> s;
+    if (a.shift_t) {
+      s = a.shift_t[k];
+    } else {
+      const double2 sk = a.shift[k];
+      s = mk<T>((T)sk.x, (T)sk.y);
+    }
     const cpx<T> *Rk = a.R ? a.R + (int64_t)k * a.ldr + off : nullptr;  // this block's row of R
     const T *rv = rvec ? rvec + off : nullptr;
     // 1. stage the right-hand side (element e at dd[e + e/M])
@@ -700,8 +707,15 @@ __global__ void __launch_bounds__(MAXT) k_pint(PintGeom g, PintArgs<T> a, size_t
     my[M - 1] = xl;
     }
     if (do_acc) {
-      const double2 omd = a.omega[k];
-      const T ox = (T)omd.x, oy = (T)omd.y;
+      T ox, oy;
+      if (a.omega_t) {
+        ox = a.omega_t[k].x;
+        oy = a.omega_t[k].y;
+      } else {
+        const double2 omd = a.omega[k];
+        ox = (T)omd.x;
+        oy = (T)omd.y;
+      }
 #pragma unroll
       for (int i = 0; i < M; ++i) acc[i * P + t] += ox * my[i].x - oy * my[i].y;
     }

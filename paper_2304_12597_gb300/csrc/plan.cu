@@ -219,6 +219,7 @@ struct pd_plan {
 
   // device buffers
   double2 *shift = nullptr, *wg = nullptr;
+  cpx<float> *shift_f = nullptr, *wg_f = nullptr;  // binary32 copies for the shifted solves
   double2 *wga = nullptr;  // alpha^{1/l} w_k gamma_k: weights of the inner system (eq. 17)
   double *ts_d = nullptr, *tsi_d = nullptr;  // D_alpha and D_alpha^{-1} (time rows)
   float *ts_f = nullptr, *tsi_f = nullptr;
@@ -602,6 +603,10 @@ size_t layout(pd_plan *p, unsigned char *base) {
   const bool mixed = p->precision == PD_MIXED;
   p->shift = A.take<double2>(nf);
   p->wg = A.take<double2>(nf);
+  if (mixed) {
+    p->shift_f = A.take<cpx<float>>(nf);
+    p->wg_f = A.take<cpx<float>>(nf);
+  }
   p->wga = A.take<double2>(nf);
   p->ts_d = A.take<double>(nt);
   p->tsi_d = A.take<double>(nt);
@@ -1009,6 +1014,7 @@ pd::PintArgs<float> base_args<float>(pd_plan *p) {
   if (p->precision == PD_MIXED) a.fac_in = reinterpret_cast<const cpx<float> *>(p->fac);
   a.xm_scale = p->aroot;
   a.shift = p->shift;
+  a.shift_t = p->shift_f;
   a.tlo = p->tlo_f;
   a.tdiag = p->tdiag_f;
   a.tup = p->tup_f;
@@ -1176,6 +1182,7 @@ pd_status emit_pre(pd_plan *p, int kind, const double *G, double *U, int use_han
   a.R = S;
   a.ldr = p->lds;
   a.omega = p->wg;
+  if constexpr (sizeof(T) == 4) a.omega_t = reinterpret_cast<const cpx<T> *>(p->wg_f);
   a.acc_part = p->acc_part;
   a.acc0 = lane_acc0<T>(p);
   if (early) {
@@ -1686,6 +1693,7 @@ pd_status paradiag_plan(const pd_desc *desc, void *workspace, size_t workspace_b
   const int64_t nt = p->nt;
   const double a = p->aroot;
   std::vector<double2> shift(nf), wg(nf), wga(nf);
+  std::vector<cpx<float>> shift_f(nf), wg_f(nf);
   for (int k = 0; k < nf; ++k) {
     const double ang = -2.0 * M_PI * (double)k / (double)nt;
     const double pr = std::cos(ang), pi_ = std::sin(ang);
@@ -1693,6 +1701,8 @@ pd_status paradiag_plan(const pd_desc *desc, void *workspace, size_t workspace_b
     shift[k] = make_double2(1.0 - a * pr, -a * pi_);
     wg[k] = make_double2(wk * pr / (double)nt, wk * pi_ / (double)nt);
     wga[k] = make_double2(a * wg[k].x, a * wg[k].y);
+    shift_f[k] = pd::mk<float>((float)shift[k].x, (float)shift[k].y);
+    wg_f[k] = pd::mk<float>((float)wg[k].x, (float)wg[k].y);
   }
   std::vector<double> ts(nt), tsi(nt);
   std::vector<float> tsf(nt), tsif(nt);
@@ -1715,7 +1725,8 @@ pd_status paradiag_plan(const pd_desc *desc, void *workspace, size_t workspace_b
       (st = upload(p->wga, wga.data(), nf, s)) || (st = upload(p->tw_d, tw.data(), ntw, s)) ||
       (st = upload(p->tw_f, twf.data(), ntw, s)) || (st = upload(p->ts_d, ts.data(), nt, s)) ||
       (st = upload(p->tsi_d, tsi.data(), nt, s)) || (st = upload(p->ts_f, tsf.data(), nt, s)) ||
-      (st = upload(p->tsi_f, tsif.data(), nt, s)))
+      (st = upload(p->tsi_f, tsif.data(), nt, s)) || (st = upload(p->shift_f, shift_f.data(), nf, s)) ||
+      (st = upload(p->wg_f, wg_f.data(), nf, s)))
     return cleanup(st);
   if (p->dim == 2) {
     const int N = (int)(2 * (p->nym + 1));
