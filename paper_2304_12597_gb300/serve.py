@@ -9,7 +9,9 @@ over time.  The scheduler groups the waiting ones into batches, and worker threa
   points (each problem's Algorithm 2 then runs in one CTA); larger grids run one per plan.
 Requests that arrive while batches are running join the next batch as soon as a
 worker and enough device memory are free.  Admission is by an HBM budget that counts
-the workspace, G and U of every batch in flight plus the cached plans.
+the workspace, G and U of every batch in flight; idle cached plans (up to
+plan_cache_bytes, half the budget by default) come on top of it, so the service can hold
+about 1.5 times budget_bytes of device memory.
 
 Plans are cached per (shape, capacity) and worker; a new batch swaps its operators in
 with paradiag_set_operator, so the workspace and the captured CUDA graph are reused.
