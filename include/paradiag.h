@@ -92,12 +92,12 @@ typedef struct pd_desc {
   double eps_krylov;     /* Algorithm 2 tolerance epsilon (stop when ||r|| <= eps * ||b||);
                             0 = 1e-13 for PD_FP64 (1e-5 for PD_FP64 batches and alpha < 1,
                             which always refine and leave a stalled step at any level),
-                            1e-5 for the first solve of PD_MIXED
-                            (its refinement sweeps use max(eps_krylov, 1e-3)).
+                            1e-4 for the first solve of PD_MIXED
+                            (its refinement sweeps use max(eps_krylov, eps_krylov_refine)).
                             Both also stop when ||r|| stalls near the precision floor (no
                             halving over 1 iteration in PD_MIXED once ||r|| <= 1e-3 ||b||, and
-                            at any level in its refinement sweeps; over 3 iterations in PD_FP64
-                            once ||r|| <= 1e-6 ||b||) */
+                            over 2 once ||r|| <= 10 eps_krylov_refine ||b|| in its refinement
+                            sweeps; over 3 iterations in PD_FP64 once ||r|| <= 1e-6 ||b||) */
   int32_t q;             /* residual check period of Algorithm 2 (Sec. 3, the frozen residual):
                             the shifted solves h_k, eq. (12) and eq. (13) run only at steps
                             m with m mod q = 0, at m = maxit and at a breakdown, so a solve
@@ -207,7 +207,7 @@ typedef struct pd_desc {
                                 early_exit_eps ||U_1||_F, the solve returns U = U_1 without
                                 Algorithm 2, the final loop or refinement (pd_stats.early_exit).
                                 0 = off (the test costs an inverse DFT and a residual pass) */
-  double eps_krylov_refine;  /* PD_MIXED: Algorithm 2 tolerance of the refinement sweeps (0 = 1e-3);
+  double eps_krylov_refine;  /* PD_MIXED: Algorithm 2 tolerance of the refinement sweeps (0 = 3e-3);
                                 a sweep's Algorithm 2 also leaves once its residual is below
                                 10 eps_krylov_refine and stops halving */
 } pd_desc;
