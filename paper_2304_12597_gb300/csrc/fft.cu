@@ -18,6 +18,9 @@ namespace pd {
 
 // Global loads a thread issues back to back before it uses any of them.
 constexpr int kLoadBatch = 8;
+// Output elements per thread in flight in the stores that read U first (mode 1): half the
+// load batch keeps those epilogues from setting the kernels' register count.
+constexpr int kEpiBatch = 4;
 // Threads per CTA of the forward time DFTs: 512 once a tile holds >= 4096 values (n TX),
 // so each thread issues one batch of loads and takes one butterfly per pass; else 256.
 // (The inverse DFT keeps 256: its FP64 update needs more than the 64 registers a thread
@@ -323,7 +326,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512)
     for (int i = 0; i < 16; ++i) {
       const int64_t j = r + i * nb;
       const Tin *row = X + j * ldx;
-      z[i] = mk<T>(va ? (T)row[ca] : T(0), vb ? (T)row[cb] : T(0));
+      z[i] = mk<T>(va ? cvt<T>(row[ca]) : T(0), vb ? cvt<T>(row[cb]) : T(0));
     }
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
@@ -363,7 +366,7 @@ __global__ void __launch_bounds__(kFftMaxThreads) k_fft_r2c(const Tin *__restric
       const int sl = idx / TX;
       const int j = idx < total ? bitrev(sl, logn) : 0;
       const int64_t col = x0 + (idx - sl * TX);
-      v[u] = (idx < total && col < ncols) ? (T)X[(int64_t)j * ldx + col] : T(0);
+      v[u] = (idx < total && col < ncols) ? cvt<T>(X[(int64_t)j * ldx + col]) : T(0);
     }
 #pragma unroll
     for (int u = 0; u < kLoadBatch; ++u) {
@@ -436,7 +439,7 @@ __global__ void __launch_bounds__(kFftMaxThreads, 2) k_fft_r2c_res(const double 
         const int j = bitrev(sq, logn);
         // four FP64 operations per element (GB300 runs FP64 at ~1/64 of the FP32 rate)
         const double res = fma(-cu, ur[q], fma(-cl, ul[q], fma(-cd, uc[q], g[q] + um[q])));
-        const T r = (T)res * msc;
+        const T r = cvt<T>(res) * msc;
         col_buf[2 * sq] = rs ? r * rs[j] : r;
         ss += r * r;
       }
@@ -528,10 +531,10 @@ __global__ void __launch_bounds__(256) k_fft_c2r(const cpx<T> *__restrict__ S, i
   }
   float ss = 0.0f;  // a few dozen squares per thread; the stop rule needs a few digits
   const int tot2 = n * TX;
-  for (int i0 = threadIdx.x; i0 < tot2; i0 += kLoadBatch * blockDim.x) {
-    double old[kLoadBatch];  // U before the update (mode 1)
+  for (int i0 = threadIdx.x; i0 < tot2; i0 += kEpiBatch * blockDim.x) {
+    double old[kEpiBatch];  // U before the update (mode 1)
 #pragma unroll
-    for (int u = 0; u < kLoadBatch; ++u) {
+    for (int u = 0; u < kEpiBatch; ++u) {
       const int idx = i0 + u * (int)blockDim.x;
       const int j = idx / TX;
       const int64_t col = x0 + (idx - j * TX);
@@ -539,7 +542,7 @@ __global__ void __launch_bounds__(256) k_fft_c2r(const cpx<T> *__restrict__ S, i
                                                          : 0.0;
     }
 #pragma unroll
-    for (int u = 0; u < kLoadBatch; ++u) {
+    for (int u = 0; u < kEpiBatch; ++u) {
       const int idx = i0 + u * (int)blockDim.x;
       const int j = idx / TX;
       const int c = idx - j * TX;
@@ -551,9 +554,9 @@ __global__ void __launch_bounds__(256) k_fft_c2r(const cpx<T> *__restrict__ S, i
       const T v = ((c & 1) == 0) ? r.x * sc : -r.y * sc;
       const int64_t o = (int64_t)j * ldo + col;
       if (mode == 0) {
-        reinterpret_cast<double *>(out)[o] = (double)v;
+        reinterpret_cast<double *>(out)[o] = cvt<double>(v);
       } else if (mode == 1) {
-        reinterpret_cast<double *>(out)[o] = old[u] + (double)v;
+        reinterpret_cast<double *>(out)[o] = old[u] + cvt<double>(v);
       } else {
         reinterpret_cast<float *>(out)[o] = (float)v;
       }
@@ -680,7 +683,7 @@ __global__ void __launch_bounds__(256) k_dst_y(const Tin *__restrict__ X, Tout *
 #pragma unroll
       for (int u = 0; u < kLoadBatch; ++u) {
         const int idx = i0 + u * (int)blockDim.x;
-        if (idx < total) rt[idx] = rin.mex ? (T)(rv[u] * msc) : (T)rv[u];
+        if (idx < total) rt[idx] = cvt<T>(rin.mex ? rv[u] * msc : rv[u]);
       }
     }
     __syncthreads();
@@ -690,7 +693,7 @@ __global__ void __launch_bounds__(256) k_dst_y(const Tin *__restrict__ X, Tout *
     if constexpr (RES)
       return rt[y * TX + (int)(col - x0)];
     else
-      return (T)Xt[(int64_t)y * nx + col];
+      return cvt<T>(Xt[(int64_t)y * nx + col]);
   };
   if constexpr (R16) {  // radix-16 first stage in registers (see k_fft_r2c16)
     const int SS = series_stride16(N), nb = N >> 4, lb = logN - 4, half = N >> 1;
@@ -747,17 +750,17 @@ __global__ void __launch_bounds__(256) k_dst_y(const Tin *__restrict__ X, Tout *
     __syncthreads();
     fft_smem<T>(buf, N, logN, np, tw);
   }
-  for (int i0 = threadIdx.x; i0 < total; i0 += kLoadBatch * blockDim.x) {
-    Tout old[kLoadBatch];  // Y before the update (mode 1)
+  for (int i0 = threadIdx.x; i0 < total; i0 += kEpiBatch * blockDim.x) {
+    Tout old[kEpiBatch];  // Y before the update (mode 1)
 #pragma unroll
-    for (int u = 0; u < kLoadBatch; ++u) {
+    for (int u = 0; u < kEpiBatch; ++u) {
       const int idx = i0 + u * (int)blockDim.x;
       const int l = idx / TX;
       const int64_t col = x0 + (idx - l * TX);
       old[u] = (mode != 0 && idx < total && col < nx) ? Yt[(int64_t)l * nx + col] : Tout(0);
     }
 #pragma unroll
-    for (int u = 0; u < kLoadBatch; ++u) {
+    for (int u = 0; u < kEpiBatch; ++u) {
       const int idx = i0 + u * (int)blockDim.x;
       const int l = idx / TX;  // output index l = 0..ny-1  <->  mode l+1
       const int c = idx - l * TX;
@@ -768,9 +771,9 @@ __global__ void __launch_bounds__(256) k_dst_y(const Tin *__restrict__ X, Tout *
       const T v = ((c & 1) == 0) ? (T(-0.5) * scale) * z.y : (T(0.5) * scale) * z.x;
       const int64_t o = (int64_t)l * nx + col;
       if (mode == 0) {
-        Yt[o] = (Tout)v;
+        Yt[o] = cvt<Tout>(v);
       } else {
-        Yt[o] = old[u] + (Tout)v;
+        Yt[o] = old[u] + cvt<Tout>(v);
       }
     }
   }

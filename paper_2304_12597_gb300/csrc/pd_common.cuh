@@ -86,6 +86,39 @@ __device__ __forceinline__ void team_sync(int P, int team_in_cta) {
   }
 }
 
+// binary64 -> binary32 by integer operations on the bit pattern: GB300 issues FP64
+// instructions, conversions included, at a small fraction of its FP32 and integer rates, and
+// the binary32 path converts every FP64 element it loads (in the kernels that also run FP64
+// arithmetic, such as the residual, this frees the FP64 pipe; measured 8% on the 2D residual
+// DST).  The significand is truncated (error below one binary32 ulp, where round-to-nearest
+// gives half an ulp); magnitudes below binary32's normal range become zero, above it
+// infinity; NaN stays NaN.  binary32 -> binary64 keeps the hardware conversion, which
+// measured faster than its integer form.
+__device__ __forceinline__ float f64_to_f32_bits(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu);
+  const int ef = e - 896;  // binary32 biased exponent: e - 1023 + 127
+  unsigned r;
+  if (ef >= 255) {
+    r = sign | 0x7f800000u | ((e == 0x7ff && ((hi & 0xfffffu) | lo)) ? 0x00400000u : 0u);
+  } else if (ef <= 0) {
+    r = sign;
+  } else {
+    r = sign | ((unsigned)ef << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  }
+  return __uint_as_float(r);
+}
+// cvt<To>(x): x in type To, binary64 -> binary32 through the integer conversion above.
+template <typename To, typename From>
+__device__ __forceinline__ To cvt(From x) {
+  if constexpr (sizeof(To) == 4 && sizeof(From) == 8)
+    return f64_to_f32_bits(x);
+  else
+    return (To)x;
+}
+
 // Programmatic dependent launch: every kernel of this library opens with this wait,
 // so a kernel scheduled early (while its predecessor in the stream drains) reads
 // nothing before the predecessor has completed; without such a launch it returns at once.
