@@ -210,6 +210,16 @@ typedef struct pd_desc {
   double eps_krylov_refine;  /* PD_MIXED: Algorithm 2 tolerance of the refinement sweeps (0 = 3e-3);
                                 a sweep's Algorithm 2 also leaves once its residual is below
                                 10 eps_krylov_refine and stops halving */
+  int32_t tune_final_loop;   /* single problems, loops = 0: when Algorithm 2 stops after one step,
+                                form Algorithm 1's final loop by linearity instead of a third set
+                                of shifted solves: Y_k = L_k - phi_k v_1 + psi_k h_k, where
+                                L_k = A_k^{-1} G^_k is stored by the first loop, h_k = A_k^{-1} v_2
+                                by Algorithm 2's step, phi_k = alpha^{1/l} y_1 / (s_k + tau t_11)
+                                and psi_k = tau t_21 phi_k (eq. 10's relation tau K v_1 =
+                                tau (t_11 v_1 + t_21 v_2)), formed by one elementwise pass over
+                                the spectrum.  0 = on where it applies (costs one spectrum-sized
+                                buffer), -1 = always run the final loop's solves.  Not used with
+                                the binary32 path's FP64 zero-frequency lane. */
 } pd_desc;
 
 /* Statistics of the last paradiag_solve / paradiag_solve_host. */
@@ -243,6 +253,8 @@ typedef struct pd_stats {
   int32_t early_exit;       /* 1 if Algorithm 3's test on U_1 passed and U = U_1 */
   double u1_rel_residual;   /* ||(I + tau K) U_1 - U_1 Sigma_1^T - G||_F / ||U_1||_F of that test
                                (0 when early_exit_eps = 0) */
+  int32_t final_by_linearity;  /* solves whose final loop was formed by linearity
+                                  (pd_desc.tune_final_loop); shifted_sweeps excludes them */
 } pd_stats;
 
 typedef struct pd_plan pd_plan;

@@ -76,6 +76,7 @@ class PdDesc(ctypes.Structure):
         ("tune_zero_lane", ctypes.c_int32),
         ("early_exit_eps", ctypes.c_double),
         ("eps_krylov_refine", ctypes.c_double),
+        ("tune_final_loop", ctypes.c_int32),
     ]
 
 
@@ -101,6 +102,7 @@ class PdStats(ctypes.Structure):
         ("persistent_step", ctypes.c_int32),
         ("early_exit", ctypes.c_int32),
         ("u1_rel_residual", ctypes.c_double),
+        ("final_by_linearity", ctypes.c_int32),
     ]
 
     def as_dict(self):

@@ -467,6 +467,79 @@ __global__ void k_xm(int n, const int *flags, const double *__restrict__ V, cons
 }
 
 // *dst = sum of part[0..nparts) (one warp, fixed order)
+// The final parallel-in-time loop by linearity, after an Algorithm-2 run of one step.
+// Arnoldi's relation (eq. 10) tau K v_1 = tau (t_11 v_1 + t_21 v_2) gives
+// A_k v_1 = (s_k + tau t_11) v_1 + tau t_21 v_2 for A_k = s_k I + tau K, hence
+// A_k^{-1} v_1 = (v_1 - tau t_21 h_k) / (s_k + tau t_11), with h_k = A_k^{-1} v_2 the
+// step's stored shifted solves.  The final loop Y_k = A_k^{-1}(G^_k - a x_1), x_1 = y_1 v_1
+// (a = alpha^{1/l}, 1 for Algorithm 1), is therefore
+//   Y_k = L_k - phi_k v_1 + psi_k h_k,  phi_k = a y_1 / (s_k + tau t_11),  psi_k = tau t_21 phi_k,
+// with L_k = A_k^{-1} G^_k stored by the first loop: an elementwise pass over the spectrum
+// instead of a third set of shifted solves.  Mode (the same in every CTA): 2, or 1 without
+// the h_k term after a breakdown (t_21 = 0, no h_k formed), when Algorithm 2 stopped at
+// m = 1 and U_1 was not taken; else 0 and S is left to the final loop.  CTAs with
+// blockIdx.x = k < nf write row k of S (kCombCols columns each, blockIdx.y the chunk);
+// blockIdx.x = nf forms x = x_m in FP64 for any m (paradiag_last_vectors).
+constexpr int kCombCols = 1024;
+template <typename T>
+__global__ void __launch_bounds__(256) k_final_comb(int nf, int64_t n, int64_t lds, double tau, double aroot,
+                                                    const double2 *__restrict__ shift, const double *__restrict__ Tm,
+                                                    const double *__restrict__ y, const double *__restrict__ V,
+                                                    const T *__restrict__ v1, const double *__restrict__ scal,
+                                                    int *flags, const cpx<T> *__restrict__ L,
+                                                    const cpx<T> *__restrict__ H, cpx<T> *__restrict__ S, double *x) {
+  grid_dep_wait();
+  __shared__ cpx<T> coef[2];
+  const int m = flags[F_M];
+  const int mode = (m == 1 && !flags[F_EARLY] && !flags[F_TIMEOUT]) ? (flags[F_NOH] ? 1 : 2) : 0;
+  const int k = blockIdx.x;
+  const int64_t cstride = (int64_t)gridDim.y * kCombCols;  // chunks beyond 65535 loop
+  if (k == nf) {  // x_m in FP64
+    if (blockIdx.y == 0 && threadIdx.x == 0) {
+      flags[F_COMB] = mode;
+      if (mode) flags[F_COMBCNT] += 1;
+    }
+    for (int64_t c0 = (int64_t)blockIdx.y * kCombCols; c0 < n; c0 += cstride)
+      for (int64_t j = c0 + threadIdx.x; j < n && j < c0 + kCombCols; j += blockDim.x) {
+        double v = 0.0;
+        for (int q = 0; q < m; ++q) v += y[q] * V[(int64_t)q * n + j];
+        x[j] = v;
+      }
+    return;
+  }
+  if (!mode) return;
+  if (threadIdx.x == 0) {
+    const double2 sk = shift[k];
+    const cpx<double> r = recip(mk<double>(sk.x + tau * Tm[0], sk.y));
+    const double ay = aroot * y[0], tt = mode == 2 ? tau * scal[S_T] : 0.0;
+    coef[0] = mk<T>((T)(ay * r.x), (T)(ay * r.y));
+    coef[1] = mk<T>((T)(tt * ay * r.x), (T)(tt * ay * r.y));
+  }
+  __syncthreads();
+  const cpx<T> ph = coef[0], ps = coef[1];
+  constexpr int kE = kCombCols / 256;
+  const int64_t o = (int64_t)k * lds;
+  for (int64_t c0 = (int64_t)blockIdx.y * kCombCols; c0 < n; c0 += cstride) {
+    cpx<T> l[kE], h[kE];
+    T v[kE];
+#pragma unroll
+    for (int e = 0; e < kE; ++e) {  // all loads in flight before any use
+      const int64_t j = c0 + threadIdx.x + e * 256;
+      const bool in = j < n;
+      l[e] = in ? L[o + j] : mk<T>(T(0), T(0));
+      h[e] = (in && mode == 2) ? H[o + j] : mk<T>(T(0), T(0));
+      v[e] = in ? v1[j] : T(0);
+    }
+#pragma unroll
+    for (int e = 0; e < kE; ++e) {
+      const int64_t j = c0 + threadIdx.x + e * 256;
+      if (j < n)
+        S[o + j] = mk<T>(l[e].x - ph.x * v[e] + ps.x * h[e].x - ps.y * h[e].y,
+                         l[e].y - ph.y * v[e] + ps.x * h[e].y + ps.y * h[e].x);
+    }
+  }
+}
+
 __global__ void k_sumsq_final(const double *part, int nparts, double *dst) {
   grid_dep_wait();
   double s = 0.0;
@@ -900,6 +973,26 @@ void launch_xm(Ctx &c, KrylovBufs &k, const double *y, double *x, float *xf) {
            [&] { pdl_launch(c.pdl, k_xm, dim3(k.grid), dim3(kBlas), 0, c.stream, k.n, (const int *)k.flags, (const double *)k.V,
                                 y, x, xf); });
 }
+
+template <typename T>
+void launch_final_comb(Ctx &c, int nf, int64_t n, int64_t lds, double tau, double aroot, const double2 *shift,
+                       const double *Tm, const double *y, const double *V, const T *v1, const double *scal,
+                       int *flags, const cpx<T> *L, const cpx<T> *H, cpx<T> *S, double *x) {
+  const dim3 grid((unsigned)(nf + 1), (unsigned)std::min<int64_t>((n + kCombCols - 1) / kCombCols, 65535));
+  // algorithmic bytes: L and h_k read, S written (when the final loop is formed here)
+  c.launch("final_comb", (double)nf * n * 3.0 * sizeof(cpx<T>), [&] {
+    pdl_launch(c.pdl, k_final_comb<T>, grid, dim3(256), 0, c.stream, nf, n, lds, tau, aroot, shift, Tm, y, V, v1,
+               scal, flags, L, H, S, x);
+  });
+}
+template void launch_final_comb<float>(Ctx &, int, int64_t, int64_t, double, double, const double2 *,
+                                       const double *, const double *, const double *, const float *,
+                                       const double *, int *, const cpx<float> *, const cpx<float> *,
+                                       cpx<float> *, double *);
+template void launch_final_comb<double>(Ctx &, int, int64_t, int64_t, double, double, const double2 *,
+                                        const double *, const double *, const double *, const double *,
+                                        const double *, int *, const cpx<double> *, const cpx<double> *,
+                                        cpx<double> *, double *);
 
 void launch_sumsq(Ctx &c, const double *part, int nparts, double *dst) {
   c.launch("krylov_sumsq", 0.0, [&] { pdl_launch(c.pdl, k_sumsq_final, dim3(1), dim3(32), 0, c.stream, part, nparts, dst); });

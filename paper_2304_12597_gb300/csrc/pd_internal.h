@@ -40,6 +40,8 @@ enum FlagIndex {
   F_BARGEN = 36,  // grid barrier of the persistent step: generation
   F_EARLY = 37,   // Algorithm 3's residual test on U_1 passed: U = U_1
   F_EARLYCNT = 38,  // completion counter of that test
+  F_COMB = 39,    // this solve forms its final loop by linearity (1; 2 with the h_k term), 0 = solves
+  F_COMBCNT = 40, // solves whose final loop was formed by linearity
   kFlagWords = 64
 };
 // CTA size of the cooperative Krylov vector kernels (pd_krylov.cuh, kCoop mode).
@@ -244,6 +246,7 @@ struct PintArgs {
   int mdots;               // number of basis vectors dotted with y_k
   double2 *gpart;          // (nf, nblk, mdots) dot products y_k . V[q]
   const int *skip_flag;    // if non-null and *skip_flag != 0 the kernel does nothing
+  const int *skip_flag2;   // a second such flag (the final loop formed by linearity)
   double xm_scale;         // with xm_count: subtract xm_scale * x_m (alpha^{1/l} in Algorithm 3)
   int64_t xm_ldy;          // block blk takes y_m from xm_y + blk * xm_ldy (0: one y_m)
   int xm_bpm;              // blocks per batch member (2D batches: the modes of its T_y; 0 = 1)
@@ -409,6 +412,16 @@ void launch_early_finish(Ctx &c, double *scal, int *flags, int use_handle, cudaG
 void launch_project_resnorm(Ctx &c, KrylovBufs &k, const double *z, double tau, const KrylovCtl &kc,
                             int use_handle, cudaGraphConditionalHandle h);
 void launch_xm(Ctx &c, KrylovBufs &k, const double *y, double *x, float *xf);
+// Algorithm 1's final loop by linearity (k_final_comb): when Algorithm 2 stopped after one
+// step (F_M == 1) and U_1 was not taken, flags[F_COMB] != 0 and the spectrum S becomes
+// Y_k = L_k - phi_k v_1 + psi_k h_k (L from the first loop, h_k in H, both (nf, lds)), so the
+// final loop's solves are skipped (PintArgs.skip_flag2); else flags[F_COMB] = 0 and S is left
+// for them.  Also x = x_m = sum_{q<m} y_q V[q] in FP64 (length n) for any m.
+template <typename T>
+void launch_final_comb(Ctx &c, int nf, int64_t n, int64_t lds, double tau, double aroot, const double2 *shift,
+                       const double *Tm, const double *y, const double *V, const T *v1, const double *scal,
+                       int *flags, const cpx<T> *L, const cpx<T> *H, cpx<T> *S, double *x);
+
 
 void launch_solve_reset(Ctx &c, double *scal, int *flags);
 void launch_krylov_decide(Ctx &c, double *scal, int *flags, const KrylovCtl &k, int use_handle,

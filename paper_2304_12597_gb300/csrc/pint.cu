@@ -355,6 +355,7 @@ template <typename T, int M, int MAXT, bool FACT>
 __global__ void __launch_bounds__(MAXT) k_pint(PintGeom g, PintArgs<T> a, size_t team_bytes) {
   grid_dep_wait();
   if (a.skip_flag && *a.skip_flag) return;
+  if (a.skip_flag2 && *a.skip_flag2) return;
   const int P = g.P;
   const int tic = threadIdx.x / P;
   const int t = threadIdx.x - tic * P;
@@ -1044,8 +1045,9 @@ static void launch_pint_m(Ctx &c, const PintGeom &g, const PintArgs<T> &a) {
   if (a.R) bytes += per * sizeof(cpx<T>);
   if (a.Y) bytes += per * sizeof(cpx<T>);
   const bool dots = a.mcount ? a.want_dots != 0 : a.mdots > 0;
-  const char *fam = sizeof(T) == 8 ? (dots ? "pint_dots_f64" : (a.Y ? "pint_store_f64" : "pint_acc_f64"))
-                                   : (dots ? "pint_dots_f32" : (a.Y ? "pint_store_f32" : "pint_acc_f32"));
+  // the b pass may also store L (Y set): it is named by its accumulation
+  const char *fam = sizeof(T) == 8 ? (dots ? "pint_dots_f64" : (a.omega ? "pint_acc_f64" : "pint_store_f64"))
+                                   : (dots ? "pint_dots_f32" : (a.omega ? "pint_acc_f32" : "pint_store_f32"));
   if (a.fac_out) {
     fam = sizeof(T) == 8 ? "pint_factor_f64" : "pint_factor_f32";
     bytes = (double)pint_factor_elems(g) * sizeof(cpx<T>);

@@ -168,6 +168,10 @@ struct pd_plan {
   double eps = 1e-13;
   double eps_refine = 3e-3;  // PD_MIXED: Algorithm 2 tolerance of the refinement sweeps
   double early_eps = 0.0;    // Algorithm 3's residual test on U_1 (0 = off)
+  // the final loop by linearity when Algorithm 2 stops at m = 1 (k_final_comb): the first
+  // loop stores L_k in lbuf
+  bool comb = false;
+  void *lbuf = nullptr;
   int max_refine = 6;
   double refine_tol = 1e-13;
   int host_io = 0;
@@ -501,6 +505,7 @@ void fill_geometry(pd_plan *p, const pd_desc *d) {
   p->refine_tol = d->refine_tol > 0 ? d->refine_tol : (d->precision == PD_FP64 ? 1e-14 : 1e-11);
   p->eps_refine = d->eps_krylov_refine > 0 ? d->eps_krylov_refine : 3e-3;
   p->early_eps = d->early_exit_eps;
+  p->comb = d->tune_final_loop >= 0 && p->batch == 1 && d->loops == 0;
   p->host_io = d->host_io;
   // tridiagonal blocks of nx rows: one per problem (1D) or per mode of T_y (2D)
   p->nblk = p->dim == 2 ? (int)p->ny : p->batch;
@@ -651,6 +656,8 @@ size_t layout(pd_plan *p, unsigned char *base) {
   }
   p->spec = mixed ? (void *)A.take<cpx<float>>((size_t)nf * p->lds) : (void *)A.take<cpx<double>>((size_t)nf * p->lds);
   p->hbuf = mixed ? (void *)A.take<cpx<float>>((size_t)nf * p->lds) : (void *)A.take<cpx<double>>((size_t)nf * p->lds);
+  if (p->comb)
+    p->lbuf = mixed ? (void *)A.take<cpx<float>>((size_t)nf * p->lds) : (void *)A.take<cpx<double>>((size_t)nf * p->lds);
   if (p->factored)
     p->fac = mixed ? (void *)A.take<cpx<float>>(pd::pint_factor_elems(p->geom))
                    : (void *)A.take<cpx<double>>(pd::pint_factor_elems(p->geom));
@@ -967,6 +974,10 @@ pd_status sync_read(pd_plan *p, bool with_tail = false) {
   return ctx_status(p);
 }
 
+// The final loop by linearity applies to single problems of the full method whose zero
+// frequency runs in binary32 like the others (the FP64 lane keeps the final loop's solves).
+bool use_comb(const pd_plan *p) { return p->comb && !(p->precision == PD_MIXED && p->lane); }
+
 template <typename T>
 const cpx<T> *time_tw(pd_plan *p);
 template <>
@@ -1177,10 +1188,12 @@ pd_status emit_pre(pd_plan *p, int kind, const double *G, double *U, int use_han
     pd::launch_inner_fixed(c, p->scal, p->flags, p->y, 1, use_handle, hk);
     return PD_OK;
   }
-  // Algorithm 3's test on U_1 (first solve): the first loop also stores L (in the h_k
-  // buffer, free until Algorithm 2 starts)
+  // Algorithm 3's test on U_1 (first solve) forms U_1 from L
   const bool early = kind == 0 && p->early_eps > 0.0;
-  cpx<T> *L = reinterpret_cast<cpx<T> *>(p->hbuf);
+  // L_k = A_k^{-1} G^_k: kept for the final loop by linearity, or for U_1 (then in the h_k
+  // buffer, free until Algorithm 2 starts)
+  const bool comb = use_comb(p);
+  cpx<T> *L = reinterpret_cast<cpx<T> *>(comb ? p->lbuf : p->hbuf);
   pd::PintArgs<T> a = base_args<T>(p);
   a.R = S;
   a.ldr = p->lds;
@@ -1188,7 +1201,7 @@ pd_status emit_pre(pd_plan *p, int kind, const double *G, double *U, int use_han
   if constexpr (sizeof(T) == 4) a.omega_t = reinterpret_cast<const cpx<T> *>(p->wg_f);
   a.acc_part = p->acc_part;
   a.acc0 = lane_acc0<T>(p);
-  if (early) {
+  if (early || comb) {
     a.Y = L;
     a.ldy = p->lds;
   }
@@ -1342,6 +1355,14 @@ pd_status emit_post(pd_plan *p, int kind, double *U, int use_handle, cudaGraphCo
   const bool early = kind == 0 && p->early_eps > 0.0;
   const int *skip = early ? p->flags + pd::F_EARLY : nullptr;  // U = U_1 already
   a.skip_flag = skip;
+  // after one Algorithm-2 step the final loop is formed by linearity (into S), and its
+  // shifted solves skip
+  if (use_comb(p)) {
+    pd::launch_final_comb<T>(c, p->nf, p->nbar, p->lds, p->tau, p->aroot, p->shift, p->T, p->y, p->V, vbasis<T>(p),
+                             p->scal, p->flags, reinterpret_cast<const cpx<T> *>(p->lbuf),
+                             reinterpret_cast<const cpx<T> *>(p->hbuf), S, p->x);
+    a.skip_flag2 = p->flags + pd::F_COMB;
+  }
   pd::launch_pint<T>(c, p->geom, a);
   if (kind == 0) {
     CK(cudaMemcpyAsync(p->b0, p->b, sizeof(double) * p->nbar, cudaMemcpyDeviceToDevice, c.stream));
@@ -1595,6 +1616,8 @@ pd_status solve_refined(pd_plan *p, const double *G, double *U, pd_stats &s) {
     s.shifted_sweeps += p->loops ? p->loops : checks + 2;
     if (p->loops) s.sweep_krylov_iters[i] = 0;  // m = 1 only carries x_m = b
   }
+  s.final_by_linearity = f[pd::F_COMBCNT];
+  s.shifted_sweeps -= f[pd::F_COMBCNT];
   s.breakdown = f[pd::F_BREAK];
   s.beta = sc[pd::S_SWBETA + last];
   s.krylov_rel_resnorm = sc[pd::S_SWRES + last];
