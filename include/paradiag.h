@@ -210,16 +210,19 @@ typedef struct pd_desc {
   double eps_krylov_refine;  /* PD_MIXED: Algorithm 2 tolerance of the refinement sweeps (0 = 3e-3);
                                 a sweep's Algorithm 2 also leaves once its residual is below
                                 10 eps_krylov_refine and stops halving */
-  int32_t tune_final_loop;   /* single problems, loops = 0: when Algorithm 2 stops after one step,
+  int32_t tune_final_loop;   /* single problems, loops = 0: when Algorithm 2 stops at 1 <= m <= 16,
                                 form Algorithm 1's final loop by linearity instead of a third set
-                                of shifted solves: Y_k = L_k - phi_k v_1 + psi_k h_k, where
-                                L_k = A_k^{-1} G^_k is stored by the first loop, h_k = A_k^{-1} v_2
-                                by Algorithm 2's step, phi_k = alpha^{1/l} y_1 / (s_k + tau t_11)
-                                and psi_k = tau t_21 phi_k (eq. 10's relation tau K v_1 =
-                                tau (t_11 v_1 + t_21 v_2)), formed by one elementwise pass over
-                                the spectrum.  0 = on where it applies (costs one spectrum-sized
-                                buffer), -1 = always run the final loop's solves.  Not used with
-                                the binary32 path's FP64 zero-frequency lane. */
+                                of shifted solves: Y_k = L_k - V_m s_k + c_k h_k, where
+                                L_k = A_k^{-1} G^_k is stored by the first loop, h_k = A_k^{-1}
+                                v_{m+1} by Algorithm 2's last step, s_k = alpha^{1/l} S_k y_m with
+                                S_k = (sigma_k I + tau T_m)^{-1} from the last eq. (12) system
+                                (sigma_k = 1 - alpha^{1/l} pi_k the frequency's shift), and
+                                c_k = tau t_{m+1,m} (e_m^T s_k) (eq. 10's relation
+                                tau K V_m = V_m tau T_m + tau t_{m+1,m} v_{m+1} e_m^T), formed by
+                                one elementwise pass over the spectrum.  0 = on where it applies
+                                (costs one spectrum-sized buffer), -1 = always run the final
+                                loop's solves.  Not used with the binary32 path's FP64
+                                zero-frequency lane. */
 } pd_desc;
 
 /* Statistics of the last paradiag_solve / paradiag_solve_host. */

@@ -239,7 +239,8 @@ __device__ void capacitance_terms_body(int cta, int ncta, int nwk, int m, int nf
                                        const double *__restrict__ T, const double2 *__restrict__ shift,
                                        const double2 *__restrict__ wg, const double2 *__restrict__ gpart,
                                        int nblk, double *msys_part, double2 *srow, const double *scal,
-                                       const int *flags, int members, int mb, unsigned char *smraw, int bpm = 1) {
+                                       const int *flags, int members, int mb, unsigned char *smraw, int bpm = 1,
+                                       double2 *sinv = nullptr) {
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const size_t wb = k5a_warp_bytes(m);
   const bool busy = wid < nwk;
@@ -334,6 +335,9 @@ __device__ void capacitance_terms_body(int cta, int ncta, int nwk, int m, int nf
       }
       __syncwarp();
       warp_gj_inverse(H, X, fcol, m);
+      if (sinv && m <= kCombMaxM && lane < m)  // S_k = (s_k I + tau T_m)^{-1}, for the final loop
+        for (int q = 0; q < m; ++q)
+          sinv[((int64_t)k * m + q) * m + lane] = make_double2(X[q * m + lane].x, X[q * m + lane].y);
       const double2 w = wg[k];
       const cpx<double> wk = mk<double>(w.x, w.y);
       if (lane < m) {
@@ -364,7 +368,8 @@ __device__ void capacitance_terms_body(int cta, int ncta, int nwk, int m, int nf
 __global__ void __launch_bounds__(kK5Warps * 32) k_capacitance_terms(
     int nf, int maxit, double tau, const double *__restrict__ T, const double2 *__restrict__ shift,
     const double2 *__restrict__ wg, const double2 *__restrict__ gpart, int nblk, double *msys_part,
-    double2 *srow, const double *scal, int *flags, double2 *omega, double *y, int members, int bpm) {
+    double2 *srow, const double *scal, int *flags, double2 *omega, double *y, int members, int bpm,
+    double2 *sinv) {
   grid_dep_wait();
   extern __shared__ __align__(16) unsigned char smraw[];
   if (members) {  // member blockIdx.y of a batch: its own Algorithm-2 state (strided views)
@@ -382,7 +387,7 @@ __global__ void __launch_bounds__(kK5Warps * 32) k_capacitance_terms(
   }
   const int m = flags[F_M] + 1;
   capacitance_terms_body(blockIdx.x, gridDim.x, kK5Warps, m, nf, maxit, tau, T, shift, wg, gpart, nblk, msys_part,
-                         srow, scal, flags, members, (int)blockIdx.y, smraw, bpm);
+                         srow, scal, flags, members, (int)blockIdx.y, smraw, bpm, members ? nullptr : sinv);
   // The last CTA to finish (counted in flags[F_CAPCNT]; no CTA waits for another) sums the
   // partials and solves the m x m system, then resets the counter.
   __shared__ int last;
@@ -467,31 +472,32 @@ __global__ void k_xm(int n, const int *flags, const double *__restrict__ V, cons
 }
 
 // *dst = sum of part[0..nparts) (one warp, fixed order)
-// The final parallel-in-time loop by linearity, after an Algorithm-2 run of one step.
-// Arnoldi's relation (eq. 10) tau K v_1 = tau (t_11 v_1 + t_21 v_2) gives
-// A_k v_1 = (s_k + tau t_11) v_1 + tau t_21 v_2 for A_k = s_k I + tau K, hence
-// A_k^{-1} v_1 = (v_1 - tau t_21 h_k) / (s_k + tau t_11), with h_k = A_k^{-1} v_2 the
-// step's stored shifted solves.  The final loop Y_k = A_k^{-1}(G^_k - a x_1), x_1 = y_1 v_1
-// (a = alpha^{1/l}, 1 for Algorithm 1), is therefore
-//   Y_k = L_k - phi_k v_1 + psi_k h_k,  phi_k = a y_1 / (s_k + tau t_11),  psi_k = tau t_21 phi_k,
+// The final parallel-in-time loop by linearity.  Arnoldi's relation (eq. 10),
+// tau K V_m = V_m (tau T_m) + tau t_{m+1,m} v_{m+1} e_m^T, gives for A_k = s_k I + tau K
+//   A_k^{-1} V_m = [V_m - tau t_{m+1,m} h_k e_m^T] S_k,  S_k = (s_k I + tau T_m)^{-1},
+// with h_k = A_k^{-1} v_{m+1} the last step's stored shifted solves.  The final loop
+// Y_k = A_k^{-1}(G^_k - a x_m), x_m = V_m y_m (a = alpha^{1/l}, 1 for Algorithm 1), is then
+//   Y_k = L_k - V_m s_k + c_k h_k,  s_k = a S_k y_m,  c_k = tau t_{m+1,m} (e_m^T s_k),
 // with L_k = A_k^{-1} G^_k stored by the first loop: an elementwise pass over the spectrum
-// instead of a third set of shifted solves.  Mode (the same in every CTA): 2, or 1 without
-// the h_k term after a breakdown (t_21 = 0, no h_k formed), when Algorithm 2 stopped at
-// m = 1 and U_1 was not taken; else 0 and S is left to the final loop.  CTAs with
-// blockIdx.x = k < nf write row k of S (kCombCols columns each, blockIdx.y the chunk);
-// blockIdx.x = nf forms x = x_m in FP64 for any m (paradiag_last_vectors).
+// instead of a third set of shifted solves.  m = 1: s_k = a y_1 / (s_k + tau t_11); m > 1:
+// S_k as the last eq. (12) system stored it (sinv).  Mode (the same in every CTA): 2, or 1
+// without the h_k term after a breakdown (t_{m+1,m} = 0, no h_k formed), when Algorithm 2
+// stopped at 1 <= m <= maxm and U_1 was not taken; else 0 and S is left to the final loop.
+// CTAs with blockIdx.x = k < nf write row k of S (kCombCols columns each, blockIdx.y the
+// chunk); blockIdx.x = nf forms x = x_m in FP64 for any m (paradiag_last_vectors).
 constexpr int kCombCols = 1024;
 template <typename T>
 __global__ void __launch_bounds__(256) k_final_comb(int nf, int64_t n, int64_t lds, double tau, double aroot,
                                                     const double2 *__restrict__ shift, const double *__restrict__ Tm,
                                                     const double *__restrict__ y, const double *__restrict__ V,
-                                                    const T *__restrict__ v1, const double *__restrict__ scal,
-                                                    int *flags, const cpx<T> *__restrict__ L,
-                                                    const cpx<T> *__restrict__ H, cpx<T> *__restrict__ S, double *x) {
+                                                    const T *__restrict__ Vb, const double *__restrict__ scal,
+                                                    int *flags, const double2 *__restrict__ sinv, int maxm,
+                                                    const cpx<T> *__restrict__ L, const cpx<T> *__restrict__ H,
+                                                    cpx<T> *__restrict__ S, double *x) {
   grid_dep_wait();
-  __shared__ cpx<T> coef[2];
+  __shared__ cpx<T> sc[kCombMaxM + 1];  // s_k, then c_k
   const int m = flags[F_M];
-  const int mode = (m == 1 && !flags[F_EARLY] && !flags[F_TIMEOUT]) ? (flags[F_NOH] ? 1 : 2) : 0;
+  const int mode = (m >= 1 && m <= maxm && !flags[F_EARLY] && !flags[F_TIMEOUT]) ? (flags[F_NOH] ? 1 : 2) : 0;
   const int k = blockIdx.x;
   const int64_t cstride = (int64_t)gridDim.y * kCombCols;  // chunks beyond 65535 loop
   if (k == nf) {  // x_m in FP64
@@ -508,34 +514,65 @@ __global__ void __launch_bounds__(256) k_final_comb(int nf, int64_t n, int64_t l
     return;
   }
   if (!mode) return;
-  if (threadIdx.x == 0) {
-    const double2 sk = shift[k];
-    const cpx<double> r = recip(mk<double>(sk.x + tau * Tm[0], sk.y));
-    const double ay = aroot * y[0], tt = mode == 2 ? tau * scal[S_T] : 0.0;
-    coef[0] = mk<T>((T)(ay * r.x), (T)(ay * r.y));
-    coef[1] = mk<T>((T)(tt * ay * r.x), (T)(tt * ay * r.y));
+  __shared__ double2 sd[kCombMaxM];
+  const int i = threadIdx.x;
+  if (i < m) {  // s_k[i] = a (S_k y_m)_i
+    double2 v;
+    if (m == 1) {
+      const double2 sk = shift[k];
+      const cpx<double> r = recip(mk<double>(sk.x + tau * Tm[0], sk.y));
+      v = make_double2(r.x * y[0], r.y * y[0]);
+    } else {
+      const double2 *X = sinv + ((int64_t)k * m + i) * m;
+      v = make_double2(0.0, 0.0);
+      for (int q = 0; q < m; ++q) {
+        const double2 xq = X[q];
+        v.x += xq.x * y[q];
+        v.y += xq.y * y[q];
+      }
+    }
+    v.x *= aroot;
+    v.y *= aroot;
+    sd[i] = v;
+    sc[i] = mk<T>((T)v.x, (T)v.y);
   }
   __syncthreads();
-  const cpx<T> ph = coef[0], ps = coef[1];
+  if (i == 0) {
+    const double tt = mode == 2 ? tau * scal[S_T] : 0.0;
+    sc[m] = mk<T>((T)(tt * sd[m - 1].x), (T)(tt * sd[m - 1].y));
+  }
+  __syncthreads();
+  const cpx<T> ck = sc[m];
   constexpr int kE = kCombCols / 256;
   const int64_t o = (int64_t)k * lds;
   for (int64_t c0 = (int64_t)blockIdx.y * kCombCols; c0 < n; c0 += cstride) {
-    cpx<T> l[kE], h[kE];
-    T v[kE];
+    cpx<T> acc[kE], h[kE];
 #pragma unroll
     for (int e = 0; e < kE; ++e) {  // all loads in flight before any use
       const int64_t j = c0 + threadIdx.x + e * 256;
       const bool in = j < n;
-      l[e] = in ? L[o + j] : mk<T>(T(0), T(0));
+      acc[e] = in ? L[o + j] : mk<T>(T(0), T(0));
       h[e] = (in && mode == 2) ? H[o + j] : mk<T>(T(0), T(0));
-      v[e] = in ? v1[j] : T(0);
+    }
+    for (int q = 0; q < m; ++q) {  // - V_m s_k
+      T v[kE];
+#pragma unroll
+      for (int e = 0; e < kE; ++e) {
+        const int64_t j = c0 + threadIdx.x + e * 256;
+        v[e] = j < n ? Vb[(int64_t)q * n + j] : T(0);
+      }
+      const cpx<T> sq = sc[q];
+#pragma unroll
+      for (int e = 0; e < kE; ++e) {
+        acc[e].x -= sq.x * v[e];
+        acc[e].y -= sq.y * v[e];
+      }
     }
 #pragma unroll
     for (int e = 0; e < kE; ++e) {
       const int64_t j = c0 + threadIdx.x + e * 256;
       if (j < n)
-        S[o + j] = mk<T>(l[e].x - ph.x * v[e] + ps.x * h[e].x - ps.y * h[e].y,
-                         l[e].y - ph.y * v[e] + ps.x * h[e].y + ps.y * h[e].x);
+        S[o + j] = mk<T>(acc[e].x + ck.x * h[e].x - ck.y * h[e].y, acc[e].y + ck.x * h[e].y + ck.y * h[e].x);
     }
   }
 }
@@ -713,7 +750,7 @@ __global__ void __launch_bounds__(kBlasSingle, 1) k_step_tail(StepArgs<T> a) {
     const int nwall = (int)blockDim.x >> 5;
     const int nwk = m == 1 ? nwall : max(1, min(nwall, (int)(a.smem / k5a_warp_bytes(m))));
     capacitance_terms_body(blockIdx.x, gridDim.x, nwk, m, a.nf, a.maxit, a.tau, a.T, a.shift, a.wg, a.gpart, a.nblk,
-                           a.msys_part, a.srow, a.scal, flags, 0, 0, smraw);
+                           a.msys_part, a.srow, a.scal, flags, 0, 0, smraw, 1, a.sinv);
     if (last_cta_done(flags + F_CAPCNT)) {
       capacitance_solve_cta(a.nf, m, gridDim.x, a.msys_part, a.srow, a.omega, a.y, a.scal, smraw);
       if (threadIdx.x == 0) flags[F_CAPCNT] = 0;
@@ -879,13 +916,13 @@ void launch_arnoldi(Ctx &c, KrylovBufs &k) {
 
 void launch_capacitance(Ctx &c, KrylovBufs &k, int nf, double tau, const double2 *shift, const double2 *wg,
                         const double2 *gpart, int nblk, double *msys_part, int k5_grid, double2 *srow,
-                        double2 *omega, double *y, int members, int bpm) {
+                        double2 *omega, double *y, int members, int bpm, double2 *sinv) {
   const size_t smem = k5a_warp_bytes(k.maxit) * kK5Warps;  // sized for the largest m
   cudaFuncSetAttribute(k_capacitance_terms, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   c.launch("capacitance", (double)nf * nblk * 16, [&] {
     pdl_launch(c.pdl, k_capacitance_terms, dim3(k5_grid, members ? members : 1), dim3(kK5Warps * 32), smem,
                c.stream, nf, k.maxit, tau, (const double *)k.T, shift, wg, gpart, nblk, msys_part, srow,
-               members ? k.mscal : k.scal, members ? k.mflags : k.flags, omega, y, members, bpm);
+               members ? k.mscal : k.scal, members ? k.mflags : k.flags, omega, y, members, bpm, sinv);
   });
 }
 
@@ -976,23 +1013,25 @@ void launch_xm(Ctx &c, KrylovBufs &k, const double *y, double *x, float *xf) {
 
 template <typename T>
 void launch_final_comb(Ctx &c, int nf, int64_t n, int64_t lds, double tau, double aroot, const double2 *shift,
-                       const double *Tm, const double *y, const double *V, const T *v1, const double *scal,
-                       int *flags, const cpx<T> *L, const cpx<T> *H, cpx<T> *S, double *x) {
+                       const double *Tm, const double *y, const double *V, const T *Vb, const double *scal,
+                       int *flags, const double2 *sinv, int maxm, const cpx<T> *L, const cpx<T> *H, cpx<T> *S,
+                       double *x) {
   const dim3 grid((unsigned)(nf + 1), (unsigned)std::min<int64_t>((n + kCombCols - 1) / kCombCols, 65535));
+  const int mm = std::min(maxm, kCombMaxM);
   // algorithmic bytes: L and h_k read, S written (when the final loop is formed here)
   c.launch("final_comb", (double)nf * n * 3.0 * sizeof(cpx<T>), [&] {
-    pdl_launch(c.pdl, k_final_comb<T>, grid, dim3(256), 0, c.stream, nf, n, lds, tau, aroot, shift, Tm, y, V, v1,
-               scal, flags, L, H, S, x);
+    pdl_launch(c.pdl, k_final_comb<T>, grid, dim3(256), 0, c.stream, nf, n, lds, tau, aroot, shift, Tm, y, V, Vb,
+               scal, flags, sinv, mm, L, H, S, x);
   });
 }
 template void launch_final_comb<float>(Ctx &, int, int64_t, int64_t, double, double, const double2 *,
                                        const double *, const double *, const double *, const float *,
-                                       const double *, int *, const cpx<float> *, const cpx<float> *,
-                                       cpx<float> *, double *);
+                                       const double *, int *, const double2 *, int, const cpx<float> *,
+                                       const cpx<float> *, cpx<float> *, double *);
 template void launch_final_comb<double>(Ctx &, int, int64_t, int64_t, double, double, const double2 *,
                                         const double *, const double *, const double *, const double *,
-                                        const double *, int *, const cpx<double> *, const cpx<double> *,
-                                        cpx<double> *, double *);
+                                        const double *, int *, const double2 *, int, const cpx<double> *,
+                                        const cpx<double> *, cpx<double> *, double *);
 
 void launch_sumsq(Ctx &c, const double *part, int nparts, double *dst) {
   c.launch("krylov_sumsq", 0.0, [&] { pdl_launch(c.pdl, k_sumsq_final, dim3(1), dim3(32), 0, c.stream, part, nparts, dst); });

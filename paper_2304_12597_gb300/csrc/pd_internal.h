@@ -339,7 +339,8 @@ void launch_arnoldi(Ctx &c, KrylovBufs &k);
 int krylov_cluster_size(int want);
 void launch_capacitance(Ctx &c, KrylovBufs &k, int nf, double tau, const double2 *shift,
                         const double2 *wg, const double2 *gpart, int nblk, double *msys_part,
-                        int k5_grid, double2 *srow, double2 *omega, double *y, int members = 0, int bpm = 1);
+                        int k5_grid, double2 *srow, double2 *omega, double *y, int members = 0, int bpm = 1,
+                        double2 *sinv = nullptr);
 // Batched plans, one Algorithm 2 per member (one CTA each; krylov_members.cu): the
 // start (beta_b, v_1), an Arnoldi step, and eq. (13) with the per-member decision; the
 // last member of the start and of eq. (13) sets the batch's control block and the
@@ -372,6 +373,7 @@ struct StepArgs {
   const double2 *shift, *wg, *gpart;
   double *msys_part, *y;
   double2 *srow, *omega;
+  double2 *sinv;  // (nf, m, m) S_k of the step, or null (the final loop by linearity)
   // z from the stored h_k (the zero frequency from the FP64 lane h0 when it is on)
   const cpx<TC> *H;
   int64_t ldh;
@@ -412,15 +414,19 @@ void launch_early_finish(Ctx &c, double *scal, int *flags, int use_handle, cudaG
 void launch_project_resnorm(Ctx &c, KrylovBufs &k, const double *z, double tau, const KrylovCtl &kc,
                             int use_handle, cudaGraphConditionalHandle h);
 void launch_xm(Ctx &c, KrylovBufs &k, const double *y, double *x, float *xf);
-// Algorithm 1's final loop by linearity (k_final_comb): when Algorithm 2 stopped after one
-// step (F_M == 1) and U_1 was not taken, flags[F_COMB] != 0 and the spectrum S becomes
-// Y_k = L_k - phi_k v_1 + psi_k h_k (L from the first loop, h_k in H, both (nf, lds)), so the
-// final loop's solves are skipped (PintArgs.skip_flag2); else flags[F_COMB] = 0 and S is left
-// for them.  Also x = x_m = sum_{q<m} y_q V[q] in FP64 (length n) for any m.
+// Algorithm 1's final loop by linearity (k_final_comb): when Algorithm 2 stopped at
+// 1 <= m <= maxm and U_1 was not taken, flags[F_COMB] != 0 and the spectrum S becomes
+// Y_k = L_k - V_m s_k + c_k h_k, s_k = a S_k y_m, c_k = tau t_{m+1,m} (e_m^T s_k) (L from the
+// first loop, h_k in H, both (nf, lds); S_k in sinv, (nf, m, m), for m > 1), so the final
+// loop's solves are skipped (PintArgs.skip_flag2); else flags[F_COMB] = 0 and S is left for
+// them.  Vb: the basis in the compute type (rows of n).  Also x = x_m = sum_{q<m} y_q V[q] in
+// FP64 (length n) for any m.
+constexpr int kCombMaxM = 16;  // largest m whose final loop is formed by linearity
 template <typename T>
 void launch_final_comb(Ctx &c, int nf, int64_t n, int64_t lds, double tau, double aroot, const double2 *shift,
-                       const double *Tm, const double *y, const double *V, const T *v1, const double *scal,
-                       int *flags, const cpx<T> *L, const cpx<T> *H, cpx<T> *S, double *x);
+                       const double *Tm, const double *y, const double *V, const T *Vb, const double *scal,
+                       int *flags, const double2 *sinv, int maxm, const cpx<T> *L, const cpx<T> *H, cpx<T> *S,
+                       double *x);
 
 
 void launch_solve_reset(Ctx &c, double *scal, int *flags);

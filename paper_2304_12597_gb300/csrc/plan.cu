@@ -172,6 +172,7 @@ struct pd_plan {
   // loop stores L_k in lbuf
   bool comb = false;
   void *lbuf = nullptr;
+  double2 *sinv = nullptr;  // S_k of the last eq. (12) system (nf, m, m), m <= maxit
   int max_refine = 6;
   double refine_tol = 1e-13;
   int host_io = 0;
@@ -656,8 +657,11 @@ size_t layout(pd_plan *p, unsigned char *base) {
   }
   p->spec = mixed ? (void *)A.take<cpx<float>>((size_t)nf * p->lds) : (void *)A.take<cpx<double>>((size_t)nf * p->lds);
   p->hbuf = mixed ? (void *)A.take<cpx<float>>((size_t)nf * p->lds) : (void *)A.take<cpx<double>>((size_t)nf * p->lds);
-  if (p->comb)
+  if (p->comb) {
     p->lbuf = mixed ? (void *)A.take<cpx<float>>((size_t)nf * p->lds) : (void *)A.take<cpx<double>>((size_t)nf * p->lds);
+    const int mc = std::min(mx, pd::kCombMaxM);
+    p->sinv = A.take<double2>((size_t)nf * mc * mc);
+  }
   if (p->factored)
     p->fac = mixed ? (void *)A.take<cpx<float>>(pd::pint_factor_elems(p->geom))
                    : (void *)A.take<cpx<double>>(pd::pint_factor_elems(p->geom));
@@ -1268,6 +1272,7 @@ pd::StepArgs<T> step_args(pd_plan *p, int kind, int use_handle, cudaGraphConditi
   a.y = p->y;
   a.srow = p->srow;
   a.omega = p->omega;
+  a.sinv = use_comb(p) ? p->sinv : nullptr;
   a.H = reinterpret_cast<const cpx<T> *>(p->hbuf);
   a.ldh = p->lds;
   a.h0 = lane_h0<T>(p);
@@ -1315,7 +1320,7 @@ pd_status emit_iter(pd_plan *p, int kind, int use_handle, cudaGraphConditionalHa
   const double *h0 = lane_h0<T>(p);
   pd::launch_capacitance(c, kb, p->nf, p->tau, p->shift, p->wga, p->gpart, p->nblk, p->msys_part,
                          kb.members ? p->k5_grid_members : p->k5_grid,
-                         p->srow, p->omega, p->y, kb.members, (int)p->nym);
+                         p->srow, p->omega, p->y, kb.members, (int)p->nym, use_comb(p) ? p->sinv : nullptr);
   // z = sum_i gamma_i h_i (e_m^T S_i y_m) from the stored h_i, then eq. (13)
   if (kb.members) {
     pd::launch_zsum<T>(c, p->nf, p->nbar, H, p->lds, p->omega, p->z, noh, nullptr, kb.mlen, h0);
@@ -1359,8 +1364,9 @@ pd_status emit_post(pd_plan *p, int kind, double *U, int use_handle, cudaGraphCo
   // shifted solves skip
   if (use_comb(p)) {
     pd::launch_final_comb<T>(c, p->nf, p->nbar, p->lds, p->tau, p->aroot, p->shift, p->T, p->y, p->V, vbasis<T>(p),
-                             p->scal, p->flags, reinterpret_cast<const cpx<T> *>(p->lbuf),
-                             reinterpret_cast<const cpx<T> *>(p->hbuf), S, p->x);
+                             p->scal, p->flags, p->sinv, std::min(p->maxit, pd::kCombMaxM),
+                             reinterpret_cast<const cpx<T> *>(p->lbuf), reinterpret_cast<const cpx<T> *>(p->hbuf), S,
+                             p->x);
     a.skip_flag2 = p->flags + pd::F_COMB;
   }
   pd::launch_pint<T>(c, p->geom, a);
