@@ -621,10 +621,11 @@ __global__ void __launch_bounds__(256) k_fft_c2r(const cpx<T> *__restrict__ S, i
 // col) of slab s (time t = s / batch, problem b = s % batch) is
 // r = G_t + u_{t-1} - [(I + tau T_x) u_t + tau T_y u_t] at row b nym + y of the stacked grid
 // (ny = batch nym rows, x-coefficients of problem b), times 2^mex[b] for batches: five
-// FMAs in FP64 per element after G_t + u_{t-1}, formed while the DST loads its tile.
+// FMAs in FP64 per element after G_t + u_{t-1} (the diagonal 1 + tau (d_x + d_y) comes
+// precombined per grid point in rdd), formed while the DST loads its tile.
 struct ResIn {
   const double *G, *U;
-  const double *rxl, *rxd, *rxu, *ryl, *ryd, *ryu;
+  const double *rxl, *rdd, *rxu, *ryl, *ryu;
   int ny, nym, batch;
   const int *mex;
 };
@@ -674,7 +675,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_dst_y(const Tin
           const double *u = rin.U + tt * nb;
           r = rin.G[tt * nb + j];
           if (tt > 0) r += u[j - nb];
-          r = fma(-(rin.rxd[cx] + rin.ryd[iy]), u[j], r);
+          r = fma(-rin.rdd[j], u[j], r);
           if (col > 0) r = fma(-rin.rxl[cx], u[j - 1], r);
           if (col + 1 < nx) r = fma(-rin.rxu[cx], u[j + 1], r);
           if (iy > 0) r = fma(-rin.ryl[iy], u[j - nx], r);
@@ -950,9 +951,9 @@ void launch_dst_y(Ctx &c, const Tin *X, Tout *Y, int64_t nt, int64_t ny, int64_t
 
 template <typename T>
 void launch_dst_y_residual(Ctx &c, const double *G, const double *U, T *Y, int64_t nt, int batch, int64_t nym,
-                           int64_t nx, const double *rxl, const double *rxd, const double *rxu, const double *ryl,
-                           const double *ryd, const double *ryu, const int *mex, const cpx<T> *tw) {
-  ResIn rin{G, U, rxl, rxd, rxu, ryl, ryd, ryu, (int)(nym * batch), (int)nym, batch, mex};
+                           int64_t nx, const double *rxl, const double *rdd, const double *rxu, const double *ryl,
+                           const double *ryu, const int *mex, const cpx<T> *tw) {
+  ResIn rin{G, U, rxl, rdd, rxu, ryl, ryu, (int)(nym * batch), (int)nym, batch, mex};
   // G and U read once (neighbours from the caches), the binary32 / FP64 transform written
   const double bytes = (double)nt * batch * nym * nx * (16.0 + sizeof(T));
   dst_launch<double, T, T, true>(c, (const double *)nullptr, Y, nt * batch, nym, nx, tw, 0, nullptr, rin,
@@ -987,9 +988,9 @@ template void launch_dst_y<float, double, float>(Ctx &, const float *, double *,
                                                  const cpx<float> *, int, const int *);
 template void launch_dst_y_residual<float>(Ctx &, const double *, const double *, float *, int64_t, int, int64_t,
                                            int64_t, const double *, const double *, const double *, const double *,
-                                           const double *, const double *, const int *, const cpx<float> *);
+                                           const double *, const int *, const cpx<float> *);
 template void launch_dst_y_residual<double>(Ctx &, const double *, const double *, double *, int64_t, int, int64_t,
                                             int64_t, const double *, const double *, const double *, const double *,
-                                            const double *, const double *, const int *, const cpx<double> *);
+                                            const double *, const int *, const cpx<double> *);
 
 }  // namespace pd

@@ -196,8 +196,8 @@ void launch_dst_y(Ctx &c, const Tin *X, Tout *Y, int64_t nt, int64_t ny, int64_t
 // ry = (tau lo_y, tau diag_y, tau up_y).
 template <typename T>
 void launch_dst_y_residual(Ctx &c, const double *G, const double *U, T *Y, int64_t nt, int batch, int64_t nym,
-                           int64_t nx, const double *rxl, const double *rxd, const double *rxu, const double *ryl,
-                           const double *ryd, const double *ryu, const int *mex, const cpx<T> *tw);
+                           int64_t nx, const double *rxl, const double *rdd, const double *rxu, const double *ryl,
+                           const double *ryu, const int *mex, const cpx<T> *tw);
 
 // ---- shifted tridiagonal solves (pint.cu) ------------------------------------------
 struct PintGeom {
@@ -400,8 +400,8 @@ int step_tail_max_grid(int nv, int E, int elem_bytes, size_t smem);
 // eps ||U_1||_F (the residual of the original system, as in the refinement).  If it passes,
 // flags[F_EARLY] is set, Algorithm 2 does not run (flags[F_KSTOP], F_M = 0, the WHILE
 // conditional set to 0) and the final loop and inverse transforms are skipped: U = U_1.
-// part: 2 * (4 * SMs) doubles of scratch.  Coefficients as launch_dst_y_residual (1D:
-// ryl == null, ny = 1).
+// part: 2 * (4 * SMs) doubles of scratch.  Coefficients: (tau lo_x, 1 + tau d_x, tau up_x)
+// and (tau lo_y, tau d_y, tau up_y) (1D: ryl == null, ny = 1).
 void launch_early_check(Ctx &c, const double *G, const double *U, int64_t nt, int64_t ny, int64_t nx,
                         const double *rxl, const double *rxd, const double *rxu, const double *ryl,
                         const double *ryd, const double *ryu, int64_t nym, double eps, double *part, double *scal,

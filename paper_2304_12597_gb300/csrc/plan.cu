@@ -234,6 +234,7 @@ struct pd_plan {
   double *xlo = nullptr, *xdiag = nullptr, *xup = nullptr, *ylo = nullptr, *ydiag = nullptr, *yup = nullptr;
   // residual coefficients: (tau lo_x, 1 + tau diag_x, tau up_x) and (tau lo_y, tau diag_y, tau up_y)
   double *rxl = nullptr, *rxd = nullptr, *rxu = nullptr, *ryl = nullptr, *ryd = nullptr, *ryu = nullptr;
+  double *rdd = nullptr;  // 2D: rxd + ryd at every point of the grid (n_bar), one FP64 add less per point
   cpx<double> *tw_d = nullptr, *twy_d = nullptr;
   cpx<float> *tw_f = nullptr, *twy_f = nullptr;
   void *spec = nullptr;
@@ -646,6 +647,7 @@ size_t layout(pd_plan *p, unsigned char *base) {
     p->yup = A.take<double>(p->ny);
     p->ryl = A.take<double>(p->ny);
     p->ryd = A.take<double>(p->ny);
+    p->rdd = A.take<double>(p->nbar);
     p->ryu = A.take<double>(p->ny);
   }
   const int ntw = std::max<int>(1, (int)(nt / 2));
@@ -938,7 +940,12 @@ pd_status upload_operator(pd_plan *p, const pd_desc *desc) {
       (st = upload(p->rxl, rxl.data(), p->nrx, s)) || (st = upload(p->rxd, rxd.data(), p->nrx, s)) ||
       (st = upload(p->rxu, rxu.data(), p->nrx, s)))
     return st;
-  if (p->dim == 2 && ((st = upload(p->ryl, ryl.data(), p->ny, s)) || (st = upload(p->ryd, ryd.data(), p->ny, s)) ||
+  std::vector<double> rdd(p->dim == 2 ? p->nbar : 0);
+  if (p->dim == 2)  // row iy of the stacked grid belongs to problem iy / nym (its x-coefficients)
+    for (int64_t iy = 0; iy < p->ny; ++iy)
+      for (int64_t x = 0; x < p->nx; ++x) rdd[iy * p->nx + x] = rxd[(iy / p->nym) * p->nx + x] + ryd[iy];
+  if (p->dim == 2 && ((st = upload(p->rdd, rdd.data(), p->nbar, s)) ||
+                      (st = upload(p->ryl, ryl.data(), p->ny, s)) || (st = upload(p->ryd, ryd.data(), p->ny, s)) ||
                       (st = upload(p->ryu, ryu.data(), p->ny, s)) || (st = upload(p->ylo, h.ylo.data(), p->ny, s)) ||
                       (st = upload(p->ydiag, h.ydiag.data(), p->ny, s)) || (st = upload(p->yup, h.yup.data(), p->ny, s))))
     return st;
@@ -1183,8 +1190,8 @@ pd_status emit_pre(pd_plan *p, int kind, const double *G, double *U, int use_han
                                      row_scale<T>(p, false), p->batch > 1 ? p->mex : nullptr, (int)p->nxm, rnp);
     } else {
       // the FP64 residual is formed while the DST along y loads its tiles
-      pd::launch_dst_y_residual<T>(c, G, U, tmp, p->nt, p->batch, p->nym, p->nx, p->rxl, p->rxd, p->rxu, p->ryl,
-                                   p->ryd, p->ryu, p->batch > 1 ? p->mex : nullptr, dst_tw<T>(p));
+      pd::launch_dst_y_residual<T>(c, G, U, tmp, p->nt, p->batch, p->nym, p->nx, p->rxl, p->rdd, p->rxu, p->ryl,
+                                   p->ryu, p->batch > 1 ? p->mex : nullptr, dst_tw<T>(p));
       pd::launch_fft_r2c<T, T>(c, tmp, p->nbar, p->nbar, nt, time_tw<T>(p), S, p->lds, row_scale<T>(p, false), rnp);
     }
   }
