@@ -286,6 +286,27 @@ pd_status paradiag_plan(const pd_desc *desc, void *workspace, size_t workspace_b
  * PD_ERR_NOT_CONVERGED: limits reached; U_dev holds the last iterate. */
 pd_status paradiag_solve(pd_plan *plan, const double *G_dev, double *U_dev, pd_stats *stats);
 
+/* Batched plans: advance the solve of every problem by up to `steps` refinement sweeps
+ * (solves of eq. 2's FP64 residual by Algorithm 1, as paradiag_solve's sweeps), so that
+ * problems can join a batch while the others are being solved: the continuous batching
+ * of a solve service.  Not part of the paper.
+ * G_dev: device, (nt, n_bar), each problem's right-hand side in its slot (zero slots are
+ * unused).  U_dev: device, (nt, n_bar), the current iterates, updated in place.
+ * join (host, length batch): nonzero for a problem that starts with this call; its U slot
+ * is set to zero and its refinement state reset, so its first sweep is its first solve
+ * (with the refinement sweeps' Algorithm-2 tolerance).  The other problems continue from
+ * U_dev and their own count of solves.
+ * state (host, length batch, out): 1 = the problem met refine_tol (its slot of U_dev is
+ * its solution; later calls keep refining it while it stays), 2 = it took max_refine + 1
+ * solves without meeting it, 0 = still running (or an unused slot).
+ * Each problem decides convergence by the same rules as in paradiag_solve, counted from
+ * its own first solve.  The sweeps run as host-driven loops on the plan's stream; the call
+ * returns after synchronising with it.  stats: this call's sweeps.
+ * Errors: PD_ERR_INVALID_ARG (not a batched plan, steps outside [1, 64], NULL or aliasing
+ * arguments), PD_ERR_UNSUPPORTED (fixed-loop variants, mass matrices), PD_ERR_NONFINITE. */
+pd_status paradiag_batch_advance(pd_plan *plan, const double *G_dev, double *U_dev, const int32_t *join,
+                                 int32_t steps, int32_t *state, pd_stats *stats);
+
 /* Same as paradiag_solve with G and U in host memory (pinned memory gives the best
  * copy rate).  The host-to-device copy of G and the device-to-host copy of U are
  * part of the call.  Requires desc->host_io != 0 at plan time. */

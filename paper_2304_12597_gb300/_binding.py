@@ -139,6 +139,9 @@ SIGNATURES = {
     "paradiag_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(PdStats)]),
     "paradiag_solve_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.POINTER(PdStats)]),
+    "paradiag_batch_advance": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                              ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
+                                              ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(PdStats)]),
     "paradiag_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "paradiag_set_operator": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(PdDesc)]),
     "paradiag_last_error": (ctypes.c_char_p, []),
@@ -214,6 +217,18 @@ def paradiag_solve_host(plan: int, G_host_ptr: int, U_host_ptr: int, allow_not_c
     allow = (5,) if allow_not_converged else ()
     check("paradiag_solve_host", load().paradiag_solve_host(plan, G_host_ptr, U_host_ptr, ctypes.byref(st)), allow)
     return st
+
+
+def paradiag_batch_advance(plan: int, G_ptr: int, U_ptr: int, join, steps: int):
+    """Advance a batched solve by up to `steps` refinement sweeps; join[b] != 0 starts
+    problem b.  Returns (state per problem: 1 converged, 2 gave up, 0 running; PdStats)."""
+    n = len(join)
+    jarr = (ctypes.c_int32 * n)(*[1 if j else 0 for j in join])
+    sarr = (ctypes.c_int32 * n)()
+    st = PdStats()
+    check("paradiag_batch_advance", load().paradiag_batch_advance(plan, G_ptr, U_ptr, jarr, int(steps), sarr,
+                                                                  ctypes.byref(st)))
+    return [int(v) for v in sarr], st
 
 
 def paradiag_destroy(plan: int) -> None:

@@ -92,6 +92,38 @@ void launch_batch_normalize(Ctx &c, const double *G, double *Gs, int64_t nt, int
                                   (const int *)nullptr, (const int *)nullptr); });
 }
 
+// A problem joining a running batch (join[b]): its U slot starts at zero and its refinement
+// state restarts; so does every unused slot (zero[b]: an all-zero right-hand side, whose U
+// may hold anything); the other slots' U goes back into the solve's units, U * 2^ex[b]
+// (exact).
+__global__ void __launch_bounds__(256) k_member_join(double *U, int ld, int nxm, int batch, const int *__restrict__ ex,
+                                                     const int *__restrict__ join, const int *__restrict__ zero,
+                                                     int *msw, double *prev, double *ref2, int *mex, int *mconv) {
+  grid_dep_wait();
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (blockIdx.y == 0 && j < batch && (join[j] || zero[j])) {  // (an unused slot's mex may be stale)
+    msw[j] = 0;
+    prev[j] = 0.0;
+    ref2[j] = 0.0;
+    mex[j] = 0;
+    mconv[j] = 0;
+  }
+  if (j >= ld) return;
+  const int b = j / nxm;
+  const int64_t i = (int64_t)blockIdx.y * ld + j;
+  U[i] = (join[b] || zero[b]) ? 0.0 : pow2_scale(U[i], ex[b]);
+}
+
+void launch_member_join(Ctx &c, double *U, int64_t nt, int batch, int nxm, const int *ex, const int *join,
+                        const int *zero, int *msw, double *prev, double *ref2, int *mex, int *mconv) {
+  const int64_t ld = (int64_t)batch * nxm;
+  const dim3 grid((unsigned)((std::max<int64_t>(ld, batch) + 255) / 256), (unsigned)nt);
+  c.launch("batch_scale", (double)nt * ld * 16.0, [&] {
+    pdl_launch(c.pdl, k_member_join, grid, dim3(256), 0, c.stream, U, (int)ld, nxm, batch, ex, join, zero, msw, prev,
+               ref2, mex, mconv);
+  });
+}
+
 void launch_batch_unscale(Ctx &c, double *U, int64_t nt, int batch, int nxm, const int *ex, const int *nxb,
                           const int *zero) {
   const int64_t ld = (int64_t)batch * nxm;

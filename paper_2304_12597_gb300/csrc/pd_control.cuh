@@ -132,24 +132,30 @@ __device__ __forceinline__ void refine_decide_members(double *scal, int *flags, 
       ref2[b] = 0.0;
       prev[b] = 0.0;
       mex[b] = 0;
+      if (r.msw) r.msw[b] = 0;
+      if (r.mconv) r.mconv[b] = 0;
       continue;
     }
+    const int sb = r.msw ? r.msw[b] : s;  // this problem's solves before this one
     const double d = d2[b];
     d2sum += d;
     if (!isfinite(d)) nonfinite = true;
-    if (s == 0) ref2[b] = d;
+    if (sb == 0) ref2[b] = d;
     const double rf = ref2[b];
     const double rel = rf > 0.0 ? sqrt(d / rf) : 0.0;
+    bool conv_b = true;
     if (rf > 0.0) {
       relmax = fmax(relmax, rel);
       const double rho = prev[b] > 0.0 ? rel / prev[b] : 0.0;
-      const bool floor_b = s > 1 && rho > 0.5;  // no longer contracting: rounding floor
-      const bool conv_b =
-          s > 0 && ((s >= 2 && rho * rel <= r.refine_tol && rel <= 1e-7) || rel <= 1e-15 || (floor_b && rel <= 1e-10));
+      const bool floor_b = sb > 1 && rho > 0.5;  // no longer contracting: rounding floor
+      conv_b = sb > 0 &&
+               ((sb >= 2 && rho * rel <= r.refine_tol && rel <= 1e-7) || rel <= 1e-15 || (floor_b && rel <= 1e-10));
       if (!conv_b) all_conv = false;
       if (!conv_b && floor_b) any_stall = true;  // stuck above the floor
       if (rel > 1e-10) all_floor = false;
     }
+    if (r.msw) r.msw[b] = sb + 1;
+    if (r.mconv) r.mconv[b] = conv_b ? 1 : ((r.member_solves > 0 && sb + 1 >= r.member_solves) ? 2 : 0);
     prev[b] = rel;
     int e = 0;
     if (d > 0.0 && isfinite(d)) {

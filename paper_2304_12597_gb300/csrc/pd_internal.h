@@ -141,6 +141,12 @@ struct RefineCtl {
   double eps_first, eps_refine;  // Algorithm-2 tolerances of the first solve / sweeps
   double refine_tol;
   int max_refine;
+  // batched plans: each problem's own count of solves (msw[b]; its refinement rules count
+  // from there, so a problem can join a running batch with msw[b] = 0), and its state after
+  // this decision (mconv[b]: 1 converged, 2 gave up after member_solves solves, 0 running)
+  int *msw;
+  int *mconv;
+  int member_solves;  // 0 = no per-problem limit (the plan's max_refine bounds the batch)
 };
 // ---- time FFT / DST (fft.cu) ----------------------------------------------------
 // Forward DFT along time of real (n, ncols) rows -> half spectrum (n/2+1, ncols).
@@ -288,6 +294,12 @@ void launch_zsum(Ctx &c, int nf, int64_t n, const cpx<T> *H, int64_t ldh, const 
 // column of an all-zero problem, set to zero.
 void launch_batch_normalize(Ctx &c, const double *G, double *Gs, int64_t nt, int batch, int nxm, int nc,
                             double *part, int *ex, int *zero);
+// Problems joining a running batched solve (paradiag_batch_advance): for join[b] != 0 the
+// slot's U is zeroed and its refinement state reset (msw, mprev, mref2, mex, mconv); unused
+// slots (zero[b]) start from U = 0 as well; the other slots' U is scaled by 2^ex[b] into
+// the solve's units (exact).
+void launch_member_join(Ctx &c, double *U, int64_t nt, int batch, int nxm, const int *ex, const int *join,
+                        const int *zero, int *msw, double *prev, double *ref2, int *mex, int *mconv);
 void launch_batch_unscale(Ctx &c, double *U, int64_t nt, int batch, int nxm, const int *ex, const int *nxb,
                           const int *zero);
 // out[t][j] = in[t][j] * s[j] over nt rows of nb columns (in place allowed; batch.cu)

@@ -197,6 +197,8 @@ struct pd_plan {
   double *colsum = nullptr;     // per-column ||delta||^2 of the last solve
   double *md2 = nullptr, *mref2 = nullptr, *mprev = nullptr;  // per-problem refinement state
   int *mex = nullptr;  // per-problem residual scaling 2^mex of the next refinement sweep
+  int *msw = nullptr, *mconv = nullptr, *mjoin = nullptr;  // per-problem solves, state, join flags
+  int member_solves = 0;  // paradiag_batch_advance: solves a problem may take (0 = no limit)
   int members = 0;     // batched plans: one Algorithm 2 per problem (0 = one for the plan)
   bool mass = false;   // diagonal mass matrix: solve for w = M^{1/2} u with K' = M^{-1/2} K M^{-1/2}
   double *msc = nullptr;  // M^{-1/2} (n_bar)
@@ -716,6 +718,9 @@ size_t layout(pd_plan *p, unsigned char *base) {
     p->mref2 = A.take<double>(p->batch);
     p->mprev = A.take<double>(p->batch);
     p->mex = A.take<int>(p->batch);
+    p->msw = A.take<int>(p->batch);
+    p->mconv = A.take<int>(p->batch);
+    p->mjoin = A.take<int>(p->batch);
   }
   if (p->host_io) {
     p->G_stage = A.take<double>((size_t)nt * nbar);
@@ -1151,6 +1156,9 @@ pd::RefineCtl refine_ctl(pd_plan *p) {
   r.eps_refine = p->refined64 ? std::max(p->eps, 1e-8) : std::max(p->eps, fp64 ? 1e-8 : p->eps_refine);
   r.refine_tol = p->refine_tol;
   r.max_refine = p->max_refine;
+  r.msw = p->batch > 1 ? p->msw : nullptr;
+  r.mconv = p->batch > 1 ? p->mconv : nullptr;
+  r.member_solves = p->member_solves;
   return r;
 }
 
@@ -1440,6 +1448,28 @@ pd_status solve_hostloop(pd_plan *p, const double *G, double *U) {
       if (p->h_flags[pd::F_TIMEOUT]) return timeout_status(p);
     }
     if ((st = emit_post<T>(p, kind, U, 0, 0)) != PD_OK) return st;
+    if ((st = sync_read(p)) != PD_OK) return st;
+    if (p->h_flags[pd::F_RSTOP]) break;
+  }
+  return ctx_status(p);
+}
+
+// Refinement sweeps only, on the U given (paradiag_batch_advance): the same kernels as the
+// host-driven loop, every solve a sweep on the FP64 residual, until the decision stops.
+template <typename T>
+pd_status solve_continue(pd_plan *p, const double *G, double *U) {
+  pd::Ctx &c = p->ctx;
+  pd_status st;
+  pd::launch_solve_reset(c, p->scal, p->flags);
+  for (;;) {
+    if ((st = emit_pre<T>(p, 1, G, U, 0, 0)) != PD_OK) return st;
+    if ((st = sync_read(p)) != PD_OK) return st;
+    while (!p->h_flags[pd::F_KSTOP]) {
+      if ((st = emit_iter<T>(p, 1, 0, 0)) != PD_OK) return st;
+      if ((st = sync_read(p)) != PD_OK) return st;
+      if (p->h_flags[pd::F_TIMEOUT]) return timeout_status(p);
+    }
+    if ((st = emit_post<T>(p, 1, U, 0, 0)) != PD_OK) return st;
     if ((st = sync_read(p)) != PD_OK) return st;
     if (p->h_flags[pd::F_RSTOP]) break;
   }
@@ -1851,6 +1881,7 @@ pd_status paradiag_solve(pd_plan *p, const double *G, double *U, pd_stats *stats
   if (p->batch > 1) {  // every problem of the batch scaled to unit norm (exactly, by 2^k)
     pd::launch_batch_normalize(p->ctx, Gin, p->Gs, p->nt, p->batch, (int)p->nxm, p->bnc, p->bpart, p->bex, p->bzero);
     Gin = p->Gs;
+    CK(cudaMemsetAsync(p->msw, 0, sizeof(int) * p->batch, p->ctx.stream));  // every problem starts here
   }
   st = p->precision == PD_FP64 ? solve_refined<double>(p, Gin, U, s) : solve_refined<float>(p, Gin, U, s);
   if (st == PD_ERR_CUDA) return st;
@@ -1867,6 +1898,56 @@ pd_status paradiag_solve(pd_plan *p, const double *G, double *U, pd_stats *stats
   if (stats) *stats = s;
   pd_status cs = ctx_status(p);
   return cs != PD_OK ? cs : st;
+}
+
+pd_status paradiag_batch_advance(pd_plan *p, const double *G, double *U, const int32_t *join, int32_t steps,
+                                 int32_t *state, pd_stats *stats) {
+  pd_status st = check_plan(p);
+  if (st != PD_OK) return st;
+  if (p->batch < 2) return fail(PD_ERR_INVALID_ARG, "paradiag_batch_advance needs a batched plan");
+  if (p->loops || p->mass)
+    return fail(PD_ERR_UNSUPPORTED, "paradiag_batch_advance: no fixed-loop variants or mass matrices");
+  if (!G || !U || !join || !state) return fail(PD_ERR_INVALID_ARG, "G, U, join and state must not be NULL");
+  if (((uintptr_t)G & 7) || ((uintptr_t)U & 7)) return fail(PD_ERR_INVALID_ARG, "G and U must be 8-byte aligned");
+  if (steps < 1 || steps > 64) return fail(PD_ERR_INVALID_ARG, "steps must be in [1, 64] (got %d)", steps);
+  const size_t bytes = (size_t)p->nt * p->nbar * sizeof(double);
+  const char *g0 = reinterpret_cast<const char *>(G), *u0 = reinterpret_cast<const char *>(U);
+  if (g0 < u0 + bytes && u0 < g0 + bytes) return fail(PD_ERR_INVALID_ARG, "U must not alias G");
+  const int64_t l0 = p->ctx.launches;
+  CK(cudaEventRecord(p->ev0, p->ctx.stream));
+  CK(cudaMemcpyAsync(p->mjoin, join, sizeof(int32_t) * p->batch, cudaMemcpyHostToDevice, p->ctx.stream));
+  pd::launch_batch_normalize(p->ctx, G, p->Gs, p->nt, p->batch, (int)p->nxm, p->bnc, p->bpart, p->bex, p->bzero);
+  pd::launch_member_join(p->ctx, U, p->nt, p->batch, (int)p->nxm, p->bex, p->mjoin, p->bzero, p->msw, p->mprev,
+                         p->mref2, p->mex, p->mconv);
+  const int keep_max = p->max_refine;
+  p->max_refine = steps - 1;         // this call's sweeps
+  p->member_solves = keep_max + 1;   // each problem's own limit, counted over calls
+  st = p->precision == PD_FP64 ? solve_continue<double>(p, p->Gs, U) : solve_continue<float>(p, p->Gs, U);
+  p->max_refine = keep_max;
+  p->member_solves = 0;
+  if (st == PD_ERR_CUDA) return st;
+  pd::launch_batch_unscale(p->ctx, U, p->nt, p->batch, (int)p->nxm, p->bex, p->bnx, p->bzero);
+  CK(cudaMemcpyAsync(state, p->mconv, sizeof(int32_t) * p->batch, cudaMemcpyDeviceToHost, p->ctx.stream));
+  CK(cudaEventRecord(p->ev1, p->ctx.stream));
+  CK(cudaEventSynchronize(p->ev1));
+  pd_stats s{};
+  const int *f = p->h_flags;
+  s.refine_sweeps = f[pd::F_SWEEP];
+  s.krylov_iters_total = f[pd::F_MTOT];
+  for (int i = 0; i < s.refine_sweeps && i < 16; ++i) {
+    s.sweep_krylov_iters[i] = f[pd::F_SWM + i];
+    s.sweep_krylov_rel_resnorm[i] = p->h_scal[pd::S_SWRES + i];
+    s.sweep_rel_update[i] = p->h_scal[pd::S_SWUPD + i];
+  }
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, p->ev0, p->ev1);
+  s.ms_total = ms;
+  s.kernel_launches = p->ctx.launches - l0;
+  p->last = s;
+  if (stats) *stats = s;
+  if (st != PD_OK) return st;
+  if (f[pd::F_NONFIN]) return fail(PD_ERR_NONFINITE, "non-finite value met (input contains NaN/Inf?)");
+  return ctx_status(p);
 }
 
 pd_status paradiag_solve_host(pd_plan *p, const double *G_host, double *U_host, pd_stats *stats) {

@@ -232,6 +232,19 @@ class Plan:
         st = B.paradiag_solve(self.handle, G.data_ptr(), U.data_ptr(), allow_not_converged)
         return U, st.as_dict()
 
+    def advance(self, G, U, join, steps=1):
+        """Batched plans: advance every problem by up to `steps` refinement sweeps on U (in
+        place); join[b] starts problem b (its slot of U restarts from zero).  Returns
+        (state per slot: 1 converged, 2 gave up, 0 running; stats dict of this call)."""
+        torch = self._torch
+        shape = (self.nt, self.nbar)
+        self._check(G, torch.float64, shape)
+        self._check(U, torch.float64, shape)
+        if len(join) != self.batch:
+            raise ValueError("join needs one flag per slot")
+        state, st = B.paradiag_batch_advance(self.handle, G.data_ptr(), U.data_ptr(), join, steps)
+        return state, st.as_dict()
+
     def solve_host(self, G_host, U_host, allow_not_converged=False):
         """Host-buffer variant: G_host, U_host are CPU tensors (pinned preferred)."""
         torch = self._torch

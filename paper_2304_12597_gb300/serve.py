@@ -7,8 +7,11 @@ over time.  The scheduler groups the waiting ones into batches, and worker threa
   slot b, zero-padded to the class's n_x);
 - 2D requests with one n_t and grid share a batched plan when the grid has at most 8192
   points (each problem's Algorithm 2 then runs in one CTA); larger grids run one per plan.
-Requests that arrive while batches are running join the next batch as soon as a
-worker and enough device memory are free.  Admission is by an HBM budget that counts
+A batched plan is advanced one refinement sweep at a time (paradiag_batch_advance): between
+sweeps, problems that have converged leave their slots and waiting requests of the same
+shape join the running batch in the free slots (continuous batching); other requests
+start a new batch as soon as a worker and enough device memory are free.  Large 2D
+grids run one per plan, solved whole.  Admission is by an HBM budget that counts
 the workspace, G and U of every batch in flight; idle cached plans (up to
 plan_cache_bytes, half the budget by default) come on top of it, so the service can hold
 about 1.5 times budget_bytes of device memory.
@@ -120,6 +123,16 @@ class Scheduler:
         self.in_flight += need
         return Batch(key, cap, group, need)
 
+    def take(self, key: BatchKey, n: int) -> list:
+        """Up to n waiting requests of `key` in arrival order, removed from the queue (they
+        join a running batch, whose memory is already counted)."""
+        if n <= 0:
+            return []
+        group = [r for r in self.waiting if key_of(r) == key][:n]
+        ids = {id(r) for r in group}
+        self.waiting = [r for r in self.waiting if id(r) not in ids]
+        return group
+
     def release(self, batch: Batch) -> None:
         self.in_flight -= batch.bytes
 
@@ -155,7 +168,7 @@ class Server:
     """Runs a request stream in real time on one GPU with `workers` CUDA streams."""
 
     def __init__(self, device=None, precision="mixed", workers=2, budget_bytes=40 << 30, max_batch=32,
-                 keep_results=False, plan_cache_bytes=None, alpha=1e-4):
+                 keep_results=False, plan_cache_bytes=None, alpha=1e-4, continuous=True):
         import torch
 
         from . import _binding as B
@@ -167,6 +180,8 @@ class Server:
         self.alpha = alpha  # Algorithm 3: slow diffusion (nu ~ 1e-4) needs it (Sec. 4)
         self.workers = workers
         self.keep_results = keep_results
+        # batched plans advance sweep by sweep and take new requests into free slots
+        self.continuous = continuous
         self.plan_cache_bytes = plan_cache_bytes if plan_cache_bytes is not None else budget_bytes // 2
         self._ws_cache: dict = {}
         self.sched = Scheduler(budget_bytes, self._workspace_bytes, max_batch)
@@ -256,13 +271,14 @@ class Server:
 
     @staticmethod
     def _slot_problems(batch: Batch, reqs):
-        """The operators of a batched plan's slots: the requests', then empty slots."""
+        """The operators of a batched plan's slots: the requests' (None: an empty slot),
+        then empty slots."""
         import workloads.serving as S
 
         k = batch.key
-        probs = [S.request_problem_operator_only(r, k.nx) for r in reqs]
-        probs += [S.empty_slot(k.nt, k.nx, k.ny) if k.dim == 2 else S.empty_slot(k.nt)
-                  for _ in range(batch.cap - len(probs))]
+        empty = lambda: S.empty_slot(k.nt, k.nx, k.ny) if k.dim == 2 else S.empty_slot(k.nt)  # noqa: E731
+        probs = [S.request_problem_operator_only(r, k.nx) if r is not None else empty() for r in reqs]
+        probs += [empty() for _ in range(batch.cap - len(probs))]
         return probs
 
     def _run(self, batch: Batch, cache: OrderedDict, stream) -> None:
@@ -305,6 +321,73 @@ class Server:
                 res = host[:, b, : r.nx * r.ny]
                 r.result = (res if self.keep_results == "full" else res[0]).copy()
 
+    def _finish(self, r, host_slot, err, now, occupancy):
+        r.done, r.batch, r.error = now, occupancy, err
+        if host_slot is not None:
+            res = host_slot[:, : r.nx * r.ny]
+            r.result = (res if self.keep_results == "full" else res[-1]).copy()
+
+    def _run_continuous(self, batch: Batch, cache: OrderedDict, stream) -> list:
+        """Advance a batched plan one refinement sweep at a time; converged problems leave
+        and waiting requests of the same key join in the free slots.  Returns every request
+        finished here (the batch's and those that joined it)."""
+        import workloads.serving as S
+
+        torch = self.torch
+        slot, _ = self._slot(cache, batch, stream)
+        key, cap = batch.key, batch.cap
+        width = key.nx * key.ny
+        occ = list(batch.requests) + [None] * (cap - len(batch.requests))
+        finished = []
+        with torch.cuda.stream(stream):
+            plan = slot.plan
+            Gv = slot.G.view(key.nt, cap, width)
+            Uv = slot.U.view(key.nt, cap, width)
+            plan.set_problems(self._slot_problems(batch, occ))
+            slot.G.zero_()
+            for b, r in enumerate(occ):
+                if r is not None:
+                    S.rhs_device(r, torch, self.device, out=Gv[:, b, :])
+            join = [1 if r is not None else 0 for r in occ]
+            while any(r is not None for r in occ):
+                try:
+                    state, _ = plan.advance(slot.G, slot.U, join, steps=1)
+                    err = None
+                except Exception as e:  # a failed call fails the requests in the batch
+                    state, err = [2] * cap, str(e)
+                join = [0] * cap
+                now = time.perf_counter() - self.t0
+                occupancy = sum(r is not None for r in occ)
+                n_before = len(finished)
+                for b, r in enumerate(occ):
+                    if r is None or state[b] == 0:
+                        continue
+                    host = None
+                    if self.keep_results == "full":
+                        host = Uv[:, b, :].cpu().numpy()
+                    elif self.keep_results:
+                        host = Uv[-1:, b, :].cpu().numpy()
+                    self._finish(r, host, err or (None if state[b] == 1 else "refinement did not converge"),
+                                 now, occupancy)
+                    finished.append(r)
+                    occ[b] = None
+                    Gv[:, b, :].zero_()  # the slot is unused from the next sweep
+                free = [b for b, r in enumerate(occ) if r is None]
+                with self.cv:  # finished requests are counted as they finish
+                    new = self.sched.take(key, len(free))
+                    self._done_count[0] += len(finished) - n_before
+                    self.cv.notify_all()
+                if new:
+                    t_join = time.perf_counter() - self.t0
+                    for b, r in zip(free, new):
+                        occ[b] = r
+                        r.start, r.joined_running = t_join, True
+                    plan.set_problems(self._slot_problems(batch, occ))
+                    for b, r in zip(free, new):
+                        S.rhs_device(r, torch, self.device, out=Gv[:, b, :])
+                        join[b] = 1
+        return finished
+
     # -- the run ------------------------------------------------------------------------
     def run(self, requests: list) -> ServeStats:
         torch = self.torch
@@ -313,6 +396,7 @@ class Server:
         pending = list(reqs)
         lock = self.cv
         done_count = [0]
+        self._done_count = done_count
         self.t0 = time.perf_counter()
 
         def feeder():
@@ -338,6 +422,13 @@ class Server:
                 t_start = time.perf_counter() - self.t0
                 for r in batch.requests:
                     r.start = t_start
+                if self.continuous and (batch.key.dim == 1 or batch.cap > 1):
+                    self._run_continuous(batch, cache, stream)  # counts its requests itself
+                    with lock:
+                        self.sched.release(batch)
+                        stats.batches += 1
+                        lock.notify_all()
+                    continue
                 self._run(batch, cache, stream)
                 with lock:
                     self.sched.release(batch)

@@ -1,7 +1,7 @@
 """The solver service on the GPU: requests of mixed kind and size, arriving together,
-are batched and run on two streams; every request's result (its final state u_l)
-must equal the result of the same request solved alone, and the oracle's, within
-the mixed-precision tolerance 1e-10."""
+are batched and run on two streams, and requests join running batches between sweeps;
+every request's result must equal the result of the same request solved alone, and the
+oracle's, within the mixed-precision tolerance 1e-10."""
 import numpy as np
 import pytest
 
@@ -78,3 +78,33 @@ def test_served_2d_requests_share_a_batch(pd):
         ref = R.be_solve_refined(P).reshape(r.result.shape)
         assert _rel(r.result, ref) <= TOL, r.rid
 
+
+
+@pytest.mark.parametrize("kind,side", [("heat1d", 0), ("heat2d", 63)])
+def test_requests_join_a_running_batch(pd, kind, side):
+    """One worker and batches of two: the first two requests start a batch, and the others
+    (same shape, queued behind them) join it as its problems converge and leave, between
+    sweeps, instead of waiting for it to end.  Every trajectory equals its solve alone and
+    the oracle's."""
+    from paper_2304_12597_gb300.serve import Server
+
+    kw = dict(kinds=(kind,), nt_choices=(64,))
+    if kind == "heat2d":
+        kw["sides_2d"] = (side,)
+    else:
+        kw["nx_range"] = (200, 250)
+    reqs = S.request_stream(5, 1e5, seed=41, **kw)
+    server = Server(device="cuda:0", workers=1, max_batch=2, keep_results="full", budget_bytes=8 << 30, alpha=1.0)
+    stats = server.run(reqs)
+    server.close()
+    assert stats.summary()["failed"] == 0, [r.error for r in reqs if r.error]
+    assert stats.batches == 1, stats.batches  # one running batch served all five
+    assert sum(r.joined_running for r in reqs) >= 3  # at most two started it
+    dev = torch.device("cuda:0")
+    for r in reqs:
+        P = S.request_problem(r)
+        with pd.Plan.from_problem(P, precision="mixed", alpha=1.0, device=dev) as plan:
+            U, _ = plan.solve(S.rhs_device(r, torch, dev).contiguous())
+        assert _rel(r.result, U.cpu().numpy().reshape(r.result.shape)) <= 2 * TOL, (r.rid, r.joined_running)
+        ref = R.be_solve_refined(P).reshape(r.result.shape)
+        assert _rel(r.result, ref) <= TOL, r.rid

@@ -124,3 +124,22 @@ def test_scheduler_batches_small_2d_grids_only():
     assert [r.rid for r in b2.requests] == [1] and b2.cap == 1  # 16129 points: one per plan
     b3 = sch.next_batch()
     assert [r.rid for r in b3.requests] == [3] and b3.cap == 1
+
+
+def test_scheduler_take_hands_same_key_requests_to_a_running_batch():
+    """Requests joining a running batch: take(key, n) removes up to n waiting requests of
+    that key, in arrival order, and leaves every other request (and the memory count) as
+    it was."""
+    sched = Scheduler(budget=1 << 40, workspace_bytes=lambda k, c: 1000, max_batch=4)
+    reqs = [_req(0, "heat1d", 200, 64, 0.0), _req(1, "heat1d", 900, 64, 0.1), _req(2, "heat1d", 210, 64, 0.2),
+            _req(3, "heat1d", 220, 64, 0.3), _req(4, "heat1d", 230, 128, 0.4)]
+    for r in reqs:
+        sched.add(r)
+    key = key_of(reqs[0])
+    before = sched.in_flight
+    got = sched.take(key, 2)
+    assert [r.rid for r in got] == [0, 2]
+    assert [r.rid for r in sched.waiting] == [1, 3, 4]
+    assert sched.take(key, 0) == [] and sched.in_flight == before
+    assert [r.rid for r in sched.take(key, 5)] == [3]
+    assert [r.rid for r in sched.waiting] == [1, 4]

@@ -43,6 +43,7 @@ class Request:
     start: Optional[float] = None
     done: Optional[float] = None
     batch: int = 0
+    joined_running: bool = False  # admitted into a batch that was already being solved
     error: Optional[str] = None
     result: Optional[np.ndarray] = None  # final state u_l (n_x * n_y), when kept
 
