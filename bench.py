@@ -603,6 +603,8 @@ def serve_bench(args, device):
     # 2,000 by default (the sweep then takes about a minute)
     rates, n = (100, 300, 1000, 3000, 5000), (10000 if args.serve else 2000)
     out = {"requests_per_rate": n, "workers": 3, "max_batch": 32, "precision": "mixed",
+           "batching": "continuous: batched plans advance one refinement sweep at a time; converged requests "
+                       "leave and waiting requests of the same shape join between sweeps",
            "warm": "each rate after a 300-request warm-up stream through the same server (module loading, "
                    "per-thread state, plan caches)",
            "mix": "1D heat / 1D advection-diffusion n_x in 127..4095, 2D heat side in {63,127,255}, "

@@ -846,12 +846,12 @@ void launch_fft_r2c(Ctx &c, const Tin *X, int64_t ldx, int64_t ncols, int n, con
       if (use_r16<T>(c, n)) {
         const int thr = fft16_threads((kTX / 2) * (n / 16), 512);
         if (smem > 48 * 1024)
-          cudaFuncSetAttribute(k_fft_r2c16<T, Tin, kTX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+          allow_dyn_smem((const void *)k_fft_r2c16<T, Tin, kTX>);
         pdl_launch(c.pdl, k_fft_r2c16<T, Tin, kTX>, dim3(grid), dim3(thr), smem, c.stream, X, ldx, ncols, n, logn, tw,
                    S, lds, rs, rn);
       } else {
         if (smem > 48 * 1024)
-          cudaFuncSetAttribute(k_fft_r2c<T, Tin, kTX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+          allow_dyn_smem((const void *)k_fft_r2c<T, Tin, kTX>);
         pdl_launch(c.pdl, k_fft_r2c<T, Tin, kTX>, dim3(grid), dim3(fft_threads(n, kTX)), smem, c.stream, X, ldx, ncols,
                    n, logn, tw, S, lds, rs, rn);
       }
@@ -872,7 +872,7 @@ void launch_fft_r2c_residual(Ctx &c, const double *G, const double *U, int64_t n
   c.launch(sizeof(T) == 8 ? "fft_r2c_res_f64" : "fft_r2c_res_f32", bytes, [&] {
     PD_TX_DISPATCH(TX, {
       if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_fft_r2c_res<T, kTX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        allow_dyn_smem((const void *)k_fft_r2c_res<T, kTX>);
       pdl_launch(c.pdl, k_fft_r2c_res<T, kTX>, dim3(grid), dim3(fft_threads(n, kTX)), smem, c.stream, G, U, ncols, n,
                  logn, rxl, rxd, rxu, tw, S, lds, rs, mex, mnx, rn);
     })
@@ -897,12 +897,12 @@ void launch_fft_c2r(Ctx &c, const cpx<T> *S, int64_t lds, int64_t ncols, int n, 
       if (use_r16<T>(c, n)) {
         const int thr = fft16_threads((kTX / 2) * (n / 16), 256);
         if (smem > 48 * 1024)
-          cudaFuncSetAttribute(k_fft_c2r<T, kTX, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+          allow_dyn_smem((const void *)k_fft_c2r<T, kTX, true>);
         pdl_launch(c.pdl, k_fft_c2r<T, kTX, true>, dim3(grid), dim3(thr), smem, c.stream, S, lds, ncols, n, logn, tw, out,
                    ldo, mode, norm_part, fin, rsi, colsum, mex, mnx, skip);
       } else {
         if (smem > 48 * 1024)
-          cudaFuncSetAttribute(k_fft_c2r<T, kTX, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+          allow_dyn_smem((const void *)k_fft_c2r<T, kTX, false>);
         pdl_launch(c.pdl, k_fft_c2r<T, kTX, false>, dim3(grid), dim3(256), smem, c.stream, S, lds, ncols, n, logn, tw,
                    out, ldo, mode, norm_part, fin, rsi, colsum, mex, mnx, skip);
       }
@@ -926,14 +926,12 @@ static void dst_launch(Ctx &c, const Tin *X, Tout *Y, int64_t nslab, int64_t ny,
     PD_TX_DISPATCH(TX, {
       if (use_r16<T>(c, N)) {
         if (smem > 48 * 1024)
-          cudaFuncSetAttribute(k_dst_y<Tin, Tout, T, kTX, true, RES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem);
+          allow_dyn_smem((const void *)k_dst_y<Tin, Tout, T, kTX, true, RES>);
         pdl_launch(c.pdl, k_dst_y<Tin, Tout, T, kTX, true, RES>, dim3((unsigned)grid), dim3(256), smem, c.stream, X, Y,
                    ny, nx, N, logN, tw, scale, mode, skip, rin, res_off);
       } else {
         if (smem > 48 * 1024)
-          cudaFuncSetAttribute(k_dst_y<Tin, Tout, T, kTX, false, RES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem);
+          allow_dyn_smem((const void *)k_dst_y<Tin, Tout, T, kTX, false, RES>);
         pdl_launch(c.pdl, k_dst_y<Tin, Tout, T, kTX, false, RES>, dim3((unsigned)grid), dim3(256), smem, c.stream, X,
                    Y, ny, nx, N, logN, tw, scale, mode, skip, rin, res_off);
       }

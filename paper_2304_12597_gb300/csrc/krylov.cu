@@ -793,7 +793,7 @@ constexpr int kClusterSpreadSmem = 120 * 1024;
 int krylov_cluster_size(int want) {
   const void *fn = (const void *)k_arnoldi_coop<kCluster, 1>;
   cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kClusterSpreadSmem);
+  allow_dyn_smem((const void *)fn);
   for (int cl = want; cl >= 4; cl >>= 1) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)cl);
@@ -831,7 +831,7 @@ static void coop_launch(Ctx &c, const char *fam, double bytes, const void *fn_si
                         const void *fn_cluster, int grid, int cluster, void **args) {
   if (grid <= 1 && cluster > 1) {
     cudaFuncSetAttribute(fn_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    cudaFuncSetAttribute(fn_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, kClusterSpreadSmem);
+    allow_dyn_smem((const void *)fn_cluster);
     c.launch(fam, bytes, [&] {
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3((unsigned)cluster);
@@ -918,7 +918,7 @@ void launch_capacitance(Ctx &c, KrylovBufs &k, int nf, double tau, const double2
                         const double2 *gpart, int nblk, double *msys_part, int k5_grid, double2 *srow,
                         double2 *omega, double *y, int members, int bpm, double2 *sinv) {
   const size_t smem = k5a_warp_bytes(k.maxit) * kK5Warps;  // sized for the largest m
-  cudaFuncSetAttribute(k_capacitance_terms, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  allow_dyn_smem((const void *)k_capacitance_terms);
   c.launch("capacitance", (double)nf * nblk * 16, [&] {
     pdl_launch(c.pdl, k_capacitance_terms, dim3(k5_grid, members ? members : 1), dim3(kK5Warps * 32), smem,
                c.stream, nf, k.maxit, tau, (const double *)k.T, shift, wg, gpart, nblk, msys_part, srow,
@@ -969,10 +969,8 @@ static const void *step_tail_pick(int nv, int E, int elem_bytes) {
 
 int step_tail_max_grid(int nv, int E, int elem_bytes, size_t smem) {
   const void *fn = step_tail_pick(nv, E, elem_bytes);
-  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-    cudaGetLastError();
-    return 0;
-  }
+  if (smem > smem_optin()) return 0;
+  allow_dyn_smem(fn);
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlasSingle, smem) != cudaSuccess) {
     cudaGetLastError();
@@ -984,7 +982,7 @@ int step_tail_max_grid(int nv, int E, int elem_bytes, size_t smem) {
 template <typename T>
 void launch_step_tail(Ctx &c, const StepArgs<T> &a0, int grid, int E) {
   const void *fn = step_tail_pick(a0.nv, E, (int)sizeof(T));
-  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a0.smem);
+  allow_dyn_smem((const void *)fn);
   StepArgs<T> a = a0;
   void *args[] = {&a};
   // algorithmic bytes: the stored h_k read once by the z sum

@@ -976,7 +976,7 @@ void launch_zsum(Ctx &c, int nf, int64_t n, const cpx<T> *H, int64_t ldh, const 
     } else {
       const int grid = (int)((n + 7) / 8);
       if (smem > 48 * 1024)
-        cudaFuncSetAttribute(k_zsum<T, 8, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        allow_dyn_smem((const void *)k_zsum<T, 8, 64>);
       pdl_launch(c.pdl, k_zsum<T, 8, 64>, dim3(grid), dim3(512), smem, c.stream, nf, n, H, ldh, omega, z,
                  skip_flag, tail, mlen, h0);
     }
@@ -1038,7 +1038,7 @@ static void launch_pint_m(Ctx &c, const PintGeom &g, const PintArgs<T> &a) {
   const int threads = g.P * g.teams_per_cta;
   auto kern = a.fac_in ? (threads <= 256 ? k_pint<T, M, 256, true> : k_pint<T, M, (M >= 16 ? 256 : 512), true>)
                        : (threads <= 256 ? k_pint<T, M, 256, false> : k_pint<T, M, (M >= 16 ? 256 : 512), false>);
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  allow_dyn_smem((const void *)kern);
   // algorithmic bytes: spectrum rows read/written as requested, plus the vector rhs
   double bytes = 0.0;
   const double per = (double)g.nf * g.nblk * g.blen;

@@ -89,6 +89,10 @@ size_t smem_optin() {
   return (size_t)v;
 }
 
+void allow_dyn_smem(const void *fn) {
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_optin());
+}
+
 int Ctx::family(const char *name) {
   for (size_t i = 0; i < fams.size(); ++i)
     if (fams[i].name == name) return (int)i;
@@ -1863,6 +1867,7 @@ pd_status paradiag_destroy(pd_plan *p) {
 }
 
 pd_status paradiag_solve(pd_plan *p, const double *G, double *U, pd_stats *stats) {
+  cudaGetLastError();  // an error an earlier call of this thread left is not this call's
   pd_status st = check_plan(p);
   if (st != PD_OK) return st;
   if (!G || !U) return fail(PD_ERR_INVALID_ARG, "G and U must be device pointers");
@@ -1902,6 +1907,7 @@ pd_status paradiag_solve(pd_plan *p, const double *G, double *U, pd_stats *stats
 
 pd_status paradiag_batch_advance(pd_plan *p, const double *G, double *U, const int32_t *join, int32_t steps,
                                  int32_t *state, pd_stats *stats) {
+  cudaGetLastError();  // an error an earlier call of this thread left is not this call's
   pd_status st = check_plan(p);
   if (st != PD_OK) return st;
   if (p->batch < 2) return fail(PD_ERR_INVALID_ARG, "paradiag_batch_advance needs a batched plan");

@@ -152,11 +152,12 @@ class ServeStats:
     batches: int = 0
     elapsed_s: float = 0.0
     unknowns: int = 0
+    joined: int = 0  # requests admitted into a batch that was already running
     latencies_ms: list = field(default_factory=list)
 
     def summary(self) -> dict:
         lat = np.array(self.latencies_ms) if self.latencies_ms else np.zeros(1)
-        return {"requests": self.requests, "failed": self.failed, "batches": self.batches,
+        return {"requests": self.requests, "failed": self.failed, "batches": self.batches, "joined_running": self.joined,
                 "mean_batch": self.requests / max(self.batches, 1), "elapsed_s": self.elapsed_s,
                 "solves_per_s": self.requests / max(self.elapsed_s, 1e-9),
                 "unknowns_per_s": self.unknowns / max(self.elapsed_s, 1e-9),
@@ -289,31 +290,32 @@ class Server:
         reqs = batch.requests
         batched = batch.key.dim == 1 or batch.cap > 1
         width = batch.key.nx * batch.key.ny  # unknowns per slot
+        host = None
         with torch.cuda.stream(stream):
-            if batched:
-                if not fresh:
-                    slot.plan.set_problems(self._slot_problems(batch, reqs))
-                slot.G.zero_()
-                Gv = slot.G.view(batch.key.nt, batch.cap, width)
-                for b, r in enumerate(reqs):
-                    S.rhs_device(r, torch, self.device, out=Gv[:, b, :])
-            else:
-                r0 = reqs[0]
-                if not fresh:
-                    kx, ky = S.operator(r0)
-                    slot.plan.set_operator(tau=r0.tau, k_lo=kx[0], k_diag=kx[1], k_up=kx[2], k_lo_y=ky[0],
-                                           k_diag_y=ky[1], k_up_y=ky[2])
-                S.rhs_device(r0, torch, self.device, out=slot.G)
-            try:
+            try:  # a failed solve fails its requests, not the service
+                if batched:
+                    if not fresh:
+                        slot.plan.set_problems(self._slot_problems(batch, reqs))
+                    slot.G.zero_()
+                    Gv = slot.G.view(batch.key.nt, batch.cap, width)
+                    for b, r in enumerate(reqs):
+                        S.rhs_device(r, torch, self.device, out=Gv[:, b, :])
+                else:
+                    r0 = reqs[0]
+                    if not fresh:
+                        kx, ky = S.operator(r0)
+                        slot.plan.set_operator(tau=r0.tau, k_lo=kx[0], k_diag=kx[1], k_up=kx[2], k_lo_y=ky[0],
+                                               k_diag_y=ky[1], k_up_y=ky[2])
+                    S.rhs_device(r0, torch, self.device, out=slot.G)
                 slot.plan.solve(slot.G, slot.U)
                 err = None
-            except Exception as e:  # a failed solve fails its requests, not the service
+                if self.keep_results == "full":  # the whole trajectory U (nt, n_bar) of each request
+                    host = slot.U.view(batch.key.nt, batch.cap, width).cpu().numpy()
+                elif self.keep_results:  # the final state u_l of each request
+                    host = slot.U[-1].view(1, batch.cap, width).cpu().numpy()
+            except Exception as e:
                 err = str(e)
-            host = None
-            if self.keep_results == "full":  # the whole trajectory U (nt, n_bar) of each request
-                host = slot.U.view(batch.key.nt, batch.cap, width).cpu().numpy()
-            elif self.keep_results:  # the final state u_l of each request
-                host = slot.U[-1].view(1, batch.cap, width).cpu().numpy()
+                self._drop_plan(cache, batch)
         now = time.perf_counter() - self.t0
         for b, r in enumerate(reqs):
             r.done, r.batch, r.error = now, len(reqs), err
@@ -327,65 +329,92 @@ class Server:
             res = host_slot[:, : r.nx * r.ny]
             r.result = (res if self.keep_results == "full" else res[-1]).copy()
 
+    def _drop_plan(self, cache: OrderedDict, batch: Batch) -> None:
+        """Forget a cached plan after an error (it may be unusable)."""
+        slot = cache.pop((batch.key, batch.cap), None)
+        if slot is not None:
+            try:
+                slot.plan.close()
+            except Exception:
+                pass
+
     def _run_continuous(self, batch: Batch, cache: OrderedDict, stream) -> list:
         """Advance a batched plan one refinement sweep at a time; converged problems leave
         and waiting requests of the same key join in the free slots.  Returns every request
-        finished here (the batch's and those that joined it)."""
+        finished here (the batch's and those that joined it), each counted once as done."""
         import workloads.serving as S
 
         torch = self.torch
-        slot, _ = self._slot(cache, batch, stream)
         key, cap = batch.key, batch.cap
         width = key.nx * key.ny
         occ = list(batch.requests) + [None] * (cap - len(batch.requests))
-        finished = []
-        with torch.cuda.stream(stream):
-            plan = slot.plan
-            Gv = slot.G.view(key.nt, cap, width)
-            Uv = slot.U.view(key.nt, cap, width)
-            plan.set_problems(self._slot_problems(batch, occ))
-            slot.G.zero_()
-            for b, r in enumerate(occ):
-                if r is not None:
-                    S.rhs_device(r, torch, self.device, out=Gv[:, b, :])
-            join = [1 if r is not None else 0 for r in occ]
-            while any(r is not None for r in occ):
-                try:
-                    state, _ = plan.advance(slot.G, slot.U, join, steps=1)
-                    err = None
-                except Exception as e:  # a failed call fails the requests in the batch
-                    state, err = [2] * cap, str(e)
-                join = [0] * cap
-                now = time.perf_counter() - self.t0
-                occupancy = sum(r is not None for r in occ)
-                n_before = len(finished)
+        finished, counted = [], [0]
+
+        def count():  # finished requests are counted as they finish
+            with self.cv:
+                self._done_count[0] += len(finished) - counted[0]
+                counted[0] = len(finished)
+                self.cv.notify_all()
+
+        try:
+            slot, _ = self._slot(cache, batch, stream)
+            with torch.cuda.stream(stream):
+                plan = slot.plan
+                Gv = slot.G.view(key.nt, cap, width)
+                Uv = slot.U.view(key.nt, cap, width)
+                plan.set_problems(self._slot_problems(batch, occ))
+                slot.G.zero_()
                 for b, r in enumerate(occ):
-                    if r is None or state[b] == 0:
-                        continue
-                    host = None
-                    if self.keep_results == "full":
-                        host = Uv[:, b, :].cpu().numpy()
-                    elif self.keep_results:
-                        host = Uv[-1:, b, :].cpu().numpy()
-                    self._finish(r, host, err or (None if state[b] == 1 else "refinement did not converge"),
-                                 now, occupancy)
-                    finished.append(r)
-                    occ[b] = None
-                    Gv[:, b, :].zero_()  # the slot is unused from the next sweep
-                free = [b for b, r in enumerate(occ) if r is None]
-                with self.cv:  # finished requests are counted as they finish
-                    new = self.sched.take(key, len(free))
-                    self._done_count[0] += len(finished) - n_before
-                    self.cv.notify_all()
-                if new:
-                    t_join = time.perf_counter() - self.t0
-                    for b, r in zip(free, new):
-                        occ[b] = r
-                        r.start, r.joined_running = t_join, True
-                    plan.set_problems(self._slot_problems(batch, occ))
-                    for b, r in zip(free, new):
+                    if r is not None:
                         S.rhs_device(r, torch, self.device, out=Gv[:, b, :])
-                        join[b] = 1
+                join = [1 if r is not None else 0 for r in occ]
+                while any(r is not None for r in occ):
+                    try:
+                        state, _ = plan.advance(slot.G, slot.U, join, steps=1)
+                        err = None
+                    except Exception as e:  # a failed call fails the requests in the batch
+                        state, err = [2] * cap, str(e)
+                    join = [0] * cap
+                    now = time.perf_counter() - self.t0
+                    occupancy = sum(r is not None for r in occ)
+                    for b, r in enumerate(occ):
+                        if r is None or state[b] == 0:
+                            continue
+                        host = None
+                        if err is None and self.keep_results == "full":
+                            host = Uv[:, b, :].cpu().numpy()
+                        elif err is None and self.keep_results:
+                            host = Uv[-1:, b, :].cpu().numpy()
+                        self._finish(r, host, err or (None if state[b] == 1 else "refinement did not converge"),
+                                     now, occupancy)
+                        finished.append(r)
+                        occ[b] = None
+                        Gv[:, b, :].zero_()  # the slot is unused from the next sweep
+                    if err is not None:
+                        self._drop_plan(cache, batch)
+                        break
+                    free = [b for b, r in enumerate(occ) if r is None]
+                    with self.cv:
+                        new = self.sched.take(key, len(free))
+                    count()
+                    if new:
+                        t_join = time.perf_counter() - self.t0
+                        for b, r in zip(free, new):
+                            occ[b] = r
+                            r.start, r.joined_running = t_join, True
+                        plan.set_problems(self._slot_problems(batch, occ))
+                        for b, r in zip(free, new):
+                            S.rhs_device(r, torch, self.device, out=Gv[:, b, :])
+                            join[b] = 1
+        except Exception as e:  # the service keeps running; this batch's requests fail
+            now = time.perf_counter() - self.t0
+            done = {id(r) for r in finished}
+            for r in occ:
+                if r is not None and id(r) not in done:
+                    self._finish(r, None, f"service: {e}", now, 0)
+                    finished.append(r)
+            self._drop_plan(cache, batch)
+        count()
         return finished
 
     # -- the run ------------------------------------------------------------------------
@@ -429,7 +458,11 @@ class Server:
                         stats.batches += 1
                         lock.notify_all()
                     continue
-                self._run(batch, cache, stream)
+                try:
+                    self._run(batch, cache, stream)
+                except Exception as e:  # (plan creation failed) the service keeps running
+                    for r in batch.requests:
+                        r.done, r.error = time.perf_counter() - self.t0, f"service: {e}"
                 with lock:
                     self.sched.release(batch)
                     done_count[0] += len(batch.requests)
@@ -448,6 +481,7 @@ class Server:
         for r in reqs:
             stats.requests += 1
             stats.failed += 1 if r.error else 0
+            stats.joined += 1 if r.joined_running else 0
             stats.unknowns += r.unknowns
             stats.latencies_ms.append((r.done - r.arrival) * 1e3)
         return stats
