@@ -969,8 +969,7 @@ static const void *step_tail_pick(int nv, int E, int elem_bytes) {
 
 int step_tail_max_grid(int nv, int E, int elem_bytes, size_t smem) {
   const void *fn = step_tail_pick(nv, E, elem_bytes);
-  if (smem > smem_optin()) return 0;
-  allow_dyn_smem(fn);
+  if ((int64_t)smem > (int64_t)allow_dyn_smem(fn)) return 0;
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlasSingle, smem) != cudaSuccess) {
     cudaGetLastError();

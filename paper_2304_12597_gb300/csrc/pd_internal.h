@@ -123,11 +123,12 @@ struct Ctx {
 
 int sm_count();
 size_t smem_optin();
-// Lets kernel fn take up to smem_optin() bytes of dynamic shared memory per CTA.  Every
-// call sets the same value: host threads that launch one kernel with different shared-
-// memory sizes (plans solved concurrently with host-driven loops) cannot lower the limit
-// another thread needs between its setting and its launch.
-void allow_dyn_smem(const void *fn);
+// Lets kernel fn take as much dynamic shared memory per CTA as its static arrays leave of
+// smem_optin(); returns that limit (0 if it could not be set).  The value is the same for
+// every call (set once per kernel): host threads that launch one kernel with different
+// shared-memory sizes (plans solved concurrently with host-driven loops) cannot lower the
+// limit another thread needs between its setting and its launch.
+int allow_dyn_smem(const void *fn);
 // Sets the thread-local message returned by paradiag_last_error().
 void set_last_error(const char *msg);
 

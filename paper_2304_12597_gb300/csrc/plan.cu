@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <unordered_map>
 #include <string>
 #include <vector>
 
@@ -89,8 +90,26 @@ size_t smem_optin() {
   return (size_t)v;
 }
 
-void allow_dyn_smem(const void *fn) {
-  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_optin());
+int allow_dyn_smem(const void *fn) {
+  // the opt-in limit covers static and dynamic shared memory together: a kernel's limit is
+  // what its static arrays leave (one value per kernel, set once)
+  static std::mutex mu;
+  static std::unordered_map<const void *, int> done;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = done.find(fn);
+  if (it != done.end()) return it->second;
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {
+    cudaGetLastError();  // leave no error for the next launch to pick up
+    return 0;
+  }
+  const int lim = (int)smem_optin() - (int)fa.sharedSizeBytes;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  done[fn] = lim;
+  return lim;
 }
 
 int Ctx::family(const char *name) {
@@ -1543,7 +1562,7 @@ cudaError_t build_graph(pd_plan *p, const double *G, double *U, cudaGraph_t *gou
     pd::launch_solve_reset(p->ctx, p->scal, p->flags);
     if (emit_pre<T>(p, 0, G, U, 1, hk0) != PD_OK) { err = cudaErrorUnknown; break; }
     p->seg.pre0 = p->ctx.launches - l0;
-    cudaGraph_t body;
+    cudaGraph_t body = nullptr;
     if ((err = splice_while(s0, hk0, &body)) != cudaSuccess) break;
     l0 = p->ctx.launches;
     if ((err = capture_iter_body<T>(p, body, s1, 0, hk0)) != cudaSuccess) break;
@@ -1552,7 +1571,7 @@ cudaError_t build_graph(pd_plan *p, const double *G, double *U, cudaGraph_t *gou
     l0 = p->ctx.launches;
     if (emit_post<T>(p, 0, U, 1, hR) != PD_OK) { err = cudaErrorUnknown; break; }
     p->seg.post0 = p->ctx.launches - l0;
-    cudaGraph_t bodyR;
+    cudaGraph_t bodyR = nullptr;
     if ((err = splice_while(s0, hR, &bodyR)) != cudaSuccess) break;
     if ((err = cudaGraphConditionalHandleCreate(&hk1, bodyR, 1, cudaGraphCondAssignDefault)) != cudaSuccess) break;
     // refinement body: pre(1), WHILE_k1 { iter(1) }, post(1), captured on s1
@@ -1563,7 +1582,7 @@ cudaError_t build_graph(pd_plan *p, const double *G, double *U, cudaGraph_t *gou
     l0 = p->ctx.launches;
     bool ok = emit_pre<T>(p, 1, G, U, 1, hk1) == PD_OK;
     p->seg.pre1 = p->ctx.launches - l0;
-    cudaGraph_t body1;
+    cudaGraph_t body1 = nullptr;
     if (ok) ok = splice_while(s1, hk1, &body1) == cudaSuccess;
     l0 = p->ctx.launches;
     if (ok) ok = capture_iter_body<T>(p, body1, s2, 1, hk1) == cudaSuccess;
