@@ -259,6 +259,20 @@ def time_steps(plan, G, U, steps, stream, flush, torch):
     return ts, launches, st
 
 
+def work_bytes(kt, st):
+    """Algorithmic bytes of the work done.  The final loop's shifted-solve launches return at
+    once in the solves that form it by linearity, and the elementwise pass does its work only
+    in those (every timed solve takes the same path): scale both families' recorded bytes by
+    the share of solves that took each path."""
+    lin = st["final_by_linearity"] / max(st["refine_sweeps"], 1)
+    for r in kt:
+        if r["name"].startswith("pint_store"):
+            r["bytes"] *= 1.0 - lin
+        elif r["name"] == "final_comb":
+            r["bytes"] *= lin
+    return kt
+
+
 def kernel_roofline(plan, G, U, flush, workload_name, nk):
     """Per-kernel CUDA-event timing pass on the plan's stream (host-driven loops, one event
     pair per launch), and the roofline of the kernel family that takes the largest share."""
@@ -268,15 +282,7 @@ def kernel_roofline(plan, G, U, flush, workload_name, nk):
         _, st = plan.solve(G, U)
     kt = plan.kernel_times()
     plan.set_timing(False)
-    # the final loop's launches return at once in the solves that form it by linearity, and
-    # the elementwise pass does its work only in those: algorithmic bytes of the work done
-    # (every timed solve takes the same path)
-    lin = st["final_by_linearity"] / max(st["refine_sweeps"], 1)
-    for r in kt:
-        if r["name"].startswith("pint_store"):
-            r["bytes"] *= 1.0 - lin
-        elif r["name"] == "final_comb":
-            r["bytes"] *= lin
+    work_bytes(kt, st)
     by_kernel = {}
     for r in kt:
         k = by_kernel.setdefault(KERNEL_OF.get(r["name"], r["name"]), {"launches": 0, "total_ms": 0.0, "bytes": 0.0})

@@ -36,3 +36,20 @@ def test_oracle_all_cores_counts_independent_solves():
     r = bench.oracle_all_cores(P, "tiny", 0.2)
     assert r["cores"] == (os.cpu_count() or 1)
     assert r["value"] > 0 and r["unit"] == bench.UNIT
+
+
+def test_work_bytes_counts_only_the_final_loop_path_taken():
+    """Solves that form the final loop by linearity skip the shifted solves of the final
+    pass (their launches do no work) and run the elementwise pass; the others the reverse."""
+    import bench
+
+    def table():
+        return [{"name": "pint_store_f32", "bytes": 100.0}, {"name": "final_comb", "bytes": 60.0},
+                {"name": "pint_dots_f32", "bytes": 10.0}]
+
+    all_lin = bench.work_bytes(table(), {"final_by_linearity": 4, "refine_sweeps": 4})
+    assert [r["bytes"] for r in all_lin] == [0.0, 60.0, 10.0]
+    none = bench.work_bytes(table(), {"final_by_linearity": 0, "refine_sweeps": 3})
+    assert [r["bytes"] for r in none] == [100.0, 0.0, 10.0]
+    half = bench.work_bytes(table(), {"final_by_linearity": 1, "refine_sweeps": 2})
+    assert [r["bytes"] for r in half] == [50.0, 30.0, 10.0]
